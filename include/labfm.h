@@ -1,0 +1,233 @@
+/*
+ * labfm.h -- C ABI of the GB300 (sm_103a) LABFM hot path.
+ *
+ * LABFM (local anisotropic basis function method) for the isothermal
+ * compressible Navier-Stokes equations, after King & Lind, "High-order
+ * simulations of isothermal flows using the local anisotropic basis function
+ * method (LABFM)".  Section numbers and equation labels below refer to that
+ * paper.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named as device buffers are caller-owned CUDA device memory; the
+ *    library never frees them.  Host pointers are marked "host".
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    All device work is ordered on that stream; calls return after enqueueing
+ *    unless a comment says the call synchronises.
+ *  - Return value: LABFM_OK (0) or a labfm_status error code.  No call aborts,
+ *    traps or throws.  labfm_last_error() returns a thread-local message for the
+ *    most recent failing call on this thread.
+ *  - Node arrays are indexed 0..N-1.  Fields are structure-of-arrays, "3 x N":
+ *    field f of node i at [f * N + i], f = 0 (ln rho), 1 (u), 2 (v).
+ *  - Operator order in every weight array (Section 2, selector C^d):
+ *    0: d/dx, 1: d/dy, 2: d2/dx2, 3: d2/dxdy, 4: d2/dy2, 5: hyperviscous nabla^m.
+ */
+#ifndef LABFM_H
+#define LABFM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum labfm_status {
+    LABFM_OK = 0,
+    LABFM_EINVAL = 1,      /* bad argument (null pointer, size, order, alignment) */
+    LABFM_ECUDA = 2,       /* a CUDA runtime call or launch failed */
+    LABFM_ENOMEM = 3,      /* device allocation failed */
+    LABFM_ECAPACITY = 4,   /* output buffer too small (required size reported) */
+    LABFM_ESINGULAR = 5,   /* at least one node's moment matrix is singular */
+    LABFM_ENONFINITE = 6,  /* a non-finite value was produced */
+    LABFM_ETIMEOUT = 7     /* a bounded device-side wait ran out */
+} labfm_status;
+
+typedef enum labfm_dtype {
+    LABFM_F64 = 0,  /* fields and weights in double precision */
+    LABFM_F32 = 1   /* fields in float, weights in float nondimensionalised by s_i^l */
+} labfm_dtype;
+
+/* Per-node flags written by labfm_build_weights into node_status. */
+#define LABFM_NODE_FEW_NEIGHBOURS 1  /* fewer stencil nodes than unknowns n */
+#define LABFM_NODE_SINGULAR 2        /* zero or non-finite pivot in the LU */
+#define LABFM_NODE_NONFINITE 4       /* non-finite weight or filter coefficient */
+
+/* Physical constants of the isothermal equations (Section 7, eq. icns):
+ * c2 = c^2 (speed of sound squared), mu = dynamic viscosity, (gx, gy) = body force. */
+typedef struct labfm_phys {
+    double c2;
+    double mu;
+    double gx;
+    double gy;
+} labfm_phys;
+
+/* An operator prepared for the time-step kernels (opaque). */
+typedef struct labfm_plan labfm_plan;
+
+typedef struct labfm_plan_info {
+    int64_t N;          /* nodes */
+    int64_t nnz;        /* stencil entries (unpadded) */
+    int64_t nnz_padded; /* entries after padding each row to a multiple of 4 */
+    int32_t dtype;      /* labfm_dtype */
+    int32_t group;      /* lanes per node in the gather kernels */
+    int32_t block;      /* threads per block in the gather kernels */
+    int32_t reserved;
+    int64_t device_bytes; /* device memory owned by the plan */
+} labfm_plan_info;
+
+/* Message for the most recent failing call on this thread ("" if none). */
+const char* labfm_last_error(void);
+
+/* ABI version of this header (incremented on incompatible changes). */
+int labfm_abi_version(void);
+
+/*
+ * Neighbour search (Section 2): the stencil of node i is every node j != i with
+ * |r_j - r_i|^2 <= (2 h_i)^2, tested exactly in FP64 (products and sums rounded
+ * separately, no fused multiply-add) on the periodic minimum image
+ * dx = x_j - x_i; dx -= Lx if dx > Lx/2; dx += Lx if dx < -Lx/2 (same in y).
+ *
+ *   xy        device, N x 2 doubles (x_i, y_i) row-major; 0 <= x < Lx, 0 <= y < Ly
+ *   h         device, N doubles, stencil scale h_i > 0
+ *   periodic_mask  bit 0: x periodic, bit 1: y periodic
+ *   row_ptr   device, N + 1 int32 (output): row i is col[row_ptr[i] .. row_ptr[i+1])
+ *   col       device, col_capacity int32 (output), each row sorted by ascending j;
+ *             may be NULL with col_capacity = 0 to query the size
+ *   nnz_out   host (output): number of stencil entries
+ *
+ * Uses a uniform cell list built in stream-ordered scratch memory that the call
+ * allocates and frees itself.  Synchronises `stream` once (to read nnz).
+ * Errors: EINVAL (bad sizes, node outside the box, N >= 2^31), ECAPACITY
+ * (col_capacity < nnz; nnz_out holds the required size, row_ptr is valid),
+ * ECAPACITY also if nnz >= 2^31.
+ */
+int labfm_build_stencils(const double* xy, const double* h, int64_t N, double Lx, double Ly,
+                         uint32_t periodic_mask, int32_t* row_ptr, int32_t* col,
+                         int64_t col_capacity, int64_t* nnz_out, void* stream);
+
+/*
+ * Weight build (Sections 2, 3 and 6), FP64 throughout.  For every node i:
+ *   X~_ji = X_ji . H_i  (monomials (x/h)^a (y/h)^b / (a! b!), eq. X and vector H)
+ *   W^q_ji = psi(|r_ji|/h_i) H_a(x_ji/(h_i sqrt2)) H_b(y_ji/(h_i sqrt2)) / sqrt(2^(a+b))
+ *            (eq. hermite; psi = Wendland C2, (1 - q/2)^4 (1 + 2q) on q <= 2)
+ *   M_i = sum_j X~_ji (x) W_ji                              (eq. disc_form)
+ *   M_i Psi^d = C~^d by LU with partial pivoting           (eq. lsys)
+ *   w^d_ji = W_ji . Psi^d                                   (eq. w_abf)
+ *   F_0,i = sum_j phi_ji w^hyp_ji, kappa_i = 2 / (3 F_0,i)   (Section 6)
+ * for the six operators listed at the top of this file (m even for the filter).
+ *
+ *   xy, h, s  device, N x 2 / N / N doubles; s_i is the node spacing (Section 2)
+ *   row_ptr, col  device CSR from labfm_build_stencils (nnz entries)
+ *   m         order of polynomial reproduction, even, 2 <= m <= 10
+ *   w         device, 6 x nnz doubles (output), operator-major: w[d * nnz + e]
+ *   kappa     device, N doubles (output): filter coefficient kappa_i
+ *   residual  device, N doubles (output, may be NULL): max over operators and
+ *             monomials of |sum_j X~_ji w_ji h^l - C^d| (nondimensional
+ *             reproduction residual, l = derivative order)
+ *   node_status device, N int32 (output): OR of LABFM_NODE_* flags, 0 = good
+ *   n_failed_out host (output, may be NULL): number of nodes with a nonzero status;
+ *             when non-NULL the call synchronises `stream`
+ * Errors: EINVAL (sizes, m), ESINGULAR (n_failed_out requested and > 0; the
+ * outputs of the good nodes are still valid).
+ */
+int labfm_build_weights(const double* xy, const double* h, const double* s, int64_t N,
+                        double Lx, double Ly, uint32_t periodic_mask,
+                        const int32_t* row_ptr, const int32_t* col, int64_t nnz, int m,
+                        double* w, double* kappa, double* residual, int32_t* node_status,
+                        int64_t* n_failed_out, void* stream);
+
+/*
+ * Prepare an operator for the time-step kernels: rows padded to a multiple of
+ * four entries (pad entries point at the node itself with weight 0, which adds
+ * exactly zero in the difference form of eq. general_do), the five RHS weight
+ * streams and the filter stream (kappa_i w^hyp_ji) packed operator-major in
+ * `dtype`.  For LABFM_F32 the RHS weights are stored nondimensionalised,
+ * w^d_ji s_i^l (l = 1 for d/dx, d/dy; 2 for second derivatives), and the kernels
+ * multiply the sums by s_i^-l.
+ *
+ *   w      device, 6 x nnz doubles as written by labfm_build_weights
+ *   kappa  device, N doubles
+ *   s      device, N doubles (node spacing)
+ * The plan allocates and owns its device memory (cudaMalloc); the input
+ * buffers may be freed after the call returns.  Synchronises `stream`.
+ * Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int labfm_plan_create(labfm_plan** plan, int64_t N, int64_t nnz, labfm_dtype dtype,
+                      const int32_t* row_ptr, const int32_t* col, const double* w,
+                      const double* kappa, const double* s, void* stream);
+
+/* Free a plan and its device memory (synchronises the device first). NULL is a no-op. */
+int labfm_plan_destroy(labfm_plan* plan);
+
+/* Describe a plan (host output). */
+int labfm_plan_get_info(const labfm_plan* plan, labfm_plan_info* info);
+
+/*
+ * Override the gather launch shape: `group` lanes per node (4, 8, 16 or 32) and
+ * `block` threads per block (a multiple of 32 and of group, 64..1024).  The
+ * defaults come from labfm_plan_create; labfm_plan_autotune picks the fastest.
+ */
+int labfm_plan_set_launch(labfm_plan* plan, int group, int block);
+
+/*
+ * Time every supported (group, block) pair on this plan with CUDA events
+ * (the RHS kernel on `fields`, `reps` launches each) and keep the fastest.
+ * Writes the chosen pair to *group_out / *block_out (host, may be NULL).
+ * Synchronises `stream`.
+ */
+int labfm_plan_autotune(labfm_plan* plan, const void* fields, void* scratch_rhs,
+                        const labfm_phys* phys, int reps, int* group_out, int* block_out,
+                        void* stream);
+
+/*
+ * Right-hand side of eq. icns in (ln rho, u, v) (Section 7):
+ *   R_a = -(u a_x + v a_y) - (u_x + v_y)
+ *   R_u = -(u u_x + v u_y) - c^2 a_x + mu e^-a (4/3 u_xx + u_yy + 1/3 v_xy) + g_x
+ *   R_v = -(u v_x + v v_y) - c^2 a_y + mu e^-a (4/3 v_yy + v_xx + 1/3 u_xy) + g_y
+ * with every derivative L^d_i(phi) = sum_j (phi_j - phi_i) w^d_ji (eq. general_do).
+ *   fields  device, 3 x N in the plan's dtype
+ *   rhs     device, 3 x N in the plan's dtype (output; must not alias fields)
+ *   phys    host
+ */
+int labfm_rhs(const labfm_plan* plan, const void* fields, void* rhs, const labfm_phys* phys,
+              void* stream);
+
+/*
+ * Filter (Section 6): phi~_i = phi_i + kappa_i sum_j (phi_j - phi_i) w^hyp_ji for
+ * ln rho, u and v, reading only `in` (every node sees its neighbours' unfiltered
+ * values).  in/out device, 3 x N in the plan's dtype; out must not alias in.
+ */
+int labfm_filter(const labfm_plan* plan, const void* in, void* out, void* stream);
+
+/* Bytes of device workspace labfm_rk_step needs for this plan. */
+size_t labfm_rk_workspace_bytes(const labfm_plan* plan);
+
+/*
+ * `nsteps` complete time steps (Section 7): each is the four stages of the
+ * low-storage RK3(2)4[2R+]C scheme with registers (Q, X),
+ *   X = Q; for k = 1..4: F = R(X); Q += dt b_k F; X = Q + dt (a_{k+1,k} - b_k) F,
+ * fused into one gather kernel per stage (F is never stored), followed by the
+ * filter on ln rho, u, v.
+ *   Q     device, 3 x N in the plan's dtype: initial state in, final state out
+ *   work  device, labfm_rk_workspace_bytes(plan) bytes, 16-byte aligned
+ *   dt    time step (see labfm_stable_dt); nsteps >= 0
+ * Capturable in a CUDA graph (no allocation, no synchronisation).
+ */
+int labfm_rk_step(const labfm_plan* plan, void* Q, void* work, size_t work_bytes, double dt,
+                  int nsteps, const labfm_phys* phys, void* stream);
+
+/*
+ * Time step of eq. dt: min over nodes of min(1.0 s_i / (|u_i| + c), 0.4 s_i^2 rho_i / mu),
+ * rho_i = exp(ln rho_i), computed exactly as a minimum (order independent).
+ *   fields  device, 3 x N in the plan's dtype
+ *   s       device, N doubles
+ *   dt_out  device, one double (output)
+ */
+int labfm_stable_dt(const labfm_plan* plan, const void* fields, const double* s, double c,
+                    double mu, double* dt_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LABFM_H */

@@ -1,0 +1,198 @@
+"""Seeded synthetic inputs shared by the oracle tests, the GPU tests and the benchmark.
+
+This module only draws node sets and initial fields.  It holds none of the
+LABFM arithmetic (no basis functions, no weights, no derivative operators):
+both the CPU oracle and the CUDA path consume what it returns.
+
+Workloads (all doubly periodic, unit square unless stated):
+
+* ``tgv_lattice(nx, ...)``: the jittered Cartesian node set of the paper's
+  uniform-resolution tests (Section 5: a lattice with spacing s, every node
+  shifted by a random vector), node ``(ix, iy)`` at
+  ``((ix + 0.5 + U[-j, j]) s, (iy + 0.5 + U[-j, j]) s)`` with ``j = 0.3``.
+  Nodes are numbered row by row (x fastest).
+* ``varres_columns(s0, ...)``: variable resolution ``s(x) = s0 (1 + 1.5 sin^2(pi x))``
+  built from periodic columns; each node's stencil scale gets a seeded
+  multiplier (the spread that stencil optimisation leaves, Section 4).
+* ``batch_instances(...)``: many independent lattices with log-uniform sizes and
+  mixed orders m in {4, 6, 8}.
+* ``tgv_fields(xy, c)``: the Taylor-Green initial condition of Section 8.1 in the
+  evolved variables (ln rho, u, v), with rho = 1 + p / c^2.
+* ``smooth_perturbation(xy, ...)``: a seeded band-limited random field
+  (integer wavevectors with |k| <= kmax), normalised to unit maximum amplitude.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+BASE_SEED = 2102_02019
+
+# h/s used for each order when a workload mixes orders (m=4 and m=8 follow the
+# two lattice workloads; m=6 uses the "safe" non-optimised value of Section 4).
+H_OVER_S = {2: 1.2, 4: 1.7, 6: 2.2, 8: 2.8, 10: 3.3}
+
+
+@dataclass
+class NodeSet:
+    """A node distribution: positions, spacing s_i and stencil scale h_i."""
+
+    xy: np.ndarray  # (N, 2) float64, inside [0, Lx) x [0, Ly)
+    s: np.ndarray  # (N,) float64
+    h: np.ndarray  # (N,) float64
+    Lx: float
+    Ly: float
+    m: int
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def N(self) -> int:
+        return int(self.xy.shape[0])
+
+
+def rng_for(config_index: int, stream: int = 0) -> np.random.Generator:
+    """PCG64 generator for a workload; ``stream`` separates independent draws."""
+    return np.random.Generator(np.random.PCG64([BASE_SEED + config_index, stream]))
+
+
+def tgv_lattice(nx: int, ny: int | None = None, m: int = 4, h_over_s: float | None = None,
+                jitter: float = 0.3, seed: int = 0, s: float | None = None) -> NodeSet:
+    """Jittered nx x ny lattice with spacing s (default 1/nx) on [0, nx s) x [0, ny s)."""
+    ny = nx if ny is None else ny
+    s = 1.0 / nx if s is None else s
+    if h_over_s is None:
+        h_over_s = H_OVER_S[m]
+    rng = rng_for(seed, 0)
+    iy, ix = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    jx = rng.uniform(-jitter, jitter, size=(ny, nx))
+    jy = rng.uniform(-jitter, jitter, size=(ny, nx))
+    x = (ix + 0.5 + jx) * s
+    y = (iy + 0.5 + jy) * s
+    xy = np.stack([x.ravel(), y.ravel()], axis=1).astype(np.float64)
+    N = nx * ny
+    sv = np.full(N, s, dtype=np.float64)
+    hv = np.full(N, h_over_s * s, dtype=np.float64)
+    return NodeSet(xy, sv, hv, nx * s, ny * s, m,
+                   {"kind": "lattice", "nx": nx, "ny": ny, "jitter": jitter, "seed": seed,
+                    "h_over_s": h_over_s})
+
+
+def varres_spacing(x: np.ndarray, s0: float) -> np.ndarray:
+    """s(x) = s0 (1 + 1.5 sin^2(pi x)) for the variable-resolution box."""
+    return s0 * (1.0 + 1.5 * np.sin(np.pi * x) ** 2)
+
+
+def varres_columns(s0: float = 6.654e-4, m: int = 10, h_over_s: float = 3.3,
+                   h_spread=(0.85, 1.25), jitter: float = 0.3, seed: int = 2) -> NodeSet:
+    """Periodic columns whose spacing follows s(x) = s0 (1 + 1.5 sin^2 pi x).
+
+    Column positions advance by s(x_k) and are rescaled to close at x = 1;
+    column k holds round(1/s(x_k)) evenly spaced nodes in y.  Every node is
+    jittered by +-0.3 s in both directions and gets
+    h_i = h_over_s * s_i * U[h_spread].
+    """
+    xs = [0.0]
+    while True:
+        nxt = xs[-1] + float(varres_spacing(np.array([xs[-1]]), s0)[0])
+        if nxt >= 1.0:
+            break
+        xs.append(nxt)
+    xs = np.asarray(xs)
+    xs = xs * (1.0 / (xs[-1] + varres_spacing(np.array([xs[-1]]), s0)[0]))
+    # centre each column in its own slab
+    widths = np.diff(np.append(xs, 1.0))
+    xc = xs + 0.5 * widths
+    rng = rng_for(seed, 0)
+    rows_x, rows_y, rows_s = [], [], []
+    for k in range(len(xc)):
+        sk = float(varres_spacing(np.array([xc[k]]), s0)[0])
+        ny = max(1, int(round(1.0 / sk)))
+        sy = 1.0 / ny
+        iy = np.arange(ny)
+        y = (iy + 0.5 + rng.uniform(-jitter, jitter, size=ny)) * sy
+        x = xc[k] + rng.uniform(-jitter, jitter, size=ny) * widths[k]
+        rows_x.append(np.mod(x, 1.0))
+        rows_y.append(np.mod(y, 1.0))
+        rows_s.append(np.full(ny, sk))
+    x = np.concatenate(rows_x)
+    y = np.concatenate(rows_y)
+    s = np.concatenate(rows_s)
+    mult = rng_for(seed, 1).uniform(h_spread[0], h_spread[1], size=x.shape[0])
+    h = h_over_s * s * mult
+    xy = np.stack([x, y], axis=1)
+    return NodeSet(xy, s, h, 1.0, 1.0, m,
+                   {"kind": "varres", "s0": s0, "columns": int(len(xc)), "seed": seed,
+                    "h_over_s": h_over_s, "h_spread": list(h_spread),
+                    "s_ratio": float(s.max() / s.min())})
+
+
+def batch_instances(count: int = 256, n_min: int = 2048, n_max: int = 65536,
+                    orders=(4, 6, 8), seed: int = 3) -> list[NodeSet]:
+    """Independent jittered lattices, N log-uniform in [n_min, n_max], m uniform in orders."""
+    rng = rng_for(seed, 0)
+    logs = rng.uniform(math.log(n_min), math.log(n_max), size=count)
+    ms = rng.choice(np.asarray(orders), size=count)
+    out = []
+    for k in range(count):
+        nx = max(8, int(round(math.sqrt(math.exp(logs[k])))))
+        m = int(ms[k])
+        out.append(tgv_lattice(nx, nx, m=m, seed=1000 + 7 * k + seed))
+    return out
+
+
+def tgv_fields(xy: np.ndarray, c: float = 10.0, H: float = 1.0) -> np.ndarray:
+    """Taylor-Green initial state (ln rho, u, v) as a (3, N) float64 array.
+
+    u = -cos(2 pi x/H) sin(2 pi y/H), v = sin(2 pi x/H) cos(2 pi y/H),
+    p = -(H/4)(cos(4 pi x/H) + cos(4 pi y/H)) and rho = 1 + p / c^2.
+    """
+    x = xy[:, 0]
+    y = xy[:, 1]
+    k = 2.0 * math.pi / H
+    u = -np.cos(k * x) * np.sin(k * y)
+    v = np.sin(k * x) * np.cos(k * y)
+    p = -(H / 4.0) * (np.cos(2 * k * x) + np.cos(2 * k * y))
+    rho = 1.0 + p / (c * c)
+    return np.stack([np.log(rho), u, v]).astype(np.float64)
+
+
+def smooth_perturbation(xy: np.ndarray, kmax: int = 8, seed: int = 4, stream: int = 0,
+                        Lx: float = 1.0, Ly: float = 1.0) -> np.ndarray:
+    """Sum over integer wavevectors 0 < |k| <= kmax of N(0,1) * cos / sin(2 pi k.x),
+    normalised so that its maximum magnitude over the nodes is 1."""
+    rng = rng_for(seed, 10 + stream)
+    x = xy[:, 0] / Lx
+    y = xy[:, 1] / Ly
+    f = np.zeros(xy.shape[0])
+    for kx in range(-kmax, kmax + 1):
+        for ky in range(-kmax, kmax + 1):
+            if (kx == 0 and ky == 0) or kx * kx + ky * ky > kmax * kmax:
+                continue
+            a, b = rng.standard_normal(2)
+            ph = 2.0 * math.pi * (kx * x + ky * y)
+            f += a * np.cos(ph) + b * np.sin(ph)
+    return f / np.abs(f).max()
+
+
+def perturbed_tgv_fields(xy: np.ndarray, c: float = 10.0, amplitude: float = 0.05,
+                         kmax: int = 8, seed: int = 4) -> np.ndarray:
+    """Taylor-Green state plus ``amplitude`` times an independent smooth field per variable."""
+    q = tgv_fields(xy, c)
+    for f in range(3):
+        q[f] += amplitude * smooth_perturbation(xy, kmax=kmax, seed=seed, stream=f)
+    return q
+
+
+# Named workloads used by tests and the benchmark.
+WORKLOADS = {
+    "tgv64_m4": dict(nx=64, m=4, steps=100, c=10.0),
+    "tgv512_m8": dict(nx=512, m=8, steps=1000, c=10.0),
+}
+
+
+def workload(name: str) -> NodeSet:
+    cfg = WORKLOADS[name]
+    idx = list(WORKLOADS).index(name)
+    return tgv_lattice(cfg["nx"], m=cfg["m"], seed=idx)

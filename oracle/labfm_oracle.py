@@ -1,0 +1,434 @@
+"""Plain FP64 CPU oracle for the LABFM hot path (test infrastructure only).
+
+This module is the correctness reference that the CUDA path is compared with.
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg
+may import it; the product path never calls it.  It shares no code with the
+CUDA library: it follows the paper's definitions step by step in numpy float64,
+vectorised across nodes only where every node still does exactly the operations
+the definitions list.
+
+Paper passages followed (King & Lind, "High-order simulations of isothermal
+flows using the local anisotropic basis function method"):
+
+* Section 2: stencil |r_ji| <= 2 h_i; monomial vector X (eq. X), derivative vector
+  D, difference-form operator L^d_i = sum_j (phi_j - phi_i) w^d_ji
+  (eq. general_do), selector C^d, w^d_ji = W_ji . Psi^d_i (eq. w_abf),
+  M_i = sum_j X_ji (x) W_ji (eq. disc_form), M_i Psi = C^d (eq. lsys) solved by LU
+  with partial pivoting, and the row scaling by powers of h (vector H).
+* Section 3: Hermite ABFs (eq. hermite) with the Wendland C2 RBF.
+* Section 6: hyperviscous filter (1 + kappa_i nabla^m), F_0,i and kappa_i = 2/(3 F_0,i).
+* Section 7: isothermal Navier-Stokes in (ln rho, u, v) (eq. icns), the
+  RK3(2)4[2R+]C low-storage Runge-Kutta scheme, time step (eq. dt), filter after
+  every complete step.
+
+Readings where the paper is silent or garbled (each is also listed in the
+design notes):
+
+* The Wendland C2 RBF is not printed; we use the 2D Wendland C2 function with
+  support 2h: psi(q) = (1 - q/2)^4 (1 + 2q) for q = |r|/h <= 2, else 0.
+* The Rodrigues formula prints d^n/dz^n; it is read as d^a/dz^a (physicists'
+  Hermite polynomials, H_{k+1} = 2 z H_k - 2 k H_{k-1}).
+* The filter selector C^hyp puts binom(m/2, k) at the position of
+  d^m / dx^{2k} dy^{m-2k} (the expansion of (d_xx + d_yy)^{m/2}), zero elsewhere.
+* Besides d = x, y the right-hand side needs xx, xy and yy separately (eq. icns);
+  the Laplacian is w^xx + w^yy.
+* RK3(2)4[2R+]C coefficients are not printed (the paper cites Kennedy,
+  Carpenter & Lewis 2000); the published values are used and checked against
+  the third-order conditions in the tests.
+* dt (eq. dt) is computed once from the initial state and held fixed.
+* Periodic minimum image: dx = x_j - x_i; if dx > L/2: dx -= L; elif dx < -L/2: dx += L.
+  Self is excluded from the stencil (it contributes exactly zero).
+
+Parity pins: see tests/test_oracle_*.py.  Parity unpinned: the absolute weight
+values when a stencil has more nodes than unknowns depend on the Wendland /
+Hermite reading above, which the paper fixes only by reference; the tests pin
+everything that the paper and the mathematics fix (reproduction, unisolvent
+finite-difference limits, symmetry, convergence order, Taylor-Green decay).
+"""
+from __future__ import annotations
+
+import math
+from fractions import Fraction
+
+import numpy as np
+
+# Operator order used for every weight array: rows of w are these operators.
+OPS = ("x", "y", "xx", "xy", "yy", "hyp")
+RHS_OPS = OPS[:5]
+
+
+# --------------------------------------------------------------------------
+# Section 2: the monomial basis, selectors and scaling
+# --------------------------------------------------------------------------
+
+def n_unknowns(m: int) -> int:
+    """Length of X for order m: n = (m^2 + 3m) / 2 (Section 2)."""
+    return (m * m + 3 * m) // 2
+
+
+def monomial_exponents(m: int) -> list[tuple[int, int]]:
+    """(a, b) of each entry x^a y^b / (a! b!) of X, in the printed order:
+    total degree 1..m, and within a degree by descending power of x (eq. X)."""
+    out = []
+    for k in range(1, m + 1):
+        for a in range(k, -1, -1):
+            out.append((a, k - a))
+    return out
+
+
+def selector(op: str, m: int, h: float) -> np.ndarray:
+    """Scaled selector C~^d = C^d . H for one node (Section 2, vector H; Section 6 for hyp)."""
+    ex = monomial_exponents(m)
+    C = np.zeros(len(ex))
+    want = {"x": {(1, 0): 1.0}, "y": {(0, 1): 1.0}, "xx": {(2, 0): 1.0},
+            "xy": {(1, 1): 1.0}, "yy": {(0, 2): 1.0}, "L": {(2, 0): 1.0, (0, 2): 1.0}}
+    if op == "hyp":
+        half = m // 2
+        coeffs = {(2 * k, m - 2 * k): float(math.comb(half, k)) for k in range(half + 1)}
+    else:
+        coeffs = want[op]
+    for q, (a, b) in enumerate(ex):
+        if (a, b) in coeffs:
+            C[q] = coeffs[(a, b)] * h ** (-(a + b))
+    return C
+
+
+def selectors(m: int, h: np.ndarray) -> np.ndarray:
+    """C~^d for d in OPS and a batch of nodes: shape (len(h), n, 6)."""
+    base = np.stack([selector(op, m, 1.0) for op in OPS], axis=1)  # (n, 6), h = 1
+    deg = np.array([a + b for (a, b) in monomial_exponents(m)], dtype=np.float64)
+    scale = np.asarray(h, dtype=np.float64)[:, None] ** (-deg[None, :])
+    return scale[:, :, None] * base[None, :, :]
+
+
+# --------------------------------------------------------------------------
+# Section 3: Hermite ABFs with a Wendland C2 RBF
+# --------------------------------------------------------------------------
+
+def wendland_c2(q: np.ndarray) -> np.ndarray:
+    """psi(q) = (1 - q/2)^4 (1 + 2 q) for 0 <= q <= 2, else 0 (support 2h)."""
+    q = np.asarray(q, dtype=np.float64)
+    t = 1.0 - 0.5 * q
+    t2 = t * t
+    val = (t2 * t2) * (1.0 + 2.0 * q)
+    return np.where(q <= 2.0, val, 0.0)
+
+
+def hermite(a: int, z: np.ndarray) -> np.ndarray:
+    """Physicists' Hermite polynomial H_a(z) by the three-term recurrence."""
+    z = np.asarray(z, dtype=np.float64)
+    h_prev = np.ones_like(z)
+    if a == 0:
+        return h_prev
+    h = 2.0 * z
+    for k in range(1, a):
+        h_prev, h = h, 2.0 * z * h - 2.0 * k * h_prev
+    return h
+
+
+def abf_matrix(dx: np.ndarray, dy: np.ndarray, h: np.ndarray, m: int) -> np.ndarray:
+    """W^q_ji (eq. hermite) for arrays of offsets: returns shape dx.shape + (n,)."""
+    ex = monomial_exponents(m)
+    q = np.sqrt(dx * dx + dy * dy) / h
+    psi = wendland_c2(q)
+    zx = dx / (h * math.sqrt(2.0))
+    zy = dy / (h * math.sqrt(2.0))
+    Hx = [hermite(a, zx) for a in range(m + 1)]
+    Hy = [hermite(b, zy) for b in range(m + 1)]
+    out = np.empty(np.shape(dx) + (len(ex),))
+    for q, (a, b) in enumerate(ex):
+        out[..., q] = psi * Hx[a] * Hy[b] / math.sqrt(2.0 ** (a + b))
+    return out
+
+
+def scaled_monomials(dx: np.ndarray, dy: np.ndarray, h: np.ndarray, m: int) -> np.ndarray:
+    """X~_ji = X_ji . H_i: entries (x/h)^a (y/h)^b / (a! b!) (Section 2)."""
+    ex = monomial_exponents(m)
+    xh = dx / h
+    yh = dy / h
+    out = np.empty(np.shape(dx) + (len(ex),))
+    for q, (a, b) in enumerate(ex):
+        out[..., q] = xh ** a * yh ** b / (math.factorial(a) * math.factorial(b))
+    return out
+
+
+# --------------------------------------------------------------------------
+# Section 2: the stencil (brute force, O(N^2))
+# --------------------------------------------------------------------------
+
+def minimum_image(d: np.ndarray, L: float, periodic: bool) -> np.ndarray:
+    if not periodic:
+        return d
+    d = np.where(d > 0.5 * L, d - L, d)
+    return np.where(d < -0.5 * L, d + L, d)
+
+
+def offsets(xy: np.ndarray, i: np.ndarray, j: np.ndarray, Lx: float, Ly: float,
+            periodic=(True, True)):
+    """r_ji = r_j - r_i with the periodic minimum image."""
+    dx = minimum_image(xy[j, 0] - xy[i, 0], Lx, periodic[0])
+    dy = minimum_image(xy[j, 1] - xy[i, 1], Ly, periodic[1])
+    return dx, dy
+
+
+def neighbours_of(xy, h, i, Lx, Ly, periodic=(True, True)):
+    """All j != i with |r_ji|^2 <= (2 h_i)^2, ascending j (Section 2)."""
+    N = xy.shape[0]
+    j = np.arange(N)
+    dx, dy = offsets(xy, np.full(N, i), j, Lx, Ly, periodic)
+    d2 = dx * dx + dy * dy
+    two_h = 2.0 * h[i]
+    keep = (d2 <= two_h * two_h) & (j != i)
+    return j[keep].astype(np.int32)
+
+
+def neighbours(xy, h, Lx, Ly, periodic=(True, True), rows=None):
+    """CSR (row_ptr int64, col int32) of the stencils of ``rows`` (default: all nodes)."""
+    N = xy.shape[0]
+    rows = np.arange(N) if rows is None else np.asarray(rows)
+    cols = [neighbours_of(xy, h, int(i), Lx, Ly, periodic) for i in rows]
+    row_ptr = np.zeros(len(rows) + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum([len(c) for c in cols])
+    col = np.concatenate(cols) if cols else np.zeros(0, np.int32)
+    return row_ptr, col.astype(np.int32)
+
+
+# --------------------------------------------------------------------------
+# Section 2: LU with partial pivoting (the dgesv algorithm), batched over nodes
+# --------------------------------------------------------------------------
+
+def lu_solve(A: np.ndarray, B: np.ndarray):
+    """Solve A X = B for a batch: A (nb, n, n), B (nb, n, k).
+
+    Gaussian elimination with partial pivoting (the first row holding the
+    largest |pivot| wins), then back substitution.  Returns (X, ok) where ok
+    is False for a node whose pivot became exactly zero or non-finite.
+    """
+    A = np.array(A, dtype=np.float64, copy=True)
+    B = np.array(B, dtype=np.float64, copy=True)
+    nb, n, _ = A.shape
+    ok = np.ones(nb, dtype=bool)
+    bidx = np.arange(nb)
+    for k in range(n):
+        p = k + np.argmax(np.abs(A[:, k:, k]), axis=1)
+        rows_k = A[bidx, k, :].copy()
+        A[bidx, k, :] = A[bidx, p, :]
+        A[bidx, p, :] = rows_k
+        rhs_k = B[bidx, k, :].copy()
+        B[bidx, k, :] = B[bidx, p, :]
+        B[bidx, p, :] = rhs_k
+        piv = A[:, k, k]
+        bad = (piv == 0.0) | ~np.isfinite(piv)
+        ok &= ~bad
+        piv = np.where(bad, 1.0, piv)
+        lk = A[:, k + 1:, k] / piv[:, None]
+        A[:, k + 1:, k] = lk
+        A[:, k + 1:, k + 1:] -= lk[:, :, None] * A[:, k, None, k + 1:]
+        B[:, k + 1:, :] -= lk[:, :, None] * B[:, k, None, :]
+    X = np.zeros_like(B)
+    for k in range(n - 1, -1, -1):
+        acc = B[:, k, :] - np.einsum("bj,bjk->bk", A[:, k, k + 1:], X[:, k + 1:, :])
+        d = A[:, k, k]
+        X[:, k, :] = acc / np.where(d == 0.0, 1.0, d)[:, None]
+    ok &= np.all(np.isfinite(X), axis=(1, 2))
+    return X, ok
+
+
+# --------------------------------------------------------------------------
+# Sections 2, 3, 6: the weight build
+# --------------------------------------------------------------------------
+
+def build_weights(xy, h, s, row_ptr, col, m, Lx, Ly, periodic=(True, True), rows=None,
+                  chunk=2048, want_cond=False, rbf=wendland_c2):
+    """Weights of the operators OPS for every node in ``rows``.
+
+    For each node: X~ and W for its neighbours, M = sum_j X~_j (x) W_j,
+    LU solve of M Psi = C~^d for d in OPS, w^d_j = W_j . Psi^d, then
+    F_0 = sum_j phi_ji w^hyp_ji and kappa = 2 / (3 F_0) (Section 6).
+
+    ``row_ptr``/``col`` describe the stencils of ``rows`` (default: all nodes, CSR
+    over all N).  Returns a dict with w (6, nnz), kappa, ok, residual (max
+    nondimensional reproduction residual per node) and optionally cond1.
+    """
+    N = xy.shape[0]
+    rows = np.arange(N) if rows is None else np.asarray(rows)
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    n = n_unknowns(m)
+    nnz = int(row_ptr[-1])
+    w = np.zeros((len(OPS), nnz))
+    kappa = np.zeros(len(rows))
+    ok = np.ones(len(rows), dtype=bool)
+    resid = np.zeros(len(rows))
+    cond = np.zeros(len(rows)) if want_cond else None
+    for c0 in range(0, len(rows), chunk):
+        c1 = min(len(rows), c0 + chunk)
+        nodes = rows[c0:c1]
+        cnt = (row_ptr[c0 + 1:c1 + 1] - row_ptr[c0:c1]).astype(np.int64)
+        nmax = int(cnt.max()) if len(cnt) else 0
+        if nmax == 0:
+            ok[c0:c1] = False
+            continue
+        # padded neighbour table; pad slots get a zero ABF row (psi = 0)
+        slot = np.arange(nmax)[None, :]
+        valid = slot < cnt[:, None]
+        ent = np.where(valid, row_ptr[c0:c1, None] + slot, row_ptr[c0:c1, None])
+        jj = col[np.minimum(ent, max(nnz - 1, 0))]
+        ii = np.broadcast_to(nodes[:, None], jj.shape)
+        dx, dy = offsets(xy, ii, jj, Lx, Ly, periodic)
+        hi = h[nodes][:, None]
+        Xt = scaled_monomials(dx, dy, hi, m)
+        W = abf_matrix(dx, dy, hi, m) if rbf is wendland_c2 else _abf_with(rbf, dx, dy, hi, m)
+        W = np.where(valid[:, :, None], W, 0.0)
+        Xt = np.where(valid[:, :, None], Xt, 0.0)
+        M = np.matmul(Xt.transpose(0, 2, 1), W)
+        Cs = selectors(m, h[nodes])
+        Psi, good = lu_solve(M, Cs)
+        wn = np.matmul(W, Psi)  # (b, nmax, 6)
+        # reproduction residual, nondimensional: sum_j X~_j w~_j - C~ h^l
+        scale = np.array([1, 1, 2, 2, 2, m], dtype=np.float64)
+        hl = hi[:, :, None] ** scale[None, None, :]
+        rep = np.matmul(Xt.transpose(0, 2, 1), wn * hl) - Cs * hl
+        resid[c0:c1] = np.abs(rep).max(axis=(1, 2))
+        if want_cond:
+            cond[c0:c1] = np.linalg.cond(M, 1)
+        # Section 6: F_0 and kappa
+        si = s[nodes][:, None]
+        kx = 3.0 * math.pi / (2.0 * si)
+        phi = 1.0 - np.cos(kx * dx) * np.cos(kx * dy)
+        F0 = np.sum(np.where(valid, phi * wn[:, :, 5], 0.0), axis=1)
+        kap = 2.0 / (3.0 * F0)
+        kappa[c0:c1] = kap
+        good &= np.isfinite(kap) & (cnt >= n)
+        ok[c0:c1] = good
+        flat = ent[valid]
+        for d in range(len(OPS)):
+            w[d, flat] = wn[:, :, d][valid]
+    out = {"w": w, "kappa": kappa, "ok": ok, "residual": resid}
+    if want_cond:
+        out["cond1"] = cond
+    return out
+
+
+def _abf_with(rbf, dx, dy, h, m):
+    """Hermite ABFs with an alternative RBF (used by the invariance pins)."""
+    ex = monomial_exponents(m)
+    q = np.sqrt(dx * dx + dy * dy) / h
+    psi = rbf(q)
+    zx = dx / (h * math.sqrt(2.0))
+    zy = dy / (h * math.sqrt(2.0))
+    cols = [psi * hermite(a, zx) * hermite(b, zy) / math.sqrt(2.0 ** (a + b)) for (a, b) in ex]
+    return np.stack(cols, axis=-1)
+
+
+# --------------------------------------------------------------------------
+# Section 2, eq. general_do: the difference-form operator
+# --------------------------------------------------------------------------
+
+def row_index(row_ptr):
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    return np.repeat(np.arange(len(row_ptr) - 1), np.diff(row_ptr))
+
+
+def apply_op(phi, wd, row_ptr, col):
+    """L^d_i(phi) = sum_j (phi_j - phi_i) w^d_ji for every node."""
+    ri = row_index(row_ptr)
+    return np.bincount(ri, weights=(phi[col] - phi[ri]) * wd, minlength=len(row_ptr) - 1)
+
+
+# --------------------------------------------------------------------------
+# Section 7: isothermal Navier-Stokes right-hand side (eq. icns)
+# --------------------------------------------------------------------------
+
+def derivatives(q, w, row_ptr, col):
+    """The 12 derivatives the RHS needs: (a_x, a_y) and (x, y, xx, xy, yy) of u and v."""
+    a, u, v = q
+    d = {}
+    d["ax"] = apply_op(a, w[0], row_ptr, col)
+    d["ay"] = apply_op(a, w[1], row_ptr, col)
+    for name, f in (("u", u), ("v", v)):
+        for k, op in enumerate(RHS_OPS):
+            d[name + op] = apply_op(f, w[k], row_ptr, col)
+    return d
+
+
+def rhs(q, w, row_ptr, col, c2, mu, g=(0.0, 0.0)):
+    """d/dt of (ln rho, u, v):
+
+    R_a = -(u a_x + v a_y) - (u_x + v_y)
+    R_u = -(u u_x + v u_y) - c^2 a_x + (mu / rho)(4/3 u_xx + u_yy + 1/3 v_xy) + g_x
+    R_v = -(u v_x + v v_y) - c^2 a_y + (mu / rho)(4/3 v_yy + v_xx + 1/3 u_xy) + g_y
+    with a = ln rho, using -(1/rho) grad p = -c^2 grad ln rho for p = c^2 rho.
+    """
+    a, u, v = q
+    d = derivatives(q, w, row_ptr, col)
+    nu = mu * np.exp(-a)
+    Ra = -(u * d["ax"] + v * d["ay"]) - (d["ux"] + d["vy"])
+    Ru = (-(u * d["ux"] + v * d["uy"]) - c2 * d["ax"]
+          + nu * (4.0 / 3.0 * d["uxx"] + d["uyy"] + 1.0 / 3.0 * d["vxy"]) + g[0])
+    Rv = (-(u * d["vx"] + v * d["vy"]) - c2 * d["ay"]
+          + nu * (4.0 / 3.0 * d["vyy"] + d["vxx"] + 1.0 / 3.0 * d["uxy"]) + g[1])
+    return np.stack([Ra, Ru, Rv])
+
+
+# --------------------------------------------------------------------------
+# Section 7: RK3(2)4[2R+]C (Kennedy, Carpenter & Lewis 2000), 2R form
+# --------------------------------------------------------------------------
+
+RK_A_SUB = (Fraction(11847461282814, 36547543011857),   # a21
+            Fraction(3943225443063, 7078155732230),     # a32
+            Fraction(-346793006927, 4029903576067))     # a43
+RK_B = (Fraction(1017324711453, 9774461848756),
+        Fraction(8237718856693, 13685301971492),
+        Fraction(57731312506979, 19404895981398),
+        Fraction(-101169746363290, 37734290219643))
+
+
+def rk_butcher():
+    """Full Butcher matrix of the 2R scheme: a_ij = b_j for j < i-1, a_{i,i-1} given."""
+    A = [[Fraction(0)] * 4 for _ in range(4)]
+    for i in range(1, 4):
+        for j in range(i - 1):
+            A[i][j] = RK_B[j]
+        A[i][i - 1] = RK_A_SUB[i - 1]
+    return A
+
+
+def rk_step(q, dt, f):
+    """One 4-stage low-storage step with registers (Q, X):
+    X = Q; for each stage k: F = f(X); Q += dt b_k F; X = Q + dt (a_{k+1,k} - b_k) F."""
+    Q = np.array(q, dtype=np.float64, copy=True)
+    X = Q.copy()
+    for k in range(4):
+        F = f(X)
+        Q = Q + (dt * float(RK_B[k])) * F
+        if k < 3:
+            X = Q + (dt * float(RK_A_SUB[k] - RK_B[k])) * F
+    return Q
+
+
+# --------------------------------------------------------------------------
+# Section 6: the filter, and eq. dt
+# --------------------------------------------------------------------------
+
+def filter_fields(q, w_hyp, kappa, row_ptr, col):
+    """phi~_i = phi_i + kappa_i sum_j (phi_j - phi_i) w^hyp_ji, for each field (Jacobi)."""
+    return np.stack([f + kappa * apply_op(f, w_hyp, row_ptr, col) for f in q])
+
+
+def stable_dt(q, s, c, mu):
+    """dt = min over nodes of min(1.0 s / (|u| + c), 0.4 s^2 rho / mu) (eq. dt)."""
+    a, u, v = q
+    speed = np.sqrt(u * u + v * v)
+    return float(np.min(np.minimum(1.0 * s / (speed + c), 0.4 * s * s * np.exp(a) / mu)))
+
+
+def time_step(q, dt, w, kappa, row_ptr, col, c2, mu, g=(0.0, 0.0)):
+    """One complete step: four RK stages, then the filter on ln rho, u, v (Section 7)."""
+    f = lambda x: rhs(x, w, row_ptr, col, c2, mu, g)
+    return filter_fields(rk_step(q, dt, f), w[5], kappa, row_ptr, col)
+
+
+def kinetic_energy(q, s):
+    """sum_i 1/2 rho_i |u_i|^2 V_i with node volume V_i = s_i^2."""
+    a, u, v = q
+    return float(np.sum(0.5 * np.exp(a) * (u * u + v * v) * s * s))
