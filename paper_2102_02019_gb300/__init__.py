@@ -1,0 +1,261 @@
+"""Python binding of liblabfm (the GB300 LABFM hot path).
+
+Argument marshalling only: every step runs in the CUDA kernels of liblabfm.so,
+reached through its C ABI (include/labfm.h) with ctypes.  PyTorch supplies
+device memory and the current CUDA stream.  There is no CPU fallback: if the
+library is missing or fails to load, importing the binding raises.
+
+Functions keep the names of the C entry points:
+
+    build_stencils(xy, h, Lx, Ly)        -> (row_ptr, col)
+    build_weights(xy, h, s, Lx, Ly, row_ptr, col, m) -> dict(w, kappa, status, residual)
+    Plan(N, row_ptr, col, w, kappa, s, dtype)  (labfm_plan_create / _destroy)
+    rhs(plan, fields, phys)              -> 3 x N
+    filter(plan, fields)                 -> 3 x N
+    rk_step(plan, Q, dt, nsteps, phys)   (in place)
+    stable_dt(plan, fields, s, c, mu)    -> 1-element device tensor
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblabfm.so")
+
+LABFM_F64 = 0
+LABFM_F32 = 1
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ECUDA", 3: "ENOMEM", 4: "ECAPACITY",
+                5: "ESINGULAR", 6: "ENONFINITE", 7: "ETIMEOUT"}
+NODE_FEW_NEIGHBOURS = 1
+NODE_SINGULAR = 2
+NODE_NONFINITE = 4
+OPS = ("x", "y", "xx", "xy", "yy", "hyp")
+
+
+class LabfmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+
+
+class _Phys(ctypes.Structure):
+    _fields_ = [("c2", ctypes.c_double), ("mu", ctypes.c_double),
+                ("gx", ctypes.c_double), ("gy", ctypes.c_double)]
+
+
+class _PlanInfo(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nnz_padded", ctypes.c_int64),
+                ("dtype", ctypes.c_int32), ("group", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int
+_D = ctypes.c_double
+_SIGS = {
+    "labfm_last_error": (ctypes.c_char_p, []),
+    "labfm_abi_version": (_I32, []),
+    "labfm_build_stencils": (_I32, [_P, _P, _I64, _D, _D, ctypes.c_uint32, _P, _P, _I64,
+                                    ctypes.POINTER(_I64), _P]),
+    "labfm_build_weights": (_I32, [_P, _P, _P, _I64, _D, _D, ctypes.c_uint32, _P, _P, _I64, _I32,
+                                   _P, _P, _P, _P, ctypes.POINTER(_I64), _P]),
+    "labfm_plan_create": (_I32, [ctypes.POINTER(_P), _I64, _I64, _I32, _P, _P, _P, _P, _P, _P]),
+    "labfm_plan_destroy": (_I32, [_P]),
+    "labfm_plan_get_info": (_I32, [_P, ctypes.POINTER(_PlanInfo)]),
+    "labfm_plan_set_launch": (_I32, [_P, _I32, _I32]),
+    "labfm_plan_autotune": (_I32, [_P, _P, _P, ctypes.POINTER(_Phys), _I32,
+                                   ctypes.POINTER(_I32), ctypes.POINTER(_I32), _P]),
+    "labfm_rhs": (_I32, [_P, _P, _P, ctypes.POINTER(_Phys), _P]),
+    "labfm_filter": (_I32, [_P, _P, _P, _P]),
+    "labfm_rk_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "labfm_rk_step": (_I32, [_P, _P, _P, ctypes.c_size_t, _D, _I32, ctypes.POINTER(_Phys), _P]),
+    "labfm_stable_dt": (_I32, [_P, _P, _P, _D, _D, _P, _P]),
+}
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is not built; run `python -c 'import __graft_entry__ as g; g.build()'` "
+            "(needs nvcc).  There is no CPU fallback.")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def exported_symbols() -> list[str]:
+    return sorted(_SIGS)
+
+
+def _check(rc: int) -> None:
+    if rc != 0:
+        raise LabfmError(rc, lib.labfm_last_error().decode())
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("liblabfm takes CUDA tensors")
+    if not t.is_contiguous():
+        raise ValueError("liblabfm takes contiguous tensors")
+    return t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+@dataclass
+class Phys:
+    """c2 = c^2, mu, body force (gx, gy) of eq. icns."""
+    c2: float
+    mu: float
+    gx: float = 0.0
+    gy: float = 0.0
+
+    def c(self) -> _Phys:
+        return _Phys(self.c2, self.mu, self.gx, self.gy)
+
+
+def build_stencils(xy: torch.Tensor, h: torch.Tensor, Lx: float, Ly: float,
+                   periodic=(True, True), stream=None):
+    """CSR (row_ptr int32 [N+1], col int32 [nnz]) of |r_ji| <= 2 h_i (labfm_build_stencils)."""
+    N = xy.shape[0]
+    mask = (1 if periodic[0] else 0) | (2 if periodic[1] else 0)
+    row_ptr = torch.empty(N + 1, dtype=torch.int32, device=xy.device)
+    nnz = _I64(0)
+    st = _stream(stream)
+    _check(lib.labfm_build_stencils(_ptr(xy), _ptr(h), N, Lx, Ly, mask, _ptr(row_ptr), None, 0,
+                                    ctypes.byref(nnz), st))
+    col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=xy.device)
+    _check(lib.labfm_build_stencils(_ptr(xy), _ptr(h), N, Lx, Ly, mask, _ptr(row_ptr), _ptr(col),
+                                    col.numel(), ctypes.byref(nnz), st))
+    return row_ptr, col[:nnz.value]
+
+
+def build_weights(xy, h, s, Lx, Ly, row_ptr, col, m, periodic=(True, True), residual=True,
+                  check=False, stream=None):
+    """FP64 weights (labfm_build_weights): dict with w (6, nnz), kappa, status, residual, n_failed.
+
+    With check=True the call synchronises and raises LabfmError(ESINGULAR) if a node failed."""
+    N = xy.shape[0]
+    nnz = col.numel()
+    dev = xy.device
+    mask = (1 if periodic[0] else 0) | (2 if periodic[1] else 0)
+    w = torch.empty((6, max(nnz, 1)), dtype=torch.float64, device=dev)
+    kappa = torch.empty(N, dtype=torch.float64, device=dev)
+    status = torch.empty(N, dtype=torch.int32, device=dev)
+    res = torch.empty(N, dtype=torch.float64, device=dev) if residual else None
+    nf = _I64(0)
+    rc = lib.labfm_build_weights(_ptr(xy), _ptr(h), _ptr(s), N, Lx, Ly, mask, _ptr(row_ptr),
+                                 _ptr(col) if nnz else None, nnz, m, _ptr(w), _ptr(kappa), _ptr(res),
+                                 _ptr(status), ctypes.byref(nf) if check else None, _stream(stream))
+    _check(rc)
+    return {"w": w[:, :nnz] if nnz else w[:, :0], "kappa": kappa, "status": status,
+            "residual": res, "n_failed": nf.value if check else None}
+
+
+class Plan:
+    """A prepared operator for the step kernels (labfm_plan_create / labfm_plan_destroy)."""
+
+    def __init__(self, row_ptr, col, w, kappa, s, dtype=torch.float32, stream=None):
+        self.N = row_ptr.numel() - 1
+        self.nnz = col.numel()
+        self.dtype = dtype
+        code = LABFM_F32 if dtype == torch.float32 else LABFM_F64
+        if dtype not in (torch.float32, torch.float64):
+            raise ValueError("dtype must be float32 or float64")
+        w = w.contiguous()
+        handle = _P()
+        _check(lib.labfm_plan_create(ctypes.byref(handle), self.N, self.nnz, code, _ptr(row_ptr),
+                                     _ptr(col) if self.nnz else None, _ptr(w), _ptr(kappa), _ptr(s),
+                                     _stream(stream)))
+        self._h = handle
+        self.device = row_ptr.device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = _PlanInfo()
+        _check(lib.labfm_plan_get_info(self._h, ctypes.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in _PlanInfo._fields_ if k != "reserved"}
+
+    def set_launch(self, group: int, block: int) -> None:
+        _check(lib.labfm_plan_set_launch(self._h, group, block))
+
+    def autotune(self, fields: torch.Tensor, phys: Phys, reps: int = 5, stream=None):
+        out = torch.empty_like(fields)
+        g, b = _I32(0), _I32(0)
+        ph = phys.c()
+        _check(lib.labfm_plan_autotune(self._h, _ptr(fields), _ptr(out), ctypes.byref(ph), reps,
+                                       ctypes.byref(g), ctypes.byref(b), _stream(stream)))
+        return g.value, b.value
+
+    def workspace_bytes(self) -> int:
+        return int(lib.labfm_rk_workspace_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.labfm_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rhs(plan: Plan, fields: torch.Tensor, phys: Phys, out: torch.Tensor | None = None, stream=None):
+    """eq. icns right-hand side of (ln rho, u, v) (labfm_rhs); fields is 3 x N."""
+    out = torch.empty_like(fields) if out is None else out
+    ph = phys.c()
+    _check(lib.labfm_rhs(plan.handle, _ptr(fields), _ptr(out), ctypes.byref(ph), _stream(stream)))
+    return out
+
+
+def filter(plan: Plan, fields: torch.Tensor, out: torch.Tensor | None = None, stream=None):  # noqa: A001
+    """Hyperviscous filter (1 + kappa nabla^m) of the three fields (labfm_filter)."""
+    out = torch.empty_like(fields) if out is None else out
+    _check(lib.labfm_filter(plan.handle, _ptr(fields), _ptr(out), _stream(stream)))
+    return out
+
+
+def workspace(plan: Plan) -> torch.Tensor:
+    """A device buffer of labfm_rk_workspace_bytes for rk_step."""
+    nb = plan.workspace_bytes()
+    return torch.empty(max(nb, 16), dtype=torch.uint8, device=plan.device)
+
+
+def rk_step(plan: Plan, Q: torch.Tensor, dt: float, nsteps: int, phys: Phys,
+            work: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """nsteps RK3(2)4[2R+]C steps + filter, in place on Q (labfm_rk_step)."""
+    work = workspace(plan) if work is None else work
+    ph = phys.c()
+    _check(lib.labfm_rk_step(plan.handle, _ptr(Q), _ptr(work), work.numel(), float(dt), int(nsteps),
+                             ctypes.byref(ph), _stream(stream)))
+    return Q
+
+
+def stable_dt(plan: Plan, fields: torch.Tensor, s: torch.Tensor, c: float, mu: float,
+              out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """eq. dt as a 1-element float64 device tensor (labfm_stable_dt)."""
+    out = torch.empty(1, dtype=torch.float64, device=fields.device) if out is None else out
+    _check(lib.labfm_stable_dt(plan.handle, _ptr(fields), _ptr(s), float(c), float(mu), _ptr(out),
+                               _stream(stream)))
+    return out

@@ -1,0 +1,208 @@
+// C ABI entry points that wrap the time-step kernels: error state, plans,
+// launch-shape autotuning, right-hand side, filter, RK steps and the time step.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <new>
+#include <string>
+
+#include "labfm_internal.cuh"
+
+namespace labfm {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+int set_error(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_error(cudaError_t e, const char* what) {
+    const int code = (e == cudaErrorMemoryAllocation) ? LABFM_ENOMEM : LABFM_ECUDA;
+    return set_error(code, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                               cudaGetErrorString(e) + ")");
+}
+
+}  // namespace labfm
+
+using namespace labfm;
+
+namespace {
+
+void free_plan_memory(labfm_plan* p) {
+    cudaFree(p->row_ptr);
+    cudaFree(p->col);
+    cudaFree(p->w);
+    cudaFree(p->wf);
+    cudaFree(p->inv_s);
+    p->row_ptr = nullptr;
+    p->col = nullptr;
+    p->w = p->wf = p->inv_s = nullptr;
+}
+
+int check_plan(const labfm_plan* p) {
+    if (!p || !p->row_ptr) return set_error(LABFM_EINVAL, "null or empty plan");
+    return LABFM_OK;
+}
+
+}  // namespace
+
+extern "C" const char* labfm_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int labfm_abi_version(void) { return 1; }
+
+extern "C" int labfm_plan_create(labfm_plan** out, int64_t N, int64_t nnz, labfm_dtype dtype,
+                                 const int32_t* row_ptr, const int32_t* col, const double* w,
+                                 const double* kappa, const double* s, void* stream) {
+    if (!out) return set_error(LABFM_EINVAL, "null plan output");
+    *out = nullptr;
+    if (!row_ptr || !w || !kappa || !s || (nnz > 0 && !col))
+        return set_error(LABFM_EINVAL, "null pointer argument");
+    if (N <= 0 || N >= (int64_t(1) << 31) - 1) return set_error(LABFM_EINVAL, "N out of range");
+    if (nnz < 0 || nnz >= (int64_t(1) << 31)) return set_error(LABFM_EINVAL, "nnz out of range");
+    if (dtype != LABFM_F32 && dtype != LABFM_F64) return set_error(LABFM_EINVAL, "unknown dtype");
+    labfm_plan* p = new (std::nothrow) labfm_plan();
+    if (!p) return set_error(LABFM_ENOMEM, "host allocation of the plan failed");
+    p->N = N;
+    p->nnz = nnz;
+    p->dtype = dtype;
+    cudaGetDevice(&p->device);
+    p->group = 8;
+    p->block = 256;
+    const int rc = pack_plan(p, row_ptr, col, w, kappa, s, as_stream(stream));
+    if (rc != LABFM_OK) {
+        free_plan_memory(p);
+        delete p;
+        return rc;
+    }
+    *out = p;
+    return LABFM_OK;
+}
+
+extern "C" int labfm_plan_destroy(labfm_plan* p) {
+    if (!p) return LABFM_OK;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != p->device) cudaSetDevice(p->device);
+    cudaDeviceSynchronize();
+    free_plan_memory(p);
+    if (dev != p->device) cudaSetDevice(dev);
+    delete p;
+    return LABFM_OK;
+}
+
+extern "C" int labfm_plan_get_info(const labfm_plan* p, labfm_plan_info* info) {
+    if (int rc = check_plan(p)) return rc;
+    if (!info) return set_error(LABFM_EINVAL, "null info output");
+    info->N = p->N;
+    info->nnz = p->nnz;
+    info->nnz_padded = p->nnz_pad;
+    info->dtype = p->dtype;
+    info->group = p->group;
+    info->block = p->block;
+    info->reserved = 0;
+    info->device_bytes = p->device_bytes;
+    return LABFM_OK;
+}
+
+extern "C" int labfm_plan_set_launch(labfm_plan* p, int group, int block) {
+    if (int rc = check_plan(p)) return rc;
+    if (!launch_shape_supported(group, block))
+        return set_error(LABFM_EINVAL, "unsupported launch shape (group " + std::to_string(group) +
+                                           ", block " + std::to_string(block) + ")");
+    p->group = group;
+    p->block = block;
+    return LABFM_OK;
+}
+
+extern "C" int labfm_plan_autotune(labfm_plan* p, const void* fields, void* scratch_rhs,
+                                   const labfm_phys* phys, int reps, int* group_out, int* block_out,
+                                   void* stream) {
+    if (int rc = check_plan(p)) return rc;
+    if (!fields || !scratch_rhs || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
+    if (reps <= 0) reps = 5;
+    cudaStream_t st = as_stream(stream);
+    cudaEvent_t e0, e1;
+    LABFM_CUDA_TRY(cudaEventCreate(&e0));
+    LABFM_CUDA_TRY(cudaEventCreate(&e1));
+    const int groups[] = {4, 8, 16, 32};
+    const int blocks[] = {128, 256, 512};
+    float best = 1e30f;
+    int bg = p->group, bb = p->block;
+    int rc = LABFM_OK;
+    for (int g : groups) {
+        for (int b : blocks) {
+            if (!launch_shape_supported(g, b)) continue;
+            // warm-up launch, then `reps` timed launches
+            if ((rc = launch_rhs(p, fields, scratch_rhs, phys, g, b, st))) break;
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < reps && rc == LABFM_OK; ++r)
+                rc = launch_rhs(p, fields, scratch_rhs, phys, g, b, st);
+            cudaEventRecord(e1, st);
+            if (rc) break;
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess) {
+                rc = cuda_error(e, "autotune timing");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) {
+                best = ms;
+                bg = g;
+                bb = b;
+            }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    p->group = bg;
+    p->block = bb;
+    if (group_out) *group_out = bg;
+    if (block_out) *block_out = bb;
+    return LABFM_OK;
+}
+
+extern "C" int labfm_rhs(const labfm_plan* p, const void* fields, void* rhs,
+                         const labfm_phys* phys, void* stream) {
+    if (int rc = check_plan(p)) return rc;
+    if (!fields || !rhs || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
+    if (fields == rhs) return set_error(LABFM_EINVAL, "rhs must not alias fields");
+    return launch_rhs(p, fields, rhs, phys, p->group, p->block, as_stream(stream));
+}
+
+extern "C" int labfm_filter(const labfm_plan* p, const void* in, void* out, void* stream) {
+    if (int rc = check_plan(p)) return rc;
+    if (!in || !out) return set_error(LABFM_EINVAL, "null pointer argument");
+    if (in == out) return set_error(LABFM_EINVAL, "filter output must not alias its input");
+    return launch_filter_soa(p, in, out, as_stream(stream));
+}
+
+extern "C" size_t labfm_rk_workspace_bytes(const labfm_plan* p) {
+    return p ? rk_work_bytes(p) : 0;
+}
+
+extern "C" int labfm_rk_step(const labfm_plan* p, void* Q, void* work, size_t work_bytes,
+                             double dt, int nsteps, const labfm_phys* phys, void* stream) {
+    if (int rc = check_plan(p)) return rc;
+    if (!Q || !work || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
+    if (nsteps < 0) return set_error(LABFM_EINVAL, "negative nsteps");
+    if (work_bytes < rk_work_bytes(p))
+        return set_error(LABFM_EINVAL, "work buffer smaller than labfm_rk_workspace_bytes");
+    if (reinterpret_cast<uintptr_t>(work) % 16 != 0)
+        return set_error(LABFM_EINVAL, "work buffer must be 16-byte aligned");
+    if (!(dt > 0.0) && nsteps > 0) return set_error(LABFM_EINVAL, "dt must be positive");
+    return launch_rk_steps(p, Q, work, dt, nsteps, phys, as_stream(stream));
+}
+
+extern "C" int labfm_stable_dt(const labfm_plan* p, const void* fields, const double* s, double c,
+                               double mu, double* dt_out, void* stream) {
+    if (int rc = check_plan(p)) return rc;
+    if (!fields || !s || !dt_out) return set_error(LABFM_EINVAL, "null pointer argument");
+    if (!(c >= 0.0) || !(mu > 0.0)) return set_error(LABFM_EINVAL, "need c >= 0 and mu > 0");
+    return launch_stable_dt(p, fields, s, c, mu, dt_out, as_stream(stream));
+}

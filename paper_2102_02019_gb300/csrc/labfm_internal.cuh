@@ -1,0 +1,87 @@
+// Internal declarations shared by the CUDA translation units of liblabfm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "labfm.h"
+
+namespace labfm {
+
+// Record `msg` as this thread's last error and return `code`.
+int set_error(int code, const std::string& msg);
+int cuda_error(cudaError_t e, const char* what);
+
+#define LABFM_CUDA_TRY(call)                                      \
+    do {                                                          \
+        cudaError_t e_ = (call);                                  \
+        if (e_ != cudaSuccess) return ::labfm::cuda_error(e_, #call); \
+    } while (0)
+
+#define LABFM_LAUNCH_CHECK(what)                                  \
+    do {                                                          \
+        cudaError_t e_ = cudaGetLastError();                      \
+        if (e_ != cudaSuccess) return ::labfm::cuda_error(e_, what); \
+    } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Periodic minimum image, written out so that the neighbour search and the
+// weight build see bit-identical offsets (no contraction, plain IEEE ops).
+__device__ __forceinline__ double min_image(double d, double L, bool periodic) {
+    if (periodic) {
+        if (d > 0.5 * L) {
+            d = __dsub_rn(d, L);
+        } else if (d < -0.5 * L) {
+            d = __dadd_rn(d, L);
+        }
+    }
+    return d;
+}
+
+// Exclusive scan of n int32 counts into out[0..n]; out[n] = total.  The total
+// is also written (as int64) to *total_dev.  Returns LABFM_ECAPACITY through the
+// caller when the host sees total >= 2^31.
+int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int64_t* total_dev,
+                       void* scratch, size_t scratch_bytes, cudaStream_t st);
+size_t exclusive_scan_scratch_bytes(int64_t n);
+
+}  // namespace labfm
+
+// The prepared operator behind labfm_plan (see labfm.h).
+struct labfm_plan {
+    int64_t N = 0;
+    int64_t nnz = 0;
+    int64_t nnz_pad = 0;
+    labfm_dtype dtype = LABFM_F64;
+    int device = 0;
+    int group = 8;
+    int block = 256;
+    int32_t* row_ptr = nullptr;  // N + 1, every entry a multiple of 4
+    int32_t* col = nullptr;      // nnz_pad; pad entries point at the row's own node
+    void* w = nullptr;           // 5 x nnz_pad RHS weights, operator-major (dtype)
+    void* wf = nullptr;          // nnz_pad filter weights kappa_i w^hyp_ji (dtype)
+    void* inv_s = nullptr;       // N values 1/s_i (dtype), used by the F32 kernels
+    int64_t device_bytes = 0;
+};
+
+namespace labfm {
+
+// Launchers implemented in step.cu.
+int launch_rhs(const labfm_plan* p, const void* fields, void* rhs, const labfm_phys* ph,
+               int group, int block, cudaStream_t st);
+int launch_filter_soa(const labfm_plan* p, const void* in, void* out, cudaStream_t st);
+int launch_rk_steps(const labfm_plan* p, void* Q, void* work, double dt, int nsteps,
+                    const labfm_phys* ph, cudaStream_t st);
+size_t rk_work_bytes(const labfm_plan* p);
+int launch_stable_dt(const labfm_plan* p, const void* fields, const double* s, double c,
+                     double mu, double* dt_out, cudaStream_t st);
+bool launch_shape_supported(int group, int block);
+
+// Plan packing (step.cu).
+int pack_plan(labfm_plan* p, const int32_t* row_ptr, const int32_t* col, const double* w,
+              const double* kappa, const double* s, cudaStream_t st);
+
+}  // namespace labfm

@@ -1,0 +1,693 @@
+// Time-step kernels: the fused neighbour-gather right-hand side of the
+// isothermal Navier-Stokes equations (Section 7, eq. icns), the RK3(2)4[2R+]C
+// stage update fused into it, the hyperviscous filter (Section 6) and the time
+// step of eq. dt.  Also the packing of a weight set into a plan.
+//
+// Layout (per plan): rows padded to multiples of 4 entries; col and the five RHS
+// weight streams (d/dx, d/dy, d2/dx2, d2/dxdy, d2/dy2) are operator-major, so a
+// lane reads 4 consecutive entries of one stream with one 16-byte (F32) or two
+// 16-byte (F64) loads.  A node is served by a group of G lanes; lane l of the
+// group takes the 4-entry chunks l, l + G, l + 2G, ... of the row.  The 12
+// partial sums are reduced across the group with xor shuffles.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <type_traits>
+
+#include "labfm_internal.cuh"
+
+namespace labfm {
+namespace {
+
+// RK3(2)4[2R+]C (Kennedy, Carpenter & Lewis 2000), the low-storage scheme named
+// in Section 7: sub-diagonal a_{k+1,k} and weights b_k.
+constexpr double kRkA[3] = {11847461282814.0 / 36547543011857.0,
+                            3943225443063.0 / 7078155732230.0,
+                            -346793006927.0 / 4029903576067.0};
+constexpr double kRkB[4] = {1017324711453.0 / 9774461848756.0,
+                            8237718856693.0 / 13685301971492.0,
+                            57731312506979.0 / 19404895981398.0,
+                            -101169746363290.0 / 37734290219643.0};
+
+// ---------------------------------------------------------------- vector helpers
+
+__device__ __forceinline__ void load4(const float* p, float (&o)[4]) {
+    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+    o[0] = t.x;
+    o[1] = t.y;
+    o[2] = t.z;
+    o[3] = t.w;
+}
+__device__ __forceinline__ void load4(const double* p, double (&o)[4]) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+    o[0] = a.x;
+    o[1] = a.y;
+    o[2] = b.x;
+    o[3] = b.y;
+}
+__device__ __forceinline__ void load4i(const int32_t* p, int (&o)[4]) {
+    const int4 t = __ldg(reinterpret_cast<const int4*>(p));
+    o[0] = t.x;
+    o[1] = t.y;
+    o[2] = t.z;
+    o[3] = t.w;
+}
+
+// Node state (ln rho, u, v) packed for one-instruction gathers: float4 for F32
+// (w unused), two double2 for F64.
+template <typename T> struct Packed;
+template <> struct Packed<float> { float4 v; };
+template <> struct Packed<double> { double2 au; double2 vp; };
+
+__device__ __forceinline__ void unpack(const Packed<float>* p, int j, float& a, float& u, float& v) {
+    const float4 t = __ldg(&p[j].v);
+    a = t.x;
+    u = t.y;
+    v = t.z;
+}
+__device__ __forceinline__ void unpack(const Packed<double>* p, int j, double& a, double& u, double& v) {
+    const double2 t = __ldg(&p[j].au);
+    a = t.x;
+    u = t.y;
+    v = __ldg(&p[j].vp.x);
+}
+// Plain (coherent) loads for a buffer that the same kernel also writes.
+__device__ __forceinline__ void unpack_rw(const Packed<float>* p, int j, float& a, float& u, float& v) {
+    const float4 t = p[j].v;
+    a = t.x;
+    u = t.y;
+    v = t.z;
+}
+__device__ __forceinline__ void unpack_rw(const Packed<double>* p, int j, double& a, double& u, double& v) {
+    const double2 t = p[j].au;
+    a = t.x;
+    u = t.y;
+    v = p[j].vp.x;
+}
+__device__ __forceinline__ void store(Packed<float>* p, int64_t j, float a, float u, float v) {
+    p[j].v = make_float4(a, u, v, 0.0f);
+}
+__device__ __forceinline__ void store(Packed<double>* p, int64_t j, double a, double u, double v) {
+    p[j].au = make_double2(a, u);
+    p[j].vp = make_double2(v, 0.0);
+}
+
+// Field access policies for the gathers: structure-of-arrays (public API) or
+// packed (inside labfm_rk_step).
+template <typename T>
+struct SoA {
+    const T* a;
+    const T* u;
+    const T* v;
+    __device__ __forceinline__ void get(int j, T& x, T& y, T& z) const {
+        x = __ldg(a + j);
+        y = __ldg(u + j);
+        z = __ldg(v + j);
+    }
+};
+template <typename T>
+struct AoS {
+    const Packed<T>* p;
+    __device__ __forceinline__ void get(int j, T& x, T& y, T& z) const { unpack(p, j, x, y, z); }
+};
+
+// Compensated (Kahan) accumulation used for the F32 second-derivative and
+// filter sums; the F64 path adds plainly.
+template <typename T, bool KAHAN>
+struct Acc {
+    T s = T(0), c = T(0);
+    __device__ __forceinline__ void add(T x) {
+        if (KAHAN) {
+            const T y = x - c;
+            const T t = s + y;
+            c = (t - s) - y;
+            s = t;
+        } else {
+            s += x;
+        }
+    }
+    __device__ __forceinline__ T value() const { return KAHAN ? s - c : s; }
+};
+
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+template <typename T>
+struct PlanView {
+    int64_t N;
+    int64_t nnz_pad;
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const T* w;   // 5 x nnz_pad
+    const T* wf;  // nnz_pad
+    const T* inv_s;
+};
+
+template <typename T>
+PlanView<T> view(const labfm_plan* p) {
+    return PlanView<T>{p->N, p->nnz_pad, p->row_ptr, p->col, static_cast<const T*>(p->w),
+                       static_cast<const T*>(p->wf), static_cast<const T*>(p->inv_s)};
+}
+
+// The 12 derivatives of eq. icns at node i: d[0..1] = (a_x, a_y),
+// d[2..6] = (u_x, u_y, u_xx, u_xy, u_yy), d[7..11] = same for v, each
+// L^d_i(phi) = sum_j (phi_j - phi_i) w^d_ji.  Every lane of the group returns them.
+template <typename T, int G, bool KAHAN, class F>
+__device__ __forceinline__ void gather_derivatives(const PlanView<T>& P, const F& fld, int i,
+                                                   int gl, T ai, T ui, T vi, T (&d)[12]) {
+    T ax = 0, ay = 0, ux = 0, uy = 0, vx = 0, vy = 0;
+    Acc<T, KAHAN> uxx, uxy, uyy, vxx, vxy, vyy;
+    if (i >= 0) {
+        const int e0 = P.row_ptr[i];
+        const int e1 = P.row_ptr[i + 1];
+        const int64_t nz = P.nnz_pad;
+        for (int e = e0 + 4 * gl; e < e1; e += 4 * G) {
+            int cj[4];
+            T wx[4], wy[4], wxx[4], wxy[4], wyy[4];
+            load4i(P.col + e, cj);
+            load4(P.w + e, wx);
+            load4(P.w + nz + e, wy);
+            load4(P.w + 2 * nz + e, wxx);
+            load4(P.w + 3 * nz + e, wxy);
+            load4(P.w + 4 * nz + e, wyy);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                T aj, uj, vj;
+                fld.get(cj[k], aj, uj, vj);
+                const T da = aj - ai, du = uj - ui, dv = vj - vi;
+                ax = fma(da, wx[k], ax);
+                ay = fma(da, wy[k], ay);
+                ux = fma(du, wx[k], ux);
+                uy = fma(du, wy[k], uy);
+                vx = fma(dv, wx[k], vx);
+                vy = fma(dv, wy[k], vy);
+                uxx.add(du * wxx[k]);
+                uxy.add(du * wxy[k]);
+                uyy.add(du * wyy[k]);
+                vxx.add(dv * wxx[k]);
+                vxy.add(dv * wxy[k]);
+                vyy.add(dv * wyy[k]);
+            }
+        }
+    }
+    d[0] = group_sum<G>(ax);
+    d[1] = group_sum<G>(ay);
+    d[2] = group_sum<G>(ux);
+    d[3] = group_sum<G>(uy);
+    d[7] = group_sum<G>(vx);
+    d[8] = group_sum<G>(vy);
+    if (KAHAN) {
+        // the compensations are summed separately and applied once
+        d[4] = group_sum<G>(uxx.s) - group_sum<G>(uxx.c);
+        d[5] = group_sum<G>(uxy.s) - group_sum<G>(uxy.c);
+        d[6] = group_sum<G>(uyy.s) - group_sum<G>(uyy.c);
+        d[9] = group_sum<G>(vxx.s) - group_sum<G>(vxx.c);
+        d[10] = group_sum<G>(vxy.s) - group_sum<G>(vxy.c);
+        d[11] = group_sum<G>(vyy.s) - group_sum<G>(vyy.c);
+    } else {
+        d[4] = group_sum<G>(uxx.s);
+        d[5] = group_sum<G>(uxy.s);
+        d[6] = group_sum<G>(uyy.s);
+        d[9] = group_sum<G>(vxx.s);
+        d[10] = group_sum<G>(vxy.s);
+        d[11] = group_sum<G>(vyy.s);
+    }
+}
+
+__device__ __forceinline__ float exp_neg(float a) { return expf(-a); }
+__device__ __forceinline__ double exp_neg(double a) { return exp(-a); }
+
+// Pointwise right-hand side of eq. icns from the derivatives.  F32 weights are
+// nondimensional (w s^l), so the sums are scaled by s^-1 or s^-2 here.
+template <typename T, bool SCALED>
+__device__ __forceinline__ void pointwise_rhs(const T (&d)[12], T a, T u, T v, T inv_s, T c2, T mu,
+                                              T gx, T gy, T& Ra, T& Ru, T& Rv) {
+    const T s1 = SCALED ? inv_s : T(1);
+    const T s2 = SCALED ? inv_s * inv_s : T(1);
+    const T ax = d[0] * s1, ay = d[1] * s1;
+    const T ux = d[2] * s1, uy = d[3] * s1, uxx = d[4] * s2, uxy = d[5] * s2, uyy = d[6] * s2;
+    const T vx = d[7] * s1, vy = d[8] * s1, vxx = d[9] * s2, vxy = d[10] * s2, vyy = d[11] * s2;
+    const T nu = mu * exp_neg(a);
+    const T third = T(1) / T(3);
+    const T four_thirds = T(4) / T(3);
+    Ra = -(u * ax + v * ay) - (ux + vy);
+    Ru = -(u * ux + v * uy) - c2 * ax + nu * (four_thirds * uxx + uyy + third * vxy) + gx;
+    Rv = -(u * vx + v * vy) - c2 * ay + nu * (four_thirds * vyy + vxx + third * uxy) + gy;
+}
+
+template <typename T>
+struct Phys {
+    T c2, mu, gx, gy;
+};
+
+// ---------------------------------------------------------------- kernels
+
+template <typename T, int G, bool KAHAN, bool SCALED>
+__global__ void k_rhs_soa(PlanView<T> P, SoA<T> in, T* __restrict__ out, Phys<T> ph) {
+    const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t node = gt / G;
+    const int gl = int(gt % G);
+    const int i = node < P.N ? int(node) : -1;
+    T ai = 0, ui = 0, vi = 0;
+    if (i >= 0) in.get(i, ai, ui, vi);
+    T d[12];
+    gather_derivatives<T, G, KAHAN>(P, in, i, gl, ai, ui, vi, d);
+    if (i >= 0 && gl == 0) {
+        T Ra, Ru, Rv;
+        const T is = SCALED ? P.inv_s[i] : T(1);
+        pointwise_rhs<T, SCALED>(d, ai, ui, vi, is, ph.c2, ph.mu, ph.gx, ph.gy, Ra, Ru, Rv);
+        out[i] = Ra;
+        out[P.N + i] = Ru;
+        out[2 * P.N + i] = Rv;
+    }
+}
+
+// One fused RK stage: F = R(X_in) at node i; Q_out = Q_in + cb F;
+// X_out = Q_out + cx F (skipped when X_out is null).  Q_in may equal Q_out, and
+// Q_in may equal X_in (first stage, where X = Q).
+template <typename T, int G, bool KAHAN, bool SCALED>
+__global__ void k_stage(PlanView<T> P, const Packed<T>* X_in, const Packed<T>* Q_in,
+                        Packed<T>* Q_out, Packed<T>* X_out, T cb, T cx, Phys<T> ph) {
+    const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t node = gt / G;
+    const int gl = int(gt % G);
+    const int i = node < P.N ? int(node) : -1;
+    const AoS<T> fld{X_in};
+    T ai = 0, ui = 0, vi = 0;
+    if (i >= 0) fld.get(i, ai, ui, vi);
+    T d[12];
+    gather_derivatives<T, G, KAHAN>(P, fld, i, gl, ai, ui, vi, d);
+    if (i >= 0 && gl == 0) {
+        T Ra, Ru, Rv;
+        const T is = SCALED ? P.inv_s[i] : T(1);
+        pointwise_rhs<T, SCALED>(d, ai, ui, vi, is, ph.c2, ph.mu, ph.gx, ph.gy, Ra, Ru, Rv);
+        T qa, qu, qv;
+        if (Q_in == X_in) {
+            qa = ai;
+            qu = ui;
+            qv = vi;
+        } else {
+            unpack_rw(Q_in, i, qa, qu, qv);
+        }
+        qa = fma(cb, Ra, qa);
+        qu = fma(cb, Ru, qu);
+        qv = fma(cb, Rv, qv);
+        store(Q_out, i, qa, qu, qv);
+        if (X_out) store(X_out, i, fma(cx, Ra, qa), fma(cx, Ru, qu), fma(cx, Rv, qv));
+    }
+}
+
+// Filter: out_i = phi_i + sum_j (phi_j - phi_i) (kappa_i w^hyp_ji) for 3 fields.
+template <typename T, int G, bool KAHAN, class Fin>
+__device__ __forceinline__ void filter_sums(const PlanView<T>& P, const Fin& fld, int i, int gl,
+                                            T ai, T ui, T vi, T& sa, T& su, T& sv) {
+    Acc<T, KAHAN> aa, uu, vv;
+    if (i >= 0) {
+        const int e0 = P.row_ptr[i];
+        const int e1 = P.row_ptr[i + 1];
+        for (int e = e0 + 4 * gl; e < e1; e += 4 * G) {
+            int cj[4];
+            T wf[4];
+            load4i(P.col + e, cj);
+            load4(P.wf + e, wf);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                T aj, uj, vj;
+                fld.get(cj[k], aj, uj, vj);
+                aa.add((aj - ai) * wf[k]);
+                uu.add((uj - ui) * wf[k]);
+                vv.add((vj - vi) * wf[k]);
+            }
+        }
+    }
+    if (KAHAN) {
+        sa = group_sum<G>(aa.s) - group_sum<G>(aa.c);
+        su = group_sum<G>(uu.s) - group_sum<G>(uu.c);
+        sv = group_sum<G>(vv.s) - group_sum<G>(vv.c);
+    } else {
+        sa = group_sum<G>(aa.s);
+        su = group_sum<G>(uu.s);
+        sv = group_sum<G>(vv.s);
+    }
+}
+
+template <typename T, int G, bool KAHAN>
+__global__ void k_filter_soa(PlanView<T> P, SoA<T> in, T* __restrict__ out) {
+    const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t node = gt / G;
+    const int gl = int(gt % G);
+    const int i = node < P.N ? int(node) : -1;
+    T ai = 0, ui = 0, vi = 0;
+    if (i >= 0) in.get(i, ai, ui, vi);
+    T sa, su, sv;
+    filter_sums<T, G, KAHAN>(P, in, i, gl, ai, ui, vi, sa, su, sv);
+    if (i >= 0 && gl == 0) {
+        out[i] = ai + sa;
+        out[P.N + i] = ui + su;
+        out[2 * P.N + i] = vi + sv;
+    }
+}
+
+template <typename T, int G, bool KAHAN>
+__global__ void k_filter_aos(PlanView<T> P, const Packed<T>* in, Packed<T>* out) {
+    const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t node = gt / G;
+    const int gl = int(gt % G);
+    const int i = node < P.N ? int(node) : -1;
+    const AoS<T> fld{in};
+    T ai = 0, ui = 0, vi = 0;
+    if (i >= 0) fld.get(i, ai, ui, vi);
+    T sa, su, sv;
+    filter_sums<T, G, KAHAN>(P, fld, i, gl, ai, ui, vi, sa, su, sv);
+    if (i >= 0 && gl == 0) store(out, i, ai + sa, ui + su, vi + sv);
+}
+
+template <typename T>
+__global__ void k_pack(int64_t N, const T* __restrict__ soa, Packed<T>* __restrict__ out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < N;
+         i += int64_t(gridDim.x) * blockDim.x)
+        store(out, i, soa[i], soa[N + i], soa[2 * N + i]);
+}
+
+template <typename T>
+__global__ void k_unpack(int64_t N, const Packed<T>* __restrict__ in, T* __restrict__ soa) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < N;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        T a, u, v;
+        unpack(in, int(i), a, u, v);
+        soa[i] = a;
+        soa[N + i] = u;
+        soa[2 * N + i] = v;
+    }
+}
+
+// eq. dt, reduced with an exact minimum (order independent).
+template <typename T>
+__global__ void k_dt(int64_t N, const T* __restrict__ f, const double* __restrict__ s, double c,
+                     double mu, unsigned long long* __restrict__ out) {
+    double best = INFINITY;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < N;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const double a = double(f[i]), u = double(f[N + i]), v = double(f[2 * N + i]);
+        const double si = s[i];
+        const double conv = 1.0 * si / (sqrt(u * u + v * v) + c);
+        const double visc = 0.4 * si * si * exp(a) / mu;
+        best = fmin(best, fmin(conv, visc));
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) best = fmin(best, __shfl_xor_sync(0xffffffffu, best, off));
+    if ((threadIdx.x & 31) == 0 && best < INFINITY)
+        atomicMin(out, static_cast<unsigned long long>(__double_as_longlong(best)));
+}
+
+__global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v; }
+
+// ---------------------------------------------------------------- plan packing
+
+__global__ void k_padded_counts(int64_t N, const int32_t* __restrict__ row_ptr,
+                                int32_t* __restrict__ cnt) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < N;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        const int len = row_ptr[i + 1] - row_ptr[i];
+        cnt[i] = (len + 3) & ~3;
+    }
+}
+
+// Warp per row: copy col, scale the RHS weights (F32: w s^l), fold kappa into
+// the filter weights, and fill the pad entries (self, weight 0).
+template <typename T, bool SCALED>
+__global__ void k_pack_rows(int64_t N, int64_t nnz, int64_t nnz_pad,
+                            const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                            const double* __restrict__ w, const double* __restrict__ kappa,
+                            const double* __restrict__ s, const int32_t* __restrict__ prow,
+                            int32_t* __restrict__ pcol, T* __restrict__ pw, T* __restrict__ pwf,
+                            T* __restrict__ inv_s) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; i < N; i += warps) {
+        const int r0 = row_ptr[i], len = row_ptr[i + 1] - r0;
+        const int p0 = prow[i], plen = prow[i + 1] - p0;
+        const double si = s[i];
+        const double sc1 = SCALED ? si : 1.0;
+        const double sc2 = SCALED ? si * si : 1.0;
+        const double kap = kappa[i];
+        for (int e = lane; e < plen; e += 32) {
+            const int64_t dst = int64_t(p0) + e;
+            if (e < len) {
+                const int64_t src = int64_t(r0) + e;
+                pcol[dst] = col[src];
+                pw[dst] = T(w[src] * sc1);
+                pw[nnz_pad + dst] = T(w[nnz + src] * sc1);
+                pw[2 * nnz_pad + dst] = T(w[2 * nnz + src] * sc2);
+                pw[3 * nnz_pad + dst] = T(w[3 * nnz + src] * sc2);
+                pw[4 * nnz_pad + dst] = T(w[4 * nnz + src] * sc2);
+                pwf[dst] = T(kap * w[5 * nnz + src]);
+            } else {
+                pcol[dst] = int32_t(i);
+                for (int d = 0; d < 5; ++d) pw[d * nnz_pad + dst] = T(0);
+                pwf[dst] = T(0);
+            }
+        }
+        if (lane == 0 && inv_s) inv_s[i] = T(1.0 / si);
+    }
+}
+
+int grid_for(int64_t threads, int block) { return int((threads + block - 1) / block); }
+
+// ---------------------------------------------------------------- dispatch
+
+template <typename T, int G>
+int rhs_launch_g(const labfm_plan* p, const void* fields, void* rhs, const Phys<T>& ph, int block,
+                 cudaStream_t st) {
+    const T* f = static_cast<const T*>(fields);
+    SoA<T> in{f, f + p->N, f + 2 * p->N};
+    const int grid = grid_for(p->N * G, block);
+    if (std::is_same<T, float>::value)
+        k_rhs_soa<T, G, true, true><<<grid, block, 0, st>>>(view<T>(p), in, static_cast<T*>(rhs), ph);
+    else
+        k_rhs_soa<T, G, false, false><<<grid, block, 0, st>>>(view<T>(p), in, static_cast<T*>(rhs), ph);
+    LABFM_LAUNCH_CHECK("rhs kernel");
+    return LABFM_OK;
+}
+
+template <typename T>
+int rhs_launch(const labfm_plan* p, const void* fields, void* rhs, const labfm_phys* php, int group,
+               int block, cudaStream_t st) {
+    const Phys<T> ph{T(php->c2), T(php->mu), T(php->gx), T(php->gy)};
+    switch (group) {
+        case 4: return rhs_launch_g<T, 4>(p, fields, rhs, ph, block, st);
+        case 8: return rhs_launch_g<T, 8>(p, fields, rhs, ph, block, st);
+        case 16: return rhs_launch_g<T, 16>(p, fields, rhs, ph, block, st);
+        case 32: return rhs_launch_g<T, 32>(p, fields, rhs, ph, block, st);
+    }
+    return set_error(LABFM_EINVAL, "unsupported group size");
+}
+
+template <typename T, int G>
+int stage_launch_g(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* qin, Packed<T>* qout,
+                   Packed<T>* xout, T cb, T cx, const Phys<T>& ph, cudaStream_t st) {
+    const int block = p->block;
+    const int grid = grid_for(p->N * G, block);
+    if (std::is_same<T, float>::value)
+        k_stage<T, G, true, true><<<grid, block, 0, st>>>(view<T>(p), xin, qin, qout, xout, cb, cx, ph);
+    else
+        k_stage<T, G, false, false><<<grid, block, 0, st>>>(view<T>(p), xin, qin, qout, xout, cb, cx, ph);
+    LABFM_LAUNCH_CHECK("rk stage kernel");
+    return LABFM_OK;
+}
+
+template <typename T>
+int stage_launch(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* qin, Packed<T>* qout,
+                 Packed<T>* xout, T cb, T cx, const Phys<T>& ph, cudaStream_t st) {
+    switch (p->group) {
+        case 4: return stage_launch_g<T, 4>(p, xin, qin, qout, xout, cb, cx, ph, st);
+        case 8: return stage_launch_g<T, 8>(p, xin, qin, qout, xout, cb, cx, ph, st);
+        case 16: return stage_launch_g<T, 16>(p, xin, qin, qout, xout, cb, cx, ph, st);
+        case 32: return stage_launch_g<T, 32>(p, xin, qin, qout, xout, cb, cx, ph, st);
+    }
+    return set_error(LABFM_EINVAL, "unsupported group size");
+}
+
+template <typename T, int G>
+int filter_aos_g(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaStream_t st) {
+    const int grid = grid_for(p->N * G, p->block);
+    k_filter_aos<T, G, std::is_same<T, float>::value><<<grid, p->block, 0, st>>>(view<T>(p), in, out);
+    LABFM_LAUNCH_CHECK("filter kernel");
+    return LABFM_OK;
+}
+
+template <typename T>
+int filter_aos(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaStream_t st) {
+    switch (p->group) {
+        case 4: return filter_aos_g<T, 4>(p, in, out, st);
+        case 8: return filter_aos_g<T, 8>(p, in, out, st);
+        case 16: return filter_aos_g<T, 16>(p, in, out, st);
+        case 32: return filter_aos_g<T, 32>(p, in, out, st);
+    }
+    return set_error(LABFM_EINVAL, "unsupported group size");
+}
+
+template <typename T, int G>
+int filter_soa_g(const labfm_plan* p, const void* in, void* out, cudaStream_t st) {
+    const T* f = static_cast<const T*>(in);
+    SoA<T> src{f, f + p->N, f + 2 * p->N};
+    const int grid = grid_for(p->N * G, p->block);
+    k_filter_soa<T, G, std::is_same<T, float>::value><<<grid, p->block, 0, st>>>(view<T>(p), src,
+                                                                                  static_cast<T*>(out));
+    LABFM_LAUNCH_CHECK("filter kernel");
+    return LABFM_OK;
+}
+
+template <typename T>
+int filter_soa(const labfm_plan* p, const void* in, void* out, cudaStream_t st) {
+    switch (p->group) {
+        case 4: return filter_soa_g<T, 4>(p, in, out, st);
+        case 8: return filter_soa_g<T, 8>(p, in, out, st);
+        case 16: return filter_soa_g<T, 16>(p, in, out, st);
+        case 32: return filter_soa_g<T, 32>(p, in, out, st);
+    }
+    return set_error(LABFM_EINVAL, "unsupported group size");
+}
+
+// nsteps complete steps.  Work holds three packed buffers P (solution Q), X, Y:
+//   X <- pack(Q)
+//   per step:  stage 1: gather X, Q_i from X, P <- Q, Y <- X-update
+//              stage 2: gather Y, P in place, X <- update
+//              stage 3: gather X, P in place, Y <- update
+//              stage 4: gather Y, P in place
+//              filter:  gather P, X <- filtered (the next step's Q = X)
+//   Q <- unpack(X)
+template <typename T>
+int rk_steps(const labfm_plan* p, void* Q, void* work, double dt, int nsteps, const labfm_phys* php,
+             cudaStream_t st) {
+    if (nsteps == 0) return LABFM_OK;
+    const Phys<T> ph{T(php->c2), T(php->mu), T(php->gx), T(php->gy)};
+    Packed<T>* P = static_cast<Packed<T>*>(work);
+    Packed<T>* X = P + p->N;
+    Packed<T>* Y = X + p->N;
+    const int pg = int(std::min<int64_t>((p->N + 255) / 256, 65535));
+    k_pack<T><<<pg, 256, 0, st>>>(p->N, static_cast<const T*>(Q), X);
+    LABFM_LAUNCH_CHECK("pack kernel");
+    T cb[4], cx[4];
+    for (int k = 0; k < 4; ++k) {
+        cb[k] = T(dt * kRkB[k]);
+        cx[k] = k < 3 ? T(dt * (kRkA[k] - kRkB[k])) : T(0);
+    }
+    int rc;
+    for (int step = 0; step < nsteps; ++step) {
+        if ((rc = stage_launch<T>(p, X, X, P, Y, cb[0], cx[0], ph, st))) return rc;
+        if ((rc = stage_launch<T>(p, Y, P, P, X, cb[1], cx[1], ph, st))) return rc;
+        if ((rc = stage_launch<T>(p, X, P, P, Y, cb[2], cx[2], ph, st))) return rc;
+        if ((rc = stage_launch<T>(p, Y, P, P, nullptr, cb[3], cx[3], ph, st))) return rc;
+        if ((rc = filter_aos<T>(p, P, X, st))) return rc;
+    }
+    k_unpack<T><<<pg, 256, 0, st>>>(p->N, X, static_cast<T*>(Q));
+    LABFM_LAUNCH_CHECK("unpack kernel");
+    return LABFM_OK;
+}
+
+}  // namespace
+
+bool launch_shape_supported(int group, int block) {
+    const bool g_ok = group == 4 || group == 8 || group == 16 || group == 32;
+    return g_ok && block >= 64 && block <= 1024 && block % 32 == 0 && block % group == 0;
+}
+
+int launch_rhs(const labfm_plan* p, const void* fields, void* rhs, const labfm_phys* ph, int group,
+               int block, cudaStream_t st) {
+    return p->dtype == LABFM_F32 ? rhs_launch<float>(p, fields, rhs, ph, group, block, st)
+                                 : rhs_launch<double>(p, fields, rhs, ph, group, block, st);
+}
+
+int launch_filter_soa(const labfm_plan* p, const void* in, void* out, cudaStream_t st) {
+    return p->dtype == LABFM_F32 ? filter_soa<float>(p, in, out, st)
+                                 : filter_soa<double>(p, in, out, st);
+}
+
+size_t rk_work_bytes(const labfm_plan* p) {
+    const size_t per = p->dtype == LABFM_F32 ? sizeof(Packed<float>) : sizeof(Packed<double>);
+    return size_t(3) * size_t(p->N) * per;
+}
+
+int launch_rk_steps(const labfm_plan* p, void* Q, void* work, double dt, int nsteps,
+                    const labfm_phys* ph, cudaStream_t st) {
+    return p->dtype == LABFM_F32 ? rk_steps<float>(p, Q, work, dt, nsteps, ph, st)
+                                 : rk_steps<double>(p, Q, work, dt, nsteps, ph, st);
+}
+
+int launch_stable_dt(const labfm_plan* p, const void* fields, const double* s, double c, double mu,
+                     double* dt_out, cudaStream_t st) {
+    unsigned long long* out = reinterpret_cast<unsigned long long*>(dt_out);
+    const unsigned long long inf_bits = 0x7ff0000000000000ull;
+    k_set_u64<<<1, 1, 0, st>>>(out, inf_bits);
+    const int grid = int(std::min<int64_t>((p->N + 255) / 256, 1184));
+    if (p->dtype == LABFM_F32)
+        k_dt<float><<<grid, 256, 0, st>>>(p->N, static_cast<const float*>(fields), s, c, mu, out);
+    else
+        k_dt<double><<<grid, 256, 0, st>>>(p->N, static_cast<const double*>(fields), s, c, mu, out);
+    LABFM_LAUNCH_CHECK("dt kernel");
+    return LABFM_OK;
+}
+
+int pack_plan(labfm_plan* p, const int32_t* row_ptr, const int32_t* col, const double* w,
+              const double* kappa, const double* s, cudaStream_t st) {
+    const int64_t N = p->N;
+    // padded row pointers
+    LABFM_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&p->row_ptr), size_t(N + 1) * sizeof(int32_t)));
+    p->device_bytes += (N + 1) * sizeof(int32_t);
+    int32_t* cnt = nullptr;
+    int64_t* total = nullptr;
+    void* scan_tmp = nullptr;
+    const size_t scan_bytes = exclusive_scan_scratch_bytes(N);
+    LABFM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&cnt), size_t(N) * sizeof(int32_t), st));
+    LABFM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&total), sizeof(int64_t), st));
+    LABFM_CUDA_TRY(cudaMallocAsync(&scan_tmp, scan_bytes, st));
+    const int g = int(std::min<int64_t>((N + 255) / 256, 65535));
+    k_padded_counts<<<g, 256, 0, st>>>(N, row_ptr, cnt);
+    int rc = exclusive_scan_i32(cnt, p->row_ptr, N, total, scan_tmp, scan_bytes, st);
+    int64_t nnz_pad = 0;
+    if (rc == LABFM_OK) {
+        cudaError_t e = cudaMemcpyAsync(&nnz_pad, total, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_error(e, "reading padded size");
+    }
+    cudaFreeAsync(cnt, st);
+    cudaFreeAsync(total, st);
+    cudaFreeAsync(scan_tmp, st);
+    if (rc) return rc;
+    if (nnz_pad >= (int64_t(1) << 31)) return set_error(LABFM_ECAPACITY, "padded stencil exceeds 2^31 entries");
+    p->nnz_pad = nnz_pad;
+    const size_t es = p->dtype == LABFM_F32 ? sizeof(float) : sizeof(double);
+    const size_t np = size_t(std::max<int64_t>(nnz_pad, 4));
+    LABFM_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&p->col), np * sizeof(int32_t)));
+    LABFM_CUDA_TRY(cudaMalloc(&p->w, 5 * np * es));
+    LABFM_CUDA_TRY(cudaMalloc(&p->wf, np * es));
+    p->device_bytes += np * (sizeof(int32_t) + 6 * es);
+    if (p->dtype == LABFM_F32) {
+        LABFM_CUDA_TRY(cudaMalloc(&p->inv_s, size_t(N) * es));
+        p->device_bytes += N * es;
+    }
+    const int gw = int(std::min<int64_t>((N * 32 + 255) / 256, 1 << 20));
+    if (p->dtype == LABFM_F32)
+        k_pack_rows<float, true><<<gw, 256, 0, st>>>(N, p->nnz, nnz_pad, row_ptr, col, w, kappa, s,
+                                                     p->row_ptr, p->col, static_cast<float*>(p->w),
+                                                     static_cast<float*>(p->wf),
+                                                     static_cast<float*>(p->inv_s));
+    else
+        k_pack_rows<double, false><<<gw, 256, 0, st>>>(N, p->nnz, nnz_pad, row_ptr, col, w, kappa, s,
+                                                       p->row_ptr, p->col, static_cast<double*>(p->w),
+                                                       static_cast<double*>(p->wf), nullptr);
+    LABFM_LAUNCH_CHECK("plan pack kernel");
+    LABFM_CUDA_TRY(cudaStreamSynchronize(st));
+    return LABFM_OK;
+}
+
+}  // namespace labfm

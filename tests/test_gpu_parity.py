@@ -1,0 +1,340 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bars: neighbour lists bit-exact; FP64 right-hand side, filter, RK steps and dt
+within 1e-12 relative L2 of the oracle given identical weights; GPU-built FP64
+weights within a conditioning-scaled bound; FP32 results within the rounding
+budget derived in test_gpu_fp32.py.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import labfm_inputs as li
+from oracle import core as oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS64 = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module")
+def lb():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2102_02019_gb300 as lb
+    return lb
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+class Case:
+    """A node set with its oracle stencil, oracle weights and GPU-built data."""
+
+    def __init__(self, lb, ns, rows_for_weights=None):
+        self.ns = ns
+        self.xy = _dev(ns.xy)
+        self.h = _dev(ns.h)
+        self.s = _dev(ns.s)
+        self.row_ptr, self.col = lb.build_stencils(self.xy, self.h, ns.Lx, ns.Ly)
+        self.rp_o, self.col_o = oracle.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly)
+        self.gw = lb.build_weights(self.xy, self.h, self.s, ns.Lx, ns.Ly, self.row_ptr, self.col, ns.m)
+        self.ow = oracle.build_weights(ns.xy, ns.h, ns.s, self.rp_o, self.col_o, ns.m, ns.Lx, ns.Ly,
+                                       want_cond=True)
+
+
+@pytest.fixture(scope="module")
+def c1(lb):
+    # 64 x 64 jittered lattice, m = 4, h/s = 1.7 (the small Taylor-Green workload)
+    return Case(lb, li.tgv_lattice(64, m=4, h_over_s=1.7, jitter=0.3, seed=0))
+
+
+@pytest.fixture(scope="module")
+def ragged(lb):
+    # non-square ragged lattice, m = 6
+    return Case(lb, li.tgv_lattice(37, 29, m=6, h_over_s=2.2, jitter=0.3, seed=5))
+
+
+# ---------------------------------------------------------------- stencils
+
+def test_stencils_bit_exact_small(c1, ragged):
+    for c in (c1, ragged):
+        assert np.array_equal(c.row_ptr.cpu().numpy(), c.rp_o)
+        assert np.array_equal(c.col.cpu().numpy(), c.col_o)
+
+
+@pytest.mark.parametrize("case", ["varh", "nonperiodic", "tiny", "wide_h"])
+def test_stencils_bit_exact_edge_cases(lb, case):
+    if case == "varh":
+        ns = li.tgv_lattice(40, 33, m=4, jitter=0.3, seed=8)
+        ns.h = ns.h * np.random.default_rng(3).uniform(0.7, 1.6, size=ns.N)
+        per = (True, True)
+    elif case == "nonperiodic":
+        ns = li.tgv_lattice(30, 30, m=4, jitter=0.3, seed=9)
+        per = (False, False)
+    elif case == "tiny":
+        ns = li.tgv_lattice(3, 2, m=2, jitter=0.3, seed=10)
+        per = (True, True)
+    else:  # stencil wider than half the box: every cell visited once
+        ns = li.tgv_lattice(6, 5, m=2, h_over_s=2.9, jitter=0.3, seed=11)
+        per = (True, True)
+    xy, h = _dev(ns.xy), _dev(ns.h)
+    rp, col = lb.build_stencils(xy, h, ns.Lx, ns.Ly, periodic=per)
+    rp_o, col_o = oracle.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly, periodic=per)
+    assert np.array_equal(rp.cpu().numpy(), rp_o)
+    assert np.array_equal(col.cpu().numpy(), col_o)
+
+
+def test_stencil_points_exactly_on_the_radius(lb):
+    # offsets of exactly 2h (representable) must be included, as in the oracle
+    xy = np.array([[0.25, 0.25], [0.5, 0.25], [0.25, 0.5], [0.75, 0.75], [0.0, 0.25]])
+    h = np.full(5, 0.125)
+    rp, col = lb.build_stencils(_dev(xy), _dev(h), 1.0, 1.0)
+    rp_o, col_o = oracle.neighbours(xy, h, 1.0, 1.0)
+    assert np.array_equal(rp.cpu().numpy(), rp_o) and np.array_equal(col.cpu().numpy(), col_o)
+    assert 1 in col_o[rp_o[0]:rp_o[1]] and 2 in col_o[rp_o[0]:rp_o[1]]
+
+
+def test_stencil_capacity_and_invalid_input(lb):
+    ns = li.tgv_lattice(16, m=4, seed=1)
+    xy, h = _dev(ns.xy), _dev(ns.h)
+    import ctypes
+    N = ns.N
+    rp = torch.empty(N + 1, dtype=torch.int32, device="cuda")
+    small = torch.full((10,), -7, dtype=torch.int32, device="cuda")
+    nnz = ctypes.c_int64(0)
+    st = torch.cuda.current_stream().cuda_stream
+    rc = lb.lib.labfm_build_stencils(xy.data_ptr(), h.data_ptr(), N, ns.Lx, ns.Ly, 3, rp.data_ptr(),
+                                     small.data_ptr(), 10, ctypes.byref(nnz), st)
+    assert rc == 4 and nnz.value > 10
+    assert torch.all(small == -7)  # nothing written past the capacity check
+    bad = ns.xy.copy()
+    bad[5, 0] = 1.5  # outside the box
+    with pytest.raises(lb.LabfmError) as ei:
+        lb.build_stencils(_dev(bad), h, ns.Lx, ns.Ly)
+    assert ei.value.status == 1
+
+
+# ---------------------------------------------------------------- weights
+
+def _weight_errors(c):
+    """Per node: max over operators of |w_gpu - w_oracle| / max_j |w_oracle| for that operator."""
+    wg = c.gw["w"].cpu().numpy()
+    wo = c.ow["w"]
+    rp = c.rp_o
+    N = len(rp) - 1
+    err = np.zeros(N)
+    for i in range(N):
+        sl = slice(rp[i], rp[i + 1])
+        scale = np.abs(wo[:, sl]).max(axis=1, keepdims=True)
+        err[i] = (np.abs(wg[:, sl] - wo[:, sl]) / scale).max()
+    return err
+
+
+def test_weights_match_oracle_within_conditioning(c1, ragged):
+    for c in (c1, ragged):
+        n = oracle.n_unknowns(c.ns.m)
+        assert int(c.gw["status"].abs().sum().item()) == 0
+        err = _weight_errors(c)
+        bound = np.maximum(50.0 * n * EPS64 * c.ow["cond1"], 1e-13)
+        assert np.all(err <= bound), (err / bound).max()
+        kg = c.gw["kappa"].cpu().numpy()
+        ko = c.ow["kappa"]
+        assert np.all(np.abs(kg - ko) <= np.abs(ko) * bound)
+        # reproduction residual of eq. lsys, nondimensional
+        assert float(c.gw["residual"].max().item()) < 1e-10 * max(1.0, 6.0 * (c.ns.m // 2))
+
+
+@pytest.mark.parametrize("m,hs,nx", [(2, 1.2, 20), (8, 2.8, 24), (10, 3.3, 24)])
+def test_weights_other_orders(lb, m, hs, nx):
+    ns = li.tgv_lattice(nx, m=m, h_over_s=hs, jitter=0.3, seed=20 + m)
+    c = Case(lb, ns)
+    assert int(c.gw["status"].abs().sum().item()) == 0
+    # operator outputs on smooth functions agree far inside the raw-weight bound
+    wg = c.gw["w"].cpu().numpy()
+    wo = c.ow["w"]
+    x, y = ns.xy[:, 0], ns.xy[:, 1]
+    f = np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y) + 0.3 * np.cos(4 * np.pi * x)
+    for d in range(5):
+        lg = oracle.apply_op(f, wg[d], c.rp_o, c.col_o)
+        lo = oracle.apply_op(f, wo[d], c.rp_o, c.col_o)
+        scale = np.abs(lo).max()
+        assert np.abs(lg - lo).max() <= 1e-7 * scale, (d, np.abs(lg - lo).max() / scale)
+    err = _weight_errors(c)
+    n = oracle.n_unknowns(m)
+    bound = np.maximum(50.0 * n * EPS64 * c.ow["cond1"], 1e-13)
+    assert np.all(err <= bound)
+
+
+def test_weights_flag_nodes_with_too_few_neighbours(lb):
+    ns = li.tgv_lattice(12, m=8, h_over_s=1.0, jitter=0.3, seed=3)  # ~12 neighbours < n = 44
+    xy, h, s = _dev(ns.xy), _dev(ns.h), _dev(ns.s)
+    rp, col = lb.build_stencils(xy, h, ns.Lx, ns.Ly)
+    with pytest.raises(lb.LabfmError) as ei:
+        lb.build_weights(xy, h, s, ns.Lx, ns.Ly, rp, col, 8, check=True)
+    assert ei.value.status == 5
+    out = lb.build_weights(xy, h, s, ns.Lx, ns.Ly, rp, col, 8)
+    st = out["status"].cpu().numpy()
+    assert np.all(st & lb.NODE_FEW_NEIGHBOURS)
+
+
+# ---------------------------------------------------------------- right-hand side, FP64
+
+def _plan(lb, c, w, kappa, dtype):
+    return lb.Plan(c.row_ptr, c.col, _dev(w) if isinstance(w, np.ndarray) else w,
+                   _dev(kappa) if isinstance(kappa, np.ndarray) else kappa, c.s, dtype=dtype)
+
+
+def _rel_l2(a, b):
+    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
+
+
+@pytest.mark.parametrize("which", ["c1", "ragged"])
+def test_rhs_fp64_matches_oracle(lb, c1, ragged, which):
+    c = c1 if which == "c1" else ragged
+    plan = _plan(lb, c, c.ow["w"], c.ow["kappa"], torch.float64)
+    q = li.perturbed_tgv_fields(c.ns.xy, 10.0, amplitude=0.05, kmax=4)
+    phys = lb.Phys(c2=100.0, mu=0.005, gx=0.1, gy=-0.2)
+    R = lb.rhs(plan, _dev(q), phys).cpu().numpy()
+    Ro = oracle.rhs(q, c.ow["w"][:5], c.rp_o, c.col_o, 100.0, 0.005, (0.1, -0.2))
+    assert np.all(_rel_l2(R, Ro) <= 1e-12), _rel_l2(R, Ro)
+    # every launch shape gives the same result to rounding
+    for g, b in ((4, 128), (16, 256), (32, 512)):
+        plan.set_launch(g, b)
+        R2 = lb.rhs(plan, _dev(q), phys).cpu().numpy()
+        assert np.all(_rel_l2(R2, Ro) <= 1e-12)
+
+
+def test_filter_fp64_matches_oracle(lb, c1):
+    c = c1
+    plan = _plan(lb, c, c.ow["w"], c.ow["kappa"], torch.float64)
+    q = li.perturbed_tgv_fields(c.ns.xy, 10.0, amplitude=0.1, kmax=8)
+    F = lb.filter(plan, _dev(q)).cpu().numpy()
+    Fo = oracle.filter_fields(q, c.ow["w"][5], c.ow["kappa"], c.rp_o, c.col_o)
+    # compare the filter increments (the fields themselves agree trivially)
+    assert np.all(_rel_l2(F - q, Fo - q) <= 1e-12), _rel_l2(F - q, Fo - q)
+
+
+def test_stable_dt_matches_oracle(lb, c1):
+    c = c1
+    plan = _plan(lb, c, c.ow["w"], c.ow["kappa"], torch.float64)
+    q = li.tgv_fields(c.ns.xy, 10.0)
+    for mu in (0.005, 2.0):
+        dt = float(lb.stable_dt(plan, _dev(q), c.s, 10.0, mu).item())
+        dto = oracle.stable_dt(q, c.ns.s, 10.0, mu)
+        assert abs(dt - dto) <= 4 * EPS64 * dto
+
+
+@pytest.mark.parametrize("nsteps", [1, 3])
+def test_rk_step_fp64_matches_oracle(lb, c1, nsteps):
+    c = c1
+    plan = _plan(lb, c, c.ow["w"], c.ow["kappa"], torch.float64)
+    q0 = li.tgv_fields(c.ns.xy, 10.0)
+    dt = oracle.stable_dt(q0, c.ns.s, 10.0, 0.005)
+    Q = _dev(q0)
+    lb.rk_step(plan, Q, dt, nsteps, lb.Phys(100.0, 0.005))
+    qo = q0
+    for _ in range(nsteps):
+        qo = oracle.time_step(qo, dt, c.ow["w"], c.ow["kappa"], c.rp_o, c.col_o, 100.0, 0.005)
+    # compare the change over the steps, a stricter test than the state
+    assert np.all(_rel_l2(Q.cpu().numpy() - q0, qo - q0) <= 1e-12)
+
+
+def test_trajectory_fp64_100_steps(lb):
+    # the small Taylor-Green workload geometry with the regular jitter of the
+    # stable runs (+-0.1 s), 100 steps, GPU-built weights on both sides
+    ns = li.tgv_lattice(64, m=4, h_over_s=1.7, jitter=0.1, seed=0)
+    c = Case(lb, ns)
+    wg = c.gw["w"].cpu().numpy()
+    kg = c.gw["kappa"].cpu().numpy()
+    plan = _plan(lb, c, c.gw["w"], c.gw["kappa"], torch.float64)
+    q0 = li.tgv_fields(ns.xy, 10.0)
+    dt = oracle.stable_dt(q0, ns.s, 10.0, 0.005)
+    Q = _dev(q0)
+    lb.rk_step(plan, Q, dt, 100, lb.Phys(100.0, 0.005))
+    qo = q0
+    for _ in range(100):
+        qo = oracle.time_step(qo, dt, wg, kg, c.rp_o, c.col_o, 100.0, 0.005)
+    assert np.all(_rel_l2(Q.cpu().numpy(), qo) <= 1e-12), _rel_l2(Q.cpu().numpy(), qo)
+    assert np.all(_rel_l2(Q.cpu().numpy() - q0, qo - q0) <= 1e-10)
+
+
+def test_zero_steps_and_bad_workspace(lb, c1):
+    c = c1
+    plan = _plan(lb, c, c.ow["w"], c.ow["kappa"], torch.float64)
+    q0 = _dev(li.tgv_fields(c.ns.xy, 10.0))
+    Q = q0.clone()
+    lb.rk_step(plan, Q, 1e-3, 0, lb.Phys(100.0, 0.005))
+    assert torch.equal(Q, q0)
+    with pytest.raises(lb.LabfmError):
+        lb.rk_step(plan, Q, 1e-3, 1, lb.Phys(100.0, 0.005),
+                   work=torch.empty(16, dtype=torch.uint8, device="cuda"))
+
+
+# ---------------------------------------------------------------- full-size workload, sampled
+
+@pytest.fixture(scope="module")
+def c2(lb):
+    ns = li.tgv_lattice(512, m=8, h_over_s=2.8, jitter=0.3, seed=1)
+    xy, h, s = _dev(ns.xy), _dev(ns.h), _dev(ns.s)
+    rp, col = lb.build_stencils(xy, h, ns.Lx, ns.Ly)
+    wb = lb.build_weights(xy, h, s, ns.Lx, ns.Ly, rp, col, ns.m)
+    rows = np.sort(np.random.default_rng(0).choice(ns.N, size=96, replace=False))
+    rows = np.concatenate([[0, ns.N - 1], rows])
+    return dict(ns=ns, xy=xy, h=h, s=s, rp=rp, col=col, wb=wb, rows=rows)
+
+
+def test_fullsize_stencil_rows_bit_exact(c2):
+    ns = c2["ns"]
+    rp = c2["rp"].cpu().numpy()
+    col = c2["col"].cpu().numpy()
+    for i in c2["rows"]:
+        ref = oracle.neighbours_of(ns.xy, ns.h, int(i), ns.Lx, ns.Ly)
+        assert np.array_equal(col[rp[i]:rp[i + 1]], ref)
+    assert abs(rp[-1] / ns.N / (4 * math.pi * 2.8 ** 2) - 1) < 0.02
+
+
+def test_fullsize_weights_sampled(c2):
+    ns = c2["ns"]
+    rows = c2["rows"]
+    rp = c2["rp"].cpu().numpy()
+    col = c2["col"].cpu().numpy()
+    rp_r = np.concatenate([[0], np.cumsum(rp[rows + 1] - rp[rows])])
+    col_r = np.concatenate([col[rp[i]:rp[i + 1]] for i in rows])
+    ow = oracle.build_weights(ns.xy, ns.h, ns.s, rp_r, col_r, ns.m, ns.Lx, ns.Ly, rows=rows,
+                              want_cond=True)
+    wg = c2["wb"]["w"].cpu().numpy()
+    assert int(c2["wb"]["status"].abs().sum().item()) == 0
+    n = oracle.n_unknowns(ns.m)
+    for k, i in enumerate(rows):
+        a, b = rp[i], rp[i + 1]
+        wo = ow["w"][:, rp_r[k]:rp_r[k + 1]]
+        scale = np.abs(wo).max(axis=1, keepdims=True)
+        err = (np.abs(wg[:, a:b] - wo) / scale).max()
+        assert err <= max(50 * n * EPS64 * ow["cond1"][k], 1e-13)
+
+
+def test_fullsize_rhs_fp64_sampled(lb, c2):
+    ns = c2["ns"]
+    plan = lb.Plan(c2["rp"], c2["col"], c2["wb"]["w"], c2["wb"]["kappa"], c2["s"], dtype=torch.float64)
+    q = li.tgv_fields(ns.xy, 10.0)
+    R = lb.rhs(plan, _dev(q), lb.Phys(100.0, 0.005)).cpu().numpy()
+    rows = c2["rows"]
+    rp = c2["rp"].cpu().numpy()
+    col = c2["col"].cpu().numpy()
+    wg = c2["wb"]["w"].cpu().numpy()
+    # oracle RHS at the sampled rows with the same weights
+    cnt = np.zeros(ns.N, dtype=np.int64)
+    cnt[rows] = rp[rows + 1] - rp[rows]
+    rps = np.concatenate([[0], np.cumsum(cnt)])
+    idx = np.concatenate([np.arange(rp[i], rp[i + 1]) for i in rows])
+    Ro = oracle.rhs(q, wg[:5, idx], rps, col[idx], 100.0, 0.005)
+    for f in range(3):
+        err = np.abs(R[f][rows] - Ro[f][rows]).max() / np.abs(Ro[f][rows]).max()
+        assert err <= 1e-12, (f, err)
+    plan.close()
