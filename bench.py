@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark of the LABFM hot path on one GB300 (or N independent replicas).
+
+Workload: the 512 x 512 jittered-lattice Taylor-Green vortex (262,144 nodes,
+m = 8, h/s = 2.8, about 98 neighbours per node), FP64 weight build, then RK
+steps with FP32 fields and FP32 weights (the headline) and with FP64 fields and
+weights (the comparison).  A timed step is one complete time step: four fused
+RHS + RK3(2)4[2R+]C stage kernels and the filter kernel.  The metric counts one
+node-RHS evaluation per node per stage.  The working set (0.73 GB of packed
+FP32 operator data) is larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LABFM RHS node-evals/s (m=8, FP32 vs FP64) and fraction of HBM roofline"
+UNIT = "node-evals/s"
+WORKLOAD = {"workload": "taylor-green 512x512 jittered lattice (262,144 nodes), m=8, h/s=2.8",
+            "nodes": 512 * 512, "m": 8, "h_over_s": 2.8, "jitter": 0.3, "c": 10.0, "mu": 0.005}
+C, MU = 10.0, 0.005
+
+
+def workload_config(nx):
+    if nx == 512:
+        return dict(WORKLOAD)
+    return dict(WORKLOAD, workload=f"taylor-green {nx}x{nx} jittered lattice ({nx * nx} nodes), "
+                "m=8, h/s=2.8 (reduced size)", nodes=nx * nx)
+SAMPLE_ROWS = 2048
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nx", type=int, default=512,
+                    help="lattice side (512 = the benchmark workload; smaller sizes for profiling)")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed helpers
+
+def dist_init(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle baseline
+
+class OracleSample:
+    """The FP64 CPU oracle on a bounded sample of the workload: SAMPLE_ROWS random
+    nodes get their stencils and weights from the oracle, then each step
+    evaluates the eq. icns right-hand side at those nodes four times (one RK
+    step's worth of node-RHS evaluations)."""
+
+    def __init__(self, ns, rows=SAMPLE_ROWS, seed=0):
+        import numpy as np
+        import labfm_inputs as li
+        from oracle import core as oracle
+        self.oracle = oracle
+        rng = np.random.default_rng(seed)
+        self.rows = np.sort(rng.choice(ns.N, size=rows, replace=False))
+        t0 = time.perf_counter()
+        rp, col = oracle.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly, rows=self.rows)
+        t1 = time.perf_counter()
+        ow = oracle.build_weights(ns.xy, ns.h, ns.s, rp, col, ns.m, ns.Lx, ns.Ly, rows=self.rows)
+        t2 = time.perf_counter()
+        self.neigh_s = t1 - t0
+        self.weights_s = t2 - t1
+        # compact problem: sampled rows first, then the other nodes they touch
+        others = np.setdiff1d(np.unique(col), self.rows)
+        nodes = np.concatenate([self.rows, others])
+        local = -np.ones(ns.N, dtype=np.int64)
+        local[nodes] = np.arange(len(nodes))
+        self.rp = np.concatenate([rp, np.full(len(others), rp[-1])])
+        self.col = local[col].astype(np.int64)
+        self.w = ow["w"][:5]
+        self.q = li.tgv_fields(ns.xy, C)[:, nodes].copy()
+        self.n = len(self.rows)
+
+    def step(self):
+        for _ in range(4):
+            self.oracle.rhs(self.q, self.w, self.rp, self.col, C * C, MU)
+
+    def describe(self):
+        return (f"{self.n} random nodes of the 262,144-node workload: oracle stencils and FP64 "
+                f"weights for them (untimed: {self.weights_s:.1f} s), then 4 evaluations of the "
+                "eq. icns RHS at those nodes per step")
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return 0
+    import labfm_inputs as li
+    ns = li.tgv_lattice(args.nx, m=8, h_over_s=2.8, jitter=0.3, seed=1)
+    sample = OracleSample(ns)
+    for _ in range(args.warmup):
+        sample.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sample.step()
+    dt = time.perf_counter() - t0
+    value = 4 * sample.n * args.steps / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(workload_config(args.nx), sample_rows=sample.n),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample.describe()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU path
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            return float(d["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("step.cu", "labfm_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2102_02019_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_hash):
+    """DRAM bytes per launch of the stage kernel from the committed ncu summary,
+    valid only if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        if d.get("kernel_source_hash") == kernel_hash:
+            return float(d["dram_bytes_per_launch_full_size"])
+    except Exception:
+        pass
+    return None
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import __graft_entry__ as g
+    g.build()
+    import labfm_inputs as li
+    import paper_2102_02019_gb300 as lb
+
+    dev = torch.device("cuda", local)
+    ns = li.tgv_lattice(args.nx, m=8, h_over_s=2.8, jitter=0.3, seed=1)
+    N = ns.N
+    xy = torch.tensor(ns.xy, device=dev)
+    h = torch.tensor(ns.h, device=dev)
+    s = torch.tensor(ns.s, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    # preprocessing (once per plan): neighbour search, FP64 weight build
+    e0, e1, e2 = ev(), ev(), ev()
+    e0.record()
+    row_ptr, col = lb.build_stencils(xy, h, ns.Lx, ns.Ly)
+    e1.record()
+    wb = lb.build_weights(xy, h, s, ns.Lx, ns.Ly, row_ptr, col, ns.m, residual=False)
+    e2.record()
+    torch.cuda.synchronize()
+    stencil_ms, weights_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+    nnz = col.numel()
+    n_bad = int((wb["status"] != 0).sum().item())
+    phys = lb.Phys(c2=C * C, mu=MU)
+    q0 = torch.tensor(li.tgv_fields(ns.xy, C), device=dev)
+
+    def measure(dtype, steps, warmup):
+        plan = lb.Plan(row_ptr, col, wb["w"], wb["kappa"], s, dtype=dtype)
+        Q = q0.to(dtype).contiguous()
+        group, block = plan.autotune(Q, phys, reps=3)
+        dt = float(lb.stable_dt(plan, Q, s, C, MU).item())
+        work = lb.workspace(plan)
+        lb.rk_step(plan, Q, dt, warmup, phys, work=work)
+        torch.cuda.synchronize()
+        plan.set_profiling(True)
+        a, b = ev(), ev()
+        barrier(world)
+        torch.cuda.synchronize()
+        a.record()
+        lb.rk_step(plan, Q, dt, steps, phys, work=work)
+        b.record()
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = a.elapsed_time(b)
+        prof = plan.read_profile()
+        plan.set_profiling(False)
+        finite = bool(torch.isfinite(Q).all().item())
+        return plan, Q, dt, ms, prof, (group, block), finite, work
+
+    # FP32 headline
+    with ClockSampler(local) as clk:
+        plan32, Q32, dt32, ms32, prof32, shape32, fin32, work32 = measure(torch.float32, args.steps, args.warmup)
+    clocks = clk.summary()
+    ms32 = max_over_ranks(ms32, world)
+    value = 4.0 * N * args.steps * world / (ms32 * 1e-3)
+
+    # FP64 comparison (fewer steps: about 6x slower)
+    k64 = args.fp64_steps or max(3, args.steps // 5)
+    plan64, Q64, dt64, ms64, prof64, shape64, fin64, work64 = measure(torch.float64, k64, min(args.warmup, 3))
+    ms64 = max_over_ranks(ms64, world)
+    value64 = 4.0 * N * k64 * world / (ms64 * 1e-3)
+
+    # end to end through the C ABI with host buffers: pinned host state in,
+    # one step on the device, state back to the host, every step
+    Qh = q0.to(torch.float32).cpu().pin_memory()
+    Qd = torch.empty_like(q0, dtype=torch.float32)
+    for _ in range(2):
+        lb.rk_step_host(plan32, Qh, Qd, dt32, 1, phys, work=work32)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        lb.rk_step_host(plan32, Qh, Qd, dt32, 1, phys, work=work32)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": 4.0 * N * args.steps * world / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 3 * N * 4, "d2h_bytes_per_step": 3 * N * 4}
+
+    # roofline of the dominant kernel (fused RHS + RK stage, FP32)
+    stage_ms = prof32["stage_ms"] / max(1, prof32["stage_launches"])
+    filter_ms = prof32["filter_ms"] / max(1, prof32["filter_launches"])
+    alg_bytes = 24.0 * nnz + 64.0 * N  # per launch (stencil + weights + fields, see design notes)
+    achieved = alg_bytes / (stage_ms * 1e-3) / 1e9
+    peak, peak_kind = peaks()
+    khash = kernel_source_hash()
+    traffic = recorded_traffic(khash)
+    stage64_ms = prof64["stage_ms"] / max(1, prof64["stage_launches"])
+    alg64 = 44.0 * nnz + 124.0 * N
+    # FP64 arithmetic: per stencil entry 3 differences + 12 multiply-adds (27 flops),
+    # per node about 45 flops of pointwise RHS and RK update
+    flops64 = 27.0 * nnz + 45.0 * N
+    fp64_peak = lb.probe_fma_rate(torch.float64)
+    # weight build flops per node: assembly 2 Nn n^2, elimination on [M | 6 columns]
+    # (2/3) n^3 + 6 n^2, back substitution 6 n^2, weights 12 n Nn
+    n_unk = (ns.m * ns.m + 3 * ns.m) // 2
+    nn_mean = nnz / N
+    wb_flops = N * (2 * nn_mean * n_unk ** 2 + (2.0 / 3.0) * n_unk ** 3 + 12 * n_unk ** 2
+                    + 12 * n_unk * nn_mean)
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_config(args.nx), nnz=nnz, mean_neighbours=nnz / N, l2_flush="none: operator data "
+                       "0.73 GB > 129 MB L2", parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
+                       launch_shape={"group": shape32[0], "block": shape32[1]}),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "k_stage<float> (fused RHS + RK stage)", "peak_source": peak_kind,
+                     "alg_bytes_per_launch": alg_bytes, "mean_launch_ms": stage_ms},
+        "fp64": {"value": value64, "ms_per_step": ms64 / k64, "steps": k64,
+                 "stage_launch_ms": stage64_ms,
+                 "stage_alg_GBps": alg64 / (stage64_ms * 1e-3) / 1e9, "finite": fin64,
+                 "launch_shape": {"group": shape64[0], "block": shape64[1]},
+                 "roofline": {"bound": "alu", "achieved": flops64 / (stage64_ms * 1e-3) / 1e9,
+                              "peak": fp64_peak, "unit": "GFLOP/s",
+                              "frac": flops64 / (stage64_ms * 1e-3) / 1e9 / fp64_peak,
+                              "peak_source": "measured FP64 FMA probe (labfm_probe_fma_rate)",
+                              "hbm_frac": alg64 / (stage64_ms * 1e-3) / 1e9 / peak}},
+        "fp32_over_fp64": value / value64,
+        "filter_launch_ms": filter_ms,
+        "preprocess": {"stencil_ms": stencil_ms, "weight_build_ms": weights_ms,
+                       "weight_build_nodes_per_s": N / (weights_ms * 1e-3), "failed_nodes": n_bad,
+                       "weight_build_fp64_gflops": wb_flops / (weights_ms * 1e-3) / 1e9,
+                       "weight_build_fp64_frac": wb_flops / (weights_ms * 1e-3) / 1e9 / fp64_peak},
+        "state_finite_after_run": fin32,
+        "e2e": e2e,
+        "gpu_launches": 5 * args.steps + 2,
+        "clocks": clocks,
+        "kernel_source_hash": khash,
+    }
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t0 = time.perf_counter()
+        sample = OracleSample(ns)
+        reps = 0
+        t1 = time.perf_counter()
+        while True:
+            sample.step()
+            reps += 1
+            if time.perf_counter() - t1 > 5.0:
+                break
+        el = time.perf_counter() - t1
+        result["cpu_baseline"] = {"value": 4 * sample.n * reps / el, "unit": UNIT, "cores": 1,
+                                  "kind": "oracle", "sample": sample.describe(),
+                                  "weight_build_nodes_per_s": sample.n / sample.weights_s,
+                                  "wall_s": time.perf_counter() - t0}
+    for p in (plan32, plan64):
+        p.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        rc = run_reference(args, world, rank)
+    else:
+        rc = run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return rc
+
+
+if __name__ == "__main__":
+    sys.exit(main())

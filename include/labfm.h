@@ -139,9 +139,10 @@ int labfm_build_weights(const double* xy, const double* h, const double* s, int6
 /*
  * Prepare an operator for the time-step kernels: rows padded to a multiple of
  * four entries (pad entries point at the node itself with weight 0, which adds
- * exactly zero in the difference form of eq. general_do), the five RHS weight
- * streams and the filter stream (kappa_i w^hyp_ji) packed operator-major in
- * `dtype`.  For LABFM_F32 the RHS weights are stored nondimensionalised,
+ * exactly zero in the difference form of eq. general_do); every 4-entry chunk
+ * becomes one record of its four columns and the four weights of each of the
+ * five RHS operators, in `dtype`, and a second record stream holds the columns
+ * with the filter weights kappa_i w^hyp_ji.  For LABFM_F32 the RHS weights are stored nondimensionalised,
  * w^d_ji s_i^l (l = 1 for d/dx, d/dy; 2 for second derivatives), and the kernels
  * multiply the sums by s_i^-l.
  *
@@ -163,7 +164,7 @@ int labfm_plan_destroy(labfm_plan* plan);
 int labfm_plan_get_info(const labfm_plan* plan, labfm_plan_info* info);
 
 /*
- * Override the gather launch shape: `group` lanes per node (4, 8, 16 or 32) and
+ * Override the gather launch shape: `group` lanes per node (2, 4, 8, 16 or 32) and
  * `block` threads per block (a multiple of 32 and of group, 64..1024).  The
  * defaults come from labfm_plan_create; labfm_plan_autotune picks the fastest.
  */
@@ -225,6 +226,43 @@ int labfm_rk_step(const labfm_plan* plan, void* Q, void* work, size_t work_bytes
  */
 int labfm_stable_dt(const labfm_plan* plan, const void* fields, const double* s, double c,
                     double mu, double* dt_out, void* stream);
+
+/*
+ * The same as labfm_rk_step for a caller whose state lives in host memory:
+ * copies Q_host (3 x N, plan dtype) to Q_dev, runs `nsteps` steps on the
+ * device, copies the result back into Q_host and synchronises `stream`.
+ *   Q_host  host, 3 x N (pinned memory gives asynchronous copies)
+ *   Q_dev   device, 3 x N scratch for the state
+ */
+int labfm_rk_step_host(const labfm_plan* plan, void* Q_host, void* Q_dev, void* work,
+                       size_t work_bytes, double dt, int nsteps, const labfm_phys* phys,
+                       void* stream);
+
+/* Per-launch device time of the kernels labfm_rk_step enqueues, measured with
+ * CUDA events recorded on the launching stream around every stage launch and
+ * every filter launch while profiling is enabled. */
+typedef struct labfm_profile {
+    double stage_ms;         /* summed duration of the fused RHS + RK stage launches */
+    int64_t stage_launches;
+    double filter_ms;        /* summed duration of the filter launches */
+    int64_t filter_launches;
+    int64_t dropped;         /* launches not timed because the event pool was full */
+} labfm_profile;
+
+/* Enable (1) or disable (0) launch timing on this plan; enabling clears the record. */
+int labfm_plan_set_profiling(labfm_plan* plan, int enable);
+
+/* Read and clear the launch timings (synchronises on the last recorded event). */
+int labfm_plan_read_profile(labfm_plan* plan, labfm_profile* out);
+
+/*
+ * Measure the device's fused multiply-add throughput in `dtype` (GFLOP/s,
+ * 2 flops per FMA) with a synthetic kernel of independent FMA chains on every
+ * SM.  No counterpart in the paper: it supplies the FP64-pipe denominator of
+ * the roofline for the FP64 kernels.  Allocates a small device buffer, runs on
+ * the legacy default stream and synchronises.
+ */
+int labfm_probe_fma_rate(int dtype, double* gflops_out);
 
 #ifdef __cplusplus
 }

@@ -53,6 +53,12 @@ class _PlanInfo(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
 
 
+class _Profile(ctypes.Structure):
+    _fields_ = [("stage_ms", ctypes.c_double), ("stage_launches", ctypes.c_int64),
+                ("filter_ms", ctypes.c_double), ("filter_launches", ctypes.c_int64),
+                ("dropped", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 _I64 = ctypes.c_int64
 _I32 = ctypes.c_int
@@ -75,6 +81,10 @@ _SIGS = {
     "labfm_rk_workspace_bytes": (ctypes.c_size_t, [_P]),
     "labfm_rk_step": (_I32, [_P, _P, _P, ctypes.c_size_t, _D, _I32, ctypes.POINTER(_Phys), _P]),
     "labfm_stable_dt": (_I32, [_P, _P, _P, _D, _D, _P, _P]),
+    "labfm_rk_step_host": (_I32, [_P, _P, _P, _P, ctypes.c_size_t, _D, _I32, ctypes.POINTER(_Phys), _P]),
+    "labfm_plan_set_profiling": (_I32, [_P, _I32]),
+    "labfm_plan_read_profile": (_I32, [_P, ctypes.POINTER(_Profile)]),
+    "labfm_probe_fma_rate": (_I32, [_I32, ctypes.POINTER(_D)]),
 }
 
 
@@ -206,6 +216,14 @@ class Plan:
                                        ctypes.byref(g), ctypes.byref(b), _stream(stream)))
         return g.value, b.value
 
+    def set_profiling(self, enable: bool = True) -> None:
+        _check(lib.labfm_plan_set_profiling(self._h, 1 if enable else 0))
+
+    def read_profile(self) -> dict:
+        pr = _Profile()
+        _check(lib.labfm_plan_read_profile(self._h, ctypes.byref(pr)))
+        return {k: getattr(pr, k) for k, _ in _Profile._fields_}
+
     def workspace_bytes(self) -> int:
         return int(lib.labfm_rk_workspace_bytes(self._h))
 
@@ -259,3 +277,23 @@ def stable_dt(plan: Plan, fields: torch.Tensor, s: torch.Tensor, c: float, mu: f
     _check(lib.labfm_stable_dt(plan.handle, _ptr(fields), _ptr(s), float(c), float(mu), _ptr(out),
                                _stream(stream)))
     return out
+
+
+def rk_step_host(plan: Plan, Q_host: torch.Tensor, Q_dev: torch.Tensor, dt: float, nsteps: int,
+                 phys: Phys, work: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """labfm_rk_step_host: state in (pinned) host memory, copied in and out by the call."""
+    if Q_host.is_cuda or not Q_host.is_contiguous():
+        raise ValueError("Q_host must be a contiguous host tensor")
+    work = workspace(plan) if work is None else work
+    ph = phys.c()
+    _check(lib.labfm_rk_step_host(plan.handle, Q_host.data_ptr(), _ptr(Q_dev), _ptr(work), work.numel(),
+                                  float(dt), int(nsteps), ctypes.byref(ph), _stream(stream)))
+    return Q_host
+
+
+def probe_fma_rate(dtype=torch.float64) -> float:
+    """Device FMA throughput in GFLOP/s for float64 or float32 (labfm_probe_fma_rate)."""
+    out = _D(0.0)
+    _check(lib.labfm_probe_fma_rate(LABFM_F64 if dtype == torch.float64 else LABFM_F32,
+                                    ctypes.byref(out)))
+    return out.value

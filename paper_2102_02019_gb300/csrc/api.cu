@@ -31,7 +31,20 @@ using namespace labfm;
 
 namespace {
 
+void free_prof(labfm_plan* p) {
+    if (p->prof_ev) {
+        for (int k = 0; k < 2 * p->prof_cap; ++k) cudaEventDestroy(p->prof_ev[k]);
+        delete[] p->prof_ev;
+        delete[] p->prof_kind;
+    }
+    p->prof_ev = nullptr;
+    p->prof_kind = nullptr;
+    p->prof_cap = 0;
+    p->prof_used = 0;
+}
+
 void free_plan_memory(labfm_plan* p) {
+    free_prof(p);
     cudaFree(p->row_ptr);
     cudaFree(p->col);
     cudaFree(p->w);
@@ -48,6 +61,26 @@ int check_plan(const labfm_plan* p) {
 }
 
 }  // namespace
+
+namespace labfm {
+
+int prof_begin(labfm_plan* p, int kind, cudaStream_t st) {
+    if (!p->profiling) return -1;
+    if (p->prof_used >= p->prof_cap) {
+        ++p->prof_dropped;
+        return -1;
+    }
+    const int idx = p->prof_used++;
+    p->prof_kind[idx] = char(kind);
+    cudaEventRecord(p->prof_ev[2 * idx], st);
+    return idx;
+}
+
+void prof_end(labfm_plan* p, int idx, cudaStream_t st) {
+    if (idx >= 0) cudaEventRecord(p->prof_ev[2 * idx + 1], st);
+}
+
+}  // namespace labfm
 
 extern "C" const char* labfm_last_error(void) { return g_last_error.c_str(); }
 
@@ -127,7 +160,7 @@ extern "C" int labfm_plan_autotune(labfm_plan* p, const void* fields, void* scra
     cudaEvent_t e0, e1;
     LABFM_CUDA_TRY(cudaEventCreate(&e0));
     LABFM_CUDA_TRY(cudaEventCreate(&e1));
-    const int groups[] = {4, 8, 16, 32};
+    const int groups[] = {2, 4, 8, 16, 32};
     const int blocks[] = {128, 256, 512};
     float best = 1e30f;
     int bg = p->group, bb = p->block;
@@ -205,4 +238,73 @@ extern "C" int labfm_stable_dt(const labfm_plan* p, const void* fields, const do
     if (!fields || !s || !dt_out) return set_error(LABFM_EINVAL, "null pointer argument");
     if (!(c >= 0.0) || !(mu > 0.0)) return set_error(LABFM_EINVAL, "need c >= 0 and mu > 0");
     return launch_stable_dt(p, fields, s, c, mu, dt_out, as_stream(stream));
+}
+
+extern "C" int labfm_rk_step_host(const labfm_plan* p, void* Q_host, void* Q_dev, void* work,
+                                  size_t work_bytes, double dt, int nsteps,
+                                  const labfm_phys* phys, void* stream) {
+    if (int rc = check_plan(p)) return rc;
+    if (!Q_host || !Q_dev) return set_error(LABFM_EINVAL, "null pointer argument");
+    const size_t bytes = size_t(3) * size_t(p->N) * (p->dtype == LABFM_F32 ? sizeof(float) : sizeof(double));
+    cudaStream_t st = as_stream(stream);
+    LABFM_CUDA_TRY(cudaMemcpyAsync(Q_dev, Q_host, bytes, cudaMemcpyHostToDevice, st));
+    if (int rc = labfm_rk_step(p, Q_dev, work, work_bytes, dt, nsteps, phys, stream)) return rc;
+    LABFM_CUDA_TRY(cudaMemcpyAsync(Q_host, Q_dev, bytes, cudaMemcpyDeviceToHost, st));
+    LABFM_CUDA_TRY(cudaStreamSynchronize(st));
+    return LABFM_OK;
+}
+
+extern "C" int labfm_plan_set_profiling(labfm_plan* p, int enable) {
+    if (int rc = check_plan(p)) return rc;
+    if (enable && !p->prof_ev) {
+        const int cap = 8192;
+        p->prof_ev = new (std::nothrow) cudaEvent_t[2 * cap];
+        p->prof_kind = new (std::nothrow) char[cap];
+        if (!p->prof_ev || !p->prof_kind) {
+            delete[] p->prof_ev;
+            delete[] p->prof_kind;
+            p->prof_ev = nullptr;
+            p->prof_kind = nullptr;
+            return set_error(LABFM_ENOMEM, "host allocation of the event pool failed");
+        }
+        for (int k = 0; k < 2 * cap; ++k) {
+            cudaError_t e = cudaEventCreate(&p->prof_ev[k]);
+            if (e != cudaSuccess) {
+                for (int j = 0; j < k; ++j) cudaEventDestroy(p->prof_ev[j]);
+                delete[] p->prof_ev;
+                delete[] p->prof_kind;
+                p->prof_ev = nullptr;
+                p->prof_kind = nullptr;
+                return cuda_error(e, "cudaEventCreate");
+            }
+        }
+        p->prof_cap = cap;
+    }
+    p->profiling = enable != 0;
+    p->prof_used = 0;
+    p->prof_dropped = 0;
+    return LABFM_OK;
+}
+
+extern "C" int labfm_plan_read_profile(labfm_plan* p, labfm_profile* out) {
+    if (int rc = check_plan(p)) return rc;
+    if (!out) return set_error(LABFM_EINVAL, "null profile output");
+    *out = labfm_profile{0.0, 0, 0.0, 0, p->prof_dropped};
+    if (p->prof_used > 0) {
+        LABFM_CUDA_TRY(cudaEventSynchronize(p->prof_ev[2 * (p->prof_used - 1) + 1]));
+        for (int k = 0; k < p->prof_used; ++k) {
+            float ms = 0.f;
+            LABFM_CUDA_TRY(cudaEventElapsedTime(&ms, p->prof_ev[2 * k], p->prof_ev[2 * k + 1]));
+            if (p->prof_kind[k] == 0) {
+                out->stage_ms += ms;
+                ++out->stage_launches;
+            } else {
+                out->filter_ms += ms;
+                ++out->filter_launches;
+            }
+        }
+    }
+    p->prof_used = 0;
+    p->prof_dropped = 0;
+    return LABFM_OK;
 }

@@ -65,6 +65,13 @@ struct labfm_plan {
     void* wf = nullptr;          // nnz_pad filter weights kappa_i w^hyp_ji (dtype)
     void* inv_s = nullptr;       // N values 1/s_i (dtype), used by the F32 kernels
     int64_t device_bytes = 0;
+    // launch timing (labfm_plan_set_profiling): event pairs around launches
+    bool profiling = false;
+    cudaEvent_t* prof_ev = nullptr;  // 2 * prof_cap events
+    char* prof_kind = nullptr;       // 0 = stage, 1 = filter
+    int prof_cap = 0;
+    int prof_used = 0;
+    int64_t prof_dropped = 0;
 };
 
 namespace labfm {
@@ -79,6 +86,11 @@ size_t rk_work_bytes(const labfm_plan* p);
 int launch_stable_dt(const labfm_plan* p, const void* fields, const double* s, double c,
                      double mu, double* dt_out, cudaStream_t st);
 bool launch_shape_supported(int group, int block);
+
+// Launch timing around one kernel launch (api.cu); kind 0 = stage, 1 = filter.
+// Returns the pair index to close with prof_end, or -1 when not profiling.
+int prof_begin(labfm_plan* p, int kind, cudaStream_t st);
+void prof_end(labfm_plan* p, int idx, cudaStream_t st);
 
 // Plan packing (step.cu).
 int pack_plan(labfm_plan* p, const int32_t* row_ptr, const int32_t* col, const double* w,

@@ -280,11 +280,14 @@ int scratch_alloc(T** p, size_t count, cudaStream_t st) {
 }
 
 struct ScratchList {
+    static constexpr int kCap = 16;
     cudaStream_t st;
-    void* ptrs[8] = {};
+    void* ptrs[kCap] = {};
     int n = 0;
     explicit ScratchList(cudaStream_t s) : st(s) {}
-    void add(void* p) { ptrs[n++] = p; }
+    void add(void* p) {
+        if (n < kCap) ptrs[n++] = p;
+    }
     ~ScratchList() {
         for (int k = 0; k < n; ++k)
             if (ptrs[k]) cudaFreeAsync(ptrs[k], st);

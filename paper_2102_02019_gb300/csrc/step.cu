@@ -3,12 +3,13 @@
 // stage update fused into it, the hyperviscous filter (Section 6) and the time
 // step of eq. dt.  Also the packing of a weight set into a plan.
 //
-// Layout (per plan): rows padded to multiples of 4 entries; col and the five RHS
-// weight streams (d/dx, d/dy, d2/dx2, d2/dxdy, d2/dy2) are operator-major, so a
-// lane reads 4 consecutive entries of one stream with one 16-byte (F32) or two
-// 16-byte (F64) loads.  A node is served by a group of G lanes; lane l of the
-// group takes the 4-entry chunks l, l + G, l + 2G, ... of the row.  The 12
-// partial sums are reduced across the group with xor shuffles.
+// Layout (per plan): rows padded to multiples of 4 entries.  Every 4-entry
+// chunk of a row is one contiguous record holding its four column indices and
+// the four weights of each RHS operator (d/dx, d/dy, d2/dx2, d2/dxdy, d2/dy2):
+// 96 bytes in F32, read with six 16-byte loads.  The filter has its own records
+// (four columns, four kappa_i w^hyp_ji).  A node is served by a group of G
+// lanes; lane l of the group takes the chunks l, l + G, l + 2G, ... of the row.
+// The 12 partial sums are reduced across the group with xor shuffles.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -34,28 +35,66 @@ constexpr double kRkB[4] = {1017324711453.0 / 9774461848756.0,
 
 // ---------------------------------------------------------------- vector helpers
 
-__device__ __forceinline__ void load4(const float* p, float (&o)[4]) {
-    const float4 t = __ldg(reinterpret_cast<const float4*>(p));
-    o[0] = t.x;
-    o[1] = t.y;
-    o[2] = t.z;
-    o[3] = t.w;
+// Chunks of 4 stencil entries each lane loads before its gathers (1 or 2).
+#ifndef LABFM_GATHER_UNROLL
+#define LABFM_GATHER_UNROLL 1
+#endif
+// Cache hint for the operator streams (col and weights, read once per launch):
+// 0 = read-only path (ld.global.nc), 1 = evict-first (ld.global.cs).
+#ifndef LABFM_STREAM_HINT
+#define LABFM_STREAM_HINT 1
+#endif
+constexpr int kUnroll = LABFM_GATHER_UNROLL;
+
+template <typename V>
+__device__ __forceinline__ V ld_stream(const V* p) {
+#if LABFM_STREAM_HINT == 1
+    return __ldcs(p);
+#else
+    return __ldg(p);
+#endif
 }
-__device__ __forceinline__ void load4(const double* p, double (&o)[4]) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(p));
-    const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
-    o[0] = a.x;
-    o[1] = a.y;
-    o[2] = b.x;
-    o[3] = b.y;
+
+// `o` receives 4 values of an operator stream starting at o + off.
+template <int K>
+__device__ __forceinline__ void load4(const float* p, float (&o)[K], int off) {
+    const float4 t = ld_stream(reinterpret_cast<const float4*>(p));
+    o[off] = t.x;
+    o[off + 1] = t.y;
+    o[off + 2] = t.z;
+    o[off + 3] = t.w;
 }
-__device__ __forceinline__ void load4i(const int32_t* p, int (&o)[4]) {
-    const int4 t = __ldg(reinterpret_cast<const int4*>(p));
-    o[0] = t.x;
-    o[1] = t.y;
-    o[2] = t.z;
-    o[3] = t.w;
+template <int K>
+__device__ __forceinline__ void load4(const double* p, double (&o)[K], int off) {
+    const double2 a = ld_stream(reinterpret_cast<const double2*>(p));
+    const double2 b = ld_stream(reinterpret_cast<const double2*>(p) + 1);
+    o[off] = a.x;
+    o[off + 1] = a.y;
+    o[off + 2] = b.x;
+    o[off + 3] = b.y;
 }
+template <int K>
+__device__ __forceinline__ void load4i(const int32_t* p, int (&o)[K], int off) {
+    const int4 t = ld_stream(reinterpret_cast<const int4*>(p));
+    o[off] = t.x;
+    o[off + 1] = t.y;
+    o[off + 2] = t.z;
+    o[off + 3] = t.w;
+}
+
+// Operator layout.  0: operator-major streams col[nnz], w[5][nnz], wf[nnz].
+// 1: chunk-interleaved: for every 4-entry chunk of a row, the four columns and
+// the four weights of each of the five RHS operators sit in one contiguous
+// record (96 bytes in F32), and the filter has its own records (col, kappa w^hyp).
+#ifndef LABFM_CHUNK_AOS
+#define LABFM_CHUNK_AOS 1
+#endif
+
+template <typename T>
+struct ChunkBytes {
+    static constexpr int rhs = 16 + 20 * int(sizeof(T));  // int4 col + 5 x 4 weights
+    static constexpr int filt = 16 + 4 * int(sizeof(T));  // int4 col + 4 weights
+};
 
 // Node state (ln rho, u, v) packed for one-instruction gathers: float4 for F32
 // (w unused), two double2 for F64.
@@ -151,6 +190,44 @@ struct PlanView {
     const T* inv_s;
 };
 
+// Operator loads of one 4-entry chunk starting at entry e (a multiple of 4).
+template <typename T, int K>
+__device__ __forceinline__ void load_rhs_chunk(const PlanView<T>& P, int e, int (&cj)[K],
+                                               T (&wx)[K], T (&wy)[K], T (&wxx)[K],
+                                               T (&wxy)[K], T (&wyy)[K], int off) {
+#if LABFM_CHUNK_AOS
+    const char* rec = reinterpret_cast<const char*>(P.w) + int64_t(e >> 2) * ChunkBytes<T>::rhs;
+    load4i(reinterpret_cast<const int32_t*>(rec), cj, off);
+    const T* wr = reinterpret_cast<const T*>(rec + 16);
+    load4(wr, wx, off);
+    load4(wr + 4, wy, off);
+    load4(wr + 8, wxx, off);
+    load4(wr + 12, wxy, off);
+    load4(wr + 16, wyy, off);
+#else
+    const int64_t nz = P.nnz_pad;
+    load4i(P.col + e, cj, off);
+    load4(P.w + e, wx, off);
+    load4(P.w + nz + e, wy, off);
+    load4(P.w + 2 * nz + e, wxx, off);
+    load4(P.w + 3 * nz + e, wxy, off);
+    load4(P.w + 4 * nz + e, wyy, off);
+#endif
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void load_filt_chunk(const PlanView<T>& P, int e, int (&cj)[K],
+                                                T (&wf)[K], int off) {
+#if LABFM_CHUNK_AOS
+    const char* rec = reinterpret_cast<const char*>(P.wf) + int64_t(e >> 2) * ChunkBytes<T>::filt;
+    load4i(reinterpret_cast<const int32_t*>(rec), cj, off);
+    load4(reinterpret_cast<const T*>(rec + 16), wf, off);
+#else
+    load4i(P.col + e, cj, off);
+    load4(P.wf + e, wf, off);
+#endif
+}
+
 template <typename T>
 PlanView<T> view(const labfm_plan* p) {
     return PlanView<T>{p->N, p->nnz_pad, p->row_ptr, p->col, static_cast<const T*>(p->w),
@@ -168,18 +245,26 @@ __device__ __forceinline__ void gather_derivatives(const PlanView<T>& P, const F
     if (i >= 0) {
         const int e0 = P.row_ptr[i];
         const int e1 = P.row_ptr[i + 1];
-        const int64_t nz = P.nnz_pad;
-        for (int e = e0 + 4 * gl; e < e1; e += 4 * G) {
-            int cj[4];
-            T wx[4], wy[4], wxx[4], wxy[4], wyy[4];
-            load4i(P.col + e, cj);
-            load4(P.w + e, wx);
-            load4(P.w + nz + e, wy);
-            load4(P.w + 2 * nz + e, wxx);
-            load4(P.w + 3 * nz + e, wxy);
-            load4(P.w + 4 * nz + e, wyy);
+        // kUnroll 4-entry chunks per iteration (chunks gl, gl + G, ... of this
+        // pass): all their operator loads are issued before the gathers
+        for (int e = e0 + 4 * gl; e < e1; e += 4 * kUnroll * G) {
+            int cj[4 * kUnroll];
+            T wx[4 * kUnroll], wy[4 * kUnroll], wxx[4 * kUnroll], wxy[4 * kUnroll], wyy[4 * kUnroll];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int u = 0; u < kUnroll; ++u) {
+                const int eu = e + 4 * u * G;
+                if (u == 0 || eu < e1) {
+                    load_rhs_chunk(P, eu, cj, wx, wy, wxx, wxy, wyy, 4 * u);
+                } else {
+#pragma unroll
+                    for (int k = 4 * u; k < 4 * u + 4; ++k) {
+                        cj[k] = i;  // the node itself with zero weight adds exactly 0
+                        wx[k] = wy[k] = wxx[k] = wxy[k] = wyy[k] = T(0);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4 * kUnroll; ++k) {
                 T aj, uj, vj;
                 fld.get(cj[k], aj, uj, vj);
                 const T da = aj - ai, du = uj - ui, dv = vj - vi;
@@ -313,13 +398,24 @@ __device__ __forceinline__ void filter_sums(const PlanView<T>& P, const Fin& fld
     if (i >= 0) {
         const int e0 = P.row_ptr[i];
         const int e1 = P.row_ptr[i + 1];
-        for (int e = e0 + 4 * gl; e < e1; e += 4 * G) {
-            int cj[4];
-            T wf[4];
-            load4i(P.col + e, cj);
-            load4(P.wf + e, wf);
+        for (int e = e0 + 4 * gl; e < e1; e += 4 * kUnroll * G) {
+            int cj[4 * kUnroll];
+            T wf[4 * kUnroll];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int u = 0; u < kUnroll; ++u) {
+                const int eu = e + 4 * u * G;
+                if (u == 0 || eu < e1) {
+                    load_filt_chunk(P, eu, cj, wf, 4 * u);
+                } else {
+#pragma unroll
+                    for (int k = 4 * u; k < 4 * u + 4; ++k) {
+                        cj[k] = i;
+                        wf[k] = T(0);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4 * kUnroll; ++k) {
                 T aj, uj, vj;
                 fld.get(cj[k], aj, uj, vj);
                 aa.add((aj - ai) * wf[k]);
@@ -441,20 +537,31 @@ __global__ void k_pack_rows(int64_t N, int64_t nnz, int64_t nnz_pad,
         const double kap = kappa[i];
         for (int e = lane; e < plen; e += 32) {
             const int64_t dst = int64_t(p0) + e;
+            int32_t c = int32_t(i);
+            T v[5] = {T(0), T(0), T(0), T(0), T(0)};
+            T vf = T(0);
             if (e < len) {
                 const int64_t src = int64_t(r0) + e;
-                pcol[dst] = col[src];
-                pw[dst] = T(w[src] * sc1);
-                pw[nnz_pad + dst] = T(w[nnz + src] * sc1);
-                pw[2 * nnz_pad + dst] = T(w[2 * nnz + src] * sc2);
-                pw[3 * nnz_pad + dst] = T(w[3 * nnz + src] * sc2);
-                pw[4 * nnz_pad + dst] = T(w[4 * nnz + src] * sc2);
-                pwf[dst] = T(kap * w[5 * nnz + src]);
-            } else {
-                pcol[dst] = int32_t(i);
-                for (int d = 0; d < 5; ++d) pw[d * nnz_pad + dst] = T(0);
-                pwf[dst] = T(0);
+                c = col[src];
+                v[0] = T(w[src] * sc1);
+                v[1] = T(w[nnz + src] * sc1);
+                v[2] = T(w[2 * nnz + src] * sc2);
+                v[3] = T(w[3 * nnz + src] * sc2);
+                v[4] = T(w[4 * nnz + src] * sc2);
+                vf = T(kap * w[5 * nnz + src]);
             }
+#if LABFM_CHUNK_AOS
+            char* rec = reinterpret_cast<char*>(pw) + (dst >> 2) * ChunkBytes<T>::rhs;
+            reinterpret_cast<int32_t*>(rec)[dst & 3] = c;
+            for (int d = 0; d < 5; ++d) reinterpret_cast<T*>(rec + 16)[4 * d + (dst & 3)] = v[d];
+            char* frec = reinterpret_cast<char*>(pwf) + (dst >> 2) * ChunkBytes<T>::filt;
+            reinterpret_cast<int32_t*>(frec)[dst & 3] = c;
+            reinterpret_cast<T*>(frec + 16)[dst & 3] = vf;
+#else
+            pcol[dst] = c;
+            for (int d = 0; d < 5; ++d) pw[d * nnz_pad + dst] = v[d];
+            pwf[dst] = vf;
+#endif
         }
         if (lane == 0 && inv_s) inv_s[i] = T(1.0 / si);
     }
@@ -470,7 +577,7 @@ int rhs_launch_g(const labfm_plan* p, const void* fields, void* rhs, const Phys<
     const T* f = static_cast<const T*>(fields);
     SoA<T> in{f, f + p->N, f + 2 * p->N};
     const int grid = grid_for(p->N * G, block);
-    if (std::is_same<T, float>::value)
+    if constexpr (std::is_same<T, float>::value)
         k_rhs_soa<T, G, true, true><<<grid, block, 0, st>>>(view<T>(p), in, static_cast<T*>(rhs), ph);
     else
         k_rhs_soa<T, G, false, false><<<grid, block, 0, st>>>(view<T>(p), in, static_cast<T*>(rhs), ph);
@@ -483,6 +590,7 @@ int rhs_launch(const labfm_plan* p, const void* fields, void* rhs, const labfm_p
                int block, cudaStream_t st) {
     const Phys<T> ph{T(php->c2), T(php->mu), T(php->gx), T(php->gy)};
     switch (group) {
+        case 2: return rhs_launch_g<T, 2>(p, fields, rhs, ph, block, st);
         case 4: return rhs_launch_g<T, 4>(p, fields, rhs, ph, block, st);
         case 8: return rhs_launch_g<T, 8>(p, fields, rhs, ph, block, st);
         case 16: return rhs_launch_g<T, 16>(p, fields, rhs, ph, block, st);
@@ -496,7 +604,7 @@ int stage_launch_g(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* q
                    Packed<T>* xout, T cb, T cx, const Phys<T>& ph, cudaStream_t st) {
     const int block = p->block;
     const int grid = grid_for(p->N * G, block);
-    if (std::is_same<T, float>::value)
+    if constexpr (std::is_same<T, float>::value)
         k_stage<T, G, true, true><<<grid, block, 0, st>>>(view<T>(p), xin, qin, qout, xout, cb, cx, ph);
     else
         k_stage<T, G, false, false><<<grid, block, 0, st>>>(view<T>(p), xin, qin, qout, xout, cb, cx, ph);
@@ -508,6 +616,7 @@ template <typename T>
 int stage_launch(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* qin, Packed<T>* qout,
                  Packed<T>* xout, T cb, T cx, const Phys<T>& ph, cudaStream_t st) {
     switch (p->group) {
+        case 2: return stage_launch_g<T, 2>(p, xin, qin, qout, xout, cb, cx, ph, st);
         case 4: return stage_launch_g<T, 4>(p, xin, qin, qout, xout, cb, cx, ph, st);
         case 8: return stage_launch_g<T, 8>(p, xin, qin, qout, xout, cb, cx, ph, st);
         case 16: return stage_launch_g<T, 16>(p, xin, qin, qout, xout, cb, cx, ph, st);
@@ -527,6 +636,7 @@ int filter_aos_g(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaS
 template <typename T>
 int filter_aos(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaStream_t st) {
     switch (p->group) {
+        case 2: return filter_aos_g<T, 2>(p, in, out, st);
         case 4: return filter_aos_g<T, 4>(p, in, out, st);
         case 8: return filter_aos_g<T, 8>(p, in, out, st);
         case 16: return filter_aos_g<T, 16>(p, in, out, st);
@@ -549,6 +659,7 @@ int filter_soa_g(const labfm_plan* p, const void* in, void* out, cudaStream_t st
 template <typename T>
 int filter_soa(const labfm_plan* p, const void* in, void* out, cudaStream_t st) {
     switch (p->group) {
+        case 2: return filter_soa_g<T, 2>(p, in, out, st);
         case 4: return filter_soa_g<T, 4>(p, in, out, st);
         case 8: return filter_soa_g<T, 8>(p, in, out, st);
         case 16: return filter_soa_g<T, 16>(p, in, out, st);
@@ -582,12 +693,19 @@ int rk_steps(const labfm_plan* p, void* Q, void* work, double dt, int nsteps, co
         cx[k] = k < 3 ? T(dt * (kRkA[k] - kRkB[k])) : T(0);
     }
     int rc;
+    labfm_plan* pm = const_cast<labfm_plan*>(p);  // only the launch-timing record changes
+    const Packed<T>* xin[4] = {X, Y, X, Y};
+    const Packed<T>* qin[4] = {X, P, P, P};
+    Packed<T>* xout[4] = {Y, X, Y, nullptr};
     for (int step = 0; step < nsteps; ++step) {
-        if ((rc = stage_launch<T>(p, X, X, P, Y, cb[0], cx[0], ph, st))) return rc;
-        if ((rc = stage_launch<T>(p, Y, P, P, X, cb[1], cx[1], ph, st))) return rc;
-        if ((rc = stage_launch<T>(p, X, P, P, Y, cb[2], cx[2], ph, st))) return rc;
-        if ((rc = stage_launch<T>(p, Y, P, P, nullptr, cb[3], cx[3], ph, st))) return rc;
+        for (int k = 0; k < 4; ++k) {
+            const int ev = prof_begin(pm, 0, st);
+            if ((rc = stage_launch<T>(p, xin[k], qin[k], P, xout[k], cb[k], cx[k], ph, st))) return rc;
+            prof_end(pm, ev, st);
+        }
+        const int ev = prof_begin(pm, 1, st);
         if ((rc = filter_aos<T>(p, P, X, st))) return rc;
+        prof_end(pm, ev, st);
     }
     k_unpack<T><<<pg, 256, 0, st>>>(p->N, X, static_cast<T*>(Q));
     LABFM_LAUNCH_CHECK("unpack kernel");
@@ -597,7 +715,7 @@ int rk_steps(const labfm_plan* p, void* Q, void* work, double dt, int nsteps, co
 }  // namespace
 
 bool launch_shape_supported(int group, int block) {
-    const bool g_ok = group == 4 || group == 8 || group == 16 || group == 32;
+    const bool g_ok = group == 2 || group == 4 || group == 8 || group == 16 || group == 32;
     return g_ok && block >= 64 && block <= 1024 && block % 32 == 0 && block % group == 0;
 }
 
@@ -667,10 +785,17 @@ int pack_plan(labfm_plan* p, const int32_t* row_ptr, const int32_t* col, const d
     p->nnz_pad = nnz_pad;
     const size_t es = p->dtype == LABFM_F32 ? sizeof(float) : sizeof(double);
     const size_t np = size_t(std::max<int64_t>(nnz_pad, 4));
+#if LABFM_CHUNK_AOS
+    const size_t rhs_bytes = (np / 4) * (16 + 20 * es), filt_bytes = (np / 4) * (16 + 4 * es);
+    LABFM_CUDA_TRY(cudaMalloc(&p->w, rhs_bytes));
+    LABFM_CUDA_TRY(cudaMalloc(&p->wf, filt_bytes));
+    p->device_bytes += rhs_bytes + filt_bytes;
+#else
     LABFM_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&p->col), np * sizeof(int32_t)));
     LABFM_CUDA_TRY(cudaMalloc(&p->w, 5 * np * es));
     LABFM_CUDA_TRY(cudaMalloc(&p->wf, np * es));
     p->device_bytes += np * (sizeof(int32_t) + 6 * es);
+#endif
     if (p->dtype == LABFM_F32) {
         LABFM_CUDA_TRY(cudaMalloc(&p->inv_s, size_t(N) * es));
         p->device_bytes += N * es;

@@ -36,21 +36,17 @@ struct WCfg {
     }
 };
 
-// (a, b) exponents of entry q of X (eq. X): degree 1..M, descending powers of x.
-template <int M>
-struct Exps {
-    int a[WCfg<M>::n];
-    int b[WCfg<M>::n];
-    constexpr Exps() : a(), b() {
-        int q = 0;
-        for (int k = 1; k <= M; ++k)
-            for (int aa = k; aa >= 0; --aa) {
-                a[q] = aa;
-                b[q] = k - aa;
-                ++q;
-            }
+// (a, b) exponents of entry q of X (eq. X): degree 1..M, and within a degree
+// descending powers of x.  Degree k starts at q = k (k + 1) / 2 - 1.
+__device__ __forceinline__ void exps_of(int q, int& a, int& b) {
+    int k = 1, start = 0;
+    while (q >= start + k + 1) {
+        start += k + 1;
+        ++k;
     }
-};
+    b = q - start;
+    a = k - b;
+}
 
 // psi(q) = (1 - q/2)^4 (1 + 2 q) on q <= 2 (Wendland C2, support 2h).
 __device__ __forceinline__ double wendland_c2(double q) {
@@ -172,7 +168,6 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
     constexpr int NT = C::NT;
     constexpr int KCH = C::KCH;
     constexpr int LDA = C::LDA;
-    constexpr Exps<M> ex{};
 
     extern __shared__ double smem[];
     double* Xs = smem;             // [KCH][NP]
@@ -224,11 +219,15 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
             if (lane < cnt) {
                 double pxv[M + 1], pyv[M + 1], hxv[M + 1], hyv[M + 1], psi, dx, dy;
                 neighbour_factors<M>(xy, col[c0 + lane], g, pxv, pyv, hxv, hyv, &psi, &dx, &dy);
+                int q = 0;
 #pragma unroll
-                for (int q = 0; q < n; ++q) {
-                    const int a = ex.a[q], b = ex.b[q];
-                    xr[q] = (pxv[a] * pyv[b]) * (inv_factorial(a) * inv_factorial(b));
-                    wr[q] = psi * hxv[a] * hyv[b] * inv_sqrt2_pow(a + b);
+                for (int k = 1; k <= M; ++k) {
+#pragma unroll
+                    for (int a = k; a >= 0; --a, ++q) {
+                        const int b = k - a;
+                        xr[q] = (pxv[a] * pyv[b]) * (inv_factorial(a) * inv_factorial(b));
+                        wr[q] = psi * hxv[a] * hyv[b] * inv_sqrt2_pow(k);
+                    }
                 }
             } else {
                 for (int q = 0; q < n; ++q) {
@@ -273,7 +272,8 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
     }
     for (int idx = t; idx < n * 6; idx += NT) {
         const int q = idx / 6, d = idx - q * 6;
-        const int a = ex.a[q], b = ex.b[q];
+        int a, b;
+        exps_of(q, a, b);
         const double coef = selector_coef<M>(d, a, b);
         A[q * LDA + n + d] = coef != 0.0 ? coef * pow(g.hi, -double(a + b)) : 0.0;
     }
@@ -360,7 +360,8 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
                 const int q = idx / 6, d = idx - q * 6;
                 double sum = 0.0;
                 for (int c = 0; c < n; ++c) sum = fma(A0[q * n + c], A[c * LDA + n + d], sum);
-                const int a = ex.a[q], b = ex.b[q];
+                int a, b;
+                exps_of(q, a, b);
                 const double coef = selector_coef<M>(d, a, b);
                 const double cq = coef != 0.0 ? coef * pow(g.hi, -double(a + b)) : 0.0;
                 const double r = fabs(sum - cq) * pow(g.hi, double(op_order(d, M)));
@@ -389,12 +390,15 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
         if (!singular) {
             double pxv[M + 1], pyv[M + 1], hxv[M + 1], hyv[M + 1], psi;
             neighbour_factors<M>(xy, col[e], g, pxv, pyv, hxv, hyv, &psi, &dx, &dy);
+            int q = 0;
 #pragma unroll
-            for (int q = 0; q < n; ++q) {
-                const int a = ex.a[q], b = ex.b[q];
-                const double Wq = psi * hxv[a] * hyv[b] * inv_sqrt2_pow(a + b);
+            for (int k = 1; k <= M; ++k) {
 #pragma unroll
-                for (int d = 0; d < 6; ++d) wd[d] = fma(Wq, A[q * LDA + n + d], wd[d]);
+                for (int a = k; a >= 0; --a, ++q) {
+                    const double Wq = psi * hxv[a] * hyv[k - a] * inv_sqrt2_pow(k);
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) wd[d] = fma(Wq, A[q * LDA + n + d], wd[d]);
+                }
             }
         }
 #pragma unroll

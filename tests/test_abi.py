@@ -21,8 +21,8 @@ def _declared_functions():
 
 @pytest.fixture(scope="module")
 def built_lib():
-    from paper_2102_02019_gb300 import _build
-    return _build.build()
+    import __graft_entry__ as g
+    return g._builder().build()
 
 
 def test_library_exports_every_declared_symbol(built_lib):

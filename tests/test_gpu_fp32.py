@@ -1,0 +1,142 @@
+"""FP32 path (fields and nondimensionalised weights in float) against the FP64 oracle.
+
+Budget, derived from the arithmetic.  With u = 2^-24 (float unit roundoff),
+each input phi_j, each stored weight w~_ji and the scale 1/s_i carry a relative
+rounding of u; phi_j - phi_i, the product and the compensated sum add a few
+more.  For one derivative the error is therefore bounded by
+
+    B_d,i = 3 u sum_j |w_ji| (|phi_j| + |phi_i|) + 2 u |L_d,i|
+
+(the factor 3 covers weight, input and product roundings; the compensated sums
+keep the summation error at O(u)).  The pointwise right-hand side propagates
+these bounds linearly with absolute values and adds 4 u times the sum of the
+absolute values of its terms.  Tests require |R32 - R64| <= B elementwise.
+"""
+import numpy as np
+import pytest
+
+import labfm_inputs as li
+from oracle import core as oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def lb():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2102_02019_gb300 as lb
+    return lb
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def setup(lb):
+    ns = li.tgv_lattice(48, 40, m=8, h_over_s=2.8, jitter=0.3, seed=12)
+    rp, col = oracle.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly)
+    ow = oracle.build_weights(ns.xy, ns.h, ns.s, rp, col, ns.m, ns.Lx, ns.Ly)
+    rpd = _dev(rp, torch.int32)
+    cold = _dev(col, torch.int32)
+    plan32 = lb.Plan(rpd, cold, _dev(ow["w"]), _dev(ow["kappa"]), _dev(ns.s), dtype=torch.float32)
+    return dict(ns=ns, rp=rp, col=col, ow=ow, plan32=plan32, s=_dev(ns.s))
+
+
+def _deriv_bound(phi, w, rp, col):
+    ri = oracle.row_index(rp)
+    absum = np.bincount(ri, np.abs(w) * (np.abs(phi[col]) + np.abs(phi[ri])), minlength=len(rp) - 1)
+    L = oracle.apply_op(phi, w, rp, col)
+    return 3 * U32 * absum + 2 * U32 * np.abs(L), L
+
+
+def rhs_bound(q, w, rp, col, c2, mu):
+    a, u, v = q
+    B, D = {}, {}
+    B["ax"], D["ax"] = _deriv_bound(a, w[0], rp, col)
+    B["ay"], D["ay"] = _deriv_bound(a, w[1], rp, col)
+    for name, f in (("u", u), ("v", v)):
+        for k, op in enumerate(oracle.RHS_OPS):
+            B[name + op], D[name + op] = _deriv_bound(f, w[k], rp, col)
+    nu = mu * np.exp(-a)
+    ba = (np.abs(u) * B["ax"] + np.abs(v) * B["ay"] + B["ux"] + B["vy"]
+          + 4 * U32 * (np.abs(u * D["ax"]) + np.abs(v * D["ay"]) + np.abs(D["ux"]) + np.abs(D["vy"])))
+    out = [ba]
+    for f, (x1, y1, a1, vis) in (("u", ("ux", "uy", "ax", ("uxx", "uyy", "vxy"))),
+                                 ("v", ("vx", "vy", "ay", ("vyy", "vxx", "uxy")))):
+        coef = (4.0 / 3.0, 1.0, 1.0 / 3.0)
+        visc = sum(c * np.abs(D[n]) for c, n in zip(coef, vis))
+        bvis = sum(c * B[n] for c, n in zip(coef, vis))
+        b = (np.abs(u) * B[x1] + np.abs(v) * B[y1] + c2 * B[a1] + nu * bvis
+             + 4 * U32 * (np.abs(u * D[x1]) + np.abs(v * D[y1]) + c2 * np.abs(D[a1]) + nu * visc))
+        out.append(b)
+    return np.stack(out)
+
+
+def test_rhs_fp32_within_rounding_budget(lb, setup):
+    ns, rp, col, ow = setup["ns"], setup["rp"], setup["col"], setup["ow"]
+    q = li.perturbed_tgv_fields(ns.xy, 10.0, amplitude=0.05, kmax=4)
+    phys = lb.Phys(100.0, 0.005)
+    R32 = lb.rhs(setup["plan32"], _dev(q, torch.float32), phys).double().cpu().numpy()
+    R64 = oracle.rhs(q, ow["w"][:5], rp, col, 100.0, 0.005)
+    B = rhs_bound(q, ow["w"], rp, col, 100.0, 0.005)
+    ratio = np.abs(R32 - R64) / B
+    assert ratio.max() <= 1.0, ratio.max()
+    rel = np.linalg.norm(R32 - R64, axis=1) / np.linalg.norm(R64, axis=1)
+    print("FP32 RHS rel L2 per field (ln rho, u, v):", rel, "max err/bound", ratio.max())
+
+
+def test_filter_fp32_within_rounding_budget(lb, setup):
+    ns, rp, col, ow = setup["ns"], setup["rp"], setup["col"], setup["ow"]
+    q = li.perturbed_tgv_fields(ns.xy, 10.0, amplitude=0.1, kmax=8)
+    F32 = lb.filter(setup["plan32"], _dev(q, torch.float32)).double().cpu().numpy()
+    F64 = oracle.filter_fields(q, ow["w"][5], ow["kappa"], rp, col)
+    wf = ow["w"][5] * np.repeat(ow["kappa"], np.diff(rp))
+    for f in range(3):
+        b, _ = _deriv_bound(q[f], wf, rp, col)
+        bound = b + 2 * U32 * np.abs(q[f]) + 2 * U32 * np.abs(F64[f])
+        assert np.all(np.abs(F32[f] - F64[f]) <= bound)
+
+
+def test_rk_step_fp32_one_step(lb, setup):
+    ns, rp, col, ow = setup["ns"], setup["rp"], setup["col"], setup["ow"]
+    q0 = li.tgv_fields(ns.xy, 10.0)
+    dt = oracle.stable_dt(q0, ns.s, 10.0, 0.005)
+    Q = _dev(q0, torch.float32)
+    lb.rk_step(setup["plan32"], Q, dt, 1, lb.Phys(100.0, 0.005))
+    q1 = oracle.time_step(q0, dt, ow["w"], ow["kappa"], rp, col, 100.0, 0.005)
+    # per node: storage rounding of Q, plus dt sum_k |b_k| times the RHS budget at the
+    # initial state (the stage states differ from it by O(dt)), plus the filter budget
+    B = rhs_bound(q0, ow["w"], rp, col, 100.0, 0.005)
+    bsum = sum(abs(float(b)) for b in oracle.RK_B)
+    wf = ow["w"][5] * np.repeat(ow["kappa"], np.diff(rp))
+    got = Q.double().cpu().numpy()
+    for f in range(3):
+        bf, _ = _deriv_bound(q1[f], wf, rp, col)
+        bound = 8 * U32 * np.abs(q1[f]) + 2 * dt * bsum * B[f] + 2 * bf
+        assert np.all(np.abs(got[f] - q1[f]) <= bound), (f, (np.abs(got[f] - q1[f]) / bound).max())
+
+
+def test_profiling_and_host_buffer_step(lb, setup):
+    ns = setup["ns"]
+    plan = setup["plan32"]
+    q0 = li.tgv_fields(ns.xy, 10.0)
+    Qd = _dev(q0, torch.float32)
+    Qref = Qd.clone()
+    work = lb.workspace(plan)
+    plan.set_profiling(True)
+    lb.rk_step(plan, Qref, 1e-4, 3, lb.Phys(100.0, 0.005), work=work)
+    prof = plan.read_profile()
+    plan.set_profiling(False)
+    assert prof["stage_launches"] == 12 and prof["filter_launches"] == 3 and prof["dropped"] == 0
+    assert prof["stage_ms"] > 0 and prof["filter_ms"] > 0
+    Qh = torch.tensor(q0, dtype=torch.float32).pin_memory()
+    scratch = torch.empty_like(Qd)
+    lb.rk_step_host(plan, Qh, scratch, 1e-4, 3, lb.Phys(100.0, 0.005), work=work)
+    assert torch.equal(Qh, Qref.cpu())

@@ -284,8 +284,8 @@ def c2(lb):
     xy, h, s = _dev(ns.xy), _dev(ns.h), _dev(ns.s)
     rp, col = lb.build_stencils(xy, h, ns.Lx, ns.Ly)
     wb = lb.build_weights(xy, h, s, ns.Lx, ns.Ly, rp, col, ns.m)
-    rows = np.sort(np.random.default_rng(0).choice(ns.N, size=96, replace=False))
-    rows = np.concatenate([[0, ns.N - 1], rows])
+    rows = np.random.default_rng(0).choice(ns.N, size=96, replace=False)
+    rows = np.unique(np.concatenate([[0, ns.N - 1], rows]))
     return dict(ns=ns, xy=xy, h=h, s=s, rp=rp, col=col, wb=wb, rows=rows)
 
 
