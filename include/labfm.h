@@ -238,6 +238,30 @@ int labfm_rk_step_host(const labfm_plan* plan, void* Q_host, void* Q_dev, void* 
                        size_t work_bytes, double dt, int nsteps, const labfm_phys* phys,
                        void* stream);
 
+/*
+ * labfm_rk_step for callers that cannot allocate device memory: the same
+ * kernels and the same results, but the three packed state buffers live in a
+ * 16 MiB array that is part of the library image (a static __device__ array),
+ * so the call allocates nothing and takes no work buffer.  Useful where
+ * cudaMalloc is not an option: a host application or plugin that hands the
+ * library only the memory it manages itself, or a real-time loop that must not
+ * pay for (or synchronise on) an allocation.  The paper has no counterpart; it
+ * is an interface convenience.
+ *   Limit: 3 x N x 16 bytes (F32) or 3 x N x 32 bytes (F64) must fit in 16 MiB,
+ *   i.e. N <= 349,525 nodes in F32 and N <= 174,762 in F64; larger plans get
+ *   LABFM_ECAPACITY with the required size in labfm_last_error().
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any stream
+ *   capture.  Every GPU that loads the library holds the 16 MiB until exit.
+ *   All calls on a device share the array: two calls whose work overlaps on the
+ *   GPU (different streams or threads) race and corrupt each other's state.
+ *   Nothing in the array needs to start at zero; every buffer is written before
+ *   it is read within a call.
+ *   Q, dt, nsteps, phys, stream: as for labfm_rk_step.
+ */
+int labfm_rk_step_noalloc(const labfm_plan* plan, void* Q, double dt, int nsteps,
+                          const labfm_phys* phys, void* stream);
+
 /* Per-launch device time of the kernels labfm_rk_step enqueues, measured with
  * CUDA events recorded on the launching stream around every stage launch and
  * every filter launch while profiling is enabled. */

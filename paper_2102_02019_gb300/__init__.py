@@ -85,6 +85,7 @@ _SIGS = {
     "labfm_plan_set_profiling": (_I32, [_P, _I32]),
     "labfm_plan_read_profile": (_I32, [_P, ctypes.POINTER(_Profile)]),
     "labfm_probe_fma_rate": (_I32, [_I32, ctypes.POINTER(_D)]),
+    "labfm_rk_step_noalloc": (_I32, [_P, _P, _D, _I32, ctypes.POINTER(_Phys), _P]),
 }
 
 
@@ -297,3 +298,14 @@ def probe_fma_rate(dtype=torch.float64) -> float:
     _check(lib.labfm_probe_fma_rate(LABFM_F64 if dtype == torch.float64 else LABFM_F32,
                                     ctypes.byref(out)))
     return out.value
+
+
+def rk_step_noalloc(plan: Plan, Q: torch.Tensor, dt: float, nsteps: int, phys: Phys,
+                    stream=None) -> torch.Tensor:
+    """labfm_rk_step_noalloc: rk_step without a work buffer, for callers that cannot
+    allocate device memory; the state buffers live in the library's static device
+    array (16 MiB: N <= 349,525 in float32, <= 174,762 in float64)."""
+    ph = phys.c()
+    _check(lib.labfm_rk_step_noalloc(plan.handle, _ptr(Q), float(dt), int(nsteps), ctypes.byref(ph),
+                                     _stream(stream)))
+    return Q
