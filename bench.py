@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and variable-resolution workloads")
     ap.add_argument("--nx", type=int, default=512,
                     help="lattice side (512 = the benchmark workload; smaller sizes for profiling)")
     return ap.parse_args()
@@ -248,6 +250,107 @@ def recorded_traffic(kernel_hash):
     return None
 
 
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_batch(lb, torch, args):
+    """256 independent Taylor-Green instances, N log-uniform in [2k, 64k], m in {4, 6, 8},
+    FP32, each with its own time step: one batched plan, one CUDA graph per step."""
+    import labfm_inputs as li
+    t0 = time.perf_counter()
+    instances = []
+    for ns in li.batch_instances(256):
+        d = {"xy": torch.tensor(ns.xy, device="cuda"), "h": torch.tensor(ns.h, device="cuda"),
+             "s": torch.tensor(ns.s, device="cuda"), "ns": ns}
+        d["row_ptr"], d["col"] = lb.build_stencils(d["xy"], d["h"], ns.Lx, ns.Ly)
+        wb = lb.build_weights(d["xy"], d["h"], d["s"], ns.Lx, ns.Ly, d["row_ptr"], d["col"], ns.m,
+                              residual=False)
+        d["w"], d["kappa"] = wb["w"], wb["kappa"]
+        instances.append(d)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    plan = lb.Plan.batched(instances, dtype=torch.float32)
+    N = plan.N
+    q0 = torch.cat([torch.tensor(li.tgv_fields(d["ns"].xy, C), dtype=torch.float32, device="cuda")
+                    for d in instances], dim=1).contiguous()
+    s_all = torch.cat([d["s"] for d in instances])
+    plan.set_dt(plan.stable_dt_instances(q0, s_all, C, MU).cpu().tolist())
+    phys = lb.Phys(C * C, MU)
+    tune = plan.tune_step(q0, phys, 0.0)
+    graph = lb.StepGraph(plan, 0.0, phys)
+    Q = q0.clone()
+    graph.run(Q, args.warmup)
+    a, b = _events(torch)
+    torch.cuda.synchronize()
+    a.record()
+    graph.run(Q, args.steps)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    ms_one = ms / args.steps
+    ms_pack = 0.0
+    out = {"workload": "256 Taylor-Green instances, N log-uniform in [2048, 65536] (rounded to "
+                       "square lattices), m uniform in {4, 6, 8}, h/s 1.7/2.2/2.8, FP32, "
+                       "per-instance dt, one CUDA graph launch per step",
+           "instances": len(instances), "nodes_total": N, "nnz_total": plan.nnz,
+           "node_evals_per_s": 4.0 * N * args.steps / (ms * 1e-3),
+           "instance_steps_per_s": len(instances) * args.steps / (ms * 1e-3),
+           "ms_per_step": ms_one, "tuned": tune, "build_s": build_s,
+           "alg_GBps_step": (4 * (24.0 * plan.nnz + 64.0 * N) + 8.0 * plan.nnz + 36.0 * N)
+           / (ms_one * 1e-3) / 1e9}
+    graph.close()
+    plan.close()
+    return out
+
+
+def run_varres(lb, torch, args):
+    """Variable resolution s(x) = s0 (1 + 1.5 sin^2 pi x), ~1.0M nodes, m = 10,
+    h = 3.3 s U[0.85, 1.25]: FP64 weight build, then FP32 steps."""
+    import labfm_inputs as li
+    ns = li.varres_columns()
+    xy = torch.tensor(ns.xy, device="cuda")
+    h = torch.tensor(ns.h, device="cuda")
+    s = torch.tensor(ns.s, device="cuda")
+    a, b = _events(torch)
+    a.record()
+    rp, col = lb.build_stencils(xy, h, ns.Lx, ns.Ly)
+    b.record()
+    c, d = _events(torch)
+    c.record()
+    wb = lb.build_weights(xy, h, s, ns.Lx, ns.Ly, rp, col, 10, residual=False)
+    d.record()
+    torch.cuda.synchronize()
+    counts = (rp[1:] - rp[:-1]).float()
+    plan = lb.Plan(rp, col, wb["w"], wb["kappa"], s, dtype=torch.float32)
+    q0 = torch.tensor(li.tgv_fields(ns.xy, C), dtype=torch.float32, device="cuda")
+    dt = float(lb.stable_dt(plan, q0, s, C, MU).item())
+    phys = lb.Phys(C * C, MU)
+    tune = plan.tune_step(q0, phys, dt)
+    work = lb.workspace(plan)
+    Q = q0.clone()
+    lb.rk_step(plan, Q, dt, args.warmup, phys, work=work)
+    e, f = _events(torch)
+    torch.cuda.synchronize()
+    e.record()
+    lb.rk_step(plan, Q, dt, args.steps, phys, work=work)
+    f.record()
+    torch.cuda.synchronize()
+    ms = e.elapsed_time(f)
+    out = {"workload": "variable-resolution periodic box, s(x) = s0 (1 + 1.5 sin^2 pi x), "
+                       f"s0 = 6.654e-4 (s varies {ns.meta['s_ratio']:.2f}x), m = 10, "
+                       "h = 3.3 s U[0.85, 1.25]",
+           "nodes": ns.N, "nnz": int(col.numel()),
+           "neighbours_min_mean_max": [float(counts.min()), float(counts.mean()), float(counts.max())],
+           "stencil_ms": a.elapsed_time(b), "weight_build_ms": c.elapsed_time(d),
+           "weight_build_nodes_per_s": ns.N / (c.elapsed_time(d) * 1e-3),
+           "failed_nodes": int((wb["status"] != 0).sum().item()),
+           "fp32_node_evals_per_s": 4.0 * ns.N * args.steps / (ms * 1e-3),
+           "ms_per_step": ms / args.steps, "tuned": tune}
+    plan.close()
+    return out
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -382,6 +485,10 @@ def run_ours(args, world, rank, local):
         "clocks": clocks,
         "kernel_source_hash": khash,
     }
+
+    if not args.no_extras:
+        result["batch256"] = run_batch(lb, torch, args)
+        result["varres_m10"] = run_varres(lb, torch, args)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t0 = time.perf_counter()

@@ -71,7 +71,7 @@ typedef struct labfm_plan_info {
     int32_t dtype;      /* labfm_dtype */
     int32_t group;      /* lanes per node in the gather kernels */
     int32_t block;      /* threads per block in the gather kernels */
-    int32_t reserved;
+    int32_t n_instances; /* independent instances (1 unless built by labfm_plan_create_batched) */
     int64_t device_bytes; /* device memory owned by the plan */
 } labfm_plan_info;
 
@@ -157,6 +157,50 @@ int labfm_plan_create(labfm_plan** plan, int64_t N, int64_t nnz, labfm_dtype dty
                       const int32_t* row_ptr, const int32_t* col, const double* w,
                       const double* kappa, const double* s, void* stream);
 
+/*
+ * A plan over many independent instances (for example flow problems of
+ * different sizes and orders m): the instances' operators are concatenated
+ * block-diagonally, node k of instance i becoming node off_i + k with
+ * off_i = N_0 + ... + N_{i-1}, so that one launch of each step kernel serves
+ * all of them.  Fields and states of a batched plan are 3 x N_total, instance
+ * after instance within each field.  Host arrays of n_inst entries:
+ *   N_inst, nnz_inst  sizes of each instance
+ *   row_ptr, col, w, kappa, s  device pointers of each instance, as for
+ *                     labfm_plan_create
+ * Synchronises `stream`.  Errors as labfm_plan_create.
+ */
+int labfm_plan_create_batched(labfm_plan** plan, int n_inst, const int64_t* N_inst,
+                              const int64_t* nnz_inst, const int32_t* const* row_ptr,
+                              const int32_t* const* col, const double* const* w,
+                              const double* const* kappa, const double* const* s,
+                              labfm_dtype dtype, void* stream);
+
+/*
+ * Per-instance time steps (host, n_instances values > 0).  Afterwards
+ * labfm_rk_step, labfm_rk_step_noalloc and labfm_step_graph_create accept
+ * dt = 0, meaning "each instance with its own step" (eq. dt applies per
+ * instance: the instances are independent problems).
+ */
+int labfm_plan_set_dt(labfm_plan* plan, const double* dt_inst, void* stream);
+
+/*
+ * eq. dt for every instance of a plan: the exact minimum over the instance's
+ * nodes of min(1.0 s_i / (|u_i| + c), 0.4 s_i^2 rho_i / mu).
+ *   dt_inst_out  device, n_instances doubles (output)
+ */
+int labfm_stable_dt_instances(const labfm_plan* plan, const void* fields, const double* s,
+                              double c, double mu, double* dt_inst_out, void* stream);
+
+/*
+ * Persistent stage kernel on (1) or off (0).  When on, labfm_rk_step launches
+ * one stage kernel per stage with a grid of (SMs x resident blocks); each warp
+ * takes tiles of consecutive nodes from a work-queue ticket (reset at every
+ * step), which balances uneven stencils and mixed instances dynamically.  The
+ * workspace grows by 64 bytes for the tickets (query labfm_rk_workspace_bytes
+ * after changing this).
+ */
+int labfm_plan_set_persistent(labfm_plan* plan, int enable);
+
 /* Free a plan and its device memory (synchronises the device first). NULL is a no-op. */
 int labfm_plan_destroy(labfm_plan* plan);
 
@@ -211,7 +255,8 @@ size_t labfm_rk_workspace_bytes(const labfm_plan* plan);
  * filter on ln rho, u, v.
  *   Q     device, 3 x N in the plan's dtype: initial state in, final state out
  *   work  device, labfm_rk_workspace_bytes(plan) bytes, 16-byte aligned
- *   dt    time step (see labfm_stable_dt); nsteps >= 0
+ *   dt    time step (see labfm_stable_dt), or 0 to use the per-instance steps set
+ *         with labfm_plan_set_dt; nsteps >= 0
  * Capturable in a CUDA graph (no allocation, no synchronisation).
  */
 int labfm_rk_step(const labfm_plan* plan, void* Q, void* work, size_t work_bytes, double dt,
@@ -237,6 +282,22 @@ int labfm_stable_dt(const labfm_plan* plan, const void* fields, const double* s,
 int labfm_rk_step_host(const labfm_plan* plan, void* Q_host, void* Q_dev, void* work,
                        size_t work_bytes, double dt, int nsteps, const labfm_phys* phys,
                        void* stream);
+
+/*
+ * One complete time step of labfm_rk_step (four fused stage kernels and the
+ * filter, plus the ticket reset of a persistent plan) captured once into a CUDA
+ * graph; labfm_step_graph_run packs Q into the workspace, replays the graph
+ * `nsteps` times on `stream` (one graph launch per step for every instance of
+ * a batched plan) and unpacks the result into Q.  The plan and `work` must
+ * outlive the graph; dt as for labfm_rk_step (0 = per-instance steps, whose
+ * values may be changed between runs with labfm_plan_set_dt).  The capture
+ * uses a private stream; create the graph outside any other capture.
+ */
+typedef struct labfm_step_graph labfm_step_graph;
+int labfm_step_graph_create(labfm_step_graph** graph, const labfm_plan* plan, void* work,
+                            size_t work_bytes, double dt, const labfm_phys* phys);
+int labfm_step_graph_run(labfm_step_graph* graph, void* Q, int nsteps, void* stream);
+int labfm_step_graph_destroy(labfm_step_graph* graph);
 
 /*
  * labfm_rk_step for callers that cannot allocate device memory: the same

@@ -50,7 +50,7 @@ class _Phys(ctypes.Structure):
 class _PlanInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nnz_padded", ctypes.c_int64),
                 ("dtype", ctypes.c_int32), ("group", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+                ("n_instances", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
 
 
 class _Profile(ctypes.Structure):
@@ -86,6 +86,13 @@ _SIGS = {
     "labfm_plan_read_profile": (_I32, [_P, ctypes.POINTER(_Profile)]),
     "labfm_probe_fma_rate": (_I32, [_I32, ctypes.POINTER(_D)]),
     "labfm_rk_step_noalloc": (_I32, [_P, _P, _D, _I32, ctypes.POINTER(_Phys), _P]),
+    "labfm_plan_create_batched": (_I32, [ctypes.POINTER(_P), _I32, _P, _P, _P, _P, _P, _P, _P, _I32, _P]),
+    "labfm_plan_set_dt": (_I32, [_P, _P, _P]),
+    "labfm_stable_dt_instances": (_I32, [_P, _P, _P, _D, _D, _P, _P]),
+    "labfm_plan_set_persistent": (_I32, [_P, _I32]),
+    "labfm_step_graph_create": (_I32, [ctypes.POINTER(_P), _P, _P, ctypes.c_size_t, _D, ctypes.POINTER(_Phys)]),
+    "labfm_step_graph_run": (_I32, [_P, _P, _I32, _P]),
+    "labfm_step_graph_destroy": (_I32, [_P]),
 }
 
 
@@ -182,6 +189,49 @@ def build_weights(xy, h, s, Lx, Ly, row_ptr, col, m, periodic=(True, True), resi
 class Plan:
     """A prepared operator for the step kernels (labfm_plan_create / labfm_plan_destroy)."""
 
+    @classmethod
+    def batched(cls, instances, dtype=torch.float32, stream=None):
+        """labfm_plan_create_batched over a list of dicts with row_ptr, col, w, kappa, s."""
+        n = len(instances)
+        arr = lambda vals, ct: (ct * n)(*vals)
+        Ns = arr([d["row_ptr"].numel() - 1 for d in instances], _I64)
+        nnzs = arr([d["col"].numel() for d in instances], _I64)
+        ptrs = {k: arr([_ptr(d[k]) if d[k].numel() else None for d in instances], _P)
+                for k in ("row_ptr", "col", "w", "kappa", "s")}
+        self = cls.__new__(cls)
+        self.N = int(sum(Ns))
+        self.nnz = int(sum(nnzs))
+        self.dtype = dtype
+        self.device = instances[0]["row_ptr"].device
+        self._keep = [d["w"].contiguous() for d in instances]
+        handle = _P()
+        _check(lib.labfm_plan_create_batched(
+            ctypes.byref(handle), n, ctypes.cast(Ns, _P), ctypes.cast(nnzs, _P),
+            ctypes.cast(ptrs["row_ptr"], _P), ctypes.cast(ptrs["col"], _P),
+            ctypes.cast(ptrs["w"], _P), ctypes.cast(ptrs["kappa"], _P), ctypes.cast(ptrs["s"], _P),
+            LABFM_F32 if dtype == torch.float32 else LABFM_F64, _stream(stream)))
+        self._h = handle
+        self.n_instances = n
+        self.offsets = [0]
+        for v in Ns:
+            self.offsets.append(self.offsets[-1] + int(v))
+        return self
+
+    def set_dt(self, dt_inst, stream=None):
+        """labfm_plan_set_dt: per-instance time steps (host sequence)."""
+        vals = (_D * len(dt_inst))(*[float(v) for v in dt_inst])
+        _check(lib.labfm_plan_set_dt(self._h, ctypes.cast(vals, _P), _stream(stream)))
+
+    def stable_dt_instances(self, fields, s, c, mu, stream=None):
+        """labfm_stable_dt_instances: eq. dt per instance (float64 device tensor)."""
+        out = torch.empty(getattr(self, "n_instances", 1), dtype=torch.float64, device=fields.device)
+        _check(lib.labfm_stable_dt_instances(self._h, _ptr(fields), _ptr(s), float(c), float(mu),
+                                             _ptr(out), _stream(stream)))
+        return out
+
+    def set_persistent(self, enable: bool = True) -> None:
+        _check(lib.labfm_plan_set_persistent(self._h, 1 if enable else 0))
+
     def __init__(self, row_ptr, col, w, kappa, s, dtype=torch.float32, stream=None):
         self.N = row_ptr.numel() - 1
         self.nnz = col.numel()
@@ -204,7 +254,7 @@ class Plan:
     def info(self) -> dict:
         inf = _PlanInfo()
         _check(lib.labfm_plan_get_info(self._h, ctypes.byref(inf)))
-        return {k: getattr(inf, k) for k, _ in _PlanInfo._fields_ if k != "reserved"}
+        return {k: getattr(inf, k) for k, _ in _PlanInfo._fields_}
 
     def set_launch(self, group: int, block: int) -> None:
         _check(lib.labfm_plan_set_launch(self._h, group, block))
@@ -224,6 +274,29 @@ class Plan:
         pr = _Profile()
         _check(lib.labfm_plan_read_profile(self._h, ctypes.byref(pr)))
         return {k: getattr(pr, k) for k, _ in _Profile._fields_}
+
+    def tune_step(self, Q: torch.Tensor, phys: Phys, dt: float, steps: int = 3) -> dict:
+        """Autotune the launch shape (labfm_plan_autotune) and then choose between the
+        plain and the persistent stage kernel by timing `steps` RK steps of each with
+        CUDA events.  Q is not modified.  Returns the chosen configuration."""
+        group, block = self.autotune(Q, phys)
+        best = None
+        for persistent in (False, True):
+            self.set_persistent(persistent)
+            work = workspace(self)
+            Qs = Q.clone()
+            rk_step(self, Qs, dt, 1, phys, work=work)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            rk_step(self, Qs, dt, steps, phys, work=work)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / steps
+            if best is None or ms < best[0]:
+                best = (ms, persistent)
+        self.set_persistent(best[1])
+        return {"group": group, "block": block, "persistent": best[1], "ms_per_step": best[0]}
 
     def workspace_bytes(self) -> int:
         return int(lib.labfm_rk_workspace_bytes(self._h))
@@ -309,3 +382,31 @@ def rk_step_noalloc(plan: Plan, Q: torch.Tensor, dt: float, nsteps: int, phys: P
     _check(lib.labfm_rk_step_noalloc(plan.handle, _ptr(Q), float(dt), int(nsteps), ctypes.byref(ph),
                                      _stream(stream)))
     return Q
+
+
+class StepGraph:
+    """labfm_step_graph_*: one captured CUDA graph per time step, replayed per step."""
+
+    def __init__(self, plan: Plan, dt: float, phys: Phys, work: torch.Tensor | None = None):
+        self.plan = plan
+        self.work = workspace(plan) if work is None else work
+        self._phys = phys.c()
+        h = _P()
+        _check(lib.labfm_step_graph_create(ctypes.byref(h), plan.handle, _ptr(self.work),
+                                           self.work.numel(), float(dt), ctypes.byref(self._phys)))
+        self._h = h
+
+    def run(self, Q: torch.Tensor, nsteps: int, stream=None) -> torch.Tensor:
+        _check(lib.labfm_step_graph_run(self._h, _ptr(Q), int(nsteps), _stream(stream)))
+        return Q
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib.labfm_step_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

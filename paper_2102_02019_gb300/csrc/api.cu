@@ -50,13 +50,41 @@ void free_plan_memory(labfm_plan* p) {
     cudaFree(p->w);
     cudaFree(p->wf);
     cudaFree(p->inv_s);
+    cudaFree(p->inst_off);
+    cudaFree(p->dt_node);
+    delete[] p->inst_off_host;
     p->row_ptr = nullptr;
     p->col = nullptr;
     p->w = p->wf = p->inv_s = nullptr;
+    p->inst_off = nullptr;
+    p->dt_node = nullptr;
+    p->inst_off_host = nullptr;
 }
 
 int check_plan(const labfm_plan* p) {
     if (!p || !p->row_ptr) return set_error(LABFM_EINVAL, "null or empty plan");
+    return LABFM_OK;
+}
+
+int create_plan(labfm_plan** out, const PlanInput* in, int n_inst, labfm_dtype dtype, void* stream) {
+    if (dtype != LABFM_F32 && dtype != LABFM_F64) return set_error(LABFM_EINVAL, "unknown dtype");
+    labfm_plan* p = new (std::nothrow) labfm_plan();
+    if (!p) return set_error(LABFM_ENOMEM, "host allocation of the plan failed");
+    for (int k = 0; k < n_inst; ++k) {
+        p->N += in[k].N;
+        p->nnz += in[k].nnz;
+    }
+    p->dtype = dtype;
+    cudaGetDevice(&p->device);
+    p->group = 4;
+    p->block = 128;
+    const int rc = pack_plan(p, in, n_inst, as_stream(stream));
+    if (rc != LABFM_OK) {
+        free_plan_memory(p);
+        delete p;
+        return rc;
+    }
+    *out = p;
     return LABFM_OK;
 }
 
@@ -96,21 +124,57 @@ extern "C" int labfm_plan_create(labfm_plan** out, int64_t N, int64_t nnz, labfm
     if (N <= 0 || N >= (int64_t(1) << 31) - 1) return set_error(LABFM_EINVAL, "N out of range");
     if (nnz < 0 || nnz >= (int64_t(1) << 31)) return set_error(LABFM_EINVAL, "nnz out of range");
     if (dtype != LABFM_F32 && dtype != LABFM_F64) return set_error(LABFM_EINVAL, "unknown dtype");
-    labfm_plan* p = new (std::nothrow) labfm_plan();
-    if (!p) return set_error(LABFM_ENOMEM, "host allocation of the plan failed");
-    p->N = N;
-    p->nnz = nnz;
-    p->dtype = dtype;
-    cudaGetDevice(&p->device);
-    p->group = 8;
-    p->block = 256;
-    const int rc = pack_plan(p, row_ptr, col, w, kappa, s, as_stream(stream));
-    if (rc != LABFM_OK) {
-        free_plan_memory(p);
-        delete p;
-        return rc;
+    const PlanInput in{N, nnz, row_ptr, col, w, kappa, s};
+    return create_plan(out, &in, 1, dtype, stream);
+}
+
+extern "C" int labfm_plan_create_batched(labfm_plan** out, int n_inst, const int64_t* N_inst,
+                                         const int64_t* nnz_inst, const int32_t* const* row_ptr,
+                                         const int32_t* const* col, const double* const* w,
+                                         const double* const* kappa, const double* const* s,
+                                         labfm_dtype dtype, void* stream) {
+    if (!out) return set_error(LABFM_EINVAL, "null plan output");
+    *out = nullptr;
+    if (n_inst <= 0) return set_error(LABFM_EINVAL, "need at least one instance");
+    if (!N_inst || !nnz_inst || !row_ptr || !col || !w || !kappa || !s)
+        return set_error(LABFM_EINVAL, "null pointer argument");
+    PlanInput* in = new (std::nothrow) PlanInput[n_inst];
+    if (!in) return set_error(LABFM_ENOMEM, "host allocation failed");
+    int64_t Ntot = 0, nnztot = 0;
+    int rc = LABFM_OK;
+    for (int k = 0; k < n_inst && rc == LABFM_OK; ++k) {
+        in[k] = PlanInput{N_inst[k], nnz_inst[k], row_ptr[k], col[k], w[k], kappa[k], s[k]};
+        if (N_inst[k] <= 0 || nnz_inst[k] < 0 || !row_ptr[k] || !w[k] || !kappa[k] || !s[k] ||
+            (nnz_inst[k] > 0 && !col[k]))
+            rc = set_error(LABFM_EINVAL, "bad instance " + std::to_string(k));
+        Ntot += N_inst[k];
+        nnztot += nnz_inst[k];
     }
-    *out = p;
+    if (rc == LABFM_OK && (Ntot >= (int64_t(1) << 31) - 1 || nnztot >= (int64_t(1) << 31)))
+        rc = set_error(LABFM_EINVAL, "combined size out of range");
+    if (rc == LABFM_OK) rc = create_plan(out, in, n_inst, dtype, stream);
+    delete[] in;
+    return rc;
+}
+
+extern "C" int labfm_plan_set_dt(labfm_plan* p, const double* dt_inst, void* stream) {
+    if (int rc = check_plan(p)) return rc;
+    if (!dt_inst) return set_error(LABFM_EINVAL, "null dt array");
+    return set_node_dt(p, dt_inst, as_stream(stream));
+}
+
+extern "C" int labfm_stable_dt_instances(const labfm_plan* p, const void* fields, const double* s,
+                                         double c, double mu, double* dt_inst_out, void* stream) {
+    if (int rc = check_plan(p)) return rc;
+    if (!fields || !s || !dt_inst_out) return set_error(LABFM_EINVAL, "null pointer argument");
+    if (!(c >= 0.0) || !(mu > 0.0)) return set_error(LABFM_EINVAL, "need c >= 0 and mu > 0");
+    return launch_stable_dt_instances(p, fields, s, c, mu, dt_inst_out, as_stream(stream));
+}
+
+extern "C" int labfm_plan_set_persistent(labfm_plan* p, int enable) {
+    if (int rc = check_plan(p)) return rc;
+    p->persistent = enable != 0;
+    p->persist_grid = p->persistent ? persistent_grid(p) : 0;
     return LABFM_OK;
 }
 
@@ -135,7 +199,7 @@ extern "C" int labfm_plan_get_info(const labfm_plan* p, labfm_plan_info* info) {
     info->dtype = p->dtype;
     info->group = p->group;
     info->block = p->block;
-    info->reserved = 0;
+    info->n_instances = p->n_inst;
     info->device_bytes = p->device_bytes;
     return LABFM_OK;
 }
@@ -147,6 +211,7 @@ extern "C" int labfm_plan_set_launch(labfm_plan* p, int group, int block) {
                                            ", block " + std::to_string(block) + ")");
     p->group = group;
     p->block = block;
+    if (p->persistent) p->persist_grid = persistent_grid(p);
     return LABFM_OK;
 }
 
@@ -195,6 +260,7 @@ extern "C" int labfm_plan_autotune(labfm_plan* p, const void* fields, void* scra
     if (rc) return rc;
     p->group = bg;
     p->block = bb;
+    if (p->persistent) p->persist_grid = persistent_grid(p);
     if (group_out) *group_out = bg;
     if (block_out) *block_out = bb;
     return LABFM_OK;
@@ -228,7 +294,8 @@ extern "C" int labfm_rk_step(const labfm_plan* p, void* Q, void* work, size_t wo
         return set_error(LABFM_EINVAL, "work buffer smaller than labfm_rk_workspace_bytes");
     if (reinterpret_cast<uintptr_t>(work) % 16 != 0)
         return set_error(LABFM_EINVAL, "work buffer must be 16-byte aligned");
-    if (!(dt > 0.0) && nsteps > 0) return set_error(LABFM_EINVAL, "dt must be positive");
+    if (nsteps > 0 && !(dt > 0.0) && !(dt == 0.0 && p->dt_node))
+        return set_error(LABFM_EINVAL, "dt must be positive (or 0 with per-instance dt set)");
     return launch_rk_steps(p, Q, work, dt, nsteps, phys, as_stream(stream));
 }
 

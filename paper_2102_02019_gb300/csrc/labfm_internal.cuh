@@ -65,6 +65,14 @@ struct labfm_plan {
     void* wf = nullptr;          // nnz_pad filter weights kappa_i w^hyp_ji (dtype)
     void* inv_s = nullptr;       // N values 1/s_i (dtype), used by the F32 kernels
     int64_t device_bytes = 0;
+    // instances of a batched plan (one instance for labfm_plan_create): node
+    // ranges [inst_off[k], inst_off[k+1]) on the host and on the device
+    int n_inst = 1;
+    int64_t* inst_off_host = nullptr;
+    int64_t* inst_off = nullptr;
+    double* dt_node = nullptr;   // per-node time step (labfm_plan_set_dt), or null
+    bool persistent = false;     // stage kernel takes node tiles from a work queue
+    int persist_grid = 0;
     // launch timing (labfm_plan_set_profiling): event pairs around launches
     bool profiling = false;
     cudaEvent_t* prof_ev = nullptr;  // 2 * prof_cap events
@@ -75,6 +83,15 @@ struct labfm_plan {
 };
 
 namespace labfm {
+
+struct PlanInput {  // one instance's build outputs, for plan packing
+    int64_t N, nnz;
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const double* w;
+    const double* kappa;
+    const double* s;
+};
 
 // Launchers implemented in step.cu.
 int launch_rhs(const labfm_plan* p, const void* fields, void* rhs, const labfm_phys* ph,
@@ -92,8 +109,19 @@ bool launch_shape_supported(int group, int block);
 int prof_begin(labfm_plan* p, int kind, cudaStream_t st);
 void prof_end(labfm_plan* p, int idx, cudaStream_t st);
 
-// Plan packing (step.cu).
-int pack_plan(labfm_plan* p, const int32_t* row_ptr, const int32_t* col, const double* w,
-              const double* kappa, const double* s, cudaStream_t st);
+// Plan packing (step.cu): concatenates the instances block-diagonally.
+int pack_plan(labfm_plan* p, const PlanInput* in, int n_inst, cudaStream_t st);
+
+// The pieces of labfm_rk_step (step.cu), also used by the step graphs.
+// dt > 0: uniform step; dt == 0: the plan's per-node dt.  `profile` enables the
+// launch-timing hooks (off while a graph is being captured).
+int rk_pack(const labfm_plan* p, const void* Q, void* work, cudaStream_t st);
+int rk_unpack(const labfm_plan* p, void* Q, const void* work, cudaStream_t st);
+int rk_one_step(const labfm_plan* p, void* work, double dt, const labfm_phys* ph, bool profile,
+                cudaStream_t st);
+int set_node_dt(labfm_plan* p, const double* dt_inst_host, cudaStream_t st);
+int launch_stable_dt_instances(const labfm_plan* p, const void* fields, const double* s, double c,
+                               double mu, double* dt_inst, cudaStream_t st);
+int persistent_grid(const labfm_plan* p);
 
 }  // namespace labfm

@@ -46,7 +46,8 @@ extern "C" int labfm_rk_step_noalloc(const labfm_plan* p, void* Q, double dt, in
     if (!p || !p->row_ptr) return labfm::set_error(LABFM_EINVAL, "null or empty plan");
     if (!Q || !phys) return labfm::set_error(LABFM_EINVAL, "null pointer argument");
     if (nsteps < 0) return labfm::set_error(LABFM_EINVAL, "negative nsteps");
-    if (!(dt > 0.0) && nsteps > 0) return labfm::set_error(LABFM_EINVAL, "dt must be positive");
+    if (nsteps > 0 && !(dt > 0.0) && !(dt == 0.0 && p->dt_node))
+        return labfm::set_error(LABFM_EINVAL, "dt must be positive (or 0 with per-instance dt set)");
     const size_t need = labfm::rk_work_bytes(p);
     if (need > kStaticWorkBytes)
         return labfm::set_error(

@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <new>
 #include <string>
 #include <type_traits>
 
@@ -188,6 +189,7 @@ struct PlanView {
     const T* w;   // 5 x nnz_pad
     const T* wf;  // nnz_pad
     const T* inv_s;
+    const double* dt_node;  // per-node time step, or null for a uniform dt
 };
 
 // Operator loads of one 4-entry chunk starting at entry e (a multiple of 4).
@@ -231,7 +233,7 @@ __device__ __forceinline__ void load_filt_chunk(const PlanView<T>& P, int e, int
 template <typename T>
 PlanView<T> view(const labfm_plan* p) {
     return PlanView<T>{p->N, p->nnz_pad, p->row_ptr, p->col, static_cast<const T*>(p->w),
-                       static_cast<const T*>(p->wf), static_cast<const T*>(p->inv_s)};
+                       static_cast<const T*>(p->wf), static_cast<const T*>(p->inv_s), p->dt_node};
 }
 
 // The 12 derivatives of eq. icns at node i: d[0..1] = (a_x, a_y),
@@ -355,16 +357,15 @@ __global__ void k_rhs_soa(PlanView<T> P, SoA<T> in, T* __restrict__ out, Phys<T>
     }
 }
 
-// One fused RK stage: F = R(X_in) at node i; Q_out = Q_in + cb F;
-// X_out = Q_out + cx F (skipped when X_out is null).  Q_in may equal Q_out, and
-// Q_in may equal X_in (first stage, where X = Q).
+// One fused RK stage at node i (i < 0: an idle group that still joins the
+// shuffles): F = R(X_in); Q_out = Q_in + dt_i b_k F; X_out = Q_out + dt_i (a - b) F
+// (skipped when X_out is null).  Q_in may equal Q_out, and Q_in may equal X_in
+// (first stage, where X = Q).  dt_i is the uniform dt or the plan's per-node dt.
 template <typename T, int G, bool KAHAN, bool SCALED>
-__global__ void k_stage(PlanView<T> P, const Packed<T>* X_in, const Packed<T>* Q_in,
-                        Packed<T>* Q_out, Packed<T>* X_out, T cb, T cx, Phys<T> ph) {
-    const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    const int64_t node = gt / G;
-    const int gl = int(gt % G);
-    const int i = node < P.N ? int(node) : -1;
+__device__ __forceinline__ void stage_node(const PlanView<T>& P, int i, int gl,
+                                           const Packed<T>* X_in, const Packed<T>* Q_in,
+                                           Packed<T>* Q_out, Packed<T>* X_out, double dt,
+                                           double bk, double ck, const Phys<T>& ph) {
     const AoS<T> fld{X_in};
     T ai = 0, ui = 0, vi = 0;
     if (i >= 0) fld.get(i, ai, ui, vi);
@@ -374,6 +375,8 @@ __global__ void k_stage(PlanView<T> P, const Packed<T>* X_in, const Packed<T>* Q
         T Ra, Ru, Rv;
         const T is = SCALED ? P.inv_s[i] : T(1);
         pointwise_rhs<T, SCALED>(d, ai, ui, vi, is, ph.c2, ph.mu, ph.gx, ph.gy, Ra, Ru, Rv);
+        const double dti = P.dt_node ? P.dt_node[i] : dt;
+        const T cb = T(dti * bk), cx = T(dti * ck);
         T qa, qu, qv;
         if (Q_in == X_in) {
             qa = ai;
@@ -387,6 +390,43 @@ __global__ void k_stage(PlanView<T> P, const Packed<T>* X_in, const Packed<T>* Q
         qv = fma(cb, Rv, qv);
         store(Q_out, i, qa, qu, qv);
         if (X_out) store(X_out, i, fma(cx, Ra, qa), fma(cx, Ru, qu), fma(cx, Rv, qv));
+    }
+}
+
+// Nodes per work-queue tile of the persistent stage kernel, per warp.
+constexpr int kTileRows = 4;
+
+// PERSIST = false: one group of G lanes per node over a full grid.
+// PERSIST = true: a grid of (SMs x resident blocks); every warp repeatedly takes
+// the next tile of kTileRows * (32 / G) consecutive nodes from an atomic ticket
+// (*counter, zeroed before the launch), so that uneven stencils and mixed
+// instances balance dynamically across the GPU.
+template <typename T, int G, bool KAHAN, bool SCALED, bool PERSIST>
+__global__ void k_stage(PlanView<T> P, const Packed<T>* X_in, const Packed<T>* Q_in,
+                        Packed<T>* Q_out, Packed<T>* X_out, double dt, double bk, double ck,
+                        Phys<T> ph, int* counter) {
+    if (!PERSIST) {
+        const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+        const int64_t node = gt / G;
+        const int i = node < P.N ? int(node) : -1;
+        stage_node<T, G, KAHAN, SCALED>(P, i, int(gt % G), X_in, Q_in, Q_out, X_out, dt, bk, ck, ph);
+        return;
+    }
+    constexpr int per_warp = 32 / G;
+    constexpr int tile = kTileRows * per_warp;
+    const int lane = threadIdx.x & 31;
+    const int64_t ntiles = (P.N + tile - 1) / tile;
+    while (true) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(counter, 1);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= ntiles) break;
+#pragma unroll 1
+        for (int r = 0; r < kTileRows; ++r) {
+            const int64_t node = int64_t(t) * tile + r * per_warp + lane / G;
+            const int i = node < P.N ? int(node) : -1;
+            stage_node<T, G, KAHAN, SCALED>(P, i, lane % G, X_in, Q_in, Q_out, X_out, dt, bk, ck, ph);
+        }
     }
 }
 
@@ -509,7 +549,7 @@ __global__ void k_set_u64(unsigned long long* p, unsigned long long v) { *p = v;
 // ---------------------------------------------------------------- plan packing
 
 __global__ void k_padded_counts(int64_t N, const int32_t* __restrict__ row_ptr,
-                                int32_t* __restrict__ cnt) {
+                                int32_t* __restrict__ cnt) {  // cnt points at this instance's slice
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < N;
          i += int64_t(gridDim.x) * blockDim.x) {
         const int len = row_ptr[i + 1] - row_ptr[i];
@@ -520,7 +560,7 @@ __global__ void k_padded_counts(int64_t N, const int32_t* __restrict__ row_ptr,
 // Warp per row: copy col, scale the RHS weights (F32: w s^l), fold kappa into
 // the filter weights, and fill the pad entries (self, weight 0).
 template <typename T, bool SCALED>
-__global__ void k_pack_rows(int64_t N, int64_t nnz, int64_t nnz_pad,
+__global__ void k_pack_rows(int64_t N, int64_t nnz, int64_t nnz_pad, int64_t off,
                             const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                             const double* __restrict__ w, const double* __restrict__ kappa,
                             const double* __restrict__ s, const int32_t* __restrict__ prow,
@@ -528,13 +568,15 @@ __global__ void k_pack_rows(int64_t N, int64_t nnz, int64_t nnz_pad,
                             T* __restrict__ inv_s) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
-    for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; i < N; i += warps) {
-        const int r0 = row_ptr[i], len = row_ptr[i + 1] - r0;
+    for (int64_t il = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; il < N; il += warps) {
+        // il: node within this instance; i: node of the combined plan
+        const int64_t i = off + il;
+        const int r0 = row_ptr[il], len = row_ptr[il + 1] - r0;
         const int p0 = prow[i], plen = prow[i + 1] - p0;
-        const double si = s[i];
+        const double si = s[il];
         const double sc1 = SCALED ? si : 1.0;
         const double sc2 = SCALED ? si * si : 1.0;
-        const double kap = kappa[i];
+        const double kap = kappa[il];
         for (int e = lane; e < plen; e += 32) {
             const int64_t dst = int64_t(p0) + e;
             int32_t c = int32_t(i);
@@ -542,7 +584,7 @@ __global__ void k_pack_rows(int64_t N, int64_t nnz, int64_t nnz_pad,
             T vf = T(0);
             if (e < len) {
                 const int64_t src = int64_t(r0) + e;
-                c = col[src];
+                c = int32_t(off + col[src]);
                 v[0] = T(w[src] * sc1);
                 v[1] = T(w[nnz + src] * sc1);
                 v[2] = T(w[2 * nnz + src] * sc2);
@@ -601,26 +643,32 @@ int rhs_launch(const labfm_plan* p, const void* fields, void* rhs, const labfm_p
 
 template <typename T, int G>
 int stage_launch_g(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* qin, Packed<T>* qout,
-                   Packed<T>* xout, T cb, T cx, const Phys<T>& ph, cudaStream_t st) {
+                   Packed<T>* xout, double dt, double bk, double ck, const Phys<T>& ph,
+                   int* counter, cudaStream_t st) {
     const int block = p->block;
-    const int grid = grid_for(p->N * G, block);
-    if constexpr (std::is_same<T, float>::value)
-        k_stage<T, G, true, true><<<grid, block, 0, st>>>(view<T>(p), xin, qin, qout, xout, cb, cx, ph);
-    else
-        k_stage<T, G, false, false><<<grid, block, 0, st>>>(view<T>(p), xin, qin, qout, xout, cb, cx, ph);
+    constexpr bool F = std::is_same<T, float>::value;
+    if (p->persistent) {
+        k_stage<T, G, F, F, true><<<p->persist_grid, block, 0, st>>>(view<T>(p), xin, qin, qout, xout,
+                                                                      dt, bk, ck, ph, counter);
+    } else {
+        const int grid = grid_for(p->N * G, block);
+        k_stage<T, G, F, F, false><<<grid, block, 0, st>>>(view<T>(p), xin, qin, qout, xout, dt, bk,
+                                                           ck, ph, counter);
+    }
     LABFM_LAUNCH_CHECK("rk stage kernel");
     return LABFM_OK;
 }
 
 template <typename T>
 int stage_launch(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* qin, Packed<T>* qout,
-                 Packed<T>* xout, T cb, T cx, const Phys<T>& ph, cudaStream_t st) {
+                 Packed<T>* xout, double dt, double bk, double ck, const Phys<T>& ph, int* counter,
+                 cudaStream_t st) {
     switch (p->group) {
-        case 2: return stage_launch_g<T, 2>(p, xin, qin, qout, xout, cb, cx, ph, st);
-        case 4: return stage_launch_g<T, 4>(p, xin, qin, qout, xout, cb, cx, ph, st);
-        case 8: return stage_launch_g<T, 8>(p, xin, qin, qout, xout, cb, cx, ph, st);
-        case 16: return stage_launch_g<T, 16>(p, xin, qin, qout, xout, cb, cx, ph, st);
-        case 32: return stage_launch_g<T, 32>(p, xin, qin, qout, xout, cb, cx, ph, st);
+        case 2: return stage_launch_g<T, 2>(p, xin, qin, qout, xout, dt, bk, ck, ph, counter, st);
+        case 4: return stage_launch_g<T, 4>(p, xin, qin, qout, xout, dt, bk, ck, ph, counter, st);
+        case 8: return stage_launch_g<T, 8>(p, xin, qin, qout, xout, dt, bk, ck, ph, counter, st);
+        case 16: return stage_launch_g<T, 16>(p, xin, qin, qout, xout, dt, bk, ck, ph, counter, st);
+        case 32: return stage_launch_g<T, 32>(p, xin, qin, qout, xout, dt, bk, ck, ph, counter, st);
     }
     return set_error(LABFM_EINVAL, "unsupported group size");
 }
@@ -668,7 +716,8 @@ int filter_soa(const labfm_plan* p, const void* in, void* out, cudaStream_t st) 
     return set_error(LABFM_EINVAL, "unsupported group size");
 }
 
-// nsteps complete steps.  Work holds three packed buffers P (solution Q), X, Y:
+// Work layout: three packed buffers P (solution Q), X, Y of N nodes each, then
+// (persistent plans) 64 bytes of work-queue tickets.
 //   X <- pack(Q)
 //   per step:  stage 1: gather X, Q_i from X, P <- Q, Y <- X-update
 //              stage 2: gather Y, P in place, X <- update
@@ -677,41 +726,68 @@ int filter_soa(const labfm_plan* p, const void* in, void* out, cudaStream_t st) 
 //              filter:  gather P, X <- filtered (the next step's Q = X)
 //   Q <- unpack(X)
 template <typename T>
-int rk_steps(const labfm_plan* p, void* Q, void* work, double dt, int nsteps, const labfm_phys* php,
-             cudaStream_t st) {
-    if (nsteps == 0) return LABFM_OK;
+int rk_one_step_t(const labfm_plan* p, void* work, double dt, const labfm_phys* php, bool profile,
+                  cudaStream_t st) {
     const Phys<T> ph{T(php->c2), T(php->mu), T(php->gx), T(php->gy)};
     Packed<T>* P = static_cast<Packed<T>*>(work);
     Packed<T>* X = P + p->N;
     Packed<T>* Y = X + p->N;
-    const int pg = int(std::min<int64_t>((p->N + 255) / 256, 65535));
-    k_pack<T><<<pg, 256, 0, st>>>(p->N, static_cast<const T*>(Q), X);
-    LABFM_LAUNCH_CHECK("pack kernel");
-    T cb[4], cx[4];
-    for (int k = 0; k < 4; ++k) {
-        cb[k] = T(dt * kRkB[k]);
-        cx[k] = k < 3 ? T(dt * (kRkA[k] - kRkB[k])) : T(0);
-    }
+    int* tickets = reinterpret_cast<int*>(Y + p->N);
+    if (p->persistent) LABFM_CUDA_TRY(cudaMemsetAsync(tickets, 0, 4 * sizeof(int), st));
     int rc;
     labfm_plan* pm = const_cast<labfm_plan*>(p);  // only the launch-timing record changes
     const Packed<T>* xin[4] = {X, Y, X, Y};
     const Packed<T>* qin[4] = {X, P, P, P};
     Packed<T>* xout[4] = {Y, X, Y, nullptr};
-    for (int step = 0; step < nsteps; ++step) {
-        for (int k = 0; k < 4; ++k) {
-            const int ev = prof_begin(pm, 0, st);
-            if ((rc = stage_launch<T>(p, xin[k], qin[k], P, xout[k], cb[k], cx[k], ph, st))) return rc;
-            prof_end(pm, ev, st);
-        }
-        const int ev = prof_begin(pm, 1, st);
-        if ((rc = filter_aos<T>(p, P, X, st))) return rc;
+    for (int k = 0; k < 4; ++k) {
+        const double bk = kRkB[k];
+        const double ck = k < 3 ? kRkA[k] - kRkB[k] : 0.0;
+        const int ev = profile ? prof_begin(pm, 0, st) : -1;
+        if ((rc = stage_launch<T>(p, xin[k], qin[k], P, xout[k], dt, bk, ck, ph, tickets + k, st)))
+            return rc;
         prof_end(pm, ev, st);
     }
-    k_unpack<T><<<pg, 256, 0, st>>>(p->N, X, static_cast<T*>(Q));
+    const int ev = profile ? prof_begin(pm, 1, st) : -1;
+    if ((rc = filter_aos<T>(p, P, X, st))) return rc;
+    prof_end(pm, ev, st);
+    return LABFM_OK;
+}
+
+}  // namespace
+
+int rk_pack(const labfm_plan* p, const void* Q, void* work, cudaStream_t st) {
+    const int pg = int(std::min<int64_t>((p->N + 255) / 256, 65535));
+    if (p->dtype == LABFM_F32) {
+        Packed<float>* X = static_cast<Packed<float>*>(work) + p->N;
+        k_pack<float><<<pg, 256, 0, st>>>(p->N, static_cast<const float*>(Q), X);
+    } else {
+        Packed<double>* X = static_cast<Packed<double>*>(work) + p->N;
+        k_pack<double><<<pg, 256, 0, st>>>(p->N, static_cast<const double*>(Q), X);
+    }
+    LABFM_LAUNCH_CHECK("pack kernel");
+    return LABFM_OK;
+}
+
+int rk_unpack(const labfm_plan* p, void* Q, const void* work, cudaStream_t st) {
+    const int pg = int(std::min<int64_t>((p->N + 255) / 256, 65535));
+    if (p->dtype == LABFM_F32) {
+        const Packed<float>* X = static_cast<const Packed<float>*>(work) + p->N;
+        k_unpack<float><<<pg, 256, 0, st>>>(p->N, X, static_cast<float*>(Q));
+    } else {
+        const Packed<double>* X = static_cast<const Packed<double>*>(work) + p->N;
+        k_unpack<double><<<pg, 256, 0, st>>>(p->N, X, static_cast<double*>(Q));
+    }
     LABFM_LAUNCH_CHECK("unpack kernel");
     return LABFM_OK;
 }
 
+int rk_one_step(const labfm_plan* p, void* work, double dt, const labfm_phys* ph, bool profile,
+                cudaStream_t st) {
+    return p->dtype == LABFM_F32 ? rk_one_step_t<float>(p, work, dt, ph, profile, st)
+                                 : rk_one_step_t<double>(p, work, dt, ph, profile, st);
+}
+
+namespace {
 }  // namespace
 
 bool launch_shape_supported(int group, int block) {
@@ -732,13 +808,49 @@ int launch_filter_soa(const labfm_plan* p, const void* in, void* out, cudaStream
 
 size_t rk_work_bytes(const labfm_plan* p) {
     const size_t per = p->dtype == LABFM_F32 ? sizeof(Packed<float>) : sizeof(Packed<double>);
-    return size_t(3) * size_t(p->N) * per;
+    return size_t(3) * size_t(p->N) * per + (p->persistent ? 64 : 0);
 }
 
 int launch_rk_steps(const labfm_plan* p, void* Q, void* work, double dt, int nsteps,
                     const labfm_phys* ph, cudaStream_t st) {
-    return p->dtype == LABFM_F32 ? rk_steps<float>(p, Q, work, dt, nsteps, ph, st)
-                                 : rk_steps<double>(p, Q, work, dt, nsteps, ph, st);
+    if (nsteps == 0) return LABFM_OK;
+    int rc;
+    if ((rc = rk_pack(p, Q, work, st))) return rc;
+    for (int step = 0; step < nsteps; ++step)
+        if ((rc = rk_one_step(p, work, dt, ph, true, st))) return rc;
+    return rk_unpack(p, Q, work, st);
+}
+
+int persistent_grid(const labfm_plan* p) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaErrorInvalidValue;
+#define LABFM_OCC(T, G)                                                                      \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                       \
+        &per_sm, k_stage<T, G, std::is_same<T, float>::value, std::is_same<T, float>::value, \
+                         true>,                                                             \
+        p->block, 0)
+    if (p->dtype == LABFM_F32) {
+        switch (p->group) {
+            case 2: LABFM_OCC(float, 2); break;
+            case 4: LABFM_OCC(float, 4); break;
+            case 8: LABFM_OCC(float, 8); break;
+            case 16: LABFM_OCC(float, 16); break;
+            case 32: LABFM_OCC(float, 32); break;
+        }
+    } else {
+        switch (p->group) {
+            case 2: LABFM_OCC(double, 2); break;
+            case 4: LABFM_OCC(double, 4); break;
+            case 8: LABFM_OCC(double, 8); break;
+            case 16: LABFM_OCC(double, 16); break;
+            case 32: LABFM_OCC(double, 32); break;
+        }
+    }
+#undef LABFM_OCC
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    return sms * per_sm;
 }
 
 int launch_stable_dt(const labfm_plan* p, const void* fields, const double* s, double c, double mu,
@@ -755,10 +867,19 @@ int launch_stable_dt(const labfm_plan* p, const void* fields, const double* s, d
     return LABFM_OK;
 }
 
-int pack_plan(labfm_plan* p, const int32_t* row_ptr, const int32_t* col, const double* w,
-              const double* kappa, const double* s, cudaStream_t st) {
+int pack_plan(labfm_plan* p, const PlanInput* in, int n_inst, cudaStream_t st) {
     const int64_t N = p->N;
-    // padded row pointers
+    // instance node offsets
+    p->n_inst = n_inst;
+    p->inst_off_host = new (std::nothrow) int64_t[n_inst + 1];
+    if (!p->inst_off_host) return set_error(LABFM_ENOMEM, "host allocation failed");
+    p->inst_off_host[0] = 0;
+    for (int k = 0; k < n_inst; ++k) p->inst_off_host[k + 1] = p->inst_off_host[k] + in[k].N;
+    LABFM_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&p->inst_off), size_t(n_inst + 1) * sizeof(int64_t)));
+    LABFM_CUDA_TRY(cudaMemcpyAsync(p->inst_off, p->inst_off_host, size_t(n_inst + 1) * sizeof(int64_t),
+                                   cudaMemcpyHostToDevice, st));
+    p->device_bytes += (n_inst + 1) * sizeof(int64_t);
+    // padded row pointers over all instances
     LABFM_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&p->row_ptr), size_t(N + 1) * sizeof(int32_t)));
     p->device_bytes += (N + 1) * sizeof(int32_t);
     int32_t* cnt = nullptr;
@@ -768,8 +889,10 @@ int pack_plan(labfm_plan* p, const int32_t* row_ptr, const int32_t* col, const d
     LABFM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&cnt), size_t(N) * sizeof(int32_t), st));
     LABFM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&total), sizeof(int64_t), st));
     LABFM_CUDA_TRY(cudaMallocAsync(&scan_tmp, scan_bytes, st));
-    const int g = int(std::min<int64_t>((N + 255) / 256, 65535));
-    k_padded_counts<<<g, 256, 0, st>>>(N, row_ptr, cnt);
+    for (int k = 0; k < n_inst; ++k) {
+        const int g = int(std::min<int64_t>((in[k].N + 255) / 256, 65535));
+        k_padded_counts<<<g, 256, 0, st>>>(in[k].N, in[k].row_ptr, cnt + p->inst_off_host[k]);
+    }
     int rc = exclusive_scan_i32(cnt, p->row_ptr, N, total, scan_tmp, scan_bytes, st);
     int64_t nnz_pad = 0;
     if (rc == LABFM_OK) {
@@ -800,18 +923,113 @@ int pack_plan(labfm_plan* p, const int32_t* row_ptr, const int32_t* col, const d
         LABFM_CUDA_TRY(cudaMalloc(&p->inv_s, size_t(N) * es));
         p->device_bytes += N * es;
     }
-    const int gw = int(std::min<int64_t>((N * 32 + 255) / 256, 1 << 20));
-    if (p->dtype == LABFM_F32)
-        k_pack_rows<float, true><<<gw, 256, 0, st>>>(N, p->nnz, nnz_pad, row_ptr, col, w, kappa, s,
-                                                     p->row_ptr, p->col, static_cast<float*>(p->w),
-                                                     static_cast<float*>(p->wf),
-                                                     static_cast<float*>(p->inv_s));
-    else
-        k_pack_rows<double, false><<<gw, 256, 0, st>>>(N, p->nnz, nnz_pad, row_ptr, col, w, kappa, s,
-                                                       p->row_ptr, p->col, static_cast<double*>(p->w),
-                                                       static_cast<double*>(p->wf), nullptr);
-    LABFM_LAUNCH_CHECK("plan pack kernel");
+    for (int k = 0; k < n_inst; ++k) {
+        const PlanInput& I = in[k];
+        const int64_t off = p->inst_off_host[k];
+        const int gw = int(std::min<int64_t>((I.N * 32 + 255) / 256, 1 << 20));
+        if (p->dtype == LABFM_F32)
+            k_pack_rows<float, true><<<gw, 256, 0, st>>>(
+                I.N, I.nnz, nnz_pad, off, I.row_ptr, I.col, I.w, I.kappa, I.s, p->row_ptr, p->col,
+                static_cast<float*>(p->w), static_cast<float*>(p->wf), static_cast<float*>(p->inv_s));
+        else
+            k_pack_rows<double, false><<<gw, 256, 0, st>>>(
+                I.N, I.nnz, nnz_pad, off, I.row_ptr, I.col, I.w, I.kappa, I.s, p->row_ptr, p->col,
+                static_cast<double*>(p->w), static_cast<double*>(p->wf), nullptr);
+        LABFM_LAUNCH_CHECK("plan pack kernel");
+    }
     LABFM_CUDA_TRY(cudaStreamSynchronize(st));
+    return LABFM_OK;
+}
+
+// ---------------------------------------------------------------- per-instance time steps
+
+namespace {
+
+__global__ void k_fill_dt(int64_t n, double v, double* __restrict__ out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n;
+         i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = v;
+}
+
+__device__ __forceinline__ int instance_of(const int64_t* off, int n_inst, int64_t i) {
+    int lo = 0, hi = n_inst - 1;  // largest k with off[k] <= i
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// eq. dt per instance: exact minimum over the instance's nodes.
+template <typename T>
+__global__ void k_dt_instances(int64_t N, const T* __restrict__ f, const double* __restrict__ s,
+                               double c, double mu, const int64_t* __restrict__ off, int n_inst,
+                               unsigned long long* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    // warp-uniform loop: nodes of an instance are contiguous, so most warps hold a
+    // single instance and need one atomic
+    for (int64_t base = blockIdx.x * int64_t(blockDim.x) + (threadIdx.x & ~31); base < N;
+         base += stride) {
+        const int64_t i = base + lane;
+        double dt = INFINITY;
+        int inst = -1;
+        if (i < N) {
+            const double a = double(f[i]), u = double(f[N + i]), v = double(f[2 * N + i]);
+            const double si = s[i];
+            const double conv = 1.0 * si / (sqrt(u * u + v * v) + c);
+            const double visc = 0.4 * si * si * exp(a) / mu;
+            dt = fmin(conv, visc);
+            inst = instance_of(off, n_inst, i);
+        }
+        const int inst0 = __shfl_sync(0xffffffffu, inst, 0);
+        if (__all_sync(0xffffffffu, inst == inst0 || inst < 0)) {
+            double m = dt;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if (lane == 0 && inst0 >= 0)
+                atomicMin(out + inst0, static_cast<unsigned long long>(__double_as_longlong(m)));
+        } else if (inst >= 0) {
+            atomicMin(out + inst, static_cast<unsigned long long>(__double_as_longlong(dt)));
+        }
+    }
+}
+
+__global__ void k_set_u64_n(unsigned long long* p, int n, unsigned long long v) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) p[k] = v;
+}
+
+}  // namespace
+
+int set_node_dt(labfm_plan* p, const double* dt_inst_host, cudaStream_t st) {
+    if (!p->dt_node) {
+        LABFM_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&p->dt_node), size_t(p->N) * sizeof(double)));
+        p->device_bytes += p->N * sizeof(double);
+    }
+    for (int k = 0; k < p->n_inst; ++k) {
+        const int64_t a = p->inst_off_host[k], n = p->inst_off_host[k + 1] - a;
+        if (!(dt_inst_host[k] > 0.0)) return set_error(LABFM_EINVAL, "instance dt must be positive");
+        if (n == 0) continue;
+        const int g = int(std::min<int64_t>((n + 255) / 256, 4096));
+        k_fill_dt<<<g, 256, 0, st>>>(n, dt_inst_host[k], p->dt_node + a);
+    }
+    LABFM_LAUNCH_CHECK("dt fill kernel");
+    return LABFM_OK;
+}
+
+int launch_stable_dt_instances(const labfm_plan* p, const void* fields, const double* s, double c,
+                               double mu, double* dt_inst, cudaStream_t st) {
+    unsigned long long* out = reinterpret_cast<unsigned long long*>(dt_inst);
+    k_set_u64_n<<<(p->n_inst + 255) / 256, 256, 0, st>>>(out, p->n_inst, 0x7ff0000000000000ull);
+    const int grid = int(std::min<int64_t>((p->N + 255) / 256, 4096));
+    if (p->dtype == LABFM_F32)
+        k_dt_instances<float><<<grid, 256, 0, st>>>(p->N, static_cast<const float*>(fields), s, c, mu,
+                                                    p->inst_off, p->n_inst, out);
+    else
+        k_dt_instances<double><<<grid, 256, 0, st>>>(p->N, static_cast<const double*>(fields), s, c,
+                                                     mu, p->inst_off, p->n_inst, out);
+    LABFM_LAUNCH_CHECK("instance dt kernel");
     return LABFM_OK;
 }
 
