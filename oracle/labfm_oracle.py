@@ -432,3 +432,108 @@ def kinetic_energy(q, s):
     """sum_i 1/2 rho_i |u_i|^2 V_i with node volume V_i = s_i^2."""
     a, u, v = q
     return float(np.sum(0.5 * np.exp(a) * (u * u + v * v) * s * s))
+
+
+# --------------------------------------------------------------------------
+# Discrete adjoint (vector-Jacobian products) of the step above.  The paper has
+# no adjoint; these are derived by hand from eq. general_do, eq. icns, the RK
+# scheme and the filter, and pinned by finite differences in the tests.
+# --------------------------------------------------------------------------
+
+def apply_op_transpose(g, wd, row_ptr, col):
+    """(L^d)^T g for L^d_i(phi) = sum_j (phi_j - phi_i) w_ji: entry (i, j)
+    sends w_ji g_i to node j and -w_ji g_i to node i."""
+    ri = row_index(row_ptr)
+    N = len(row_ptr) - 1
+    contrib = wd * g[ri]
+    out = np.zeros(N)
+    np.add.at(out, col, contrib)
+    return out - np.bincount(ri, weights=contrib, minlength=N)
+
+
+def rhs_vjp(q, mbar, w, row_ptr, col, c2, mu):
+    """(dR/dq)^T mbar for the right-hand side of eq. icns at state q."""
+    a, u, v = q
+    ma, mu_, mv = mbar
+    d = derivatives(q, w, row_ptr, col)
+    nu = mu * np.exp(-a)
+    gbar = {
+        "ax": -u * ma - c2 * mu_, "ay": -v * ma - c2 * mv,
+        "ux": -ma - u * mu_, "uy": -v * mu_,
+        "uxx": nu * (4.0 / 3.0) * mu_, "uxy": nu * (1.0 / 3.0) * mv, "uyy": nu * mu_,
+        "vx": -u * mv, "vy": -ma - v * mv,
+        "vxx": nu * mv, "vxy": nu * (1.0 / 3.0) * mu_, "vyy": nu * (4.0 / 3.0) * mv,
+    }
+    # dependence on the node's own values (besides the differences)
+    own_a = -nu * ((4.0 / 3.0 * d["uxx"] + d["uyy"] + 1.0 / 3.0 * d["vxy"]) * mu_
+                   + (4.0 / 3.0 * d["vyy"] + d["vxx"] + 1.0 / 3.0 * d["uxy"]) * mv)
+    own_u = -(d["ax"] * ma + d["ux"] * mu_ + d["vx"] * mv)
+    own_v = -(d["ay"] * ma + d["uy"] * mu_ + d["vy"] * mv)
+    abar = own_a + apply_op_transpose(gbar["ax"], w[0], row_ptr, col) \
+        + apply_op_transpose(gbar["ay"], w[1], row_ptr, col)
+    ubar = own_u + sum(apply_op_transpose(gbar["u" + op], w[k], row_ptr, col)
+                       for k, op in enumerate(RHS_OPS))
+    vbar = own_v + sum(apply_op_transpose(gbar["v" + op], w[k], row_ptr, col)
+                       for k, op in enumerate(RHS_OPS))
+    return np.stack([abar, ubar, vbar])
+
+
+def filter_vjp(lam, w_hyp, kappa, row_ptr, col):
+    """Transpose of phi -> phi + kappa L^hyp(phi), per field."""
+    return np.stack([f + apply_op_transpose(kappa * f, w_hyp, row_ptr, col) for f in lam])
+
+
+def rk_step_vjp(q, lam, dt, f, f_vjp):
+    """(dQ_next/dQ)^T lam for one RK3(2)4[2R+]C step written with its full
+    Butcher matrix: stages X_k = q + dt sum_{j<k} A_kj F_j, F_k = f(X_k),
+    Q_next = q + dt sum_k b_k F_k.  Reverse: Fbar_k = dt b_k lam +
+    dt sum_{l>k} A_lk Xbar_l, Xbar_k = f_vjp(X_k, Fbar_k), qbar = lam + sum_k Xbar_k."""
+    A = [[float(x) for x in row] for row in rk_butcher()]
+    b = [float(x) for x in RK_B]
+    q = np.asarray(q, dtype=np.float64)
+    X, F = [], []
+    for k in range(4):
+        Xk = q + dt * sum(A[k][j] * F[j] for j in range(k)) if k else q.copy()
+        X.append(Xk)
+        F.append(f(Xk))
+    Xbar = [None] * 4
+    for k in range(3, -1, -1):
+        Fbar = dt * b[k] * lam + dt * sum(A[l][k] * Xbar[l] for l in range(k + 1, 4)) if k < 3 \
+            else dt * b[k] * lam
+        Xbar[k] = f_vjp(X[k], Fbar)
+    return lam + sum(Xbar)
+
+
+def time_step_vjp(q, lam, dt, w, kappa, row_ptr, col, c2, mu):
+    """(d time_step / dq)^T lam: the filter is linear, so its transpose acts first."""
+    lam4 = filter_vjp(lam, w[5], kappa, row_ptr, col)
+    f = lambda x: rhs(x, w, row_ptr, col, c2, mu)
+    fv = lambda x, m: rhs_vjp(x, m, w, row_ptr, col, c2, mu)
+    return rk_step_vjp(q, lam4, dt, f, fv)
+
+
+def conserved_to_primitive(c):
+    """(rho, rho u, rho v) -> (ln rho, u, v)."""
+    rho, mx, my = c
+    return np.stack([np.log(rho), mx / rho, my / rho])
+
+
+def primitive_to_conserved(q):
+    a, u, v = q
+    rho = np.exp(a)
+    return np.stack([rho, rho * u, rho * v])
+
+
+def conserved_vjp(c, qbar):
+    """(d primitive / d conserved)^T qbar at conserved state c."""
+    rho, mx, my = c
+    ab, ub, vb = qbar
+    return np.stack([ab / rho - (ub * mx + vb * my) / (rho * rho), ub / rho, vb / rho])
+
+
+def kinetic_energy_grad(q, s):
+    """d KE / d (ln rho, u, v) for KE = sum_i 1/2 rho |u|^2 s_i^2."""
+    a, u, v = q
+    rho = np.exp(a)
+    V = s * s
+    return np.stack([0.5 * rho * (u * u + v * v) * V, rho * u * V, rho * v * V])
