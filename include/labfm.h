@@ -284,6 +284,68 @@ int labfm_rk_step_host(const labfm_plan* plan, void* Q_host, void* Q_dev, void* 
                        void* stream);
 
 /*
+ * ---- Adjoint (reverse mode).  The paper has no adjoint; these are the exact
+ * transposes of the forward operators above (eq. general_do, eq. icns, the RK
+ * step of Section 7 and the filter of Section 6), used to differentiate a flow
+ * objective with respect to the initial state.
+ *
+ * Build the transposed operator of a plan: for every node k, the rows i whose
+ * stencil contains k with their weights w_ik (same record layout as the forward
+ * operator), and the row sums of the forward weights.  Allocates device memory
+ * owned by the plan; synchronises `stream`.  Needed by the calls below.
+ */
+int labfm_plan_enable_adjoint(labfm_plan* plan, void* stream);
+
+/* Bytes of device workspace the adjoint calls need for this plan. */
+size_t labfm_adjoint_workspace_bytes(const labfm_plan* plan);
+
+/*
+ * grad = (dR/dq)^T lambda: the vector-Jacobian product of the eq. icns
+ * right-hand side at state `fields` (3 x N, plan dtype) with cotangent
+ * `lambda` (3 x N).  Derivative adjoints are applied through the transposed
+ * operator as a gather (no atomics); grad must not alias the inputs.
+ */
+int labfm_rhs_adjoint(const labfm_plan* plan, const void* fields, const void* lambda, void* grad,
+                      const labfm_phys* phys, void* work, size_t work_bytes, void* stream);
+
+/*
+ * One time step backwards: lambda <- (dQ_next/dQ)^T lambda for the step
+ * Q -> filter(RK3(2)4[2R+]C(Q)) that labfm_rk_step takes from the state Q
+ * (3 x N, the state at the start of the step, not modified).  The stage states
+ * are recomputed from Q; the reverse sweep is the low-storage transpose of the
+ * scheme: Lambda = Fil^T lambda, Fbar_4 = dt b_4 Lambda, then for k = 4..1
+ * Xbar_k = J_R(X_k)^T Fbar_k, Lambda += Xbar_k,
+ * Fbar_{k-1} = dt (b_{k-1} Lambda + (a_{k,k-1} - b_{k-1}) Xbar_k).
+ * dt as for labfm_rk_step.
+ */
+int labfm_rk_step_adjoint(const labfm_plan* plan, const void* Q, void* lambda, double dt,
+                          const labfm_phys* phys, void* work, size_t work_bytes, void* stream);
+
+/* lam_out = Fil^T lam_in = lam + L_hyp^T (kappa lam), per field (3 x N). */
+int labfm_filter_adjoint(const labfm_plan* plan, const void* lam_in, void* lam_out, void* work,
+                         size_t work_bytes, void* stream);
+
+/*
+ * Conserved (rho, rho u, rho v) to evolved (ln rho, u, v) variables, 3 x N in
+ * `dtype`, and its vector-Jacobian product cbar = (dq/dc)^T qbar at c.
+ */
+int labfm_conserved_to_primitive(const void* c, void* q, int64_t N, labfm_dtype dtype,
+                                 void* stream);
+int labfm_conserved_vjp(const void* c, const void* qbar, void* cbar, int64_t N,
+                        labfm_dtype dtype, void* stream);
+
+/*
+ * Domain kinetic energy KE = sum_i 1/2 rho_i |u_i|^2 s_i^2 (node volume s_i^2)
+ * of a state q = (ln rho, u, v), summed in FP64 in a fixed order by one block
+ * (the same result on every call), into one device double; and
+ * grad_out = scale * dKE/dq.
+ */
+int labfm_kinetic_energy(const void* q, const double* s, int64_t N, labfm_dtype dtype,
+                         double* ke_out, void* stream);
+int labfm_kinetic_energy_grad(const void* q, const double* s, int64_t N, labfm_dtype dtype,
+                              double scale, void* grad_out, void* stream);
+
+/*
  * One complete time step of labfm_rk_step (four fused stage kernels and the
  * filter, plus the ticket reset of a persistent plan) captured once into a CUDA
  * graph; labfm_step_graph_run packs Q into the workspace, replays the graph

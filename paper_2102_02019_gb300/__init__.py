@@ -93,6 +93,15 @@ _SIGS = {
     "labfm_step_graph_create": (_I32, [ctypes.POINTER(_P), _P, _P, ctypes.c_size_t, _D, ctypes.POINTER(_Phys)]),
     "labfm_step_graph_run": (_I32, [_P, _P, _I32, _P]),
     "labfm_step_graph_destroy": (_I32, [_P]),
+    "labfm_plan_enable_adjoint": (_I32, [_P, _P]),
+    "labfm_adjoint_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "labfm_rhs_adjoint": (_I32, [_P, _P, _P, _P, ctypes.POINTER(_Phys), _P, ctypes.c_size_t, _P]),
+    "labfm_rk_step_adjoint": (_I32, [_P, _P, _P, _D, ctypes.POINTER(_Phys), _P, ctypes.c_size_t, _P]),
+    "labfm_filter_adjoint": (_I32, [_P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "labfm_conserved_to_primitive": (_I32, [_P, _P, _I64, _I32, _P]),
+    "labfm_conserved_vjp": (_I32, [_P, _P, _P, _I64, _I32, _P]),
+    "labfm_kinetic_energy": (_I32, [_P, _P, _I64, _I32, _P, _P]),
+    "labfm_kinetic_energy_grad": (_I32, [_P, _P, _I64, _I32, _D, _P, _P]),
 }
 
 
@@ -410,3 +419,158 @@ class StepGraph:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- adjoint
+
+def _dcode(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return LABFM_F32
+    if t.dtype == torch.float64:
+        return LABFM_F64
+    raise ValueError("float32 or float64 tensors only")
+
+
+def enable_adjoint(plan: Plan, stream=None) -> None:
+    """labfm_plan_enable_adjoint: build the transposed operator of the plan."""
+    _check(lib.labfm_plan_enable_adjoint(plan.handle, _stream(stream)))
+
+
+def adjoint_workspace(plan: Plan) -> torch.Tensor:
+    nb = int(lib.labfm_adjoint_workspace_bytes(plan.handle))
+    return torch.empty(max(nb, 16), dtype=torch.uint8, device=plan.device)
+
+
+def rhs_adjoint(plan: Plan, fields, lam, phys: Phys, work=None, stream=None):
+    """(dR/dq)^T lam at state `fields` (labfm_rhs_adjoint)."""
+    work = adjoint_workspace(plan) if work is None else work
+    out = torch.empty_like(fields)
+    ph = phys.c()
+    _check(lib.labfm_rhs_adjoint(plan.handle, _ptr(fields), _ptr(lam), _ptr(out), ctypes.byref(ph),
+                                 _ptr(work), work.numel(), _stream(stream)))
+    return out
+
+
+def rk_step_adjoint(plan: Plan, Q, lam, dt: float, phys: Phys, work=None, stream=None):
+    """lam <- (dQ_next/dQ)^T lam for one step from state Q (labfm_rk_step_adjoint), in place."""
+    work = adjoint_workspace(plan) if work is None else work
+    ph = phys.c()
+    _check(lib.labfm_rk_step_adjoint(plan.handle, _ptr(Q), _ptr(lam), float(dt), ctypes.byref(ph),
+                                     _ptr(work), work.numel(), _stream(stream)))
+    return lam
+
+
+def filter_adjoint(plan: Plan, lam, work=None, stream=None):
+    work = adjoint_workspace(plan) if work is None else work
+    out = torch.empty_like(lam)
+    _check(lib.labfm_filter_adjoint(plan.handle, _ptr(lam), _ptr(out), _ptr(work), work.numel(),
+                                    _stream(stream)))
+    return out
+
+
+def conserved_to_primitive(c, stream=None):
+    q = torch.empty_like(c)
+    _check(lib.labfm_conserved_to_primitive(_ptr(c), _ptr(q), c.shape[1], _dcode(c), _stream(stream)))
+    return q
+
+
+def conserved_vjp(c, qbar, stream=None):
+    cb = torch.empty_like(c)
+    _check(lib.labfm_conserved_vjp(_ptr(c), _ptr(qbar), _ptr(cb), c.shape[1], _dcode(c),
+                                   _stream(stream)))
+    return cb
+
+
+def kinetic_energy(q, s, stream=None) -> torch.Tensor:
+    out = torch.empty(1, dtype=torch.float64, device=q.device)
+    _check(lib.labfm_kinetic_energy(_ptr(q), _ptr(s), q.shape[1], _dcode(q), _ptr(out), _stream(stream)))
+    return out
+
+
+def kinetic_energy_grad(q, s, scale: float = 1.0, stream=None):
+    g = torch.empty_like(q)
+    _check(lib.labfm_kinetic_energy_grad(_ptr(q), _ptr(s), q.shape[1], _dcode(q), float(scale), _ptr(g),
+                                         _stream(stream)))
+    return g
+
+
+class _Rollout(torch.autograd.Function):
+    """nsteps time steps of a plan as a differentiable map q0 -> q_final.
+
+    Forward keeps a checkpoint of the state every `every` steps.  Backward walks
+    the segments last to first: it recomputes the segment's step states from
+    its checkpoint, then applies labfm_rk_step_adjoint step by step in reverse."""
+
+    @staticmethod
+    def forward(ctx, q0, plan, dt, nsteps, phys, every):
+        work = workspace(plan)
+        q = q0.detach().clone()
+        ckpts = []
+        for k in range(nsteps):
+            if k % every == 0:
+                ckpts.append(q.clone())
+            rk_step(plan, q, dt, 1, phys, work=work)
+        ctx.plan, ctx.dt, ctx.nsteps, ctx.phys, ctx.every = plan, dt, nsteps, phys, every
+        ctx.ckpts = ckpts
+        return q
+
+    @staticmethod
+    def backward(ctx, gq):
+        plan, dt, nsteps, phys, every = ctx.plan, ctx.dt, ctx.nsteps, ctx.phys, ctx.every
+        lam = gq.detach().clone().contiguous()
+        work = workspace(plan)
+        awork = adjoint_workspace(plan)
+        for seg in range(len(ctx.ckpts) - 1, -1, -1):
+            k0 = seg * every
+            k1 = min(nsteps, k0 + every)
+            states = [ctx.ckpts[seg].clone()]
+            for _ in range(k0, k1 - 1):
+                q = states[-1].clone()
+                rk_step(plan, q, dt, 1, phys, work=work)
+                states.append(q)
+            for q in reversed(states):
+                rk_step_adjoint(plan, q, lam, dt, phys, work=awork)
+        ctx.ckpts = None
+        return lam, None, None, None, None, None
+
+
+def rollout(plan: Plan, q0: torch.Tensor, dt: float, nsteps: int, phys: Phys,
+            checkpoint_every: int = 50) -> torch.Tensor:
+    """Differentiable nsteps-step rollout of the evolved state (ln rho, u, v).
+    Requires enable_adjoint(plan) before backward."""
+    return _Rollout.apply(q0, plan, dt, nsteps, phys, checkpoint_every)
+
+
+class _ToPrimitive(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, c):
+        ctx.save_for_backward(c)
+        return conserved_to_primitive(c.detach().contiguous())
+
+    @staticmethod
+    def backward(ctx, qbar):
+        (c,) = ctx.saved_tensors
+        return conserved_vjp(c.detach().contiguous(), qbar.contiguous())
+
+
+class _KineticEnergy(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, q, s):
+        ctx.save_for_backward(q, s)
+        return kinetic_energy(q.detach().contiguous(), s)
+
+    @staticmethod
+    def backward(ctx, g):
+        q, s = ctx.saved_tensors
+        grad = kinetic_energy_grad(q.detach().contiguous(), s, float(g.sum().item()))
+        return grad, None
+
+
+def to_primitive(c: torch.Tensor) -> torch.Tensor:
+    """Differentiable (rho, rho u, rho v) -> (ln rho, u, v)."""
+    return _ToPrimitive.apply(c)
+
+
+def domain_kinetic_energy(q: torch.Tensor, s: torch.Tensor) -> torch.Tensor:
+    """Differentiable sum_i 1/2 rho |u|^2 s_i^2 (1-element float64 tensor)."""
+    return _KineticEnergy.apply(q, s)

@@ -1,0 +1,612 @@
+// Discrete adjoint of the time step: vector-Jacobian products of the eq. icns
+// right-hand side, of the filter and of one RK3(2)4[2R+]C step.  The paper has
+// no adjoint; the products are the exact transposes of the forward kernels.
+//
+// The transpose of a difference-form operator L(phi)_i = sum_j (phi_j - phi_i) w_ij
+// is (L^T g)_k = sum_{i : k in N(i)} w_ik g_i - (sum_j w_kj) g_k.  It is applied as
+// a gather over a transposed operator (for node k: the rows i that contain k,
+// with their weights w_ik), stored in the same 4-entry record layout as the
+// forward operator, plus the forward row sums: no scatter, no atomics.
+//
+// RHS adjoint at state X with cotangent m (two passes):
+//   pass A (node i): forward derivatives d_i, then the derivative adjoints
+//     g_i = (dR_i/dd_i)^T m_i (12 values, scaled by s_i^-l in F32 to match the
+//     nondimensional weights) and the own-value adjoints o_i = (dR_i/dX_i)^T m_i;
+//   pass B (node k): Xbar_k = o_k + sum over operators of (L^T g)_k.
+// One RK step backwards (low-storage form of the reverse sweep):
+//   Lambda = Fil^T lambda;  Fbar_4 = dt b_4 Lambda
+//   for k = 4..1: Xbar_k = J_R(X_k)^T Fbar_k; Lambda += Xbar_k;
+//                 Fbar_{k-1} = dt (b_{k-1} Lambda + (a_{k,k-1} - b_{k-1}) Xbar_k)
+//   result: Lambda (the cotangent of the state at the start of the step).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <string>
+#include <type_traits>
+
+#include "gather.cuh"
+#include "labfm_internal.cuh"
+
+#if !LABFM_CHUNK_AOS
+#error "the transposed-operator build reads the chunk-record layout"
+#endif
+
+namespace labfm {
+namespace {
+
+// Twelve derivative adjoints of one node, packed for three 16-byte gathers (F32):
+// [g_ax, g_ay, g_ux, g_uy] [g_uxx, g_uxy, g_uyy, g_vx] [g_vy, g_vxx, g_vxy, g_vyy]
+template <typename T> struct G12;
+template <> struct G12<float> { float4 q[3]; };
+template <> struct G12<double> { double2 q[6]; };
+
+__device__ __forceinline__ void g12_store(G12<float>* p, int64_t i, const float (&g)[12]) {
+    p[i].q[0] = make_float4(g[0], g[1], g[2], g[3]);
+    p[i].q[1] = make_float4(g[4], g[5], g[6], g[7]);
+    p[i].q[2] = make_float4(g[8], g[9], g[10], g[11]);
+}
+__device__ __forceinline__ void g12_store(G12<double>* p, int64_t i, const double (&g)[12]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) p[i].q[k] = make_double2(g[2 * k], g[2 * k + 1]);
+}
+__device__ __forceinline__ void g12_load(const G12<float>* p, int i, float (&g)[12]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float4 t = __ldg(&p[i].q[k]);
+        g[4 * k] = t.x;
+        g[4 * k + 1] = t.y;
+        g[4 * k + 2] = t.z;
+        g[4 * k + 3] = t.w;
+    }
+}
+__device__ __forceinline__ void g12_load(const G12<double>* p, int i, double (&g)[12]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const double2 t = __ldg(&p[i].q[k]);
+        g[2 * k] = t.x;
+        g[2 * k + 1] = t.y;
+    }
+}
+
+// Position of each operator's adjoint in G12 order, by field: a uses x, y
+// (0, 1); u and v use x, y, xx, xy, yy (2..6 and 7..11).
+constexpr int kGa = 0, kGu = 2, kGv = 7;
+
+template <typename T>
+PlanView<T> tview(const labfm_plan* p) {
+    return PlanView<T>{p->N, p->tnnz_pad, p->trow_ptr, nullptr, static_cast<const T*>(p->tw),
+                       static_cast<const T*>(p->twf), static_cast<const T*>(p->inv_s), p->dt_node};
+}
+
+// ---------------------------------------------------------------- pass A
+
+template <typename T, int G, bool KAHAN, bool SCALED>
+__global__ void k_adj_pointwise(PlanView<T> P, const Packed<T>* X, const Packed<T>* M,
+                                G12<T>* __restrict__ gout, Packed<T>* __restrict__ oout, Phys<T> ph) {
+    const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t node = gt / G;
+    const int gl = int(gt % G);
+    const int i = node < P.N ? int(node) : -1;
+    const AoS<T> fld{X};
+    T a = 0, u = 0, v = 0;
+    if (i >= 0) fld.get(i, a, u, v);
+    T d[12];
+    gather_derivatives<T, G, KAHAN>(P, fld, i, gl, a, u, v, d);
+    if (i < 0 || gl != 0) return;
+    const T is = SCALED ? P.inv_s[i] : T(1);
+    const T s1 = SCALED ? is : T(1), s2 = SCALED ? is * is : T(1);
+    const T ax = d[0] * s1, ay = d[1] * s1;
+    const T ux = d[2] * s1, uy = d[3] * s1, uxx = d[4] * s2, uxy = d[5] * s2, uyy = d[6] * s2;
+    const T vx = d[7] * s1, vy = d[8] * s1, vxx = d[9] * s2, vxy = d[10] * s2, vyy = d[11] * s2;
+    T ma, mu, mv;
+    unpack(M, i, ma, mu, mv);
+    const T nu = ph.mu * exp_neg(a);
+    const T third = T(1) / T(3), four_thirds = T(4) / T(3);
+    T g[12];
+    g[0] = (-u * ma - ph.c2 * mu) * s1;  // a_x
+    g[1] = (-v * ma - ph.c2 * mv) * s1;  // a_y
+    g[2] = (-ma - u * mu) * s1;          // u_x
+    g[3] = (-v * mu) * s1;               // u_y
+    g[4] = (nu * four_thirds * mu) * s2; // u_xx
+    g[5] = (nu * third * mv) * s2;       // u_xy
+    g[6] = (nu * mu) * s2;               // u_yy
+    g[7] = (-u * mv) * s1;               // v_x
+    g[8] = (-ma - v * mv) * s1;          // v_y
+    g[9] = (nu * mv) * s2;               // v_xx
+    g[10] = (nu * third * mu) * s2;      // v_xy
+    g[11] = (nu * four_thirds * mv) * s2;// v_yy
+    g12_store(gout, i, g);
+    const T oa = -nu * ((four_thirds * uxx + uyy + third * vxy) * mu +
+                        (four_thirds * vyy + vxx + third * uxy) * mv);
+    const T ou = -(ax * ma + ux * mu + vx * mv);
+    const T ov = -(ay * ma + uy * mu + vy * mv);
+    store(oout, i, oa, ou, ov);
+}
+
+// ---------------------------------------------------------------- pass B
+
+// MODE 0: out = Xbar.  MODE 1 (RK reverse sweep): Lam += Xbar, and when
+// Fnext is not null, Fnext = dt_i (bprev Lam + cprev Xbar).
+template <typename T, int G, int MODE>
+__global__ void k_adj_transpose(PlanView<T> PT, const G12<T>* gin, const Packed<T>* oin,
+                                const T* __restrict__ rsum, Packed<T>* out, Packed<T>* Lam,
+                                Packed<T>* Fnext, double dt, double bprev, double cprev) {
+    const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t node = gt / G;
+    const int gl = int(gt % G);
+    const int k = node < PT.N ? int(node) : -1;
+    T sa = 0, su = 0, sv = 0;
+    if (k >= 0) {
+        const int e0 = PT.row_ptr[k];
+        const int e1 = PT.row_ptr[k + 1];
+        for (int e = e0 + 4 * gl; e < e1; e += 4 * G) {
+            int ci[4];
+            T wx[4], wy[4], wxx[4], wxy[4], wyy[4];
+            load_rhs_chunk(PT, e, ci, wx, wy, wxx, wxy, wyy, 0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                T g[12];
+                g12_load(gin, ci[q], g);
+                const T w5[5] = {wx[q], wy[q], wxx[q], wxy[q], wyy[q]};
+                sa = fma(w5[0], g[kGa], sa);
+                sa = fma(w5[1], g[kGa + 1], sa);
+#pragma unroll
+                for (int o = 0; o < 5; ++o) {
+                    su = fma(w5[o], g[kGu + o], su);
+                    sv = fma(w5[o], g[kGv + o], sv);
+                }
+            }
+        }
+    }
+    sa = group_sum<G>(sa);
+    su = group_sum<G>(su);
+    sv = group_sum<G>(sv);
+    if (k < 0 || gl != 0) return;
+    T g[12];
+    g12_load(gin, k, g);
+    T r[5];
+#pragma unroll
+    for (int o = 0; o < 5; ++o) r[o] = rsum[int64_t(o) * PT.N + k];
+    T oa, ou, ov;
+    unpack(oin, k, oa, ou, ov);
+    T xa = oa + sa - (r[0] * g[kGa] + r[1] * g[kGa + 1]);
+    T xu = ou + su, xv = ov + sv;
+#pragma unroll
+    for (int o = 0; o < 5; ++o) {
+        xu -= r[o] * g[kGu + o];
+        xv -= r[o] * g[kGv + o];
+    }
+    if (MODE == 0) {
+        store(out, k, xa, xu, xv);
+        return;
+    }
+    T la, lu, lv;
+    unpack_rw(Lam, k, la, lu, lv);
+    la += xa;
+    lu += xu;
+    lv += xv;
+    store(Lam, k, la, lu, lv);
+    if (Fnext) {
+        const double h = PT.dt_node ? PT.dt_node[k] : dt;
+        const T cb = T(h * bprev), cx = T(h * cprev);
+        store(Fnext, k, cb * la + cx * xa, cb * lu + cx * xu, cb * lv + cx * xv);
+    }
+}
+
+// ---------------------------------------------------------------- filter adjoint
+
+// Lam_out = lam + L_hyp^T (kappa lam) = lam + sum_i wf_ik lam_i - (sum_j wf_kj) lam_k;
+// F_out (if not null) = dt_k b4 Lam_out.
+template <typename T, int G>
+__global__ void k_filter_adjoint(PlanView<T> PT, const Packed<T>* lam, const T* __restrict__ rsum_f,
+                                 Packed<T>* Lam_out, Packed<T>* F_out, double dt, double b4) {
+    const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t node = gt / G;
+    const int gl = int(gt % G);
+    const int k = node < PT.N ? int(node) : -1;
+    const AoS<T> fld{lam};
+    T sa = 0, su = 0, sv = 0;
+    if (k >= 0) {
+        const int e0 = PT.row_ptr[k];
+        const int e1 = PT.row_ptr[k + 1];
+        for (int e = e0 + 4 * gl; e < e1; e += 4 * G) {
+            int ci[4];
+            T wf[4];
+            load_filt_chunk(PT, e, ci, wf, 0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                T a, u, v;
+                fld.get(ci[q], a, u, v);
+                sa = fma(wf[q], a, sa);
+                su = fma(wf[q], u, su);
+                sv = fma(wf[q], v, sv);
+            }
+        }
+    }
+    sa = group_sum<G>(sa);
+    su = group_sum<G>(su);
+    sv = group_sum<G>(sv);
+    if (k < 0 || gl != 0) return;
+    T a, u, v;
+    fld.get(k, a, u, v);
+    const T r = rsum_f[k];
+    const T la = a + sa - r * a, lu = u + su - r * u, lv = v + sv - r * v;
+    store(Lam_out, k, la, lu, lv);
+    if (F_out) {
+        const double h = PT.dt_node ? PT.dt_node[k] : dt;
+        const T cb = T(h * b4);
+        store(F_out, k, cb * la, cb * lu, cb * lv);
+    }
+}
+
+// ---------------------------------------------------------------- transposed operator build
+
+// Warp per forward row i: count the in-degree of every column k (pads, which
+// point at the row itself, are skipped).
+template <typename T>
+__global__ void k_in_degree(PlanView<T> P, int32_t* __restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; i < P.N; i += warps) {
+        const int e0 = P.row_ptr[i], e1 = P.row_ptr[i + 1];
+        for (int e = e0 + lane; e < e1; e += 32) {
+            const char* rec = reinterpret_cast<const char*>(P.w) + int64_t(e >> 2) * ChunkBytes<T>::rhs;
+            const int k = reinterpret_cast<const int32_t*>(rec)[e & 3];
+            if (k != i) atomicAdd(cnt + k, 1);
+        }
+    }
+}
+
+__global__ void k_pad4(int64_t N, const int32_t* __restrict__ cnt, int32_t* __restrict__ out) {
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < N;
+         i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = (cnt[i] + 3) & ~3;
+}
+
+// Warp per forward row i: append (i, e) to the transposed row of every column.
+template <typename T>
+__global__ void k_fill_transposed(PlanView<T> P, const int32_t* __restrict__ trow,
+                                  int32_t* __restrict__ cursor, int32_t* __restrict__ ti,
+                                  int32_t* __restrict__ te) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; i < P.N; i += warps) {
+        const int e0 = P.row_ptr[i], e1 = P.row_ptr[i + 1];
+        for (int e = e0 + lane; e < e1; e += 32) {
+            const char* rec = reinterpret_cast<const char*>(P.w) + int64_t(e >> 2) * ChunkBytes<T>::rhs;
+            const int k = reinterpret_cast<const int32_t*>(rec)[e & 3];
+            if (k == i) continue;
+            const int slot = trow[k] + atomicAdd(cursor + k, 1);
+            ti[slot] = int32_t(i);
+            te[slot] = e;
+        }
+    }
+}
+
+// Warp per transposed row k: order the entries by source row i (the fill order
+// is nondeterministic) and write the records: column i, the forward weights of
+// entry (i -> k), and the filter weight; pads point at k with weight 0.
+template <typename T>
+__global__ void k_write_transposed(PlanView<T> P, int64_t N, const int32_t* __restrict__ trow,
+                                   const int32_t* __restrict__ cnt, const int32_t* __restrict__ ti,
+                                   const int32_t* __restrict__ te, T* __restrict__ tw,
+                                   T* __restrict__ twf) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t k = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; k < N; k += warps) {
+        const int t0 = trow[k], plen = trow[k + 1] - t0, len = cnt[k];
+        for (int q = lane; q < plen; q += 32) {
+            int32_t src_i = int32_t(k);
+            T v[5] = {T(0), T(0), T(0), T(0), T(0)};
+            T vf = T(0);
+            int rank = q;
+            if (q < len) {
+                src_i = ti[t0 + q];
+                rank = 0;
+                for (int r = 0; r < len; ++r) rank += ti[t0 + r] < src_i;
+                const int e = te[t0 + q];
+                const char* rec = reinterpret_cast<const char*>(P.w) + int64_t(e >> 2) * ChunkBytes<T>::rhs;
+                const T* wr = reinterpret_cast<const T*>(rec + 16);
+#pragma unroll
+                for (int d = 0; d < 5; ++d) v[d] = wr[4 * d + (e & 3)];
+                const char* frec = reinterpret_cast<const char*>(P.wf) + int64_t(e >> 2) * ChunkBytes<T>::filt;
+                vf = reinterpret_cast<const T*>(frec + 16)[e & 3];
+            }
+            const int64_t dst = int64_t(t0) + rank;
+            char* trec = reinterpret_cast<char*>(tw) + (dst >> 2) * ChunkBytes<T>::rhs;
+            reinterpret_cast<int32_t*>(trec)[dst & 3] = src_i;
+#pragma unroll
+            for (int d = 0; d < 5; ++d) reinterpret_cast<T*>(trec + 16)[4 * d + (dst & 3)] = v[d];
+            char* tfrec = reinterpret_cast<char*>(twf) + (dst >> 2) * ChunkBytes<T>::filt;
+            reinterpret_cast<int32_t*>(tfrec)[dst & 3] = src_i;
+            reinterpret_cast<T*>(tfrec + 16)[dst & 3] = vf;
+        }
+    }
+}
+
+// Warp per forward row i: sums of its RHS weights and filter weights (pads add 0).
+template <typename T>
+__global__ void k_row_sums(PlanView<T> P, T* __restrict__ rsum) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; i < P.N; i += warps) {
+        const int e0 = P.row_ptr[i], e1 = P.row_ptr[i + 1];
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        for (int e = e0 + lane; e < e1; e += 32) {
+            const char* rec = reinterpret_cast<const char*>(P.w) + int64_t(e >> 2) * ChunkBytes<T>::rhs;
+            const T* wr = reinterpret_cast<const T*>(rec + 16);
+#pragma unroll
+            for (int d = 0; d < 5; ++d) acc[d] += double(wr[4 * d + (e & 3)]);
+            const char* frec = reinterpret_cast<const char*>(P.wf) + int64_t(e >> 2) * ChunkBytes<T>::filt;
+            acc[5] += double(reinterpret_cast<const T*>(frec + 16)[e & 3]);
+        }
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            double v = acc[d];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) rsum[int64_t(d) * P.N + i] = T(v);
+        }
+    }
+}
+
+template <typename T>
+int build_transposed(labfm_plan* p, cudaStream_t st) {
+    const int64_t N = p->N;
+    const PlanView<T> P = view<T>(p);
+    int32_t *cnt = nullptr, *pcnt = nullptr, *cursor = nullptr, *ti = nullptr, *te = nullptr;
+    int64_t* total = nullptr;
+    void* scan_tmp = nullptr;
+    const size_t scan_bytes = exclusive_scan_scratch_bytes(N);
+    LABFM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&cnt), size_t(N) * 4, st));
+    LABFM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&pcnt), size_t(N) * 4, st));
+    LABFM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&cursor), size_t(N) * 4, st));
+    LABFM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&total), 8, st));
+    LABFM_CUDA_TRY(cudaMallocAsync(&scan_tmp, scan_bytes, st));
+    LABFM_CUDA_TRY(cudaMemsetAsync(cnt, 0, size_t(N) * 4, st));
+    LABFM_CUDA_TRY(cudaMemsetAsync(cursor, 0, size_t(N) * 4, st));
+    const int gw = int(std::min<int64_t>((N * 32 + 255) / 256, 1 << 20));
+    const int gn = int(std::min<int64_t>((N + 255) / 256, 65535));
+    k_in_degree<T><<<gw, 256, 0, st>>>(P, cnt);
+    k_pad4<<<gn, 256, 0, st>>>(N, cnt, pcnt);
+    LABFM_LAUNCH_CHECK("in-degree kernels");
+    LABFM_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&p->trow_ptr), size_t(N + 1) * 4));
+    int rc = exclusive_scan_i32(pcnt, p->trow_ptr, N, total, scan_tmp, scan_bytes, st);
+    int64_t tpad = 0;
+    if (rc == LABFM_OK) {
+        cudaError_t e = cudaMemcpyAsync(&tpad, total, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_error(e, "reading transposed size");
+    }
+    const size_t es = sizeof(T);
+    const size_t np = size_t(std::max<int64_t>(tpad, 4));
+    if (rc == LABFM_OK) {
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ti), np * 4, st);
+        if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&te), np * 4, st);
+        if (e == cudaSuccess) e = cudaMalloc(&p->tw, (np / 4) * ChunkBytes<T>::rhs);
+        if (e == cudaSuccess) e = cudaMalloc(&p->twf, (np / 4) * ChunkBytes<T>::filt);
+        if (e == cudaSuccess) e = cudaMalloc(&p->rsum, size_t(6) * N * es);
+        if (e != cudaSuccess) rc = cuda_error(e, "transposed operator allocation");
+    }
+    if (rc == LABFM_OK) {
+        p->tnnz_pad = tpad;
+        p->device_bytes += (N + 1) * 4 + (np / 4) * (ChunkBytes<T>::rhs + ChunkBytes<T>::filt) + 6 * N * es;
+        k_fill_transposed<T><<<gw, 256, 0, st>>>(P, p->trow_ptr, cursor, ti, te);
+        k_write_transposed<T><<<gw, 256, 0, st>>>(P, N, p->trow_ptr, cnt, ti, te, static_cast<T*>(p->tw),
+                                                  static_cast<T*>(p->twf));
+        k_row_sums<T><<<gw, 256, 0, st>>>(P, static_cast<T*>(p->rsum));
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_error(e, "transposed operator kernels");
+    }
+    cudaFreeAsync(cnt, st);
+    cudaFreeAsync(pcnt, st);
+    cudaFreeAsync(cursor, st);
+    cudaFreeAsync(total, st);
+    cudaFreeAsync(scan_tmp, st);
+    if (ti) cudaFreeAsync(ti, st);
+    if (te) cudaFreeAsync(te, st);
+    if (rc == LABFM_OK) {
+        const cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_error(e, "building the transposed operator");
+    }
+    return rc;
+}
+
+// ---------------------------------------------------------------- launches
+
+template <typename T>
+struct AdjWork {
+    Packed<T>* X[4];
+    Packed<T>* P;
+    Packed<T>* Lam;
+    Packed<T>* Fb;
+    Packed<T>* Ob;
+    G12<T>* g;
+};
+
+template <typename T>
+AdjWork<T> split_work(const labfm_plan* p, void* work) {
+    AdjWork<T> w;
+    Packed<T>* base = static_cast<Packed<T>*>(work);
+    for (int k = 0; k < 4; ++k) w.X[k] = base + k * p->N;
+    w.P = base + 4 * p->N;
+    w.Lam = base + 5 * p->N;
+    w.Fb = base + 6 * p->N;
+    w.Ob = base + 7 * p->N;
+    w.g = reinterpret_cast<G12<T>*>(base + 8 * p->N);
+    return w;
+}
+
+template <typename T, int G>
+int pass_a_g(const labfm_plan* p, const Packed<T>* X, const Packed<T>* M, G12<T>* g, Packed<T>* o,
+             const Phys<T>& ph, cudaStream_t st) {
+    constexpr bool F = std::is_same<T, float>::value;
+    const int grid = int((p->N * G + p->block - 1) / p->block);
+    k_adj_pointwise<T, G, F, F><<<grid, p->block, 0, st>>>(view<T>(p), X, M, g, o, ph);
+    LABFM_LAUNCH_CHECK("adjoint pointwise kernel");
+    return LABFM_OK;
+}
+
+template <typename T, int G>
+int pass_b_g(const labfm_plan* p, int mode, const G12<T>* g, const Packed<T>* o, Packed<T>* out,
+             Packed<T>* Lam, Packed<T>* Fnext, double dt, double bprev, double cprev,
+             cudaStream_t st) {
+    const int grid = int((p->N * G + p->block - 1) / p->block);
+    const T* rs = static_cast<const T*>(p->rsum);
+    if (mode == 0)
+        k_adj_transpose<T, G, 0><<<grid, p->block, 0, st>>>(tview<T>(p), g, o, rs, out, Lam, Fnext, dt,
+                                                            bprev, cprev);
+    else
+        k_adj_transpose<T, G, 1><<<grid, p->block, 0, st>>>(tview<T>(p), g, o, rs, out, Lam, Fnext, dt,
+                                                            bprev, cprev);
+    LABFM_LAUNCH_CHECK("adjoint transpose kernel");
+    return LABFM_OK;
+}
+
+template <typename T, int G>
+int filt_adj_g(const labfm_plan* p, const Packed<T>* lam, Packed<T>* Lam, Packed<T>* F, double dt,
+               double b4, cudaStream_t st) {
+    const int grid = int((p->N * G + p->block - 1) / p->block);
+    const T* rsf = static_cast<const T*>(p->rsum) + 5 * p->N;
+    k_filter_adjoint<T, G><<<grid, p->block, 0, st>>>(tview<T>(p), lam, rsf, Lam, F, dt, b4);
+    LABFM_LAUNCH_CHECK("filter adjoint kernel");
+    return LABFM_OK;
+}
+
+#define LABFM_G_DISPATCH(call)                                  \
+    switch (p->group) {                                         \
+        case 2: { constexpr int G = 2; return call; }           \
+        case 4: { constexpr int G = 4; return call; }           \
+        case 8: { constexpr int G = 8; return call; }           \
+        case 16: { constexpr int G = 16; return call; }         \
+        case 32: { constexpr int G = 32; return call; }         \
+    }                                                           \
+    return set_error(LABFM_EINVAL, "unsupported group size")
+
+template <typename T>
+int pass_a(const labfm_plan* p, const Packed<T>* X, const Packed<T>* M, G12<T>* g, Packed<T>* o,
+           const Phys<T>& ph, cudaStream_t st) {
+    LABFM_G_DISPATCH((pass_a_g<T, G>(p, X, M, g, o, ph, st)));
+}
+
+template <typename T>
+int pass_b(const labfm_plan* p, int mode, const G12<T>* g, const Packed<T>* o, Packed<T>* out,
+           Packed<T>* Lam, Packed<T>* Fnext, double dt, double bprev, double cprev, cudaStream_t st) {
+    LABFM_G_DISPATCH((pass_b_g<T, G>(p, mode, g, o, out, Lam, Fnext, dt, bprev, cprev, st)));
+}
+
+template <typename T>
+int filt_adj(const labfm_plan* p, const Packed<T>* lam, Packed<T>* Lam, Packed<T>* F, double dt,
+             double b4, cudaStream_t st) {
+    LABFM_G_DISPATCH((filt_adj_g<T, G>(p, lam, Lam, F, dt, b4, st)));
+}
+
+template <typename T>
+int rhs_adjoint_t(const labfm_plan* p, const void* fields, const void* lambda, void* grad,
+                  const labfm_phys* php, void* work, cudaStream_t st) {
+    const Phys<T> ph{T(php->c2), T(php->mu), T(php->gx), T(php->gy)};
+    AdjWork<T> w = split_work<T>(p, work);
+    int rc;
+    if ((rc = pack_fields(p, fields, w.X[0], st))) return rc;
+    if ((rc = pack_fields(p, lambda, w.Fb, st))) return rc;
+    if ((rc = pass_a<T>(p, w.X[0], w.Fb, w.g, w.Ob, ph, st))) return rc;
+    if ((rc = pass_b<T>(p, 0, w.g, w.Ob, w.Lam, nullptr, nullptr, 0.0, 0.0, 0.0, st))) return rc;
+    return unpack_fields(p, w.Lam, grad, st);
+}
+
+template <typename T>
+int rk_step_adjoint_t(const labfm_plan* p, const void* Q, void* lambda, double dt,
+                      const labfm_phys* php, void* work, cudaStream_t st) {
+    const Phys<T> ph{T(php->c2), T(php->mu), T(php->gx), T(php->gy)};
+    AdjWork<T> w = split_work<T>(p, work);
+    int rc;
+    // forward recompute of the stage states X1..X4 of this step
+    if ((rc = pack_fields(p, Q, w.X[0], st))) return rc;
+    if ((rc = forward_stage_states(p, w.X[0], w.P, w.X[1], w.X[2], w.X[3], dt, php, st))) return rc;
+    // filter transpose, then the stages backwards
+    if ((rc = pack_fields(p, lambda, w.Ob, st))) return rc;
+    if ((rc = filt_adj<T>(p, w.Ob, w.Lam, w.Fb, dt, kRkB[3], st))) return rc;
+    for (int k = 3; k >= 0; --k) {
+        if ((rc = pass_a<T>(p, w.X[k], w.Fb, w.g, w.Ob, ph, st))) return rc;
+        const double bprev = k > 0 ? kRkB[k - 1] : 0.0;
+        const double cprev = k > 0 ? kRkA[k - 1] - kRkB[k - 1] : 0.0;
+        if ((rc = pass_b<T>(p, 1, w.g, w.Ob, nullptr, w.Lam, k > 0 ? w.Fb : nullptr, dt, bprev, cprev,
+                            st)))
+            return rc;
+    }
+    return unpack_fields(p, w.Lam, lambda, st);
+}
+
+template <typename T>
+int filter_adjoint_t(const labfm_plan* p, const void* lam_in, void* lam_out, void* work,
+                     cudaStream_t st) {
+    AdjWork<T> w = split_work<T>(p, work);
+    int rc;
+    if ((rc = pack_fields(p, lam_in, w.Ob, st))) return rc;
+    if ((rc = filt_adj<T>(p, w.Ob, w.Lam, nullptr, 0.0, 0.0, st))) return rc;
+    return unpack_fields(p, w.Lam, lam_out, st);
+}
+
+size_t adjoint_work_bytes(const labfm_plan* p) {
+    if (p->dtype == LABFM_F32) return size_t(p->N) * (8 * sizeof(Packed<float>) + sizeof(G12<float>));
+    return size_t(p->N) * (8 * sizeof(Packed<double>) + sizeof(G12<double>));
+}
+
+int check_adjoint(const labfm_plan* p, void* work, size_t work_bytes) {
+    if (!p || !p->row_ptr) return set_error(LABFM_EINVAL, "null or empty plan");
+    if (!p->trow_ptr) return set_error(LABFM_EINVAL, "call labfm_plan_enable_adjoint first");
+    if (!work) return set_error(LABFM_EINVAL, "null work buffer");
+    if (work_bytes < adjoint_work_bytes(p))
+        return set_error(LABFM_EINVAL, "work buffer smaller than labfm_adjoint_workspace_bytes");
+    if (reinterpret_cast<uintptr_t>(work) % 16 != 0)
+        return set_error(LABFM_EINVAL, "work buffer must be 16-byte aligned");
+    return LABFM_OK;
+}
+
+}  // namespace
+}  // namespace labfm
+
+using namespace labfm;
+
+extern "C" int labfm_plan_enable_adjoint(labfm_plan* p, void* stream) {
+    if (!p || !p->row_ptr) return set_error(LABFM_EINVAL, "null or empty plan");
+    if (p->trow_ptr) return LABFM_OK;
+    cudaStream_t st = as_stream(stream);
+    return p->dtype == LABFM_F32 ? build_transposed<float>(p, st) : build_transposed<double>(p, st);
+}
+
+extern "C" size_t labfm_adjoint_workspace_bytes(const labfm_plan* p) {
+    return p ? adjoint_work_bytes(p) : 0;
+}
+
+extern "C" int labfm_rhs_adjoint(const labfm_plan* p, const void* fields, const void* lambda,
+                                 void* grad, const labfm_phys* phys, void* work, size_t work_bytes,
+                                 void* stream) {
+    if (int rc = check_adjoint(p, work, work_bytes)) return rc;
+    if (!fields || !lambda || !grad || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
+    cudaStream_t st = as_stream(stream);
+    return p->dtype == LABFM_F32 ? rhs_adjoint_t<float>(p, fields, lambda, grad, phys, work, st)
+                                 : rhs_adjoint_t<double>(p, fields, lambda, grad, phys, work, st);
+}
+
+extern "C" int labfm_rk_step_adjoint(const labfm_plan* p, const void* Q, void* lambda, double dt,
+                                     const labfm_phys* phys, void* work, size_t work_bytes,
+                                     void* stream) {
+    if (int rc = check_adjoint(p, work, work_bytes)) return rc;
+    if (!Q || !lambda || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
+    if (!(dt > 0.0) && !(dt == 0.0 && p->dt_node))
+        return set_error(LABFM_EINVAL, "dt must be positive (or 0 with per-instance dt set)");
+    cudaStream_t st = as_stream(stream);
+    return p->dtype == LABFM_F32 ? rk_step_adjoint_t<float>(p, Q, lambda, dt, phys, work, st)
+                                 : rk_step_adjoint_t<double>(p, Q, lambda, dt, phys, work, st);
+}
+
+extern "C" int labfm_filter_adjoint(const labfm_plan* p, const void* lam_in, void* lam_out,
+                                    void* work, size_t work_bytes, void* stream) {
+    if (int rc = check_adjoint(p, work, work_bytes)) return rc;
+    if (!lam_in || !lam_out) return set_error(LABFM_EINVAL, "null pointer argument");
+    cudaStream_t st = as_stream(stream);
+    return p->dtype == LABFM_F32 ? filter_adjoint_t<float>(p, lam_in, lam_out, work, st)
+                                 : filter_adjoint_t<double>(p, lam_in, lam_out, work, st);
+}

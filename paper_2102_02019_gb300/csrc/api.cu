@@ -52,6 +52,12 @@ void free_plan_memory(labfm_plan* p) {
     cudaFree(p->inv_s);
     cudaFree(p->inst_off);
     cudaFree(p->dt_node);
+    cudaFree(p->trow_ptr);
+    cudaFree(p->tw);
+    cudaFree(p->twf);
+    cudaFree(p->rsum);
+    p->trow_ptr = nullptr;
+    p->tw = p->twf = p->rsum = nullptr;
     delete[] p->inst_off_host;
     p->row_ptr = nullptr;
     p->col = nullptr;

@@ -1,0 +1,327 @@
+// Device helpers shared by the time-step kernels (step.cu) and the adjoint
+// kernels (adjoint.cu): RK coefficients, packed node state, operator-record
+// loads, the fused 12-derivative gather and the pointwise right-hand side.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "labfm_internal.cuh"
+
+namespace labfm {
+namespace {
+
+// RK3(2)4[2R+]C (Kennedy, Carpenter & Lewis 2000), the low-storage scheme named
+// in Section 7: sub-diagonal a_{k+1,k} and weights b_k.
+constexpr double kRkA[3] = {11847461282814.0 / 36547543011857.0,
+                            3943225443063.0 / 7078155732230.0,
+                            -346793006927.0 / 4029903576067.0};
+constexpr double kRkB[4] = {1017324711453.0 / 9774461848756.0,
+                            8237718856693.0 / 13685301971492.0,
+                            57731312506979.0 / 19404895981398.0,
+                            -101169746363290.0 / 37734290219643.0};
+
+// ---------------------------------------------------------------- vector helpers
+
+// Chunks of 4 stencil entries each lane loads before its gathers (1 or 2).
+#ifndef LABFM_GATHER_UNROLL
+#define LABFM_GATHER_UNROLL 1
+#endif
+// Cache hint for the operator streams (col and weights, read once per launch):
+// 0 = read-only path (ld.global.nc), 1 = evict-first (ld.global.cs).
+#ifndef LABFM_STREAM_HINT
+#define LABFM_STREAM_HINT 1
+#endif
+constexpr int kUnroll = LABFM_GATHER_UNROLL;
+
+template <typename V>
+__device__ __forceinline__ V ld_stream(const V* p) {
+#if LABFM_STREAM_HINT == 1
+    return __ldcs(p);
+#else
+    return __ldg(p);
+#endif
+}
+
+// `o` receives 4 values of an operator stream starting at o + off.
+template <int K>
+__device__ __forceinline__ void load4(const float* p, float (&o)[K], int off) {
+    const float4 t = ld_stream(reinterpret_cast<const float4*>(p));
+    o[off] = t.x;
+    o[off + 1] = t.y;
+    o[off + 2] = t.z;
+    o[off + 3] = t.w;
+}
+template <int K>
+__device__ __forceinline__ void load4(const double* p, double (&o)[K], int off) {
+    const double2 a = ld_stream(reinterpret_cast<const double2*>(p));
+    const double2 b = ld_stream(reinterpret_cast<const double2*>(p) + 1);
+    o[off] = a.x;
+    o[off + 1] = a.y;
+    o[off + 2] = b.x;
+    o[off + 3] = b.y;
+}
+template <int K>
+__device__ __forceinline__ void load4i(const int32_t* p, int (&o)[K], int off) {
+    const int4 t = ld_stream(reinterpret_cast<const int4*>(p));
+    o[off] = t.x;
+    o[off + 1] = t.y;
+    o[off + 2] = t.z;
+    o[off + 3] = t.w;
+}
+
+// Operator layout.  0: operator-major streams col[nnz], w[5][nnz], wf[nnz].
+// 1: chunk-interleaved: for every 4-entry chunk of a row, the four columns and
+// the four weights of each of the five RHS operators sit in one contiguous
+// record (96 bytes in F32), and the filter has its own records (col, kappa w^hyp).
+#ifndef LABFM_CHUNK_AOS
+#define LABFM_CHUNK_AOS 1
+#endif
+
+template <typename T>
+struct ChunkBytes {
+    static constexpr int rhs = 16 + 20 * int(sizeof(T));  // int4 col + 5 x 4 weights
+    static constexpr int filt = 16 + 4 * int(sizeof(T));  // int4 col + 4 weights
+};
+
+// Node state (ln rho, u, v) packed for one-instruction gathers: float4 for F32
+// (w unused), two double2 for F64.
+template <typename T> struct Packed;
+template <> struct Packed<float> { float4 v; };
+template <> struct Packed<double> { double2 au; double2 vp; };
+
+__device__ __forceinline__ void unpack(const Packed<float>* p, int j, float& a, float& u, float& v) {
+    const float4 t = __ldg(&p[j].v);
+    a = t.x;
+    u = t.y;
+    v = t.z;
+}
+__device__ __forceinline__ void unpack(const Packed<double>* p, int j, double& a, double& u, double& v) {
+    const double2 t = __ldg(&p[j].au);
+    a = t.x;
+    u = t.y;
+    v = __ldg(&p[j].vp.x);
+}
+// Plain (coherent) loads for a buffer that the same kernel also writes.
+__device__ __forceinline__ void unpack_rw(const Packed<float>* p, int j, float& a, float& u, float& v) {
+    const float4 t = p[j].v;
+    a = t.x;
+    u = t.y;
+    v = t.z;
+}
+__device__ __forceinline__ void unpack_rw(const Packed<double>* p, int j, double& a, double& u, double& v) {
+    const double2 t = p[j].au;
+    a = t.x;
+    u = t.y;
+    v = p[j].vp.x;
+}
+__device__ __forceinline__ void store(Packed<float>* p, int64_t j, float a, float u, float v) {
+    p[j].v = make_float4(a, u, v, 0.0f);
+}
+__device__ __forceinline__ void store(Packed<double>* p, int64_t j, double a, double u, double v) {
+    p[j].au = make_double2(a, u);
+    p[j].vp = make_double2(v, 0.0);
+}
+
+// Field access policies for the gathers: structure-of-arrays (public API) or
+// packed (inside labfm_rk_step).
+template <typename T>
+struct SoA {
+    const T* a;
+    const T* u;
+    const T* v;
+    __device__ __forceinline__ void get(int j, T& x, T& y, T& z) const {
+        x = __ldg(a + j);
+        y = __ldg(u + j);
+        z = __ldg(v + j);
+    }
+};
+template <typename T>
+struct AoS {
+    const Packed<T>* p;
+    __device__ __forceinline__ void get(int j, T& x, T& y, T& z) const { unpack(p, j, x, y, z); }
+};
+
+// Compensated (Kahan) accumulation used for the F32 second-derivative and
+// filter sums; the F64 path adds plainly.
+template <typename T, bool KAHAN>
+struct Acc {
+    T s = T(0), c = T(0);
+    __device__ __forceinline__ void add(T x) {
+        if (KAHAN) {
+            const T y = x - c;
+            const T t = s + y;
+            c = (t - s) - y;
+            s = t;
+        } else {
+            s += x;
+        }
+    }
+    __device__ __forceinline__ T value() const { return KAHAN ? s - c : s; }
+};
+
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+template <typename T>
+struct PlanView {
+    int64_t N;
+    int64_t nnz_pad;
+    const int32_t* row_ptr;
+    const int32_t* col;
+    const T* w;   // 5 x nnz_pad
+    const T* wf;  // nnz_pad
+    const T* inv_s;
+    const double* dt_node;  // per-node time step, or null for a uniform dt
+};
+
+// Operator loads of one 4-entry chunk starting at entry e (a multiple of 4).
+template <typename T, int K>
+__device__ __forceinline__ void load_rhs_chunk(const PlanView<T>& P, int e, int (&cj)[K],
+                                               T (&wx)[K], T (&wy)[K], T (&wxx)[K],
+                                               T (&wxy)[K], T (&wyy)[K], int off) {
+#if LABFM_CHUNK_AOS
+    const char* rec = reinterpret_cast<const char*>(P.w) + int64_t(e >> 2) * ChunkBytes<T>::rhs;
+    load4i(reinterpret_cast<const int32_t*>(rec), cj, off);
+    const T* wr = reinterpret_cast<const T*>(rec + 16);
+    load4(wr, wx, off);
+    load4(wr + 4, wy, off);
+    load4(wr + 8, wxx, off);
+    load4(wr + 12, wxy, off);
+    load4(wr + 16, wyy, off);
+#else
+    const int64_t nz = P.nnz_pad;
+    load4i(P.col + e, cj, off);
+    load4(P.w + e, wx, off);
+    load4(P.w + nz + e, wy, off);
+    load4(P.w + 2 * nz + e, wxx, off);
+    load4(P.w + 3 * nz + e, wxy, off);
+    load4(P.w + 4 * nz + e, wyy, off);
+#endif
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void load_filt_chunk(const PlanView<T>& P, int e, int (&cj)[K],
+                                                T (&wf)[K], int off) {
+#if LABFM_CHUNK_AOS
+    const char* rec = reinterpret_cast<const char*>(P.wf) + int64_t(e >> 2) * ChunkBytes<T>::filt;
+    load4i(reinterpret_cast<const int32_t*>(rec), cj, off);
+    load4(reinterpret_cast<const T*>(rec + 16), wf, off);
+#else
+    load4i(P.col + e, cj, off);
+    load4(P.wf + e, wf, off);
+#endif
+}
+
+template <typename T>
+PlanView<T> view(const labfm_plan* p) {
+    return PlanView<T>{p->N, p->nnz_pad, p->row_ptr, p->col, static_cast<const T*>(p->w),
+                       static_cast<const T*>(p->wf), static_cast<const T*>(p->inv_s), p->dt_node};
+}
+
+// The 12 derivatives of eq. icns at node i: d[0..1] = (a_x, a_y),
+// d[2..6] = (u_x, u_y, u_xx, u_xy, u_yy), d[7..11] = same for v, each
+// L^d_i(phi) = sum_j (phi_j - phi_i) w^d_ji.  Every lane of the group returns them.
+template <typename T, int G, bool KAHAN, class F>
+__device__ __forceinline__ void gather_derivatives(const PlanView<T>& P, const F& fld, int i,
+                                                   int gl, T ai, T ui, T vi, T (&d)[12]) {
+    T ax = 0, ay = 0, ux = 0, uy = 0, vx = 0, vy = 0;
+    Acc<T, KAHAN> uxx, uxy, uyy, vxx, vxy, vyy;
+    if (i >= 0) {
+        const int e0 = P.row_ptr[i];
+        const int e1 = P.row_ptr[i + 1];
+        // kUnroll 4-entry chunks per iteration (chunks gl, gl + G, ... of this
+        // pass): all their operator loads are issued before the gathers
+        for (int e = e0 + 4 * gl; e < e1; e += 4 * kUnroll * G) {
+            int cj[4 * kUnroll];
+            T wx[4 * kUnroll], wy[4 * kUnroll], wxx[4 * kUnroll], wxy[4 * kUnroll], wyy[4 * kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int eu = e + 4 * u * G;
+                if (u == 0 || eu < e1) {
+                    load_rhs_chunk(P, eu, cj, wx, wy, wxx, wxy, wyy, 4 * u);
+                } else {
+#pragma unroll
+                    for (int k = 4 * u; k < 4 * u + 4; ++k) {
+                        cj[k] = i;  // the node itself with zero weight adds exactly 0
+                        wx[k] = wy[k] = wxx[k] = wxy[k] = wyy[k] = T(0);
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4 * kUnroll; ++k) {
+                T aj, uj, vj;
+                fld.get(cj[k], aj, uj, vj);
+                const T da = aj - ai, du = uj - ui, dv = vj - vi;
+                ax = fma(da, wx[k], ax);
+                ay = fma(da, wy[k], ay);
+                ux = fma(du, wx[k], ux);
+                uy = fma(du, wy[k], uy);
+                vx = fma(dv, wx[k], vx);
+                vy = fma(dv, wy[k], vy);
+                uxx.add(du * wxx[k]);
+                uxy.add(du * wxy[k]);
+                uyy.add(du * wyy[k]);
+                vxx.add(dv * wxx[k]);
+                vxy.add(dv * wxy[k]);
+                vyy.add(dv * wyy[k]);
+            }
+        }
+    }
+    d[0] = group_sum<G>(ax);
+    d[1] = group_sum<G>(ay);
+    d[2] = group_sum<G>(ux);
+    d[3] = group_sum<G>(uy);
+    d[7] = group_sum<G>(vx);
+    d[8] = group_sum<G>(vy);
+    if (KAHAN) {
+        // the compensations are summed separately and applied once
+        d[4] = group_sum<G>(uxx.s) - group_sum<G>(uxx.c);
+        d[5] = group_sum<G>(uxy.s) - group_sum<G>(uxy.c);
+        d[6] = group_sum<G>(uyy.s) - group_sum<G>(uyy.c);
+        d[9] = group_sum<G>(vxx.s) - group_sum<G>(vxx.c);
+        d[10] = group_sum<G>(vxy.s) - group_sum<G>(vxy.c);
+        d[11] = group_sum<G>(vyy.s) - group_sum<G>(vyy.c);
+    } else {
+        d[4] = group_sum<G>(uxx.s);
+        d[5] = group_sum<G>(uxy.s);
+        d[6] = group_sum<G>(uyy.s);
+        d[9] = group_sum<G>(vxx.s);
+        d[10] = group_sum<G>(vxy.s);
+        d[11] = group_sum<G>(vyy.s);
+    }
+}
+
+__device__ __forceinline__ float exp_neg(float a) { return expf(-a); }
+__device__ __forceinline__ double exp_neg(double a) { return exp(-a); }
+
+// Pointwise right-hand side of eq. icns from the derivatives.  F32 weights are
+// nondimensional (w s^l), so the sums are scaled by s^-1 or s^-2 here.
+template <typename T, bool SCALED>
+__device__ __forceinline__ void pointwise_rhs(const T (&d)[12], T a, T u, T v, T inv_s, T c2, T mu,
+                                              T gx, T gy, T& Ra, T& Ru, T& Rv) {
+    const T s1 = SCALED ? inv_s : T(1);
+    const T s2 = SCALED ? inv_s * inv_s : T(1);
+    const T ax = d[0] * s1, ay = d[1] * s1;
+    const T ux = d[2] * s1, uy = d[3] * s1, uxx = d[4] * s2, uxy = d[5] * s2, uyy = d[6] * s2;
+    const T vx = d[7] * s1, vy = d[8] * s1, vxx = d[9] * s2, vxy = d[10] * s2, vyy = d[11] * s2;
+    const T nu = mu * exp_neg(a);
+    const T third = T(1) / T(3);
+    const T four_thirds = T(4) / T(3);
+    Ra = -(u * ax + v * ay) - (ux + vy);
+    Ru = -(u * ux + v * uy) - c2 * ax + nu * (four_thirds * uxx + uyy + third * vxy) + gx;
+    Rv = -(u * vx + v * vy) - c2 * ay + nu * (four_thirds * vyy + vxx + third * uxy) + gy;
+}
+
+template <typename T>
+struct Phys {
+    T c2, mu, gx, gy;
+};
+
+}  // namespace
+}  // namespace labfm

@@ -73,6 +73,14 @@ struct labfm_plan {
     double* dt_node = nullptr;   // per-node time step (labfm_plan_set_dt), or null
     bool persistent = false;     // stage kernel takes node tiles from a work queue
     int persist_grid = 0;
+    // transposed operator for the adjoint (labfm_plan_enable_adjoint): for node k
+    // the entries (i, w_ik) of every row i whose stencil contains k, in the same
+    // record layout as the forward operator, plus row sums of the forward weights
+    int32_t* trow_ptr = nullptr;  // N + 1, multiples of 4
+    int64_t tnnz_pad = 0;
+    void* tw = nullptr;           // transposed RHS records
+    void* twf = nullptr;          // transposed filter records
+    void* rsum = nullptr;         // 6 x N (dtype): sum_j w~^d_kj for the 5 RHS operators, sum_j wf_kj
     // launch timing (labfm_plan_set_profiling): event pairs around launches
     bool profiling = false;
     cudaEvent_t* prof_ev = nullptr;  // 2 * prof_cap events
@@ -120,6 +128,14 @@ int rk_unpack(const labfm_plan* p, void* Q, const void* work, cudaStream_t st);
 int rk_one_step(const labfm_plan* p, void* work, double dt, const labfm_phys* ph, bool profile,
                 cudaStream_t st);
 int set_node_dt(labfm_plan* p, const double* dt_inst_host, cudaStream_t st);
+// Pack / unpack a 3 x N structure-of-arrays state into / out of the packed node
+// layout of the step kernels (step.cu).
+int pack_fields(const labfm_plan* p, const void* soa, void* packed, cudaStream_t st);
+int unpack_fields(const labfm_plan* p, const void* packed, void* soa, cudaStream_t st);
+// Stages 1-3 of one RK step from the packed state X1, storing the stage states
+// X2, X3, X4 (P receives the partial solution register) (step.cu).
+int forward_stage_states(const labfm_plan* p, const void* X1, void* P, void* X2, void* X3,
+                         void* X4, double dt, const labfm_phys* ph, cudaStream_t st);
 int launch_stable_dt_instances(const labfm_plan* p, const void* fields, const double* s, double c,
                                double mu, double* dt_inst, cudaStream_t st);
 int persistent_grid(const labfm_plan* p);

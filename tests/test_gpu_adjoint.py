@@ -1,0 +1,156 @@
+"""The hand-written adjoint on the GPU against the FP64 oracle's adjoint and
+against central finite differences of the GPU's own forward map."""
+import numpy as np
+import pytest
+
+import labfm_inputs as li
+from oracle import core as oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+C, MU = 10.0, 0.005
+
+
+@pytest.fixture(scope="module")
+def lb():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2102_02019_gb300 as lb
+    return lb
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
+
+
+def _case(lb, ns):
+    rp, col = oracle.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly)
+    ow = oracle.build_weights(ns.xy, ns.h, ns.s, rp, col, ns.m, ns.Lx, ns.Ly)
+    plans = {}
+    for dt_ in (torch.float64, torch.float32):
+        plan = lb.Plan(_dev(rp, torch.int32), _dev(col, torch.int32), _dev(ow["w"]), _dev(ow["kappa"]),
+                       _dev(ns.s), dtype=dt_)
+        lb.enable_adjoint(plan)
+        plans[dt_] = plan
+    return dict(ns=ns, rp=rp, col=col, w=ow["w"], kappa=ow["kappa"], plans=plans, s=_dev(ns.s))
+
+
+@pytest.fixture(scope="module")
+def stable(lb):
+    # multi-step gradients need a trajectory that stays bounded: the raw +-0.3 s
+    # jitter makes the locally tuned filter amplify a few modes (see the design
+    # notes), so the rollouts use the +-0.1 s lattice
+    return _case(lb, li.tgv_lattice(36, 32, m=4, h_over_s=1.7, jitter=0.1, seed=52))
+
+
+@pytest.fixture(scope="module")
+def case(lb):
+    return _case(lb, li.tgv_lattice(40, 36, m=6, h_over_s=2.2, jitter=0.3, seed=51))
+
+
+def test_rhs_adjoint_matches_oracle(lb, case):
+    ns = case["ns"]
+    q = li.perturbed_tgv_fields(ns.xy, C, amplitude=0.05, kmax=4)
+    m = np.random.default_rng(0).standard_normal(q.shape)
+    phys = lb.Phys(C * C, MU)
+    got = lb.rhs_adjoint(case["plans"][torch.float64], _dev(q), _dev(m), phys).cpu().numpy()
+    ref = oracle.rhs_vjp(q, m, case["w"], case["rp"], case["col"], C * C, MU)
+    assert np.all(_rel(got, ref) <= 1e-12), _rel(got, ref)
+
+
+def test_filter_adjoint_matches_oracle(lb, case):
+    ns = case["ns"]
+    m = np.random.default_rng(1).standard_normal((3, ns.N))
+    got = lb.filter_adjoint(case["plans"][torch.float64], _dev(m)).cpu().numpy()
+    ref = oracle.filter_vjp(m, case["w"][5], case["kappa"], case["rp"], case["col"])
+    assert np.all(_rel(got - m, ref - m) <= 1e-12)
+
+
+def test_rk_step_adjoint_matches_oracle(lb, case):
+    ns = case["ns"]
+    q = li.tgv_fields(ns.xy, C)
+    dt = oracle.stable_dt(q, ns.s, C, MU)
+    m = np.random.default_rng(2).standard_normal(q.shape)
+    lam = _dev(m)
+    lb.rk_step_adjoint(case["plans"][torch.float64], _dev(q), lam, dt, lb.Phys(C * C, MU))
+    ref = oracle.time_step_vjp(q, m, dt, case["w"], case["kappa"], case["rp"], case["col"], C * C, MU)
+    got = lam.cpu().numpy()
+    assert np.all(_rel(got, ref) <= 1e-12), _rel(got, ref)
+
+
+def _ke_gradient(lb, plan, c0, s, dt, nsteps, every):
+    c = c0.clone().requires_grad_(True)
+    q = lb.to_primitive(c)
+    qf = lb.rollout(plan, q, dt, nsteps, lb.Phys(C * C, MU), checkpoint_every=every)
+    ke = lb.domain_kinetic_energy(qf, s)
+    ke.backward()
+    return float(ke.item()), c.grad.detach()
+
+
+def test_kinetic_energy_gradient_matches_oracle_chain(lb, stable):
+    case = stable
+    ns = case["ns"]
+    q0 = li.perturbed_tgv_fields(ns.xy, C, amplitude=0.05, kmax=8)
+    c0 = oracle.primitive_to_conserved(q0)
+    dt = oracle.stable_dt(q0, ns.s, C, MU)
+    nsteps, every = 7, 3
+    ke, grad = _ke_gradient(lb, case["plans"][torch.float64], _dev(c0), case["s"], dt, nsteps, every)
+    # oracle: forward storing states, reverse with the step VJP
+    w, kap, rp, col = case["w"], case["kappa"], case["rp"], case["col"]
+    states = [q0]
+    for _ in range(nsteps):
+        states.append(oracle.time_step(states[-1], dt, w, kap, rp, col, C * C, MU))
+    assert abs(ke - oracle.kinetic_energy(states[-1], ns.s)) <= 1e-12 * ke
+    lam = oracle.kinetic_energy_grad(states[-1], ns.s)
+    for k in range(nsteps - 1, -1, -1):
+        lam = oracle.time_step_vjp(states[k], lam, dt, w, kap, rp, col, C * C, MU)
+    ref = oracle.conserved_vjp(c0, lam)
+    got = grad.cpu().numpy()
+    assert np.all(_rel(got, ref) <= 1e-10), _rel(got, ref)
+
+
+def test_kinetic_energy_gradient_matches_central_differences(lb, stable):
+    case = stable
+    ns = case["ns"]
+    plan = case["plans"][torch.float64]
+    q0 = li.perturbed_tgv_fields(ns.xy, C, amplitude=0.05, kmax=8)
+    c0 = _dev(oracle.primitive_to_conserved(q0))
+    dt = oracle.stable_dt(q0, ns.s, C, MU)
+    nsteps = 6
+    _, grad = _ke_gradient(lb, plan, c0, case["s"], dt, nsteps, 4)
+    phys = lb.Phys(C * C, MU)
+
+    def J(c):
+        q = lb.conserved_to_primitive(c)
+        lb.rk_step(plan, q, dt, nsteps, phys)
+        return float(lb.kinetic_energy(q, case["s"]).item())
+
+    rng = np.random.default_rng(3)
+    eps = 1e-6
+    for _ in range(3):
+        v = _dev(rng.standard_normal((3, ns.N)))
+        fd = (J(c0 + eps * v) - J(c0 - eps * v)) / (2 * eps)
+        ad = float((grad * v).sum().item())
+        assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+
+
+def test_fp32_adjoint_close_to_fp64(lb, case):
+    ns = case["ns"]
+    q = li.tgv_fields(ns.xy, C)
+    dt = oracle.stable_dt(q, ns.s, C, MU)
+    m = np.random.default_rng(4).standard_normal(q.shape)
+    out = {}
+    for dt_ in (torch.float64, torch.float32):
+        lam = _dev(m, dt_)
+        lb.rk_step_adjoint(case["plans"][dt_], _dev(q, dt_), lam, dt, lb.Phys(C * C, MU))
+        out[dt_] = lam.double().cpu().numpy()
+    # float32 rounding of inputs, weights and the twelve derivative adjoints: a few
+    # units of 2^-24 amplified by the stencil sums (|w| ~ s^-2) over 8 passes
+    assert np.all(_rel(out[torch.float32], out[torch.float64]) <= 1e-4)
