@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and variable-resolution workloads")
+    ap.add_argument("--group", type=int, default=0,
+                    help="fix the lanes per node of the main workload (0 = autotune)")
     ap.add_argument("--nx", type=int, default=512,
                     help="lattice side (512 = the benchmark workload; smaller sizes for profiling)")
     return ap.parse_args()
@@ -351,6 +353,92 @@ def run_varres(lb, torch, args):
     return out
 
 
+def _build(lb, torch, ns, residual=False):
+    xy = torch.tensor(ns.xy, device="cuda")
+    h = torch.tensor(ns.h, device="cuda")
+    s = torch.tensor(ns.s, device="cuda")
+    rp, col = lb.build_stencils(xy, h, ns.Lx, ns.Ly)
+    wb = lb.build_weights(xy, h, s, ns.Lx, ns.Ly, rp, col, ns.m, residual=residual)
+    return rp, col, wb, s
+
+
+def run_adjoint(lb, torch, args, nsteps=500, every=50):
+    """Gradient of the final domain kinetic energy w.r.t. the initial (rho, rho u, rho v):
+    262,144 nodes, m = 8, FP32, 500 steps, checkpoints every 50 steps.  The node set
+    uses +-0.1 s jitter so that the 500-step trajectory stays bounded."""
+    import numpy as np
+    import labfm_inputs as li
+    ns = li.tgv_lattice(512, m=8, h_over_s=2.8, jitter=0.05, seed=5)
+    rp, col, wb, s = _build(lb, torch, ns)
+    plan = lb.Plan(rp, col, wb["w"], wb["kappa"], s, dtype=torch.float32)
+    lb.enable_adjoint(plan)
+    q0 = li.perturbed_tgv_fields(ns.xy, C, amplitude=0.05, kmax=8)
+    c0 = torch.tensor(np.stack([np.exp(q0[0]), np.exp(q0[0]) * q0[1], np.exp(q0[0]) * q0[2]]),
+                      dtype=torch.float32, device="cuda")
+    phys = lb.Phys(C * C, MU)
+    dt = float(lb.stable_dt(plan, lb.conserved_to_primitive(c0), s, C, MU).item())
+    a, b = _events(torch)
+    c = c0.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    a.record()
+    q = lb.to_primitive(c)
+    qf = lb.rollout(plan, q, dt, nsteps, phys, checkpoint_every=every)
+    ke = lb.domain_kinetic_energy(qf, s)
+    b.record()
+    torch.cuda.synchronize()
+    fwd_ms = a.elapsed_time(b)
+    e, f = _events(torch)
+    e.record()
+    ke.backward()
+    f.record()
+    torch.cuda.synchronize()
+    bwd_ms = e.elapsed_time(f)
+    g = c.grad
+    out = {"workload": "262,144-node lattice (+-0.05 s jitter), m = 8, Taylor-Green + 0.05 x "
+                       "band-limited perturbation (|k| <= 8), FP32, 500 steps, checkpoint every 50",
+           "steps": nsteps, "checkpoint_every": every, "forward_ms": fwd_ms, "backward_ms": bwd_ms,
+           "backward_over_forward": bwd_ms / fwd_ms, "ke_final": float(ke.item()),
+           "grad_finite": bool(torch.isfinite(g).all().item()),
+           "grad_norm_per_field": [float(x) for x in g.double().norm(dim=1).cpu()]}
+    plan.close()
+    return out
+
+
+def run_fp32_error(lb, torch, args, nsteps=1000):
+    """FP32 trajectory against the FP64 one (which matches the CPU oracle to 1e-12 in
+    the parity tests) after nsteps steps, per field and per order m, on +-0.05 s
+    jittered lattices; also the kinetic-energy decay rate against the analytic
+    2b = -8 pi^2 / Re of Section 8.1."""
+    import math
+    import labfm_inputs as li
+    out = {}
+    two_b = -8.0 * math.pi ** 2 / 100.0
+    for m, hs, nx, steps in ((8, 2.8, 512, nsteps), (4, 1.7, 128, nsteps), (6, 2.2, 128, nsteps),
+                             (10, 3.3, 128, nsteps)):
+        ns = li.tgv_lattice(nx, m=m, h_over_s=hs, jitter=0.05, seed=6)
+        rp, col, wb, s = _build(lb, torch, ns)
+        res, rates = {}, {}
+        for dt_ in (torch.float64, torch.float32):
+            plan = lb.Plan(rp, col, wb["w"], wb["kappa"], s, dtype=dt_)
+            Q = torch.tensor(li.tgv_fields(ns.xy, C), dtype=dt_, device="cuda")
+            if dt_ == torch.float64:
+                dt = float(lb.stable_dt(plan, Q, s, C, MU).item())
+            ke0 = float(lb.kinetic_energy(Q, s).item())
+            lb.rk_step(plan, Q, dt, steps, lb.Phys(C * C, MU))
+            ke1 = float(lb.kinetic_energy(Q, s).item())
+            rates[dt_] = math.log(ke1 / ke0) / (steps * dt) / two_b if ke1 > 0 else float("nan")
+            res[dt_] = Q.double()
+            plan.close()
+        d = res[torch.float32] - res[torch.float64]
+        rel = (d.norm(dim=1) / res[torch.float64].norm(dim=1)).cpu().tolist()
+        out[f"m{m}_{nx}x{nx}"] = {"steps": steps, "t_end": steps * dt,
+                                 "rel_l2": {"ln_rho": rel[0], "u": rel[1], "v": rel[2]},
+                                 "finite": bool(torch.isfinite(res[torch.float32]).all().item()),
+                                 "ke_decay_over_2b": {"fp64": rates[torch.float64],
+                                                      "fp32": rates[torch.float32]}}
+    return out
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -382,11 +470,19 @@ def run_ours(args, world, rank, local):
     phys = lb.Phys(c2=C * C, mu=MU)
     q0 = torch.tensor(li.tgv_fields(ns.xy, C), device=dev)
 
+    shape_persistent = {}
+
     def measure(dtype, steps, warmup):
         plan = lb.Plan(row_ptr, col, wb["w"], wb["kappa"], s, dtype=dtype)
         Q = q0.to(dtype).contiguous()
-        group, block = plan.autotune(Q, phys, reps=3)
         dt = float(lb.stable_dt(plan, Q, s, C, MU).item())
+        if args.group:
+            plan.set_launch(args.group, 128)
+            tuned = {"group": args.group, "block": 128, "persistent": False}
+        else:
+            tuned = plan.tune_step(Q, phys, dt)
+        group, block = tuned["group"], tuned["block"]
+        shape_persistent[dtype] = tuned["persistent"]
         work = lb.workspace(plan)
         lb.rk_step(plan, Q, dt, warmup, phys, work=work)
         torch.cuda.synchronize()
@@ -459,7 +555,8 @@ def run_ours(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(args.nx), nnz=nnz, mean_neighbours=nnz / N, l2_flush="none: operator data "
                        "0.73 GB > 129 MB L2", parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
-                       launch_shape={"group": shape32[0], "block": shape32[1]}),
+                       launch_shape={"group": shape32[0], "block": shape32[1],
+                                     "persistent": shape_persistent[torch.float32]}),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": "k_stage<float> (fused RHS + RK stage)", "peak_source": peak_kind,
@@ -489,6 +586,8 @@ def run_ours(args, world, rank, local):
     if not args.no_extras:
         result["batch256"] = run_batch(lb, torch, args)
         result["varres_m10"] = run_varres(lb, torch, args)
+        result["adjoint"] = run_adjoint(lb, torch, args)
+        result["fp32_error"] = run_fp32_error(lb, torch, args)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t0 = time.perf_counter()

@@ -208,15 +208,17 @@ int labfm_plan_destroy(labfm_plan* plan);
 int labfm_plan_get_info(const labfm_plan* plan, labfm_plan_info* info);
 
 /*
- * Override the gather launch shape: `group` lanes per node (2, 4, 8, 16 or 32) and
- * `block` threads per block (a multiple of 32 and of group, 64..1024).  The
- * defaults come from labfm_plan_create; labfm_plan_autotune picks the fastest.
+ * Override the launch shape: `group` lanes per node (2, 4, 8, 16 or 32) in every
+ * gather kernel, and `block` threads per block (a multiple of 32 and of group,
+ * 64..1024) for the filter and adjoint kernels; the fused right-hand-side and
+ * stage kernels always run 128-thread blocks.  Defaults: group 4, block 128;
+ * labfm_plan_autotune picks the fastest group.
  */
 int labfm_plan_set_launch(labfm_plan* plan, int group, int block);
 
 /*
- * Time every supported (group, block) pair on this plan with CUDA events
- * (the RHS kernel on `fields`, `reps` launches each) and keep the fastest.
+ * Time every supported group size on this plan with CUDA events (the RHS
+ * kernel on `fields`, `reps` launches each) and keep the fastest.
  * Writes the chosen pair to *group_out / *block_out (host, may be NULL).
  * Synchronises `stream`.
  */

@@ -284,28 +284,33 @@ class Plan:
         _check(lib.labfm_plan_read_profile(self._h, ctypes.byref(pr)))
         return {k: getattr(pr, k) for k, _ in _Profile._fields_}
 
-    def tune_step(self, Q: torch.Tensor, phys: Phys, dt: float, steps: int = 3) -> dict:
-        """Autotune the launch shape (labfm_plan_autotune) and then choose between the
-        plain and the persistent stage kernel by timing `steps` RK steps of each with
-        CUDA events.  Q is not modified.  Returns the chosen configuration."""
-        group, block = self.autotune(Q, phys)
+    def tune_step(self, Q: torch.Tensor, phys: Phys, dt: float, steps: int = 3,
+                  groups=(2, 4, 8, 16)) -> dict:
+        """Autotune the time step itself: time `steps` RK steps (CUDA events) for every
+        lanes-per-node group and for the plain and the persistent stage kernel, keep
+        the fastest.  Q is not modified.  Returns the chosen configuration."""
+        info = self.info()
+        block = info["block"]
         best = None
         for persistent in (False, True):
             self.set_persistent(persistent)
             work = workspace(self)
-            Qs = Q.clone()
-            rk_step(self, Qs, dt, 1, phys, work=work)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            rk_step(self, Qs, dt, steps, phys, work=work)
-            b.record()
-            torch.cuda.synchronize()
-            ms = a.elapsed_time(b) / steps
-            if best is None or ms < best[0]:
-                best = (ms, persistent)
+            for g in groups:
+                self.set_launch(g, block)
+                Qs = Q.clone()
+                rk_step(self, Qs, dt, 1, phys, work=work)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record()
+                rk_step(self, Qs, dt, steps, phys, work=work)
+                b.record()
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b) / steps
+                if best is None or ms < best[0]:
+                    best = (ms, persistent, g)
         self.set_persistent(best[1])
-        return {"group": group, "block": block, "persistent": best[1], "ms_per_step": best[0]}
+        self.set_launch(best[2], block)
+        return {"group": best[2], "block": block, "persistent": best[1], "ms_per_step": best[0]}
 
     def workspace_bytes(self) -> int:
         return int(lib.labfm_rk_workspace_bytes(self._h))

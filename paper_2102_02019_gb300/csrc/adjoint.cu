@@ -251,8 +251,7 @@ __global__ void k_in_degree(PlanView<T> P, int32_t* __restrict__ cnt) {
     for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; i < P.N; i += warps) {
         const int e0 = P.row_ptr[i], e1 = P.row_ptr[i + 1];
         for (int e = e0 + lane; e < e1; e += 32) {
-            const char* rec = reinterpret_cast<const char*>(P.w) + int64_t(e >> 2) * ChunkBytes<T>::rhs;
-            const int k = reinterpret_cast<const int32_t*>(rec)[e & 3];
+            const int k = *reinterpret_cast<const int32_t*>(reinterpret_cast<const char*>(P.w) + Rec<T>::col_e(e));
             if (k != i) atomicAdd(cnt + k, 1);
         }
     }
@@ -274,8 +273,7 @@ __global__ void k_fill_transposed(PlanView<T> P, const int32_t* __restrict__ tro
     for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; i < P.N; i += warps) {
         const int e0 = P.row_ptr[i], e1 = P.row_ptr[i + 1];
         for (int e = e0 + lane; e < e1; e += 32) {
-            const char* rec = reinterpret_cast<const char*>(P.w) + int64_t(e >> 2) * ChunkBytes<T>::rhs;
-            const int k = reinterpret_cast<const int32_t*>(rec)[e & 3];
+            const int k = *reinterpret_cast<const int32_t*>(reinterpret_cast<const char*>(P.w) + Rec<T>::col_e(e));
             if (k == i) continue;
             const int slot = trow[k] + atomicAdd(cursor + k, 1);
             ti[slot] = int32_t(i);
@@ -306,21 +304,19 @@ __global__ void k_write_transposed(PlanView<T> P, int64_t N, const int32_t* __re
                 rank = 0;
                 for (int r = 0; r < len; ++r) rank += ti[t0 + r] < src_i;
                 const int e = te[t0 + q];
-                const char* rec = reinterpret_cast<const char*>(P.w) + int64_t(e >> 2) * ChunkBytes<T>::rhs;
-                const T* wr = reinterpret_cast<const T*>(rec + 16);
+                const char* rb = reinterpret_cast<const char*>(P.w);
 #pragma unroll
-                for (int d = 0; d < 5; ++d) v[d] = wr[4 * d + (e & 3)];
-                const char* frec = reinterpret_cast<const char*>(P.wf) + int64_t(e >> 2) * ChunkBytes<T>::filt;
-                vf = reinterpret_cast<const T*>(frec + 16)[e & 3];
+                for (int d = 0; d < 5; ++d) v[d] = *reinterpret_cast<const T*>(rb + Rec<T>::w_e(e, d));
+                vf = *reinterpret_cast<const T*>(reinterpret_cast<const char*>(P.wf) + Rec<T>::fw_e(e));
             }
             const int64_t dst = int64_t(t0) + rank;
-            char* trec = reinterpret_cast<char*>(tw) + (dst >> 2) * ChunkBytes<T>::rhs;
-            reinterpret_cast<int32_t*>(trec)[dst & 3] = src_i;
+            char* tb = reinterpret_cast<char*>(tw);
+            *reinterpret_cast<int32_t*>(tb + Rec<T>::col_e(dst)) = src_i;
 #pragma unroll
-            for (int d = 0; d < 5; ++d) reinterpret_cast<T*>(trec + 16)[4 * d + (dst & 3)] = v[d];
-            char* tfrec = reinterpret_cast<char*>(twf) + (dst >> 2) * ChunkBytes<T>::filt;
-            reinterpret_cast<int32_t*>(tfrec)[dst & 3] = src_i;
-            reinterpret_cast<T*>(tfrec + 16)[dst & 3] = vf;
+            for (int d = 0; d < 5; ++d) *reinterpret_cast<T*>(tb + Rec<T>::w_e(dst, d)) = v[d];
+            char* tfb = reinterpret_cast<char*>(twf);
+            *reinterpret_cast<int32_t*>(tfb + Rec<T>::fcol_e(dst)) = src_i;
+            *reinterpret_cast<T*>(tfb + Rec<T>::fw_e(dst)) = vf;
         }
     }
 }
@@ -334,12 +330,10 @@ __global__ void k_row_sums(PlanView<T> P, T* __restrict__ rsum) {
         const int e0 = P.row_ptr[i], e1 = P.row_ptr[i + 1];
         double acc[6] = {0, 0, 0, 0, 0, 0};
         for (int e = e0 + lane; e < e1; e += 32) {
-            const char* rec = reinterpret_cast<const char*>(P.w) + int64_t(e >> 2) * ChunkBytes<T>::rhs;
-            const T* wr = reinterpret_cast<const T*>(rec + 16);
+            const char* rb = reinterpret_cast<const char*>(P.w);
 #pragma unroll
-            for (int d = 0; d < 5; ++d) acc[d] += double(wr[4 * d + (e & 3)]);
-            const char* frec = reinterpret_cast<const char*>(P.wf) + int64_t(e >> 2) * ChunkBytes<T>::filt;
-            acc[5] += double(reinterpret_cast<const T*>(frec + 16)[e & 3]);
+            for (int d = 0; d < 5; ++d) acc[d] += double(*reinterpret_cast<const T*>(rb + Rec<T>::w_e(e, d)));
+            acc[5] += double(*reinterpret_cast<const T*>(reinterpret_cast<const char*>(P.wf) + Rec<T>::fw_e(e)));
         }
 #pragma unroll
         for (int d = 0; d < 6; ++d) {
@@ -384,14 +378,14 @@ int build_transposed(labfm_plan* p, cudaStream_t st) {
     if (rc == LABFM_OK) {
         cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&ti), np * 4, st);
         if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&te), np * 4, st);
-        if (e == cudaSuccess) e = cudaMalloc(&p->tw, (np / 4) * ChunkBytes<T>::rhs);
-        if (e == cudaSuccess) e = cudaMalloc(&p->twf, (np / 4) * ChunkBytes<T>::filt);
+        if (e == cudaSuccess) e = cudaMalloc(&p->tw, Rec<T>::rhs_bytes(int64_t(np)));
+        if (e == cudaSuccess) e = cudaMalloc(&p->twf, Rec<T>::filt_bytes(int64_t(np)));
         if (e == cudaSuccess) e = cudaMalloc(&p->rsum, size_t(6) * N * es);
         if (e != cudaSuccess) rc = cuda_error(e, "transposed operator allocation");
     }
     if (rc == LABFM_OK) {
         p->tnnz_pad = tpad;
-        p->device_bytes += (N + 1) * 4 + (np / 4) * (ChunkBytes<T>::rhs + ChunkBytes<T>::filt) + 6 * N * es;
+        p->device_bytes += (N + 1) * 4 + Rec<T>::rhs_bytes(int64_t(np)) + Rec<T>::filt_bytes(int64_t(np)) + 6 * N * es;
         k_fill_transposed<T><<<gw, 256, 0, st>>>(P, p->trow_ptr, cursor, ti, te);
         k_write_transposed<T><<<gw, 256, 0, st>>>(P, N, p->trow_ptr, cnt, ti, te, static_cast<T*>(p->tw),
                                                   static_cast<T*>(p->twf));

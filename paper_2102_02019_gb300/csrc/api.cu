@@ -231,8 +231,9 @@ extern "C" int labfm_plan_autotune(labfm_plan* p, const void* fields, void* scra
     cudaEvent_t e0, e1;
     LABFM_CUDA_TRY(cudaEventCreate(&e0));
     LABFM_CUDA_TRY(cudaEventCreate(&e1));
+    // the gather kernels run fixed 128-thread blocks; the lanes per node are tuned
     const int groups[] = {2, 4, 8, 16, 32};
-    const int blocks[] = {128, 256, 512};
+    const int blocks[] = {p->block};
     float best = 1e30f;
     int bg = p->group, bb = p->block;
     int rc = LABFM_OK;

@@ -72,17 +72,57 @@ __device__ __forceinline__ void load4i(const int32_t* p, int (&o)[K], int off) {
 }
 
 // Operator layout.  0: operator-major streams col[nnz], w[5][nnz], wf[nnz].
-// 1: chunk-interleaved: for every 4-entry chunk of a row, the four columns and
-// the four weights of each of the five RHS operators sit in one contiguous
-// record (96 bytes in F32), and the filter has its own records (col, kappa w^hyp).
+// 1: chunk records: for every 4-entry chunk of a row, its four columns and the
+//    four weights of each of the five RHS operators in one contiguous record
+//    (96 bytes in F32); the filter has its own records (columns, kappa w^hyp).
+// 2: quad-interleaved records: four consecutive chunks form a block stored
+//    component-major (the 4 x 4 columns, then the 4 x 4 weights of each
+//    operator), so that the G lanes of a group, which take consecutive chunks,
+//    read 64 contiguous bytes with every 16-byte load instruction.
 #ifndef LABFM_CHUNK_AOS
-#define LABFM_CHUNK_AOS 1
+#define LABFM_CHUNK_AOS 2
 #endif
 
 template <typename T>
 struct ChunkBytes {
     static constexpr int rhs = 16 + 20 * int(sizeof(T));  // int4 col + 5 x 4 weights
     static constexpr int filt = 16 + 4 * int(sizeof(T));  // int4 col + 4 weights
+};
+
+// Byte offsets of the parts of chunk c (entries 4c .. 4c + 3) in the record
+// streams: its four columns, the four weights of RHS operator d, its four
+// filter columns and filter weights.
+template <typename T>
+struct Rec {
+    static constexpr int64_t W4 = 4 * int64_t(sizeof(T));  // four weights
+#if LABFM_CHUNK_AOS == 2
+    __host__ __device__ static int64_t col(int64_t c) {
+        return (c >> 2) * 4 * ChunkBytes<T>::rhs + (c & 3) * 16;
+    }
+    __host__ __device__ static int64_t w(int64_t c, int d) {
+        return (c >> 2) * 4 * ChunkBytes<T>::rhs + 64 + d * 4 * W4 + (c & 3) * W4;
+    }
+    __host__ __device__ static int64_t fcol(int64_t c) {
+        return (c >> 2) * 4 * ChunkBytes<T>::filt + (c & 3) * 16;
+    }
+    __host__ __device__ static int64_t fw(int64_t c) {
+        return (c >> 2) * 4 * ChunkBytes<T>::filt + 64 + (c & 3) * W4;
+    }
+    static size_t rhs_bytes(int64_t nnz_pad) { return size_t((nnz_pad / 4 + 3) / 4) * 4 * ChunkBytes<T>::rhs; }
+    static size_t filt_bytes(int64_t nnz_pad) { return size_t((nnz_pad / 4 + 3) / 4) * 4 * ChunkBytes<T>::filt; }
+#else
+    __host__ __device__ static int64_t col(int64_t c) { return c * ChunkBytes<T>::rhs; }
+    __host__ __device__ static int64_t w(int64_t c, int d) { return c * ChunkBytes<T>::rhs + 16 + d * W4; }
+    __host__ __device__ static int64_t fcol(int64_t c) { return c * ChunkBytes<T>::filt; }
+    __host__ __device__ static int64_t fw(int64_t c) { return c * ChunkBytes<T>::filt + 16; }
+    static size_t rhs_bytes(int64_t nnz_pad) { return size_t(nnz_pad / 4) * ChunkBytes<T>::rhs; }
+    static size_t filt_bytes(int64_t nnz_pad) { return size_t(nnz_pad / 4) * ChunkBytes<T>::filt; }
+#endif
+    // entry-level accessors (entry e of the padded operator)
+    __host__ __device__ static int64_t col_e(int64_t e) { return col(e >> 2) + 4 * (e & 3); }
+    __host__ __device__ static int64_t w_e(int64_t e, int d) { return w(e >> 2, d) + sizeof(T) * (e & 3); }
+    __host__ __device__ static int64_t fcol_e(int64_t e) { return fcol(e >> 2) + 4 * (e & 3); }
+    __host__ __device__ static int64_t fw_e(int64_t e) { return fw(e >> 2) + sizeof(T) * (e & 3); }
 };
 
 // Node state (ln rho, u, v) packed for one-instruction gathers: float4 for F32
@@ -186,14 +226,14 @@ __device__ __forceinline__ void load_rhs_chunk(const PlanView<T>& P, int e, int 
                                                T (&wx)[K], T (&wy)[K], T (&wxx)[K],
                                                T (&wxy)[K], T (&wyy)[K], int off) {
 #if LABFM_CHUNK_AOS
-    const char* rec = reinterpret_cast<const char*>(P.w) + int64_t(e >> 2) * ChunkBytes<T>::rhs;
-    load4i(reinterpret_cast<const int32_t*>(rec), cj, off);
-    const T* wr = reinterpret_cast<const T*>(rec + 16);
-    load4(wr, wx, off);
-    load4(wr + 4, wy, off);
-    load4(wr + 8, wxx, off);
-    load4(wr + 12, wxy, off);
-    load4(wr + 16, wyy, off);
+    const char* base = reinterpret_cast<const char*>(P.w);
+    const int64_t c = e >> 2;
+    load4i(reinterpret_cast<const int32_t*>(base + Rec<T>::col(c)), cj, off);
+    load4(reinterpret_cast<const T*>(base + Rec<T>::w(c, 0)), wx, off);
+    load4(reinterpret_cast<const T*>(base + Rec<T>::w(c, 1)), wy, off);
+    load4(reinterpret_cast<const T*>(base + Rec<T>::w(c, 2)), wxx, off);
+    load4(reinterpret_cast<const T*>(base + Rec<T>::w(c, 3)), wxy, off);
+    load4(reinterpret_cast<const T*>(base + Rec<T>::w(c, 4)), wyy, off);
 #else
     const int64_t nz = P.nnz_pad;
     load4i(P.col + e, cj, off);
@@ -209,9 +249,10 @@ template <typename T, int K>
 __device__ __forceinline__ void load_filt_chunk(const PlanView<T>& P, int e, int (&cj)[K],
                                                 T (&wf)[K], int off) {
 #if LABFM_CHUNK_AOS
-    const char* rec = reinterpret_cast<const char*>(P.wf) + int64_t(e >> 2) * ChunkBytes<T>::filt;
-    load4i(reinterpret_cast<const int32_t*>(rec), cj, off);
-    load4(reinterpret_cast<const T*>(rec + 16), wf, off);
+    const char* base = reinterpret_cast<const char*>(P.wf);
+    const int64_t c = e >> 2;
+    load4i(reinterpret_cast<const int32_t*>(base + Rec<T>::fcol(c)), cj, off);
+    load4(reinterpret_cast<const T*>(base + Rec<T>::fw(c)), wf, off);
 #else
     load4i(P.col + e, cj, off);
     load4(P.wf + e, wf, off);
