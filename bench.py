@@ -252,6 +252,24 @@ def recorded_traffic(kernel_hash):
     return None
 
 
+def weight_build_flops_per_node(m, nn):
+    """FP64 flops per node of the weight build as implemented: weighted moments
+    (2 (2m+1)(2m+2)/2 per neighbour, plus 2 (2m+1) for the power tables), M from
+    the moments (2 flops per Hermite term of every entry), elimination on the
+    augmented [M | 6] system, back substitution for 6 right-hand sides, and per
+    neighbour the ABF evaluation (Hermite recurrences and n products) and the six
+    length-n dot products."""
+    n = (m * m + 3 * m) // 2
+    ex = [(a, k - a) for k in range(1, m + 1) for a in range(k, -1, -1)]
+    terms = sum((a // 2 + 1) * (b // 2 + 1) for a, b in ex)
+    moments = nn * (2 * (2 * m + 1) * (2 * m + 2) // 2 + 2 * (2 * m + 1))
+    assembly = 2 * n * terms
+    elimination = sum(2 * (n - k - 1) * (n + 5 - k) + (n - k - 1) for k in range(n))
+    back = 12 * n * n / 2
+    weights = nn * (6 * m + 3 * n + 12 * n)
+    return moments + assembly + elimination + back + weights
+
+
 def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
@@ -542,12 +560,7 @@ def run_ours(args, world, rank, local):
     # per node about 45 flops of pointwise RHS and RK update
     flops64 = 27.0 * nnz + 45.0 * N
     fp64_peak = lb.probe_fma_rate(torch.float64)
-    # weight build flops per node: assembly 2 Nn n^2, elimination on [M | 6 columns]
-    # (2/3) n^3 + 6 n^2, back substitution 6 n^2, weights 12 n Nn
-    n_unk = (ns.m * ns.m + 3 * ns.m) // 2
-    nn_mean = nnz / N
-    wb_flops = N * (2 * nn_mean * n_unk ** 2 + (2.0 / 3.0) * n_unk ** 3 + 12 * n_unk ** 2
-                    + 12 * n_unk * nn_mean)
+    wb_flops = N * weight_build_flops_per_node(ns.m, nnz / N)
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -110,7 +110,9 @@ int labfm_build_stencils(const double* xy, const double* h, int64_t N, double Lx
  *   X~_ji = X_ji . H_i  (monomials (x/h)^a (y/h)^b / (a! b!), eq. X and vector H)
  *   W^q_ji = psi(|r_ji|/h_i) H_a(x_ji/(h_i sqrt2)) H_b(y_ji/(h_i sqrt2)) / sqrt(2^(a+b))
  *            (eq. hermite; psi = Wendland C2, (1 - q/2)^4 (1 + 2q) on q <= 2)
- *   M_i = sum_j X~_ji (x) W_ji                              (eq. disc_form)
+ *   M_i = sum_j X~_ji (x) W_ji                              (eq. disc_form;
+ *         assembled from the weighted moments sum_j psi (x/h)^p (y/h)^q, p + q <= 2m,
+ *         since W = psi He_a(x/h) He_b(y/h) with probabilists' Hermite He_a)
  *   M_i Psi^d = C~^d by LU with partial pivoting           (eq. lsys)
  *   w^d_ji = W_ji . Psi^d                                   (eq. w_abf)
  *   F_0,i = sum_j phi_ji w^hyp_ji, kappa_i = 2 / (3 F_0,i)   (Section 6)

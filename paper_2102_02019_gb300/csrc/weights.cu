@@ -1,12 +1,17 @@
 // Batched FP64 weight build (Sections 2, 3 and 6 of the paper).
 //
-// One CTA per node.  For each chunk of 32 neighbours, warp 0 evaluates the
-// scaled monomials X~_ji and the Hermite ABFs W_ji into shared memory; every
-// thread owns a TILE x TILE block of the moment matrix M_i = sum_j X~_ji (x) W_ji
-// in registers.  M_i, augmented with the six scaled selectors C~^d, is then
-// reduced by Gaussian elimination with partial pivoting (the first row holding
-// the largest |pivot| wins) and back substitution; finally every thread takes
-// neighbours j and forms w^d_ji = W_ji . Psi^d and the filter sum F_0,i.
+// One CTA per node.  The moment matrix M_i = sum_j X~_ji (x) W_ji (eq. disc_form)
+// is assembled from weighted moments instead of neighbour by neighbour: every
+// entry X~^r_ji W^c_ji is psi_j times a polynomial in (x/h, y/h), because
+// W^c = psi He_a(x/h) He_b(y/h) with the probabilists' Hermite polynomials
+// He_a(z) = 2^(-a/2) H_a(z / sqrt 2) (eq. hermite).  So
+//   M[r][c] = 1/(a_r! b_r!) sum_{k,l} he_{a_c,k} he_{b_c,l} mu_{a_r+k, b_r+l},
+//   mu_{p,q} = sum_j psi_j (x_ji/h)^p (y_ji/h)^q,  p + q <= 2m,
+// which needs (2m+1)(2m+2)/2 moment sums per neighbour instead of n^2 products
+// (153 vs 1936 at m = 8).  M_i, augmented with the six scaled selectors C~^d, is
+// then reduced by Gaussian elimination with partial pivoting (the first row
+// holding the largest |pivot| wins) and back substitution; finally every thread
+// takes neighbours j and forms w^d_ji = W_ji . Psi^d and the filter sum F_0,i.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -21,13 +26,12 @@ namespace {
 template <int M>
 struct WCfg {
     static constexpr int n = (M * M + 3 * M) / 2;
-    static constexpr int TILE = n <= 5 ? 1 : (n <= 14 ? 2 : (n <= 27 ? 3 : (n <= 44 ? 4 : 5)));
-    static constexpr int TPD = (n + TILE - 1) / TILE;  // tiles per dimension
-    static constexpr int NP = TPD * TILE;              // padded row length of the chunk buffers
-    static constexpr int NT = ((TPD * TPD + 31) / 32) * 32;
-    static constexpr int KCH = 32;                     // neighbours per chunk
+    // threads per node: 32 / 64 / 96 / 128 / 192 for m = 2 / 4 / 6 / 8 / 10
+    static constexpr int NT = M <= 2 ? 32 : (M <= 4 ? 64 : (M <= 6 ? 96 : (M <= 8 ? 128 : 192)));
     static constexpr int LDA = n + 6;                  // augmented row length
-    static constexpr size_t chunk_bytes = size_t(2) * KCH * NP * sizeof(double);
+    static constexpr int NPOW = 2 * M + 1;                    // powers 0..2M
+    static constexpr int NMOM = (2 * M + 1) * (2 * M + 2) / 2;  // moments p + q <= 2M
+    static constexpr size_t chunk_bytes = size_t(2) * NT * NPOW * sizeof(double);
     static constexpr size_t lu_bytes(bool resid) {
         return (size_t(n) * LDA + (resid ? size_t(n) * n : 0)) * sizeof(double);
     }
@@ -98,37 +102,21 @@ __device__ __forceinline__ void neighbour_factors(const double* __restrict__ xy,
     }
 }
 
-__device__ __forceinline__ double inv_factorial(int k) {
-    constexpr double f[11] = {1.0, 1.0, 2.0, 6.0, 24.0, 120.0, 720.0, 5040.0, 40320.0,
-                              362880.0, 3628800.0};
-    return 1.0 / f[k];
-}
+// 1/k! and 1/sqrt(2^k) tables in constant memory (indexed at run time).
+__constant__ double c_inv_fact[11] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0,
+                                      1.0 / 720.0, 1.0 / 5040.0, 1.0 / 40320.0, 1.0 / 362880.0,
+                                      1.0 / 3628800.0};
+__constant__ double c_inv_sqrt2_pow[21] = {
+    1.0, 0.70710678118654752440, 0.5, 0.35355339059327376220, 0.25, 0.17677669529663688110,
+    0.125, 0.088388347648318440550, 0.0625, 0.044194173824159220275, 0.03125,
+    0.022097086912079610138, 0.015625, 0.011048543456039805069, 0.0078125,
+    0.0055242717280199025344, 0.00390625, 0.0027621358640099512672, 0.001953125,
+    0.0013810679320049756336, 0.0009765625};
+
+__device__ __forceinline__ double inv_factorial(int k) { return c_inv_fact[k]; }
 
 // 1 / sqrt(2^k)
-__device__ __forceinline__ double inv_sqrt2_pow(int k) {
-    constexpr double v[21] = {1.0,
-                              0.70710678118654752440,
-                              0.5,
-                              0.35355339059327376220,
-                              0.25,
-                              0.17677669529663688110,
-                              0.125,
-                              0.088388347648318440550,
-                              0.0625,
-                              0.044194173824159220275,
-                              0.03125,
-                              0.022097086912079610138,
-                              0.015625,
-                              0.011048543456039805069,
-                              0.0078125,
-                              0.0055242717280199025344,
-                              0.00390625,
-                              0.0027621358640099512672,
-                              0.001953125,
-                              0.0013810679320049756336,
-                              0.0009765625};
-    return v[k];
-}
+__device__ __forceinline__ double inv_sqrt2_pow(int k) { return c_inv_sqrt2_pow[k]; }
 
 // Selector entry C~^d_q / h^-deg for op d at monomial (a, b) (Section 2 and,
 // for d = 5, the expansion of (d_xx + d_yy)^{M/2} from Section 6).
@@ -162,17 +150,11 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
                    int32_t* __restrict__ node_status, unsigned long long* __restrict__ n_failed) {
     using C = WCfg<M>;
     constexpr int n = C::n;
-    constexpr int TILE = C::TILE;
-    constexpr int TPD = C::TPD;
-    constexpr int NP = C::NP;
     constexpr int NT = C::NT;
-    constexpr int KCH = C::KCH;
     constexpr int LDA = C::LDA;
 
     extern __shared__ double smem[];
-    double* Xs = smem;             // [KCH][NP]
-    double* Ws = smem + KCH * NP;  // [KCH][NP]
-    double* A = smem;              // [n][LDA], aliases the chunk buffers after assembly
+    double* A = smem;              // [n][LDA], aliases the moment buffers after assembly
     double* A0 = smem + n * LDA;   // [n][n] copy of M for the residual
     __shared__ int s_piv;
     __shared__ int s_flags;
@@ -201,74 +183,87 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
         return;
     }
 
-    // ---- assembly of M_i = sum_j X~_j (x) W_j
-    const int tr = t / TPD;
-    const int tc = t - tr * TPD;
-    const bool owner = t < TPD * TPD;
-    double acc[TILE][TILE];
-#pragma unroll
-    for (int r = 0; r < TILE; ++r)
-#pragma unroll
-        for (int c = 0; c < TILE; ++c) acc[r][c] = 0.0;
-
-    for (int c0 = r0; c0 < r1; c0 += KCH) {
-        const int cnt = min(KCH, r1 - c0);
-        if (warp == 0) {
-            double* xr = Xs + lane * NP;
-            double* wr = Ws + lane * NP;
-            if (lane < cnt) {
-                double pxv[M + 1], pyv[M + 1], hxv[M + 1], hyv[M + 1], psi, dx, dy;
-                neighbour_factors<M>(xy, col[c0 + lane], g, pxv, pyv, hxv, hyv, &psi, &dx, &dy);
-                int q = 0;
-#pragma unroll
-                for (int k = 1; k <= M; ++k) {
-#pragma unroll
-                    for (int a = k; a >= 0; --a, ++q) {
-                        const int b = k - a;
-                        xr[q] = (pxv[a] * pyv[b]) * (inv_factorial(a) * inv_factorial(b));
-                        wr[q] = psi * hxv[a] * hyv[b] * inv_sqrt2_pow(k);
-                    }
-                }
-            } else {
-                for (int q = 0; q < n; ++q) {
-                    xr[q] = 0.0;
-                    wr[q] = 0.0;
-                }
+    // ---- weighted moments mu_{p,q} = sum_j psi_j xh^p yh^q, p + q <= 2M
+    constexpr int NPOW = C::NPOW;
+    constexpr int NMOM = C::NMOM;
+    constexpr int MPT = (NMOM + NT - 1) / NT;  // moments per thread
+    double* XP = smem;              // [NT][NPOW]: psi xh^p
+    double* YP = smem + NT * NPOW;  // [NT][NPOW]: yh^q
+    __shared__ double s_mu[NMOM];
+    __shared__ double s_he[(M + 1) * (M + 1)];  // he[a][k]: coefficient of z^k in He_a
+    if (t == 0) {
+        for (int k = 0; k < (M + 1) * (M + 1); ++k) s_he[k] = 0.0;
+        s_he[0] = 1.0;
+        if (M >= 1) s_he[(M + 1) + 1] = 1.0;
+        for (int a = 1; a < M; ++a)  // He_{a+1} = z He_a - a He_{a-1}
+            for (int k = 0; k <= a + 1; ++k) {
+                const double up = k > 0 ? s_he[a * (M + 1) + k - 1] : 0.0;
+                s_he[(a + 1) * (M + 1) + k] = up - double(a) * s_he[(a - 1) * (M + 1) + k];
             }
-            for (int q = n; q < NP; ++q) {
-                xr[q] = 0.0;
-                wr[q] = 0.0;
+    }
+    int mp[MPT], mq[MPT];
+    double macc[MPT];
+#pragma unroll
+    for (int u = 0; u < MPT; ++u) {
+        macc[u] = 0.0;
+        const int idx = t + u * NT;
+        int d = 0;
+        while (idx >= (d + 1) * (d + 2) / 2 && d < 2 * M) ++d;
+        mp[u] = d - (idx - d * (d + 1) / 2);
+        mq[u] = d - mp[u];
+    }
+    for (int c0 = r0; c0 < r1; c0 += NT) {
+        const int cnt = min(NT, r1 - c0);
+        if (t < cnt) {
+            const int j = col[c0 + t];
+            const double dx = min_image(__dsub_rn(xy[2 * j], g.xi), g.Lx, g.px);
+            const double dy = min_image(__dsub_rn(xy[2 * j + 1], g.yi), g.Ly, g.py);
+            const double xh = dx / g.hi;
+            const double yh = dy / g.hi;
+            double xp = wendland_c2(sqrt(dx * dx + dy * dy) / g.hi), yp = 1.0;
+            double* xr = XP + t * NPOW;
+            double* yr = YP + t * NPOW;
+#pragma unroll
+            for (int p = 0; p < NPOW; ++p) {
+                xr[p] = xp;
+                yr[p] = yp;
+                xp *= xh;
+                yp *= yh;
             }
         }
         __syncthreads();
-        if (owner) {
-            for (int k = 0; k < cnt; ++k) {
-                double xv[TILE], wv[TILE];
 #pragma unroll
-                for (int r = 0; r < TILE; ++r) xv[r] = Xs[k * NP + tr * TILE + r];
-#pragma unroll
-                for (int c = 0; c < TILE; ++c) wv[c] = Ws[k * NP + tc * TILE + c];
-#pragma unroll
-                for (int r = 0; r < TILE; ++r)
-#pragma unroll
-                    for (int c = 0; c < TILE; ++c) acc[r][c] = fma(xv[r], wv[c], acc[r][c]);
+        for (int u = 0; u < MPT; ++u) {
+            if (t + u * NT < NMOM) {
+                double acc = macc[u];
+                for (int k = 0; k < cnt; ++k) acc = fma(XP[k * NPOW + mp[u]], YP[k * NPOW + mq[u]], acc);
+                macc[u] = acc;
             }
         }
         __syncthreads();
     }
+#pragma unroll
+    for (int u = 0; u < MPT; ++u)
+        if (t + u * NT < NMOM) s_mu[t + u * NT] = macc[u];
+    __syncthreads();
 
-    // ---- augmented system [M | C~]
-    if (owner) {
-#pragma unroll
-        for (int r = 0; r < TILE; ++r)
-#pragma unroll
-            for (int c = 0; c < TILE; ++c) {
-                const int rr = tr * TILE + r, cc = tc * TILE + c;
-                if (rr < n && cc < n) {
-                    A[rr * LDA + cc] = acc[r][c];
-                    if (RESID) A0[rr * n + cc] = acc[r][c];
-                }
+    // ---- M_i from the moments, into the augmented system [M | C~]
+    for (int idx = t; idx < n * n; idx += NT) {
+        const int r = idx / n, c = idx - r * n;
+        int ar, br, ac, bc;
+        exps_of(r, ar, br);
+        exps_of(c, ac, bc);
+        double sum = 0.0;
+        for (int k = ac; k >= 0; k -= 2) {
+            const double hk = s_he[ac * (M + 1) + k];
+            for (int l = bc; l >= 0; l -= 2) {
+                const int pp = ar + k, qq = br + l, dd = pp + qq;
+                sum = fma(hk * s_he[bc * (M + 1) + l], s_mu[dd * (dd + 1) / 2 + (dd - pp)], sum);
             }
+        }
+        const double v = sum * (inv_factorial(ar) * inv_factorial(br));
+        A[r * LDA + c] = v;
+        if (RESID) A0[r * n + c] = v;
     }
     for (int idx = t; idx < n * 6; idx += NT) {
         const int q = idx / 6, d = idx - q * 6;
