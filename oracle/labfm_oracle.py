@@ -537,3 +537,75 @@ def kinetic_energy_grad(q, s):
     rho = np.exp(a)
     V = s * s
     return np.stack([0.5 * rho * (u * u + v * v) * V, rho * u * V, rho * v * V])
+
+
+# --------------------------------------------------------------------------
+# Sections 3 and 4: modal (amplitude) response and stencil optimisation
+# --------------------------------------------------------------------------
+
+def amplitude_response(dx, dy, s_i, wx, wy, wl, nk=16):
+    """A^x, A^y, A^L of one node's operators at k = k_Ny n / nk, n = 1..nk, k_Ny = pi / s_i
+    (Section 4, step 3): A^x = L^x(sin k x_ji) / k, A^y = L^y(sin k y_ji) / k,
+    A^L = L^L(0.5 - 0.5 cos k x_ji cos k y_ji) / k^2."""
+    ks = np.pi / s_i * np.arange(1, nk + 1) / nk
+    Ax = np.array([np.sum(np.sin(k * dx) * wx) / k for k in ks])
+    Ay = np.array([np.sum(np.sin(k * dy) * wy) / k for k in ks])
+    AL = np.array([np.sum((0.5 - 0.5 * np.cos(k * dx) * np.cos(k * dy)) * wl) / (k * k) for k in ks])
+    return Ax, Ay, AL
+
+
+def modal_response(xy, s, row_ptr, col, w, Lx, Ly, nk=16, periodic=(True, True)):
+    """Per node amplitude responses (N, 3, nk) of d/dx, d/dy and the Laplacian (Section 3)."""
+    N = len(row_ptr) - 1
+    out = np.zeros((N, 3, nk))
+    for i in range(N):
+        sl = slice(row_ptr[i], row_ptr[i + 1])
+        dx, dy = offsets(xy, np.full(row_ptr[i + 1] - row_ptr[i], i), col[sl], Lx, Ly, periodic)
+        out[i] = amplitude_response(dx, dy, s[i], w[0][sl], w[1][sl], w[2][sl] + w[4][sl], nk)
+    return out
+
+
+def laplacian_residual(M, psi_L, C_L, h):
+    """alpha_L = || M Psi^L - C~^L ||_2 in the nondimensional form of the h-scaled
+    system (each entry times h^2, so that C^L has unit entries)."""
+    return float(np.linalg.norm((M @ psi_L - C_L) * h * h))
+
+
+def optimise_stencil_node(xy, s, i, cand, m, Lx, Ly, h0, nk=16, factor=0.99, amp_max=1.01,
+                          periodic=(True, True), max_iter=400):
+    """Section 4: starting from h0, while the Laplacian residual alpha_L <= alpha_0 =
+    1e-4 eps n^4 / (h m) and max(A^x, A^y, A^L) <= amp_max over nk wavenumbers up to
+    Nyquist, shrink h by `factor`.  Returns (the last h that passed both tests, or h0
+    if none did; number of systems solved).  cand: the stencil of node i at h0."""
+    n = n_unknowns(m)
+    eps = np.finfo(np.float64).eps
+    dx0, dy0 = offsets(xy, np.full(len(cand), i), cand, Lx, Ly, periodic)
+    r2 = dx0 * dx0 + dy0 * dy0
+    hi = h0
+    best = h0
+    solves = 0
+    for _ in range(max_iter):
+        two_h = 2.0 * hi
+        keep = r2 <= two_h * two_h
+        if keep.sum() < n:
+            break
+        dx, dy = dx0[keep], dy0[keep]
+        Xt = scaled_monomials(dx, dy, hi, m)
+        W = abf_matrix(dx, dy, hi, m)
+        M = Xt.T @ W
+        C = np.stack([selector("x", m, hi), selector("y", m, hi), selector("L", m, hi)], axis=1)
+        Psi, ok = lu_solve(M[None], C[None])
+        solves += 1
+        if not ok[0]:
+            break
+        alpha = laplacian_residual(M, Psi[0][:, 2], C[:, 2], hi)
+        alpha0 = 1e-4 * eps * n ** 4 / (hi * m)
+        if alpha > alpha0:
+            break
+        wts = W @ Psi[0]
+        Ax, Ay, AL = amplitude_response(dx, dy, s[i], wts[:, 0], wts[:, 1], wts[:, 2], nk)
+        if max(Ax.max(), Ay.max(), AL.max()) > amp_max:
+            break
+        best = hi
+        hi = hi * factor
+    return best, solves
