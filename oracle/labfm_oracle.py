@@ -572,11 +572,12 @@ def laplacian_residual(M, psi_L, C_L, h):
 
 
 def optimise_stencil_node(xy, s, i, cand, m, Lx, Ly, h0, nk=16, factor=0.99, amp_max=1.01,
-                          periodic=(True, True), max_iter=400):
+                          periodic=(True, True), max_iter=400, resid_coef=1e-4):
     """Section 4: starting from h0, while the Laplacian residual alpha_L <= alpha_0 =
-    1e-4 eps n^4 / (h m) and max(A^x, A^y, A^L) <= amp_max over nk wavenumbers up to
-    Nyquist, shrink h by `factor`.  Returns (the last h that passed both tests, or h0
-    if none did; number of systems solved).  cand: the stencil of node i at h0."""
+    resid_coef eps n^4 / (h m) (resid_coef = 1e-4 in the paper; inf switches the test
+    off) and max(A^x, A^y, A^L) <= amp_max over nk wavenumbers up to Nyquist, shrink
+    h by `factor`.  Returns (the last h that passed both tests, or h0 if none did;
+    number of systems solved).  cand: the stencil of node i at h0."""
     n = n_unknowns(m)
     eps = np.finfo(np.float64).eps
     dx0, dy0 = offsets(xy, np.full(len(cand), i), cand, Lx, Ly, periodic)
@@ -599,7 +600,7 @@ def optimise_stencil_node(xy, s, i, cand, m, Lx, Ly, h0, nk=16, factor=0.99, amp
         if not ok[0]:
             break
         alpha = laplacian_residual(M, Psi[0][:, 2], C[:, 2], hi)
-        alpha0 = 1e-4 * eps * n ** 4 / (hi * m)
+        alpha0 = resid_coef * eps * n ** 4 / (hi * m)
         if alpha > alpha0:
             break
         wts = W @ Psi[0]

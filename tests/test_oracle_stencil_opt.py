@@ -107,3 +107,25 @@ def test_sixth_order_optimised_stencils_match_the_paper():
         cand = o.neighbours_of(ns.xy, h0, i, ns.Lx, ns.Ly)
         hs.append(o.optimise_stencil_node(ns.xy, ns.s, i, cand, 6, ns.Lx, ns.Ly, h0[i])[0] / ns.s[i])
     assert 1.4 <= np.mean(hs) <= 1.9, np.mean(hs)
+
+
+def test_amplitude_only_optimisation_is_solver_independent():
+    """With the residual test off (resid_coef = inf) the loop stops on the node count
+    or on a response against 1.01, so the oracle's LU and LAPACK agree exactly."""
+    ns = li.tgv_lattice(96, 80, m=4, h_over_s=2.8, jitter=0.3, seed=64)
+    h0 = 2.8 * ns.s
+    rows = np.random.default_rng(4).choice(ns.N, 8, replace=False)
+    lapack = lambda M, C: (np.linalg.solve(M, C), np.ones(M.shape[0], dtype=bool))
+    for i in rows:
+        cand = o.neighbours_of(ns.xy, h0, i, ns.Lx, ns.Ly)
+        ha, na = o.optimise_stencil_node(ns.xy, ns.s, i, cand, 4, ns.Lx, ns.Ly, h0[i],
+                                         resid_coef=math.inf)
+        orig = o.lu_solve
+        try:
+            o.lu_solve = lapack
+            hb, nb = o.optimise_stencil_node(ns.xy, ns.s, i, cand, 4, ns.Lx, ns.Ly, h0[i],
+                                             resid_coef=math.inf)
+        finally:
+            o.lu_solve = orig
+        assert ha == hb and na == nb
+        assert ha < h0[i]
