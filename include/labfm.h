@@ -139,6 +139,65 @@ int labfm_build_weights(const double* xy, const double* h, const double* s, int6
                         int64_t* n_failed_out, void* stream);
 
 /*
+ * Stencil optimisation (Section 4), FP64.  For every node i, starting from
+ * h = h0_i and the stencil of labfm_build_stencils at h0_i, repeat:
+ *   1. stop if fewer than n = (m^2 + 3m)/2 stencil nodes lie within |r_ji| <= 2h;
+ *   2. build M_i at h (as labfm_build_weights) and solve for Psi^x, Psi^y and
+ *      Psi^L (selector C~^L = C~^xx + C~^yy); stop if M_i is singular;
+ *   3. stop if alpha_L = || (M_i Psi^L - C~^L) h^2 ||_2 > alpha_0 =
+ *      resid_coef eps n^4 / (h m), eps = 2^-52 (Laplacian residual test; the
+ *      paper's resid_coef is 1e-4);
+ *   4. stop if the largest amplitude response of d/dx, d/dy or the Laplacian
+ *      exceeds amp_max at any of the 16 wavenumbers k_n = (pi/s_i) n/16,
+ *      n = 1..16, where A^x = sum_j w^x_ji sin(k x_ji) / k,
+ *      A^y = sum_j w^y_ji sin(k y_ji) / k and
+ *      A^L = sum_j w^L_ji (1/2 - cos(k x_ji) cos(k y_ji) / 2) / k^2;
+ *   5. record h as passing and set h <- factor h.
+ * The output is the last h that passed every test (h0_i if none did).  The
+ * paper's values are factor = 0.99 and amp_max = 1.01 (a response at most 1 %
+ * above the exact one).  alpha_L is a rounding-level quantity, so near alpha_0
+ * the outcome of test 3 depends on the order of the floating-point operations:
+ * two correct solvers can stop a few factors apart on the same node.
+ * resid_coef = +inf switches test 3 off.
+ *
+ *   xy, h0, s  device, N x 2 / N / N doubles
+ *   row_ptr, col device CSR from labfm_build_stencils at h0 (candidates)
+ *   m          order, even, 2 <= m <= 10
+ *   factor     shrink factor in (0, 1); amp_max: response bound;
+ *              resid_coef: > 0 (may be +inf)
+ *   max_iter   host, iteration limit per node (>= 0)
+ *   h_out      device, N doubles (output)
+ *   solves_out device, N int32 (output, may be NULL): systems solved per node
+ * One CTA per node; no allocation, no synchronisation.
+ * Errors: EINVAL (null pointers, N, m, factor, max_iter).
+ */
+int labfm_stencil_optimise(const double* xy, const double* h0, const double* s, int64_t N,
+                           double Lx, double Ly, uint32_t periodic_mask,
+                           const int32_t* row_ptr, const int32_t* col, int m, double factor,
+                           double amp_max, double resid_coef, int max_iter, double* h_out,
+                           int32_t* solves_out, void* stream);
+
+/*
+ * Modal (amplitude) response of built operators (Section 3): per node i and
+ * wavenumber k_n = (pi/s_i) n/nk, n = 1..nk,
+ *   out[(i * 3 + 0) * nk + n - 1] = sum_j w^x_ji sin(k x_ji) / k
+ *   out[(i * 3 + 1) * nk + n - 1] = sum_j w^y_ji sin(k y_ji) / k
+ *   out[(i * 3 + 2) * nk + n - 1] = sum_j (w^xx_ji + w^yy_ji)
+ *                                   (1/2 - cos(k x_ji) cos(k y_ji) / 2) / k^2
+ * (1 for an exact operator on a mode that the node spacing resolves).
+ *
+ *   xy, s        device, N x 2 / N doubles
+ *   row_ptr, col device CSR (nnz entries); w: device, 6 x nnz doubles from
+ *                labfm_build_weights
+ *   nk           wavenumbers per node, 1 <= nk <= 4096
+ *   out          device, N x 3 x nk doubles (output)
+ * Errors: EINVAL (null pointers, N, nk).
+ */
+int labfm_modal_response(const double* xy, const double* s, int64_t N, double Lx, double Ly,
+                         uint32_t periodic_mask, const int32_t* row_ptr, const int32_t* col,
+                         int64_t nnz, const double* w, int nk, double* out, void* stream);
+
+/*
  * Prepare an operator for the time-step kernels: rows padded to a multiple of
  * four entries (pad entries point at the node itself with weight 0, which adds
  * exactly zero in the difference form of eq. general_do); every 4-entry chunk

@@ -70,6 +70,10 @@ _SIGS = {
                                     ctypes.POINTER(_I64), _P]),
     "labfm_build_weights": (_I32, [_P, _P, _P, _I64, _D, _D, ctypes.c_uint32, _P, _P, _I64, _I32,
                                    _P, _P, _P, _P, ctypes.POINTER(_I64), _P]),
+    "labfm_stencil_optimise": (_I32, [_P, _P, _P, _I64, _D, _D, ctypes.c_uint32, _P, _P, _I32, _D, _D,
+                                      _D, _I32, _P, _P, _P]),
+    "labfm_modal_response": (_I32, [_P, _P, _I64, _D, _D, ctypes.c_uint32, _P, _P, _I64, _P, _I32, _P,
+                                    _P]),
     "labfm_plan_create": (_I32, [ctypes.POINTER(_P), _I64, _I64, _I32, _P, _P, _P, _P, _P, _P]),
     "labfm_plan_destroy": (_I32, [_P]),
     "labfm_plan_get_info": (_I32, [_P, ctypes.POINTER(_PlanInfo)]),
@@ -193,6 +197,35 @@ def build_weights(xy, h, s, Lx, Ly, row_ptr, col, m, periodic=(True, True), resi
     _check(rc)
     return {"w": w[:, :nnz] if nnz else w[:, :0], "kappa": kappa, "status": status,
             "residual": res, "n_failed": nf.value if check else None}
+
+
+def stencil_optimise(xy, h0, s, Lx, Ly, row_ptr, col, m, factor=0.99, amp_max=1.01, resid_coef=1e-4,
+                     max_iter=400, periodic=(True, True), stream=None):
+    """labfm_stencil_optimise: per-node optimised h (Section 4) and the number of systems
+    solved per node, as (h, solves) device tensors.  resid_coef=math.inf switches the
+    Laplacian-residual test off."""
+    N = xy.shape[0]
+    mask = (1 if periodic[0] else 0) | (2 if periodic[1] else 0)
+    h = torch.empty(N, dtype=torch.float64, device=xy.device)
+    solves = torch.empty(N, dtype=torch.int32, device=xy.device)
+    _check(lib.labfm_stencil_optimise(_ptr(xy), _ptr(h0), _ptr(s), N, Lx, Ly, mask, _ptr(row_ptr),
+                                      _ptr(col), m, factor, amp_max, resid_coef, max_iter, _ptr(h), _ptr(solves),
+                                      _stream(stream)))
+    return h, solves
+
+
+def modal_response(xy, s, Lx, Ly, row_ptr, col, w, nk=16, periodic=(True, True), stream=None):
+    """labfm_modal_response: (N, 3, nk) amplitude responses of d/dx, d/dy and the
+    Laplacian of FP64 weights w (6, nnz) (Section 3)."""
+    N = xy.shape[0]
+    nnz = col.numel()
+    mask = (1 if periodic[0] else 0) | (2 if periodic[1] else 0)
+    w = w.contiguous()
+    out = torch.empty((N, 3, nk), dtype=torch.float64, device=xy.device)
+    _check(lib.labfm_modal_response(_ptr(xy), _ptr(s), N, Lx, Ly, mask, _ptr(row_ptr),
+                                    _ptr(col) if nnz else None, nnz, _ptr(w), nk, _ptr(out),
+                                    _stream(stream)))
+    return out
 
 
 class Plan:

@@ -16,6 +16,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 
 #include "labfm_internal.cuh"
@@ -141,66 +142,36 @@ __device__ __forceinline__ double selector_coef(int d, int a, int b) {
 
 __device__ __forceinline__ int op_order(int d, int M) { return d < 2 ? 1 : (d < 5 ? 2 : M); }
 
-template <int M, bool RESID>
-__global__ void __launch_bounds__(WCfg<M>::NT)
-    k_weight_build(const double* __restrict__ xy, const double* __restrict__ h,
-                   const double* __restrict__ s, int64_t N, double Lx, double Ly, int px_, int py_,
-                   const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t nnz,
-                   double* __restrict__ w, double* __restrict__ kappa, double* __restrict__ residual,
-                   int32_t* __restrict__ node_status, unsigned long long* __restrict__ n_failed) {
-    using C = WCfg<M>;
-    constexpr int n = C::n;
-    constexpr int NT = C::NT;
-    constexpr int LDA = C::LDA;
+// ---------------------------------------------------------------- block-level building blocks
+// (one CTA of NT threads per node; every function is called by all threads)
 
-    extern __shared__ double smem[];
-    double* A = smem;              // [n][LDA], aliases the moment buffers after assembly
-    double* A0 = smem + n * LDA;   // [n][n] copy of M for the residual
-    __shared__ int s_piv;
-    __shared__ int s_flags;
-    __shared__ double s_red[NT / 32];
-
-    const int64_t i = blockIdx.x;
-    if (i >= N) return;
-    const int t = threadIdx.x;
-    const int lane = t & 31;
-    const int warp = t >> 5;
-    NodeGeom g{xy[2 * i], xy[2 * i + 1], h[i], Lx, Ly, px_ != 0, py_ != 0};
-    const int r0 = row_ptr[i];
-    const int r1 = row_ptr[i + 1];
-    const int nn = r1 - r0;
-    if (t == 0) s_flags = 0;
-
-    if (nn < n) {  // M_i singular: fewer stencil nodes than unknowns
-        for (int e = r0 + t; e < r1; e += NT)
-            for (int d = 0; d < 6; ++d) w[int64_t(d) * nnz + e] = 0.0;
-        if (t == 0) {
-            kappa[i] = 0.0;
-            if (RESID) residual[i] = INFINITY;
-            node_status[i] = LABFM_NODE_FEW_NEIGHBOURS;
-            if (n_failed) atomicAdd(n_failed, 1ull);
-        }
-        return;
-    }
-
-    // ---- weighted moments mu_{p,q} = sum_j psi_j xh^p yh^q, p + q <= 2M
-    constexpr int NPOW = C::NPOW;
-    constexpr int NMOM = C::NMOM;
-    constexpr int MPT = (NMOM + NT - 1) / NT;  // moments per thread
-    double* XP = smem;              // [NT][NPOW]: psi xh^p
-    double* YP = smem + NT * NPOW;  // [NT][NPOW]: yh^q
-    __shared__ double s_mu[NMOM];
-    __shared__ double s_he[(M + 1) * (M + 1)];  // he[a][k]: coefficient of z^k in He_a
-    if (t == 0) {
+// he[a][k]: coefficient of z^k in the probabilists' Hermite polynomial He_a
+// (He_0 = 1, He_1 = z, He_{a+1} = z He_a - a He_{a-1}); integers, exact in FP64.
+template <int M>
+__device__ void build_he(double* s_he) {
+    if (threadIdx.x == 0) {
         for (int k = 0; k < (M + 1) * (M + 1); ++k) s_he[k] = 0.0;
         s_he[0] = 1.0;
         if (M >= 1) s_he[(M + 1) + 1] = 1.0;
-        for (int a = 1; a < M; ++a)  // He_{a+1} = z He_a - a He_{a-1}
+        for (int a = 1; a < M; ++a)
             for (int k = 0; k <= a + 1; ++k) {
                 const double up = k > 0 ? s_he[a * (M + 1) + k - 1] : 0.0;
                 s_he[(a + 1) * (M + 1) + k] = up - double(a) * s_he[(a - 1) * (M + 1) + k];
             }
     }
+}
+
+// Weighted moments mu_{p,q} = sum_j psi_j (x_ji/h)^p (y_ji/h)^q, p + q <= 2M, over
+// the candidate neighbours col[r0 .. r1) with stencil scale g.hi (candidates
+// beyond 2h have psi = 0 and add nothing).  XP, YP: 2 NT (2M+1) doubles of
+// scratch; s_mu: (2M+1)(2M+2)/2 doubles.  Ends with a barrier.
+template <int M>
+__device__ void block_moments(const double* __restrict__ xy, const int32_t* __restrict__ col, int r0,
+                              int r1, const NodeGeom& g, double* XP, double* YP, double* s_mu) {
+    using C = WCfg<M>;
+    constexpr int NT = C::NT, NPOW = C::NPOW, NMOM = C::NMOM;
+    constexpr int MPT = (NMOM + NT - 1) / NT;  // moments per thread
+    const int t = threadIdx.x;
     int mp[MPT], mq[MPT];
     double macc[MPT];
 #pragma unroll
@@ -246,9 +217,15 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
     for (int u = 0; u < MPT; ++u)
         if (t + u * NT < NMOM) s_mu[t + u * NT] = macc[u];
     __syncthreads();
+}
 
-    // ---- M_i from the moments, into the augmented system [M | C~]
-    for (int idx = t; idx < n * n; idx += NT) {
+// M_i[r][c] = 1/(a_r! b_r!) sum_{k,l} he_{a_c,k} he_{b_c,l} mu_{a_r+k, b_r+l} into
+// A (row stride LDA) and, when A0 is not null, a copy with stride n.  No barrier.
+template <int M, int LDA>
+__device__ void block_assemble(double* A, double* A0, const double* s_mu, const double* s_he) {
+    using C = WCfg<M>;
+    constexpr int n = C::n, NT = C::NT;
+    for (int idx = threadIdx.x; idx < n * n; idx += NT) {
         const int r = idx / n, c = idx - r * n;
         int ar, br, ac, bc;
         exps_of(r, ar, br);
@@ -263,18 +240,21 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
         }
         const double v = sum * (inv_factorial(ar) * inv_factorial(br));
         A[r * LDA + c] = v;
-        if (RESID) A0[r * n + c] = v;
+        if (A0) A0[r * n + c] = v;
     }
-    for (int idx = t; idx < n * 6; idx += NT) {
-        const int q = idx / 6, d = idx - q * 6;
-        int a, b;
-        exps_of(q, a, b);
-        const double coef = selector_coef<M>(d, a, b);
-        A[q * LDA + n + d] = coef != 0.0 ? coef * pow(g.hi, -double(a + b)) : 0.0;
-    }
-    __syncthreads();
+}
 
-    // ---- Gaussian elimination with partial pivoting on [M | C~]
+// Gaussian elimination with partial pivoting (the first row holding the largest
+// |pivot| wins) on the augmented system [M | B] (n x LDA, NRHS = LDA - n right-hand
+// sides), then back substitution by warp 0: the solutions overwrite B.  Returns
+// true (uniformly) if a pivot was zero or not finite.  Starts and ends with a barrier.
+template <int M, int LDA>
+__device__ bool block_lu_solve(double* A, int* s_piv, int* s_flag) {
+    using C = WCfg<M>;
+    constexpr int n = C::n, NT = C::NT, NRHS = LDA - n;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) *s_flag = 0;
+    __syncthreads();
     for (int k = 0; k < n; ++k) {
         if (warp == 0) {
             double best = -1.0;
@@ -296,13 +276,13 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
                 }
             }
             if (lane == 0) {
-                s_piv = bidx;
-                if (!(best > 0.0) || !isfinite(best) || bidx >= n) s_flags |= LABFM_NODE_SINGULAR;
+                *s_piv = bidx;
+                if (!(best > 0.0) || !isfinite(best) || bidx >= n) *s_flag = 1;
             }
         }
         __syncthreads();
-        if (s_flags & LABFM_NODE_SINGULAR) break;
-        const int p = s_piv;
+        if (*s_flag) break;
+        const int p = *s_piv;
         if (p != k) {
             for (int c = t; c < LDA; c += NT) {
                 const double tmp = A[k * LDA + c];
@@ -323,29 +303,97 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
         }
         __syncthreads();
     }
-
-    const bool singular = (s_flags & LABFM_NODE_SINGULAR) != 0;
-    // ---- back substitution (warp 0), Psi^d overwrites the C~ columns
+    const bool singular = *s_flag != 0;
     if (!singular && warp == 0) {
         for (int k = n - 1; k >= 0; --k) {
             const double dkk = A[k * LDA + k];
-            double psi[6];
+            double psi[NRHS];
 #pragma unroll
-            for (int d = 0; d < 6; ++d) psi[d] = A[k * LDA + n + d] / dkk;
+            for (int d = 0; d < NRHS; ++d) psi[d] = A[k * LDA + n + d] / dkk;
             __syncwarp();
             for (int r = lane; r < k; r += 32) {
                 const double ark = A[r * LDA + k];
 #pragma unroll
-                for (int d = 0; d < 6; ++d) A[r * LDA + n + d] -= ark * psi[d];
+                for (int d = 0; d < NRHS; ++d) A[r * LDA + n + d] -= ark * psi[d];
             }
             if (lane == 0) {
 #pragma unroll
-                for (int d = 0; d < 6; ++d) A[k * LDA + n + d] = psi[d];
+                for (int d = 0; d < NRHS; ++d) A[k * LDA + n + d] = psi[d];
             }
             __syncwarp();
         }
     }
     __syncthreads();
+    return singular;
+}
+
+// Block-wide sum (all threads get the result).  s_red: NT / 32 doubles.
+template <int NT>
+__device__ double block_sum(double v, double* s_red) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double tot = 0.0;
+    for (int k = 0; k < NT / 32; ++k) tot += s_red[k];
+    return tot;
+}
+
+// ---------------------------------------------------------------- weight build
+
+template <int M, bool RESID>
+__global__ void __launch_bounds__(WCfg<M>::NT)
+    k_weight_build(const double* __restrict__ xy, const double* __restrict__ h,
+                   const double* __restrict__ s, int64_t N, double Lx, double Ly, int px_, int py_,
+                   const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t nnz,
+                   double* __restrict__ w, double* __restrict__ kappa, double* __restrict__ residual,
+                   int32_t* __restrict__ node_status, unsigned long long* __restrict__ n_failed) {
+    using C = WCfg<M>;
+    constexpr int n = C::n;
+    constexpr int NT = C::NT;
+    constexpr int LDA = C::LDA;
+    extern __shared__ double smem[];
+    double* A = smem;              // [n][LDA], aliases the moment scratch after assembly
+    double* A0 = smem + n * LDA;   // [n][n] copy of M for the residual
+    __shared__ double s_mu[C::NMOM];
+    __shared__ double s_he[(M + 1) * (M + 1)];
+    __shared__ int s_piv;
+    __shared__ int s_flag;
+    __shared__ int s_nonfinite;
+    __shared__ double s_red[NT / 32];
+
+    const int64_t i = blockIdx.x;
+    if (i >= N) return;
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int warp = t >> 5;
+    NodeGeom g{xy[2 * i], xy[2 * i + 1], h[i], Lx, Ly, px_ != 0, py_ != 0};
+    const int r0 = row_ptr[i];
+    const int r1 = row_ptr[i + 1];
+    if (r1 - r0 < n) {  // M_i singular: fewer stencil nodes than unknowns
+        for (int e = r0 + t; e < r1; e += NT)
+            for (int d = 0; d < 6; ++d) w[int64_t(d) * nnz + e] = 0.0;
+        if (t == 0) {
+            kappa[i] = 0.0;
+            if (RESID) residual[i] = INFINITY;
+            node_status[i] = LABFM_NODE_FEW_NEIGHBOURS;
+            if (n_failed) atomicAdd(n_failed, 1ull);
+        }
+        return;
+    }
+    if (t == 0) s_nonfinite = 0;
+    build_he<M>(s_he);
+    block_moments<M>(xy, col, r0, r1, g, smem, smem + NT * C::NPOW, s_mu);
+    block_assemble<M, LDA>(A, RESID ? A0 : nullptr, s_mu, s_he);
+    for (int idx = t; idx < n * 6; idx += NT) {  // selectors C~^d
+        const int q = idx / 6, d = idx - q * 6;
+        int a, b;
+        exps_of(q, a, b);
+        const double coef = selector_coef<M>(d, a, b);
+        A[q * LDA + n + d] = coef != 0.0 ? coef * pow(g.hi, -double(a + b)) : 0.0;
+    }
+    const bool singular = block_lu_solve<M, LDA>(A, &s_piv, &s_flag);
 
     // ---- residual of eq. lsys in nondimensional form: (M Psi^d - C~^d)_q h^l
     if (RESID) {
@@ -404,24 +452,244 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
         const double phi = 1.0 - cos(kx * dx) * cos(kx * dy);
         f0 = fma(phi, wd[5], f0);
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) f0 += __shfl_xor_sync(0xffffffffu, f0, off);
-    const unsigned badw = __ballot_sync(0xffffffffu, bad);
-    __syncthreads();
-    if (lane == 0) {
-        s_red[warp] = f0;
-        if (badw) atomicOr(&s_flags, LABFM_NODE_NONFINITE);
-    }
-    __syncthreads();
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&s_nonfinite, 1);
+    const double F0 = block_sum<NT>(f0, s_red);
     if (t == 0) {
-        double F0 = 0.0;
-        for (int k = 0; k < NT / 32; ++k) F0 += s_red[k];
         const double kap = singular ? 0.0 : 2.0 / (3.0 * F0);
-        int flags = s_flags;
+        int flags = singular ? LABFM_NODE_SINGULAR : 0;
+        if (s_nonfinite) flags |= LABFM_NODE_NONFINITE;
         if (!singular && !isfinite(kap)) flags |= LABFM_NODE_NONFINITE;
         kappa[i] = kap;
         node_status[i] = flags;
         if (flags && n_failed) atomicAdd(n_failed, 1ull);
+    }
+}
+
+// ---------------------------------------------------------------- stencil optimisation (Section 4)
+
+constexpr int kNk = 16;  // wavenumbers of the amplitude test (n_k = 16 in Section 4)
+
+// Amplitude responses of the d/dx, d/dy and Laplacian operators of node i at
+// k_n = (pi / s_i) n / kNk, n = 1..kNk (Section 4, step 3).  Neighbours are taken
+// NT at a time: each thread stages one neighbour's offsets and its three weights
+// (Psi^x, Psi^y, Psi^L in columns n, n + 1, n + 2 of A) in s_nb, then each of the
+// 3 kNk (operator, wavenumber) pairs is summed by one thread.  Returns the
+// largest of the 3 kNk responses (the same value in every thread).
+template <int M, int LDA>
+__device__ double block_amplitude_max(const double* __restrict__ xy, const int32_t* __restrict__ col,
+                                      int r0, int r1, const NodeGeom& g, double s_i, const double* A,
+                                      double* s_nb, double* s_amp) {
+    using C = WCfg<M>;
+    constexpr int n = C::n, NT = C::NT;
+    constexpr int NP = 3 * kNk, PPT = (NP + NT - 1) / NT;
+    const int t = threadIdx.x;
+    const double kny = 3.141592653589793 / s_i;
+    double acc[PPT];
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) acc[u] = 0.0;
+    for (int c0 = r0; c0 < r1; c0 += NT) {
+        const int cnt = min(NT, r1 - c0);
+        if (t < cnt) {
+            double pxv[M + 1], pyv[M + 1], hxv[M + 1], hyv[M + 1], psi, dx, dy;
+            neighbour_factors<M>(xy, col[c0 + t], g, pxv, pyv, hxv, hyv, &psi, &dx, &dy);
+            double w0 = 0.0, w1 = 0.0, w2 = 0.0;
+            int q = 0;
+#pragma unroll
+            for (int kk = 1; kk <= M; ++kk) {
+#pragma unroll
+                for (int a = kk; a >= 0; --a, ++q) {
+                    const double Wq = psi * hxv[a] * hyv[kk - a] * inv_sqrt2_pow(kk);
+                    w0 = fma(Wq, A[q * LDA + n], w0);
+                    w1 = fma(Wq, A[q * LDA + n + 1], w1);
+                    w2 = fma(Wq, A[q * LDA + n + 2], w2);
+                }
+            }
+            double* r = s_nb + 5 * t;
+            r[0] = dx;
+            r[1] = dy;
+            r[2] = w0;
+            r[3] = w1;
+            r[4] = w2;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < PPT; ++u) {
+            const int pr = t + u * NT;
+            if (pr < NP) {
+                const int d = pr / kNk;
+                const double kn = kny * double(pr - d * kNk + 1) / kNk;
+                double v = acc[u];
+                for (int e = 0; e < cnt; ++e) {
+                    const double* r = s_nb + 5 * e;
+                    if (d == 0) {
+                        v = fma(sin(kn * r[0]), r[2], v);
+                    } else if (d == 1) {
+                        v = fma(sin(kn * r[1]), r[3], v);
+                    } else {
+                        v = fma(0.5 - 0.5 * cos(kn * r[0]) * cos(kn * r[1]), r[4], v);
+                    }
+                }
+                acc[u] = v;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+        const int pr = t + u * NT;
+        if (pr < NP) {
+            const int d = pr / kNk;
+            const double kn = kny * double(pr - d * kNk + 1) / kNk;
+            s_amp[pr] = d < 2 ? acc[u] / kn : acc[u] / (kn * kn);
+        }
+    }
+    __syncthreads();
+    double mx = -INFINITY;
+    for (int q2 = 0; q2 < NP; ++q2) mx = fmax(mx, s_amp[q2]);
+    return mx;
+}
+
+template <int M>
+__global__ void __launch_bounds__(WCfg<M>::NT)
+    k_stencil_opt(const double* __restrict__ xy, const double* __restrict__ h0,
+                  const double* __restrict__ s, int64_t N, double Lx, double Ly, int px_, int py_,
+                  const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                  double factor, double amp_max, double resid_coef, int max_iter,
+                  double* __restrict__ h_out, int32_t* __restrict__ solves_out) {
+    using C = WCfg<M>;
+    constexpr int n = C::n;
+    constexpr int NT = C::NT;
+    constexpr int LDA = n + 3;  // [M | C~x C~y C~L]
+    extern __shared__ double smem[];
+    double* A = smem;
+    double* A0 = smem + n * LDA;
+    __shared__ double s_mu[C::NMOM];
+    __shared__ double s_he[(M + 1) * (M + 1)];
+    __shared__ double s_red[NT / 32];
+    __shared__ double s_nb[5 * NT];
+    __shared__ double s_amp[3 * kNk];
+    __shared__ int s_piv;
+    __shared__ int s_flag;
+
+    const int64_t i = blockIdx.x;
+    if (i >= N) return;
+    const int t = threadIdx.x;
+    const int r0 = row_ptr[i];
+    const int r1 = row_ptr[i + 1];
+    const double eps = 2.220446049250313e-16;
+    build_he<M>(s_he);
+    NodeGeom g{xy[2 * i], xy[2 * i + 1], h0[i], Lx, Ly, px_ != 0, py_ != 0};
+    double best = h0[i];
+    int solves = 0;
+    for (int it = 0; it < max_iter; ++it) {
+        // nodes inside the current radius (the same exact test as the neighbour search)
+        const double two_h = 2.0 * g.hi;
+        const double rad2 = __dmul_rn(two_h, two_h);
+        double cnt = 0.0;
+        for (int e = r0 + t; e < r1; e += NT) {
+            const int j = col[e];
+            const double dx = min_image(__dsub_rn(xy[2 * j], g.xi), g.Lx, g.px);
+            const double dy = min_image(__dsub_rn(xy[2 * j + 1], g.yi), g.Ly, g.py);
+            cnt += __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)) <= rad2 ? 1.0 : 0.0;
+        }
+        if (block_sum<NT>(cnt, s_red) < double(n)) break;
+        // Section 4 steps 1-2: solve for x, y and L and test the Laplacian residual
+        block_moments<M>(xy, col, r0, r1, g, smem, smem + NT * C::NPOW, s_mu);
+        block_assemble<M, LDA>(A, A0, s_mu, s_he);
+        for (int idx = t; idx < n * 3; idx += NT) {
+            const int q = idx / 3, d = idx - q * 3;
+            int a, b;
+            exps_of(q, a, b);
+            double coef;
+            if (d < 2) coef = selector_coef<M>(d, a, b);
+            else coef = ((a == 2 && b == 0) || (a == 0 && b == 2)) ? 1.0 : 0.0;
+            A[q * LDA + n + d] = coef != 0.0 ? coef * pow(g.hi, -double(a + b)) : 0.0;
+        }
+        const bool singular = block_lu_solve<M, LDA>(A, &s_piv, &s_flag);
+        ++solves;
+        if (singular) break;
+        double r2 = 0.0;
+        for (int q = t; q < n; q += NT) {
+            double sum = 0.0;
+            for (int c = 0; c < n; ++c) sum = fma(A0[q * n + c], A[c * LDA + n + 2], sum);
+            int a, b;
+            exps_of(q, a, b);
+            const double cq = ((a == 2 && b == 0) || (a == 0 && b == 2)) ? pow(g.hi, -2.0) : 0.0;
+            const double r = (sum - cq) * g.hi * g.hi;
+            r2 = fma(r, r, r2);
+        }
+        const double alpha = sqrt(block_sum<NT>(r2, s_red));
+        const double alpha0 = resid_coef * eps * double(n) * double(n) * double(n) * double(n) / (g.hi * M);
+        if (!(alpha <= alpha0)) break;
+        // steps 3-4: amplitude response up to Nyquist
+        const double amax = block_amplitude_max<M, LDA>(xy, col, r0, r1, g, s[i], A, s_nb, s_amp);
+        if (!(amax <= amp_max)) break;
+        // step 5
+        best = g.hi;
+        g.hi = g.hi * factor;
+        __syncthreads();
+    }
+    if (t == 0) {
+        h_out[i] = best;
+        if (solves_out) solves_out[i] = solves;
+    }
+}
+
+template <int M>
+int launch_stencil_opt(const double* xy, const double* h0, const double* s, int64_t N, double Lx,
+                       double Ly, uint32_t pm, const int32_t* row_ptr, const int32_t* col,
+                       double factor, double amp_max, double resid_coef, int max_iter, double* h_out,
+                       int32_t* solves, cudaStream_t st) {
+    using C = WCfg<M>;
+    const size_t sm = C::smem(true);
+    LABFM_CUDA_TRY(cudaFuncSetAttribute(k_stencil_opt<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+    k_stencil_opt<M><<<unsigned(N), C::NT, sm, st>>>(xy, h0, s, N, Lx, Ly, pm & 1u, (pm >> 1) & 1u,
+                                                     row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves);
+    LABFM_LAUNCH_CHECK("stencil optimisation kernel");
+    return LABFM_OK;
+}
+
+// ---------------------------------------------------------------- modal response (Section 3)
+
+// Per node, the amplitude responses of d/dx, d/dy and the Laplacian (w^xx + w^yy)
+// of built weights at k_n = n pi / (s_i nk), n = 1..nk: out[(i * 3 + d) * nk + n - 1].
+__global__ void k_modal_response(const double* __restrict__ xy, const double* __restrict__ s,
+                                 int64_t N, double Lx, double Ly, int px_, int py_,
+                                 const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                 int64_t nnz, const double* __restrict__ w, int nk,
+                                 double* __restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = int64_t(gridDim.x) * (blockDim.x >> 5);
+    for (int64_t i = (blockIdx.x * int64_t(blockDim.x) + threadIdx.x) >> 5; i < N; i += warps) {
+        const int r0 = row_ptr[i], r1 = row_ptr[i + 1];
+        const double xi = xy[2 * i], yi = xy[2 * i + 1];
+        const double k0 = 3.141592653589793 / (s[i] * nk);
+        for (int k = 1; k <= nk; ++k) {
+            const double kn = double(k) * k0;
+            double ax = 0.0, ay = 0.0, al = 0.0;
+            for (int e = r0 + lane; e < r1; e += 32) {
+                const int j = col[e];
+                const double dx = min_image(__dsub_rn(xy[2 * j], xi), Lx, px_ != 0);
+                const double dy = min_image(__dsub_rn(xy[2 * j + 1], yi), Ly, py_ != 0);
+                double sx, cx, sy, cy;
+                sincos(kn * dx, &sx, &cx);
+                sincos(kn * dy, &sy, &cy);
+                ax = fma(sx, w[e], ax);
+                ay = fma(sy, w[nnz + e], ay);
+                al = fma(0.5 - 0.5 * cx * cy, w[2 * nnz + e] + w[4 * nnz + e], al);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, off);
+                ay += __shfl_xor_sync(0xffffffffu, ay, off);
+                al += __shfl_xor_sync(0xffffffffu, al, off);
+            }
+            if (lane == 0) {
+                out[(i * 3 + 0) * nk + k - 1] = ax / kn;
+                out[(i * 3 + 1) * nk + k - 1] = ay / kn;
+                out[(i * 3 + 2) * nk + k - 1] = al / (kn * kn);
+            }
+        }
     }
 }
 
@@ -494,4 +762,42 @@ extern "C" int labfm_build_weights(const double* xy, const double* h, const doub
             return set_error(LABFM_ESINGULAR, std::to_string(hf) + " node(s) failed; see node_status");
     }
     return rc;
+}
+
+extern "C" int labfm_stencil_optimise(const double* xy, const double* h0, const double* s, int64_t N,
+                                      double Lx, double Ly, uint32_t periodic_mask,
+                                      const int32_t* row_ptr, const int32_t* col, int m,
+                                      double factor, double amp_max, double resid_coef, int max_iter,
+                                      double* h_out, int32_t* solves_out, void* stream) {
+    if (!xy || !h0 || !s || !row_ptr || !col || !h_out)
+        return set_error(LABFM_EINVAL, "null pointer argument");
+    if (N <= 0 || N >= (int64_t(1) << 31) - 1) return set_error(LABFM_EINVAL, "N out of range");
+    if (m < 2 || m > 10 || (m & 1)) return set_error(LABFM_EINVAL, "order m must be even and in [2, 10]");
+    if (!(factor > 0.0 && factor < 1.0)) return set_error(LABFM_EINVAL, "factor must be in (0, 1)");
+    if (max_iter < 0) return set_error(LABFM_EINVAL, "negative max_iter");
+    if (!(resid_coef > 0.0)) return set_error(LABFM_EINVAL, "resid_coef must be positive");
+    cudaStream_t st = as_stream(stream);
+    switch (m) {
+        case 2: return launch_stencil_opt<2>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, st);
+        case 4: return launch_stencil_opt<4>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, st);
+        case 6: return launch_stencil_opt<6>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, st);
+        case 8: return launch_stencil_opt<8>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, st);
+        default: return launch_stencil_opt<10>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, st);
+    }
+}
+
+extern "C" int labfm_modal_response(const double* xy, const double* s, int64_t N, double Lx,
+                                    double Ly, uint32_t periodic_mask, const int32_t* row_ptr,
+                                    const int32_t* col, int64_t nnz, const double* w, int nk,
+                                    double* out, void* stream) {
+    if (!xy || !s || !row_ptr || !w || !out || (nnz > 0 && !col))
+        return set_error(LABFM_EINVAL, "null pointer argument");
+    if (N <= 0 || N >= (int64_t(1) << 31) - 1) return set_error(LABFM_EINVAL, "N out of range");
+    if (nk < 1 || nk > 4096) return set_error(LABFM_EINVAL, "nk out of range");
+    cudaStream_t st = as_stream(stream);
+    const int grid = int(std::min<int64_t>((N + 7) / 8, 1 << 20));
+    k_modal_response<<<grid, 256, 0, st>>>(xy, s, N, Lx, Ly, periodic_mask & 1u, (periodic_mask >> 1) & 1u,
+                                           row_ptr, col, nnz, w, nk, out);
+    LABFM_LAUNCH_CHECK("modal response kernel");
+    return LABFM_OK;
 }
