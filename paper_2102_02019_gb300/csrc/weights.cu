@@ -304,22 +304,20 @@ __device__ bool block_lu_solve(double* A, int* s_piv, int* s_flag) {
         __syncthreads();
     }
     const bool singular = *s_flag != 0;
+    static_assert(NRHS <= 32, "one lane per right-hand side");
     if (!singular && warp == 0) {
         for (int k = n - 1; k >= 0; --k) {
-            const double dkk = A[k * LDA + k];
+            // lane d divides right-hand side d (one division sequence for the warp)
+            const double mine = lane < NRHS ? A[k * LDA + n + lane] / A[k * LDA + k] : 0.0;
             double psi[NRHS];
 #pragma unroll
-            for (int d = 0; d < NRHS; ++d) psi[d] = A[k * LDA + n + d] / dkk;
-            __syncwarp();
+            for (int d = 0; d < NRHS; ++d) psi[d] = __shfl_sync(0xffffffffu, mine, d);
             for (int r = lane; r < k; r += 32) {
                 const double ark = A[r * LDA + k];
 #pragma unroll
                 for (int d = 0; d < NRHS; ++d) A[r * LDA + n + d] -= ark * psi[d];
             }
-            if (lane == 0) {
-#pragma unroll
-                for (int d = 0; d < NRHS; ++d) A[k * LDA + n + d] = psi[d];
-            }
+            if (lane < NRHS) A[k * LDA + n + lane] = mine;
             __syncwarp();
         }
     }
@@ -362,6 +360,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
     __shared__ int s_flag;
     __shared__ int s_nonfinite;
     __shared__ double s_red[NT / 32];
+    __shared__ double s_hp[2 * M + 1];  // h^k, k = -M..M, at [k + M]
 
     const int64_t i = blockIdx.x;
     if (i >= N) return;
@@ -383,6 +382,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
         return;
     }
     if (t == 0) s_nonfinite = 0;
+    if (t <= 2 * M) s_hp[t] = pow(g.hi, double(t - M));
     build_he<M>(s_he);
     block_moments<M>(xy, col, r0, r1, g, smem, smem + NT * C::NPOW, s_mu);
     block_assemble<M, LDA>(A, RESID ? A0 : nullptr, s_mu, s_he);
@@ -390,8 +390,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
         const int q = idx / 6, d = idx - q * 6;
         int a, b;
         exps_of(q, a, b);
-        const double coef = selector_coef<M>(d, a, b);
-        A[q * LDA + n + d] = coef != 0.0 ? coef * pow(g.hi, -double(a + b)) : 0.0;
+        A[q * LDA + n + d] = selector_coef<M>(d, a, b) * s_hp[M - (a + b)];
     }
     const bool singular = block_lu_solve<M, LDA>(A, &s_piv, &s_flag);
 
@@ -405,9 +404,8 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
                 for (int c = 0; c < n; ++c) sum = fma(A0[q * n + c], A[c * LDA + n + d], sum);
                 int a, b;
                 exps_of(q, a, b);
-                const double coef = selector_coef<M>(d, a, b);
-                const double cq = coef != 0.0 ? coef * pow(g.hi, -double(a + b)) : 0.0;
-                const double r = fabs(sum - cq) * pow(g.hi, double(op_order(d, M)));
+                const double cq = selector_coef<M>(d, a, b) * s_hp[M - (a + b)];
+                const double r = fabs(sum - cq) * s_hp[M + op_order(d, M)];
                 rmax = (r > rmax || isnan(r)) ? r : rmax;
             }
         }
@@ -470,83 +468,98 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
 constexpr int kNk = 16;  // wavenumbers of the amplitude test (n_k = 16 in Section 4)
 
 // Amplitude responses of the d/dx, d/dy and Laplacian operators of node i at
-// k_n = (pi / s_i) n / kNk, n = 1..kNk (Section 4, step 3).  Neighbours are taken
-// NT at a time: each thread stages one neighbour's offsets and its three weights
-// (Psi^x, Psi^y, Psi^L in columns n, n + 1, n + 2 of A) in s_nb, then each of the
-// 3 kNk (operator, wavenumber) pairs is summed by one thread.  Returns the
-// largest of the 3 kNk responses (the same value in every thread).
+// k_n = (pi / s_i) n / kNk, n = 1..kNk (Section 4, step 3).  Each thread takes one
+// neighbour per pass: its three weights (Psi^x, Psi^y, Psi^L in columns n, n + 1,
+// n + 2 of A), then sin and cos of n k_1 x_ji and n k_1 y_ji for n = 1..kNk by
+// rotation from one sincos each (every step multiplies by e^{i k_1 x}, so the
+// rounding error grows linearly in n), each product reduced across the warp.
+// s_part: (NT / 32) x 3 kNk doubles.  Returns the largest of the 3 kNk
+// responses (the same value in every thread).
 template <int M, int LDA>
 __device__ double block_amplitude_max(const double* __restrict__ xy, const int32_t* __restrict__ col,
                                       int r0, int r1, const NodeGeom& g, double s_i, const double* A,
-                                      double* s_nb, double* s_amp) {
+                                      double* s_psi, double* s_part, double* s_amax) {
     using C = WCfg<M>;
-    constexpr int n = C::n, NT = C::NT;
-    constexpr int NP = 3 * kNk, PPT = (NP + NT - 1) / NT;
-    const int t = threadIdx.x;
+    constexpr int n = C::n, NT = C::NT, NW = NT / 32;
+    constexpr int NP = 3 * kNk;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const double kny = 3.141592653589793 / s_i;
-    double acc[PPT];
-#pragma unroll
-    for (int u = 0; u < PPT; ++u) acc[u] = 0.0;
+    const double k1 = kny / kNk;
+    // Psi^d_q / sqrt(2^deg q), so that w^d_j = psi_j sum_q H_a H_b s_psi[q][d]
+    for (int idx = t; idx < n * 3; idx += NT) {
+        const int q = idx / 3, d = idx - q * 3;
+        int a, b;
+        exps_of(q, a, b);
+        s_psi[idx] = A[q * LDA + n + d] * inv_sqrt2_pow(a + b);
+    }
+    for (int u = t; u < NW * NP; u += NT) s_part[u] = 0.0;
+    __syncthreads();
     for (int c0 = r0; c0 < r1; c0 += NT) {
-        const int cnt = min(NT, r1 - c0);
-        if (t < cnt) {
-            double pxv[M + 1], pyv[M + 1], hxv[M + 1], hyv[M + 1], psi, dx, dy;
-            neighbour_factors<M>(xy, col[c0 + t], g, pxv, pyv, hxv, hyv, &psi, &dx, &dy);
-            double w0 = 0.0, w1 = 0.0, w2 = 0.0;
+        if (c0 + warp * 32 >= r1) continue;  // warp-uniform: no neighbour for this warp
+        const int e = c0 + t;
+        double w0 = 0.0, w1 = 0.0, w2 = 0.0, dx = 0.0, dy = 0.0;
+        if (e < r1) {
+            double pxv[M + 1], pyv[M + 1], hxv[M + 1], hyv[M + 1], psi;
+            neighbour_factors<M>(xy, col[e], g, pxv, pyv, hxv, hyv, &psi, &dx, &dy);
             int q = 0;
 #pragma unroll
             for (int kk = 1; kk <= M; ++kk) {
 #pragma unroll
                 for (int a = kk; a >= 0; --a, ++q) {
-                    const double Wq = psi * hxv[a] * hyv[kk - a] * inv_sqrt2_pow(kk);
-                    w0 = fma(Wq, A[q * LDA + n], w0);
-                    w1 = fma(Wq, A[q * LDA + n + 1], w1);
-                    w2 = fma(Wq, A[q * LDA + n + 2], w2);
+                    const double Hq = hxv[a] * hyv[kk - a];
+                    w0 = fma(Hq, s_psi[3 * q], w0);
+                    w1 = fma(Hq, s_psi[3 * q + 1], w1);
+                    w2 = fma(Hq, s_psi[3 * q + 2], w2);
                 }
             }
-            double* r = s_nb + 5 * t;
-            r[0] = dx;
-            r[1] = dy;
-            r[2] = w0;
-            r[3] = w1;
-            r[4] = w2;
+            w0 *= psi;
+            w1 *= psi;
+            w2 *= psi;
         }
-        __syncthreads();
+        double s1x, c1x, s1y, c1y;
+        sincos(k1 * dx, &s1x, &c1x);
+        sincos(k1 * dy, &s1y, &c1y);
+        double sx = s1x, cx = c1x, sy = s1y, cy = c1y;
 #pragma unroll
-        for (int u = 0; u < PPT; ++u) {
-            const int pr = t + u * NT;
-            if (pr < NP) {
-                const int d = pr / kNk;
-                const double kn = kny * double(pr - d * kNk + 1) / kNk;
-                double v = acc[u];
-                for (int e = 0; e < cnt; ++e) {
-                    const double* r = s_nb + 5 * e;
-                    if (d == 0) {
-                        v = fma(sin(kn * r[0]), r[2], v);
-                    } else if (d == 1) {
-                        v = fma(sin(kn * r[1]), r[3], v);
-                    } else {
-                        v = fma(0.5 - 0.5 * cos(kn * r[0]) * cos(kn * r[1]), r[4], v);
-                    }
-                }
-                acc[u] = v;
+        for (int k = 0; k < kNk; ++k) {
+            double vx = sx * w0;
+            double vy = sy * w1;
+            double vl = (0.5 - 0.5 * cx * cy) * w2;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                vx += __shfl_xor_sync(0xffffffffu, vx, off);
+                vy += __shfl_xor_sync(0xffffffffu, vy, off);
+                vl += __shfl_xor_sync(0xffffffffu, vl, off);
             }
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int u = 0; u < PPT; ++u) {
-        const int pr = t + u * NT;
-        if (pr < NP) {
-            const int d = pr / kNk;
-            const double kn = kny * double(pr - d * kNk + 1) / kNk;
-            s_amp[pr] = d < 2 ? acc[u] / kn : acc[u] / (kn * kn);
+            if (lane == 0) {
+                s_part[warp * NP + k] += vx;
+                s_part[warp * NP + kNk + k] += vy;
+                s_part[warp * NP + 2 * kNk + k] += vl;
+            }
+            const double nsx = fma(sx, c1x, cx * s1x), ncx = fma(cx, c1x, -(sx * s1x));
+            const double nsy = fma(sy, c1y, cy * s1y), ncy = fma(cy, c1y, -(sy * s1y));
+            sx = nsx;
+            cx = ncx;
+            sy = nsy;
+            cy = ncy;
         }
     }
     __syncthreads();
-    double mx = -INFINITY;
-    for (int q2 = 0; q2 < NP; ++q2) mx = fmax(mx, s_amp[q2]);
-    return mx;
+    if (warp == 0) {
+        double mx = -INFINITY;
+        for (int pr = lane; pr < NP; pr += 32) {
+            double v = 0.0;
+            for (int wp = 0; wp < NW; ++wp) v += s_part[wp * NP + pr];
+            const int d = pr / kNk;
+            const double kn = kny * double(pr - d * kNk + 1) / kNk;
+            mx = fmax(mx, d < 2 ? v / kn : v / (kn * kn));
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if (lane == 0) *s_amax = mx;
+    }
+    __syncthreads();
+    return *s_amax;
 }
 
 template <int M>
@@ -566,8 +579,10 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
     __shared__ double s_mu[C::NMOM];
     __shared__ double s_he[(M + 1) * (M + 1)];
     __shared__ double s_red[NT / 32];
-    __shared__ double s_nb[5 * NT];
-    __shared__ double s_amp[3 * kNk];
+    __shared__ double s_part[(NT / 32) * 3 * kNk];
+    __shared__ double s_psi[3 * n];
+    __shared__ double s_hp[M + 1];
+    __shared__ double s_amax;
     __shared__ int s_piv;
     __shared__ int s_flag;
 
@@ -582,6 +597,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
     double best = h0[i];
     int solves = 0;
     for (int it = 0; it < max_iter; ++it) {
+        if (t <= M) s_hp[t] = pow(g.hi, -double(t));  // h^-k (read after the next barrier)
         // nodes inside the current radius (the same exact test as the neighbour search)
         const double two_h = 2.0 * g.hi;
         const double rad2 = __dmul_rn(two_h, two_h);
@@ -603,7 +619,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
             double coef;
             if (d < 2) coef = selector_coef<M>(d, a, b);
             else coef = ((a == 2 && b == 0) || (a == 0 && b == 2)) ? 1.0 : 0.0;
-            A[q * LDA + n + d] = coef != 0.0 ? coef * pow(g.hi, -double(a + b)) : 0.0;
+            A[q * LDA + n + d] = coef * s_hp[a + b];
         }
         const bool singular = block_lu_solve<M, LDA>(A, &s_piv, &s_flag);
         ++solves;
@@ -614,7 +630,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
             for (int c = 0; c < n; ++c) sum = fma(A0[q * n + c], A[c * LDA + n + 2], sum);
             int a, b;
             exps_of(q, a, b);
-            const double cq = ((a == 2 && b == 0) || (a == 0 && b == 2)) ? pow(g.hi, -2.0) : 0.0;
+            const double cq = ((a == 2 && b == 0) || (a == 0 && b == 2)) ? s_hp[2] : 0.0;
             const double r = (sum - cq) * g.hi * g.hi;
             r2 = fma(r, r, r2);
         }
@@ -622,7 +638,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
         const double alpha0 = resid_coef * eps * double(n) * double(n) * double(n) * double(n) / (g.hi * M);
         if (!(alpha <= alpha0)) break;
         // steps 3-4: amplitude response up to Nyquist
-        const double amax = block_amplitude_max<M, LDA>(xy, col, r0, r1, g, s[i], A, s_nb, s_amp);
+        const double amax = block_amplitude_max<M, LDA>(xy, col, r0, r1, g, s[i], A, s_psi, s_part, &s_amax);
         if (!(amax <= amp_max)) break;
         // step 5
         best = g.hi;
