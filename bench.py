@@ -56,6 +56,8 @@ def parse():
                     help="fix the lanes per node of the main workload (0 = autotune)")
     ap.add_argument("--nx", type=int, default=512,
                     help="lattice side (512 = the benchmark workload; smaller sizes for profiling)")
+    ap.add_argument("--only", choices=["stencil_opt"], default=None,
+                    help="run one extra workload alone on --nx and print its JSON (for profiling)")
     return ap.parse_args()
 
 
@@ -372,13 +374,15 @@ def run_varres(lb, torch, args):
 
 
 def run_stencil_opt(lb, torch, args):
-    """Section 4 stencil optimisation on the 512 x 512 (+-0.3 s) lattice from h0 = 2.8 s for
-    m = 6 and m = 8, and the modal response (16 wavenumbers) of the m = 8 operator."""
+    """Section 4 stencil optimisation on the nx x nx (+-0.3 s) lattice (512: 262,144 nodes)
+    from h0 = 2.8 s for m = 6 and m = 8, and the modal response (16 wavenumbers) of the
+    m = 8 operator on the optimised stencils."""
     import labfm_inputs as li
-    out = {"workload": "262,144-node jittered lattice (+-0.3 s), every node from h0 = 2.8 s, "
+    nx = args.nx
+    out = {"workload": f"{nx * nx:,}-node jittered lattice (+-0.3 s), every node from h0 = 2.8 s, "
                        "factor 0.99, amplitude bound 1.01, residual coefficient 1e-4"}
     for m in (6, 8):
-        ns = li.tgv_lattice(512, m=m, h_over_s=2.8, jitter=0.3, seed=3)
+        ns = li.tgv_lattice(nx, m=m, h_over_s=2.8, jitter=0.3, seed=3)
         xy = torch.tensor(ns.xy, device="cuda")
         s = torch.tensor(ns.s, device="cuda")
         h0 = 2.8 * s
@@ -672,6 +676,14 @@ def run_ours(args, world, rank, local):
 def main():
     args = parse()
     world, rank, local = dist_init(args)
+    if args.only == "stencil_opt":
+        import torch
+
+        import __graft_entry__ as g
+        g.build()
+        import paper_2102_02019_gb300 as lb
+        print(json.dumps(run_stencil_opt(lb, torch, args)), flush=True)
+        return 0
     if args.impl == "reference":
         rc = run_reference(args, world, rank)
     else:
