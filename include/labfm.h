@@ -262,6 +262,32 @@ int labfm_stable_dt_instances(const labfm_plan* plan, const void* fields, const 
  */
 int labfm_plan_set_persistent(labfm_plan* plan, int enable);
 
+/*
+ * Shared-memory staging of the operator stream for the F32 stage kernel
+ * (stages = 2, 3 or 4 ring slots per CTA; 0 = off).  With staging on and 16 or
+ * 32 lanes per node (labfm_plan_set_launch), labfm_rk_step runs a stage kernel
+ * in which the bulk-copy (TMA) engine moves the operator records of whole
+ * rounds of consecutive nodes (4 x 32/G nodes per 128-thread CTA) into shared
+ * memory ahead of the warps that use them; results are bit-identical to the
+ * unstaged kernel with the same lanes per node.  Other lane counts, and F64
+ * plans' steps, run the unstaged kernel.  The call measures the largest round
+ * (synchronising `stream`) and sizes the grid; a lane count whose largest round
+ * does not fit `stages` slots in shared memory keeps the unstaged kernel.  Each
+ * wait of the staged kernel on a copy is bounded (1 s); one that runs out is
+ * reported by labfm_plan_device_status.
+ * Errors: EINVAL (F64 plan with stages != 0, stages not in {0, 2, 3, 4}).
+ */
+int labfm_plan_set_staging(labfm_plan* plan, int stages, void* stream);
+
+/*
+ * Device-side status of the plan's kernels since the last query: LABFM_OK, or
+ * LABFM_ETIMEOUT when a bounded wait of the staged stage kernel ran out (that
+ * step's results are then invalid).  Synchronises the device and clears the
+ * status.
+ *   status_out  host (output)
+ */
+int labfm_plan_device_status(const labfm_plan* plan, int* status_out);
+
 /* Free a plan and its device memory (synchronises the device first). NULL is a no-op. */
 int labfm_plan_destroy(labfm_plan* plan);
 

@@ -94,6 +94,8 @@ _SIGS = {
     "labfm_plan_set_dt": (_I32, [_P, _P, _P]),
     "labfm_stable_dt_instances": (_I32, [_P, _P, _P, _D, _D, _P, _P]),
     "labfm_plan_set_persistent": (_I32, [_P, _I32]),
+    "labfm_plan_set_staging": (_I32, [_P, _I32, _P]),
+    "labfm_plan_device_status": (_I32, [_P, ctypes.POINTER(_I32)]),
     "labfm_step_graph_create": (_I32, [ctypes.POINTER(_P), _P, _P, ctypes.c_size_t, _D, ctypes.POINTER(_Phys)]),
     "labfm_step_graph_run": (_I32, [_P, _P, _I32, _P]),
     "labfm_step_graph_destroy": (_I32, [_P]),
@@ -274,6 +276,17 @@ class Plan:
     def set_persistent(self, enable: bool = True) -> None:
         _check(lib.labfm_plan_set_persistent(self._h, 1 if enable else 0))
 
+    def set_staging(self, stages: int = 3, stream=None) -> None:
+        """labfm_plan_set_staging: shared-memory staging of the operator stream for the
+        F32 stage kernel with 16 or 32 lanes per node (0 = off)."""
+        _check(lib.labfm_plan_set_staging(self._h, int(stages), _stream(stream)))
+
+    def device_status(self) -> int:
+        """labfm_plan_device_status: LABFM_OK (0) or LABFM_ETIMEOUT (7); clears it."""
+        st = _I32(0)
+        _check(lib.labfm_plan_device_status(self._h, ctypes.byref(st)))
+        return st.value
+
     def __init__(self, row_ptr, col, w, kappa, s, dtype=torch.float32, stream=None):
         self.N = row_ptr.numel() - 1
         self.nnz = col.numel()
@@ -318,32 +331,41 @@ class Plan:
         return {k: getattr(pr, k) for k, _ in _Profile._fields_}
 
     def tune_step(self, Q: torch.Tensor, phys: Phys, dt: float, steps: int = 3,
-                  groups=(2, 4, 8, 16)) -> dict:
+                  groups=(2, 4, 8, 16), staged=((16, 3), (32, 3), (32, 4))) -> dict:
         """Autotune the time step itself: time `steps` RK steps (CUDA events) for every
-        lanes-per-node group and for the plain and the persistent stage kernel, keep
-        the fastest.  Q is not modified.  Returns the chosen configuration."""
+        lanes-per-node group with the plain and the persistent stage kernel, and (F32)
+        for the staged kernel at the given (lanes per node, ring slots), keep the
+        fastest.  Q is not modified.  Returns the chosen configuration."""
         info = self.info()
         block = info["block"]
+        configs = [(g, p, 0) for p in (False, True) for g in groups]
+        if self.dtype == torch.float32:
+            configs += [(g, False, k) for g, k in staged]
         best = None
-        for persistent in (False, True):
+        for g, persistent, stages in configs:
             self.set_persistent(persistent)
+            self.set_staging(stages)
+            self.set_launch(g, block)
             work = workspace(self)
-            for g in groups:
-                self.set_launch(g, block)
-                Qs = Q.clone()
-                rk_step(self, Qs, dt, 1, phys, work=work)
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                a.record()
-                rk_step(self, Qs, dt, steps, phys, work=work)
-                b.record()
-                torch.cuda.synchronize()
-                ms = a.elapsed_time(b) / steps
-                if best is None or ms < best[0]:
-                    best = (ms, persistent, g)
-        self.set_persistent(best[1])
-        self.set_launch(best[2], block)
-        return {"group": best[2], "block": block, "persistent": best[1], "ms_per_step": best[0]}
+            Qs = Q.clone()
+            rk_step(self, Qs, dt, 1, phys, work=work)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            rk_step(self, Qs, dt, steps, phys, work=work)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / steps
+            if best is None or ms < best[0]:
+                best = (ms, g, persistent, stages)
+        _, g, persistent, stages = best
+        self.set_persistent(persistent)
+        self.set_staging(stages)
+        self.set_launch(g, block)
+        if self.device_status() != 0:
+            raise LabfmError(7, "a staged stage kernel's bounded wait ran out while tuning")
+        return {"group": g, "block": block, "persistent": persistent, "staging": stages,
+                "ms_per_step": best[0]}
 
     def workspace_bytes(self) -> int:
         return int(lib.labfm_rk_workspace_bytes(self._h))

@@ -56,6 +56,8 @@ void free_plan_memory(labfm_plan* p) {
     cudaFree(p->tw);
     cudaFree(p->twf);
     cudaFree(p->rsum);
+    cudaFree(p->dev_status);
+    p->dev_status = nullptr;
     p->trow_ptr = nullptr;
     p->tw = p->twf = p->rsum = nullptr;
     delete[] p->inst_off_host;
@@ -181,6 +183,21 @@ extern "C" int labfm_plan_set_persistent(labfm_plan* p, int enable) {
     if (int rc = check_plan(p)) return rc;
     p->persistent = enable != 0;
     p->persist_grid = p->persistent ? persistent_grid(p) : 0;
+    return LABFM_OK;
+}
+
+extern "C" int labfm_plan_set_staging(labfm_plan* p, int stages, void* stream) {
+    if (int rc = check_plan(p)) return rc;
+    return configure_staging(p, stages, as_stream(stream));
+}
+
+extern "C" int labfm_plan_device_status(const labfm_plan* p, int* status_out) {
+    if (int rc = check_plan(p)) return rc;
+    if (!status_out) return set_error(LABFM_EINVAL, "null status output");
+    *status_out = LABFM_OK;
+    if (!p->dev_status) return LABFM_OK;
+    LABFM_CUDA_TRY(cudaMemcpy(status_out, p->dev_status, sizeof(int), cudaMemcpyDeviceToHost));
+    LABFM_CUDA_TRY(cudaMemset(p->dev_status, 0, sizeof(int)));
     return LABFM_OK;
 }
 

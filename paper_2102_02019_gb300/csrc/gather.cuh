@@ -29,15 +29,38 @@ constexpr double kRkB[4] = {1017324711453.0 / 9774461848756.0,
 #define LABFM_GATHER_UNROLL 1
 #endif
 // Cache hint for the operator streams (col and weights, read once per launch):
-// 0 = read-only path (ld.global.nc), 1 = evict-first (ld.global.cs).
+// 0 = read-only path (ld.global.nc), 1 = evict-first (ld.global.cs),
+// 2 = read-only without L1 allocation, so that L1 keeps the gathered fields.
 #ifndef LABFM_STREAM_HINT
 #define LABFM_STREAM_HINT 1
 #endif
 constexpr int kUnroll = LABFM_GATHER_UNROLL;
 
+__device__ __forceinline__ float4 ld_na(const float4* p) {
+    float4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+__device__ __forceinline__ int4 ld_na(const int4* p) {
+    int4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+__device__ __forceinline__ double2 ld_na(const double2* p) {
+    double2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+    return v;
+}
+
 template <typename V>
 __device__ __forceinline__ V ld_stream(const V* p) {
-#if LABFM_STREAM_HINT == 1
+#if LABFM_STREAM_HINT == 2
+    return ld_na(p);
+#elif LABFM_STREAM_HINT == 1
     return __ldcs(p);
 #else
     return __ldg(p);
@@ -75,13 +98,19 @@ __device__ __forceinline__ void load4i(const int32_t* p, int (&o)[K], int off) {
 // 1: chunk records: for every 4-entry chunk of a row, its four columns and the
 //    four weights of each of the five RHS operators in one contiguous record
 //    (96 bytes in F32); the filter has its own records (columns, kappa w^hyp).
-// 2: quad-interleaved records: four consecutive chunks form a block stored
-//    component-major (the 4 x 4 columns, then the 4 x 4 weights of each
-//    operator), so that the G lanes of a group, which take consecutive chunks,
-//    read 64 contiguous bytes with every 16-byte load instruction.
+// 2: interleaved records: kIL consecutive chunks form a block stored
+//    component-major (the kIL x 4 columns, then the kIL x 4 weights of each
+//    operator), so that lanes taking consecutive chunks read contiguous bytes
+//    with every 16-byte load instruction (64 bytes per 4 lanes for kIL = 4, 128
+//    bytes per 8 lanes for kIL = 8, the shared-memory bank width of a
+//    quarter-warp).
 #ifndef LABFM_CHUNK_AOS
 #define LABFM_CHUNK_AOS 2
 #endif
+#ifndef LABFM_CHUNK_IL
+#define LABFM_CHUNK_IL 4
+#endif
+constexpr int kIL = LABFM_CHUNK_IL;
 
 template <typename T>
 struct ChunkBytes {
@@ -96,20 +125,16 @@ template <typename T>
 struct Rec {
     static constexpr int64_t W4 = 4 * int64_t(sizeof(T));  // four weights
 #if LABFM_CHUNK_AOS == 2
-    __host__ __device__ static int64_t col(int64_t c) {
-        return (c >> 2) * 4 * ChunkBytes<T>::rhs + (c & 3) * 16;
-    }
+    static constexpr int64_t BB = int64_t(kIL) * ChunkBytes<T>::rhs;    // bytes per RHS block
+    static constexpr int64_t FB = int64_t(kIL) * ChunkBytes<T>::filt;   // bytes per filter block
+    __host__ __device__ static int64_t col(int64_t c) { return (c / kIL) * BB + (c % kIL) * 16; }
     __host__ __device__ static int64_t w(int64_t c, int d) {
-        return (c >> 2) * 4 * ChunkBytes<T>::rhs + 64 + d * 4 * W4 + (c & 3) * W4;
+        return (c / kIL) * BB + kIL * 16 + d * kIL * W4 + (c % kIL) * W4;
     }
-    __host__ __device__ static int64_t fcol(int64_t c) {
-        return (c >> 2) * 4 * ChunkBytes<T>::filt + (c & 3) * 16;
-    }
-    __host__ __device__ static int64_t fw(int64_t c) {
-        return (c >> 2) * 4 * ChunkBytes<T>::filt + 64 + (c & 3) * W4;
-    }
-    static size_t rhs_bytes(int64_t nnz_pad) { return size_t((nnz_pad / 4 + 3) / 4) * 4 * ChunkBytes<T>::rhs; }
-    static size_t filt_bytes(int64_t nnz_pad) { return size_t((nnz_pad / 4 + 3) / 4) * 4 * ChunkBytes<T>::filt; }
+    __host__ __device__ static int64_t fcol(int64_t c) { return (c / kIL) * FB + (c % kIL) * 16; }
+    __host__ __device__ static int64_t fw(int64_t c) { return (c / kIL) * FB + kIL * 16 + (c % kIL) * W4; }
+    static size_t rhs_bytes(int64_t nnz_pad) { return size_t((nnz_pad / 4 + kIL - 1) / kIL) * BB; }
+    static size_t filt_bytes(int64_t nnz_pad) { return size_t((nnz_pad / 4 + kIL - 1) / kIL) * FB; }
 #else
     __host__ __device__ static int64_t col(int64_t c) { return c * ChunkBytes<T>::rhs; }
     __host__ __device__ static int64_t w(int64_t c, int d) { return c * ChunkBytes<T>::rhs + 16 + d * W4; }
@@ -265,53 +290,62 @@ PlanView<T> view(const labfm_plan* p) {
                        static_cast<const T*>(p->wf), static_cast<const T*>(p->inv_s), p->dt_node};
 }
 
-// The 12 derivatives of eq. icns at node i: d[0..1] = (a_x, a_y),
-// d[2..6] = (u_x, u_y, u_xx, u_xy, u_yy), d[7..11] = same for v, each
-// L^d_i(phi) = sum_j (phi_j - phi_i) w^d_ji.  Every lane of the group returns them.
-template <typename T, int G, bool KAHAN, class F>
-__device__ __forceinline__ void gather_derivatives(const PlanView<T>& P, const F& fld, int i,
-                                                   int gl, T ai, T ui, T vi, T (&d)[12]) {
+// Chunk loaders for the gathers: from the plan's record stream in global memory,
+// or from a copy of a contiguous range of its blocks in shared memory.
+template <typename T>
+struct GlobalChunks {
+    const PlanView<T>& P;
+    template <int K>
+    __device__ __forceinline__ void load(int e, int (&cj)[K], T (&wx)[K], T (&wy)[K], T (&wxx)[K],
+                                         T (&wxy)[K], T (&wyy)[K], int off) const {
+        load_rhs_chunk(P, e, cj, wx, wy, wxx, wxy, wyy, off);
+    }
+};
+
+// The 12 derivatives of eq. icns at node i over its padded entries [e0, e1):
+// d[0..1] = (a_x, a_y), d[2..6] = (u_x, u_y, u_xx, u_xy, u_yy), d[7..11] = same
+// for v, each L^d_i(phi) = sum_j (phi_j - phi_i) w^d_ji.  Every lane of the
+// group returns them; an idle group (i < 0, e0 = e1) returns zeros.
+template <typename T, int G, bool KAHAN, class F, class Ld>
+__device__ __forceinline__ void gather_derivatives_ld(const Ld& ld, const F& fld, int i, int e0,
+                                                      int e1, int gl, T ai, T ui, T vi, T (&d)[12]) {
     T ax = 0, ay = 0, ux = 0, uy = 0, vx = 0, vy = 0;
     Acc<T, KAHAN> uxx, uxy, uyy, vxx, vxy, vyy;
-    if (i >= 0) {
-        const int e0 = P.row_ptr[i];
-        const int e1 = P.row_ptr[i + 1];
-        // kUnroll 4-entry chunks per iteration (chunks gl, gl + G, ... of this
-        // pass): all their operator loads are issued before the gathers
-        for (int e = e0 + 4 * gl; e < e1; e += 4 * kUnroll * G) {
-            int cj[4 * kUnroll];
-            T wx[4 * kUnroll], wy[4 * kUnroll], wxx[4 * kUnroll], wxy[4 * kUnroll], wyy[4 * kUnroll];
+    // kUnroll 4-entry chunks per iteration (chunks gl, gl + G, ... of this
+    // pass): all their operator loads are issued before the gathers
+    for (int e = e0 + 4 * gl; e < e1; e += 4 * kUnroll * G) {
+        int cj[4 * kUnroll];
+        T wx[4 * kUnroll], wy[4 * kUnroll], wxx[4 * kUnroll], wxy[4 * kUnroll], wyy[4 * kUnroll];
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const int eu = e + 4 * u * G;
-                if (u == 0 || eu < e1) {
-                    load_rhs_chunk(P, eu, cj, wx, wy, wxx, wxy, wyy, 4 * u);
-                } else {
+        for (int u = 0; u < kUnroll; ++u) {
+            const int eu = e + 4 * u * G;
+            if (u == 0 || eu < e1) {
+                ld.load(eu, cj, wx, wy, wxx, wxy, wyy, 4 * u);
+            } else {
 #pragma unroll
-                    for (int k = 4 * u; k < 4 * u + 4; ++k) {
-                        cj[k] = i;  // the node itself with zero weight adds exactly 0
-                        wx[k] = wy[k] = wxx[k] = wxy[k] = wyy[k] = T(0);
-                    }
+                for (int k = 4 * u; k < 4 * u + 4; ++k) {
+                    cj[k] = i;  // the node itself with zero weight adds exactly 0
+                    wx[k] = wy[k] = wxx[k] = wxy[k] = wyy[k] = T(0);
                 }
             }
+        }
 #pragma unroll
-            for (int k = 0; k < 4 * kUnroll; ++k) {
-                T aj, uj, vj;
-                fld.get(cj[k], aj, uj, vj);
-                const T da = aj - ai, du = uj - ui, dv = vj - vi;
-                ax = fma(da, wx[k], ax);
-                ay = fma(da, wy[k], ay);
-                ux = fma(du, wx[k], ux);
-                uy = fma(du, wy[k], uy);
-                vx = fma(dv, wx[k], vx);
-                vy = fma(dv, wy[k], vy);
-                uxx.add(du * wxx[k]);
-                uxy.add(du * wxy[k]);
-                uyy.add(du * wyy[k]);
-                vxx.add(dv * wxx[k]);
-                vxy.add(dv * wxy[k]);
-                vyy.add(dv * wyy[k]);
-            }
+        for (int k = 0; k < 4 * kUnroll; ++k) {
+            T aj, uj, vj;
+            fld.get(cj[k], aj, uj, vj);
+            const T da = aj - ai, du = uj - ui, dv = vj - vi;
+            ax = fma(da, wx[k], ax);
+            ay = fma(da, wy[k], ay);
+            ux = fma(du, wx[k], ux);
+            uy = fma(du, wy[k], uy);
+            vx = fma(dv, wx[k], vx);
+            vy = fma(dv, wy[k], vy);
+            uxx.add(du * wxx[k]);
+            uxy.add(du * wxy[k]);
+            uyy.add(du * wyy[k]);
+            vxx.add(dv * wxx[k]);
+            vxy.add(dv * wxy[k]);
+            vyy.add(dv * wyy[k]);
         }
     }
     d[0] = group_sum<G>(ax);
@@ -336,6 +370,17 @@ __device__ __forceinline__ void gather_derivatives(const PlanView<T>& P, const F
         d[10] = group_sum<G>(vxy.s);
         d[11] = group_sum<G>(vyy.s);
     }
+}
+
+template <typename T, int G, bool KAHAN, class F>
+__device__ __forceinline__ void gather_derivatives(const PlanView<T>& P, const F& fld, int i,
+                                                   int gl, T ai, T ui, T vi, T (&d)[12]) {
+    int e0 = 0, e1 = 0;
+    if (i >= 0) {
+        e0 = P.row_ptr[i];
+        e1 = P.row_ptr[i + 1];
+    }
+    gather_derivatives_ld<T, G, KAHAN>(GlobalChunks<T>{P}, fld, i, e0, e1, gl, ai, ui, vi, d);
 }
 
 __device__ __forceinline__ float exp_neg(float a) { return expf(-a); }

@@ -73,6 +73,14 @@ struct labfm_plan {
     double* dt_node = nullptr;   // per-node time step (labfm_plan_set_dt), or null
     bool persistent = false;     // stage kernel takes node tiles from a work queue
     int persist_grid = 0;
+    // F32 stage kernel with the operator staged through shared memory
+    // (labfm_plan_set_staging): `stages` ring slots per CTA; for 16 and 32 lanes
+    // per node ([0], [1]) the bytes of the largest round and the grid (0 = the
+    // shape does not fit in shared memory)
+    int stages = 0;
+    int stage_slot_bytes[2] = {0, 0};
+    int stage_grid[2] = {0, 0};
+    int* dev_status = nullptr;   // device word: LABFM_ETIMEOUT after a bounded wait ran out
     // transposed operator for the adjoint (labfm_plan_enable_adjoint): for node k
     // the entries (i, w_ik) of every row i whose stencil contains k, in the same
     // record layout as the forward operator, plus row sums of the forward weights
@@ -139,5 +147,7 @@ int forward_stage_states(const labfm_plan* p, const void* X1, void* P, void* X2,
 int launch_stable_dt_instances(const labfm_plan* p, const void* fields, const double* s, double c,
                                double mu, double* dt_inst, cudaStream_t st);
 int persistent_grid(const labfm_plan* p);
+// Configure the staged F32 stage kernel for `stages` ring slots (0 = off); synchronises.
+int configure_staging(labfm_plan* p, int stages, cudaStream_t st);
 
 }  // namespace labfm

@@ -19,6 +19,7 @@
 #include <string>
 #include <type_traits>
 
+#include "bulk.cuh"
 #include "gather.cuh"
 #include "labfm_internal.cuh"
 
@@ -58,20 +59,17 @@ __global__ void LABFM_STAGE_BOUNDS k_rhs_soa(PlanView<T> P, SoA<T> in, T* __rest
     }
 }
 
-// One fused RK stage at node i (i < 0: an idle group that still joins the
-// shuffles): F = R(X_in); Q_out = Q_in + dt_i b_k F; X_out = Q_out + dt_i (a - b) F
-// (skipped when X_out is null).  Q_in may equal Q_out, and Q_in may equal X_in
-// (first stage, where X = Q).  dt_i is the uniform dt or the plan's per-node dt.
-template <typename T, int G, bool KAHAN, bool SCALED>
-__device__ __forceinline__ void stage_node(const PlanView<T>& P, int i, int gl,
-                                           const Packed<T>* X_in, const Packed<T>* Q_in,
-                                           Packed<T>* Q_out, Packed<T>* X_out, double dt,
-                                           double bk, double ck, const Phys<T>& ph) {
-    const AoS<T> fld{X_in};
-    T ai = 0, ui = 0, vi = 0;
-    if (i >= 0) fld.get(i, ai, ui, vi);
-    T d[12];
-    gather_derivatives<T, G, KAHAN>(P, fld, i, gl, ai, ui, vi, d);
+// The RK stage update at node i from its 12 derivatives: F = R(X_in);
+// Q_out = Q_in + dt_i b_k F; X_out = Q_out + dt_i (a - b) F (skipped when X_out
+// is null).  Q_in may equal Q_out, and Q_in may equal X_in (first stage, where
+// X = Q).  dt_i is the uniform dt or the plan's per-node dt.  Lane 0 of the
+// group stores.
+template <typename T, bool SCALED>
+__device__ __forceinline__ void stage_epilogue(const PlanView<T>& P, int i, int gl, const T (&d)[12],
+                                               T ai, T ui, T vi, const Packed<T>* X_in,
+                                               const Packed<T>* Q_in, Packed<T>* Q_out,
+                                               Packed<T>* X_out, double dt, double bk, double ck,
+                                               const Phys<T>& ph) {
     if (i >= 0 && gl == 0) {
         T Ra, Ru, Rv;
         const T is = SCALED ? P.inv_s[i] : T(1);
@@ -92,6 +90,21 @@ __device__ __forceinline__ void stage_node(const PlanView<T>& P, int i, int gl,
         store(Q_out, i, qa, qu, qv);
         if (X_out) store(X_out, i, fma(cx, Ra, qa), fma(cx, Ru, qu), fma(cx, Rv, qv));
     }
+}
+
+// One fused RK stage at node i (i < 0: an idle group that still joins the
+// shuffles).
+template <typename T, int G, bool KAHAN, bool SCALED>
+__device__ __forceinline__ void stage_node(const PlanView<T>& P, int i, int gl,
+                                           const Packed<T>* X_in, const Packed<T>* Q_in,
+                                           Packed<T>* Q_out, Packed<T>* X_out, double dt,
+                                           double bk, double ck, const Phys<T>& ph) {
+    const AoS<T> fld{X_in};
+    T ai = 0, ui = 0, vi = 0;
+    if (i >= 0) fld.get(i, ai, ui, vi);
+    T d[12];
+    gather_derivatives<T, G, KAHAN>(P, fld, i, gl, ai, ui, vi, d);
+    stage_epilogue<T, SCALED>(P, i, gl, d, ai, ui, vi, X_in, Q_in, Q_out, X_out, dt, bk, ck, ph);
 }
 
 // Nodes per work-queue tile of the persistent stage kernel, per warp.
@@ -130,6 +143,157 @@ __global__ void LABFM_STAGE_BOUNDS k_stage(PlanView<T> P, const Packed<T>* X_in,
             stage_node<T, G, KAHAN, SCALED>(P, i, lane % G, X_in, Q_in, Q_out, X_out, dt, bk, ck, ph);
         }
     }
+}
+
+// ---------------------------------------------------------------- staged stage kernel
+//
+// F32 stage kernel with the operator stream staged through shared memory by the
+// bulk-copy (TMA) engine.  The nodes are cut into rounds of kRoundWarps x 32/G
+// consecutive nodes, one per group of G lanes.  The interleaved blocks holding a
+// round's chunks are one contiguous byte range of the plan, so one
+// cp.async.bulk moves a round into a ring slot whose mbarrier counts the bytes.
+// CTA b takes rounds b, b + gridDim.x, ... and keeps S rounds in flight, so the
+// copy engine, not the registers of the consumer warps, holds the loads in
+// flight.  Neighbour fields are gathered from global memory as in k_stage.  A
+// wait that runs out (1 s) sets *status = LABFM_ETIMEOUT; the CTA then lets its
+// copies in flight land (bounded again) and returns.
+constexpr int kBulkBlock = 128;
+constexpr int kRoundWarps = kBulkBlock / 32;
+constexpr uint64_t kBulkWaitNs = 1000000000ull;
+
+template <int G>
+constexpr int round_nodes() {
+    return kRoundWarps * (32 / G);
+}
+
+struct RoundRange {
+    int64_t off;     // byte offset of the round's first block in the RHS record stream
+    uint32_t bytes;  // whole blocks, a multiple of 16
+};
+
+__device__ __forceinline__ RoundRange round_range(const int32_t* row_ptr, int64_t N, int64_t r, int rn) {
+    const int64_t n0 = r * rn;
+    const int64_t n1 = n0 + rn < N ? n0 + rn : N;
+    const int64_t c0 = row_ptr[n0] >> 2;
+    const int64_t c1 = row_ptr[n1] >> 2;
+    const int64_t b0 = c0 / kIL;
+    const int64_t b1 = (c1 + kIL - 1) / kIL;
+    return {b0 * Rec<float>::BB, uint32_t((b1 - b0) * Rec<float>::BB)};
+}
+
+// Chunk loads from a ring slot holding the blocks from byte `off` of the stream.
+struct SharedChunks {
+    const unsigned char* slot;
+    int64_t off;
+    template <int K>
+    __device__ __forceinline__ void load(int e, int (&cj)[K], float (&wx)[K], float (&wy)[K],
+                                         float (&wxx)[K], float (&wxy)[K], float (&wyy)[K],
+                                         int o) const {
+        const int64_t c = e >> 2;
+        const int4 ci = *reinterpret_cast<const int4*>(slot + (Rec<float>::col(c) - off));
+        cj[o] = ci.x;
+        cj[o + 1] = ci.y;
+        cj[o + 2] = ci.z;
+        cj[o + 3] = ci.w;
+        get4(c, 0, wx, o);
+        get4(c, 1, wy, o);
+        get4(c, 2, wxx, o);
+        get4(c, 3, wxy, o);
+        get4(c, 4, wyy, o);
+    }
+    template <int K>
+    __device__ __forceinline__ void get4(int64_t c, int d, float (&w)[K], int o) const {
+        const float4 v = *reinterpret_cast<const float4*>(slot + (Rec<float>::w(c, d) - off));
+        w[o] = v.x;
+        w[o + 1] = v.y;
+        w[o + 2] = v.z;
+        w[o + 3] = v.w;
+    }
+};
+
+__device__ __forceinline__ void issue_round(const PlanView<float>& P, int64_t r, int rn,
+                                            unsigned char* slot, uint64_t* bar, uint64_t policy) {
+    const RoundRange rr = round_range(P.row_ptr, P.N, r, rn);
+    mbar_arrive_expect_tx(smem_u32(bar), rr.bytes);
+    if (rr.bytes)
+        bulk_g2s(smem_u32(slot), reinterpret_cast<const char*>(P.w) + rr.off, rr.bytes, smem_u32(bar),
+                 policy);
+}
+
+template <int G, int S>
+__global__ void __launch_bounds__(kBulkBlock)
+    k_stage_bulk(PlanView<float> P, const Packed<float>* X_in, const Packed<float>* Q_in,
+                 Packed<float>* Q_out, Packed<float>* X_out, double dt, double bk, double ck,
+                 Phys<float> ph, uint32_t slot_bytes, int* status) {
+    extern __shared__ __align__(128) unsigned char ring[];
+    __shared__ __align__(8) uint64_t full[S];
+    constexpr int RN = round_nodes<G>();
+    const int t = threadIdx.x;
+    const int64_t nrounds = (P.N + RN - 1) / RN;
+    if (t == 0) {
+#pragma unroll
+        for (int k = 0; k < S; ++k) mbar_init(smem_u32(&full[k]), 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    uint64_t policy = 0;
+    if (t == 0) {
+        policy = l2_evict_first_policy();
+        for (int k = 0; k < S; ++k) {
+            const int64_t r = blockIdx.x + int64_t(k) * gridDim.x;
+            if (r >= nrounds) break;
+            issue_round(P, r, RN, ring + size_t(k) * slot_bytes, &full[k], policy);
+        }
+    }
+    const int lane = t & 31;
+    const int gl = lane % G;
+    const AoS<float> fld{X_in};
+    int it = 0;
+    for (int64_t r = blockIdx.x; r < nrounds; r += gridDim.x, ++it) {
+        const int slot = it % S;
+        const bool ok = mbar_wait_bounded(smem_u32(&full[slot]), uint32_t(it / S) & 1u, kBulkWaitNs);
+        if (__syncthreads_or(!ok)) {
+            if (t == 0) {
+                atomicExch(status, LABFM_ETIMEOUT);
+                for (int k = 0; k < S; ++k) {  // copies still in flight land before exit
+                    const int j = it + k;
+                    if (blockIdx.x + int64_t(j) * gridDim.x >= nrounds) break;
+                    mbar_wait_bounded(smem_u32(&full[j % S]), uint32_t(j / S) & 1u, kBulkWaitNs);
+                }
+            }
+            return;
+        }
+        const RoundRange rr = round_range(P.row_ptr, P.N, r, RN);
+        const SharedChunks ld{ring + size_t(slot) * slot_bytes, rr.off};
+        const int64_t node = r * RN + (t >> 5) * (32 / G) + lane / G;
+        const int i = node < P.N ? int(node) : -1;
+        float ai = 0, ui = 0, vi = 0;
+        int e0 = 0, e1 = 0;
+        if (i >= 0) {
+            fld.get(i, ai, ui, vi);
+            e0 = P.row_ptr[i];
+            e1 = P.row_ptr[i + 1];
+        }
+        float d[12];
+        gather_derivatives_ld<float, G, true>(ld, fld, i, e0, e1, gl, ai, ui, vi, d);
+        stage_epilogue<float, true>(P, i, gl, d, ai, ui, vi, X_in, Q_in, Q_out, X_out, dt, bk, ck, ph);
+        __syncthreads();  // the slot is free: every thread has read its chunks
+        if (t == 0) {
+            const int64_t rn = r + int64_t(S) * gridDim.x;
+            if (rn < nrounds) {
+                fence_proxy_async_smem();
+                issue_round(P, rn, RN, ring + size_t(slot) * slot_bytes, &full[slot], policy);
+            }
+        }
+    }
+}
+
+// Bytes of the largest round (whole interleaved blocks) for rn nodes per round.
+__global__ void k_max_round_bytes(const int32_t* row_ptr, int64_t N, int rn, unsigned int* out) {
+    const int64_t nrounds = (N + rn - 1) / rn;
+    for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < nrounds;
+         r += int64_t(gridDim.x) * blockDim.x)
+        atomicMax(out, round_range(row_ptr, N, r, rn).bytes);
 }
 
 // Filter: out_i = phi_i + sum_j (phi_j - phi_i) (kappa_i w^hyp_ji) for 3 fields.
@@ -362,10 +526,48 @@ int stage_launch_g(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* q
     return LABFM_OK;
 }
 
+template <int G, int S>
+int stage_bulk_launch(const labfm_plan* p, const Packed<float>* xin, const Packed<float>* qin,
+                      Packed<float>* qout, Packed<float>* xout, double dt, double bk, double ck,
+                      const Phys<float>& ph, cudaStream_t st) {
+    const int gi = G == 32 ? 1 : 0;
+    const uint32_t slot = uint32_t(p->stage_slot_bytes[gi]);
+    k_stage_bulk<G, S><<<p->stage_grid[gi], kBulkBlock, size_t(S) * slot, st>>>(
+        view<float>(p), xin, qin, qout, xout, dt, bk, ck, ph, slot, p->dev_status);
+    LABFM_LAUNCH_CHECK("staged rk stage kernel");
+    return LABFM_OK;
+}
+
+template <int G>
+int stage_bulk_launch_s(const labfm_plan* p, const Packed<float>* xin, const Packed<float>* qin,
+                        Packed<float>* qout, Packed<float>* xout, double dt, double bk, double ck,
+                        const Phys<float>& ph, cudaStream_t st) {
+    switch (p->stages) {
+        case 2: return stage_bulk_launch<G, 2>(p, xin, qin, qout, xout, dt, bk, ck, ph, st);
+        case 3: return stage_bulk_launch<G, 3>(p, xin, qin, qout, xout, dt, bk, ck, ph, st);
+        case 4: return stage_bulk_launch<G, 4>(p, xin, qin, qout, xout, dt, bk, ck, ph, st);
+    }
+    return set_error(LABFM_EINVAL, "unsupported number of staging slots");
+}
+
+// The staged kernel serves F32 plans with staging on and 16 or 32 lanes per node
+// whose largest round fits in shared memory; every other case runs k_stage.
+bool staged(const labfm_plan* p) {
+    if (p->dtype != LABFM_F32 || p->stages == 0) return false;
+    if (p->group != 16 && p->group != 32) return false;
+    return p->stage_grid[p->group == 32 ? 1 : 0] > 0;
+}
+
 template <typename T>
 int stage_launch(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* qin, Packed<T>* qout,
                  Packed<T>* xout, double dt, double bk, double ck, const Phys<T>& ph, int* counter,
                  cudaStream_t st) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (staged(p)) {
+            if (p->group == 32) return stage_bulk_launch_s<32>(p, xin, qin, qout, xout, dt, bk, ck, ph, st);
+            return stage_bulk_launch_s<16>(p, xin, qin, qout, xout, dt, bk, ck, ph, st);
+        }
+    }
     switch (p->group) {
         case 2: return stage_launch_g<T, 2>(p, xin, qin, qout, xout, dt, bk, ck, ph, counter, st);
         case 4: return stage_launch_g<T, 4>(p, xin, qin, qout, xout, dt, bk, ck, ph, counter, st);
@@ -786,6 +988,77 @@ int launch_stable_dt_instances(const labfm_plan* p, const void* fields, const do
         k_dt_instances<double><<<grid, 256, 0, st>>>(p->N, static_cast<const double*>(fields), s, c,
                                                      mu, p->inst_off, p->n_inst, out);
     LABFM_LAUNCH_CHECK("instance dt kernel");
+    return LABFM_OK;
+}
+
+}  // namespace labfm
+
+namespace labfm {
+namespace {
+template <int G, int S>
+int staging_shape(labfm_plan* p, int gi, size_t slot, int sms) {
+    const size_t smem = size_t(S) * slot;
+    p->stage_slot_bytes[gi] = int(slot);
+    p->stage_grid[gi] = 0;
+    if (smem > size_t(226) * 1024) return LABFM_OK;  // this shape does not fit (static smem too)
+    LABFM_CUDA_TRY(cudaFuncSetAttribute(k_stage_bulk<G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        int(smem)));
+    int per_sm = 0;
+    LABFM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage_bulk<G, S>, kBulkBlock,
+                                                                 smem));
+    const int64_t nrounds = (p->N + round_nodes<G>() - 1) / round_nodes<G>();
+    p->stage_grid[gi] = int(std::min<int64_t>(nrounds, int64_t(per_sm) * sms));
+    return LABFM_OK;
+}
+
+template <int G>
+int staging_shape_s(labfm_plan* p, int gi, size_t slot, int sms) {
+    switch (p->stages) {
+        case 2: return staging_shape<G, 2>(p, gi, slot, sms);
+        case 3: return staging_shape<G, 3>(p, gi, slot, sms);
+        default: return staging_shape<G, 4>(p, gi, slot, sms);
+    }
+}
+}  // namespace
+
+int configure_staging(labfm_plan* p, int stages, cudaStream_t st) {
+    p->stages = 0;
+    p->stage_slot_bytes[0] = p->stage_slot_bytes[1] = 0;
+    p->stage_grid[0] = p->stage_grid[1] = 0;
+    if (stages == 0) return LABFM_OK;
+    if (p->dtype != LABFM_F32) return set_error(LABFM_EINVAL, "staging serves F32 plans only");
+    if (stages < 2 || stages > 4) return set_error(LABFM_EINVAL, "stages must be 0 or 2..4");
+    if (!p->dev_status) {
+        LABFM_CUDA_TRY(cudaMalloc(&p->dev_status, sizeof(int)));
+        p->device_bytes += sizeof(int);
+    }
+    LABFM_CUDA_TRY(cudaMemsetAsync(p->dev_status, 0, sizeof(int), st));
+    int dev = 0, sms = 0;
+    LABFM_CUDA_TRY(cudaGetDevice(&dev));
+    LABFM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    unsigned int* d_max = nullptr;
+    LABFM_CUDA_TRY(cudaMallocAsync(&d_max, 2 * sizeof(unsigned int), st));
+    cudaError_t e = cudaMemsetAsync(d_max, 0, 2 * sizeof(unsigned int), st);
+    const int grid = int(std::min<int64_t>((p->N + 255) / 256 + 1, 4096));
+    if (e == cudaSuccess) {
+        k_max_round_bytes<<<grid, 256, 0, st>>>(p->row_ptr, p->N, round_nodes<16>(), d_max);
+        k_max_round_bytes<<<grid, 256, 0, st>>>(p->row_ptr, p->N, round_nodes<32>(), d_max + 1);
+        e = cudaGetLastError();
+    }
+    unsigned int h_max[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_max, d_max, sizeof(h_max), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFreeAsync(d_max, st);
+    if (e != cudaSuccess) return cuda_error(e, "staging: largest round");
+    p->stages = stages;
+    for (int gi = 0; gi < 2; ++gi) {
+        const size_t slot = std::max<size_t>(h_max[gi], 16);
+        const int rc = gi ? staging_shape_s<32>(p, gi, slot, sms) : staging_shape_s<16>(p, gi, slot, sms);
+        if (rc) {
+            p->stages = 0;
+            return rc;
+        }
+    }
     return LABFM_OK;
 }
 
