@@ -183,6 +183,7 @@ __device__ __forceinline__ RoundRange round_range(const int32_t* row_ptr, int64_
 
 // Chunk loads from a ring slot holding the blocks from byte `off` of the stream.
 struct SharedChunks {
+    static constexpr bool kColAhead = false;
     const unsigned char* slot;
     int64_t off;
     template <int K>
@@ -425,6 +426,26 @@ __global__ void k_padded_counts(int64_t N, const int32_t* __restrict__ row_ptr,
 
 // Warp per row: copy col, scale the RHS weights (F32: w s^l), fold kappa into
 // the filter weights, and fill the pad entries (self, weight 0).
+// Slot of padded row entry e (0 <= e < plen, plen a multiple of 4) within its
+// row.  With LABFM_ENTRY_PERM, each segment of up to 16 entries (nc chunks) is
+// transposed so that chunk q holds entries q, q + nc, q + 2 nc, q + 3 nc: lanes
+// that take consecutive chunks then gather consecutive stencil entries (mostly
+// neighbouring nodes) with each load instruction.
+#ifndef LABFM_ENTRY_PERM
+#define LABFM_ENTRY_PERM 1
+#endif
+__device__ __forceinline__ int entry_slot(int e, int plen) {
+#if LABFM_ENTRY_PERM
+    const int base = e & ~15;
+    const int nc = min(16, plen - base) >> 2;
+    const int r = e - base;
+    return base + 4 * (r % nc) + r / nc;
+#else
+    (void)plen;
+    return e;
+#endif
+}
+
 template <typename T, bool SCALED>
 __global__ void k_pack_rows(int64_t N, int64_t nnz, int64_t nnz_pad, int64_t off,
                             const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -444,7 +465,7 @@ __global__ void k_pack_rows(int64_t N, int64_t nnz, int64_t nnz_pad, int64_t off
         const double sc2 = SCALED ? si * si : 1.0;
         const double kap = kappa[il];
         for (int e = lane; e < plen; e += 32) {
-            const int64_t dst = int64_t(p0) + e;
+            const int64_t dst = int64_t(p0) + entry_slot(e, plen);
             int32_t c = int32_t(i);
             T v[5] = {T(0), T(0), T(0), T(0), T(0)};
             T vf = T(0);
