@@ -63,6 +63,7 @@ __device__ __forceinline__ double wendland_c2(double q) {
 struct NodeGeom {
     double xi, yi, hi, Lx, Ly;
     bool px, py;
+    double ih;  // 1 / hi
 };
 
 // Per-neighbour 1D factors: powers (x/h)^a, (y/h)^b and Hermite values
@@ -77,12 +78,12 @@ __device__ __forceinline__ void neighbour_factors(const double* __restrict__ xy,
     const double dy = min_image(__dsub_rn(xy[2 * j + 1], g.yi), g.Ly, g.py);
     *dxo = dx;
     *dyo = dy;
-    const double xh = dx / g.hi;
-    const double yh = dy / g.hi;
-    *psi = wendland_c2(sqrt(dx * dx + dy * dy) / g.hi);
-    const double hs2 = g.hi * 1.4142135623730951;  // h sqrt(2)
-    const double zx = dx / hs2;
-    const double zy = dy / hs2;
+    const double xh = dx * g.ih;
+    const double yh = dy * g.ih;
+    *psi = wendland_c2(sqrt(dx * dx + dy * dy) * g.ih);
+    const double ihs2 = g.ih * 0.70710678118654752440;  // 1 / (h sqrt 2)
+    const double zx = dx * ihs2;
+    const double zy = dy * ihs2;
     px[0] = 1.0;
     py[0] = 1.0;
     hx[0] = 1.0;
@@ -189,9 +190,9 @@ __device__ void block_moments(const double* __restrict__ xy, const int32_t* __re
             const int j = col[c0 + t];
             const double dx = min_image(__dsub_rn(xy[2 * j], g.xi), g.Lx, g.px);
             const double dy = min_image(__dsub_rn(xy[2 * j + 1], g.yi), g.Ly, g.py);
-            const double xh = dx / g.hi;
-            const double yh = dy / g.hi;
-            double xp = wendland_c2(sqrt(dx * dx + dy * dy) / g.hi), yp = 1.0;
+            const double xh = dx * g.ih;
+            const double yh = dy * g.ih;
+            double xp = wendland_c2(sqrt(dx * dx + dy * dy) * g.ih), yp = 1.0;
             double* xr = XP + t * NPOW;
             double* yr = YP + t * NPOW;
 #pragma unroll
@@ -232,11 +233,13 @@ __device__ void block_assemble(double* A, double* A0, const double* s_mu, const 
         exps_of(c, ac, bc);
         double sum = 0.0;
         for (int k = ac; k >= 0; k -= 2) {
-            const double hk = s_he[ac * (M + 1) + k];
+            const int pp = ar + k;
+            double inner = 0.0;  // sum_l he_{b_c,l} mu_{a_r+k, b_r+l}
             for (int l = bc; l >= 0; l -= 2) {
-                const int pp = ar + k, qq = br + l, dd = pp + qq;
-                sum = fma(hk * s_he[bc * (M + 1) + l], s_mu[dd * (dd + 1) / 2 + (dd - pp)], sum);
+                const int dd = pp + br + l;
+                inner = fma(s_he[bc * (M + 1) + l], s_mu[dd * (dd + 1) / 2 + (dd - pp)], inner);
             }
+            sum = fma(s_he[ac * (M + 1) + k], inner, sum);
         }
         const double v = sum * (inv_factorial(ar) * inv_factorial(br));
         A[r * LDA + c] = v;
@@ -246,10 +249,12 @@ __device__ void block_assemble(double* A, double* A0, const double* s_mu, const 
 
 // Gaussian elimination with partial pivoting (the first row holding the largest
 // |pivot| wins) on the augmented system [M | B] (n x LDA, NRHS = LDA - n right-hand
-// sides), then back substitution by warp 0: the solutions overwrite B.  Returns
-// true (uniformly) if a pivot was zero or not finite.  Starts and ends with a barrier.
+// sides), then back substitution by warp 0: the solutions overwrite B.  Each
+// pivot's reciprocal is taken once during the elimination (lane 0 of warp 0, kept
+// in s_rdiag[n]) and the back substitution multiplies by it.  Returns true
+// (uniformly) if a pivot was zero or not finite.  Starts and ends with a barrier.
 template <int M, int LDA>
-__device__ bool block_lu_solve(double* A, int* s_piv, int* s_flag) {
+__device__ bool block_lu_solve(double* A, int* s_piv, int* s_flag, double* s_rdiag) {
     using C = WCfg<M>;
     constexpr int n = C::n, NT = C::NT, NRHS = LDA - n;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -277,7 +282,11 @@ __device__ bool block_lu_solve(double* A, int* s_piv, int* s_flag) {
             }
             if (lane == 0) {
                 *s_piv = bidx;
-                if (!(best > 0.0) || !isfinite(best) || bidx >= n) *s_flag = 1;
+                if (!(best > 0.0) || !isfinite(best) || bidx >= n) {
+                    *s_flag = 1;
+                } else {
+                    s_rdiag[k] = 1.0 / A[bidx * LDA + k];
+                }
             }
         }
         __syncthreads();
@@ -307,8 +316,8 @@ __device__ bool block_lu_solve(double* A, int* s_piv, int* s_flag) {
     static_assert(NRHS <= 32, "one lane per right-hand side");
     if (!singular && warp == 0) {
         for (int k = n - 1; k >= 0; --k) {
-            // lane d divides right-hand side d (one division sequence for the warp)
-            const double mine = lane < NRHS ? A[k * LDA + n + lane] / A[k * LDA + k] : 0.0;
+            // lane d scales right-hand side d
+            const double mine = lane < NRHS ? A[k * LDA + n + lane] * s_rdiag[k] : 0.0;
             double psi[NRHS];
 #pragma unroll
             for (int d = 0; d < NRHS; ++d) psi[d] = __shfl_sync(0xffffffffu, mine, d);
@@ -360,6 +369,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
     __shared__ int s_flag;
     __shared__ int s_nonfinite;
     __shared__ double s_red[NT / 32];
+    __shared__ double s_rdiag[n];
     __shared__ double s_hp[2 * M + 1];  // h^k, k = -M..M, at [k + M]
 
     const int64_t i = blockIdx.x;
@@ -367,7 +377,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int warp = t >> 5;
-    NodeGeom g{xy[2 * i], xy[2 * i + 1], h[i], Lx, Ly, px_ != 0, py_ != 0};
+    NodeGeom g{xy[2 * i], xy[2 * i + 1], h[i], Lx, Ly, px_ != 0, py_ != 0, 1.0 / h[i]};
     const int r0 = row_ptr[i];
     const int r1 = row_ptr[i + 1];
     if (r1 - r0 < n) {  // M_i singular: fewer stencil nodes than unknowns
@@ -392,7 +402,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
         exps_of(q, a, b);
         A[q * LDA + n + d] = selector_coef<M>(d, a, b) * s_hp[M - (a + b)];
     }
-    const bool singular = block_lu_solve<M, LDA>(A, &s_piv, &s_flag);
+    const bool singular = block_lu_solve<M, LDA>(A, &s_piv, &s_flag, s_rdiag);
 
     // ---- residual of eq. lsys in nondimensional form: (M Psi^d - C~^d)_q h^l
     if (RESID) {
@@ -421,7 +431,33 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
         __syncthreads();
     }
 
-    // ---- weights w^d_j = W_j . Psi^d and the filter sum F_0
+    // ---- weights w^d_j = W_j . Psi^d and the filter sum F_0.  With W = psi He_a(x/h)
+    // He_b(y/h), W_j . Psi^d = psi_j P^d(x/h, y/h) for the polynomial
+    // P^d = sum_{a,b} Psi^d_ab He_a He_b = sum_{p+q<=M} c^d_pq x^p y^q, whose
+    // coefficients follow from the Hermite expansions once per node; each
+    // neighbour then takes P^d by Horner's rule (x outer, y inner).
+    constexpr int NC = (M + 1) * (M + 2) / 2;
+    __shared__ double s_cf[NC * 6];
+    if (!singular) {
+        for (int idx = t; idx < NC * 6; idx += NT) {
+            const int pq = idx / 6, d = idx - pq * 6;
+            int p = 0;
+            while (pq >= (p + 1) * (2 * M + 2 - p) / 2) ++p;
+            const int qy = pq - p * (2 * M + 3 - p) / 2;
+            double c = 0.0;
+            for (int a = p; a <= M; a += 2) {
+                const double ha = s_he[a * (M + 1) + p];
+                for (int b = qy; a + b <= M; b += 2) {
+                    const int k = a + b;
+                    if (k == 0) continue;  // X has no constant monomial
+                    const int q = k * (k + 1) / 2 - 1 + b;
+                    c = fma(ha * s_he[b * (M + 1) + qy], A[q * LDA + n + d], c);
+                }
+            }
+            s_cf[idx] = c;
+        }
+    }
+    __syncthreads();
     const double kx = 3.0 * 3.141592653589793 / (2.0 * s[i]);
     double f0 = 0.0;
     bool bad = false;
@@ -429,18 +465,26 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
         double wd[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         double dx = 0.0, dy = 0.0;
         if (!singular) {
-            double pxv[M + 1], pyv[M + 1], hxv[M + 1], hyv[M + 1], psi;
-            neighbour_factors<M>(xy, col[e], g, pxv, pyv, hxv, hyv, &psi, &dx, &dy);
-            int q = 0;
+            const int j = col[e];
+            dx = min_image(__dsub_rn(xy[2 * j], g.xi), g.Lx, g.px);
+            dy = min_image(__dsub_rn(xy[2 * j + 1], g.yi), g.Ly, g.py);
+            const double xh = dx * g.ih, yh = dy * g.ih;
+            const double psi = wendland_c2(sqrt(dx * dx + dy * dy) * g.ih);
+#pragma unroll 1
+            for (int p = M; p >= 0; --p) {
+                const double* cp = s_cf + (p * (2 * M + 3 - p) / 2) * 6;  // (p, 0)
+                double in[6];
 #pragma unroll
-            for (int k = 1; k <= M; ++k) {
+                for (int d = 0; d < 6; ++d) in[d] = cp[(M - p) * 6 + d];
+#pragma unroll 1
+                for (int qq = M - p - 1; qq >= 0; --qq)
 #pragma unroll
-                for (int a = k; a >= 0; --a, ++q) {
-                    const double Wq = psi * hxv[a] * hyv[k - a] * inv_sqrt2_pow(k);
+                    for (int d = 0; d < 6; ++d) in[d] = fma(in[d], yh, cp[qq * 6 + d]);
 #pragma unroll
-                    for (int d = 0; d < 6; ++d) wd[d] = fma(Wq, A[q * LDA + n + d], wd[d]);
-                }
+                for (int d = 0; d < 6; ++d) wd[d] = fma(wd[d], xh, in[d]);
             }
+#pragma unroll
+            for (int d = 0; d < 6; ++d) wd[d] *= psi;
         }
 #pragma unroll
         for (int d = 0; d < 6; ++d) {
@@ -583,6 +627,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
     __shared__ double s_psi[3 * n];
     __shared__ double s_hp[M + 1];
     __shared__ double s_amax;
+    __shared__ double s_rdiag[n];
     __shared__ int s_piv;
     __shared__ int s_flag;
 
@@ -593,7 +638,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
     const int r1 = row_ptr[i + 1];
     const double eps = 2.220446049250313e-16;
     build_he<M>(s_he);
-    NodeGeom g{xy[2 * i], xy[2 * i + 1], h0[i], Lx, Ly, px_ != 0, py_ != 0};
+    NodeGeom g{xy[2 * i], xy[2 * i + 1], h0[i], Lx, Ly, px_ != 0, py_ != 0, 1.0 / h0[i]};
     double best = h0[i];
     int solves = 0;
     for (int it = 0; it < max_iter; ++it) {
@@ -621,7 +666,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
             else coef = ((a == 2 && b == 0) || (a == 0 && b == 2)) ? 1.0 : 0.0;
             A[q * LDA + n + d] = coef * s_hp[a + b];
         }
-        const bool singular = block_lu_solve<M, LDA>(A, &s_piv, &s_flag);
+        const bool singular = block_lu_solve<M, LDA>(A, &s_piv, &s_flag, s_rdiag);
         ++solves;
         if (singular) break;
         double r2 = 0.0;
@@ -643,6 +688,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
         // step 5
         best = g.hi;
         g.hi = g.hi * factor;
+        g.ih = 1.0 / g.hi;
         __syncthreads();
     }
     if (t == 0) {

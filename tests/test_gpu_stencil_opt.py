@@ -77,17 +77,47 @@ def _opt_case(lb, m, resid_coef):
     return ns, h0, rp.cpu().numpy(), col.cpu().numpy(), hg, solves
 
 
+def _oracle_amax(ns, i, cand, m, h):
+    """The oracle's largest amplitude response at stencil scale h (Section 4, steps 1-4)
+    and cond_2(M_i) there."""
+    dx0, dy0 = oracle.offsets(ns.xy, np.full(len(cand), i), cand, ns.Lx, ns.Ly)
+    keep = dx0 * dx0 + dy0 * dy0 <= (2 * h) * (2 * h)
+    dx, dy = dx0[keep], dy0[keep]
+    W = oracle.abf_matrix(dx, dy, h, m)
+    M = oracle.scaled_monomials(dx, dy, h, m).T @ W
+    C = np.stack([oracle.selector(op, m, h) for op in ("x", "y", "L")], axis=1)
+    psi, ok = oracle.lu_solve(M[None], C[None])
+    assert ok[0]
+    wts = W @ psi[0]
+    amax = max(a.max() for a in oracle.amplitude_response(dx, dy, ns.s[i], wts[:, 0], wts[:, 1],
+                                                          wts[:, 2], 16))
+    return amax, np.linalg.cond(M)
+
+
 @pytest.mark.parametrize("m", [4, 6, 8])
 def test_stencil_optimise_matches_oracle_amplitude_test(lb, m):
-    # with the residual test off, every stop is decided by the node count or by an
-    # amplitude response against 1.01, far from rounding: bit-identical h and
-    # identical solve counts on every sampled node
+    # with the residual test off, every stop is decided by the node count (exact on
+    # both sides) or by an amplitude response against 1.01.  The responses agree to
+    # rounding amplified by cond(M_i), so a node may stop one factor apart, but only
+    # where the oracle's own response at the contested h lies within 1e-5 of the
+    # bound, or where M_i is numerically singular there (cond > 1e14: a stencil with
+    # exactly n nodes can reach 1e19, and then no two FP64 solvers agree on the
+    # weights; the residual test exists to stop before such systems); everywhere
+    # else h and the number of solves are identical
     ns, h0, rpn, coln, hg, solves = _opt_case(lb, m, math.inf)
-    for i in np.random.default_rng(m).choice(ns.N, 48, replace=False):
+    same = 0
+    rows = np.random.default_rng(m).choice(ns.N, 48, replace=False)
+    for i in rows:
         cand = coln[rpn[i]:rpn[i + 1]]
         hb, nsol = oracle.optimise_stencil_node(ns.xy, ns.s, i, cand, m, ns.Lx, ns.Ly, h0[i],
                                                 resid_coef=math.inf)
-        assert hg[i] == hb and solves[i] == nsol, (i, _steps(hg[i], h0[i]), _steps(hb, h0[i]))
+        if hg[i] == hb and solves[i] == nsol:
+            same += 1
+            continue
+        assert abs(round(_steps(hg[i], h0[i]) - _steps(hb, h0[i]))) == 1, (i, hg[i], hb)
+        amax, cond = _oracle_amax(ns, i, cand, m, min(hg[i], hb))
+        assert cond > 1e14 or abs(amax / 1.01 - 1.0) < 1e-5, (i, amax, cond)
+    assert same >= len(rows) - 2, same
 
 
 @pytest.mark.parametrize("m", [4, 6])
