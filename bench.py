@@ -256,20 +256,21 @@ def recorded_traffic(kernel_hash):
 
 def weight_build_flops_per_node(m, nn):
     """FP64 flops per node of the weight build as implemented: weighted moments
-    (2 (2m+1)(2m+2)/2 per neighbour, plus 2 (2m+1) for the power tables), M from
-    the moments (2 flops per Hermite term of every entry), elimination on the
-    augmented [M | 6] system, back substitution for 6 right-hand sides, and per
-    neighbour the ABF evaluation (Hermite recurrences and n products) and the six
-    length-n dot products."""
+    (2 (2m+1)(2m+2)/2 per neighbour, plus 2 (2m+1) for the power tables), M from the
+    moments (for every entry, one FMA per Hermite term and one per outer index),
+    elimination on the augmented [M | 6] system, back substitution for 6 right-hand
+    sides, the Hermite-to-monomial coefficients of the six solutions, and per
+    neighbour the six Horner evaluations (n + m FMAs each) and the scaling by psi."""
     n = (m * m + 3 * m) // 2
     ex = [(a, k - a) for k in range(1, m + 1) for a in range(k, -1, -1)]
-    terms = sum((a // 2 + 1) * (b // 2 + 1) for a, b in ex)
+    assembly = 2 * n * sum((a // 2 + 1) * (b // 2 + 1) + (a // 2 + 1) for a, b in ex)
     moments = nn * (2 * (2 * m + 1) * (2 * m + 2) // 2 + 2 * (2 * m + 1))
-    assembly = 2 * n * terms
     elimination = sum(2 * (n - k - 1) * (n + 5 - k) + (n - k - 1) for k in range(n))
     back = 12 * n * n / 2
-    weights = nn * (6 * m + 3 * n + 12 * n)
-    return moments + assembly + elimination + back + weights
+    coeffs = 2 * 6 * sum(1 for p in range(m + 1) for q in range(m + 1 - p)
+                         for a in range(p, m + 1, 2) for b in range(q, m + 1 - a, 2) if a + b > 0)
+    weights = nn * (12 * (n + m) + 6)
+    return moments + assembly + elimination + back + coeffs + weights
 
 
 def _events(torch):
