@@ -600,7 +600,9 @@ def run_ours(args, world, rank, local):
     # roofline of the dominant kernel (fused RHS + RK stage, FP32)
     stage_ms = prof32["stage_ms"] / max(1, prof32["stage_launches"])
     filter_ms = prof32["filter_ms"] / max(1, prof32["filter_launches"])
-    alg_bytes = 24.0 * nnz + 64.0 * N  # per launch (stencil + weights + fields, see design notes)
+    # per launch: the record stream (plan entry bytes per stencil entry, 24 = 4-byte column +
+    # five 4-byte weights) + row pointer and node state (64 B per node)
+    alg_bytes = float(plan32.info()["entry_bytes"]) * nnz + 64.0 * N
     achieved = alg_bytes / (stage_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
     khash = kernel_source_hash()

@@ -72,6 +72,8 @@ typedef struct labfm_plan_info {
     int32_t group;      /* lanes per node in the gather kernels */
     int32_t block;      /* threads per block in the gather kernels */
     int32_t n_instances; /* independent instances (1 unless built by labfm_plan_create_batched) */
+    int32_t entry_bytes;        /* bytes of the RHS record stream per padded stencil entry */
+    int32_t filter_entry_bytes; /* bytes of the filter record stream per padded entry */
     int64_t device_bytes; /* device memory owned by the plan */
 } labfm_plan_info;
 

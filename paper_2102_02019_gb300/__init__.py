@@ -50,7 +50,8 @@ class _Phys(ctypes.Structure):
 class _PlanInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nnz_padded", ctypes.c_int64),
                 ("dtype", ctypes.c_int32), ("group", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("n_instances", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+                ("n_instances", ctypes.c_int32), ("entry_bytes", ctypes.c_int32),
+                ("filter_entry_bytes", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
 
 
 class _Profile(ctypes.Structure):

@@ -120,7 +120,7 @@ void prof_end(labfm_plan* p, int idx, cudaStream_t st) {
 
 extern "C" const char* labfm_last_error(void) { return g_last_error.c_str(); }
 
-extern "C" int labfm_abi_version(void) { return 1; }
+extern "C" int labfm_abi_version(void) { return 2; }
 
 extern "C" int labfm_plan_create(labfm_plan** out, int64_t N, int64_t nnz, labfm_dtype dtype,
                                  const int32_t* row_ptr, const int32_t* col, const double* w,
@@ -223,6 +223,8 @@ extern "C" int labfm_plan_get_info(const labfm_plan* p, labfm_plan_info* info) {
     info->group = p->group;
     info->block = p->block;
     info->n_instances = p->n_inst;
+    info->entry_bytes = plan_entry_bytes(p, false);
+    info->filter_entry_bytes = plan_entry_bytes(p, true);
     info->device_bytes = p->device_bytes;
     return LABFM_OK;
 }

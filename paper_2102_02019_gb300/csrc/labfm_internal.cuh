@@ -149,5 +149,8 @@ int launch_stable_dt_instances(const labfm_plan* p, const void* fields, const do
 int persistent_grid(const labfm_plan* p);
 // Configure the staged F32 stage kernel for `stages` ring slots (0 = off); synchronises.
 int configure_staging(labfm_plan* p, int stages, cudaStream_t st);
+// Bytes per padded stencil entry of the plan's RHS (filter = false) or filter
+// record stream (step.cu).
+int plan_entry_bytes(const labfm_plan* p, bool filter);
 
 }  // namespace labfm

@@ -1042,6 +1042,16 @@ int staging_shape_s(labfm_plan* p, int gi, size_t slot, int sms) {
 }
 }  // namespace
 
+int plan_entry_bytes(const labfm_plan* p, bool filter) {
+#if LABFM_CHUNK_AOS
+    if (p->dtype == LABFM_F32) return int((filter ? Rec<float>::FB : Rec<float>::BB) / (4 * kIL));
+    return int((filter ? Rec<double>::FB : Rec<double>::BB) / (4 * kIL));
+#else
+    const int es = p->dtype == LABFM_F32 ? 4 : 8;
+    return filter ? 4 + es : 4 + 5 * es;
+#endif
+}
+
 int configure_staging(labfm_plan* p, int stages, cudaStream_t st) {
     p->stages = 0;
     p->stage_slot_bytes[0] = p->stage_slot_bytes[1] = 0;
