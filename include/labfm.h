@@ -476,9 +476,12 @@ int labfm_step_graph_destroy(labfm_step_graph* graph);
 int labfm_rk_step_noalloc(const labfm_plan* plan, void* Q, double dt, int nsteps,
                           const labfm_phys* phys, void* stream);
 
-/* Per-launch device time of the kernels labfm_rk_step enqueues, measured with
- * CUDA events recorded on the launching stream around every stage launch and
- * every filter launch while profiling is enabled. */
+/* Device time of the kernels labfm_rk_step enqueues while profiling is enabled,
+ * measured with CUDA events recorded on the launching stream: one pair around the
+ * four consecutive stage launches of every step (counted as four launches, so
+ * stage_ms / stage_launches is the mean launch duration including the short
+ * gaps between them) and one pair around every filter launch.  Timing whole
+ * blocks keeps the events from stalling the stream between every launch. */
 typedef struct labfm_profile {
     double stage_ms;         /* summed duration of the fused RHS + RK stage launches */
     int64_t stage_launches;

@@ -388,9 +388,9 @@ extern "C" int labfm_plan_read_profile(labfm_plan* p, labfm_profile* out) {
         for (int k = 0; k < p->prof_used; ++k) {
             float ms = 0.f;
             LABFM_CUDA_TRY(cudaEventElapsedTime(&ms, p->prof_ev[2 * k], p->prof_ev[2 * k + 1]));
-            if (p->prof_kind[k] == 0) {
+            if (p->prof_kind[k] == 0 || p->prof_kind[k] == 2) {
                 out->stage_ms += ms;
-                ++out->stage_launches;
+                out->stage_launches += p->prof_kind[k] == 2 ? 4 : 1;
             } else {
                 out->filter_ms += ms;
                 ++out->filter_launches;

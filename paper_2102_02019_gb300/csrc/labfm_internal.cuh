@@ -120,7 +120,8 @@ int launch_stable_dt(const labfm_plan* p, const void* fields, const double* s, d
                      double mu, double* dt_out, cudaStream_t st);
 bool launch_shape_supported(int group, int block);
 
-// Launch timing around one kernel launch (api.cu); kind 0 = stage, 1 = filter.
+// Launch timing around kernel launches (api.cu); kind 0 = one stage launch,
+// 1 = one filter launch, 2 = the four stage launches of a step.
 // Returns the pair index to close with prof_end, or -1 when not profiling.
 int prof_begin(labfm_plan* p, int kind, cudaStream_t st);
 void prof_end(labfm_plan* p, int idx, cudaStream_t st);

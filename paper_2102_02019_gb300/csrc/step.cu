@@ -665,14 +665,14 @@ int rk_one_step_t(const labfm_plan* p, void* work, double dt, const labfm_phys* 
     const Packed<T>* xin[4] = {X, Y, X, Y};
     const Packed<T>* qin[4] = {X, P, P, P};
     Packed<T>* xout[4] = {Y, X, Y, nullptr};
+    const int evs = profile ? prof_begin(pm, 2, st) : -1;  // the four stages as one block
     for (int k = 0; k < 4; ++k) {
         const double bk = kRkB[k];
         const double ck = k < 3 ? kRkA[k] - kRkB[k] : 0.0;
-        const int ev = profile ? prof_begin(pm, 0, st) : -1;
         if ((rc = stage_launch<T>(p, xin[k], qin[k], P, xout[k], dt, bk, ck, ph, tickets + k, st)))
             return rc;
-        prof_end(pm, ev, st);
     }
+    prof_end(pm, evs, st);
     const int ev = profile ? prof_begin(pm, 1, st) : -1;
     if ((rc = filter_aos<T>(p, P, X, st))) return rc;
     prof_end(pm, ev, st);
