@@ -539,6 +539,20 @@ def kinetic_energy_grad(q, s):
     return np.stack([0.5 * rho * (u * u + v * v) * V, rho * u * V, rho * v * V])
 
 
+def probe_momentum(q, px, py):
+    """Probe-weighted momentum sum_i rho_i (px_i u_i + py_i v_i) (px, py: probe weights,
+    e.g. a smooth bump around a sensor position), the second flow objective."""
+    a, u, v = q
+    return float(np.sum(np.exp(a) * (px * u + py * v)))
+
+
+def probe_momentum_grad(q, px, py):
+    """d J / d (ln rho, u, v) for J = sum_i rho_i (px_i u_i + py_i v_i)."""
+    a, u, v = q
+    rho = np.exp(a)
+    return np.stack([rho * (px * u + py * v), rho * px, rho * py])
+
+
 # --------------------------------------------------------------------------
 # Sections 3 and 4: modal (amplitude) response and stencil optimisation
 # --------------------------------------------------------------------------

@@ -99,3 +99,19 @@ def test_conversions_and_energy_gradient(small):
     ke = lambda x: o.kinetic_energy(x, ns.s)
     assert np.isclose((ke(q + 1e-6 * dq) - ke(q - 1e-6 * dq)) / 2e-6,
                       np.sum(dq * o.kinetic_energy_grad(q, ns.s)), rtol=1e-7)
+
+
+def test_probe_momentum_and_gradient(small):
+    ns, rp, col, w, kap, q = small
+    rng = np.random.default_rng(7)
+    # a smooth probe around (0.4, 0.6): closed form on a uniform state
+    r2 = (ns.xy[:, 0] - 0.4) ** 2 + (ns.xy[:, 1] - 0.6) ** 2
+    px, py = np.exp(-r2 / 0.02), 0.5 * np.exp(-r2 / 0.05)
+    qu = np.stack([np.full(ns.N, np.log(1.2)), np.full(ns.N, 0.3), np.full(ns.N, -0.1)])
+    assert o.probe_momentum(qu, px, py) == pytest.approx(1.2 * (0.3 * px.sum() - 0.1 * py.sum()),
+                                                         rel=1e-14)
+    g = o.probe_momentum_grad(q, px, py)
+    for _ in range(3):
+        v = rng.standard_normal(q.shape)
+        fd = _fd(lambda x: o.probe_momentum(x, px, py), q, v, 1e-6)
+        assert fd == pytest.approx(float(np.sum(g * v)), rel=1e-8)
