@@ -437,6 +437,18 @@ int labfm_kinetic_energy_grad(const void* q, const double* s, int64_t N, labfm_d
                               double scale, void* grad_out, void* stream);
 
 /*
+ * Probe-weighted momentum J = sum_i rho_i (px_i u_i + py_i v_i) of a state
+ * q = (ln rho, u, v) (px, py: device, N doubles of probe weights, e.g. a smooth
+ * bump around a sensor), summed in FP64 in a fixed order by one block into one
+ * device double; and grad_out = scale * dJ/dq (the flow objective alternative to
+ * the kinetic energy for the adjoint; the paper itself has no adjoint).
+ */
+int labfm_probe_momentum(const void* q, const double* px, const double* py, int64_t N,
+                         labfm_dtype dtype, double* j_out, void* stream);
+int labfm_probe_momentum_grad(const void* q, const double* px, const double* py, int64_t N,
+                              labfm_dtype dtype, double scale, void* grad_out, void* stream);
+
+/*
  * One complete time step of labfm_rk_step (four fused stage kernels and the
  * filter, plus the ticket reset of a persistent plan) captured once into a CUDA
  * graph; labfm_step_graph_run packs Q into the workspace, replays the graph

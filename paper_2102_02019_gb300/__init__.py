@@ -109,6 +109,8 @@ _SIGS = {
     "labfm_conserved_vjp": (_I32, [_P, _P, _P, _I64, _I32, _P]),
     "labfm_kinetic_energy": (_I32, [_P, _P, _I64, _I32, _P, _P]),
     "labfm_kinetic_energy_grad": (_I32, [_P, _P, _I64, _I32, _D, _P, _P]),
+    "labfm_probe_momentum": (_I32, [_P, _P, _P, _I64, _I32, _P, _P]),
+    "labfm_probe_momentum_grad": (_I32, [_P, _P, _P, _I64, _I32, _D, _P, _P]),
 }
 
 
@@ -555,6 +557,21 @@ def kinetic_energy_grad(q, s, scale: float = 1.0, stream=None):
     return g
 
 
+def probe_momentum(q, px, py, stream=None) -> torch.Tensor:
+    """labfm_probe_momentum: sum_i rho_i (px_i u_i + py_i v_i), 1-element float64 tensor."""
+    out = torch.empty(1, dtype=torch.float64, device=q.device)
+    _check(lib.labfm_probe_momentum(_ptr(q), _ptr(px), _ptr(py), q.shape[1], _dcode(q), _ptr(out),
+                                    _stream(stream)))
+    return out
+
+
+def probe_momentum_grad(q, px, py, scale: float = 1.0, stream=None):
+    g = torch.empty_like(q)
+    _check(lib.labfm_probe_momentum_grad(_ptr(q), _ptr(px), _ptr(py), q.shape[1], _dcode(q), float(scale),
+                                         _ptr(g), _stream(stream)))
+    return g
+
+
 class _Rollout(torch.autograd.Function):
     """nsteps time steps of a plan as a differentiable map q0 -> q_final.
 
@@ -627,6 +644,18 @@ class _KineticEnergy(torch.autograd.Function):
         return grad, None
 
 
+class _ProbeMomentum(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, q, px, py):
+        ctx.save_for_backward(q, px, py)
+        return probe_momentum(q.detach().contiguous(), px, py)
+
+    @staticmethod
+    def backward(ctx, g):
+        q, px, py = ctx.saved_tensors
+        return probe_momentum_grad(q.detach().contiguous(), px, py, float(g.sum().item())), None, None
+
+
 def to_primitive(c: torch.Tensor) -> torch.Tensor:
     """Differentiable (rho, rho u, rho v) -> (ln rho, u, v)."""
     return _ToPrimitive.apply(c)
@@ -635,3 +664,8 @@ def to_primitive(c: torch.Tensor) -> torch.Tensor:
 def domain_kinetic_energy(q: torch.Tensor, s: torch.Tensor) -> torch.Tensor:
     """Differentiable sum_i 1/2 rho |u|^2 s_i^2 (1-element float64 tensor)."""
     return _KineticEnergy.apply(q, s)
+
+
+def domain_probe_momentum(q: torch.Tensor, px: torch.Tensor, py: torch.Tensor) -> torch.Tensor:
+    """Differentiable sum_i rho_i (px_i u_i + py_i v_i) (1-element float64 tensor)."""
+    return _ProbeMomentum.apply(q, px, py)

@@ -154,3 +154,58 @@ def test_fp32_adjoint_close_to_fp64(lb, case):
     # float32 rounding of inputs, weights and the twelve derivative adjoints: a few
     # units of 2^-24 amplified by the stencil sums (|w| ~ s^-2) over 8 passes
     assert np.all(_rel(out[torch.float32], out[torch.float64]) <= 1e-4)
+
+
+def _probe(ns):
+    r2 = (ns.xy[:, 0] - 0.4) ** 2 + (ns.xy[:, 1] - 0.6) ** 2
+    return np.exp(-r2 / 0.02), 0.5 * np.exp(-r2 / 0.05)
+
+
+def test_probe_momentum_matches_oracle(lb, case):
+    ns = case["ns"]
+    px, py = _probe(ns)
+    q = li.perturbed_tgv_fields(ns.xy, C, amplitude=0.05, kmax=4)
+    j = float(lb.probe_momentum(_dev(q), _dev(px), _dev(py)).item())
+    assert j == pytest.approx(oracle.probe_momentum(q, px, py), rel=1e-13)
+    g = lb.probe_momentum_grad(_dev(q), _dev(px), _dev(py), 2.0).cpu().numpy()
+    assert np.all(_rel(g, 2.0 * oracle.probe_momentum_grad(q, px, py)) <= 1e-14)
+
+
+def test_probe_momentum_gradient_through_rollout(lb, stable):
+    # gradient of the final probe-weighted momentum w.r.t. the initial conserved
+    # state: the oracle's adjoint chain and central differences of the GPU forward
+    case = stable
+    ns = case["ns"]
+    px, py = _probe(ns)
+    q0 = li.perturbed_tgv_fields(ns.xy, C, amplitude=0.05, kmax=8)
+    c0 = oracle.primitive_to_conserved(q0)
+    dt = oracle.stable_dt(q0, ns.s, C, MU)
+    nsteps = 5
+    plan = case["plans"][torch.float64]
+    phys = lb.Phys(C * C, MU)
+    pxd, pyd = _dev(px), _dev(py)
+    c = _dev(c0).requires_grad_(True)
+    qf = lb.rollout(plan, lb.to_primitive(c), dt, nsteps, phys, checkpoint_every=2)
+    J = lb.domain_probe_momentum(qf, pxd, pyd)
+    J.backward()
+    grad = c.grad.detach()
+    w, kap, rp, col = case["w"], case["kappa"], case["rp"], case["col"]
+    states = [q0]
+    for _ in range(nsteps):
+        states.append(oracle.time_step(states[-1], dt, w, kap, rp, col, C * C, MU))
+    assert float(J.item()) == pytest.approx(oracle.probe_momentum(states[-1], px, py), rel=1e-12)
+    lam = oracle.probe_momentum_grad(states[-1], px, py)
+    for k in range(nsteps - 1, -1, -1):
+        lam = oracle.time_step_vjp(states[k], lam, dt, w, kap, rp, col, C * C, MU)
+    ref = oracle.conserved_vjp(c0, lam)
+    assert np.all(_rel(grad.cpu().numpy(), ref) <= 1e-10)
+
+    def Jf(cc):
+        q = lb.conserved_to_primitive(cc)
+        lb.rk_step(plan, q, dt, nsteps, phys)
+        return float(lb.probe_momentum(q, pxd, pyd).item())
+
+    v = _dev(np.random.default_rng(8).standard_normal((3, ns.N)))
+    fd = (Jf(_dev(c0) + 1e-6 * v) - Jf(_dev(c0) - 1e-6 * v)) / 2e-6
+    ad = float((grad * v).sum().item())
+    assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
