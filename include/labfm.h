@@ -412,6 +412,27 @@ int labfm_rhs_adjoint(const labfm_plan* plan, const void* fields, const void* la
 int labfm_rk_step_adjoint(const labfm_plan* plan, const void* Q, void* lambda, double dt,
                           const labfm_phys* phys, void* work, size_t work_bytes, void* stream);
 
+/*
+ * The same reverse step without the recompute, for a caller that keeps the stage
+ * states: labfm_rk_step_record advances Q (3 x N, in place) by one step exactly as
+ * labfm_rk_step does and stores the step's four stage states X_1..X_4 (the state
+ * each of the four RK stages evaluates eq. icns at) in `states`, in the plan's
+ * packed node layout (opaque; labfm_stage_states_bytes bytes, 16-byte aligned);
+ * labfm_rk_step_adjoint_recorded then applies the reverse sweep of
+ * labfm_rk_step_adjoint to lambda with those states.  The results are identical
+ * to labfm_rk_step and labfm_rk_step_adjoint.  A checkpointed rollout that
+ * recomputes a segment with labfm_rk_step_record skips the three stage
+ * evaluations per step that labfm_rk_step_adjoint repeats.
+ *   work  (record): labfm_rk_workspace_bytes; (adjoint): labfm_adjoint_workspace_bytes
+ */
+size_t labfm_stage_states_bytes(const labfm_plan* plan);
+int labfm_rk_step_record(const labfm_plan* plan, void* Q, void* states, size_t states_bytes,
+                         void* work, size_t work_bytes, double dt, const labfm_phys* phys,
+                         void* stream);
+int labfm_rk_step_adjoint_recorded(const labfm_plan* plan, const void* states, void* lambda,
+                                   double dt, const labfm_phys* phys, void* work,
+                                   size_t work_bytes, void* stream);
+
 /* lam_out = Fil^T lam_in = lam + L_hyp^T (kappa lam), per field (3 x N). */
 int labfm_filter_adjoint(const labfm_plan* plan, const void* lam_in, void* lam_out, void* work,
                          size_t work_bytes, void* stream);

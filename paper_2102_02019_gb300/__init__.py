@@ -105,6 +105,11 @@ _SIGS = {
     "labfm_rhs_adjoint": (_I32, [_P, _P, _P, _P, ctypes.POINTER(_Phys), _P, ctypes.c_size_t, _P]),
     "labfm_rk_step_adjoint": (_I32, [_P, _P, _P, _D, ctypes.POINTER(_Phys), _P, ctypes.c_size_t, _P]),
     "labfm_filter_adjoint": (_I32, [_P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "labfm_stage_states_bytes": (ctypes.c_size_t, [_P]),
+    "labfm_rk_step_record": (_I32, [_P, _P, _P, ctypes.c_size_t, _P, ctypes.c_size_t, _D,
+                                    ctypes.POINTER(_Phys), _P]),
+    "labfm_rk_step_adjoint_recorded": (_I32, [_P, _P, _P, _D, ctypes.POINTER(_Phys), _P, ctypes.c_size_t,
+                                              _P]),
     "labfm_conserved_to_primitive": (_I32, [_P, _P, _I64, _I32, _P]),
     "labfm_conserved_vjp": (_I32, [_P, _P, _P, _I64, _I32, _P]),
     "labfm_kinetic_energy": (_I32, [_P, _P, _I64, _I32, _P, _P]),
@@ -523,6 +528,30 @@ def rk_step_adjoint(plan: Plan, Q, lam, dt: float, phys: Phys, work=None, stream
     return lam
 
 
+def stage_states(plan: Plan) -> torch.Tensor:
+    """A buffer for the four packed stage states of one step (labfm_stage_states_bytes)."""
+    nb = int(lib.labfm_stage_states_bytes(plan.handle))
+    return torch.empty((nb + 15) // 16 * 16, dtype=torch.uint8, device=plan.device)
+
+
+def rk_step_record(plan: Plan, Q, states, dt: float, phys: Phys, work=None, stream=None):
+    """labfm_rk_step_record: Q advanced one step in place, its stage states kept in `states`."""
+    work = workspace(plan) if work is None else work
+    ph = phys.c()
+    _check(lib.labfm_rk_step_record(plan.handle, _ptr(Q), _ptr(states), states.numel(), _ptr(work),
+                                    work.numel(), float(dt), ctypes.byref(ph), _stream(stream)))
+    return Q
+
+
+def rk_step_adjoint_recorded(plan: Plan, states, lam, dt: float, phys: Phys, work=None, stream=None):
+    """lam <- (dQ_next/dQ)^T lam from recorded stage states (labfm_rk_step_adjoint_recorded)."""
+    work = adjoint_workspace(plan) if work is None else work
+    ph = phys.c()
+    _check(lib.labfm_rk_step_adjoint_recorded(plan.handle, _ptr(states), _ptr(lam), float(dt),
+                                              ctypes.byref(ph), _ptr(work), work.numel(), _stream(stream)))
+    return lam
+
+
 def filter_adjoint(plan: Plan, lam, work=None, stream=None):
     work = adjoint_workspace(plan) if work is None else work
     out = torch.empty_like(lam)
@@ -576,8 +605,9 @@ class _Rollout(torch.autograd.Function):
     """nsteps time steps of a plan as a differentiable map q0 -> q_final.
 
     Forward keeps a checkpoint of the state every `every` steps.  Backward walks
-    the segments last to first: it recomputes the segment's step states from
-    its checkpoint, then applies labfm_rk_step_adjoint step by step in reverse."""
+    the segments last to first: it recomputes the segment from its checkpoint with
+    labfm_rk_step_record, keeping every step's stage states, then applies
+    labfm_rk_step_adjoint_recorded step by step in reverse."""
 
     @staticmethod
     def forward(ctx, q0, plan, dt, nsteps, phys, every):
@@ -601,13 +631,14 @@ class _Rollout(torch.autograd.Function):
         for seg in range(len(ctx.ckpts) - 1, -1, -1):
             k0 = seg * every
             k1 = min(nsteps, k0 + every)
-            states = [ctx.ckpts[seg].clone()]
-            for _ in range(k0, k1 - 1):
-                q = states[-1].clone()
-                rk_step(plan, q, dt, 1, phys, work=work)
-                states.append(q)
-            for q in reversed(states):
-                rk_step_adjoint(plan, q, lam, dt, phys, work=awork)
+            q = ctx.ckpts[seg].clone()
+            recorded = []
+            for _ in range(k0, k1):
+                X = stage_states(plan)
+                rk_step_record(plan, q, X, dt, phys, work=work)
+                recorded.append(X)
+            for X in reversed(recorded):
+                rk_step_adjoint_recorded(plan, X, lam, dt, phys, work=awork)
         ctx.ckpts = None
         return lam, None, None, None, None, None
 

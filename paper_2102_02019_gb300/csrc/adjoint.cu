@@ -509,6 +509,25 @@ int rhs_adjoint_t(const labfm_plan* p, const void* fields, const void* lambda, v
     return unpack_fields(p, w.Lam, grad, st);
 }
 
+// The reverse sweep of one step given its stage states X[0..3] (packed).
+template <typename T>
+int adjoint_sweep_t(const labfm_plan* p, const Packed<T>* const (&X)[4], void* lambda, double dt,
+                    const Phys<T>& ph, AdjWork<T>& w, cudaStream_t st) {
+    int rc;
+    // filter transpose, then the stages backwards
+    if ((rc = pack_fields(p, lambda, w.Ob, st))) return rc;
+    if ((rc = filt_adj<T>(p, w.Ob, w.Lam, w.Fb, dt, kRkB[3], st))) return rc;
+    for (int k = 3; k >= 0; --k) {
+        if ((rc = pass_a<T>(p, X[k], w.Fb, w.g, w.Ob, ph, st))) return rc;
+        const double bprev = k > 0 ? kRkB[k - 1] : 0.0;
+        const double cprev = k > 0 ? kRkA[k - 1] - kRkB[k - 1] : 0.0;
+        if ((rc = pass_b<T>(p, 1, w.g, w.Ob, nullptr, w.Lam, k > 0 ? w.Fb : nullptr, dt, bprev, cprev,
+                            st)))
+            return rc;
+    }
+    return unpack_fields(p, w.Lam, lambda, st);
+}
+
 template <typename T>
 int rk_step_adjoint_t(const labfm_plan* p, const void* Q, void* lambda, double dt,
                       const labfm_phys* php, void* work, cudaStream_t st) {
@@ -518,18 +537,18 @@ int rk_step_adjoint_t(const labfm_plan* p, const void* Q, void* lambda, double d
     // forward recompute of the stage states X1..X4 of this step
     if ((rc = pack_fields(p, Q, w.X[0], st))) return rc;
     if ((rc = forward_stage_states(p, w.X[0], w.P, w.X[1], w.X[2], w.X[3], dt, php, st))) return rc;
-    // filter transpose, then the stages backwards
-    if ((rc = pack_fields(p, lambda, w.Ob, st))) return rc;
-    if ((rc = filt_adj<T>(p, w.Ob, w.Lam, w.Fb, dt, kRkB[3], st))) return rc;
-    for (int k = 3; k >= 0; --k) {
-        if ((rc = pass_a<T>(p, w.X[k], w.Fb, w.g, w.Ob, ph, st))) return rc;
-        const double bprev = k > 0 ? kRkB[k - 1] : 0.0;
-        const double cprev = k > 0 ? kRkA[k - 1] - kRkB[k - 1] : 0.0;
-        if ((rc = pass_b<T>(p, 1, w.g, w.Ob, nullptr, w.Lam, k > 0 ? w.Fb : nullptr, dt, bprev, cprev,
-                            st)))
-            return rc;
-    }
-    return unpack_fields(p, w.Lam, lambda, st);
+    const Packed<T>* const X[4] = {w.X[0], w.X[1], w.X[2], w.X[3]};
+    return adjoint_sweep_t<T>(p, X, lambda, dt, ph, w, st);
+}
+
+template <typename T>
+int rk_step_adjoint_recorded_t(const labfm_plan* p, const void* states, void* lambda, double dt,
+                               const labfm_phys* php, void* work, cudaStream_t st) {
+    const Phys<T> ph{T(php->c2), T(php->mu), T(php->gx), T(php->gy)};
+    AdjWork<T> w = split_work<T>(p, work);
+    const Packed<T>* S = static_cast<const Packed<T>*>(states);
+    const Packed<T>* const X[4] = {S, S + p->N, S + 2 * p->N, S + 3 * p->N};
+    return adjoint_sweep_t<T>(p, X, lambda, dt, ph, w, st);
 }
 
 template <typename T>
@@ -594,6 +613,44 @@ extern "C" int labfm_rk_step_adjoint(const labfm_plan* p, const void* Q, void* l
     cudaStream_t st = as_stream(stream);
     return p->dtype == LABFM_F32 ? rk_step_adjoint_t<float>(p, Q, lambda, dt, phys, work, st)
                                  : rk_step_adjoint_t<double>(p, Q, lambda, dt, phys, work, st);
+}
+
+extern "C" size_t labfm_stage_states_bytes(const labfm_plan* p) {
+    if (!p || !p->row_ptr) return 0;
+    return size_t(4) * size_t(p->N) *
+           (p->dtype == LABFM_F32 ? sizeof(Packed<float>) : sizeof(Packed<double>));
+}
+
+extern "C" int labfm_rk_step_record(const labfm_plan* p, void* Q, void* states, size_t states_bytes,
+                                    void* work, size_t work_bytes, double dt, const labfm_phys* phys,
+                                    void* stream) {
+    if (!p || !p->row_ptr) return set_error(LABFM_EINVAL, "null or empty plan");
+    if (!Q || !states || !work || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
+    if (states_bytes < labfm_stage_states_bytes(p))
+        return set_error(LABFM_EINVAL, "states buffer smaller than labfm_stage_states_bytes");
+    if (work_bytes < rk_work_bytes(p))
+        return set_error(LABFM_EINVAL, "work buffer smaller than labfm_rk_workspace_bytes");
+    if ((reinterpret_cast<uintptr_t>(states) | reinterpret_cast<uintptr_t>(work)) % 16 != 0)
+        return set_error(LABFM_EINVAL, "states and work buffers must be 16-byte aligned");
+    if (!(dt > 0.0) && !(dt == 0.0 && p->dt_node))
+        return set_error(LABFM_EINVAL, "dt must be positive (or 0 with per-instance dt set)");
+    const size_t ps = p->dtype == LABFM_F32 ? sizeof(Packed<float>) : sizeof(Packed<double>);
+    char* wb = static_cast<char*>(work);
+    return rk_step_record(p, Q, states, wb, wb + size_t(p->N) * ps, dt, phys, as_stream(stream));
+}
+
+extern "C" int labfm_rk_step_adjoint_recorded(const labfm_plan* p, const void* states, void* lambda,
+                                              double dt, const labfm_phys* phys, void* work,
+                                              size_t work_bytes, void* stream) {
+    if (int rc = check_adjoint(p, work, work_bytes)) return rc;
+    if (!states || !lambda || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
+    if (reinterpret_cast<uintptr_t>(states) % 16 != 0)
+        return set_error(LABFM_EINVAL, "states buffer must be 16-byte aligned");
+    if (!(dt > 0.0) && !(dt == 0.0 && p->dt_node))
+        return set_error(LABFM_EINVAL, "dt must be positive (or 0 with per-instance dt set)");
+    cudaStream_t st = as_stream(stream);
+    return p->dtype == LABFM_F32 ? rk_step_adjoint_recorded_t<float>(p, states, lambda, dt, phys, work, st)
+                                 : rk_step_adjoint_recorded_t<double>(p, states, lambda, dt, phys, work, st);
 }
 
 extern "C" int labfm_filter_adjoint(const labfm_plan* p, const void* lam_in, void* lam_out,

@@ -145,6 +145,10 @@ int unpack_fields(const labfm_plan* p, const void* packed, void* soa, cudaStream
 // X2, X3, X4 (P receives the partial solution register) (step.cu).
 int forward_stage_states(const labfm_plan* p, const void* X1, void* P, void* X2, void* X3,
                          void* X4, double dt, const labfm_phys* ph, cudaStream_t st);
+// One RK step from Q (3 x N SoA, replaced by the next state) that stores its four
+// stage states, packed, in X (4 x N); P and Y are scratch packed states (step.cu).
+int rk_step_record(const labfm_plan* p, void* Q, void* X, void* P, void* Y, double dt,
+                   const labfm_phys* ph, cudaStream_t st);
 int launch_stable_dt_instances(const labfm_plan* p, const void* fields, const double* s, double c,
                                double mu, double* dt_inst, cudaStream_t st);
 int persistent_grid(const labfm_plan* p);

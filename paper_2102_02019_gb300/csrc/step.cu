@@ -727,6 +727,36 @@ int forward_stage_states_t(const labfm_plan* p, const void* X1v, void* Pv, void*
 }
 }  // namespace
 
+namespace {
+// One step that keeps its stage states: X1 = pack(Q), X2..X4 the inputs of
+// stages 2..4, then stage 4 and the filter as labfm_rk_step takes them; Q is
+// replaced by the next state.  P and Y: scratch packed states.
+template <typename T>
+int rk_step_record_t(const labfm_plan* p, void* Q, void* Xv, void* Pv, void* Yv, double dt,
+                     const labfm_phys* php, cudaStream_t st) {
+    const Phys<T> ph{T(php->c2), T(php->mu), T(php->gx), T(php->gy)};
+    Packed<T>* X = static_cast<Packed<T>*>(Xv);
+    Packed<T>* P = static_cast<Packed<T>*>(Pv);
+    Packed<T>* Y = static_cast<Packed<T>*>(Yv);
+    int rc;
+    if ((rc = pack_fields(p, Q, X, st))) return rc;
+    if ((rc = forward_stage_states_t<T>(p, X, P, X + p->N, X + 2 * p->N, X + 3 * p->N, dt, php, st)))
+        return rc;
+    labfm_plan q = *p;
+    q.persistent = false;
+    if ((rc = stage_launch<T>(&q, X + 3 * p->N, P, P, nullptr, dt, kRkB[3], 0.0, ph, nullptr, st)))
+        return rc;
+    if ((rc = filter_aos<T>(p, P, Y, st))) return rc;
+    return unpack_fields(p, Y, Q, st);
+}
+}  // namespace
+
+int rk_step_record(const labfm_plan* p, void* Q, void* X, void* P, void* Y, double dt,
+                   const labfm_phys* ph, cudaStream_t st) {
+    return p->dtype == LABFM_F32 ? rk_step_record_t<float>(p, Q, X, P, Y, dt, ph, st)
+                                 : rk_step_record_t<double>(p, Q, X, P, Y, dt, ph, st);
+}
+
 int forward_stage_states(const labfm_plan* p, const void* X1, void* P, void* X2, void* X3,
                          void* X4, double dt, const labfm_phys* ph, cudaStream_t st) {
     return p->dtype == LABFM_F32 ? forward_stage_states_t<float>(p, X1, P, X2, X3, X4, dt, ph, st)

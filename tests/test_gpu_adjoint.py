@@ -209,3 +209,22 @@ def test_probe_momentum_gradient_through_rollout(lb, stable):
     fd = (Jf(_dev(c0) + 1e-6 * v) - Jf(_dev(c0) - 1e-6 * v)) / 2e-6
     ad = float((grad * v).sum().item())
     assert abs(fd - ad) <= 1e-6 * abs(ad), (fd, ad)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_recorded_step_and_adjoint_equal_the_recomputing_ones(lb, case, dtype):
+    ns = case["ns"]
+    plan = case["plans"][dtype]
+    q = li.perturbed_tgv_fields(ns.xy, C, amplitude=0.05, kmax=4)
+    dt = oracle.stable_dt(q, ns.s, C, MU)
+    phys = lb.Phys(C * C, MU)
+    m = np.random.default_rng(9).standard_normal(q.shape)
+    Qa, Qb = _dev(q, dtype), _dev(q, dtype)
+    X = lb.stage_states(plan)
+    lb.rk_step_record(plan, Qa, X, dt, phys)
+    lb.rk_step(plan, Qb, dt, 1, phys)
+    assert torch.equal(Qa, Qb)
+    la, lbb = _dev(m, dtype), _dev(m, dtype)
+    lb.rk_step_adjoint_recorded(plan, X, la, dt, phys)
+    lb.rk_step_adjoint(plan, _dev(q, dtype), lbb, dt, phys)
+    assert torch.equal(la, lbb)
