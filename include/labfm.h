@@ -365,10 +365,13 @@ int labfm_stable_dt(const labfm_plan* plan, const void* fields, const double* s,
 
 /*
  * The same as labfm_rk_step for a caller whose state lives in host memory:
- * copies Q_host (3 x N, plan dtype) to Q_dev, runs `nsteps` steps on the
- * device, copies the result back into Q_host and synchronises `stream`.
- *   Q_host  host, 3 x N (pinned memory gives asynchronous copies)
- *   Q_dev   device, 3 x N scratch for the state
+ * runs `nsteps` steps on the device with the state taken from and returned to
+ * Q_host (3 x N, plan dtype), and synchronises `stream`.  Page-locked (pinned,
+ * mapped) host memory is read and written directly by the step's pack and
+ * unpack kernels over the host link (Q_dev is not used); other host memory is
+ * copied to Q_dev, stepped there and copied back.
+ *   Q_host  host, 3 x N
+ *   Q_dev   device, 3 x N scratch for the state (used for pageable Q_host)
  */
 int labfm_rk_step_host(const labfm_plan* plan, void* Q_host, void* Q_dev, void* work,
                        size_t work_bytes, double dt, int nsteps, const labfm_phys* phys,

@@ -340,6 +340,17 @@ extern "C" int labfm_rk_step_host(const labfm_plan* p, void* Q_host, void* Q_dev
     if (!Q_host || !Q_dev) return set_error(LABFM_EINVAL, "null pointer argument");
     const size_t bytes = size_t(3) * size_t(p->N) * (p->dtype == LABFM_F32 ? sizeof(float) : sizeof(double));
     cudaStream_t st = as_stream(stream);
+    // Page-locked, mapped host memory: the pack and unpack kernels of the step read
+    // and write it directly over the host link, without a staging copy.
+    cudaPointerAttributes attr{};
+    if (cudaPointerGetAttributes(&attr, Q_host) == cudaSuccess && attr.type == cudaMemoryTypeHost &&
+        attr.devicePointer && reinterpret_cast<uintptr_t>(attr.devicePointer) % 16 == 0) {
+        if (int rc = labfm_rk_step(p, attr.devicePointer, work, work_bytes, dt, nsteps, phys, stream))
+            return rc;
+        LABFM_CUDA_TRY(cudaStreamSynchronize(st));
+        return LABFM_OK;
+    }
+    cudaGetLastError();  // pageable memory: not an error, take the copy path
     LABFM_CUDA_TRY(cudaMemcpyAsync(Q_dev, Q_host, bytes, cudaMemcpyHostToDevice, st));
     if (int rc = labfm_rk_step(p, Q_dev, work, work_bytes, dt, nsteps, phys, stream)) return rc;
     LABFM_CUDA_TRY(cudaMemcpyAsync(Q_host, Q_dev, bytes, cudaMemcpyDeviceToHost, st));
