@@ -645,7 +645,11 @@ def run_ours(args, world, rank, local):
         "preprocess": {"stencil_ms": stencil_ms, "weight_build_ms": weights_ms,
                        "weight_build_nodes_per_s": N / (weights_ms * 1e-3), "failed_nodes": n_bad,
                        "weight_build_fp64_gflops": wb_flops / (weights_ms * 1e-3) / 1e9,
-                       "weight_build_fp64_frac": wb_flops / (weights_ms * 1e-3) / 1e9 / fp64_peak},
+                       "weight_build_fp64_frac": wb_flops / (weights_ms * 1e-3) / 1e9 / fp64_peak,
+                       # its memory side: 6 FP64 weights out and a 4-byte column in per entry,
+                       # coordinates, h, s, kappa, status and row pointer per node
+                       "weight_build_hbm_GBps": (52.0 * nnz + 48.0 * N) / (weights_ms * 1e-3) / 1e9,
+                       "weight_build_hbm_frac": (52.0 * nnz + 48.0 * N) / (weights_ms * 1e-3) / 1e9 / peak},
         "state_finite_after_run": fin32,
         "e2e": e2e,
         "gpu_launches": 5 * args.steps + 2,

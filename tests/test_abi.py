@@ -53,3 +53,32 @@ def test_errors_are_reported_without_a_gpu(built_lib):
     assert rc == 1 and b"order m" in lb.lib.labfm_last_error()
     rc = lb.lib.labfm_rhs(None, 1, 2, None, None)
     assert rc == 1
+
+
+def test_later_entry_points_validate_on_the_host(built_lib):
+    import ctypes
+    import paper_2102_02019_gb300 as lb
+    L = lb.lib
+    err = lambda: L.labfm_last_error()
+    # stencil optimisation: order and shrink factor are checked before any launch
+    assert L.labfm_stencil_optimise(1, 1, 1, 10, 1.0, 1.0, 3, 1, 1, 5, 0.99, 1.01, 1e-4, 10, 1, None, None) == 1
+    assert b"order m" in err()
+    assert L.labfm_stencil_optimise(1, 1, 1, 10, 1.0, 1.0, 3, 1, 1, 4, 1.0, 1.01, 1e-4, 10, 1, None, None) == 1
+    assert b"factor" in err()
+    assert L.labfm_stencil_optimise(1, 1, 1, 10, 1.0, 1.0, 3, 1, 1, 4, 0.99, 1.01, 0.0, 10, 1, None, None) == 1
+    assert b"resid_coef" in err()
+    assert L.labfm_modal_response(1, 1, 10, 1.0, 1.0, 3, 1, 1, 10, 1, 0, 1, None) == 1
+    assert b"nk" in err()
+    # plan-level calls on a null plan
+    for fn, args in (("labfm_plan_set_staging", (None, 3, None)),
+                     ("labfm_plan_set_persistent", (None, 1)),
+                     ("labfm_rk_step_adjoint_recorded", (None, 1, 1, 1e-3, None, 1, 16, None))):
+        assert getattr(L, fn)(*args) == 1, fn
+    st = ctypes.c_int(0)
+    assert L.labfm_plan_device_status(None, ctypes.byref(st)) == 1
+    assert L.labfm_stage_states_bytes(None) == 0
+    # objectives: null pointers and bad sizes
+    out = ctypes.c_double(0.0)
+    assert L.labfm_probe_momentum(None, 1, 1, 10, 0, ctypes.byref(out), None) == 1
+    assert L.labfm_probe_momentum_grad(1, 1, 1, 0, 0, 1.0, 1, None) == 1
+    assert b"N must be positive" in err()
