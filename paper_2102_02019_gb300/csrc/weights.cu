@@ -226,8 +226,10 @@ template <int M, int LDA>
 __device__ void block_assemble(double* A, double* A0, const double* s_mu, const double* s_he) {
     using C = WCfg<M>;
     constexpr int n = C::n, NT = C::NT;
+    // column-major over the threads: the lanes of a warp share the column c, whose
+    // Hermite exponents fix the trip counts of the loops below (no divergence)
     for (int idx = threadIdx.x; idx < n * n; idx += NT) {
-        const int r = idx / n, c = idx - r * n;
+        const int c = idx / n, r = idx - c * n;
         int ar, br, ac, bc;
         exps_of(r, ar, br);
         exps_of(c, ac, bc);
@@ -461,7 +463,14 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
     const double kx = 3.0 * 3.141592653589793 / (2.0 * s[i]);
     double f0 = 0.0;
     bool bad = false;
-    for (int e = r0 + t; e < r1; e += NT) {
+    // Neighbours go one per lane with all six operators.  When the last warp would
+    // hold only a few (rem <= 21 of 32), those are split one (neighbour, operator)
+    // pair per lane instead: a sixth of the Horner work per lane, fewer idle lanes.
+    const int nn = r1 - r0;
+    const int rem = nn % 32;
+    const bool split = !singular && rem > 0 && rem <= 21;
+    const int nmain = split ? nn - rem : nn;
+    for (int e = r0 + t; e < r0 + nmain; e += NT) {
         double wd[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         double dx = 0.0, dy = 0.0;
         if (!singular) {
@@ -493,6 +502,30 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
         }
         const double phi = 1.0 - cos(kx * dx) * cos(kx * dy);
         f0 = fma(phi, wd[5], f0);
+    }
+    if (split) {
+        for (int task = t; task < 6 * rem; task += NT) {
+            const int e = r0 + nmain + task / 6;
+            const int d = task - (task / 6) * 6;
+            const int j = col[e];
+            const double dx = min_image(__dsub_rn(xy[2 * j], g.xi), g.Lx, g.px);
+            const double dy = min_image(__dsub_rn(xy[2 * j + 1], g.yi), g.Ly, g.py);
+            const double xh = dx * g.ih, yh = dy * g.ih;
+            const double psi = wendland_c2(sqrt(dx * dx + dy * dy) * g.ih);
+            double acc = 0.0;
+#pragma unroll 1
+            for (int p = M; p >= 0; --p) {
+                const double* cp = s_cf + (p * (2 * M + 3 - p) / 2) * 6 + d;  // (p, 0), operator d
+                double in = cp[(M - p) * 6];
+#pragma unroll 1
+                for (int qq = M - p - 1; qq >= 0; --qq) in = fma(in, yh, cp[qq * 6]);
+                acc = fma(acc, xh, in);
+            }
+            const double wv = acc * psi;
+            w[int64_t(d) * nnz + e] = wv;
+            bad |= !isfinite(wv);
+            if (d == 5) f0 = fma(1.0 - cos(kx * dx) * cos(kx * dy), wv, f0);
+        }
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&s_nonfinite, 1);
     const double F0 = block_sum<NT>(f0, s_red);
