@@ -544,50 +544,110 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
 
 constexpr int kNk = 16;  // wavenumbers of the amplitude test (n_k = 16 in Section 4)
 
+// Sum of 16 values over the 32 lanes of a warp by recursive halving: at each
+// level a lane keeps half of its values and adds its partner's copy of that half
+// (16 shuffles and adds instead of 80).  Afterwards lane L holds the total of
+// value (L >> 1) & 15.
+__device__ __forceinline__ double warp_sum16(double (&v)[16], int lane) {
+    {
+        const bool hi = lane & 16;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const double keep = hi ? v[8 + i] : v[i], send = hi ? v[i] : v[8 + i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+    }
+    {
+        const bool hi = lane & 8;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const double keep = hi ? v[4 + i] : v[i], send = hi ? v[i] : v[4 + i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        }
+    }
+    {
+        const bool hi = lane & 4;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const double keep = hi ? v[2 + i] : v[i], send = hi ? v[i] : v[2 + i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+    }
+    {
+        const bool hi = lane & 2;
+        const double keep = hi ? v[1] : v[0], send = hi ? v[0] : v[1];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
 // Amplitude responses of the d/dx, d/dy and Laplacian operators of node i at
-// k_n = (pi / s_i) n / kNk, n = 1..kNk (Section 4, step 3).  Each thread takes one
-// neighbour per pass: its three weights (Psi^x, Psi^y, Psi^L in columns n, n + 1,
-// n + 2 of A), then sin and cos of n k_1 x_ji and n k_1 y_ji for n = 1..kNk by
-// rotation from one sincos each (every step multiplies by e^{i k_1 x}, so the
-// rounding error grows linearly in n), each product reduced across the warp.
-// s_part: (NT / 32) x 3 kNk doubles.  Returns the largest of the 3 kNk
-// responses (the same value in every thread).
+// k_n = (pi / s_i) n / kNk, n = 1..kNk (Section 4, step 3).  The three solutions
+// (Psi^x, Psi^y, Psi^L in columns n, n + 1, n + 2 of A) are turned into monomial
+// coefficients once (as in the weight build), so each lane gets its neighbour's
+// three weights by Horner's rule; sin and cos of n k_1 x_ji and n k_1 y_ji for
+// n = 1..kNk follow by rotation from one sincos each (every step multiplies by
+// e^{i k_1 x}, so the rounding error grows linearly in n).  Each lane accumulates
+// its 3 kNk sums over all its neighbours; they are reduced across the warp once.
+// s_cf3: (m+1)(m+2)/2 x 3 doubles; s_part: (NT / 32) x 3 kNk doubles.  Returns
+// the largest of the 3 kNk responses (the same value in every thread).
 template <int M, int LDA>
 __device__ double block_amplitude_max(const double* __restrict__ xy, const int32_t* __restrict__ col,
                                       int r0, int r1, const NodeGeom& g, double s_i, const double* A,
-                                      double* s_psi, double* s_part, double* s_amax) {
+                                      const double* s_he, double* s_cf3, double* s_part,
+                                      double* s_amax) {
     using C = WCfg<M>;
     constexpr int n = C::n, NT = C::NT, NW = NT / 32;
     constexpr int NP = 3 * kNk;
+    constexpr int NC = (M + 1) * (M + 2) / 2;
+    static_assert(kNk == 16, "the warp reduction takes 16 values per operator");
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const double kny = 3.141592653589793 / s_i;
     const double k1 = kny / kNk;
-    // Psi^d_q / sqrt(2^deg q), so that w^d_j = psi_j sum_q H_a H_b s_psi[q][d]
-    for (int idx = t; idx < n * 3; idx += NT) {
-        const int q = idx / 3, d = idx - q * 3;
-        int a, b;
-        exps_of(q, a, b);
-        s_psi[idx] = A[q * LDA + n + d] * inv_sqrt2_pow(a + b);
+    // coefficients c^d_pq of psi^-1 W . Psi^d = sum_pq c^d_pq (x/h)^p (y/h)^q
+    for (int idx = t; idx < NC * 3; idx += NT) {
+        const int pq = idx / 3, d = idx - pq * 3;
+        int p = 0;
+        while (pq >= (p + 1) * (2 * M + 2 - p) / 2) ++p;
+        const int qy = pq - p * (2 * M + 3 - p) / 2;
+        double c = 0.0;
+        for (int a = p; a <= M; a += 2) {
+            const double ha = s_he[a * (M + 1) + p];
+            for (int b = qy; a + b <= M; b += 2) {
+                const int k = a + b;
+                if (k == 0) continue;
+                c = fma(ha * s_he[b * (M + 1) + qy], A[(k * (k + 1) / 2 - 1 + b) * LDA + n + d], c);
+            }
+        }
+        s_cf3[idx] = c;
     }
-    for (int u = t; u < NW * NP; u += NT) s_part[u] = 0.0;
     __syncthreads();
+    double acc[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) acc[k] = 0.0;
     for (int c0 = r0; c0 < r1; c0 += NT) {
         if (c0 + warp * 32 >= r1) continue;  // warp-uniform: no neighbour for this warp
         const int e = c0 + t;
         double w0 = 0.0, w1 = 0.0, w2 = 0.0, dx = 0.0, dy = 0.0;
         if (e < r1) {
-            double pxv[M + 1], pyv[M + 1], hxv[M + 1], hyv[M + 1], psi;
-            neighbour_factors<M>(xy, col[e], g, pxv, pyv, hxv, hyv, &psi, &dx, &dy);
-            int q = 0;
-#pragma unroll
-            for (int kk = 1; kk <= M; ++kk) {
-#pragma unroll
-                for (int a = kk; a >= 0; --a, ++q) {
-                    const double Hq = hxv[a] * hyv[kk - a];
-                    w0 = fma(Hq, s_psi[3 * q], w0);
-                    w1 = fma(Hq, s_psi[3 * q + 1], w1);
-                    w2 = fma(Hq, s_psi[3 * q + 2], w2);
+            const int j = col[e];
+            dx = min_image(__dsub_rn(xy[2 * j], g.xi), g.Lx, g.px);
+            dy = min_image(__dsub_rn(xy[2 * j + 1], g.yi), g.Ly, g.py);
+            const double xh = dx * g.ih, yh = dy * g.ih;
+            const double psi = wendland_c2(sqrt(dx * dx + dy * dy) * g.ih);
+#pragma unroll 1
+            for (int p = M; p >= 0; --p) {
+                const double* cp = s_cf3 + (p * (2 * M + 3 - p) / 2) * 3;  // (p, 0)
+                double i0 = cp[(M - p) * 3], i1 = cp[(M - p) * 3 + 1], i2 = cp[(M - p) * 3 + 2];
+#pragma unroll 1
+                for (int qq = M - p - 1; qq >= 0; --qq) {
+                    i0 = fma(i0, yh, cp[qq * 3]);
+                    i1 = fma(i1, yh, cp[qq * 3 + 1]);
+                    i2 = fma(i2, yh, cp[qq * 3 + 2]);
                 }
+                w0 = fma(w0, xh, i0);
+                w1 = fma(w1, xh, i1);
+                w2 = fma(w2, xh, i2);
             }
             w0 *= psi;
             w1 *= psi;
@@ -599,20 +659,9 @@ __device__ double block_amplitude_max(const double* __restrict__ xy, const int32
         double sx = s1x, cx = c1x, sy = s1y, cy = c1y;
 #pragma unroll
         for (int k = 0; k < kNk; ++k) {
-            double vx = sx * w0;
-            double vy = sy * w1;
-            double vl = (0.5 - 0.5 * cx * cy) * w2;
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                vx += __shfl_xor_sync(0xffffffffu, vx, off);
-                vy += __shfl_xor_sync(0xffffffffu, vy, off);
-                vl += __shfl_xor_sync(0xffffffffu, vl, off);
-            }
-            if (lane == 0) {
-                s_part[warp * NP + k] += vx;
-                s_part[warp * NP + kNk + k] += vy;
-                s_part[warp * NP + 2 * kNk + k] += vl;
-            }
+            acc[k] = fma(sx, w0, acc[k]);
+            acc[kNk + k] = fma(sy, w1, acc[kNk + k]);
+            acc[2 * kNk + k] = fma(0.5 - 0.5 * cx * cy, w2, acc[2 * kNk + k]);
             const double nsx = fma(sx, c1x, cx * s1x), ncx = fma(cx, c1x, -(sx * s1x));
             const double nsy = fma(sy, c1y, cy * s1y), ncy = fma(cy, c1y, -(sy * s1y));
             sx = nsx;
@@ -620,6 +669,14 @@ __device__ double block_amplitude_max(const double* __restrict__ xy, const int32
             sy = nsy;
             cy = ncy;
         }
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double v[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = acc[d * kNk + k];
+        const double tot = warp_sum16(v, lane);
+        if ((lane & 1) == 0) s_part[warp * NP + d * kNk + ((lane >> 1) & 15)] = tot;
     }
     __syncthreads();
     if (warp == 0) {
@@ -657,7 +714,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
     __shared__ double s_he[(M + 1) * (M + 1)];
     __shared__ double s_red[NT / 32];
     __shared__ double s_part[(NT / 32) * 3 * kNk];
-    __shared__ double s_psi[3 * n];
+    __shared__ double s_cf3[(M + 1) * (M + 2) / 2 * 3];
     __shared__ double s_hp[M + 1];
     __shared__ double s_amax;
     __shared__ double s_rdiag[n];
@@ -716,7 +773,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
         const double alpha0 = resid_coef * eps * double(n) * double(n) * double(n) * double(n) / (g.hi * M);
         if (!(alpha <= alpha0)) break;
         // steps 3-4: amplitude response up to Nyquist
-        const double amax = block_amplitude_max<M, LDA>(xy, col, r0, r1, g, s[i], A, s_psi, s_part, &s_amax);
+        const double amax = block_amplitude_max<M, LDA>(xy, col, r0, r1, g, s[i], A, s_he, s_cf3, s_part, &s_amax);
         if (!(amax <= amp_max)) break;
         // step 5
         best = g.hi;
