@@ -696,8 +696,16 @@ __device__ double block_amplitude_max(const double* __restrict__ xy, const int32
     return *s_amax;
 }
 
+// Register budget of the stencil-optimisation kernel: at most 128 per thread
+// (its 48 per-lane amplitude sums need ~150 unconstrained, which left 4 CTAs of
+// 96 threads per SM at m = 6 and the FP64 pipe 72 % busy).
 template <int M>
-__global__ void __launch_bounds__(WCfg<M>::NT)
+constexpr int stencil_opt_min_blocks() {
+    return 65536 / (WCfg<M>::NT * 128);
+}
+
+template <int M>
+__global__ void __launch_bounds__(WCfg<M>::NT, stencil_opt_min_blocks<M>())
     k_stencil_opt(const double* __restrict__ xy, const double* __restrict__ h0,
                   const double* __restrict__ s, int64_t N, double Lx, double Ly, int px_, int py_,
                   const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
