@@ -82,3 +82,23 @@ def test_later_entry_points_validate_on_the_host(built_lib):
     assert L.labfm_probe_momentum(None, 1, 1, 10, 0, ctypes.byref(out), None) == 1
     assert L.labfm_probe_momentum_grad(1, 1, 1, 0, 0, 1.0, 1, None) == 1
     assert b"N must be positive" in err()
+
+
+def test_empty_and_oversize_inputs_are_rejected_on_the_host(built_lib):
+    # N = 0 (an empty node set) and N >= 2^31 - 1 (beyond the int32 row pointers)
+    # are EINVAL before any device access; the pointers are never dereferenced
+    import ctypes
+    import paper_2102_02019_gb300 as lb
+    L = lb.lib
+    p = 16  # non-null, never read
+    nnz = ctypes.c_int64(-1)
+    for N in (0, -3, 2 ** 31 - 1):
+        assert L.labfm_build_stencils(p, p, N, 1.0, 1.0, 3, p, p, 0, ctypes.byref(nnz), None) == 1
+        assert b"N out of range" in L.labfm_last_error()
+        assert L.labfm_build_weights(p, p, p, N, 1.0, 1.0, 3, p, p, 0, 4, p, p, None, p, None,
+                                     None) == 1
+        assert b"N out of range" in L.labfm_last_error()
+        plan = ctypes.c_void_p(1)
+        assert L.labfm_plan_create(ctypes.byref(plan), N, 0, 1, p, None, p, p, p, None) == 1
+        assert b"N out of range" in L.labfm_last_error() and plan.value is None
+    assert nnz.value == -1
