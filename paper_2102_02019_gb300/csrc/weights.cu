@@ -249,12 +249,32 @@ __device__ void block_assemble(double* A, double* A0, const double* s_mu, const 
     }
 }
 
+// Pivot-search key of |v|: for non-negative doubles the IEEE bit patterns order
+// like the values, so the search compares 64-bit integers (off the FP64 pipe).
+// NaN maps to -1 and is never chosen, as with a floating-point compare.
+__device__ __forceinline__ long long abs_key(double v) {
+    const long long b = __double_as_longlong(v) & 0x7fffffffffffffffll;
+    return b > 0x7ff0000000000000ll ? -1ll : b;
+}
+
+// a / d from y = 1/d (correctly rounded) by Markstein's correction (P. Markstein,
+// IBM J. Res. Develop. 34 (1990)): q0 = a y is within an ulp of a / d, the
+// remainder a - q0 d is exact in one fused multiply-add, and q0 + (a - q0 d) y
+// rounds to the correctly rounded quotient, barring underflow and overflow.
+// Three FP64 instructions per quotient once y is known.
+__device__ __forceinline__ double div_by_recip(double a, double d, double y) {
+    const double q0 = a * y;
+    return fma(fma(-q0, d, a), y, q0);
+}
+
 // Gaussian elimination with partial pivoting (the first row holding the largest
 // |pivot| wins) on the augmented system [M | B] (n x LDA, NRHS = LDA - n right-hand
 // sides), then back substitution by warp 0: the solutions overwrite B.  Each
 // pivot's reciprocal is taken once during the elimination (lane 0 of warp 0, kept
-// in s_rdiag[n]) and the back substitution multiplies by it.  Returns true
-// (uniformly) if a pivot was zero or not finite.  Starts and ends with a barrier.
+// in s_rdiag[n]); the multipliers a_rk / a_kk are formed from it by Markstein's
+// correction (the exact quotients), and the back substitution multiplies by it.
+// Returns true (uniformly) if a pivot was zero or not finite.  Starts and ends
+// with a barrier.
 template <int M, int LDA>
 __device__ bool block_lu_solve(double* A, int* s_piv, int* s_flag, double* s_rdiag) {
     using C = WCfg<M>;
@@ -264,10 +284,10 @@ __device__ bool block_lu_solve(double* A, int* s_piv, int* s_flag, double* s_rdi
     __syncthreads();
     for (int k = 0; k < n; ++k) {
         if (warp == 0) {
-            double best = -1.0;
+            long long best = -1;
             int bidx = n;
             for (int r = k + lane; r < n; r += 32) {
-                const double v = fabs(A[r * LDA + k]);
+                const long long v = abs_key(A[r * LDA + k]);
                 if (v > best) {
                     best = v;
                     bidx = r;
@@ -275,7 +295,7 @@ __device__ bool block_lu_solve(double* A, int* s_piv, int* s_flag, double* s_rdi
             }
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
-                const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+                const long long ob = __shfl_xor_sync(0xffffffffu, best, off);
                 const int oi = __shfl_xor_sync(0xffffffffu, bidx, off);
                 if (ob > best || (ob == best && oi < bidx)) {
                     best = ob;
@@ -284,7 +304,8 @@ __device__ bool block_lu_solve(double* A, int* s_piv, int* s_flag, double* s_rdi
             }
             if (lane == 0) {
                 *s_piv = bidx;
-                if (!(best > 0.0) || !isfinite(best) || bidx >= n) {
+                // zero, NaN-only or infinite pivot column: singular
+                if (best <= 0 || best >= 0x7ff0000000000000ll || bidx >= n) {
                     *s_flag = 1;
                 } else {
                     s_rdiag[k] = 1.0 / A[bidx * LDA + k];
@@ -302,8 +323,8 @@ __device__ bool block_lu_solve(double* A, int* s_piv, int* s_flag, double* s_rdi
             }
             __syncthreads();
         }
-        const double piv = A[k * LDA + k];
-        for (int r = k + 1 + t; r < n; r += NT) A[r * LDA + k] = A[r * LDA + k] / piv;
+        const double piv = A[k * LDA + k], rp = s_rdiag[k];
+        for (int r = k + 1 + t; r < n; r += NT) A[r * LDA + k] = div_by_recip(A[r * LDA + k], piv, rp);
         __syncthreads();
         const int rows = n - k - 1;
         const int cols = LDA - k - 1;
