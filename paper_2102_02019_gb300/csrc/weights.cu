@@ -32,7 +32,11 @@ struct WCfg {
     static constexpr int LDA = n + 6;                  // augmented row length
     static constexpr int NPOW = 2 * M + 1;                    // powers 0..2M
     static constexpr int NMOM = (2 * M + 1) * (2 * M + 2) / 2;  // moments p + q <= 2M
-    static constexpr size_t chunk_bytes = size_t(2) * NT * NPOW * sizeof(double);
+    // neighbours per round of the moment accumulation: the x and y power tables of
+    // a round (2 MCH NPOW doubles) share shared memory with the LU matrix, and
+    // rounds of 64 keep them no larger than it, so that more CTAs fit on an SM
+    static constexpr int MCH = NT < 64 ? NT : 64;
+    static constexpr size_t chunk_bytes = size_t(2) * MCH * NPOW * sizeof(double);
     static constexpr size_t lu_bytes(bool resid) {
         return (size_t(n) * LDA + (resid ? size_t(n) * n : 0)) * sizeof(double);
     }
@@ -164,13 +168,14 @@ __device__ void build_he(double* s_he) {
 
 // Weighted moments mu_{p,q} = sum_j psi_j (x_ji/h)^p (y_ji/h)^q, p + q <= 2M, over
 // the candidate neighbours col[r0 .. r1) with stencil scale g.hi (candidates
-// beyond 2h have psi = 0 and add nothing).  XP, YP: 2 NT (2M+1) doubles of
-// scratch; s_mu: (2M+1)(2M+2)/2 doubles.  Ends with a barrier.
+// beyond 2h have psi = 0 and add nothing), in rounds of MCH neighbours.  XP, YP:
+// 2 MCH (2M+1) doubles of scratch; s_mu: (2M+1)(2M+2)/2 doubles.  Ends with a
+// barrier.
 template <int M>
 __device__ void block_moments(const double* __restrict__ xy, const int32_t* __restrict__ col, int r0,
                               int r1, const NodeGeom& g, double* XP, double* YP, double* s_mu) {
     using C = WCfg<M>;
-    constexpr int NT = C::NT, NPOW = C::NPOW, NMOM = C::NMOM;
+    constexpr int NT = C::NT, NPOW = C::NPOW, NMOM = C::NMOM, MCH = C::MCH;
     constexpr int MPT = (NMOM + NT - 1) / NT;  // moments per thread
     const int t = threadIdx.x;
     int mp[MPT], mq[MPT];
@@ -184,8 +189,8 @@ __device__ void block_moments(const double* __restrict__ xy, const int32_t* __re
         mp[u] = d - (idx - d * (d + 1) / 2);
         mq[u] = d - mp[u];
     }
-    for (int c0 = r0; c0 < r1; c0 += NT) {
-        const int cnt = min(NT, r1 - c0);
+    for (int c0 = r0; c0 < r1; c0 += MCH) {
+        const int cnt = min(MCH, r1 - c0);
         if (t < cnt) {
             const int j = col[c0 + t];
             const double dx = min_image(__dsub_rn(xy[2 * j], g.xi), g.Lx, g.px);
@@ -339,17 +344,14 @@ __device__ bool block_lu_solve(double* A, int* s_piv, int* s_flag, double* s_rdi
     static_assert(NRHS <= 32, "one lane per right-hand side");
     if (!singular && warp == 0) {
         for (int k = n - 1; k >= 0; --k) {
-            // lane d scales right-hand side d
-            const double mine = lane < NRHS ? A[k * LDA + n + lane] * s_rdiag[k] : 0.0;
-            double psi[NRHS];
-#pragma unroll
-            for (int d = 0; d < NRHS; ++d) psi[d] = __shfl_sync(0xffffffffu, mine, d);
-            for (int r = lane; r < k; r += 32) {
-                const double ark = A[r * LDA + k];
-#pragma unroll
-                for (int d = 0; d < NRHS; ++d) A[r * LDA + n + d] -= ark * psi[d];
+            // lane d finishes unknown k of right-hand side d, then the lanes take the
+            // (row, right-hand side) pairs of rows 0 .. k-1
+            if (lane < NRHS) A[k * LDA + n + lane] *= s_rdiag[k];
+            __syncwarp();
+            for (int idx = lane; idx < k * NRHS; idx += 32) {
+                const int r = idx / NRHS, d = idx - r * NRHS;
+                A[r * LDA + n + d] -= A[r * LDA + k] * A[k * LDA + n + d];
             }
-            if (lane < NRHS) A[k * LDA + n + lane] = mine;
             __syncwarp();
         }
     }
@@ -417,7 +419,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
     if (t == 0) s_nonfinite = 0;
     if (t <= 2 * M) s_hp[t] = pow(g.hi, double(t - M));
     build_he<M>(s_he);
-    block_moments<M>(xy, col, r0, r1, g, smem, smem + NT * C::NPOW, s_mu);
+    block_moments<M>(xy, col, r0, r1, g, smem, smem + C::MCH * C::NPOW, s_mu);
     block_assemble<M, LDA>(A, RESID ? A0 : nullptr, s_mu, s_he);
     for (int idx = t; idx < n * 6; idx += NT) {  // selectors C~^d
         const int q = idx / 6, d = idx - q * 6;
@@ -774,7 +776,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT, stencil_opt_min_blocks<M>())
         }
         if (block_sum<NT>(cnt, s_red) < double(n)) break;
         // Section 4 steps 1-2: solve for x, y and L and test the Laplacian residual
-        block_moments<M>(xy, col, r0, r1, g, smem, smem + NT * C::NPOW, s_mu);
+        block_moments<M>(xy, col, r0, r1, g, smem, smem + C::MCH * C::NPOW, s_mu);
         block_assemble<M, LDA>(A, A0, s_mu, s_he);
         for (int idx = t; idx < n * 3; idx += NT) {
             const int q = idx / 3, d = idx - q * 3;
