@@ -719,12 +719,18 @@ __device__ double block_amplitude_max(const double* __restrict__ xy, const int32
     return *s_amax;
 }
 
-// Register budget of the stencil-optimisation kernel: at most 128 per thread
-// (its 48 per-lane amplitude sums need ~150 unconstrained, which left 4 CTAs of
-// 96 threads per SM at m = 6 and the FP64 pipe 72 % busy).
+// Register budget of the stencil-optimisation kernel: resident CTAs per SM as for
+// 96 registers a thread (80 at m = 6, 96 at m = 8 after rounding).  Its 48
+// per-lane amplitude sums need ~150 unconstrained, which left 4 CTAs of 96 threads
+// per SM at m = 6 and the FP64 pipe 72 % busy; the spills of the tighter budget
+// stay in L1 and cost less than the occupancy gains (full size: 128 registers
+// 2.69 / 1.93 s, 96: 2.57 / 1.80 s for m = 6 / 8).
+#ifndef LABFM_SOPT_REGS
+#define LABFM_SOPT_REGS 96
+#endif
 template <int M>
 constexpr int stencil_opt_min_blocks() {
-    return 65536 / (WCfg<M>::NT * 128);
+    return 65536 / (WCfg<M>::NT * LABFM_SOPT_REGS);
 }
 
 template <int M>
