@@ -418,14 +418,16 @@ int labfm_rk_step_adjoint(const labfm_plan* plan, const void* Q, void* lambda, d
 /*
  * The same reverse step without the recompute, for a caller that keeps the stage
  * states: labfm_rk_step_record advances Q (3 x N, in place) by one step exactly as
- * labfm_rk_step does and stores the step's four stage states X_1..X_4 (the state
- * each of the four RK stages evaluates eq. icns at) in `states`, in the plan's
- * packed node layout (opaque; labfm_stage_states_bytes bytes, 16-byte aligned);
- * labfm_rk_step_adjoint_recorded then applies the reverse sweep of
- * labfm_rk_step_adjoint to lambda with those states.  The results are identical
- * to labfm_rk_step and labfm_rk_step_adjoint.  A checkpointed rollout that
- * recomputes a segment with labfm_rk_step_record skips the three stage
- * evaluations per step that labfm_rk_step_adjoint repeats.
+ * labfm_rk_step does and stores in `states` the step's four stage states X_1..X_4
+ * (the state each of the four RK stages evaluates eq. icns at) and, per stage and
+ * node, the eight combinations of the derivatives at X_k that the transpose of
+ * eq. icns with respect to the node's own state needs (opaque layout;
+ * labfm_stage_states_bytes bytes, 16-byte aligned); labfm_rk_step_adjoint_recorded
+ * then applies the reverse sweep of labfm_rk_step_adjoint to lambda with them.
+ * The results are identical to labfm_rk_step and labfm_rk_step_adjoint (which
+ * recomputes the same records).  A checkpointed rollout that recomputes a segment
+ * with labfm_rk_step_record skips the four stage evaluations per step that
+ * labfm_rk_step_adjoint repeats; neither reverse sweep gathers derivatives again.
  *   work  (record): labfm_rk_workspace_bytes; (adjoint): labfm_adjoint_workspace_bytes
  */
 size_t labfm_stage_states_bytes(const labfm_plan* plan);

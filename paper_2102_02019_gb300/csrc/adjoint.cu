@@ -81,24 +81,16 @@ PlanView<T> tview(const labfm_plan* p) {
 
 // ---------------------------------------------------------------- pass A
 
-template <typename T, int G, bool KAHAN, bool SCALED>
-__global__ void k_adj_pointwise(PlanView<T> P, const Packed<T>* X, const Packed<T>* M,
-                                G12<T>* __restrict__ gout, Packed<T>* __restrict__ oout, Phys<T> ph) {
-    const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    const int64_t node = gt / G;
-    const int gl = int(gt % G);
-    const int i = node < P.N ? int(node) : -1;
-    const AoS<T> fld{X};
-    T a = 0, u = 0, v = 0;
-    if (i >= 0) fld.get(i, a, u, v);
-    T d[12];
-    gather_derivatives<T, G, KAHAN>(P, fld, i, gl, a, u, v, d);
-    if (i < 0 || gl != 0) return;
+// Pass A at node i from its state (a, u, v), its eight derivative combinations c
+// (own_coeffs) and its cotangent M_i: the twelve derivative adjoints g_i and the
+// own-value adjoints o_i.
+template <typename T, bool SCALED>
+__device__ __forceinline__ void node_adjoints(const PlanView<T>& P, int i, T a, T u, T v,
+                                              const T (&c)[8], const Packed<T>* M,
+                                              G12<T>* __restrict__ gout, Packed<T>* __restrict__ oout,
+                                              const Phys<T>& ph) {
     const T is = SCALED ? P.inv_s[i] : T(1);
     const T s1 = SCALED ? is : T(1), s2 = SCALED ? is * is : T(1);
-    const T ax = d[0] * s1, ay = d[1] * s1;
-    const T ux = d[2] * s1, uy = d[3] * s1, uxx = d[4] * s2, uxy = d[5] * s2, uyy = d[6] * s2;
-    const T vx = d[7] * s1, vy = d[8] * s1, vxx = d[9] * s2, vxy = d[10] * s2, vyy = d[11] * s2;
     T ma, mu, mv;
     unpack(M, i, ma, mu, mv);
     const T nu = ph.mu * exp_neg(a);
@@ -117,11 +109,47 @@ __global__ void k_adj_pointwise(PlanView<T> P, const Packed<T>* X, const Packed<
     g[10] = (nu * third * mu) * s2;      // v_xy
     g[11] = (nu * four_thirds * mv) * s2;// v_yy
     g12_store(gout, i, g);
-    const T oa = -nu * ((four_thirds * uxx + uyy + third * vxy) * mu +
-                        (four_thirds * vyy + vxx + third * uxy) * mv);
-    const T ou = -(ax * ma + ux * mu + vx * mv);
-    const T ov = -(ay * ma + uy * mu + vy * mv);
+    // c = (a_x, a_y, u_x, u_y, v_x, v_y, 4/3 u_xx + u_yy + 1/3 v_xy, 4/3 v_yy + v_xx + 1/3 u_xy)
+    const T oa = -nu * (c[6] * mu + c[7] * mv);
+    const T ou = -(c[0] * ma + c[2] * mu + c[4] * mv);
+    const T ov = -(c[1] * ma + c[3] * mu + c[5] * mv);
     store(oout, i, oa, ou, ov);
+}
+
+// Pass A with the derivatives gathered at X (the single right-hand-side adjoint).
+template <typename T, int G, bool KAHAN, bool SCALED>
+__global__ void k_adj_pointwise(PlanView<T> P, const Packed<T>* X, const Packed<T>* M,
+                                G12<T>* __restrict__ gout, Packed<T>* __restrict__ oout, Phys<T> ph) {
+    const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t node = gt / G;
+    const int gl = int(gt % G);
+    const int i = node < P.N ? int(node) : -1;
+    const AoS<T> fld{X};
+    T a = 0, u = 0, v = 0;
+    if (i >= 0) fld.get(i, a, u, v);
+    T d[12];
+    gather_derivatives<T, G, KAHAN>(P, fld, i, gl, a, u, v, d);
+    if (i < 0 || gl != 0) return;
+    T c[8];
+    own_coeffs<T, SCALED>(d, SCALED ? P.inv_s[i] : T(1), c);
+    node_adjoints<T, SCALED>(P, i, a, u, v, c, M, gout, oout, ph);
+}
+
+// Pass A from the derivative combinations the recording step kept (one thread
+// per node, no gather): the reverse sweep of labfm_rk_step_adjoint(_recorded).
+template <typename T, bool SCALED>
+__global__ void k_adj_pointwise_rec(PlanView<T> P, const Packed<T>* X, const D8<T>* __restrict__ D,
+                                    const Packed<T>* M, G12<T>* __restrict__ gout,
+                                    Packed<T>* __restrict__ oout, Phys<T> ph) {
+    for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < P.N;
+         k += int64_t(gridDim.x) * blockDim.x) {
+        const int i = int(k);
+        T a, u, v;
+        unpack(X, i, a, u, v);
+        T c[8];
+        d8_load(D, i, c);
+        node_adjoints<T, SCALED>(P, i, a, u, v, c, M, gout, oout, ph);
+    }
 }
 
 // ---------------------------------------------------------------- pass B
@@ -417,6 +445,7 @@ struct AdjWork {
     Packed<T>* Fb;
     Packed<T>* Ob;
     G12<T>* g;
+    D8<T>* D;  // 4 x N: the stages' derivative combinations (recomputing sweep)
 };
 
 template <typename T>
@@ -429,6 +458,7 @@ AdjWork<T> split_work(const labfm_plan* p, void* work) {
     w.Fb = base + 6 * p->N;
     w.Ob = base + 7 * p->N;
     w.g = reinterpret_cast<G12<T>*>(base + 8 * p->N);
+    w.D = reinterpret_cast<D8<T>*>(w.g + p->N);
     return w;
 }
 
@@ -439,6 +469,16 @@ int pass_a_g(const labfm_plan* p, const Packed<T>* X, const Packed<T>* M, G12<T>
     const int grid = int((p->N * G + p->block - 1) / p->block);
     k_adj_pointwise<T, G, F, F><<<grid, p->block, 0, st>>>(view<T>(p), X, M, g, o, ph);
     LABFM_LAUNCH_CHECK("adjoint pointwise kernel");
+    return LABFM_OK;
+}
+
+template <typename T>
+int pass_a_rec(const labfm_plan* p, const Packed<T>* X, const D8<T>* D, const Packed<T>* M, G12<T>* g,
+               Packed<T>* o, const Phys<T>& ph, cudaStream_t st) {
+    constexpr bool F = std::is_same<T, float>::value;
+    const int grid = int(std::min<int64_t>((p->N + 255) / 256, 152 * 16));
+    k_adj_pointwise_rec<T, F><<<grid, 256, 0, st>>>(view<T>(p), X, D, M, g, o, ph);
+    LABFM_LAUNCH_CHECK("adjoint pointwise kernel (recorded derivatives)");
     return LABFM_OK;
 }
 
@@ -509,16 +549,17 @@ int rhs_adjoint_t(const labfm_plan* p, const void* fields, const void* lambda, v
     return unpack_fields(p, w.Lam, grad, st);
 }
 
-// The reverse sweep of one step given its stage states X[0..3] (packed).
+// The reverse sweep of one step given its stage states X[0..3] (packed) and
+// their derivative combinations D (4 x N).
 template <typename T>
-int adjoint_sweep_t(const labfm_plan* p, const Packed<T>* const (&X)[4], void* lambda, double dt,
-                    const Phys<T>& ph, AdjWork<T>& w, cudaStream_t st) {
+int adjoint_sweep_t(const labfm_plan* p, const Packed<T>* const (&X)[4], const D8<T>* D, void* lambda,
+                    double dt, const Phys<T>& ph, AdjWork<T>& w, cudaStream_t st) {
     int rc;
     // filter transpose, then the stages backwards
     if ((rc = pack_fields(p, lambda, w.Ob, st))) return rc;
     if ((rc = filt_adj<T>(p, w.Ob, w.Lam, w.Fb, dt, kRkB[3], st))) return rc;
     for (int k = 3; k >= 0; --k) {
-        if ((rc = pass_a<T>(p, X[k], w.Fb, w.g, w.Ob, ph, st))) return rc;
+        if ((rc = pass_a_rec<T>(p, X[k], D + k * p->N, w.Fb, w.g, w.Ob, ph, st))) return rc;
         const double bprev = k > 0 ? kRkB[k - 1] : 0.0;
         const double cprev = k > 0 ? kRkA[k - 1] - kRkB[k - 1] : 0.0;
         if ((rc = pass_b<T>(p, 1, w.g, w.Ob, nullptr, w.Lam, k > 0 ? w.Fb : nullptr, dt, bprev, cprev,
@@ -534,11 +575,12 @@ int rk_step_adjoint_t(const labfm_plan* p, const void* Q, void* lambda, double d
     const Phys<T> ph{T(php->c2), T(php->mu), T(php->gx), T(php->gy)};
     AdjWork<T> w = split_work<T>(p, work);
     int rc;
-    // forward recompute of the stage states X1..X4 of this step
+    // forward recompute of the stage states X1..X4 of this step and of their
+    // derivative combinations (the same kernels as labfm_rk_step_record)
     if ((rc = pack_fields(p, Q, w.X[0], st))) return rc;
-    if ((rc = forward_stage_states(p, w.X[0], w.P, w.X[1], w.X[2], w.X[3], dt, php, st))) return rc;
+    if ((rc = forward_stages(p, w.X[0], w.P, w.X[1], w.X[2], w.X[3], w.D, dt, php, st))) return rc;
     const Packed<T>* const X[4] = {w.X[0], w.X[1], w.X[2], w.X[3]};
-    return adjoint_sweep_t<T>(p, X, lambda, dt, ph, w, st);
+    return adjoint_sweep_t<T>(p, X, w.D, lambda, dt, ph, w, st);
 }
 
 template <typename T>
@@ -548,7 +590,8 @@ int rk_step_adjoint_recorded_t(const labfm_plan* p, const void* states, void* la
     AdjWork<T> w = split_work<T>(p, work);
     const Packed<T>* S = static_cast<const Packed<T>*>(states);
     const Packed<T>* const X[4] = {S, S + p->N, S + 2 * p->N, S + 3 * p->N};
-    return adjoint_sweep_t<T>(p, X, lambda, dt, ph, w, st);
+    const D8<T>* D = reinterpret_cast<const D8<T>*>(S + 4 * p->N);
+    return adjoint_sweep_t<T>(p, X, D, lambda, dt, ph, w, st);
 }
 
 template <typename T>
@@ -562,8 +605,9 @@ int filter_adjoint_t(const labfm_plan* p, const void* lam_in, void* lam_out, voi
 }
 
 size_t adjoint_work_bytes(const labfm_plan* p) {
-    if (p->dtype == LABFM_F32) return size_t(p->N) * (8 * sizeof(Packed<float>) + sizeof(G12<float>));
-    return size_t(p->N) * (8 * sizeof(Packed<double>) + sizeof(G12<double>));
+    if (p->dtype == LABFM_F32)
+        return size_t(p->N) * (8 * sizeof(Packed<float>) + sizeof(G12<float>) + 4 * sizeof(D8<float>));
+    return size_t(p->N) * (8 * sizeof(Packed<double>) + sizeof(G12<double>) + 4 * sizeof(D8<double>));
 }
 
 int check_adjoint(const labfm_plan* p, void* work, size_t work_bytes) {
@@ -617,8 +661,7 @@ extern "C" int labfm_rk_step_adjoint(const labfm_plan* p, const void* Q, void* l
 
 extern "C" size_t labfm_stage_states_bytes(const labfm_plan* p) {
     if (!p || !p->row_ptr) return 0;
-    return size_t(4) * size_t(p->N) *
-           (p->dtype == LABFM_F32 ? sizeof(Packed<float>) : sizeof(Packed<double>));
+    return size_t(4) * size_t(p->N) * (packed_bytes(p) + d8_bytes(p));
 }
 
 extern "C" int labfm_rk_step_record(const labfm_plan* p, void* Q, void* states, size_t states_bytes,

@@ -572,5 +572,58 @@ struct Phys {
     T c2, mu, gx, gy;
 };
 
+// The eight combinations of a node's derivatives through which the transpose of
+// eq. icns with respect to the node's own state depends on them (physical units):
+// a_x, a_y, u_x, u_y, v_x, v_y and the viscous sums 4/3 u_xx + u_yy + 1/3 v_xy,
+// 4/3 v_yy + v_xx + 1/3 u_xy.  Kept per stage by the recording time step, so that
+// the reverse sweep need not gather the derivatives again.
+template <typename T> struct D8;
+template <> struct D8<float> { float4 q[2]; };
+template <> struct D8<double> { double2 q[4]; };
+
+template <typename T, bool SCALED>
+__device__ __forceinline__ void own_coeffs(const T (&d)[12], T inv_s, T (&c)[8]) {
+    const T s1 = SCALED ? inv_s : T(1);
+    const T s2 = SCALED ? inv_s * inv_s : T(1);
+    const T third = T(1) / T(3);
+    const T four_thirds = T(4) / T(3);
+    c[0] = d[0] * s1;
+    c[1] = d[1] * s1;
+    c[2] = d[2] * s1;
+    c[3] = d[3] * s1;
+    c[4] = d[7] * s1;
+    c[5] = d[8] * s1;
+    c[6] = four_thirds * (d[4] * s2) + d[6] * s2 + third * (d[10] * s2);
+    c[7] = four_thirds * (d[11] * s2) + d[9] * s2 + third * (d[5] * s2);
+}
+
+__device__ __forceinline__ void d8_store(D8<float>* p, int64_t i, const float (&c)[8]) {
+    p[i].q[0] = make_float4(c[0], c[1], c[2], c[3]);
+    p[i].q[1] = make_float4(c[4], c[5], c[6], c[7]);
+}
+__device__ __forceinline__ void d8_store(D8<double>* p, int64_t i, const double (&c)[8]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) p[i].q[k] = make_double2(c[2 * k], c[2 * k + 1]);
+}
+__device__ __forceinline__ void d8_load(const D8<float>* p, int64_t i, float (&c)[8]) {
+    const float4 a = p[i].q[0], b = p[i].q[1];
+    c[0] = a.x;
+    c[1] = a.y;
+    c[2] = a.z;
+    c[3] = a.w;
+    c[4] = b.x;
+    c[5] = b.y;
+    c[6] = b.z;
+    c[7] = b.w;
+}
+__device__ __forceinline__ void d8_load(const D8<double>* p, int64_t i, double (&c)[8]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const double2 t = p[i].q[k];
+        c[2 * k] = t.x;
+        c[2 * k + 1] = t.y;
+    }
+}
+
 }  // namespace
 }  // namespace labfm

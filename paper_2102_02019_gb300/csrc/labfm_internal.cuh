@@ -141,14 +141,21 @@ int set_node_dt(labfm_plan* p, const double* dt_inst_host, cudaStream_t st);
 // layout of the step kernels (step.cu).
 int pack_fields(const labfm_plan* p, const void* soa, void* packed, cudaStream_t st);
 int unpack_fields(const labfm_plan* p, const void* packed, void* soa, cudaStream_t st);
-// Stages 1-3 of one RK step from the packed state X1, storing the stage states
-// X2, X3, X4 (P receives the partial solution register) (step.cu).
-int forward_stage_states(const labfm_plan* p, const void* X1, void* P, void* X2, void* X3,
-                         void* X4, double dt, const labfm_phys* ph, cudaStream_t st);
+// The four stages of one RK step from the packed state X1, storing the stage
+// states X2, X3, X4; P receives the partial solution register (after stage 4, the
+// unfiltered next state).  Every stage also stores, at D + (stage - 1) N (D8
+// records of the plan's precision), the eight derivative combinations the
+// reverse sweep needs (step.cu).
+int forward_stages(const labfm_plan* p, const void* X1, void* P, void* X2, void* X3, void* X4,
+                   void* D, double dt, const labfm_phys* ph, cudaStream_t st);
 // One RK step from Q (3 x N SoA, replaced by the next state) that stores its four
-// stage states, packed, in X (4 x N); P and Y are scratch packed states (step.cu).
+// stage states, packed, in X (4 x N) followed by their derivative combinations
+// (4 x N D8 records); P and Y are scratch packed states (step.cu).
 int rk_step_record(const labfm_plan* p, void* Q, void* X, void* P, void* Y, double dt,
                    const labfm_phys* ph, cudaStream_t st);
+// Bytes of one packed node state and of one D8 record in the plan's precision.
+size_t packed_bytes(const labfm_plan* p);
+size_t d8_bytes(const labfm_plan* p);
 int launch_stable_dt_instances(const labfm_plan* p, const void* fields, const double* s, double c,
                                double mu, double* dt_inst, cudaStream_t st);
 int persistent_grid(const labfm_plan* p);

@@ -145,6 +145,29 @@ __global__ void LABFM_STAGE_BOUNDS k_stage(PlanView<T> P, const Packed<T>* X_in,
     }
 }
 
+// The stage kernel of the recording time step: k_stage (plain grid) that also
+// stores the node's eight derivative combinations for the reverse sweep.
+template <typename T, int G, bool KAHAN, bool SCALED>
+__global__ void LABFM_STAGE_BOUNDS k_stage_rec(PlanView<T> P, const Packed<T>* X_in, const Packed<T>* Q_in,
+                                               Packed<T>* Q_out, Packed<T>* X_out, double dt, double bk,
+                                               double ck, Phys<T> ph, D8<T>* __restrict__ Dout) {
+    const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    const int64_t node = gt / G;
+    const int gl = int(gt % G);
+    const int i = node < P.N ? int(node) : -1;
+    const AoS<T> fld{X_in};
+    T ai = 0, ui = 0, vi = 0;
+    if (i >= 0) fld.get(i, ai, ui, vi);
+    T d[12];
+    gather_derivatives<T, G, KAHAN>(P, fld, i, gl, ai, ui, vi, d);
+    stage_epilogue<T, SCALED>(P, i, gl, d, ai, ui, vi, X_in, Q_in, Q_out, X_out, dt, bk, ck, ph);
+    if (i >= 0 && gl == 0) {
+        T c[8];
+        own_coeffs<T, SCALED>(d, SCALED ? P.inv_s[i] : T(1), c);
+        d8_store(Dout, i, c);
+    }
+}
+
 // ---------------------------------------------------------------- staged stage kernel
 //
 // F32 stage kernel with the operator stream staged through shared memory by the
@@ -706,45 +729,67 @@ int unpack_fields(const labfm_plan* p, const void* packed, void* soa, cudaStream
 }
 
 namespace {
+template <typename T, int G>
+int stage_rec_launch_g(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* qin, Packed<T>* qout,
+                       Packed<T>* xout, double dt, double bk, double ck, const Phys<T>& ph, D8<T>* D,
+                       cudaStream_t st) {
+    constexpr bool F = std::is_same<T, float>::value;
+    const int grid = grid_for(p->N * G, kGatherBlock);
+    k_stage_rec<T, G, F, F><<<grid, kGatherBlock, 0, st>>>(view<T>(p), xin, qin, qout, xout, dt, bk, ck, ph,
+                                                           D);
+    LABFM_LAUNCH_CHECK("recording rk stage kernel");
+    return LABFM_OK;
+}
+
 template <typename T>
-int forward_stage_states_t(const labfm_plan* p, const void* X1v, void* Pv, void* X2v, void* X3v,
-                           void* X4v, double dt, const labfm_phys* php, cudaStream_t st) {
+int stage_rec_launch(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* qin, Packed<T>* qout,
+                     Packed<T>* xout, double dt, double bk, double ck, const Phys<T>& ph, D8<T>* D,
+                     cudaStream_t st) {
+    switch (p->group) {
+        case 2: return stage_rec_launch_g<T, 2>(p, xin, qin, qout, xout, dt, bk, ck, ph, D, st);
+        case 4: return stage_rec_launch_g<T, 4>(p, xin, qin, qout, xout, dt, bk, ck, ph, D, st);
+        case 8: return stage_rec_launch_g<T, 8>(p, xin, qin, qout, xout, dt, bk, ck, ph, D, st);
+        case 16: return stage_rec_launch_g<T, 16>(p, xin, qin, qout, xout, dt, bk, ck, ph, D, st);
+        case 32: return stage_rec_launch_g<T, 32>(p, xin, qin, qout, xout, dt, bk, ck, ph, D, st);
+    }
+    return set_error(LABFM_EINVAL, "unsupported group size");
+}
+
+// The four stages with the recording kernel: the same arithmetic per node as the
+// stage kernels of labfm_rk_step (same lanes per node and summation order).
+template <typename T>
+int forward_stages_t(const labfm_plan* p, const void* X1v, void* Pv, void* X2v, void* X3v, void* X4v,
+                     void* Dv, double dt, const labfm_phys* php, cudaStream_t st) {
     const Phys<T> ph{T(php->c2), T(php->mu), T(php->gx), T(php->gy)};
     const Packed<T>* X1 = static_cast<const Packed<T>*>(X1v);
     Packed<T>* P = static_cast<Packed<T>*>(Pv);
     Packed<T>* X2 = static_cast<Packed<T>*>(X2v);
     Packed<T>* X3 = static_cast<Packed<T>*>(X3v);
     Packed<T>* X4 = static_cast<Packed<T>*>(X4v);
-    // the plain (non-persistent) stage kernel: no work-queue tickets needed
-    labfm_plan q = *p;
-    q.persistent = false;
+    D8<T>* D = static_cast<D8<T>*>(Dv);
+    const int64_t N = p->N;
     int rc;
-    if ((rc = stage_launch<T>(&q, X1, X1, P, X2, dt, kRkB[0], kRkA[0] - kRkB[0], ph, nullptr, st)))
+    if ((rc = stage_rec_launch<T>(p, X1, X1, P, X2, dt, kRkB[0], kRkA[0] - kRkB[0], ph, D, st))) return rc;
+    if ((rc = stage_rec_launch<T>(p, X2, P, P, X3, dt, kRkB[1], kRkA[1] - kRkB[1], ph, D + N, st))) return rc;
+    if ((rc = stage_rec_launch<T>(p, X3, P, P, X4, dt, kRkB[2], kRkA[2] - kRkB[2], ph, D + 2 * N, st)))
         return rc;
-    if ((rc = stage_launch<T>(&q, X2, P, P, X3, dt, kRkB[1], kRkA[1] - kRkB[1], ph, nullptr, st)))
-        return rc;
-    return stage_launch<T>(&q, X3, P, P, X4, dt, kRkB[2], kRkA[2] - kRkB[2], ph, nullptr, st);
+    return stage_rec_launch<T>(p, X4, P, P, nullptr, dt, kRkB[3], 0.0, ph, D + 3 * N, st);
 }
-}  // namespace
 
-namespace {
 // One step that keeps its stage states: X1 = pack(Q), X2..X4 the inputs of
-// stages 2..4, then stage 4 and the filter as labfm_rk_step takes them; Q is
-// replaced by the next state.  P and Y: scratch packed states.
+// stages 2..4, the derivative combinations of all four after them, then the
+// filter as labfm_rk_step takes it; Q is replaced by the next state.  P and Y:
+// scratch packed states.
 template <typename T>
 int rk_step_record_t(const labfm_plan* p, void* Q, void* Xv, void* Pv, void* Yv, double dt,
                      const labfm_phys* php, cudaStream_t st) {
-    const Phys<T> ph{T(php->c2), T(php->mu), T(php->gx), T(php->gy)};
     Packed<T>* X = static_cast<Packed<T>*>(Xv);
     Packed<T>* P = static_cast<Packed<T>*>(Pv);
     Packed<T>* Y = static_cast<Packed<T>*>(Yv);
     int rc;
     if ((rc = pack_fields(p, Q, X, st))) return rc;
-    if ((rc = forward_stage_states_t<T>(p, X, P, X + p->N, X + 2 * p->N, X + 3 * p->N, dt, php, st)))
-        return rc;
-    labfm_plan q = *p;
-    q.persistent = false;
-    if ((rc = stage_launch<T>(&q, X + 3 * p->N, P, P, nullptr, dt, kRkB[3], 0.0, ph, nullptr, st)))
+    if ((rc = forward_stages_t<T>(p, X, P, X + p->N, X + 2 * p->N, X + 3 * p->N, X + 4 * p->N, dt, php,
+                                  st)))
         return rc;
     if ((rc = filter_aos<T>(p, P, Y, st))) return rc;
     return unpack_fields(p, Y, Q, st);
@@ -757,10 +802,18 @@ int rk_step_record(const labfm_plan* p, void* Q, void* X, void* P, void* Y, doub
                                  : rk_step_record_t<double>(p, Q, X, P, Y, dt, ph, st);
 }
 
-int forward_stage_states(const labfm_plan* p, const void* X1, void* P, void* X2, void* X3,
-                         void* X4, double dt, const labfm_phys* ph, cudaStream_t st) {
-    return p->dtype == LABFM_F32 ? forward_stage_states_t<float>(p, X1, P, X2, X3, X4, dt, ph, st)
-                                 : forward_stage_states_t<double>(p, X1, P, X2, X3, X4, dt, ph, st);
+int forward_stages(const labfm_plan* p, const void* X1, void* P, void* X2, void* X3, void* X4, void* D,
+                   double dt, const labfm_phys* ph, cudaStream_t st) {
+    return p->dtype == LABFM_F32 ? forward_stages_t<float>(p, X1, P, X2, X3, X4, D, dt, ph, st)
+                                 : forward_stages_t<double>(p, X1, P, X2, X3, X4, D, dt, ph, st);
+}
+
+size_t packed_bytes(const labfm_plan* p) {
+    return p->dtype == LABFM_F32 ? sizeof(Packed<float>) : sizeof(Packed<double>);
+}
+
+size_t d8_bytes(const labfm_plan* p) {
+    return p->dtype == LABFM_F32 ? sizeof(D8<float>) : sizeof(D8<double>);
 }
 
 int rk_pack(const labfm_plan* p, const void* Q, void* work, cudaStream_t st) {
