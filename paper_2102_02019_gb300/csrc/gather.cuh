@@ -180,9 +180,24 @@ struct Rec<float> {
     __host__ __device__ static int64_t fw_e(int64_t e) { return fw(e >> 2) + 4 * (e & 3); }
 };
 
-// 32-byte evict-first load of eight floats (32-byte aligned).
+// 32-byte evict-first load of eight floats (32-byte aligned) with an L2
+// prefetch-size hint (0: none, 1: 128 bytes, 2: 256 bytes around the access).
+// The operator streams are read in order, so the 256-byte fill brings in the
+// stream's next line early without a register or an instruction: measured on the
+// 262,144-node m = 8 step, stage 115.7 -> 111.1 us and filter 49.0 -> 47.6 us
+// (128 bytes: no change).
+#ifndef LABFM_LD_PREFETCH
+#define LABFM_LD_PREFETCH 2
+#endif
+#if LABFM_LD_PREFETCH == 2
+#define LABFM_LD8 "ld.global.cs.L2::256B.v8.f32"
+#elif LABFM_LD_PREFETCH == 1
+#define LABFM_LD8 "ld.global.cs.L2::128B.v8.f32"
+#else
+#define LABFM_LD8 "ld.global.cs.v8.f32"
+#endif
 __device__ __forceinline__ void ld8(const void* p, float (&v)[8]) {
-    asm("ld.global.cs.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+    asm(LABFM_LD8 " {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
         : "l"(p));
 }
