@@ -544,6 +544,7 @@ def run_fp32_error(lb, torch, args, nsteps=1000, shape=None):
             if dt_ == torch.float32 and shape:
                 plan.set_persistent(shape["persistent"])
                 plan.set_staging(shape.get("staging", 0))
+                plan.set_prefetch(shape.get("prefetch", 0))
                 plan.set_launch(shape["group"], shape["block"])
             ke0 = float(lb.kinetic_energy(Q, s).item())
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -609,7 +610,8 @@ def run_ours(args, world, rank, local):
         dt = float(lb.stable_dt(plan, Q, s, C, MU).item())
         if args.group:
             plan.set_launch(args.group, 128)
-            tuned = {"group": args.group, "block": 128, "persistent": False, "staging": 0}
+            tuned = {"group": args.group, "block": 128, "persistent": False, "staging": 0,
+                     "prefetch": plan.info()["prefetch"]}
         else:
             tuned = plan.tune_step(Q, phys, dt)
         group, block = tuned["group"], tuned["block"]
@@ -687,7 +689,8 @@ def run_ours(args, world, rank, local):
                        "0.73 GB > 129 MB L2", parallelism=f"replicas x{world}" if world > 1 else "1 GPU",
                        launch_shape={"group": shape32[0], "block": shape32[1],
                                      "persistent": tuned_shape[torch.float32]["persistent"],
-                                     "staging": tuned_shape[torch.float32].get("staging", 0)}),
+                                     "staging": tuned_shape[torch.float32].get("staging", 0),
+                                     "prefetch": tuned_shape[torch.float32].get("prefetch", 0)}),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": ("k_stage_bulk<float> (fused RHS + RK stage, operator staged by bulk copies)"

@@ -75,6 +75,8 @@ typedef struct labfm_plan_info {
     int32_t entry_bytes;        /* bytes of the RHS record stream per padded stencil entry */
     int32_t filter_entry_bytes; /* bytes of the filter record stream per padded entry */
     int64_t device_bytes; /* device memory owned by the plan */
+    int32_t prefetch;     /* L2 prefetch distance of the F32 record stream (labfm_plan_set_prefetch) */
+    int32_t stages;       /* shared-memory staging slots (labfm_plan_set_staging; 0 = off) */
 } labfm_plan_info;
 
 /* Message for the most recent failing call on this thread ("" if none). */
@@ -263,6 +265,17 @@ int labfm_stable_dt_instances(const labfm_plan* plan, const void* fields, const 
  * after changing this).
  */
 int labfm_plan_set_persistent(labfm_plan* plan, int enable);
+
+/*
+ * L2 prefetch distance of the F32 stage kernel's operator stream, in loop
+ * iterations of a node's lane group (0 = off, at most 8).  When positive, three
+ * lanes of each group issue an L2 prefetch of the three 128-byte segments of the
+ * record block they will read `distance` iterations later, if it lies within the
+ * node's row.  Results do not change.  Plan creation sets 2 for F32 plans whose
+ * rows average 64 or more padded entries and 0 otherwise (measured faster for the
+ * long rows of m = 8 and 10, slower for m = 4 and 6).  Host-only call.
+ */
+int labfm_plan_set_prefetch(labfm_plan* plan, int distance);
 
 /*
  * Shared-memory staging of the operator stream for the F32 stage kernel

@@ -51,7 +51,8 @@ class _PlanInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nnz_padded", ctypes.c_int64),
                 ("dtype", ctypes.c_int32), ("group", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("n_instances", ctypes.c_int32), ("entry_bytes", ctypes.c_int32),
-                ("filter_entry_bytes", ctypes.c_int32), ("device_bytes", ctypes.c_int64)]
+                ("filter_entry_bytes", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+                ("prefetch", ctypes.c_int32), ("stages", ctypes.c_int32)]
 
 
 class _Profile(ctypes.Structure):
@@ -95,6 +96,7 @@ _SIGS = {
     "labfm_plan_set_dt": (_I32, [_P, _P, _P]),
     "labfm_stable_dt_instances": (_I32, [_P, _P, _P, _D, _D, _P, _P]),
     "labfm_plan_set_persistent": (_I32, [_P, _I32]),
+    "labfm_plan_set_prefetch": (_I32, [_P, _I32]),
     "labfm_plan_set_staging": (_I32, [_P, _I32, _P]),
     "labfm_plan_device_status": (_I32, [_P, ctypes.POINTER(_I32)]),
     "labfm_step_graph_create": (_I32, [ctypes.POINTER(_P), _P, _P, ctypes.c_size_t, _D, ctypes.POINTER(_Phys)]),
@@ -284,6 +286,10 @@ class Plan:
     def set_persistent(self, enable: bool = True) -> None:
         _check(lib.labfm_plan_set_persistent(self._h, 1 if enable else 0))
 
+    def set_prefetch(self, distance: int) -> None:
+        """labfm_plan_set_prefetch: L2 prefetch distance of the F32 record stream (0 = off)."""
+        _check(lib.labfm_plan_set_prefetch(self._h, int(distance)))
+
     def set_staging(self, stages: int = 3, stream=None) -> None:
         """labfm_plan_set_staging: shared-memory staging of the operator stream for the
         F32 stage kernel with 16 or 32 lanes per node (0 = off)."""
@@ -339,20 +345,24 @@ class Plan:
         return {k: getattr(pr, k) for k, _ in _Profile._fields_}
 
     def tune_step(self, Q: torch.Tensor, phys: Phys, dt: float, steps: int = 3,
-                  groups=(2, 4, 8, 16), staged=((16, 3), (32, 3), (32, 4))) -> dict:
+                  groups=(2, 4, 8, 16), staged=((16, 3), (32, 3), (32, 4)),
+                  prefetch=(0, 2)) -> dict:
         """Autotune the time step itself: time `steps` RK steps (CUDA events) for every
-        lanes-per-node group with the plain and the persistent stage kernel, and (F32)
-        for the staged kernel at the given (lanes per node, ring slots), keep the
-        fastest.  Q is not modified.  Returns the chosen configuration."""
+        lanes-per-node group with the plain and the persistent stage kernel (F32: with
+        each L2 prefetch distance), and (F32) for the staged kernel at the given (lanes
+        per node, ring slots), keep the fastest.  Q is not modified.  Returns the chosen
+        configuration."""
         info = self.info()
         block = info["block"]
-        configs = [(g, p, 0) for p in (False, True) for g in groups]
+        pfs = tuple(prefetch) if self.dtype == torch.float32 else (info["prefetch"],)
+        configs = [(g, p, 0, pf) for pf in pfs for p in (False, True) for g in groups]
         if self.dtype == torch.float32:
-            configs += [(g, False, k) for g, k in staged]
+            configs += [(g, False, k, 0) for g, k in staged]
         best = None
-        for g, persistent, stages in configs:
+        for g, persistent, stages, pf in configs:
             self.set_persistent(persistent)
             self.set_staging(stages)
+            self.set_prefetch(pf)
             self.set_launch(g, block)
             work = workspace(self)
             Qs = Q.clone()
@@ -365,15 +375,16 @@ class Plan:
             torch.cuda.synchronize()
             ms = a.elapsed_time(b) / steps
             if best is None or ms < best[0]:
-                best = (ms, g, persistent, stages)
-        _, g, persistent, stages = best
+                best = (ms, g, persistent, stages, pf)
+        _, g, persistent, stages, pf = best
         self.set_persistent(persistent)
         self.set_staging(stages)
+        self.set_prefetch(pf)
         self.set_launch(g, block)
         if self.device_status() != 0:
             raise LabfmError(7, "a staged stage kernel's bounded wait ran out while tuning")
         return {"group": g, "block": block, "persistent": persistent, "staging": stages,
-                "ms_per_step": best[0]}
+                "prefetch": pf, "ms_per_step": best[0]}
 
     def workspace_bytes(self) -> int:
         return int(lib.labfm_rk_workspace_bytes(self._h))

@@ -120,7 +120,7 @@ void prof_end(labfm_plan* p, int idx, cudaStream_t st) {
 
 extern "C" const char* labfm_last_error(void) { return g_last_error.c_str(); }
 
-extern "C" int labfm_abi_version(void) { return 2; }
+extern "C" int labfm_abi_version(void) { return 3; }
 
 extern "C" int labfm_plan_create(labfm_plan** out, int64_t N, int64_t nnz, labfm_dtype dtype,
                                  const int32_t* row_ptr, const int32_t* col, const double* w,
@@ -186,6 +186,13 @@ extern "C" int labfm_plan_set_persistent(labfm_plan* p, int enable) {
     return LABFM_OK;
 }
 
+extern "C" int labfm_plan_set_prefetch(labfm_plan* p, int distance) {
+    if (int rc = check_plan(p)) return rc;
+    if (distance < 0 || distance > 8) return set_error(LABFM_EINVAL, "prefetch distance must be in [0, 8]");
+    p->prefetch = distance;
+    return LABFM_OK;
+}
+
 extern "C" int labfm_plan_set_staging(labfm_plan* p, int stages, void* stream) {
     if (int rc = check_plan(p)) return rc;
     return configure_staging(p, stages, as_stream(stream));
@@ -226,6 +233,8 @@ extern "C" int labfm_plan_get_info(const labfm_plan* p, labfm_plan_info* info) {
     info->entry_bytes = plan_entry_bytes(p, false);
     info->filter_entry_bytes = plan_entry_bytes(p, true);
     info->device_bytes = p->device_bytes;
+    info->prefetch = p->prefetch;
+    info->stages = p->stages;
     return LABFM_OK;
 }
 

@@ -296,6 +296,7 @@ struct PlanView {
     const T* wf;  // nnz_pad
     const T* inv_s;
     const double* dt_node;  // per-node time step, or null for a uniform dt
+    int pf;                 // L2 prefetch distance of the F32 record stream, in iterations (0: off)
 };
 
 // Operator loads of one 4-entry chunk starting at entry e (a multiple of 4).
@@ -369,8 +370,9 @@ __device__ __forceinline__ void load_filt_chunk(const PlanView<T>& P, int e, int
 
 template <typename T>
 PlanView<T> view(const labfm_plan* p) {
-    return PlanView<T>{p->N, p->nnz_pad, p->row_ptr, p->col, static_cast<const T*>(p->w),
-                       static_cast<const T*>(p->wf), static_cast<const T*>(p->inv_s), p->dt_node};
+    return PlanView<T>{p->N,        p->nnz_pad,  p->row_ptr, p->col, static_cast<const T*>(p->w),
+                       static_cast<const T*>(p->wf), static_cast<const T*>(p->inv_s), p->dt_node,
+                       p->prefetch};
 }
 
 // Chunk loaders for the gathers: from the plan's record stream in global memory,
@@ -383,7 +385,13 @@ struct GlobalChunks {
 #else
     static constexpr bool kPaired = false;
 #endif
+    static constexpr bool kPrefetch = kPaired;
     const PlanView<T>& P;
+    // L2 prefetch of segment `seg` of the block holding the chunk of entry e
+    __device__ __forceinline__ void prefetch(int e, int seg) const {
+        const char* a = reinterpret_cast<const char*>(P.w) + Rec<T>::col(e >> 2) + seg * 128;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+    }
     template <int K>
     __device__ __forceinline__ void load(int e, int (&cj)[K], T (&wx)[K], T (&wy)[K], T (&wxx)[K],
                                          T (&wxy)[K], T (&wyy)[K], int off) const {
@@ -492,6 +500,15 @@ __device__ __forceinline__ void gather_derivatives_ld(const Ld& ld, const F& fld
     // kUnroll 4-entry chunks per iteration (chunks gl, gl + G, ... of this
     // pass): all their operator loads are issued before the gathers
     for (int e = e0 + 4 * gl; e < e1; e += 4 * kUnroll * G) {
+        if constexpr (Ld::kPrefetch) {
+            // lanes 0-2 of the group fetch into L2 one 128-byte segment each of the
+            // block they will read pf iterations later (within the row)
+            const int pf = ld.P.pf;
+            if (pf > 0) {
+                const int ep = e + 4 * kUnroll * G * pf;
+                if (ep < e1 && gl < 3) ld.prefetch(ep, gl);
+            }
+        }
         int cj[4 * kUnroll];
         T wx[4 * kUnroll], wy[4 * kUnroll], wxx[4 * kUnroll], wxy[4 * kUnroll], wyy[4 * kUnroll];
 #pragma unroll

@@ -72,6 +72,7 @@ struct labfm_plan {
     int64_t* inst_off = nullptr;
     double* dt_node = nullptr;   // per-node time step (labfm_plan_set_dt), or null
     bool persistent = false;     // stage kernel takes node tiles from a work queue
+    int prefetch = 0;            // L2 prefetch distance of the F32 record stream (labfm_plan_set_prefetch)
     int persist_grid = 0;
     // F32 stage kernel with the operator staged through shared memory
     // (labfm_plan_set_staging): `stages` ring slots per CTA; for 16 and 32 lanes

@@ -207,6 +207,8 @@ __device__ __forceinline__ RoundRange round_range(const int32_t* row_ptr, int64_
 // Chunk loads from a ring slot holding the blocks from byte `off` of the stream.
 struct SharedChunks {
     static constexpr bool kColAhead = false;
+    static constexpr bool kPrefetch = false;
+    __device__ __forceinline__ void prefetch(int, int) const {}
     const unsigned char* slot;
     int64_t off;
     template <int K>
@@ -967,6 +969,10 @@ int pack_plan(labfm_plan* p, const PlanInput* in, int n_inst, cudaStream_t st) {
     if (rc) return rc;
     if (nnz_pad >= (int64_t(1) << 31)) return set_error(LABFM_ECAPACITY, "padded stencil exceeds 2^31 entries");
     p->nnz_pad = nnz_pad;
+    // F32 record stream prefetched two iterations ahead when rows are long (a mean
+    // of 64 or more padded entries): measured faster for m = 8 and m = 10 stencils
+    // and slower for the short rows of m = 4 and m = 6 (labfm_plan_set_prefetch)
+    p->prefetch = (p->dtype == LABFM_F32 && nnz_pad >= 64 * N) ? 2 : 0;
     const size_t es = p->dtype == LABFM_F32 ? sizeof(float) : sizeof(double);
     const size_t np = size_t(std::max<int64_t>(nnz_pad, 4));
 #if LABFM_CHUNK_AOS

@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol(built_lib):
 
 def test_binding_loads_and_covers_the_header(built_lib):
     import paper_2102_02019_gb300 as lb
-    assert lb.lib.labfm_abi_version() == 2
+    assert lb.lib.labfm_abi_version() == 3
     assert lb.lib.labfm_last_error() == b""
     declared = set(_declared_functions())
     assert declared <= set(lb.exported_symbols()), declared - set(lb.exported_symbols())
@@ -72,6 +72,7 @@ def test_later_entry_points_validate_on_the_host(built_lib):
     # plan-level calls on a null plan
     for fn, args in (("labfm_plan_set_staging", (None, 3, None)),
                      ("labfm_plan_set_persistent", (None, 1)),
+                     ("labfm_plan_set_prefetch", (None, 2)),
                      ("labfm_rk_step_adjoint_recorded", (None, 1, 1, 1e-3, None, 1, 16, None))):
         assert getattr(L, fn)(*args) == 1, fn
     st = ctypes.c_int(0)

@@ -128,3 +128,24 @@ def test_staging_argument_checks(lb, uniform):
             p32.set_staging(bad)
     assert p32.device_status() == 0
     p32.close()
+
+
+def test_prefetch_distance_changes_nothing_but_time(lb, uniform):
+    # the L2 prefetch of the record stream only moves data earlier: every distance
+    # gives the same bits, with the plain and the persistent kernel
+    d = uniform
+    plan = lb.Plan(d["row_ptr"], d["col"], d["w"], d["kappa"], d["s"], dtype=torch.float32)
+    assert plan.info()["prefetch"] == 2  # m = 8 rows average ~100 entries
+    q0 = torch.tensor(li.tgv_fields(d["ns"].xy, C), dtype=torch.float32, device="cuda")
+    dt = float(lb.stable_dt(plan, q0, d["s"], C, MU).item())
+    plan.set_prefetch(0)
+    ref = _run(lb, plan, q0, dt, 3, 4, 0)
+    for persistent in (False, True):
+        plan.set_persistent(persistent)
+        for pf in (1, 2, 5, 8):
+            plan.set_prefetch(pf)
+            assert torch.equal(_run(lb, plan, q0, dt, 3, 4, 0), ref), (persistent, pf)
+    for bad in (-1, 9):
+        with pytest.raises(lb.LabfmError):
+            plan.set_prefetch(bad)
+    plan.close()
