@@ -369,7 +369,9 @@ def run_batch(lb, torch, args):
            "instance_steps_per_s": len(instances) * args.steps / (ms * 1e-3),
            "ms_per_step": ms_one, "tuned": tune, "build_s": build_s,
            "alg_GBps_step": (4 * (24.0 * plan.nnz + 64.0 * N) + 8.0 * plan.nnz + 36.0 * N)
-           / (ms_one * 1e-3) / 1e9}
+           / (ms_one * 1e-3) / 1e9,
+           # +-0.3 s lattices without node shifting go non-finite (see finite_state_control)
+           "state_finite_after_run": bool(torch.isfinite(Q).all().item())}
     graph.close()
     plan.close()
     return out
@@ -417,7 +419,8 @@ def run_varres(lb, torch, args):
            "weight_build_nodes_per_s": ns.N / (c.elapsed_time(d) * 1e-3),
            "failed_nodes": int((wb["status"] != 0).sum().item()),
            "fp32_node_evals_per_s": 4.0 * ns.N * args.steps / (ms * 1e-3),
-           "ms_per_step": ms / args.steps, "tuned": tune}
+           "ms_per_step": ms / args.steps, "tuned": tune,
+           "state_finite_after_run": bool(torch.isfinite(Q).all().item())}
     plan.close()
     return out
 

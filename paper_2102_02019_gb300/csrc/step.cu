@@ -331,6 +331,19 @@ __device__ __forceinline__ void filter_sums(const PlanView<T>& P, const Fin& fld
         const int e0 = P.row_ptr[i];
         const int e1 = P.row_ptr[i + 1];
         for (int e = e0 + 4 * gl; e < e1; e += 4 * kUnroll * G) {
+#if LABFM_CHUNK_AOS == 3
+            if constexpr (std::is_same<T, float>::value) {
+                // lane 0 of the group fetches into L2 the filter block it will read
+                // pf iterations later (within the row)
+                if (P.pf > 0 && gl == 0) {
+                    const int ep = e + 4 * kUnroll * G * P.pf;
+                    if (ep < e1) {
+                        const char* a = reinterpret_cast<const char*>(P.wf) + Rec<float>::fcol(ep >> 2);
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+                    }
+                }
+            }
+#endif
             int cj[4 * kUnroll];
             T wf[4 * kUnroll];
 #pragma unroll
