@@ -267,11 +267,12 @@ int labfm_stable_dt_instances(const labfm_plan* plan, const void* fields, const 
 int labfm_plan_set_persistent(labfm_plan* plan, int enable);
 
 /*
- * L2 prefetch distance of the F32 stage kernel's operator stream, in loop
- * iterations of a node's lane group (0 = off, at most 8).  When positive, three
- * lanes of each group issue an L2 prefetch of the three 128-byte segments of the
- * record block they will read `distance` iterations later, if it lies within the
- * node's row.  Results do not change.  Plan creation sets 2 for F32 plans whose
+ * L2 prefetch distance of the F32 stage and filter kernels' operator streams, in
+ * loop iterations of a node's lane group (0 = off, at most 8).  When positive,
+ * three lanes of each group issue an L2 prefetch of the three 128-byte segments
+ * of the record block they will read `distance` iterations later (in the filter,
+ * one lane the 128-byte filter block), if it lies within the node's row.
+ * Results do not change.  Plan creation sets 2 for F32 plans whose
  * rows average 64 or more padded entries and 0 otherwise (measured faster for the
  * long rows of m = 8 and 10, slower for m = 4 and 6).  Host-only call.
  */
