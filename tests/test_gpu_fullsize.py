@@ -84,15 +84,19 @@ def test_varres_rhs_sampled_fp64_and_fp32(lb, c3):
     B = rhs_bound(q, wg[:, idx], rps, cols, C * C, MU)
     for dtype in (torch.float64, torch.float32):
         plan = lb.Plan(c3["rp"], c3["col"], c3["wb"]["w"], c3["wb"]["kappa"], c3["s"], dtype=dtype)
-        plan.set_launch(8, 128)  # the shape the step tuner picks for this workload
-        R = lb.rhs(plan, _dev(q, dtype), phys).double().cpu().numpy()
-        if dtype == torch.float64:
-            for f in range(3):
-                err = np.abs(R[f][rows] - Ro[f][rows]).max() / np.abs(Ro[f][rows]).max()
-                assert err <= 1e-12, (f, err)
-        else:
-            ratio = np.abs(R[:, rows] - Ro[:, rows]) / B[:, rows]
-            assert ratio.max() <= 1.0, ratio.max()
+        # the shapes the step tuner picks for this workload: 4 lanes per node with the
+        # record prefetch (the F32 plan default here), and 8 lanes
+        for g in (4, 8):
+            plan.set_launch(g, 128)
+            R = lb.rhs(plan, _dev(q, dtype), phys).double().cpu().numpy()
+            if dtype == torch.float64:
+                for f in range(3):
+                    err = np.abs(R[f][rows] - Ro[f][rows]).max() / np.abs(Ro[f][rows]).max()
+                    assert err <= 1e-12, (f, err)
+            else:
+                assert plan.info()["prefetch"] == 2
+                ratio = np.abs(R[:, rows] - Ro[:, rows]) / B[:, rows]
+                assert ratio.max() <= 1.0, ratio.max()
         plan.close()
 
 

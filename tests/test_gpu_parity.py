@@ -338,3 +338,55 @@ def test_fullsize_rhs_fp64_sampled(lb, c2):
         err = np.abs(R[f][rows] - Ro[f][rows]).max() / np.abs(Ro[f][rows]).max()
         assert err <= 1e-12, (f, err)
     plan.close()
+
+
+def test_fullsize_fp32_in_the_bench_launch_shape(lb, c2):
+    # the headline path as bench.py times it: 4 lanes per node, 128-thread blocks, the
+    # record prefetch on (the plan default for these rows).  The sampled FP32 RHS is held
+    # to the FP32 budget against the oracle, and one full FP32 time step to the per-node
+    # budget of test_gpu_fp32 against the FP64 step (which matches the oracle to 1e-12)
+    from test_gpu_fp32 import U32, _deriv_bound, rhs_bound
+    ns, rows = c2["ns"], c2["rows"]
+    rp, col = c2["rp"].cpu().numpy(), c2["col"].cpu().numpy()
+    w, kap = c2["wb"]["w"], c2["wb"]["kappa"]
+    wg = w.cpu().numpy()
+    q = li.tgv_fields(ns.xy, 10.0)
+    phys = lb.Phys(100.0, 0.005)
+    p32 = lb.Plan(c2["rp"], c2["col"], w, kap, c2["s"], dtype=torch.float32)
+    p32.set_launch(4, 128)
+    assert p32.info()["prefetch"] == 2
+    cnt = np.zeros(ns.N, dtype=np.int64)
+    cnt[rows] = rp[rows + 1] - rp[rows]
+    rps = np.concatenate([[0], np.cumsum(cnt)])
+    idx = np.concatenate([np.arange(rp[i], rp[i + 1]) for i in rows])
+    Ro = oracle.rhs(q, wg[:5, idx], rps, col[idx], 100.0, 0.005)
+    B = rhs_bound(q, wg[:, idx], rps, col[idx], 100.0, 0.005)
+    R = lb.rhs(p32, _dev(q, torch.float32), phys).double().cpu().numpy()
+    ratio = np.abs(R[:, rows] - Ro[:, rows]) / B[:, rows]
+    assert ratio.max() <= 1.0, ratio.max()
+    # one step
+    p64 = lb.Plan(c2["rp"], c2["col"], w, kap, c2["s"], dtype=torch.float64)
+    dt = oracle.stable_dt(q, ns.s, 10.0, 0.005)
+    Q64 = _dev(q)
+    lb.rk_step(p64, Q64, dt, 1, phys)
+    Q32 = _dev(q, torch.float32)
+    lb.rk_step(p32, Q32, dt, 1, phys)
+    q1 = Q64.cpu().numpy()
+    got = Q32.double().cpu().numpy()
+    Bfull = rhs_bound(q, wg, rp, col, 100.0, 0.005)
+    bsum = sum(abs(float(b)) for b in oracle.RK_B)
+    wf = wg[5] * np.repeat(kap.cpu().numpy(), np.diff(rp))
+    ri = oracle.row_index(rp)
+    for f in range(3):
+        bf, _ = _deriv_bound(q1[f], wf, rp, col)
+        # A: the per-node budget of the state before the filter (as in test_gpu_fp32);
+        # the filter of Section 6, phi_i + kappa_i sum_j (phi_j - phi_i) w^hyp_ji,
+        # carries the errors of node i and of its neighbours with weights |kappa_i
+        # w^hyp_ji| (large at the few irregular stencils with an outsized kappa), and
+        # adds its own rounding budget bf
+        A = 8 * U32 * np.abs(q1[f]) + 2 * dt * bsum * Bfull[f]
+        carried = np.bincount(ri, np.abs(wf) * (A[col] + A[ri]), minlength=ns.N)
+        bound = A + carried + 2 * bf
+        assert np.all(np.abs(got[f] - q1[f]) <= bound), (f, (np.abs(got[f] - q1[f]) / bound).max())
+    p32.close()
+    p64.close()
