@@ -377,6 +377,12 @@ PlanView<T> view(const labfm_plan* p) {
 
 // Chunk loaders for the gathers: from the plan's record stream in global memory,
 // or from a copy of a contiguous range of its blocks in shared memory.
+// Shortest row (padded entries) whose record stream the stage and filter kernels
+// prefetch: m = 8 and 10 stencils (~100-220 entries, 6 or more iterations of a lane
+// group) gained 4-8 %, m = 6 stencils (~60 entries, 4 iterations) lost 2-3 %,
+// m = 4 (~35) neither.
+constexpr int kPrefetchMinRow = 80;
+
 template <typename T>
 struct GlobalChunks {
     static constexpr bool kColAhead = LABFM_CHUNK_AOS >= 2;
@@ -502,9 +508,10 @@ __device__ __forceinline__ void gather_derivatives_ld(const Ld& ld, const F& fld
     for (int e = e0 + 4 * gl; e < e1; e += 4 * kUnroll * G) {
         if constexpr (Ld::kPrefetch) {
             // lanes 0-2 of the group fetch into L2 one 128-byte segment each of the
-            // block they will read pf iterations later (within the row)
+            // block they will read pf iterations later (within the row; rows shorter
+            // than kPrefetchMinRow entries, where it was measured slower, skip it)
             const int pf = ld.P.pf;
-            if (pf > 0) {
+            if (pf > 0 && e1 - e0 >= kPrefetchMinRow) {
                 const int ep = e + 4 * kUnroll * G * pf;
                 if (ep < e1 && gl < 3) ld.prefetch(ep, gl);
             }

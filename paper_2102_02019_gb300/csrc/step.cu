@@ -335,7 +335,7 @@ __device__ __forceinline__ void filter_sums(const PlanView<T>& P, const Fin& fld
             if constexpr (std::is_same<T, float>::value) {
                 // lane 0 of the group fetches into L2 the filter block it will read
                 // pf iterations later (within the row)
-                if (P.pf > 0 && gl == 0) {
+                if (P.pf > 0 && gl == 0 && e1 - e0 >= kPrefetchMinRow) {
                     const int ep = e + 4 * kUnroll * G * P.pf;
                     if (ep < e1) {
                         const char* a = reinterpret_cast<const char*>(P.wf) + Rec<float>::fcol(ep >> 2);
@@ -982,10 +982,9 @@ int pack_plan(labfm_plan* p, const PlanInput* in, int n_inst, cudaStream_t st) {
     if (rc) return rc;
     if (nnz_pad >= (int64_t(1) << 31)) return set_error(LABFM_ECAPACITY, "padded stencil exceeds 2^31 entries");
     p->nnz_pad = nnz_pad;
-    // F32 record stream prefetched two iterations ahead when rows are long (a mean
-    // of 64 or more padded entries): measured faster for m = 8 and m = 10 stencils
-    // and slower for the short rows of m = 4 and m = 6 (labfm_plan_set_prefetch)
-    p->prefetch = (p->dtype == LABFM_F32 && nnz_pad >= 64 * N) ? 2 : 0;
+    // F32 record streams prefetched two iterations ahead (labfm_plan_set_prefetch);
+    // the kernels skip rows shorter than kPrefetchMinRow entries
+    p->prefetch = p->dtype == LABFM_F32 ? 2 : 0;
     const size_t es = p->dtype == LABFM_F32 ? sizeof(float) : sizeof(double);
     const size_t np = size_t(std::max<int64_t>(nnz_pad, 4));
 #if LABFM_CHUNK_AOS

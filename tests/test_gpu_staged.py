@@ -135,7 +135,7 @@ def test_prefetch_distance_changes_nothing_but_time(lb, uniform):
     # gives the same bits, with the plain and the persistent kernel
     d = uniform
     plan = lb.Plan(d["row_ptr"], d["col"], d["w"], d["kappa"], d["s"], dtype=torch.float32)
-    assert plan.info()["prefetch"] == 2  # m = 8 rows average ~100 entries
+    assert plan.info()["prefetch"] == 2  # the F32 default
     q0 = torch.tensor(li.tgv_fields(d["ns"].xy, C), dtype=torch.float32, device="cuda")
     dt = float(lb.stable_dt(plan, q0, d["s"], C, MU).item())
     plan.set_prefetch(0)
