@@ -195,20 +195,25 @@ class OracleSample:
                 "eq. icns RHS at those nodes per step")
 
 
-def _oracle_worker(nx, seed, reps, ready, start, results):
-    """One host core's share of the all-cores oracle baseline (a spawned process)."""
-    import labfm_inputs as li
-    ns = li.tgv_lattice(nx, m=8, h_over_s=2.8, jitter=0.3, seed=1)
-    sample = OracleSample(ns, seed=seed)
-    sample.step()
-    ready.put(seed)
-    start.wait()
+def _oracle_worker(nx, rows, seed, reps, ready, start, results):
+    """One host core's share of the all-cores oracle baseline (a spawned process).
+    A failure is reported through `ready` so that the parent does not wait for it."""
+    try:
+        import labfm_inputs as li
+        ns = li.tgv_lattice(nx, m=8, h_over_s=2.8, jitter=0.3, seed=1)
+        sample = OracleSample(ns, rows=min(rows, ns.N), seed=seed)
+        sample.step()
+    except Exception as e:  # noqa: BLE001 (any failure ends this baseline)
+        ready.put(f"{type(e).__name__}: {e}")
+        return
+    ready.put(None)
+    start.wait(timeout=600)
     for _ in range(reps):
         sample.step()
     results.put(sample.n * reps * 4)
 
 
-def oracle_all_cores(nx, reps, cores):
+def oracle_all_cores(nx, reps, cores, rows=SAMPLE_ROWS):
     """The oracle as it stands on every host core at once: `cores` spawned
     processes, each with its own random sample of the workload (different seeds),
     each doing `reps` steps; node-RHS evaluations of all of them over the wall time
@@ -219,13 +224,16 @@ def oracle_all_cores(nx, reps, cores):
     saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
     for k in saved:
         os.environ[k] = "1"
-    procs = [ctx.Process(target=_oracle_worker, args=(nx, 100 + k, reps, ready, start, results))
+    procs = [ctx.Process(target=_oracle_worker, args=(nx, rows, 100 + k, reps, ready, start, results))
              for k in range(cores)]
     try:
         for pr in procs:
             pr.start()
         for _ in procs:
-            ready.get(timeout=600)
+            err = ready.get(timeout=600)
+            if err is not None:
+                start.set()  # release the workers that are ready
+                raise RuntimeError(f"oracle worker failed: {err}")
         t0 = time.perf_counter()
         start.set()
         evals = sum(results.get(timeout=600) for _ in procs)
