@@ -28,13 +28,15 @@ namespace {
 
 // ---------------------------------------------------------------- kernels
 
-// The fused gather kernels (stage, right-hand side) run 128-thread blocks with
-// a register budget that keeps 8 blocks (32 warps) resident per SM: more loads
-// in flight per SM, measured faster than the unconstrained allocation.
+// The fused gather kernels (stage, right-hand side) run 128-thread blocks.  A
+// register budget for 8 resident blocks per SM (64 registers) had been faster
+// than the unconstrained allocation while the lanes' own loads were the only
+// bytes in flight; with the L2 prefetch of the record stream the natural 72
+// registers (7 blocks per SM) are faster (m = 8: 111.4 -> 106.7 us, m = 10:
+// 599 -> 572 us), so the bound asks for no more than 6.
 constexpr int kGatherBlock = 128;
-// (FP64 keeps 6 resident blocks: its accumulators need more registers.)
 #ifndef LABFM_STAGE_MINB
-#define LABFM_STAGE_MINB 8
+#define LABFM_STAGE_MINB 6
 #endif
 #define LABFM_STAGE_BOUNDS \
     __launch_bounds__(kGatherBlock, sizeof(T) == 4 ? LABFM_STAGE_MINB : 6)
