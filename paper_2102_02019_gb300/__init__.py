@@ -121,6 +121,10 @@ _SIGS = {
 }
 
 
+# the C ABI this binding's signatures and structures follow (include/labfm.h)
+ABI_VERSION = 3
+
+
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(
@@ -131,6 +135,9 @@ def _load() -> ctypes.CDLL:
         fn = getattr(lib, name)
         fn.restype = res
         fn.argtypes = args
+    if lib.labfm_abi_version() != ABI_VERSION:
+        raise ImportError(f"{LIB_PATH} has ABI {lib.labfm_abi_version()}, this binding needs "
+                          f"{ABI_VERSION}: rebuild it (`__graft_entry__.build()`)")
     return lib
 
 
