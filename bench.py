@@ -105,9 +105,19 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index=0):
+        # the samples go to $LABFM_CLOCK_LOG_DIR/clocks_rank<i>.csv when that is set
+        # (kept), else to a temporary file removed after the summary
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        log_dir = os.environ.get("LABFM_CLOCK_LOG_DIR")
+        if log_dir:
+            self.path = os.path.join(log_dir, f"clocks_rank{index}.csv")
+            self.keep = True
+        else:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix=f"labfm_clocks_rank{index}_", suffix=".csv")
+            os.close(fd)
+            self.keep = False
 
     def __enter__(self):
         try:
@@ -133,6 +143,8 @@ class ClockSampler:
 
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
+            if not self.keep and os.path.exists(self.path):
+                os.remove(self.path)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -148,6 +160,11 @@ class ClockSampler:
             for k, nm in enumerate(names):
                 if parts[5 + k].lower().startswith("active"):
                     reasons.add(nm)
+        if not self.keep:
+            try:
+                os.remove(self.path)
+            except OSError:
+                pass
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
                 "reasons": sorted(reasons), "samples": len(sm)}
 
