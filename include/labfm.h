@@ -126,6 +126,7 @@ int labfm_build_stencils(const double* xy, const double* h, int64_t N, double Lx
  *   row_ptr, col  device CSR from labfm_build_stencils (nnz entries)
  *   m         order of polynomial reproduction, even, 2 <= m <= 10
  *   w         device, 6 x nnz doubles (output), operator-major: w[d * nnz + e]
+ *             (may be NULL, like col, when nnz = 0: every stencil is empty)
  *   kappa     device, N doubles (output): filter coefficient kappa_i
  *   residual  device, N doubles (output, may be NULL): max over operators and
  *             monomials of |sum_j X~_ji w_ji h^l - C^d| (nondimensional
@@ -192,7 +193,7 @@ int labfm_stencil_optimise(const double* xy, const double* h0, const double* s, 
  *
  *   xy, s        device, N x 2 / N doubles
  *   row_ptr, col device CSR (nnz entries); w: device, 6 x nnz doubles from
- *                labfm_build_weights
+ *                labfm_build_weights (col and w may be NULL when nnz = 0)
  *   nk           wavenumbers per node, 1 <= nk <= 4096
  *   out          device, N x 3 x nk doubles (output)
  * Errors: EINVAL (null pointers, N, nk).
@@ -211,7 +212,8 @@ int labfm_modal_response(const double* xy, const double* s, int64_t N, double Lx
  * w^d_ji s_i^l (l = 1 for d/dx, d/dy; 2 for second derivatives), and the kernels
  * multiply the sums by s_i^-l.
  *
- *   w      device, 6 x nnz doubles as written by labfm_build_weights
+ *   w      device, 6 x nnz doubles as written by labfm_build_weights (col and w
+ *          may be NULL when nnz = 0; such a plan's steps leave the state unchanged)
  *   kappa  device, N doubles
  *   s      device, N doubles (node spacing)
  * The plan allocates and owns its device memory (cudaMalloc); the input

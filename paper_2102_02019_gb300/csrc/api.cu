@@ -127,7 +127,7 @@ extern "C" int labfm_plan_create(labfm_plan** out, int64_t N, int64_t nnz, labfm
                                  const double* kappa, const double* s, void* stream) {
     if (!out) return set_error(LABFM_EINVAL, "null plan output");
     *out = nullptr;
-    if (!row_ptr || !w || !kappa || !s || (nnz > 0 && !col))
+    if (!row_ptr || !kappa || !s || (nnz > 0 && (!col || !w)))
         return set_error(LABFM_EINVAL, "null pointer argument");
     if (N <= 0 || N >= (int64_t(1) << 31) - 1) return set_error(LABFM_EINVAL, "N out of range");
     if (nnz < 0 || nnz >= (int64_t(1) << 31)) return set_error(LABFM_EINVAL, "nnz out of range");
@@ -152,8 +152,8 @@ extern "C" int labfm_plan_create_batched(labfm_plan** out, int n_inst, const int
     int rc = LABFM_OK;
     for (int k = 0; k < n_inst && rc == LABFM_OK; ++k) {
         in[k] = PlanInput{N_inst[k], nnz_inst[k], row_ptr[k], col[k], w[k], kappa[k], s[k]};
-        if (N_inst[k] <= 0 || nnz_inst[k] < 0 || !row_ptr[k] || !w[k] || !kappa[k] || !s[k] ||
-            (nnz_inst[k] > 0 && !col[k]))
+        if (N_inst[k] <= 0 || nnz_inst[k] < 0 || !row_ptr[k] || !kappa[k] || !s[k] ||
+            (nnz_inst[k] > 0 && (!col[k] || !w[k])))
             rc = set_error(LABFM_EINVAL, "bad instance " + std::to_string(k));
         Ntot += N_inst[k];
         nnztot += nnz_inst[k];

@@ -915,7 +915,7 @@ extern "C" int labfm_build_weights(const double* xy, const double* h, const doub
                                    const int32_t* row_ptr, const int32_t* col, int64_t nnz, int m,
                                    double* w, double* kappa, double* residual,
                                    int32_t* node_status, int64_t* n_failed_out, void* stream) {
-    if (!xy || !h || !s || !row_ptr || !w || !kappa || !node_status)
+    if (!xy || !h || !s || !row_ptr || !kappa || !node_status || (nnz > 0 && !w))
         return set_error(LABFM_EINVAL, "null pointer argument");
     if (nnz > 0 && !col) return set_error(LABFM_EINVAL, "null col with nnz > 0");
     if (N <= 0 || N >= (int64_t(1) << 31) - 1) return set_error(LABFM_EINVAL, "N out of range");
@@ -979,7 +979,7 @@ extern "C" int labfm_modal_response(const double* xy, const double* s, int64_t N
                                     double Ly, uint32_t periodic_mask, const int32_t* row_ptr,
                                     const int32_t* col, int64_t nnz, const double* w, int nk,
                                     double* out, void* stream) {
-    if (!xy || !s || !row_ptr || !w || !out || (nnz > 0 && !col))
+    if (!xy || !s || !row_ptr || !out || (nnz > 0 && (!col || !w)))
         return set_error(LABFM_EINVAL, "null pointer argument");
     if (N <= 0 || N >= (int64_t(1) << 31) - 1) return set_error(LABFM_EINVAL, "N out of range");
     if (nk < 1 || nk > 4096) return set_error(LABFM_EINVAL, "nk out of range");

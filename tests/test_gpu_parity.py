@@ -183,6 +183,31 @@ def test_weights_flag_nodes_with_too_few_neighbours(lb):
     assert np.all(st & lb.NODE_FEW_NEIGHBOURS)
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("n_side", [1, 5])
+def test_empty_stencils_leave_the_state_unchanged(lb, dtype, n_side):
+    # degenerate node sets: a single node, or stencils too small to hold a neighbour.
+    # Every stencil is empty (nnz = 0), so every derivative and kappa are zero, the
+    # right-hand side of eq. icns is zero and a time step (stages and filter) is the
+    # identity, bit for bit, with the plain, the persistent and the prefetching kernels
+    ns = li.tgv_lattice(n_side, m=2, h_over_s=0.2, jitter=0.0, seed=4)
+    xy, h, s = _dev(ns.xy), _dev(ns.h), _dev(ns.s)
+    rp, col = lb.build_stencils(xy, h, ns.Lx, ns.Ly)
+    assert col.numel() == 0 and int(rp[-1].item()) == 0
+    wb = lb.build_weights(xy, h, s, ns.Lx, ns.Ly, rp, col, 2)
+    assert np.all(wb["status"].cpu().numpy() & lb.NODE_FEW_NEIGHBOURS)
+    plan = lb.Plan(rp, col, wb["w"], wb["kappa"], s, dtype=dtype)
+    q0 = _dev(li.tgv_fields(ns.xy, 10.0), dtype)
+    phys = lb.Phys(100.0, 0.005)
+    assert float(lb.rhs(plan, q0, phys).abs().max().item()) == 0.0
+    for persistent in (False, True):
+        plan.set_persistent(persistent)
+        Q = q0.clone()
+        lb.rk_step(plan, Q, 1e-3, 3, phys)
+        assert torch.equal(Q, q0), persistent
+    plan.close()
+
+
 # ---------------------------------------------------------------- right-hand side, FP64
 
 def _plan(lb, c, w, kappa, dtype):
