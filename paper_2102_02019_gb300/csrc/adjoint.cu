@@ -27,6 +27,7 @@
 
 #include "gather.cuh"
 #include "labfm_internal.cuh"
+#include "nvtx.cuh"
 
 #if !LABFM_CHUNK_AOS
 #error "the transposed-operator build reads the chunk-record layout"
@@ -627,6 +628,7 @@ int check_adjoint(const labfm_plan* p, void* work, size_t work_bytes) {
 using namespace labfm;
 
 extern "C" int labfm_plan_enable_adjoint(labfm_plan* p, void* stream) {
+    LABFM_NVTX("labfm_plan_enable_adjoint");
     if (!p || !p->row_ptr) return set_error(LABFM_EINVAL, "null or empty plan");
     if (p->trow_ptr) return LABFM_OK;
     cudaStream_t st = as_stream(stream);
@@ -640,6 +642,7 @@ extern "C" size_t labfm_adjoint_workspace_bytes(const labfm_plan* p) {
 extern "C" int labfm_rhs_adjoint(const labfm_plan* p, const void* fields, const void* lambda,
                                  void* grad, const labfm_phys* phys, void* work, size_t work_bytes,
                                  void* stream) {
+    LABFM_NVTX("labfm_rhs_adjoint");
     if (int rc = check_adjoint(p, work, work_bytes)) return rc;
     if (!fields || !lambda || !grad || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
     cudaStream_t st = as_stream(stream);
@@ -650,6 +653,7 @@ extern "C" int labfm_rhs_adjoint(const labfm_plan* p, const void* fields, const 
 extern "C" int labfm_rk_step_adjoint(const labfm_plan* p, const void* Q, void* lambda, double dt,
                                      const labfm_phys* phys, void* work, size_t work_bytes,
                                      void* stream) {
+    LABFM_NVTX("labfm_rk_step_adjoint");
     if (int rc = check_adjoint(p, work, work_bytes)) return rc;
     if (!Q || !lambda || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
     if (!(dt > 0.0) && !(dt == 0.0 && p->dt_node))
@@ -667,6 +671,7 @@ extern "C" size_t labfm_stage_states_bytes(const labfm_plan* p) {
 extern "C" int labfm_rk_step_record(const labfm_plan* p, void* Q, void* states, size_t states_bytes,
                                     void* work, size_t work_bytes, double dt, const labfm_phys* phys,
                                     void* stream) {
+    LABFM_NVTX("labfm_rk_step_record");
     if (!p || !p->row_ptr) return set_error(LABFM_EINVAL, "null or empty plan");
     if (!Q || !states || !work || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
     if (states_bytes < labfm_stage_states_bytes(p))
@@ -685,6 +690,7 @@ extern "C" int labfm_rk_step_record(const labfm_plan* p, void* Q, void* states, 
 extern "C" int labfm_rk_step_adjoint_recorded(const labfm_plan* p, const void* states, void* lambda,
                                               double dt, const labfm_phys* phys, void* work,
                                               size_t work_bytes, void* stream) {
+    LABFM_NVTX("labfm_rk_step_adjoint_recorded");
     if (int rc = check_adjoint(p, work, work_bytes)) return rc;
     if (!states || !lambda || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
     if (reinterpret_cast<uintptr_t>(states) % 16 != 0)
@@ -698,6 +704,7 @@ extern "C" int labfm_rk_step_adjoint_recorded(const labfm_plan* p, const void* s
 
 extern "C" int labfm_filter_adjoint(const labfm_plan* p, const void* lam_in, void* lam_out,
                                     void* work, size_t work_bytes, void* stream) {
+    LABFM_NVTX("labfm_filter_adjoint");
     if (int rc = check_adjoint(p, work, work_bytes)) return rc;
     if (!lam_in || !lam_out) return set_error(LABFM_EINVAL, "null pointer argument");
     cudaStream_t st = as_stream(stream);

@@ -7,6 +7,7 @@
 #include <string>
 
 #include "labfm_internal.cuh"
+#include "nvtx.cuh"
 
 namespace labfm {
 
@@ -125,6 +126,7 @@ extern "C" int labfm_abi_version(void) { return 3; }
 extern "C" int labfm_plan_create(labfm_plan** out, int64_t N, int64_t nnz, labfm_dtype dtype,
                                  const int32_t* row_ptr, const int32_t* col, const double* w,
                                  const double* kappa, const double* s, void* stream) {
+    LABFM_NVTX("labfm_plan_create");
     if (!out) return set_error(LABFM_EINVAL, "null plan output");
     *out = nullptr;
     if (!row_ptr || !kappa || !s || (nnz > 0 && (!col || !w)))
@@ -141,6 +143,7 @@ extern "C" int labfm_plan_create_batched(labfm_plan** out, int n_inst, const int
                                          const int32_t* const* col, const double* const* w,
                                          const double* const* kappa, const double* const* s,
                                          labfm_dtype dtype, void* stream) {
+    LABFM_NVTX("labfm_plan_create_batched");
     if (!out) return set_error(LABFM_EINVAL, "null plan output");
     *out = nullptr;
     if (n_inst <= 0) return set_error(LABFM_EINVAL, "need at least one instance");
@@ -252,6 +255,7 @@ extern "C" int labfm_plan_set_launch(labfm_plan* p, int group, int block) {
 extern "C" int labfm_plan_autotune(labfm_plan* p, const void* fields, void* scratch_rhs,
                                    const labfm_phys* phys, int reps, int* group_out, int* block_out,
                                    void* stream) {
+    LABFM_NVTX("labfm_plan_autotune");
     if (int rc = check_plan(p)) return rc;
     if (!fields || !scratch_rhs || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
     if (reps <= 0) reps = 5;
@@ -303,6 +307,7 @@ extern "C" int labfm_plan_autotune(labfm_plan* p, const void* fields, void* scra
 
 extern "C" int labfm_rhs(const labfm_plan* p, const void* fields, void* rhs,
                          const labfm_phys* phys, void* stream) {
+    LABFM_NVTX("labfm_rhs");
     if (int rc = check_plan(p)) return rc;
     if (!fields || !rhs || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
     if (fields == rhs) return set_error(LABFM_EINVAL, "rhs must not alias fields");
@@ -310,6 +315,7 @@ extern "C" int labfm_rhs(const labfm_plan* p, const void* fields, void* rhs,
 }
 
 extern "C" int labfm_filter(const labfm_plan* p, const void* in, void* out, void* stream) {
+    LABFM_NVTX("labfm_filter");
     if (int rc = check_plan(p)) return rc;
     if (!in || !out) return set_error(LABFM_EINVAL, "null pointer argument");
     if (in == out) return set_error(LABFM_EINVAL, "filter output must not alias its input");
@@ -322,6 +328,7 @@ extern "C" size_t labfm_rk_workspace_bytes(const labfm_plan* p) {
 
 extern "C" int labfm_rk_step(const labfm_plan* p, void* Q, void* work, size_t work_bytes,
                              double dt, int nsteps, const labfm_phys* phys, void* stream) {
+    LABFM_NVTX("labfm_rk_step");
     if (int rc = check_plan(p)) return rc;
     if (!Q || !work || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
     if (nsteps < 0) return set_error(LABFM_EINVAL, "negative nsteps");
@@ -336,6 +343,7 @@ extern "C" int labfm_rk_step(const labfm_plan* p, void* Q, void* work, size_t wo
 
 extern "C" int labfm_stable_dt(const labfm_plan* p, const void* fields, const double* s, double c,
                                double mu, double* dt_out, void* stream) {
+    LABFM_NVTX("labfm_stable_dt");
     if (int rc = check_plan(p)) return rc;
     if (!fields || !s || !dt_out) return set_error(LABFM_EINVAL, "null pointer argument");
     if (!(c >= 0.0) || !(mu > 0.0)) return set_error(LABFM_EINVAL, "need c >= 0 and mu > 0");
@@ -345,6 +353,7 @@ extern "C" int labfm_stable_dt(const labfm_plan* p, const void* fields, const do
 extern "C" int labfm_rk_step_host(const labfm_plan* p, void* Q_host, void* Q_dev, void* work,
                                   size_t work_bytes, double dt, int nsteps,
                                   const labfm_phys* phys, void* stream) {
+    LABFM_NVTX("labfm_rk_step_host");
     if (int rc = check_plan(p)) return rc;
     if (!Q_host || !Q_dev) return set_error(LABFM_EINVAL, "null pointer argument");
     const size_t bytes = size_t(3) * size_t(p->N) * (p->dtype == LABFM_F32 ? sizeof(float) : sizeof(double));

@@ -7,6 +7,7 @@
 #include <new>
 
 #include "labfm_internal.cuh"
+#include "nvtx.cuh"
 
 struct labfm_step_graph {
     const labfm_plan* plan = nullptr;
@@ -27,6 +28,7 @@ void destroy_graph(labfm_step_graph* g) {
 
 extern "C" int labfm_step_graph_create(labfm_step_graph** out, const labfm_plan* plan, void* work,
                                        size_t work_bytes, double dt, const labfm_phys* phys) {
+    LABFM_NVTX("labfm_step_graph_create");
     if (!out) return set_error(LABFM_EINVAL, "null graph output");
     *out = nullptr;
     if (!plan || !plan->row_ptr || !work || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
@@ -69,6 +71,7 @@ extern "C" int labfm_step_graph_create(labfm_step_graph** out, const labfm_plan*
 }
 
 extern "C" int labfm_step_graph_run(labfm_step_graph* g, void* Q, int nsteps, void* stream) {
+    LABFM_NVTX("labfm_step_graph_run");
     if (!g || !g->exec) return set_error(LABFM_EINVAL, "null graph");
     if (!Q) return set_error(LABFM_EINVAL, "null state");
     if (nsteps < 0) return set_error(LABFM_EINVAL, "negative nsteps");

@@ -8,6 +8,7 @@
 #include <string>
 
 #include "labfm_internal.cuh"
+#include "nvtx.cuh"
 
 namespace {
 
@@ -43,6 +44,7 @@ int static_work_address(void** out) {
 
 extern "C" int labfm_rk_step_noalloc(const labfm_plan* p, void* Q, double dt, int nsteps,
                                      const labfm_phys* phys, void* stream) {
+    LABFM_NVTX("labfm_rk_step_noalloc");
     if (!p || !p->row_ptr) return labfm::set_error(LABFM_EINVAL, "null or empty plan");
     if (!Q || !phys) return labfm::set_error(LABFM_EINVAL, "null pointer argument");
     if (nsteps < 0) return labfm::set_error(LABFM_EINVAL, "negative nsteps");

@@ -9,6 +9,7 @@
 #include <string>
 
 #include "labfm_internal.cuh"
+#include "nvtx.cuh"
 
 namespace labfm {
 
@@ -303,6 +304,7 @@ extern "C" int labfm_build_stencils(const double* xy, const double* h, int64_t N
                                     double Ly, uint32_t periodic_mask, int32_t* row_ptr,
                                     int32_t* col, int64_t col_capacity, int64_t* nnz_out,
                                     void* stream) {
+    LABFM_NVTX("labfm_build_stencils");
     if (!xy || !h || !row_ptr || !nnz_out) return set_error(LABFM_EINVAL, "null pointer argument");
     if (N <= 0 || N >= (int64_t(1) << 31) - 1) return set_error(LABFM_EINVAL, "N out of range");
     if (!(Lx > 0.0) || !(Ly > 0.0) || !isfinite(Lx) || !isfinite(Ly))

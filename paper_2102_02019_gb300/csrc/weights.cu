@@ -20,6 +20,7 @@
 #include <string>
 
 #include "labfm_internal.cuh"
+#include "nvtx.cuh"
 
 namespace labfm {
 namespace {
@@ -915,6 +916,7 @@ extern "C" int labfm_build_weights(const double* xy, const double* h, const doub
                                    const int32_t* row_ptr, const int32_t* col, int64_t nnz, int m,
                                    double* w, double* kappa, double* residual,
                                    int32_t* node_status, int64_t* n_failed_out, void* stream) {
+    LABFM_NVTX("labfm_build_weights");
     if (!xy || !h || !s || !row_ptr || !kappa || !node_status || (nnz > 0 && !w))
         return set_error(LABFM_EINVAL, "null pointer argument");
     if (nnz > 0 && !col) return set_error(LABFM_EINVAL, "null col with nnz > 0");
@@ -958,6 +960,7 @@ extern "C" int labfm_stencil_optimise(const double* xy, const double* h0, const 
                                       const int32_t* row_ptr, const int32_t* col, int m,
                                       double factor, double amp_max, double resid_coef, int max_iter,
                                       double* h_out, int32_t* solves_out, void* stream) {
+    LABFM_NVTX("labfm_stencil_optimise");
     if (!xy || !h0 || !s || !row_ptr || !col || !h_out)
         return set_error(LABFM_EINVAL, "null pointer argument");
     if (N <= 0 || N >= (int64_t(1) << 31) - 1) return set_error(LABFM_EINVAL, "N out of range");
@@ -979,6 +982,7 @@ extern "C" int labfm_modal_response(const double* xy, const double* s, int64_t N
                                     double Ly, uint32_t periodic_mask, const int32_t* row_ptr,
                                     const int32_t* col, int64_t nnz, const double* w, int nk,
                                     double* out, void* stream) {
+    LABFM_NVTX("labfm_modal_response");
     if (!xy || !s || !row_ptr || !out || (nnz > 0 && (!col || !w)))
         return set_error(LABFM_EINVAL, "null pointer argument");
     if (N <= 0 || N >= (int64_t(1) << 31) - 1) return set_error(LABFM_EINVAL, "N out of range");
