@@ -1,0 +1,132 @@
+"""Pins of the boundary operators of the oracle (Section 7.1 and Appendix A): the
+five-point differences against the classical coefficient tables (Fornberg, Math.
+Comp. 51 (1988)) and against exact differentiation of polynomials; one-dimensional
+LABFM by exact reproduction of eta^k, k <= m, by its reduction to the central
+differences on a uniform unisolvent row (independent of the RBF), by invariance to
+the scale of psi, and by its convergence order; the rotation of Section 7.1 on
+linear fields."""
+from fractions import Fraction as F
+from math import factorial
+
+import numpy as np
+import pytest
+
+from oracle import boundary_oracle as bo
+from oracle.labfm_oracle import wendland_c2
+
+# classical five-point coefficients (units of s^-d), point offsets in increasing order
+TABLES = {
+    (bo.FD_CENTRAL, 1): [F(1, 12), F(-2, 3), F(0), F(2, 3), F(-1, 12)],
+    (bo.FD_CENTRAL, 2): [F(-1, 12), F(4, 3), F(-5, 2), F(4, 3), F(-1, 12)],
+    (bo.FD_ONE_SIDED, 1): [F(-25, 12), F(4), F(-3), F(4, 3), F(-1, 4)],
+    (bo.FD_ONE_SIDED, 2): [F(35, 12), F(-26, 3), F(19, 2), F(-14, 3), F(11, 12)],
+    (bo.FD_ASYMMETRIC, 1): [F(-1, 4), F(-5, 6), F(3, 2), F(-1, 2), F(1, 12)],
+    (bo.FD_ASYMMETRIC, 2): [F(11, 12), F(-5, 3), F(1, 2), F(1, 3), F(-1, 12)],
+}
+
+
+@pytest.mark.parametrize("key", list(TABLES))
+def test_five_point_differences_match_the_classical_tables(key):
+    offsets, d = key
+    assert bo.fd_weights(offsets, d) == TABLES[key]
+
+
+@pytest.mark.parametrize("offsets", [bo.FD_ONE_SIDED, bo.FD_ASYMMETRIC, bo.FD_CENTRAL])
+@pytest.mark.parametrize("d", [1, 2])
+def test_five_point_differences_are_exact_on_quartics(offsets, d):
+    # random quartic polynomials in exact rationals, differentiated at 0 with spacing s
+    rng = np.random.default_rng(d + len(offsets))
+    w = bo.fd_weights(offsets, d)
+    for s in (F(1, 7), F(3, 2)):
+        for _ in range(5):
+            c = [F(int(v), 5) for v in rng.integers(-20, 20, size=5)]
+            p = lambda x: sum(ck * x ** k for k, ck in enumerate(c))  # noqa: E731
+            approx = sum(wq * p(q * s) for wq, q in zip(w, offsets)) / s ** d
+            exact = factorial(d) * c[d]
+            assert approx == exact
+    # and not on every higher power: the first error term is q^5 (q^6 for the
+    # symmetric central second difference, whose q^5 term cancels)
+    x5, x6 = (sum(wq * F(q) ** k for wq, q in zip(w, offsets)) for k in (5, 6))
+    assert x5 != 0 or x6 != 0
+    if offsets == bo.FD_CENTRAL and d == 2:
+        assert x5 == 0 and x6 != 0
+
+
+def _row(n_side, s, jitter, seed):
+    rng = np.random.default_rng(seed)
+    q = np.arange(-n_side, n_side + 1, dtype=np.float64)
+    eta = (q + rng.uniform(-jitter, jitter, size=q.size)) * s
+    eta -= eta[n_side]  # node i at the origin
+    return np.delete(eta, n_side)
+
+
+@pytest.mark.parametrize("m", [2, 4, 6])
+def test_1d_labfm_reproduces_monomials_up_to_order_m(m):
+    s = 0.01
+    h = 1.3 * (m / 2 + 1) * s / 2  # support 2h spans ~m/2 + 1 nodes on each side
+    eta = _row(m, s, 0.2, seed=m)
+    eta = eta[np.abs(eta) <= 2 * h]
+    we, wee, ok = bo.labfm_1d_weights(eta, h, m)
+    assert ok and eta.size >= m
+    for k in range(1, m + 1):
+        phi = eta ** k / factorial(k)  # phi_i = 0 at the node
+        scale = np.sum(np.abs(phi * we)) + 1.0
+        assert abs(bo.apply_1d(0.0, phi, we) - (1.0 if k == 1 else 0.0)) <= 1e-9 * scale
+        scale2 = np.sum(np.abs(phi * wee)) + 1.0
+        assert abs(bo.apply_1d(0.0, phi, wee) - (1.0 if k == 2 else 0.0)) <= 1e-9 * scale2
+
+
+@pytest.mark.parametrize("rbf", [wendland_c2, lambda q: np.where(q <= 2.0, 1.0, 0.0)],
+                         ids=["wendland", "constant"])
+def test_1d_labfm_on_a_uniform_unisolvent_row_is_the_central_difference(rbf):
+    # m = 4 with the four nodes at -2s, -s, s, 2s: as many nodes as unknowns, so the
+    # weights do not depend on the basis and equal the five-point central formulas
+    s, h = 0.02, 0.021
+    eta = np.array([-2.0, -1.0, 1.0, 2.0]) * s
+    we, wee, ok = bo.labfm_1d_weights(eta, h, 4, rbf)
+    assert ok
+    c1 = [float(v) for v in TABLES[(bo.FD_CENTRAL, 1)]]
+    c2 = [float(v) for v in TABLES[(bo.FD_CENTRAL, 2)]]
+    np.testing.assert_allclose(we, np.array([c1[0], c1[1], c1[3], c1[4]]) / s, rtol=1e-9)
+    np.testing.assert_allclose(wee, np.array([c2[0], c2[1], c2[3], c2[4]]) / s ** 2, rtol=1e-9)
+    # the difference form puts -sum_j w_j on the node itself: the central -5/2
+    assert abs(-np.sum(wee) * s ** 2 - float(c2[2])) < 1e-9
+
+
+def test_1d_labfm_weights_do_not_depend_on_the_scale_of_psi():
+    eta = _row(4, 0.01, 0.25, seed=5)
+    h = 0.022
+    eta = eta[np.abs(eta) <= 2 * h]
+    a = bo.labfm_1d_weights(eta, h, 4)
+    b = bo.labfm_1d_weights(eta, h, 4, lambda q: 7.5 * wendland_c2(q))
+    np.testing.assert_allclose(a[0], b[0], rtol=1e-10)
+    np.testing.assert_allclose(a[1], b[1], rtol=1e-10)
+
+
+@pytest.mark.parametrize("m", [2, 4])
+def test_1d_labfm_converges_at_order_m(m):
+    # derivative of sin(2 pi eta) at a node of a jittered row, spacing halved
+    errs = []
+    for s in (0.02, 0.01, 0.005):
+        h = (m / 2 + 1.2) * s / 2
+        eta = _row(m + 2, s, 0.2, seed=11)
+        eta = eta[np.abs(eta) <= 2 * h]
+        x0 = 0.137
+        we, _, ok = bo.labfm_1d_weights(eta, h, m)
+        assert ok
+        approx = bo.apply_1d(np.sin(2 * np.pi * x0), np.sin(2 * np.pi * (x0 + eta)), we)
+        errs.append(abs(approx - 2 * np.pi * np.cos(2 * np.pi * x0)))
+    slopes = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(slopes > m - 0.6), slopes
+
+
+def test_rotation_from_boundary_coordinates():
+    # phi = a x + b y: d/dxi = grad . n, d/deta = grad . t with t = (-n_y, n_x)
+    rng = np.random.default_rng(2)
+    for _ in range(10):
+        th = rng.uniform(0, 2 * np.pi)
+        n = np.array([np.cos(th), np.sin(th)])
+        t = np.array([-n[1], n[0]])
+        g = rng.standard_normal(2)
+        dx, dy = bo.boundary_to_xy(n, g @ n, g @ t)
+        assert abs(dx - g[0]) < 1e-14 and abs(dy - g[1]) < 1e-14
