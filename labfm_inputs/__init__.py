@@ -18,6 +18,8 @@ Workloads (all doubly periodic, unit square unless stated):
   mixed orders m in {4, 6, 8}.
 * ``tgv_fields(xy, c)``: the Taylor-Green initial condition of Section 8.1 in the
   evolved variables (ln rho, u, v), with rho = 1 + p / c^2.
+* ``channel(nx, ny, ...)``: a channel periodic in x between two walls, with the five
+  uniform node rows along each wall that the boundary scheme of Section 7.1 needs.
 * ``smooth_perturbation(xy, ...)``: a seeded band-limited random field
   (integer wavevectors with |k| <= kmax), normalised to unit maximum amplitude.
 """
@@ -140,6 +142,49 @@ def batch_instances(count: int = 256, n_min: int = 2048, n_max: int = 65536,
         m = int(ms[k])
         out.append(tgv_lattice(nx, nx, m=m, seed=1000 + 7 * k + seed))
     return out
+
+
+def channel(nx: int, ny: int, m: int = 4, h_over_s: float | None = None, jitter: float = 0.3,
+            seed: int = 0) -> NodeSet:
+    """A channel periodic in x on [0, nx s) with walls at y = 0 and y = ny s (s = 1/nx):
+    the node layout of Section 7.1 near walls.  Along each wall five uniform rows
+    (row index q = 0 on the wall, q = 1..4 at q s along the inward normal) share
+    their x positions ((ix + 0.5) s), so every wall node has its four normal
+    neighbours; the rows in between are jittered lattice rows at y = iy s,
+    iy = 5 .. ny - 5 (ny >= 10).  meta: ``row`` (q, or 5 in the interior),
+    ``normal`` (inward unit normal of the nearest wall, zero in the interior),
+    ``column`` (the node's x index in the uniform rows, -1 in the interior) and
+    ``wall`` (0 bottom, 1 top, -1 interior)."""
+    if ny < 10:
+        raise ValueError("need ny >= 10: five uniform rows at each wall and a jittered interior")
+    s = 1.0 / nx
+    H = ny * s
+    rng = rng_for(20, seed)
+    xs, ys, row, nrm, colx, wall = [], [], [], [], [], []
+    for w, (y0, sign) in enumerate(((0.0, 1.0), (H, -1.0))):
+        for q in range(5):
+            for ix in range(nx):
+                xs.append((ix + 0.5) * s)
+                ys.append(y0 + sign * q * s)
+                row.append(q)
+                nrm.append((0.0, sign))
+                colx.append(ix)
+                wall.append(w)
+    for iy in range(5, ny - 4):
+        for ix in range(nx):
+            dx, dy = rng.uniform(-jitter, jitter, size=2)
+            xs.append(((ix + 0.5 + dx) * s) % 1.0)
+            ys.append((iy + dy) * s)
+            row.append(5)
+            nrm.append((0.0, 0.0))
+            colx.append(-1)
+            wall.append(-1)
+    xy = np.stack([np.array(xs), np.array(ys)], axis=1)
+    hs = H_OVER_S[m] if h_over_s is None else h_over_s
+    N = xy.shape[0]
+    return NodeSet(xy=xy, s=np.full(N, s), h=np.full(N, hs * s), Lx=1.0, Ly=H, m=m,
+                   meta={"row": np.array(row), "normal": np.array(nrm), "column": np.array(colx),
+                         "wall": np.array(wall), "nx": nx, "ny": ny, "h_over_s": hs})
 
 
 def tgv_fields(xy: np.ndarray, c: float = 10.0, H: float = 1.0) -> np.ndarray:

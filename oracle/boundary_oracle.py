@@ -92,3 +92,75 @@ def boundary_to_xy(n: np.ndarray, d_xi: np.ndarray, d_eta: np.ndarray):
     eta along the tangent t = (-n_y, n_x) (the rotation of Section 7.1)."""
     nx, ny = float(n[0]), float(n[1])
     return nx * d_xi - ny * d_eta, ny * d_xi + nx * d_eta
+
+
+# --------------------------------------------------------------------------
+# Section 7.1: first derivatives on the uniform rows along a wall
+# --------------------------------------------------------------------------
+
+_NORMAL_FD = {0: FD_ONE_SIDED, 1: FD_ASYMMETRIC, 2: FD_CENTRAL}
+
+
+def strip_first_derivative_rows(ns, i: int, m1d: int = 4, h1d_over_s: float = 1.7, rbf=wendland_c2):
+    """d/dx and d/dy at a node of the first three rows along a wall (row q = 0, 1, 2
+    of ``labfm_inputs.channel``), as weights over nodes: the boundary-normal
+    derivative by the five-point difference over the node's column (one-sided on
+    the wall, asymmetric at q = 1, central at q = 2), the tangential one by
+    one-dimensional LABFM of order m1d over the node's row (support 2 h, h =
+    h1d_over_s s), both rotated to (x, y) (Table "Schemes for derivatives near
+    boundaries").  Returns (nodes, w_x, w_y) with sum_j w_j phi_j the derivative
+    (the node itself included)."""
+    meta = ns.meta
+    q = int(meta["row"][i])
+    if q not in _NORMAL_FD:
+        raise ValueError("strip rows 0, 1 and 2 only")
+    wall, ix = meta["wall"][i], meta["column"][i]
+    n = meta["normal"][i]
+    s = float(ns.s[i])
+    # the column: rows 0..4 of the same wall and x index, in order of distance
+    col = np.array([int(np.flatnonzero((meta["wall"] == wall) & (meta["column"] == ix) &
+                                       (meta["row"] == r))[0]) for r in range(5)])
+    w_xi = np.array([float(v) for v in fd_weights(_NORMAL_FD[q], 1)]) / s
+    # the row: same wall and row index, within 2h along the (periodic) tangent
+    t = np.array([-n[1], n[0]])
+    same = np.flatnonzero((meta["wall"] == wall) & (meta["row"] == q))
+    same = same[same != i]
+    d = ns.xy[same] - ns.xy[i]
+    d[:, 0] -= ns.Lx * np.round(d[:, 0] / ns.Lx)  # minimum image in x
+    eta = d @ t
+    h = h1d_over_s * s
+    keep = np.abs(eta) <= 2 * h
+    row_nodes, eta = same[keep], eta[keep]
+    w_eta, _, ok = labfm_1d_weights(eta, h, m1d, rbf)
+    if not ok:
+        raise ValueError("singular one-dimensional system")
+    nodes = np.concatenate([col, row_nodes, [i]])
+    d_xi = np.concatenate([w_xi, np.zeros(row_nodes.size + 1)])
+    d_eta = np.concatenate([np.zeros(5), w_eta, [-np.sum(w_eta)]])  # difference form
+    wx, wy = boundary_to_xy(n, d_xi, d_eta)
+    return nodes, wx, wy
+
+
+# --------------------------------------------------------------------------
+# Section 7.1: the no-slip wall in the characteristic (LODI) form
+# --------------------------------------------------------------------------
+
+def wave_amplitudes(rho, c, u_xi, dp_dxi, du_xi_dxi, du_eta_dxi):
+    """L1, L3 and L4 of eq. Ldef (L2 = 0 for isothermal flow)."""
+    L1 = 0.5 * (u_xi - c) * (dp_dxi - rho * c * du_xi_dxi)
+    L3 = u_xi * du_eta_dxi
+    L4 = 0.5 * (u_xi + c) * (dp_dxi + rho * c * du_xi_dxi)
+    return L1, L3, L4
+
+
+def wall_rhs(rho, c, dp_dxi, du_xi_dxi, du_eta_deta, g_n, visc_xi=0.0, wall_factor=1.0):
+    """d ln rho/dt (eq. lodilnro) and d u_xi/dt (eq. lodiu) at a no-slip wall node,
+    u = 0, with L1 from eq. Ldef and the incoming wave set to L4 = L1 + f rho c g.n.
+    The paper prints f = 2; with eq. lodiu only f = 1 holds u_xi at zero (its
+    time derivative is -(L4 - L1)/(rho c) + visc_xi + g.n), which is the reading
+    taken (wall_factor selects it).  visc_xi: the viscous term of eq. lodiu."""
+    L1, _, _ = wave_amplitudes(rho, c, 0.0, dp_dxi, du_xi_dxi, 0.0)
+    L4 = L1 + wall_factor * rho * c * g_n
+    dlnrho = -(L4 + L1) / (rho * c * c) - du_eta_deta
+    du_xi = -(L4 - L1) / (rho * c) + visc_xi + g_n
+    return dlnrho, du_xi

@@ -130,3 +130,64 @@ def test_rotation_from_boundary_coordinates():
         g = rng.standard_normal(2)
         dx, dy = bo.boundary_to_xy(n, g @ n, g @ t)
         assert abs(dx - g[0]) < 1e-14 and abs(dy - g[1]) < 1e-14
+
+
+def _poly(c, x, y):
+    # sum over i + j <= 4 of c[i, j] x^i y^j, and its x and y derivatives
+    v = dx = dy = 0.0
+    for i in range(5):
+        for j in range(5 - i):
+            v = v + c[i, j] * x ** i * y ** j
+            if i:
+                dx = dx + i * c[i, j] * x ** (i - 1) * y ** j
+            if j:
+                dy = dy + j * c[i, j] * x ** i * y ** (j - 1)
+    return v, dx, dy
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_strip_first_derivatives_are_exact_on_quartics(q):
+    # Section 7.1: five-point differences along the normal and 4th-order 1D LABFM
+    # along the wall differentiate every polynomial of total degree <= 4 exactly,
+    # on both walls (normals +y and -y)
+    import labfm_inputs as li
+    ns = li.channel(32, 14)
+    rng = np.random.default_rng(q)
+    c = rng.standard_normal((5, 5))
+    meta = ns.meta
+    nodes_q = np.flatnonzero((meta["row"] == q) & (np.abs(ns.xy[:, 0] - 0.5) < 0.2))
+    assert nodes_q.size > 0 and set(meta["wall"][nodes_q]) == {0, 1}
+    for i in nodes_q:
+        nodes, wx, wy = bo.strip_first_derivative_rows(ns, int(i))
+        # the polynomial about node i (unwrapped positions; no node crosses x = 0 or 1 here)
+        d = ns.xy[nodes] - ns.xy[i]
+        phi, _, _ = _poly(c, d[:, 0], d[:, 1])
+        _, gx, gy = _poly(c, 0.0, 0.0)
+        scale = np.sum(np.abs(wx * phi)) + np.sum(np.abs(wy * phi)) + 1.0
+        assert abs(np.sum(wx * phi) - gx) <= 1e-11 * scale
+        assert abs(np.sum(wy * phi) - gy) <= 1e-11 * scale
+
+
+def test_wall_keeps_a_hydrostatic_column_at_rest_with_the_consistent_wave():
+    # a resting isothermal column under wall-normal gravity: dp/dxi = rho g.n.  With
+    # L4 = L1 + rho c g.n the wall node's ln rho and u_xi stay put; with the printed
+    # factor 2 ln rho drifts at -g.n / c
+    c, rho = 10.0, 1.3
+    for g_n in (-9.81, 0.7):
+        dp = rho * g_n
+        dl1, du1 = bo.wall_rhs(rho, c, dp, 0.0, 0.0, g_n, wall_factor=1.0)
+        assert abs(dl1) < 1e-15 and abs(du1) < 1e-15
+        dl2, _ = bo.wall_rhs(rho, c, dp, 0.0, 0.0, g_n, wall_factor=2.0)
+        assert abs(dl2 + g_n / c) < 1e-14
+
+
+def test_wall_without_gravity_reflects_acoustic_waves():
+    # g = 0: L4 = L1, the incoming wave mirrors the outgoing one (perfect reflection),
+    # and ln rho follows the compression -2 L1 / (rho c^2)
+    c, rho = 10.0, 1.0
+    dp, du = 0.3, -0.02
+    L1, _, L4 = bo.wave_amplitudes(rho, c, 0.0, dp, du, 0.0)
+    dl, dux = bo.wall_rhs(rho, c, dp, du, 0.0, 0.0)
+    assert abs(dl - (-2 * L1 / (rho * c * c))) < 1e-15 and dux == 0.0
+    # the outgoing amplitude at rest: L1 = -(c/2)(dp/dxi - rho c du/dxi)
+    assert abs(L1 + 0.5 * c * (dp - rho * c * du)) < 1e-15
