@@ -145,7 +145,7 @@ def batch_instances(count: int = 256, n_min: int = 2048, n_max: int = 65536,
 
 
 def channel(nx: int, ny: int, m: int = 4, h_over_s: float | None = None, jitter: float = 0.3,
-            seed: int = 0) -> NodeSet:
+            seed: int = 0, h_wall_over_s: float = 2.2) -> NodeSet:
     """A channel periodic in x on [0, nx s) with walls at y = 0 and y = ny s (s = 1/nx):
     the node layout of Section 7.1 near walls.  Along each wall five uniform rows
     (row index q = 0 on the wall, q = 1..4 at q s along the inward normal) share
@@ -154,7 +154,10 @@ def channel(nx: int, ny: int, m: int = 4, h_over_s: float | None = None, jitter:
     iy = 5 .. ny - 5 (ny >= 10).  meta: ``row`` (q, or 5 in the interior),
     ``normal`` (inward unit normal of the nearest wall, zero in the interior),
     ``column`` (the node's x index in the uniform rows, -1 in the interior) and
-    ``wall`` (0 bottom, 1 top, -1 interior)."""
+    ``wall`` (0 bottom, 1 top, -1 interior).  The rows q = 1, 2, whose second
+    derivatives come from one-sided order-4 stencils, get h = h_wall_over_s s (the
+    paper gives no value; 2.2 s, its "safe" m = 6 scale, keeps those systems
+    conditioned), every other node h = h_over_s s."""
     if ny < 10:
         raise ValueError("need ny >= 10: five uniform rows at each wall and a jittered interior")
     s = 1.0 / nx
@@ -182,7 +185,9 @@ def channel(nx: int, ny: int, m: int = 4, h_over_s: float | None = None, jitter:
     xy = np.stack([np.array(xs), np.array(ys)], axis=1)
     hs = H_OVER_S[m] if h_over_s is None else h_over_s
     N = xy.shape[0]
-    return NodeSet(xy=xy, s=np.full(N, s), h=np.full(N, hs * s), Lx=1.0, Ly=H, m=m,
+    rows = np.array(row)
+    hv = np.where((rows == 1) | (rows == 2), h_wall_over_s * s, hs * s)
+    return NodeSet(xy=xy, s=np.full(N, s), h=hv, Lx=1.0, Ly=H, m=m,
                    meta={"row": np.array(row), "normal": np.array(nrm), "column": np.array(colx),
                          "wall": np.array(wall), "nx": nx, "ny": ny, "h_over_s": hs})
 

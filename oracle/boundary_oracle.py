@@ -164,3 +164,101 @@ def wall_rhs(rho, c, dp_dxi, du_xi_dxi, du_eta_deta, g_n, visc_xi=0.0, wall_fact
     dlnrho = -(L4 + L1) / (rho * c * c) - du_eta_deta
     du_xi = -(L4 - L1) / (rho * c) + visc_xi + g_n
     return dlnrho, du_xi
+
+
+# --------------------------------------------------------------------------
+# Section 7.1: the channel (walls at y = 0 and H, periodic in x), all operators
+# --------------------------------------------------------------------------
+
+def channel_operator(ns, m: int = 4, m_wall: int = 4, h1d_over_s: float = 1.7):
+    """Difference-form operators (row_ptr, col, w (6, nnz), kappa) for the node set of
+    ``labfm_inputs.channel``, following the Table "Schemes for derivatives near
+    boundaries":
+
+    * interior and wall rows q = 3, 4: LABFM of order m (Sections 2, 3, 6) on the
+      stencils |r_ji| <= 2 h_i inside the channel (periodic in x only);
+    * rows q = 1, 2: d/dx, d/dy from ``strip_first_derivative_rows``; the second
+      derivatives and the filter from LABFM of order m_wall on the same stencils;
+    * wall nodes q = 0: d/dx, d/dy from ``strip_first_derivative_rows`` only (the
+      velocity is held at zero there, the density follows eq. lodilnro), and
+      kappa = 0: the wall node is not filtered (a reading: the paper lists
+      "FD + 1D-LABFM" for its hyperviscous operator without the form of the mixed
+      terms).
+    """
+    from . import labfm_oracle as core
+    rp, col = core.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly, periodic=(True, False))
+    per = (True, False)
+    bw = core.build_weights(ns.xy, ns.h, ns.s, rp, col, m, ns.Lx, ns.Ly, periodic=per)
+    bw4 = bw if m_wall == m else core.build_weights(ns.xy, ns.h, ns.s, rp, col, m_wall, ns.Lx, ns.Ly,
+                                                    periodic=per)
+    row = ns.meta["row"]
+    N = ns.N
+    entries, kappa = [], np.zeros(N)
+    for i in range(N):
+        a, b = rp[i], rp[i + 1]
+        acc = {}
+        if row[i] >= 3:
+            if not bw["ok"][i]:
+                raise ValueError(f"singular LABFM system at node {i}")
+            for e in range(a, b):
+                acc[int(col[e])] = bw["w"][:, e].copy()
+            kappa[i] = bw["kappa"][i]
+        else:
+            if row[i] > 0:
+                if not bw4["ok"][i]:
+                    raise ValueError(f"singular LABFM system at node {i}")
+                for e in range(a, b):
+                    v = np.zeros(6)
+                    v[2:] = bw4["w"][2:, e]
+                    acc[int(col[e])] = v
+                kappa[i] = bw4["kappa"][i]
+            nodes, wx, wy = strip_first_derivative_rows(ns, i, 4, h1d_over_s)
+            for j, ax, ay in zip(nodes, wx, wy):
+                if j == i:
+                    continue  # difference form: the node's own weight is -sum of the others
+                v = acc.setdefault(int(j), np.zeros(6))
+                v[0] += ax
+                v[1] += ay
+        entries.append(sorted(acc.items()))
+    row_ptr = np.zeros(N + 1, dtype=np.int64)
+    row_ptr[1:] = np.cumsum([len(e) for e in entries])
+    cols = np.array([j for e in entries for j, _ in e], dtype=np.int64)
+    w = np.array([v for e in entries for _, v in e]).T.reshape(6, -1)
+    return row_ptr, cols, w, kappa
+
+
+def channel_rhs(q, op, ns, c: float, mu: float, g=(0.0, 0.0)):
+    """d/dt of (ln rho, u, v) in the channel: eq. icns at every node but the wall,
+    where u = 0 is held (zero right-hand side for u, v) and ln rho follows
+    eq. lodilnro through ``wall_rhs`` (wall-normal derivatives from the one-sided
+    differences, the tangential one from 1D LABFM)."""
+    from . import labfm_oracle as core
+    row_ptr, col, w, _ = op
+    R = core.rhs(q, w, row_ptr, col, c * c, mu, g)
+    d = core.derivatives(q, w, row_ptr, col)
+    wall = np.flatnonzero(ns.meta["row"] == 0)
+    n = ns.meta["normal"][wall]
+    t = np.stack([-n[:, 1], n[:, 0]], axis=1)
+    a = q[0][wall]
+    rho = np.exp(a)
+    grad = lambda f: np.stack([d[f + "x"][wall], d[f + "y"][wall]], axis=1)  # noqa: E731
+    ga, gu, gv = np.stack([d["ax"][wall], d["ay"][wall]], axis=1), grad("u"), grad("v")
+    dn = lambda gr, vec: np.sum(gr * vec, axis=1)  # noqa: E731
+    dlnrho_dxi = dn(ga, n)
+    du_xi_dxi = n[:, 0] * dn(gu, n) + n[:, 1] * dn(gv, n)
+    du_eta_deta = t[:, 0] * dn(gu, t) + t[:, 1] * dn(gv, t)
+    g_n = n @ np.asarray(g, dtype=np.float64)
+    Ra, _ = wall_rhs(rho, c, c * c * rho * dlnrho_dxi, du_xi_dxi, du_eta_deta, g_n)
+    R[0][wall] = Ra
+    R[1][wall] = 0.0
+    R[2][wall] = 0.0
+    return R
+
+
+def channel_time_step(q, dt: float, op, ns, c: float, mu: float, g=(0.0, 0.0)):
+    """One step in the channel: the four RK stages with ``channel_rhs``, then the
+    filter (Section 6) with the operator's kappa (zero on the walls)."""
+    from . import labfm_oracle as core
+    row_ptr, col, w, kappa = op
+    Q = core.rk_step(q, dt, lambda x: channel_rhs(x, op, ns, c, mu, g))
+    return core.filter_fields(Q, w[5], kappa, row_ptr, col)

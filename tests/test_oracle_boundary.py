@@ -191,3 +191,47 @@ def test_wall_without_gravity_reflects_acoustic_waves():
     assert abs(dl - (-2 * L1 / (rho * c * c))) < 1e-15 and dux == 0.0
     # the outgoing amplitude at rest: L1 = -(c/2)(dp/dxi - rho c du/dxi)
     assert abs(L1 + 0.5 * c * (dp - rho * c * du)) < 1e-15
+
+
+def _poiseuille_start_up(y, t, H, g, nu, nterms=400):
+    # the channel started from rest under a constant body force g (x) between no-slip
+    # walls: the sine series of the steady parabola decaying at the rates n^2 pi^2 nu / H^2
+    u = g / (2 * nu) * y * (H - y)
+    for k in range(nterms):
+        n = 2 * k + 1
+        u = u - (4 * g * H * H / (nu * np.pi ** 3 * n ** 3) * np.sin(n * np.pi * y / H)
+                 * np.exp(-(n * np.pi) ** 2 * nu * t / H ** 2))
+    return u
+
+
+def _poiseuille_error(nx):
+    # Section 8.2: Re = 10, Ma = 0.05, started from rest, velocity error at t U0 / H = 1
+    import labfm_inputs as li
+    from oracle import labfm_oracle as core
+    ns = li.channel(nx, nx, m=6, jitter=0.1)
+    H, U0 = ns.Ly, 1.0
+    mu = U0 * H / 10.0
+    g = 8 * mu * U0 / H ** 2
+    c = U0 / 0.05
+    op = bo.channel_operator(ns, 6, 4)
+    q = np.zeros((3, ns.N))
+    dt0 = core.stable_dt(np.stack([q[0], q[1] + U0, q[2]]), ns.s, c, mu)
+    nsteps = int(np.ceil(1.0 / dt0))
+    for _ in range(nsteps):
+        q = bo.channel_time_step(q, 1.0 / nsteps, op, ns, c, mu, (g, 0.0))
+    ua = _poiseuille_start_up(ns.xy[:, 1], 1.0, H, g, mu)
+    assert np.all(q[1][ns.meta["row"] == 0] == 0.0) and np.all(q[2][ns.meta["row"] == 0] == 0.0)
+    return np.linalg.norm(q[1] - ua) / np.linalg.norm(ua), float(np.abs(q[2]).max())
+
+
+def test_poiseuille_start_up_converges_to_the_analytic_solution():
+    # the transient is an exact solution of the isothermal equations (parallel flow,
+    # uniform density): interior LABFM m = 6, the wall rows of Section 7.1, the no-slip
+    # wall in LODI form.  The paper reports about 4th order at t* = 1
+    e16, v16 = _poiseuille_error(16)
+    e24, v24 = _poiseuille_error(24)
+    order = np.log(e16 / e24) / np.log(24 / 16)
+    assert e16 < 3e-3 and e24 < 4e-4, (e16, e24)
+    assert order > 4.0, order
+    # no cross-channel velocity develops beyond the discretisation error
+    assert v16 < 1e-3 and v24 < 1e-3
