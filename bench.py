@@ -58,8 +58,9 @@ def parse():
                     help="lattice side (512 = the benchmark workload; smaller sizes for profiling)")
     ap.add_argument("--ref-cores", type=int, default=0,
                     help="host cores for --impl reference (0 = all, 1 = one, in this process)")
-    ap.add_argument("--only", choices=["stencil_opt"], default=None,
-                    help="run one extra workload alone on --nx and print its JSON (for profiling)")
+    ap.add_argument("--only", choices=["stencil_opt", "adjoint"], default=None,
+                    help="run one extra workload alone on --nx and print its JSON (for profiling; "
+                         "adjoint: --steps steps)")
     return ap.parse_args()
 
 
@@ -529,13 +530,34 @@ def _build(lb, torch, ns, residual=False):
     return rp, col, wb, s
 
 
-def run_adjoint(lb, torch, args, nsteps=500, every=50):
+def adjoint_kernel_bytes(nnz, N):
+    """Algorithmic bytes per launch of the kernels of a checkpointed FP32 rollout's
+    backward pass (every stencil entry's record once, every node value once):
+      recording stage: the stage kernel's 24 B per entry + 64 B per node, and the
+        eight derivative combinations it stores (32 B per node);
+      pass A: per node the stage state (16 B), its derivative combinations (32 B),
+        the cotangent (16 B), 1/s (4 B) in; twelve derivative adjoints (48 B) and
+        three own-value adjoints (16 B) out;
+      pass B: per transposed entry its record (24 B); per node the row pointer
+        (4 B), the twelve derivative adjoints gathered (48 B, once), five row sums
+        (20 B), the own-value adjoints (16 B), the running cotangent in and out
+        (32 B) and the next stage's cotangent (16 B);
+      filter transpose: per entry 8 B; per node row pointer, cotangent (gathered
+        once), filter row sum, two outputs: 4 + 16 + 4 + 32 B;
+      filter (forward, also in the recompute): 8 B per entry + 36 B per node."""
+    return {"rec_stage": 24.0 * nnz + 96.0 * N, "adj_a": 132.0 * N, "adj_b": 24.0 * nnz + 136.0 * N,
+            "adj_filter": 8.0 * nnz + 56.0 * N, "filter": 8.0 * nnz + 36.0 * N}
+
+
+def run_adjoint(lb, torch, args, nsteps=500, every=50, nx=512):
     """Gradient of the final domain kinetic energy w.r.t. the initial (rho, rho u, rho v):
     262,144 nodes, m = 8, FP32, 500 steps, checkpoints every 50 steps.  The node set
-    uses +-0.1 s jitter so that the 500-step trajectory stays bounded."""
+    uses +-0.05 s jitter so that the 500-step trajectory stays bounded.  Then one
+    checkpoint segment again with launch timing on, for the per-kernel breakdown of
+    the backward pass."""
     import numpy as np
     import labfm_inputs as li
-    ns = li.tgv_lattice(512, m=8, h_over_s=2.8, jitter=0.05, seed=5)
+    ns = li.tgv_lattice(nx, m=8, h_over_s=2.8, jitter=0.05, seed=5)
     rp, col, wb, s = _build(lb, torch, ns)
     plan = lb.Plan(rp, col, wb["w"], wb["kappa"], s, dtype=torch.float32)
     lb.enable_adjoint(plan)
@@ -561,12 +583,61 @@ def run_adjoint(lb, torch, args, nsteps=500, every=50):
     torch.cuda.synchronize()
     bwd_ms = e.elapsed_time(f)
     g = c.grad
-    out = {"workload": "262,144-node lattice (+-0.05 s jitter), m = 8, Taylor-Green + 0.05 x "
-                       "band-limited perturbation (|k| <= 8), FP32, 500 steps, checkpoint every 50",
+    out = {"workload": f"{ns.N:,}-node lattice (+-0.05 s jitter), m = 8, Taylor-Green + 0.05 x "
+                       f"band-limited perturbation (|k| <= 8), FP32, {nsteps} steps, checkpoint every {every}",
            "steps": nsteps, "checkpoint_every": every, "forward_ms": fwd_ms, "backward_ms": bwd_ms,
            "backward_over_forward": bwd_ms / fwd_ms, "ke_final": float(ke.item()),
            "grad_finite": bool(torch.isfinite(g).all().item()),
            "grad_norm_per_field": [float(x) for x in g.double().norm(dim=1).cpu()]}
+    # per-kernel breakdown: one segment of `every` steps forward and backward with
+    # launch timing on (CUDA events on the launching stream around every adjoint
+    # launch, around each step's four stage launches and each filter launch)
+    seg = min(every, nsteps)
+    plan.set_profiling(True)
+    c2 = c0.clone().requires_grad_(True)
+    ke2 = lb.domain_kinetic_energy(lb.rollout(plan, lb.to_primitive(c2), dt, seg, phys,
+                                              checkpoint_every=seg), s)
+    ke2.backward()
+    torch.cuda.synchronize()
+    prof = plan.read_profile()
+    plan.set_profiling(False)
+    peak, _ = peaks()
+    nnz = int(col.numel())
+    alg = adjoint_kernel_bytes(nnz, ns.N)
+    kernels = {}
+    for key, kname, launches in (("rec_stage", "k_stage_rec<float> (recording stage)", "rec_stage_launches"),
+                                 ("adj_a", "k_adj_pointwise_rec<float> (pass A)", "adj_a_launches"),
+                                 ("adj_b", "k_adj_transpose<float> (pass B)", "adj_b_launches"),
+                                 ("adj_filter", "k_filter_adjoint<float> (filter transpose)",
+                                  "adj_filter_launches")):
+        n = prof[launches]
+        ms = prof[key + "_ms"] / max(1, n)
+        kernels[key] = {"kernel": kname, "launches": n, "mean_launch_ms": ms,
+                        "alg_bytes_per_launch": alg[key],
+                        "achieved_GBps": alg[key] / (ms * 1e-3) / 1e9 if n else None,
+                        "frac_of_measured_hbm": alg[key] / (ms * 1e-3) / 1e9 / peak if n else None}
+    fms = prof["filter_ms"] / max(1, prof["filter_launches"])
+    kernels["filter"] = {"kernel": "k_filter_aos<float> (forward and recompute)",
+                         "launches": prof["filter_launches"], "mean_launch_ms": fms,
+                         "alg_bytes_per_launch": alg["filter"],
+                         "achieved_GBps": alg["filter"] / (fms * 1e-3) / 1e9,
+                         "frac_of_measured_hbm": alg["filter"] / (fms * 1e-3) / 1e9 / peak}
+    sms = prof["stage_ms"] / max(1, prof["stage_launches"])
+    kernels["stage"] = {"kernel": "k_stage<float> (forward rollout)", "launches": prof["stage_launches"],
+                        "mean_launch_ms": sms}
+    # backward time per step, kernel by kernel: one recorded recompute (4 recording
+    # stages + filter) and the reverse sweep (4 x (pass A + pass B) + filter transpose)
+    per_step = {"recorded_stages": 4 * kernels["rec_stage"]["mean_launch_ms"],
+                "recorded_filter": fms,
+                "pass_a": 4 * kernels["adj_a"]["mean_launch_ms"],
+                "pass_b": 4 * kernels["adj_b"]["mean_launch_ms"],
+                "filter_transpose": kernels["adj_filter"]["mean_launch_ms"]}
+    fwd_step = 4 * sms + fms
+    out["breakdown"] = {"segment_steps": seg, "kernels": kernels, "backward_ms_per_step_by_kernel": per_step,
+                        "backward_kernels_ms_per_step": sum(per_step.values()),
+                        "forward_kernels_ms_per_step": fwd_step,
+                        "backward_kernels_over_forward_kernels": sum(per_step.values()) / fwd_step,
+                        "dropped": prof["dropped"]}
     plan.close()
     return out
 
@@ -836,13 +907,18 @@ def run_ours(args, world, rank, local):
 def main():
     args = parse()
     world, rank, local = dist_init(args)
-    if args.only == "stencil_opt":
+    if args.only:
         import torch
 
         import __graft_entry__ as g
         g.build()
         import paper_2102_02019_gb300 as lb
-        print(json.dumps(run_stencil_opt(lb, torch, args)), flush=True)
+        if args.only == "stencil_opt":
+            out = run_stencil_opt(lb, torch, args)
+        else:
+            out = run_adjoint(lb, torch, args, nsteps=args.steps, every=max(1, min(50, args.steps // 2)),
+                              nx=args.nx)
+        print(json.dumps(out), flush=True)
         return 0
     if args.impl == "reference":
         rc = run_reference(args, world, rank)

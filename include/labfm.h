@@ -16,6 +16,18 @@
  *  - Return value: LABFM_OK (0) or a labfm_status error code.  No call aborts,
  *    traps or throws.  labfm_last_error() returns a thread-local message for the
  *    most recent failing call on this thread.
+ *  - Fault injection (for tests of callers' error handling): the environment
+ *    variable LABFM_FAULT, read at each call, makes entry points fail on the
+ *    host as they would on a real fault.  "alloc": every call that would
+ *    allocate device memory (plan creation, labfm_build_stencils,
+ *    labfm_build_weights with n_failed_out, labfm_plan_set_dt's first call,
+ *    labfm_plan_set_staging, labfm_plan_enable_adjoint, labfm_step_graph_create)
+ *    returns LABFM_ENOMEM before touching the device.  "capacity":
+ *    labfm_build_stencils with a col buffer returns LABFM_ECAPACITY with
+ *    *nnz_out = col_capacity + 1 before touching the device.
+ *    "singular_node:<i>": labfm_build_weights also flags node i
+ *    LABFM_NODE_SINGULAR (and counts it as failed).  Unset or any other value:
+ *    nothing is injected.
  *  - Node arrays are indexed 0..N-1.  Fields are structure-of-arrays, "3 x N":
  *    field f of node i at [f * N + i], f = 0 (ln rho), 1 (u), 2 (v).
  *  - Operator order in every weight array (Section 2, selector C^d):
@@ -292,11 +304,25 @@ int labfm_plan_set_prefetch(labfm_plan* plan, int distance);
  * plans' steps, run the unstaged kernel.  The call measures the largest round
  * (synchronising `stream`) and sizes the grid; a lane count whose largest round
  * does not fit `stages` slots in shared memory keeps the unstaged kernel.  Each
- * wait of the staged kernel on a copy is bounded (1 s); one that runs out is
- * reported by labfm_plan_device_status.
+ * wait of the staged kernel on a copy is bounded (1 s by default,
+ * labfm_plan_set_wait_limit); one that runs out is reported by
+ * labfm_plan_device_status.
  * Errors: EINVAL (F64 plan with stages != 0, stages not in {0, 2, 3, 4}).
  */
 int labfm_plan_set_staging(labfm_plan* plan, int stages, void* stream);
+
+/*
+ * Limit of every bounded wait of the staged stage kernel on a bulk copy, in
+ * nanoseconds (0 .. 10 s; the default is 1 s).  0 makes each wait a single
+ * non-blocking test of the copy's barrier, so that waits run out: this exercises
+ * the timeout path, which leaves LABFM_ETIMEOUT for labfm_plan_device_status and
+ * that step's results invalid.  A CTA whose wait ran out lets its copies in
+ * flight land (waiting at most 1 s more for each) before it exits, so the
+ * context stays usable.  No counterpart in the paper (failure detection).
+ * Host-only call.
+ * Errors: EINVAL (limit out of range).
+ */
+int labfm_plan_set_wait_limit(labfm_plan* plan, int64_t limit_ns);
 
 /*
  * Device-side status of the plan's kernels since the last query: LABFM_OK, or
@@ -516,12 +542,18 @@ int labfm_step_graph_destroy(labfm_step_graph* graph);
  * library only the memory it manages itself, or a real-time loop that must not
  * pay for (or synchronise on) an allocation.  The paper has no counterpart; it
  * is an interface convenience.
- *   Limit: 3 x N x 16 bytes (F32) or 3 x N x 32 bytes (F64) must fit in 16 MiB,
- *   i.e. N <= 349,525 nodes in F32 and N <= 174,762 in F64; larger plans get
- *   LABFM_ECAPACITY with the required size in labfm_last_error().
+ *   Limit: labfm_rk_workspace_bytes(plan) must fit in 16 MiB: 3 x N x 16 bytes
+ *   (F32) or 3 x N x 32 bytes (F64), plus 64 bytes of work-queue tickets for a
+ *   persistent plan, i.e. N <= 349,525 nodes in F32 (349,524 persistent) and
+ *   N <= 174,762 in F64; larger plans get LABFM_ECAPACITY with the required
+ *   size in labfm_last_error().
+ *   The plan must belong to the current device (else LABFM_EINVAL).
  *   The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any stream
- *   capture.  Every GPU that loads the library holds the 16 MiB until exit.
+ *   capture.  The address is kept for the life of the process: a caller that
+ *   resets a device (cudaDeviceReset) must not call this entry point on that
+ *   device afterwards.  Every GPU that loads the library holds the 16 MiB until
+ *   exit.
  *   All calls on a device share the array: two calls whose work overlaps on the
  *   GPU (different streams or threads) race and corrupt each other's state.
  *   Nothing in the array needs to start at zero; every buffer is written before
@@ -536,13 +568,26 @@ int labfm_rk_step_noalloc(const labfm_plan* plan, void* Q, double dt, int nsteps
  * four consecutive stage launches of every step (counted as four launches, so
  * stage_ms / stage_launches is the mean launch duration including the short
  * gaps between them) and one pair around every filter launch.  Timing whole
- * blocks keeps the events from stalling the stream between every launch. */
+ * blocks keeps the events from stalling the stream between every launch.
+ * The adjoint calls are timed the same way: the four recording stage launches of
+ * labfm_rk_step_record as one block (its filter launch counts as a filter
+ * launch), and in the reverse sweep every pass A (pointwise derivative
+ * adjoints), pass B (transposed-operator gather) and filter-transpose launch on
+ * its own. */
 typedef struct labfm_profile {
     double stage_ms;         /* summed duration of the fused RHS + RK stage launches */
     int64_t stage_launches;
     double filter_ms;        /* summed duration of the filter launches */
     int64_t filter_launches;
     int64_t dropped;         /* launches not timed because the event pool was full */
+    double rec_stage_ms;     /* recording stage launches (labfm_rk_step_record) */
+    int64_t rec_stage_launches;
+    double adj_a_ms;         /* adjoint pass A launches */
+    int64_t adj_a_launches;
+    double adj_b_ms;         /* adjoint pass B launches */
+    int64_t adj_b_launches;
+    double adj_filter_ms;    /* filter-transpose launches */
+    int64_t adj_filter_launches;
 } labfm_profile;
 
 /* Enable (1) or disable (0) launch timing on this plan; enabling clears the record. */

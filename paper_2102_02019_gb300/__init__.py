@@ -58,7 +58,11 @@ class _PlanInfo(ctypes.Structure):
 class _Profile(ctypes.Structure):
     _fields_ = [("stage_ms", ctypes.c_double), ("stage_launches", ctypes.c_int64),
                 ("filter_ms", ctypes.c_double), ("filter_launches", ctypes.c_int64),
-                ("dropped", ctypes.c_int64)]
+                ("dropped", ctypes.c_int64),
+                ("rec_stage_ms", ctypes.c_double), ("rec_stage_launches", ctypes.c_int64),
+                ("adj_a_ms", ctypes.c_double), ("adj_a_launches", ctypes.c_int64),
+                ("adj_b_ms", ctypes.c_double), ("adj_b_launches", ctypes.c_int64),
+                ("adj_filter_ms", ctypes.c_double), ("adj_filter_launches", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p
@@ -99,6 +103,8 @@ _SIGS = {
     "labfm_plan_set_prefetch": (_I32, [_P, _I32]),
     "labfm_plan_set_staging": (_I32, [_P, _I32, _P]),
     "labfm_plan_device_status": (_I32, [_P, ctypes.POINTER(_I32)]),
+    "labfm_plan_set_wait_limit": (_I32, [_P, _I64]),
+    "labfm_plan_set_wait_limit": (_I32, [_P, _I64]),
     "labfm_step_graph_create": (_I32, [ctypes.POINTER(_P), _P, _P, ctypes.c_size_t, _D, ctypes.POINTER(_Phys)]),
     "labfm_step_graph_run": (_I32, [_P, _P, _I32, _P]),
     "labfm_step_graph_destroy": (_I32, [_P]),
@@ -122,7 +128,7 @@ _SIGS = {
 
 
 # the C ABI this binding's signatures and structures follow (include/labfm.h)
-ABI_VERSION = 3
+ABI_VERSION = 4
 
 
 def _load() -> ctypes.CDLL:
@@ -161,6 +167,25 @@ def _ptr(t: torch.Tensor | None) -> int | None:
     if not t.is_contiguous():
         raise ValueError("liblabfm takes contiguous tensors")
     return t.data_ptr()
+
+
+def _state(plan, t: torch.Tensor, name: str = "Q") -> int:
+    """Device pointer of a 3 x N state of the plan's element type.  The C side sees
+    only a pointer, so a tensor of another dtype or fewer than 3 N elements would
+    make the kernels read and write past its end: both are checked here, before
+    any launch."""
+    if t.dtype != plan.dtype:
+        raise ValueError(f"{name} is {t.dtype} but the plan computes in {plan.dtype}")
+    if tuple(t.shape) != (3, plan.N):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}; the plan needs (3, {plan.N})")
+    return _ptr(t)
+
+
+def _nodes(plan, t: torch.Tensor, name: str) -> torch.Tensor:
+    """N float64 node values (node spacing s), checked like _state; returns t."""
+    if t.dtype != torch.float64 or t.numel() != plan.N:
+        raise ValueError(f"{name} must hold {plan.N} float64 values")
+    return t
 
 
 def _stream(stream=None) -> int:
@@ -285,8 +310,10 @@ class Plan:
 
     def stable_dt_instances(self, fields, s, c, mu, stream=None):
         """labfm_stable_dt_instances: eq. dt per instance (float64 device tensor)."""
+        _nodes(self, s, "s")
+        fp, sp = _state(self, fields, "fields"), _ptr(s)
         out = torch.empty(getattr(self, "n_instances", 1), dtype=torch.float64, device=fields.device)
-        _check(lib.labfm_stable_dt_instances(self._h, _ptr(fields), _ptr(s), float(c), float(mu),
+        _check(lib.labfm_stable_dt_instances(self._h, fp, sp, float(c), float(mu),
                                              _ptr(out), _stream(stream)))
         return out
 
@@ -301,6 +328,16 @@ class Plan:
         """labfm_plan_set_staging: shared-memory staging of the operator stream for the
         F32 stage kernel with 16 or 32 lanes per node (0 = off)."""
         _check(lib.labfm_plan_set_staging(self._h, int(stages), _stream(stream)))
+
+    def set_wait_limit(self, limit_ns: int) -> None:
+        """labfm_plan_set_wait_limit: limit of the staged kernel's bounded waits (ns;
+        0 = one non-blocking test, which makes the waits run out)."""
+        _check(lib.labfm_plan_set_wait_limit(self._h, int(limit_ns)))
+
+    def set_wait_limit(self, limit_ns: int) -> None:
+        """labfm_plan_set_wait_limit: limit of the staged kernel's bounded waits (ns;
+        0 = one non-blocking test, which makes the waits run out)."""
+        _check(lib.labfm_plan_set_wait_limit(self._h, int(limit_ns)))
 
     def device_status(self) -> int:
         """labfm_plan_device_status: LABFM_OK (0) or LABFM_ETIMEOUT (7); clears it."""
@@ -336,6 +373,7 @@ class Plan:
         _check(lib.labfm_plan_set_launch(self._h, group, block))
 
     def autotune(self, fields: torch.Tensor, phys: Phys, reps: int = 5, stream=None):
+        _state(self, fields, "fields")
         out = torch.empty_like(fields)
         g, b = _I32(0), _I32(0)
         ph = phys.c()
@@ -359,6 +397,7 @@ class Plan:
         each L2 prefetch distance), and (F32) for the staged kernel at the given (lanes
         per node, ring slots), keep the fastest.  Q is not modified.  Returns the chosen
         configuration."""
+        _state(self, Q)
         info = self.info()
         block = info["block"]
         pfs = tuple(prefetch) if self.dtype == torch.float32 else (info["prefetch"],)
@@ -410,16 +449,19 @@ class Plan:
 
 def rhs(plan: Plan, fields: torch.Tensor, phys: Phys, out: torch.Tensor | None = None, stream=None):
     """eq. icns right-hand side of (ln rho, u, v) (labfm_rhs); fields is 3 x N."""
+    fp = _state(plan, fields, "fields")
     out = torch.empty_like(fields) if out is None else out
+    op = _state(plan, out, "out")
     ph = phys.c()
-    _check(lib.labfm_rhs(plan.handle, _ptr(fields), _ptr(out), ctypes.byref(ph), _stream(stream)))
+    _check(lib.labfm_rhs(plan.handle, fp, op, ctypes.byref(ph), _stream(stream)))
     return out
 
 
 def filter(plan: Plan, fields: torch.Tensor, out: torch.Tensor | None = None, stream=None):  # noqa: A001
     """Hyperviscous filter (1 + kappa nabla^m) of the three fields (labfm_filter)."""
+    fp = _state(plan, fields, "fields")
     out = torch.empty_like(fields) if out is None else out
-    _check(lib.labfm_filter(plan.handle, _ptr(fields), _ptr(out), _stream(stream)))
+    _check(lib.labfm_filter(plan.handle, fp, _state(plan, out, "out"), _stream(stream)))
     return out
 
 
@@ -432,9 +474,10 @@ def workspace(plan: Plan) -> torch.Tensor:
 def rk_step(plan: Plan, Q: torch.Tensor, dt: float, nsteps: int, phys: Phys,
             work: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """nsteps RK3(2)4[2R+]C steps + filter, in place on Q (labfm_rk_step)."""
+    qp = _state(plan, Q)
     work = workspace(plan) if work is None else work
     ph = phys.c()
-    _check(lib.labfm_rk_step(plan.handle, _ptr(Q), _ptr(work), work.numel(), float(dt), int(nsteps),
+    _check(lib.labfm_rk_step(plan.handle, qp, _ptr(work), work.numel(), float(dt), int(nsteps),
                              ctypes.byref(ph), _stream(stream)))
     return Q
 
@@ -442,8 +485,10 @@ def rk_step(plan: Plan, Q: torch.Tensor, dt: float, nsteps: int, phys: Phys,
 def stable_dt(plan: Plan, fields: torch.Tensor, s: torch.Tensor, c: float, mu: float,
               out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
     """eq. dt as a 1-element float64 device tensor (labfm_stable_dt)."""
+    _nodes(plan, s, "s")
+    fp, sp = _state(plan, fields, "fields"), _ptr(s)
     out = torch.empty(1, dtype=torch.float64, device=fields.device) if out is None else out
-    _check(lib.labfm_stable_dt(plan.handle, _ptr(fields), _ptr(s), float(c), float(mu), _ptr(out),
+    _check(lib.labfm_stable_dt(plan.handle, fp, sp, float(c), float(mu), _ptr(out),
                                _stream(stream)))
     return out
 
@@ -453,9 +498,12 @@ def rk_step_host(plan: Plan, Q_host: torch.Tensor, Q_dev: torch.Tensor, dt: floa
     """labfm_rk_step_host: state in (pinned) host memory, copied in and out by the call."""
     if Q_host.is_cuda or not Q_host.is_contiguous():
         raise ValueError("Q_host must be a contiguous host tensor")
+    if Q_host.dtype != plan.dtype or tuple(Q_host.shape) != (3, plan.N):
+        raise ValueError(f"Q_host must be {plan.dtype} of shape (3, {plan.N})")
+    qd = _state(plan, Q_dev, "Q_dev")
     work = workspace(plan) if work is None else work
     ph = phys.c()
-    _check(lib.labfm_rk_step_host(plan.handle, Q_host.data_ptr(), _ptr(Q_dev), _ptr(work), work.numel(),
+    _check(lib.labfm_rk_step_host(plan.handle, Q_host.data_ptr(), qd, _ptr(work), work.numel(),
                                   float(dt), int(nsteps), ctypes.byref(ph), _stream(stream)))
     return Q_host
 
@@ -472,9 +520,11 @@ def rk_step_noalloc(plan: Plan, Q: torch.Tensor, dt: float, nsteps: int, phys: P
                     stream=None) -> torch.Tensor:
     """labfm_rk_step_noalloc: rk_step without a work buffer, for callers that cannot
     allocate device memory; the state buffers live in the library's static device
-    array (16 MiB: N <= 349,525 in float32, <= 174,762 in float64)."""
+    array (16 MiB: N <= 349,525 in float32 (349,524 for a persistent plan),
+    <= 174,762 in float64)."""
+    qp = _state(plan, Q)
     ph = phys.c()
-    _check(lib.labfm_rk_step_noalloc(plan.handle, _ptr(Q), float(dt), int(nsteps), ctypes.byref(ph),
+    _check(lib.labfm_rk_step_noalloc(plan.handle, qp, float(dt), int(nsteps), ctypes.byref(ph),
                                      _stream(stream)))
     return Q
 
@@ -492,7 +542,7 @@ class StepGraph:
         self._h = h
 
     def run(self, Q: torch.Tensor, nsteps: int, stream=None) -> torch.Tensor:
-        _check(lib.labfm_step_graph_run(self._h, _ptr(Q), int(nsteps), _stream(stream)))
+        _check(lib.labfm_step_graph_run(self._h, _state(self.plan, Q), int(nsteps), _stream(stream)))
         return Q
 
     def close(self):
@@ -529,19 +579,21 @@ def adjoint_workspace(plan: Plan) -> torch.Tensor:
 
 def rhs_adjoint(plan: Plan, fields, lam, phys: Phys, work=None, stream=None):
     """(dR/dq)^T lam at state `fields` (labfm_rhs_adjoint)."""
+    fp, lp = _state(plan, fields, "fields"), _state(plan, lam, "lam")
     work = adjoint_workspace(plan) if work is None else work
     out = torch.empty_like(fields)
     ph = phys.c()
-    _check(lib.labfm_rhs_adjoint(plan.handle, _ptr(fields), _ptr(lam), _ptr(out), ctypes.byref(ph),
+    _check(lib.labfm_rhs_adjoint(plan.handle, fp, lp, _ptr(out), ctypes.byref(ph),
                                  _ptr(work), work.numel(), _stream(stream)))
     return out
 
 
 def rk_step_adjoint(plan: Plan, Q, lam, dt: float, phys: Phys, work=None, stream=None):
     """lam <- (dQ_next/dQ)^T lam for one step from state Q (labfm_rk_step_adjoint), in place."""
+    qp, lp = _state(plan, Q), _state(plan, lam, "lam")
     work = adjoint_workspace(plan) if work is None else work
     ph = phys.c()
-    _check(lib.labfm_rk_step_adjoint(plan.handle, _ptr(Q), _ptr(lam), float(dt), ctypes.byref(ph),
+    _check(lib.labfm_rk_step_adjoint(plan.handle, qp, lp, float(dt), ctypes.byref(ph),
                                      _ptr(work), work.numel(), _stream(stream)))
     return lam
 
@@ -554,26 +606,29 @@ def stage_states(plan: Plan) -> torch.Tensor:
 
 def rk_step_record(plan: Plan, Q, states, dt: float, phys: Phys, work=None, stream=None):
     """labfm_rk_step_record: Q advanced one step in place, its stage states kept in `states`."""
+    qp = _state(plan, Q)
     work = workspace(plan) if work is None else work
     ph = phys.c()
-    _check(lib.labfm_rk_step_record(plan.handle, _ptr(Q), _ptr(states), states.numel(), _ptr(work),
+    _check(lib.labfm_rk_step_record(plan.handle, qp, _ptr(states), states.numel(), _ptr(work),
                                     work.numel(), float(dt), ctypes.byref(ph), _stream(stream)))
     return Q
 
 
 def rk_step_adjoint_recorded(plan: Plan, states, lam, dt: float, phys: Phys, work=None, stream=None):
     """lam <- (dQ_next/dQ)^T lam from recorded stage states (labfm_rk_step_adjoint_recorded)."""
+    lp = _state(plan, lam, "lam")
     work = adjoint_workspace(plan) if work is None else work
     ph = phys.c()
-    _check(lib.labfm_rk_step_adjoint_recorded(plan.handle, _ptr(states), _ptr(lam), float(dt),
+    _check(lib.labfm_rk_step_adjoint_recorded(plan.handle, _ptr(states), lp, float(dt),
                                               ctypes.byref(ph), _ptr(work), work.numel(), _stream(stream)))
     return lam
 
 
 def filter_adjoint(plan: Plan, lam, work=None, stream=None):
+    lp = _state(plan, lam, "lam")
     work = adjoint_workspace(plan) if work is None else work
     out = torch.empty_like(lam)
-    _check(lib.labfm_filter_adjoint(plan.handle, _ptr(lam), _ptr(out), _ptr(work), work.numel(),
+    _check(lib.labfm_filter_adjoint(plan.handle, lp, _ptr(out), _ptr(work), work.numel(),
                                     _stream(stream)))
     return out
 

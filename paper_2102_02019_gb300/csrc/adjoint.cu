@@ -556,16 +556,23 @@ template <typename T>
 int adjoint_sweep_t(const labfm_plan* p, const Packed<T>* const (&X)[4], const D8<T>* D, void* lambda,
                     double dt, const Phys<T>& ph, AdjWork<T>& w, cudaStream_t st) {
     int rc;
+    labfm_plan* pm = const_cast<labfm_plan*>(p);  // only the launch-timing record changes
     // filter transpose, then the stages backwards
     if ((rc = pack_fields(p, lambda, w.Ob, st))) return rc;
+    int ev = prof_begin(pm, kProfAdjFilter, st);
     if ((rc = filt_adj<T>(p, w.Ob, w.Lam, w.Fb, dt, kRkB[3], st))) return rc;
+    prof_end(pm, ev, st);
     for (int k = 3; k >= 0; --k) {
+        ev = prof_begin(pm, kProfAdjA, st);
         if ((rc = pass_a_rec<T>(p, X[k], D + k * p->N, w.Fb, w.g, w.Ob, ph, st))) return rc;
+        prof_end(pm, ev, st);
         const double bprev = k > 0 ? kRkB[k - 1] : 0.0;
         const double cprev = k > 0 ? kRkA[k - 1] - kRkB[k - 1] : 0.0;
+        ev = prof_begin(pm, kProfAdjB, st);
         if ((rc = pass_b<T>(p, 1, w.g, w.Ob, nullptr, w.Lam, k > 0 ? w.Fb : nullptr, dt, bprev, cprev,
                             st)))
             return rc;
+        prof_end(pm, ev, st);
     }
     return unpack_fields(p, w.Lam, lambda, st);
 }
@@ -631,6 +638,7 @@ extern "C" int labfm_plan_enable_adjoint(labfm_plan* p, void* stream) {
     LABFM_NVTX("labfm_plan_enable_adjoint");
     if (!p || !p->row_ptr) return set_error(LABFM_EINVAL, "null or empty plan");
     if (p->trow_ptr) return LABFM_OK;
+    if (fault_alloc()) return injected_alloc_error("labfm_plan_enable_adjoint");
     cudaStream_t st = as_stream(stream);
     return p->dtype == LABFM_F32 ? build_transposed<float>(p, st) : build_transposed<double>(p, st);
 }

@@ -3,6 +3,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <stdlib.h>
+#include <string.h>
+
 #include <new>
 #include <string>
 
@@ -24,6 +27,32 @@ int cuda_error(cudaError_t e, const char* what) {
     const int code = (e == cudaErrorMemoryAllocation) ? LABFM_ENOMEM : LABFM_ECUDA;
     return set_error(code, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
                                cudaGetErrorString(e) + ")");
+}
+
+namespace {
+const char* fault_spec() {
+    const char* f = getenv("LABFM_FAULT");
+    return f ? f : "";
+}
+}  // namespace
+
+bool fault_alloc() { return strcmp(fault_spec(), "alloc") == 0; }
+
+bool fault_capacity() { return strcmp(fault_spec(), "capacity") == 0; }
+
+int64_t fault_singular_node() {
+    const char* f = fault_spec();
+    const char* key = "singular_node:";
+    const size_t n = strlen(key);
+    if (strncmp(f, key, n) != 0 || f[n] == '\0') return -1;
+    char* end = nullptr;
+    const long long v = strtoll(f + n, &end, 10);
+    if (*end != '\0' || v < 0) return -1;
+    return int64_t(v);
+}
+
+int injected_alloc_error(const char* where) {
+    return set_error(LABFM_ENOMEM, std::string(where) + ": injected allocation failure (LABFM_FAULT=alloc)");
 }
 
 }  // namespace labfm
@@ -121,7 +150,7 @@ void prof_end(labfm_plan* p, int idx, cudaStream_t st) {
 
 extern "C" const char* labfm_last_error(void) { return g_last_error.c_str(); }
 
-extern "C" int labfm_abi_version(void) { return 3; }
+extern "C" int labfm_abi_version(void) { return 4; }
 
 extern "C" int labfm_plan_create(labfm_plan** out, int64_t N, int64_t nnz, labfm_dtype dtype,
                                  const int32_t* row_ptr, const int32_t* col, const double* w,
@@ -134,6 +163,7 @@ extern "C" int labfm_plan_create(labfm_plan** out, int64_t N, int64_t nnz, labfm
     if (N <= 0 || N >= (int64_t(1) << 31) - 1) return set_error(LABFM_EINVAL, "N out of range");
     if (nnz < 0 || nnz >= (int64_t(1) << 31)) return set_error(LABFM_EINVAL, "nnz out of range");
     if (dtype != LABFM_F32 && dtype != LABFM_F64) return set_error(LABFM_EINVAL, "unknown dtype");
+    if (fault_alloc()) return injected_alloc_error("labfm_plan_create");
     const PlanInput in{N, nnz, row_ptr, col, w, kappa, s};
     return create_plan(out, &in, 1, dtype, stream);
 }
@@ -163,6 +193,7 @@ extern "C" int labfm_plan_create_batched(labfm_plan** out, int n_inst, const int
     }
     if (rc == LABFM_OK && (Ntot >= (int64_t(1) << 31) - 1 || nnztot >= (int64_t(1) << 31)))
         rc = set_error(LABFM_EINVAL, "combined size out of range");
+    if (rc == LABFM_OK && fault_alloc()) rc = injected_alloc_error("labfm_plan_create_batched");
     if (rc == LABFM_OK) rc = create_plan(out, in, n_inst, dtype, stream);
     delete[] in;
     return rc;
@@ -171,6 +202,7 @@ extern "C" int labfm_plan_create_batched(labfm_plan** out, int n_inst, const int
 extern "C" int labfm_plan_set_dt(labfm_plan* p, const double* dt_inst, void* stream) {
     if (int rc = check_plan(p)) return rc;
     if (!dt_inst) return set_error(LABFM_EINVAL, "null dt array");
+    if (!p->dt_node && fault_alloc()) return injected_alloc_error("labfm_plan_set_dt");
     return set_node_dt(p, dt_inst, as_stream(stream));
 }
 
@@ -198,7 +230,16 @@ extern "C" int labfm_plan_set_prefetch(labfm_plan* p, int distance) {
 
 extern "C" int labfm_plan_set_staging(labfm_plan* p, int stages, void* stream) {
     if (int rc = check_plan(p)) return rc;
+    if (stages != 0 && fault_alloc()) return injected_alloc_error("labfm_plan_set_staging");
     return configure_staging(p, stages, as_stream(stream));
+}
+
+extern "C" int labfm_plan_set_wait_limit(labfm_plan* p, int64_t limit_ns) {
+    if (int rc = check_plan(p)) return rc;
+    if (limit_ns < 0 || limit_ns > int64_t(10000000000))
+        return set_error(LABFM_EINVAL, "wait limit must be in [0, 10 s]");
+    p->wait_ns = uint64_t(limit_ns);
+    return LABFM_OK;
 }
 
 extern "C" int labfm_plan_device_status(const labfm_plan* p, int* status_out) {
@@ -411,18 +452,39 @@ extern "C" int labfm_plan_set_profiling(labfm_plan* p, int enable) {
 extern "C" int labfm_plan_read_profile(labfm_plan* p, labfm_profile* out) {
     if (int rc = check_plan(p)) return rc;
     if (!out) return set_error(LABFM_EINVAL, "null profile output");
-    *out = labfm_profile{0.0, 0, 0.0, 0, p->prof_dropped};
+    *out = labfm_profile{};
+    out->dropped = p->prof_dropped;
     if (p->prof_used > 0) {
         LABFM_CUDA_TRY(cudaEventSynchronize(p->prof_ev[2 * (p->prof_used - 1) + 1]));
         for (int k = 0; k < p->prof_used; ++k) {
             float ms = 0.f;
             LABFM_CUDA_TRY(cudaEventElapsedTime(&ms, p->prof_ev[2 * k], p->prof_ev[2 * k + 1]));
-            if (p->prof_kind[k] == 0 || p->prof_kind[k] == 2) {
-                out->stage_ms += ms;
-                out->stage_launches += p->prof_kind[k] == 2 ? 4 : 1;
-            } else {
-                out->filter_ms += ms;
-                ++out->filter_launches;
+            switch (p->prof_kind[k]) {
+                case kProfStage:
+                case kProfStages4:
+                    out->stage_ms += ms;
+                    out->stage_launches += p->prof_kind[k] == kProfStages4 ? 4 : 1;
+                    break;
+                case kProfFilter:
+                    out->filter_ms += ms;
+                    ++out->filter_launches;
+                    break;
+                case kProfRecStages4:
+                    out->rec_stage_ms += ms;
+                    out->rec_stage_launches += 4;
+                    break;
+                case kProfAdjA:
+                    out->adj_a_ms += ms;
+                    ++out->adj_a_launches;
+                    break;
+                case kProfAdjB:
+                    out->adj_b_ms += ms;
+                    ++out->adj_b_launches;
+                    break;
+                case kProfAdjFilter:
+                    out->adj_filter_ms += ms;
+                    ++out->adj_filter_launches;
+                    break;
             }
         }
     }

@@ -38,6 +38,7 @@ extern "C" int labfm_step_graph_create(labfm_step_graph** out, const labfm_plan*
         return set_error(LABFM_EINVAL, "work buffer must be 16-byte aligned");
     if (!(dt > 0.0) && !(dt == 0.0 && plan->dt_node))
         return set_error(LABFM_EINVAL, "dt must be positive (or 0 with per-instance dt set)");
+    if (fault_alloc()) return injected_alloc_error("labfm_step_graph_create");
     labfm_step_graph* g = new (std::nothrow) labfm_step_graph();
     if (!g) return set_error(LABFM_ENOMEM, "host allocation failed");
     g->plan = plan;

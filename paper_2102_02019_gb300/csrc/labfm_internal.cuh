@@ -28,6 +28,19 @@ int cuda_error(cudaError_t e, const char* what);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Host-side fault injection for tests of the error paths (api.cu), read from the
+// environment variable LABFM_FAULT at every call that honours it:
+//   "alloc"             entry points that allocate device memory return
+//                       LABFM_ENOMEM before touching the device;
+//   "capacity"          labfm_build_stencils reports a col buffer one entry too
+//                       small (LABFM_ECAPACITY) before touching the device;
+//   "singular_node:<i>" labfm_build_weights flags node i as singular.
+// Nothing is injected when the variable is unset or holds anything else.
+bool fault_alloc();
+bool fault_capacity();
+int64_t fault_singular_node();  // the node to flag, or -1
+int injected_alloc_error(const char* where);
+
 // Periodic minimum image, written out so that the neighbour search and the
 // weight build see bit-identical offsets (no contraction, plain IEEE ops).
 __device__ __forceinline__ double min_image(double d, double L, bool periodic) {
@@ -82,6 +95,7 @@ struct labfm_plan {
     int stage_slot_bytes[2] = {0, 0};
     int stage_grid[2] = {0, 0};
     int* dev_status = nullptr;   // device word: LABFM_ETIMEOUT after a bounded wait ran out
+    uint64_t wait_ns = 1000000000ull;  // limit of each bounded wait (labfm_plan_set_wait_limit)
     // transposed operator for the adjoint (labfm_plan_enable_adjoint): for node k
     // the entries (i, w_ik) of every row i whose stencil contains k, in the same
     // record layout as the forward operator, plus row sums of the forward weights
@@ -93,7 +107,7 @@ struct labfm_plan {
     // launch timing (labfm_plan_set_profiling): event pairs around launches
     bool profiling = false;
     cudaEvent_t* prof_ev = nullptr;  // 2 * prof_cap events
-    char* prof_kind = nullptr;       // 0 = stage, 1 = filter
+    char* prof_kind = nullptr;       // labfm::ProfKind of each pair
     int prof_cap = 0;
     int prof_used = 0;
     int64_t prof_dropped = 0;
@@ -122,8 +136,12 @@ int launch_stable_dt(const labfm_plan* p, const void* fields, const double* s, d
 bool launch_shape_supported(int group, int block);
 
 // Launch timing around kernel launches (api.cu); kind 0 = one stage launch,
-// 1 = one filter launch, 2 = the four stage launches of a step.
+// 1 = one filter launch, 2 = the four stage launches of a step, 3 = the four
+// recording stage launches of labfm_rk_step_record, 4 = one adjoint pass A,
+// 5 = one adjoint pass B, 6 = one filter-transpose launch.
 // Returns the pair index to close with prof_end, or -1 when not profiling.
+enum ProfKind { kProfStage = 0, kProfFilter = 1, kProfStages4 = 2, kProfRecStages4 = 3,
+                kProfAdjA = 4, kProfAdjB = 5, kProfAdjFilter = 6 };
 int prof_begin(labfm_plan* p, int kind, cudaStream_t st);
 void prof_end(labfm_plan* p, int idx, cudaStream_t st);
 

@@ -23,7 +23,9 @@ void* g_addr[kMaxDevices] = {};  // device address of g_static_work, per device
 
 // The device address of g_static_work on the current device.  In host code the
 // name g_static_work is only a host-side stand-in, so the address has to be
-// looked up once per device with that device current.
+// looked up once per device with that device current.  The cached address
+// belongs to the device's context at the time of the lookup: after the caller
+// resets the device (cudaDeviceReset) it is stale, which the header documents.
 int static_work_address(void** out) {
     int dev = 0;
     LABFM_CUDA_TRY(cudaGetDevice(&dev));
@@ -57,6 +59,12 @@ extern "C" int labfm_rk_step_noalloc(const labfm_plan* p, void* Q, double dt, in
             "labfm_rk_step_noalloc: N = " + std::to_string(p->N) + " needs " +
                 std::to_string(need) + " bytes of scratch but the static array holds " +
                 std::to_string(kStaticWorkBytes) + " bytes (use labfm_rk_step with a work buffer)");
+    int dev = 0;
+    LABFM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != p->device)
+        return labfm::set_error(LABFM_EINVAL, "labfm_rk_step_noalloc: the plan lives on device " +
+                                                  std::to_string(p->device) + " but device " +
+                                                  std::to_string(dev) + " is current");
     void* work = nullptr;
     if (int rc = static_work_address(&work)) return rc;
     return labfm::launch_rk_steps(p, Q, work, dt, nsteps, phys, labfm::as_stream(stream));

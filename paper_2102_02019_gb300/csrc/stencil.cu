@@ -310,6 +310,13 @@ extern "C" int labfm_build_stencils(const double* xy, const double* h, int64_t N
     if (!(Lx > 0.0) || !(Ly > 0.0) || !isfinite(Lx) || !isfinite(Ly))
         return set_error(LABFM_EINVAL, "domain size must be positive and finite");
     if (col_capacity < 0) return set_error(LABFM_EINVAL, "negative col_capacity");
+    if (fault_alloc()) return injected_alloc_error("labfm_build_stencils");
+    if (col && fault_capacity()) {
+        *nnz_out = col_capacity + 1;
+        return set_error(LABFM_ECAPACITY, "col_capacity " + std::to_string(col_capacity) + " < required " +
+                                              std::to_string(col_capacity + 1) +
+                                              " (injected: LABFM_FAULT=capacity)");
+    }
     cudaStream_t st = as_stream(stream);
     ScratchList scratch(st);
 

@@ -180,11 +180,12 @@ __global__ void LABFM_STAGE_BOUNDS k_stage_rec(PlanView<T> P, const Packed<T>* X
 // CTA b takes rounds b, b + gridDim.x, ... and keeps S rounds in flight, so the
 // copy engine, not the registers of the consumer warps, holds the loads in
 // flight.  Neighbour fields are gathered from global memory as in k_stage.  A
-// wait that runs out (1 s) sets *status = LABFM_ETIMEOUT; the CTA then lets its
-// copies in flight land (bounded again) and returns.
+// wait that runs out (the plan's limit, 1 s by default) sets *status =
+// LABFM_ETIMEOUT; the CTA then lets its copies in flight land (waiting at most
+// kBulkDrainNs for each) and returns.
 constexpr int kBulkBlock = 128;
 constexpr int kRoundWarps = kBulkBlock / 32;
-constexpr uint64_t kBulkWaitNs = 1000000000ull;
+constexpr uint64_t kBulkDrainNs = 1000000000ull;
 
 template <int G>
 constexpr int round_nodes() {
@@ -252,7 +253,7 @@ template <int G, int S>
 __global__ void __launch_bounds__(kBulkBlock)
     k_stage_bulk(PlanView<float> P, const Packed<float>* X_in, const Packed<float>* Q_in,
                  Packed<float>* Q_out, Packed<float>* X_out, double dt, double bk, double ck,
-                 Phys<float> ph, uint32_t slot_bytes, int* status) {
+                 Phys<float> ph, uint32_t slot_bytes, int* status, uint64_t wait_ns) {
     extern __shared__ __align__(128) unsigned char ring[];
     __shared__ __align__(8) uint64_t full[S];
     constexpr int RN = round_nodes<G>();
@@ -279,14 +280,14 @@ __global__ void __launch_bounds__(kBulkBlock)
     int it = 0;
     for (int64_t r = blockIdx.x; r < nrounds; r += gridDim.x, ++it) {
         const int slot = it % S;
-        const bool ok = mbar_wait_bounded(smem_u32(&full[slot]), uint32_t(it / S) & 1u, kBulkWaitNs);
+        const bool ok = mbar_wait_bounded(smem_u32(&full[slot]), uint32_t(it / S) & 1u, wait_ns);
         if (__syncthreads_or(!ok)) {
             if (t == 0) {
                 atomicExch(status, LABFM_ETIMEOUT);
                 for (int k = 0; k < S; ++k) {  // copies still in flight land before exit
                     const int j = it + k;
                     if (blockIdx.x + int64_t(j) * gridDim.x >= nrounds) break;
-                    mbar_wait_bounded(smem_u32(&full[j % S]), uint32_t(j / S) & 1u, kBulkWaitNs);
+                    mbar_wait_bounded(smem_u32(&full[j % S]), uint32_t(j / S) & 1u, kBulkDrainNs);
                 }
             }
             return;
@@ -594,7 +595,7 @@ int stage_bulk_launch(const labfm_plan* p, const Packed<float>* xin, const Packe
     const int gi = G == 32 ? 1 : 0;
     const uint32_t slot = uint32_t(p->stage_slot_bytes[gi]);
     k_stage_bulk<G, S><<<p->stage_grid[gi], kBulkBlock, size_t(S) * slot, st>>>(
-        view<float>(p), xin, qin, qout, xout, dt, bk, ck, ph, slot, p->dev_status);
+        view<float>(p), xin, qin, qout, xout, dt, bk, ck, ph, slot, p->dev_status, p->wait_ns);
     LABFM_LAUNCH_CHECK("staged rk stage kernel");
     return LABFM_OK;
 }
@@ -705,7 +706,7 @@ int rk_one_step_t(const labfm_plan* p, void* work, double dt, const labfm_phys* 
     const Packed<T>* xin[4] = {X, Y, X, Y};
     const Packed<T>* qin[4] = {X, P, P, P};
     Packed<T>* xout[4] = {Y, X, Y, nullptr};
-    const int evs = profile ? prof_begin(pm, 2, st) : -1;  // the four stages as one block
+    const int evs = profile ? prof_begin(pm, kProfStages4, st) : -1;  // the four stages as one block
     for (int k = 0; k < 4; ++k) {
         const double bk = kRkB[k];
         const double ck = k < 3 ? kRkA[k] - kRkB[k] : 0.0;
@@ -713,7 +714,7 @@ int rk_one_step_t(const labfm_plan* p, void* work, double dt, const labfm_phys* 
             return rc;
     }
     prof_end(pm, evs, st);
-    const int ev = profile ? prof_begin(pm, 1, st) : -1;
+    const int ev = profile ? prof_begin(pm, kProfFilter, st) : -1;
     if ((rc = filter_aos<T>(p, P, X, st))) return rc;
     prof_end(pm, ev, st);
     return LABFM_OK;
@@ -785,12 +786,16 @@ int forward_stages_t(const labfm_plan* p, const void* X1v, void* Pv, void* X2v, 
     Packed<T>* X4 = static_cast<Packed<T>*>(X4v);
     D8<T>* D = static_cast<D8<T>*>(Dv);
     const int64_t N = p->N;
+    labfm_plan* pm = const_cast<labfm_plan*>(p);  // only the launch-timing record changes
+    const int ev = prof_begin(pm, kProfRecStages4, st);
     int rc;
     if ((rc = stage_rec_launch<T>(p, X1, X1, P, X2, dt, kRkB[0], kRkA[0] - kRkB[0], ph, D, st))) return rc;
     if ((rc = stage_rec_launch<T>(p, X2, P, P, X3, dt, kRkB[1], kRkA[1] - kRkB[1], ph, D + N, st))) return rc;
     if ((rc = stage_rec_launch<T>(p, X3, P, P, X4, dt, kRkB[2], kRkA[2] - kRkB[2], ph, D + 2 * N, st)))
         return rc;
-    return stage_rec_launch<T>(p, X4, P, P, nullptr, dt, kRkB[3], 0.0, ph, D + 3 * N, st);
+    if ((rc = stage_rec_launch<T>(p, X4, P, P, nullptr, dt, kRkB[3], 0.0, ph, D + 3 * N, st))) return rc;
+    prof_end(pm, ev, st);
+    return LABFM_OK;
 }
 
 // One step that keeps its stage states: X1 = pack(Q), X2..X4 the inputs of
@@ -808,7 +813,10 @@ int rk_step_record_t(const labfm_plan* p, void* Q, void* Xv, void* Pv, void* Yv,
     if ((rc = forward_stages_t<T>(p, X, P, X + p->N, X + 2 * p->N, X + 3 * p->N, X + 4 * p->N, dt, php,
                                   st)))
         return rc;
+    labfm_plan* pm = const_cast<labfm_plan*>(p);
+    const int ev = prof_begin(pm, kProfFilter, st);
     if ((rc = filter_aos<T>(p, P, Y, st))) return rc;
+    prof_end(pm, ev, st);
     return unpack_fields(p, Y, Q, st);
 }
 }  // namespace

@@ -883,6 +883,15 @@ __global__ void k_modal_response(const double* __restrict__ xy, const double* __
     }
 }
 
+// Injected failure (LABFM_FAULT=singular_node:<i>): node i flagged singular as if
+// its LU had met a zero pivot, counted once in the failed-node total.
+__global__ void k_flag_singular(int32_t* __restrict__ node_status, int64_t i,
+                                unsigned long long* __restrict__ n_failed) {
+    const int32_t old = node_status[i];
+    node_status[i] = old | LABFM_NODE_SINGULAR;
+    if (n_failed && old == 0) atomicAdd(n_failed, 1ull);
+}
+
 template <int M>
 int launch_weights(const double* xy, const double* h, const double* s, int64_t N, double Lx,
                    double Ly, uint32_t pm, const int32_t* row_ptr, const int32_t* col, int64_t nnz,
@@ -925,6 +934,7 @@ extern "C" int labfm_build_weights(const double* xy, const double* h, const doub
     if (m < 2 || m > 10 || (m & 1))
         return set_error(LABFM_EINVAL, "order m must be even and in [2, 10], got " + std::to_string(m));
     if (!(Lx > 0.0) || !(Ly > 0.0)) return set_error(LABFM_EINVAL, "domain size must be positive");
+    if (n_failed_out && fault_alloc()) return injected_alloc_error("labfm_build_weights");
     cudaStream_t st = as_stream(stream);
     unsigned long long* nf = nullptr;
     if (n_failed_out) {
@@ -938,6 +948,12 @@ extern "C" int labfm_build_weights(const double* xy, const double* h, const doub
         case 6: rc = launch_weights<6>(xy, h, s, N, Lx, Ly, periodic_mask, row_ptr, col, nnz, w, kappa, residual, node_status, nf, st); break;
         case 8: rc = launch_weights<8>(xy, h, s, N, Lx, Ly, periodic_mask, row_ptr, col, nnz, w, kappa, residual, node_status, nf, st); break;
         case 10: rc = launch_weights<10>(xy, h, s, N, Lx, Ly, periodic_mask, row_ptr, col, nnz, w, kappa, residual, node_status, nf, st); break;
+    }
+    const int64_t fnode = fault_singular_node();
+    if (rc == LABFM_OK && fnode >= 0 && fnode < N) {
+        k_flag_singular<<<1, 1, 0, st>>>(node_status, fnode, nf);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_error(e, "injected singular node");
     }
     if (n_failed_out) {
         unsigned long long hf = 0;

@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol(built_lib):
 
 def test_binding_loads_and_covers_the_header(built_lib):
     import paper_2102_02019_gb300 as lb
-    assert lb.lib.labfm_abi_version() == 3
+    assert lb.lib.labfm_abi_version() == 4
     assert lb.lib.labfm_last_error() == b""
     declared = set(_declared_functions())
     assert declared <= set(lb.exported_symbols()), declared - set(lb.exported_symbols())
@@ -103,3 +103,41 @@ def test_empty_and_oversize_inputs_are_rejected_on_the_host(built_lib):
         assert L.labfm_plan_create(ctypes.byref(plan), N, 0, 1, p, None, p, p, p, None) == 1
         assert b"N out of range" in L.labfm_last_error() and plan.value is None
     assert nnz.value == -1
+
+
+def test_binding_rejects_states_that_do_not_match_the_plan(built_lib):
+    # the C entry points see only pointers, so a state of another element type or
+    # with fewer than 3 N values would be read and written past its end: the
+    # binding checks both before any launch (no GPU needed to see the refusal)
+    import types
+
+    import torch
+
+    import paper_2102_02019_gb300 as lb
+    plan = types.SimpleNamespace(N=10, dtype=torch.float64, handle=None, device="cpu")
+    phys = lb.Phys(100.0, 0.005)
+    s = torch.ones(10, dtype=torch.float64)
+    calls = {
+        "rk_step": lambda q: lb.rk_step(plan, q, 1e-3, 1, phys),
+        "rk_step_noalloc": lambda q: lb.rk_step_noalloc(plan, q, 1e-3, 1, phys),
+        "rhs": lambda q: lb.rhs(plan, q, phys),
+        "filter": lambda q: lb.filter(plan, q),
+        "stable_dt": lambda q: lb.stable_dt(plan, q, s, 10.0, 0.005),
+        "rk_step_host": lambda q: lb.rk_step_host(plan, q, q, 1e-3, 1, phys),
+        "rhs_adjoint": lambda q: lb.rhs_adjoint(plan, q, q, phys),
+        "rk_step_adjoint": lambda q: lb.rk_step_adjoint(plan, q, q, 1e-3, phys),
+        "rk_step_record": lambda q: lb.rk_step_record(plan, q, None, 1e-3, phys),
+        "filter_adjoint": lambda q: lb.filter_adjoint(plan, q),
+    }
+    bad = {"float32": torch.zeros(3, 10, dtype=torch.float32),
+           "short": torch.zeros(3, 9, dtype=torch.float64),
+           "flat": torch.zeros(30, dtype=torch.float64)}
+    for name, call in calls.items():
+        for kind, q in bad.items():
+            with pytest.raises(ValueError, match="plan|Q_host"):
+                call(q)
+    # a state that matches passes the check and is then refused for living on the host
+    with pytest.raises(ValueError, match="CUDA"):
+        lb.rk_step(plan, torch.zeros(3, 10, dtype=torch.float64), 1e-3, 1, phys)
+    with pytest.raises(ValueError, match="float64 values"):
+        lb.stable_dt(plan, torch.zeros(3, 10, dtype=torch.float64), s[:5], 10.0, 0.005)

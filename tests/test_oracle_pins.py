@@ -366,6 +366,46 @@ def test_stable_dt_for_taylor_green():
     assert o.stable_dt(q, ns.s, 10.0, 1e3) < dt  # a large viscosity makes the viscous limit bind
 
 
+def _dt_coefficients():
+    d = {k: float(v) for k, v in golden("dt_coefficients.txt")}
+    return d["convective"], d["viscous"]
+
+
+def _one_node(a=0.0, u=0.0, v=0.0):
+    return np.array([[a], [u], [v]], dtype=np.float64)
+
+
+def test_stable_dt_viscous_branch_closed_form():
+    # where the viscous limit binds, dt = C_visc s^2 rho / mu (eq. dt); each factor
+    # is varied on its own so that a wrong coefficient, power of s, or dependence on
+    # rho or mu fails
+    _, cv = _dt_coefficients()
+    c = 10.0
+    base = o.stable_dt(_one_node(), np.array([0.01]), c, 10.0)
+    assert base == pytest.approx(cv * 0.01 ** 2 * 1.0 / 10.0, rel=1e-15)
+    assert o.stable_dt(_one_node(), np.array([0.02]), c, 10.0) == pytest.approx(4.0 * base, rel=1e-15)
+    assert o.stable_dt(_one_node(a=np.log(3.0)), np.array([0.01]), c, 10.0) == pytest.approx(3.0 * base,
+                                                                                               rel=1e-14)
+    assert o.stable_dt(_one_node(), np.array([0.01]), c, 20.0) == pytest.approx(0.5 * base, rel=1e-15)
+    # the velocity does not enter the viscous limit
+    assert o.stable_dt(_one_node(u=0.3, v=-0.4), np.array([0.01]), c, 10.0) == pytest.approx(base, rel=1e-15)
+
+
+def test_stable_dt_convective_branch_and_domain_minimum():
+    cc, cv = _dt_coefficients()
+    # |u| = 5 (3-4-5), c = 5, negligible viscosity: dt = C_conv s / (|u| + c)
+    assert o.stable_dt(_one_node(u=3.0, v=4.0), np.array([0.01]), 5.0, 1e-12) == pytest.approx(
+        cc * 0.01 / 10.0, rel=1e-15)
+    # two nodes, one limited by each branch: the minimum over the domain of both
+    q = np.array([[0.0, np.log(2.0)], [3.0, 0.0], [4.0, 0.0]])
+    s = np.array([0.01, 0.004])
+    mu = 0.05
+    expect = min(cc * 0.01 / (5.0 + 5.0), cv * 0.004 ** 2 * 2.0 / mu,
+                 cc * 0.004 / 5.0, cv * 0.01 ** 2 / mu)
+    assert o.stable_dt(q, s, 5.0, mu) == pytest.approx(expect, rel=1e-15)
+    assert expect == pytest.approx(cv * 0.004 ** 2 * 2.0 / mu, rel=1e-15)  # the viscous node binds
+
+
 # ---------------------------------------------------------------- Navier-Stokes
 
 def test_rhs_matches_tensor_form_of_the_equations():
