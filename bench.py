@@ -669,6 +669,7 @@ def run_fp32_error(lb, torch, args, nsteps=1000, shape=None):
                 plan.set_staging(shape.get("staging", 0))
                 plan.set_prefetch(shape.get("prefetch", 0))
                 plan.set_launch(shape["group"], shape["block"])
+                plan.set_filter_launch(shape.get("filter_group", 0), shape.get("filter_persistent", False))
             ke0 = float(lb.kinetic_energy(Q, s).item())
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
@@ -734,7 +735,8 @@ def run_ours(args, world, rank, local):
         if args.group:
             plan.set_launch(args.group, 128)
             tuned = {"group": args.group, "block": 128, "persistent": False, "staging": 0,
-                     "prefetch": plan.info()["prefetch"]}
+                     "prefetch": plan.info()["prefetch"], "filter_group": args.group,
+                     "filter_persistent": False}
         else:
             tuned = plan.tune_step(Q, phys, dt)
         group, block = tuned["group"], tuned["block"]
@@ -813,7 +815,9 @@ def run_ours(args, world, rank, local):
                        launch_shape={"group": shape32[0], "block": shape32[1],
                                      "persistent": tuned_shape[torch.float32]["persistent"],
                                      "staging": tuned_shape[torch.float32].get("staging", 0),
-                                     "prefetch": tuned_shape[torch.float32].get("prefetch", 0)}),
+                                     "prefetch": tuned_shape[torch.float32].get("prefetch", 0),
+                                     "filter_group": tuned_shape[torch.float32].get("filter_group"),
+                                     "filter_persistent": tuned_shape[torch.float32].get("filter_persistent")}),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "kernel": ("k_stage_bulk<float> (fused RHS + RK stage, operator staged by bulk copies)"

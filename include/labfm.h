@@ -89,6 +89,8 @@ typedef struct labfm_plan_info {
     int64_t device_bytes; /* device memory owned by the plan */
     int32_t prefetch;     /* L2 prefetch distance of the F32 record stream (labfm_plan_set_prefetch) */
     int32_t stages;       /* shared-memory staging slots (labfm_plan_set_staging; 0 = off) */
+    int32_t filter_group; /* lanes per node of the filter kernel (labfm_plan_set_filter_launch) */
+    int32_t filter_persistent; /* 1 if the filter runs a persistent grid-stride grid */
 } labfm_plan_info;
 
 /* Message for the most recent failing call on this thread ("" if none). */
@@ -103,7 +105,8 @@ int labfm_abi_version(void);
  * separately, no fused multiply-add) on the periodic minimum image
  * dx = x_j - x_i; dx -= Lx if dx > Lx/2; dx += Lx if dx < -Lx/2 (same in y).
  *
- *   xy        device, N x 2 doubles (x_i, y_i) row-major; 0 <= x < Lx, 0 <= y < Ly
+ *   xy        device, N x 2 doubles (x_i, y_i) row-major; 0 <= x < Lx on a periodic
+ *             axis, 0 <= x <= Lx on a bounded one (a wall may lie on the edge), same in y
  *   h         device, N doubles, stencil scale h_i > 0
  *   periodic_mask  bit 0: x periodic, bit 1: y periodic
  *   row_ptr   device, N + 1 int32 (output): row i is col[row_ptr[i] .. row_ptr[i+1])
@@ -185,6 +188,10 @@ int labfm_build_weights(const double* xy, const double* h, const double* s, int6
  *   max_iter   host, iteration limit per node (>= 0)
  *   h_out      device, N doubles (output)
  *   solves_out device, N int32 (output, may be NULL): systems solved per node
+ *   alpha_out  device, N x 2 doubles (output, may be NULL): per node, alpha_L at
+ *              the returned h and alpha_L at the h where the iteration stopped
+ *              (test 3 or 4 failed there); NaN where none was computed (no h
+ *              passed, or the stop came from test 1, a singular M_i or max_iter)
  * One CTA per node; no allocation, no synchronisation.
  * Errors: EINVAL (null pointers, N, m, factor, max_iter).
  */
@@ -192,7 +199,56 @@ int labfm_stencil_optimise(const double* xy, const double* h0, const double* s, 
                            double Lx, double Ly, uint32_t periodic_mask,
                            const int32_t* row_ptr, const int32_t* col, int m, double factor,
                            double amp_max, double resid_coef, int max_iter, double* h_out,
-                           int32_t* solves_out, void* stream);
+                           int32_t* solves_out, double* alpha_out, void* stream);
+
+/*
+ * Operator of a domain with walls (Section 7.1, Table "Schemes for derivatives
+ * near boundaries", and Appendix A), in the format of labfm_build_weights
+ * (difference form, six weights per entry, kappa) so that labfm_plan_create
+ * takes it unchanged.  A wall is its nodes i0 (wall node b) with their inward
+ * unit normals n_b, each with the nodes i1..i4 of its normal column at q s_b
+ * along n_b (Section 7.1).  Per node:
+ *   - rows q >= 3 and every node in no column: LABFM of order m on the stencil
+ *     |r_ji| <= 2 h_i (as labfm_build_stencils and labfm_build_weights);
+ *   - rows q = 1, 2: d/dx and d/dy from the five-point difference along the
+ *     column (asymmetric at q = 1, central at q = 2) and one-dimensional LABFM
+ *     of order 4 along the row (Appendix A: the nodes of the same q of the other
+ *     columns within 2 h1d, h1d = h1d_over_s s_i, offsets eta along the tangent
+ *     t = (-n_y, n_x)), rotated to (x, y); the second derivatives and the filter
+ *     from LABFM of order m_wall on the node's stencil;
+ *   - wall nodes q = 0: d/dx and d/dy from the one-sided five-point difference
+ *     and 1D LABFM only, no second derivatives, kappa = 0 (the wall is not
+ *     filtered; with labfm_plan_set_walls its velocity is held at zero and ln rho
+ *     follows the LODI equation of the wall).
+ * Rows are sorted by column; the union of a row's LABFM stencil and its column
+ * and row nodes.
+ *   xy, h, s        device, N x 2 / N / N doubles (bounded axes take [0, L])
+ *   m, m_wall       LABFM orders (even, 2..10; the paper uses m = 6, m_wall = 4)
+ *   n_wall          number of wall nodes (5 n_wall <= N)
+ *   wall_column     device, n_wall x 5 int32: the nodes q = 0..4 of each column
+ *   wall_normal     device, n_wall x 2 doubles: inward unit normal of each wall node
+ *   h1d_over_s      support of the 1D LABFM (the paper gives none; 1.7 for the
+ *                   uniform wall rows)
+ *   row_ptr         device, N + 1 int32 (output)
+ *   col             device, col_capacity int32 (output), or NULL with
+ *                   col_capacity = 0 to query nnz (w, kappa, node_status unused)
+ *   w               device, 6 x nnz doubles (output), operator-major w[d * nnz + e]
+ *   kappa, node_status  device, N doubles / N int32 (output); a node whose row has
+ *                   more than 64 row neighbours or a singular 1D system is flagged
+ *                   LABFM_NODE_SINGULAR with an empty row
+ *   n_failed_out    host (output, may be NULL; then no ESINGULAR)
+ * Allocates and frees stream-ordered scratch; synchronises `stream`.  The row
+ * neighbour search is the cell-list search of labfm_build_stencils.
+ * Errors: EINVAL (sizes, orders, a column node out of range or in two columns, a
+ * normal not of unit length), ECAPACITY (col_capacity < nnz; nnz_out holds the
+ * required size), ESINGULAR (n_failed_out requested and > 0).
+ */
+int labfm_build_wall_operator(const double* xy, const double* h, const double* s, int64_t N,
+                              double Lx, double Ly, uint32_t periodic_mask, int m, int m_wall,
+                              int64_t n_wall, const int32_t* wall_column, const double* wall_normal,
+                              double h1d_over_s, int32_t* row_ptr, int32_t* col, int64_t col_capacity,
+                              int64_t* nnz_out, double* w, double* kappa, int32_t* node_status,
+                              int64_t* n_failed_out, void* stream);
 
 /*
  * Modal (amplitude) response of built operators (Section 3): per node i and
@@ -253,6 +309,27 @@ int labfm_plan_create_batched(labfm_plan** plan, int n_inst, const int64_t* N_in
                               const int32_t* const* col, const double* const* w,
                               const double* const* kappa, const double* const* s,
                               labfm_dtype dtype, void* stream);
+
+/*
+ * No-slip walls of a plan (Section 7.1): at the wall nodes the step and
+ * right-hand-side kernels hold u = v = 0 (zero right-hand side) and advance
+ * ln rho by eq. lodilnro with u_xi = 0, the outgoing wave L1 of eq. Ldef
+ * (L2 = 0 for isothermal flow) and the incoming wave L4 = L1 + rho c g.n:
+ *   d ln rho/dt = -(L4 + L1) / (rho c^2) - d u_eta / d eta,
+ *   L1 = -(c/2) (dp/dxi - rho c du_xi/dxi),  dp/dxi = c^2 rho d ln rho/dxi.
+ * The paper prints L4 = L1 + 2 rho c g.n; with eq. lodiu only the factor 1 holds
+ * u_xi at zero (a resting hydrostatic column stays at rest), which is taken.  The
+ * derivatives are the plan's own (labfm_build_wall_operator gives the wall rows'
+ * one-sided differences and 1D LABFM).  Every other node follows eq. icns.
+ *   wall_nodes   device, n_wall int32; wall_normal: device, n_wall x 2 doubles
+ *                (inward unit normals); n_wall = 0 removes the walls
+ * Plans with walls run the plain stage grid (not the persistent or staged
+ * kernels); the adjoint and recording calls refuse them.  Not for batched plans.
+ * Synchronises `stream`.  Errors: EINVAL (node out of range or listed twice,
+ * normal not of unit length), ENOMEM.
+ */
+int labfm_plan_set_walls(labfm_plan* plan, int64_t n_wall, const int32_t* wall_nodes,
+                         const double* wall_normal, void* stream);
 
 /*
  * Per-instance time steps (host, n_instances values > 0).  Afterwards
@@ -347,6 +424,18 @@ int labfm_plan_get_info(const labfm_plan* plan, labfm_plan_info* info);
  * labfm_plan_autotune picks the fastest group.
  */
 int labfm_plan_set_launch(labfm_plan* plan, int group, int block);
+
+/*
+ * Launch shape of the filter kernel of labfm_rk_step (and labfm_rk_step_record):
+ * `group` lanes per node (2, 4, 8, 16 or 32; 0 = the plan's group of
+ * labfm_plan_set_launch), and persistent = 1 for a grid of (SMs x resident
+ * blocks) whose warps stride over the nodes, so that no partly filled last wave
+ * of blocks leaves the GPU idle (0 = one group per node over a full grid).
+ * The filtered state does not depend on `persistent`; with another lane count
+ * the filter sums are added in another order (FP rounding only).  Host-only.
+ * Errors: EINVAL (unsupported lanes per node).
+ */
+int labfm_plan_set_filter_launch(labfm_plan* plan, int group, int persistent);
 
 /*
  * Time every supported group size on this plan with CUDA events (the RHS

@@ -52,7 +52,8 @@ class _PlanInfo(ctypes.Structure):
                 ("dtype", ctypes.c_int32), ("group", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("n_instances", ctypes.c_int32), ("entry_bytes", ctypes.c_int32),
                 ("filter_entry_bytes", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
-                ("prefetch", ctypes.c_int32), ("stages", ctypes.c_int32)]
+                ("prefetch", ctypes.c_int32), ("stages", ctypes.c_int32),
+                ("filter_group", ctypes.c_int32), ("filter_persistent", ctypes.c_int32)]
 
 
 class _Profile(ctypes.Structure):
@@ -77,13 +78,18 @@ _SIGS = {
     "labfm_build_weights": (_I32, [_P, _P, _P, _I64, _D, _D, ctypes.c_uint32, _P, _P, _I64, _I32,
                                    _P, _P, _P, _P, ctypes.POINTER(_I64), _P]),
     "labfm_stencil_optimise": (_I32, [_P, _P, _P, _I64, _D, _D, ctypes.c_uint32, _P, _P, _I32, _D, _D,
-                                      _D, _I32, _P, _P, _P]),
+                                      _D, _I32, _P, _P, _P, _P]),
     "labfm_modal_response": (_I32, [_P, _P, _I64, _D, _D, ctypes.c_uint32, _P, _P, _I64, _P, _I32, _P,
                                     _P]),
+    "labfm_build_wall_operator": (_I32, [_P, _P, _P, _I64, _D, _D, ctypes.c_uint32, _I32, _I32, _I64, _P, _P,
+                                         _D, _P, _P, _I64, ctypes.POINTER(_I64), _P, _P, _P,
+                                         ctypes.POINTER(_I64), _P]),
+    "labfm_plan_set_walls": (_I32, [_P, _I64, _P, _P, _P]),
     "labfm_plan_create": (_I32, [ctypes.POINTER(_P), _I64, _I64, _I32, _P, _P, _P, _P, _P, _P]),
     "labfm_plan_destroy": (_I32, [_P]),
     "labfm_plan_get_info": (_I32, [_P, ctypes.POINTER(_PlanInfo)]),
     "labfm_plan_set_launch": (_I32, [_P, _I32, _I32]),
+    "labfm_plan_set_filter_launch": (_I32, [_P, _I32, _I32]),
     "labfm_plan_autotune": (_I32, [_P, _P, _P, ctypes.POINTER(_Phys), _I32,
                                    ctypes.POINTER(_I32), ctypes.POINTER(_I32), _P]),
     "labfm_rhs": (_I32, [_P, _P, _P, ctypes.POINTER(_Phys), _P]),
@@ -103,7 +109,6 @@ _SIGS = {
     "labfm_plan_set_prefetch": (_I32, [_P, _I32]),
     "labfm_plan_set_staging": (_I32, [_P, _I32, _P]),
     "labfm_plan_device_status": (_I32, [_P, ctypes.POINTER(_I32)]),
-    "labfm_plan_set_wait_limit": (_I32, [_P, _I64]),
     "labfm_plan_set_wait_limit": (_I32, [_P, _I64]),
     "labfm_step_graph_create": (_I32, [ctypes.POINTER(_P), _P, _P, ctypes.c_size_t, _D, ctypes.POINTER(_Phys)]),
     "labfm_step_graph_run": (_I32, [_P, _P, _I32, _P]),
@@ -244,18 +249,51 @@ def build_weights(xy, h, s, Lx, Ly, row_ptr, col, m, periodic=(True, True), resi
 
 
 def stencil_optimise(xy, h0, s, Lx, Ly, row_ptr, col, m, factor=0.99, amp_max=1.01, resid_coef=1e-4,
-                     max_iter=400, periodic=(True, True), stream=None):
+                     max_iter=400, periodic=(True, True), alpha=False, stream=None):
     """labfm_stencil_optimise: per-node optimised h (Section 4) and the number of systems
-    solved per node, as (h, solves) device tensors.  resid_coef=math.inf switches the
-    Laplacian-residual test off."""
+    solved per node, as (h, solves) device tensors, and with alpha=True also the
+    (N, 2) Laplacian residuals alpha_L at the returned h and where the iteration
+    stopped.  resid_coef=math.inf switches the Laplacian-residual test off."""
     N = xy.shape[0]
     mask = (1 if periodic[0] else 0) | (2 if periodic[1] else 0)
     h = torch.empty(N, dtype=torch.float64, device=xy.device)
     solves = torch.empty(N, dtype=torch.int32, device=xy.device)
+    al = torch.empty((N, 2), dtype=torch.float64, device=xy.device) if alpha else None
     _check(lib.labfm_stencil_optimise(_ptr(xy), _ptr(h0), _ptr(s), N, Lx, Ly, mask, _ptr(row_ptr),
                                       _ptr(col), m, factor, amp_max, resid_coef, max_iter, _ptr(h), _ptr(solves),
-                                      _stream(stream)))
-    return h, solves
+                                      _ptr(al), _stream(stream)))
+    return (h, solves, al) if alpha else (h, solves)
+
+
+def build_wall_operator(xy, h, s, Lx, Ly, m, m_wall, wall_column, wall_normal, h1d_over_s=1.7,
+                        periodic=(True, False), check=False, stream=None):
+    """labfm_build_wall_operator (Section 7.1): the operator of a domain with walls as
+    dict(row_ptr, col, w (6, nnz), kappa, status, n_failed), ready for Plan.
+    wall_column: (n_wall, 5) int32 nodes q = 0..4 of each wall column; wall_normal:
+    (n_wall, 2) float64 inward unit normals."""
+    N = xy.shape[0]
+    n_wall = wall_column.shape[0]
+    if wall_column.dtype != torch.int32 or tuple(wall_column.shape) != (n_wall, 5):
+        raise ValueError("wall_column must be int32 of shape (n_wall, 5)")
+    if wall_normal.dtype != torch.float64 or tuple(wall_normal.shape) != (n_wall, 2):
+        raise ValueError("wall_normal must be float64 of shape (n_wall, 2)")
+    mask = (1 if periodic[0] else 0) | (2 if periodic[1] else 0)
+    row_ptr = torch.empty(N + 1, dtype=torch.int32, device=xy.device)
+    nnz = _I64(0)
+    st = _stream(stream)
+    args = (_ptr(xy), _ptr(h), _ptr(s), N, Lx, Ly, mask, m, m_wall, n_wall, _ptr(wall_column),
+            _ptr(wall_normal), float(h1d_over_s), _ptr(row_ptr))
+    _check(lib.labfm_build_wall_operator(*args, None, 0, ctypes.byref(nnz), None, None, None, None, st))
+    n = nnz.value
+    col = torch.empty(max(n, 1), dtype=torch.int32, device=xy.device)
+    w = torch.empty((6, max(n, 1)), dtype=torch.float64, device=xy.device)
+    kappa = torch.empty(N, dtype=torch.float64, device=xy.device)
+    status = torch.empty(N, dtype=torch.int32, device=xy.device)
+    nf = _I64(0)
+    _check(lib.labfm_build_wall_operator(*args, _ptr(col), col.numel(), ctypes.byref(nnz), _ptr(w),
+                                         _ptr(kappa), _ptr(status), ctypes.byref(nf) if check else None, st))
+    return {"row_ptr": row_ptr, "col": col[:n], "w": w[:, :n], "kappa": kappa, "status": status,
+            "n_failed": nf.value if check else None}
 
 
 def modal_response(xy, s, Lx, Ly, row_ptr, col, w, nk=16, periodic=(True, True), stream=None):
@@ -329,10 +367,16 @@ class Plan:
         F32 stage kernel with 16 or 32 lanes per node (0 = off)."""
         _check(lib.labfm_plan_set_staging(self._h, int(stages), _stream(stream)))
 
-    def set_wait_limit(self, limit_ns: int) -> None:
-        """labfm_plan_set_wait_limit: limit of the staged kernel's bounded waits (ns;
-        0 = one non-blocking test, which makes the waits run out)."""
-        _check(lib.labfm_plan_set_wait_limit(self._h, int(limit_ns)))
+    def set_walls(self, wall_nodes: torch.Tensor, wall_normal: torch.Tensor, stream=None) -> None:
+        """labfm_plan_set_walls: no-slip walls (Section 7.1) at the given nodes (int32,
+        n_wall) with inward unit normals (float64, (n_wall, 2)); an empty wall_nodes
+        removes them."""
+        n = wall_nodes.numel()
+        if wall_nodes.dtype != torch.int32 or (n and (wall_normal.dtype != torch.float64
+                                                      or tuple(wall_normal.shape) != (n, 2))):
+            raise ValueError("wall_nodes int32 (n_wall,), wall_normal float64 (n_wall, 2)")
+        _check(lib.labfm_plan_set_walls(self._h, n, _ptr(wall_nodes) if n else None,
+                                        _ptr(wall_normal.contiguous()) if n else None, _stream(stream)))
 
     def set_wait_limit(self, limit_ns: int) -> None:
         """labfm_plan_set_wait_limit: limit of the staged kernel's bounded waits (ns;
@@ -372,6 +416,11 @@ class Plan:
     def set_launch(self, group: int, block: int) -> None:
         _check(lib.labfm_plan_set_launch(self._h, group, block))
 
+    def set_filter_launch(self, group: int = 0, persistent: bool = False) -> None:
+        """labfm_plan_set_filter_launch: the filter's lanes per node (0 = the plan's
+        group) and its persistent grid-stride grid."""
+        _check(lib.labfm_plan_set_filter_launch(self._h, int(group), 1 if persistent else 0))
+
     def autotune(self, fields: torch.Tensor, phys: Phys, reps: int = 5, stream=None):
         _state(self, fields, "fields")
         out = torch.empty_like(fields)
@@ -391,12 +440,13 @@ class Plan:
 
     def tune_step(self, Q: torch.Tensor, phys: Phys, dt: float, steps: int = 3,
                   groups=(2, 4, 8, 16), staged=((16, 3), (32, 3), (32, 4)),
-                  prefetch=(0, 2)) -> dict:
+                  prefetch=(0, 2), filter_groups=(2, 4, 8, 16)) -> dict:
         """Autotune the time step itself: time `steps` RK steps (CUDA events) for every
         lanes-per-node group with the plain and the persistent stage kernel (F32: with
         each L2 prefetch distance), and (F32) for the staged kernel at the given (lanes
-        per node, ring slots), keep the fastest.  Q is not modified.  Returns the chosen
-        configuration."""
+        per node, ring slots), keep the fastest; then, with that stage kernel, time the
+        filter's own lanes per node with its plain and persistent grids and keep the
+        fastest.  Q is not modified.  Returns the chosen configuration."""
         _state(self, Q)
         info = self.info()
         block = info["block"]
@@ -404,12 +454,8 @@ class Plan:
         configs = [(g, p, 0, pf) for pf in pfs for p in (False, True) for g in groups]
         if self.dtype == torch.float32:
             configs += [(g, False, k, 0) for g, k in staged]
-        best = None
-        for g, persistent, stages, pf in configs:
-            self.set_persistent(persistent)
-            self.set_staging(stages)
-            self.set_prefetch(pf)
-            self.set_launch(g, block)
+
+        def timed():
             work = workspace(self)
             Qs = Q.clone()
             rk_step(self, Qs, dt, 1, phys, work=work)
@@ -419,7 +465,16 @@ class Plan:
             rk_step(self, Qs, dt, steps, phys, work=work)
             b.record()
             torch.cuda.synchronize()
-            ms = a.elapsed_time(b) / steps
+            return a.elapsed_time(b) / steps
+
+        self.set_filter_launch(0, False)
+        best = None
+        for g, persistent, stages, pf in configs:
+            self.set_persistent(persistent)
+            self.set_staging(stages)
+            self.set_prefetch(pf)
+            self.set_launch(g, block)
+            ms = timed()
             if best is None or ms < best[0]:
                 best = (ms, g, persistent, stages, pf)
         _, g, persistent, stages, pf = best
@@ -427,10 +482,19 @@ class Plan:
         self.set_staging(stages)
         self.set_prefetch(pf)
         self.set_launch(g, block)
+        fbest = (best[0], 0, False)
+        for fg in filter_groups:
+            for fp in (False, True):
+                self.set_filter_launch(fg, fp)
+                ms = timed()
+                if ms < fbest[0]:
+                    fbest = (ms, fg, fp)
+        self.set_filter_launch(fbest[1], fbest[2])
         if self.device_status() != 0:
             raise LabfmError(7, "a staged stage kernel's bounded wait ran out while tuning")
         return {"group": g, "block": block, "persistent": persistent, "staging": stages,
-                "prefetch": pf, "ms_per_step": best[0]}
+                "prefetch": pf, "filter_group": fbest[1] or g, "filter_persistent": fbest[2],
+                "ms_per_step": fbest[0]}
 
     def workspace_bytes(self) -> int:
         return int(lib.labfm_rk_workspace_bytes(self._h))

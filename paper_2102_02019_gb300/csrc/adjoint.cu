@@ -10,8 +10,9 @@
 //
 // RHS adjoint at state X with cotangent m (two passes):
 //   pass A (node i): forward derivatives d_i, then the derivative adjoints
-//     g_i = (dR_i/dd_i)^T m_i (12 values, scaled by s_i^-l in F32 to match the
-//     nondimensional weights) and the own-value adjoints o_i = (dR_i/dX_i)^T m_i;
+//     g_i = (dR_i/dd_i)^T m_i (twelve values, carried as eight: see G8; scaled
+//     by s_i^-l in F32 to match the nondimensional weights) and the own-value
+//     adjoints o_i = (dR_i/dX_i)^T m_i;
 //   pass B (node k): Xbar_k = o_k + sum over operators of (L^T g)_k.
 // One RK step backwards (low-storage form of the reverse sweep):
 //   Lambda = Fil^T lambda;  Fbar_4 = dt b_4 Lambda
@@ -36,24 +37,30 @@
 namespace labfm {
 namespace {
 
-// Twelve derivative adjoints of one node, packed for three 16-byte gathers (F32):
-// [g_ax, g_ay, g_ux, g_uy] [g_uxx, g_uxy, g_uyy, g_vx] [g_vy, g_vxx, g_vxy, g_vyy]
-template <typename T> struct G12;
-template <> struct G12<float> { float4 q[3]; };
-template <> struct G12<double> { double2 q[6]; };
+// The twelve derivative adjoints of one node in eight values, packed for two
+// 16-byte gathers (F32):
+//   [g_ax, g_ay, g_ux, g_uy] [g_vx, g_vy, A, B].
+// The second derivatives enter eq. icns only through
+// nu (4/3 u_xx + u_yy + 1/3 v_xy) in R_u and nu (4/3 v_yy + v_xx + 1/3 u_xy) in
+// R_v, so their six adjoints are fixed multiples of A = nu m_u and B = nu m_v:
+//   g_uxx = 4/3 A, g_uyy = A, g_vxy = 1/3 A, g_vxx = B, g_vyy = 4/3 B, g_uxy = 1/3 B.
+// The transposed records carry the matching operator combinations (see
+// k_write_transposed), so that pass B gathers 32 bytes per stencil entry, not 48.
+template <typename T> struct G8;
+template <> struct G8<float> { float4 q[2]; };
+template <> struct G8<double> { double2 q[4]; };
 
-__device__ __forceinline__ void g12_store(G12<float>* p, int64_t i, const float (&g)[12]) {
+__device__ __forceinline__ void g8_store(G8<float>* p, int64_t i, const float (&g)[8]) {
     p[i].q[0] = make_float4(g[0], g[1], g[2], g[3]);
     p[i].q[1] = make_float4(g[4], g[5], g[6], g[7]);
-    p[i].q[2] = make_float4(g[8], g[9], g[10], g[11]);
 }
-__device__ __forceinline__ void g12_store(G12<double>* p, int64_t i, const double (&g)[12]) {
+__device__ __forceinline__ void g8_store(G8<double>* p, int64_t i, const double (&g)[8]) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) p[i].q[k] = make_double2(g[2 * k], g[2 * k + 1]);
+    for (int k = 0; k < 4; ++k) p[i].q[k] = make_double2(g[2 * k], g[2 * k + 1]);
 }
-__device__ __forceinline__ void g12_load(const G12<float>* p, int i, float (&g)[12]) {
+__device__ __forceinline__ void g8_load(const G8<float>* p, int i, float (&g)[8]) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 2; ++k) {
         const float4 t = __ldg(&p[i].q[k]);
         g[4 * k] = t.x;
         g[4 * k + 1] = t.y;
@@ -61,23 +68,23 @@ __device__ __forceinline__ void g12_load(const G12<float>* p, int i, float (&g)[
         g[4 * k + 3] = t.w;
     }
 }
-__device__ __forceinline__ void g12_load(const G12<double>* p, int i, double (&g)[12]) {
+__device__ __forceinline__ void g8_load(const G8<double>* p, int i, double (&g)[8]) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) {
+    for (int k = 0; k < 4; ++k) {
         const double2 t = __ldg(&p[i].q[k]);
         g[2 * k] = t.x;
         g[2 * k + 1] = t.y;
     }
 }
 
-// Position of each operator's adjoint in G12 order, by field: a uses x, y
-// (0, 1); u and v use x, y, xx, xy, yy (2..6 and 7..11).
-constexpr int kGa = 0, kGu = 2, kGv = 7;
+// Slots of G8.
+constexpr int kGax = 0, kGay = 1, kGux = 2, kGuy = 3, kGvx = 4, kGvy = 5, kGA = 6, kGB = 7;
 
 template <typename T>
 PlanView<T> tview(const labfm_plan* p) {
     return PlanView<T>{p->N, p->tnnz_pad, p->trow_ptr, nullptr, static_cast<const T*>(p->tw),
-                       static_cast<const T*>(p->twf), static_cast<const T*>(p->inv_s), p->dt_node, 0};
+                       static_cast<const T*>(p->twf), static_cast<const T*>(p->inv_s), p->dt_node, 0,
+                       nullptr, nullptr};
 }
 
 // ---------------------------------------------------------------- pass A
@@ -88,28 +95,23 @@ PlanView<T> tview(const labfm_plan* p) {
 template <typename T, bool SCALED>
 __device__ __forceinline__ void node_adjoints(const PlanView<T>& P, int i, T a, T u, T v,
                                               const T (&c)[8], const Packed<T>* M,
-                                              G12<T>* __restrict__ gout, Packed<T>* __restrict__ oout,
+                                              G8<T>* __restrict__ gout, Packed<T>* __restrict__ oout,
                                               const Phys<T>& ph) {
     const T is = SCALED ? P.inv_s[i] : T(1);
     const T s1 = SCALED ? is : T(1), s2 = SCALED ? is * is : T(1);
     T ma, mu, mv;
     unpack(M, i, ma, mu, mv);
     const T nu = ph.mu * exp_neg(a);
-    const T third = T(1) / T(3), four_thirds = T(4) / T(3);
-    T g[12];
-    g[0] = (-u * ma - ph.c2 * mu) * s1;  // a_x
-    g[1] = (-v * ma - ph.c2 * mv) * s1;  // a_y
-    g[2] = (-ma - u * mu) * s1;          // u_x
-    g[3] = (-v * mu) * s1;               // u_y
-    g[4] = (nu * four_thirds * mu) * s2; // u_xx
-    g[5] = (nu * third * mv) * s2;       // u_xy
-    g[6] = (nu * mu) * s2;               // u_yy
-    g[7] = (-u * mv) * s1;               // v_x
-    g[8] = (-ma - v * mv) * s1;          // v_y
-    g[9] = (nu * mv) * s2;               // v_xx
-    g[10] = (nu * third * mu) * s2;      // v_xy
-    g[11] = (nu * four_thirds * mv) * s2;// v_yy
-    g12_store(gout, i, g);
+    T g[8];
+    g[kGax] = (-u * ma - ph.c2 * mu) * s1;
+    g[kGay] = (-v * ma - ph.c2 * mv) * s1;
+    g[kGux] = (-ma - u * mu) * s1;
+    g[kGuy] = (-v * mu) * s1;
+    g[kGvx] = (-u * mv) * s1;
+    g[kGvy] = (-ma - v * mv) * s1;
+    g[kGA] = (nu * mu) * s2;
+    g[kGB] = (nu * mv) * s2;
+    g8_store(gout, i, g);
     // c = (a_x, a_y, u_x, u_y, v_x, v_y, 4/3 u_xx + u_yy + 1/3 v_xy, 4/3 v_yy + v_xx + 1/3 u_xy)
     const T oa = -nu * (c[6] * mu + c[7] * mv);
     const T ou = -(c[0] * ma + c[2] * mu + c[4] * mv);
@@ -120,7 +122,7 @@ __device__ __forceinline__ void node_adjoints(const PlanView<T>& P, int i, T a, 
 // Pass A with the derivatives gathered at X (the single right-hand-side adjoint).
 template <typename T, int G, bool KAHAN, bool SCALED>
 __global__ void k_adj_pointwise(PlanView<T> P, const Packed<T>* X, const Packed<T>* M,
-                                G12<T>* __restrict__ gout, Packed<T>* __restrict__ oout, Phys<T> ph) {
+                                G8<T>* __restrict__ gout, Packed<T>* __restrict__ oout, Phys<T> ph) {
     const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     const int64_t node = gt / G;
     const int gl = int(gt % G);
@@ -140,7 +142,7 @@ __global__ void k_adj_pointwise(PlanView<T> P, const Packed<T>* X, const Packed<
 // per node, no gather): the reverse sweep of labfm_rk_step_adjoint(_recorded).
 template <typename T, bool SCALED>
 __global__ void k_adj_pointwise_rec(PlanView<T> P, const Packed<T>* X, const D8<T>* __restrict__ D,
-                                    const Packed<T>* M, G12<T>* __restrict__ gout,
+                                    const Packed<T>* M, G8<T>* __restrict__ gout,
                                     Packed<T>* __restrict__ oout, Phys<T> ph) {
     for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < P.N;
          k += int64_t(gridDim.x) * blockDim.x) {
@@ -155,10 +157,16 @@ __global__ void k_adj_pointwise_rec(PlanView<T> P, const Packed<T>* X, const D8<
 
 // ---------------------------------------------------------------- pass B
 
+// The transposed records hold, per entry (i -> k), c_0 = w^x_ik, c_1 = w^y_ik,
+// c_2 = 4/3 w^xx_ik + w^yy_ik, c_3 = w^xx_ik + 4/3 w^yy_ik, c_4 = 1/3 w^xy_ik
+// (in the slots of the forward x, y, xx, xy, yy weights), and rsum the same
+// combinations of node k's forward row sums, so that with G8:
+//   sum_d w^d_ik g_{u,d,i} = c_0 g_ux + c_1 g_uy + c_2 A + c_4 B,
+//   sum_d w^d_ik g_{v,d,i} = c_0 g_vx + c_1 g_vy + c_3 B + c_4 A.
 // MODE 0: out = Xbar.  MODE 1 (RK reverse sweep): Lam += Xbar, and when
 // Fnext is not null, Fnext = dt_i (bprev Lam + cprev Xbar).
 template <typename T, int G, int MODE>
-__global__ void k_adj_transpose(PlanView<T> PT, const G12<T>* gin, const Packed<T>* oin,
+__global__ void k_adj_transpose(PlanView<T> PT, const G8<T>* gin, const Packed<T>* oin,
                                 const T* __restrict__ rsum, Packed<T>* out, Packed<T>* Lam,
                                 Packed<T>* Fnext, double dt, double bprev, double cprev) {
     const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
@@ -171,20 +179,22 @@ __global__ void k_adj_transpose(PlanView<T> PT, const G12<T>* gin, const Packed<
         const int e1 = PT.row_ptr[k + 1];
         for (int e = e0 + 4 * gl; e < e1; e += 4 * G) {
             int ci[4];
-            T wx[4], wy[4], wxx[4], wxy[4], wyy[4];
-            load_rhs_chunk(PT, e, ci, wx, wy, wxx, wxy, wyy, 0);
+            T c0[4], c1[4], c2[4], c3[4], c4[4];
+            load_rhs_chunk(PT, e, ci, c0, c1, c2, c3, c4, 0);
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                T g[12];
-                g12_load(gin, ci[q], g);
-                const T w5[5] = {wx[q], wy[q], wxx[q], wxy[q], wyy[q]};
-                sa = fma(w5[0], g[kGa], sa);
-                sa = fma(w5[1], g[kGa + 1], sa);
-#pragma unroll
-                for (int o = 0; o < 5; ++o) {
-                    su = fma(w5[o], g[kGu + o], su);
-                    sv = fma(w5[o], g[kGv + o], sv);
-                }
+                T g[8];
+                g8_load(gin, ci[q], g);
+                sa = fma(c0[q], g[kGax], sa);
+                sa = fma(c1[q], g[kGay], sa);
+                su = fma(c0[q], g[kGux], su);
+                su = fma(c1[q], g[kGuy], su);
+                su = fma(c2[q], g[kGA], su);
+                su = fma(c4[q], g[kGB], su);
+                sv = fma(c0[q], g[kGvx], sv);
+                sv = fma(c1[q], g[kGvy], sv);
+                sv = fma(c3[q], g[kGB], sv);
+                sv = fma(c4[q], g[kGA], sv);
             }
         }
     }
@@ -192,20 +202,16 @@ __global__ void k_adj_transpose(PlanView<T> PT, const G12<T>* gin, const Packed<
     su = group_sum<G>(su);
     sv = group_sum<G>(sv);
     if (k < 0 || gl != 0) return;
-    T g[12];
-    g12_load(gin, k, g);
+    T g[8];
+    g8_load(gin, k, g);
     T r[5];
 #pragma unroll
     for (int o = 0; o < 5; ++o) r[o] = rsum[int64_t(o) * PT.N + k];
     T oa, ou, ov;
     unpack(oin, k, oa, ou, ov);
-    T xa = oa + sa - (r[0] * g[kGa] + r[1] * g[kGa + 1]);
-    T xu = ou + su, xv = ov + sv;
-#pragma unroll
-    for (int o = 0; o < 5; ++o) {
-        xu -= r[o] * g[kGu + o];
-        xv -= r[o] * g[kGv + o];
-    }
+    const T xa = oa + sa - (r[0] * g[kGax] + r[1] * g[kGay]);
+    const T xu = ou + su - (r[0] * g[kGux] + r[1] * g[kGuy] + r[2] * g[kGA] + r[4] * g[kGB]);
+    const T xv = ov + sv - (r[0] * g[kGvx] + r[1] * g[kGvy] + r[3] * g[kGB] + r[4] * g[kGA]);
     if (MODE == 0) {
         store(out, k, xa, xu, xv);
         return;
@@ -271,6 +277,22 @@ __global__ void k_filter_adjoint(PlanView<T> PT, const Packed<T>* lam, const T* 
 
 // ---------------------------------------------------------------- transposed operator build
 
+// The combinations of the five RHS weights w (x, y, xx, xy, yy) that pass B
+// applies to the G8 adjoints, formed in FP64 and rounded once to T.
+template <typename T>
+__device__ __forceinline__ void adjoint_combinations(const double (&w)[5], T (&c)[5]) {
+    c[0] = T(w[0]);
+    c[1] = T(w[1]);
+    c[2] = T(4.0 / 3.0 * w[2] + w[4]);
+    c[3] = T(w[2] + 4.0 / 3.0 * w[4]);
+    c[4] = T(w[3] / 3.0);
+}
+template <typename T>
+__device__ __forceinline__ void adjoint_combinations(const double (&w)[6], T (&c)[5]) {
+    const double v[5] = {w[0], w[1], w[2], w[3], w[4]};
+    adjoint_combinations(v, c);
+}
+
 // Warp per forward row i: count the in-degree of every column k (pads, which
 // point at the row itself, are skipped).
 template <typename T>
@@ -312,8 +334,10 @@ __global__ void k_fill_transposed(PlanView<T> P, const int32_t* __restrict__ tro
 }
 
 // Warp per transposed row k: order the entries by source row i (the fill order
-// is nondeterministic) and write the records: column i, the forward weights of
-// entry (i -> k), and the filter weight; pads point at k with weight 0.
+// is nondeterministic) and write the records: column i, the combinations of
+// the forward weights of entry (i -> k) that pass B applies (k_adj_transpose:
+// w^x, w^y, 4/3 w^xx + w^yy, w^xx + 4/3 w^yy, 1/3 w^xy, formed in FP64 and
+// rounded once), and the filter weight; pads point at k with weight 0.
 template <typename T>
 __global__ void k_write_transposed(PlanView<T> P, int64_t N, const int32_t* __restrict__ trow,
                                    const int32_t* __restrict__ cnt, const int32_t* __restrict__ ti,
@@ -334,8 +358,10 @@ __global__ void k_write_transposed(PlanView<T> P, int64_t N, const int32_t* __re
                 for (int r = 0; r < len; ++r) rank += ti[t0 + r] < src_i;
                 const int e = te[t0 + q];
                 const char* rb = reinterpret_cast<const char*>(P.w);
+                double f[5];
 #pragma unroll
-                for (int d = 0; d < 5; ++d) v[d] = *reinterpret_cast<const T*>(rb + Rec<T>::w_e(e, d));
+                for (int d = 0; d < 5; ++d) f[d] = double(*reinterpret_cast<const T*>(rb + Rec<T>::w_e(e, d)));
+                adjoint_combinations(f, v);
                 vf = *reinterpret_cast<const T*>(reinterpret_cast<const char*>(P.wf) + Rec<T>::fw_e(e));
             }
             const int64_t dst = int64_t(t0) + rank;
@@ -350,7 +376,8 @@ __global__ void k_write_transposed(PlanView<T> P, int64_t N, const int32_t* __re
     }
 }
 
-// Warp per forward row i: sums of its RHS weights and filter weights (pads add 0).
+// Warp per forward row i: sums of its RHS weights (stored as the combinations
+// of adjoint_combinations) and of its filter weights (pads add 0).
 template <typename T>
 __global__ void k_row_sums(PlanView<T> P, T* __restrict__ rsum) {
     const int lane = threadIdx.x & 31;
@@ -366,10 +393,15 @@ __global__ void k_row_sums(PlanView<T> P, T* __restrict__ rsum) {
         }
 #pragma unroll
         for (int d = 0; d < 6; ++d) {
-            double v = acc[d];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) rsum[int64_t(d) * P.N + i] = T(v);
+            for (int o = 16; o > 0; o >>= 1) acc[d] += __shfl_xor_sync(0xffffffffu, acc[d], o);
+        }
+        T comb[5];
+        adjoint_combinations(acc, comb);
+        if (lane == 0) {
+#pragma unroll
+            for (int d = 0; d < 5; ++d) rsum[int64_t(d) * P.N + i] = comb[d];
+            rsum[int64_t(5) * P.N + i] = T(acc[5]);
         }
     }
 }
@@ -445,7 +477,7 @@ struct AdjWork {
     Packed<T>* Lam;
     Packed<T>* Fb;
     Packed<T>* Ob;
-    G12<T>* g;
+    G8<T>* g;
     D8<T>* D;  // 4 x N: the stages' derivative combinations (recomputing sweep)
 };
 
@@ -458,13 +490,13 @@ AdjWork<T> split_work(const labfm_plan* p, void* work) {
     w.Lam = base + 5 * p->N;
     w.Fb = base + 6 * p->N;
     w.Ob = base + 7 * p->N;
-    w.g = reinterpret_cast<G12<T>*>(base + 8 * p->N);
+    w.g = reinterpret_cast<G8<T>*>(base + 8 * p->N);
     w.D = reinterpret_cast<D8<T>*>(w.g + p->N);
     return w;
 }
 
 template <typename T, int G>
-int pass_a_g(const labfm_plan* p, const Packed<T>* X, const Packed<T>* M, G12<T>* g, Packed<T>* o,
+int pass_a_g(const labfm_plan* p, const Packed<T>* X, const Packed<T>* M, G8<T>* g, Packed<T>* o,
              const Phys<T>& ph, cudaStream_t st) {
     constexpr bool F = std::is_same<T, float>::value;
     const int grid = int((p->N * G + p->block - 1) / p->block);
@@ -474,7 +506,7 @@ int pass_a_g(const labfm_plan* p, const Packed<T>* X, const Packed<T>* M, G12<T>
 }
 
 template <typename T>
-int pass_a_rec(const labfm_plan* p, const Packed<T>* X, const D8<T>* D, const Packed<T>* M, G12<T>* g,
+int pass_a_rec(const labfm_plan* p, const Packed<T>* X, const D8<T>* D, const Packed<T>* M, G8<T>* g,
                Packed<T>* o, const Phys<T>& ph, cudaStream_t st) {
     constexpr bool F = std::is_same<T, float>::value;
     const int grid = int(std::min<int64_t>((p->N + 255) / 256, 152 * 16));
@@ -484,7 +516,7 @@ int pass_a_rec(const labfm_plan* p, const Packed<T>* X, const D8<T>* D, const Pa
 }
 
 template <typename T, int G>
-int pass_b_g(const labfm_plan* p, int mode, const G12<T>* g, const Packed<T>* o, Packed<T>* out,
+int pass_b_g(const labfm_plan* p, int mode, const G8<T>* g, const Packed<T>* o, Packed<T>* out,
              Packed<T>* Lam, Packed<T>* Fnext, double dt, double bprev, double cprev,
              cudaStream_t st) {
     const int grid = int((p->N * G + p->block - 1) / p->block);
@@ -520,13 +552,13 @@ int filt_adj_g(const labfm_plan* p, const Packed<T>* lam, Packed<T>* Lam, Packed
     return set_error(LABFM_EINVAL, "unsupported group size")
 
 template <typename T>
-int pass_a(const labfm_plan* p, const Packed<T>* X, const Packed<T>* M, G12<T>* g, Packed<T>* o,
+int pass_a(const labfm_plan* p, const Packed<T>* X, const Packed<T>* M, G8<T>* g, Packed<T>* o,
            const Phys<T>& ph, cudaStream_t st) {
     LABFM_G_DISPATCH((pass_a_g<T, G>(p, X, M, g, o, ph, st)));
 }
 
 template <typename T>
-int pass_b(const labfm_plan* p, int mode, const G12<T>* g, const Packed<T>* o, Packed<T>* out,
+int pass_b(const labfm_plan* p, int mode, const G8<T>* g, const Packed<T>* o, Packed<T>* out,
            Packed<T>* Lam, Packed<T>* Fnext, double dt, double bprev, double cprev, cudaStream_t st) {
     LABFM_G_DISPATCH((pass_b_g<T, G>(p, mode, g, o, out, Lam, Fnext, dt, bprev, cprev, st)));
 }
@@ -614,12 +646,13 @@ int filter_adjoint_t(const labfm_plan* p, const void* lam_in, void* lam_out, voi
 
 size_t adjoint_work_bytes(const labfm_plan* p) {
     if (p->dtype == LABFM_F32)
-        return size_t(p->N) * (8 * sizeof(Packed<float>) + sizeof(G12<float>) + 4 * sizeof(D8<float>));
-    return size_t(p->N) * (8 * sizeof(Packed<double>) + sizeof(G12<double>) + 4 * sizeof(D8<double>));
+        return size_t(p->N) * (8 * sizeof(Packed<float>) + sizeof(G8<float>) + 4 * sizeof(D8<float>));
+    return size_t(p->N) * (8 * sizeof(Packed<double>) + sizeof(G8<double>) + 4 * sizeof(D8<double>));
 }
 
 int check_adjoint(const labfm_plan* p, void* work, size_t work_bytes) {
     if (!p || !p->row_ptr) return set_error(LABFM_EINVAL, "null or empty plan");
+    if (p->wall_slot) return set_error(LABFM_EINVAL, "the adjoint of a plan with walls is not implemented");
     if (!p->trow_ptr) return set_error(LABFM_EINVAL, "call labfm_plan_enable_adjoint first");
     if (!work) return set_error(LABFM_EINVAL, "null work buffer");
     if (work_bytes < adjoint_work_bytes(p))
@@ -681,6 +714,7 @@ extern "C" int labfm_rk_step_record(const labfm_plan* p, void* Q, void* states, 
                                     void* stream) {
     LABFM_NVTX("labfm_rk_step_record");
     if (!p || !p->row_ptr) return set_error(LABFM_EINVAL, "null or empty plan");
+    if (p->wall_slot) return set_error(LABFM_EINVAL, "the recording step of a plan with walls is not implemented");
     if (!Q || !states || !work || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
     if (states_bytes < labfm_stage_states_bytes(p))
         return set_error(LABFM_EINVAL, "states buffer smaller than labfm_stage_states_bytes");

@@ -87,6 +87,11 @@ void free_plan_memory(labfm_plan* p) {
     cudaFree(p->twf);
     cudaFree(p->rsum);
     cudaFree(p->dev_status);
+    cudaFree(p->wall_slot);
+    cudaFree(p->wall_n);
+    p->wall_slot = nullptr;
+    p->wall_n = nullptr;
+    p->n_wall = 0;
     p->dev_status = nullptr;
     p->trow_ptr = nullptr;
     p->tw = p->twf = p->rsum = nullptr;
@@ -279,6 +284,8 @@ extern "C" int labfm_plan_get_info(const labfm_plan* p, labfm_plan_info* info) {
     info->device_bytes = p->device_bytes;
     info->prefetch = p->prefetch;
     info->stages = p->stages;
+    info->filter_group = p->filter_group ? p->filter_group : p->group;
+    info->filter_persistent = p->filter_persistent ? 1 : 0;
     return LABFM_OK;
 }
 
@@ -290,6 +297,17 @@ extern "C" int labfm_plan_set_launch(labfm_plan* p, int group, int block) {
     p->group = group;
     p->block = block;
     if (p->persistent) p->persist_grid = persistent_grid(p);
+    if (p->filter_persistent) p->filter_grid = filter_persistent_grid(p);
+    return LABFM_OK;
+}
+
+extern "C" int labfm_plan_set_filter_launch(labfm_plan* p, int group, int persistent) {
+    if (int rc = check_plan(p)) return rc;
+    if (group != 0 && !launch_shape_supported(group, p->block))
+        return set_error(LABFM_EINVAL, "unsupported filter lanes per node " + std::to_string(group));
+    p->filter_group = group;
+    p->filter_persistent = persistent != 0;
+    p->filter_grid = p->filter_persistent ? filter_persistent_grid(p) : 0;
     return LABFM_OK;
 }
 
@@ -341,6 +359,7 @@ extern "C" int labfm_plan_autotune(labfm_plan* p, const void* fields, void* scra
     p->group = bg;
     p->block = bb;
     if (p->persistent) p->persist_grid = persistent_grid(p);
+    if (p->filter_persistent) p->filter_grid = filter_persistent_grid(p);
     if (group_out) *group_out = bg;
     if (block_out) *block_out = bb;
     return LABFM_OK;

@@ -297,6 +297,8 @@ struct PlanView {
     const T* inv_s;
     const double* dt_node;  // per-node time step, or null for a uniform dt
     int pf;                 // L2 prefetch distance of the F32 record stream, in iterations (0: off)
+    const int32_t* wall_slot;  // per node: wall slot, -1 in the fluid (null: no walls)
+    const T* wall_n;           // per wall slot: inward unit normal (n_x, n_y)
 };
 
 // Operator loads of one 4-entry chunk starting at entry e (a multiple of 4).
@@ -372,7 +374,7 @@ template <typename T>
 PlanView<T> view(const labfm_plan* p) {
     return PlanView<T>{p->N,        p->nnz_pad,  p->row_ptr, p->col, static_cast<const T*>(p->w),
                        static_cast<const T*>(p->wf), static_cast<const T*>(p->inv_s), p->dt_node,
-                       p->prefetch};
+                       p->prefetch, p->wall_slot, static_cast<const T*>(p->wall_n)};
 }
 
 // Chunk loaders for the gathers: from the plan's record stream in global memory,
@@ -610,6 +612,53 @@ template <typename T>
 struct Phys {
     T c2, mu, gx, gy;
 };
+
+__device__ __forceinline__ float exp_pos(float a) { return expf(a); }
+__device__ __forceinline__ double exp_pos(double a) { return exp(a); }
+
+// Right-hand side at a no-slip wall node (Section 7.1): u = 0 is held (R_u = R_v =
+// 0) and ln rho follows eq. lodilnro with u_xi = 0,
+//   R_a = -(L4 + L1) / (rho c^2) - d u_eta / d eta,
+//   L1 = (u_xi - c)/2 (dp/dxi - rho c du_xi/dxi) (eq. Ldef), dp/dxi = c^2 rho d ln rho/dxi,
+//   L4 = L1 + rho c g.n (the incoming wave of the wall; the paper prints a factor
+//   2 on rho c g.n, with which eq. lodiu would not hold u_xi at zero: factor 1 is
+//   the reading taken),
+// with xi along the inward normal n and eta along t = (-n_y, n_x); the derivatives
+// are those of the wall rows (one-sided differences along n, 1D LABFM along t).
+template <typename T, bool SCALED>
+__device__ __forceinline__ void wall_rhs(const T (&d)[12], T a, T inv_s, T c2, T gx, T gy, T nx, T ny,
+                                         T& Ra, T& Ru, T& Rv) {
+    const T s1 = SCALED ? inv_s : T(1);
+    const T ax = d[0] * s1, ay = d[1] * s1;
+    const T ux = d[2] * s1, uy = d[3] * s1, vx = d[7] * s1, vy = d[8] * s1;
+    const T tx = -ny, ty = nx;
+    const T a_xi = ax * nx + ay * ny;
+    const T du_xi = nx * (ux * nx + uy * ny) + ny * (vx * nx + vy * ny);
+    const T du_eta = tx * (ux * tx + uy * ty) + ty * (vx * tx + vy * ty);
+    const T rho = exp_pos(a);
+    const T c = sqrt(c2);
+    const T dp = c2 * rho * a_xi;
+    const T L1 = T(0.5) * (T(0) - c) * (dp - rho * c * du_xi);
+    const T L4 = L1 + rho * c * (nx * gx + ny * gy);
+    Ra = -(L4 + L1) / (rho * c2) - du_eta;
+    Ru = T(0);
+    Rv = T(0);
+}
+
+// eq. icns, or the wall's right-hand side at a wall node of a plan with walls.
+template <typename T, bool SCALED, bool WALL>
+__device__ __forceinline__ void node_rhs(const PlanView<T>& P, int i, const T (&d)[12], T a, T u, T v,
+                                         T inv_s, const Phys<T>& ph, T& Ra, T& Ru, T& Rv) {
+    if (WALL) {
+        const int slot = P.wall_slot[i];
+        if (slot >= 0) {
+            wall_rhs<T, SCALED>(d, a, inv_s, ph.c2, ph.gx, ph.gy, P.wall_n[2 * slot], P.wall_n[2 * slot + 1],
+                                Ra, Ru, Rv);
+            return;
+        }
+    }
+    pointwise_rhs<T, SCALED>(d, a, u, v, inv_s, ph.c2, ph.mu, ph.gx, ph.gy, Ra, Ru, Rv);
+}
 
 // The eight combinations of a node's derivatives through which the transpose of
 // eq. icns with respect to the node's own state depends on them (physical units):

@@ -87,6 +87,11 @@ struct labfm_plan {
     bool persistent = false;     // stage kernel takes node tiles from a work queue
     int prefetch = 0;            // L2 prefetch distance of the F32 record stream (labfm_plan_set_prefetch)
     int persist_grid = 0;
+    // filter launch (labfm_plan_set_filter_launch): lanes per node (0 = the plan's
+    // group) and a persistent grid-stride grid of filter_grid blocks
+    int filter_group = 0;
+    bool filter_persistent = false;
+    int filter_grid = 0;
     // F32 stage kernel with the operator staged through shared memory
     // (labfm_plan_set_staging): `stages` ring slots per CTA; for 16 and 32 lanes
     // per node ([0], [1]) the bytes of the largest round and the grid (0 = the
@@ -104,6 +109,11 @@ struct labfm_plan {
     void* tw = nullptr;           // transposed RHS records
     void* twf = nullptr;          // transposed filter records
     void* rsum = nullptr;         // 6 x N (dtype): sum_j w~^d_kj for the 5 RHS operators, sum_j wf_kj
+    // walls (labfm_plan_set_walls): per node the wall slot (-1 in the fluid) and
+    // per slot the inward unit normal (dtype, 2 values)
+    int32_t* wall_slot = nullptr;
+    void* wall_n = nullptr;
+    int64_t n_wall = 0;
     // launch timing (labfm_plan_set_profiling): event pairs around launches
     bool profiling = false;
     cudaEvent_t* prof_ev = nullptr;  // 2 * prof_cap events
@@ -145,6 +155,9 @@ enum ProfKind { kProfStage = 0, kProfFilter = 1, kProfStages4 = 2, kProfRecStage
 int prof_begin(labfm_plan* p, int kind, cudaStream_t st);
 void prof_end(labfm_plan* p, int idx, cudaStream_t st);
 
+// Walls of a plan (walls.cu): wall slots and normals; n_wall = 0 removes them.
+int set_walls(labfm_plan* p, int64_t n_wall, const int32_t* nodes, const double* normal, cudaStream_t st);
+
 // Plan packing (step.cu): concatenates the instances block-diagonally.
 int pack_plan(labfm_plan* p, const PlanInput* in, int n_inst, cudaStream_t st);
 
@@ -178,6 +191,7 @@ size_t d8_bytes(const labfm_plan* p);
 int launch_stable_dt_instances(const labfm_plan* p, const void* fields, const double* s, double c,
                                double mu, double* dt_inst, cudaStream_t st);
 int persistent_grid(const labfm_plan* p);
+int filter_persistent_grid(const labfm_plan* p);
 // Configure the staged F32 stage kernel for `stages` ring slots (0 = off); synchronises.
 int configure_staging(labfm_plan* p, int stages, cudaStream_t st);
 // Bytes per padded stencil entry of the plan's RHS (filter = false) or filter

@@ -136,16 +136,17 @@ __device__ __forceinline__ unsigned long long dbl_bits(double v) {
     return static_cast<unsigned long long>(__double_as_longlong(v));
 }
 
-// h range and input validation.  hmin/hmax are kept as the bit patterns of
-// positive doubles, which order like the values.
+// h range and input validation: a periodic axis takes [0, L), a bounded one
+// [0, L] (a wall may lie on the edge of the box).  hmin/hmax are kept as the bit
+// patterns of positive doubles, which order like the values.
 __global__ void k_bounds(const double* __restrict__ xy, const double* __restrict__ h, int64_t N,
-                         double Lx, double Ly, unsigned long long* hmin, unsigned long long* hmax,
-                         int* bad) {
+                         double Lx, double Ly, bool px, bool py, unsigned long long* hmin,
+                         unsigned long long* hmax, int* bad) {
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < N;
          i += int64_t(gridDim.x) * blockDim.x) {
         const double x = xy[2 * i], y = xy[2 * i + 1], hi = h[i];
         const bool ok = isfinite(x) && isfinite(y) && isfinite(hi) && hi > 0.0 && x >= 0.0 &&
-                        x < Lx && y >= 0.0 && y < Ly;
+                        (px ? x < Lx : x <= Lx) && y >= 0.0 && (py ? y < Ly : y <= Ly);
         if (!ok) {
             atomicOr(bad, 1);
             continue;
@@ -332,14 +333,16 @@ extern "C" int labfm_build_stencils(const double* xy, const double* h, int64_t N
     Bounds init{~0ull, 0ull, 0, 0};
     LABFM_CUDA_TRY(cudaMemcpyAsync(b_dev, &init, sizeof(init), cudaMemcpyHostToDevice, st));
     const int nblk = int(std::min<int64_t>((N + 255) / 256, 65535));
-    k_bounds<<<nblk, 256, 0, st>>>(xy, h, N, Lx, Ly, &b_dev->hmin, &b_dev->hmax, &b_dev->bad);
+    k_bounds<<<nblk, 256, 0, st>>>(xy, h, N, Lx, Ly, (periodic_mask & 1u) != 0, (periodic_mask & 2u) != 0,
+                                   &b_dev->hmin, &b_dev->hmax, &b_dev->bad);
     LABFM_LAUNCH_CHECK("bounds kernel");
     Bounds bh{};
     LABFM_CUDA_TRY(cudaMemcpyAsync(&bh, b_dev, sizeof(bh), cudaMemcpyDeviceToHost, st));
     LABFM_CUDA_TRY(cudaStreamSynchronize(st));
     if (bh.bad)
         return set_error(LABFM_EINVAL,
-                         "a node lies outside [0,Lx)x[0,Ly) or has a non-positive or non-finite h");
+                         "a node lies outside the box ([0, L) on a periodic axis, [0, L] on a bounded "
+                         "one) or has a non-positive or non-finite h");
     double hmin, hmax;
     memcpy(&hmin, &bh.hmin, sizeof(double));
     memcpy(&hmax, &bh.hmax, sizeof(double));

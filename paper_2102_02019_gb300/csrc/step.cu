@@ -41,7 +41,7 @@ constexpr int kGatherBlock = 128;
 #define LABFM_STAGE_BOUNDS \
     __launch_bounds__(kGatherBlock, sizeof(T) == 4 ? LABFM_STAGE_MINB : 6)
 
-template <typename T, int G, bool KAHAN, bool SCALED>
+template <typename T, int G, bool KAHAN, bool SCALED, bool WALL = false>
 __global__ void LABFM_STAGE_BOUNDS k_rhs_soa(PlanView<T> P, SoA<T> in, T* __restrict__ out, Phys<T> ph) {
     const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     const int64_t node = gt / G;
@@ -54,7 +54,7 @@ __global__ void LABFM_STAGE_BOUNDS k_rhs_soa(PlanView<T> P, SoA<T> in, T* __rest
     if (i >= 0 && gl == 0) {
         T Ra, Ru, Rv;
         const T is = SCALED ? P.inv_s[i] : T(1);
-        pointwise_rhs<T, SCALED>(d, ai, ui, vi, is, ph.c2, ph.mu, ph.gx, ph.gy, Ra, Ru, Rv);
+        node_rhs<T, SCALED, WALL>(P, i, d, ai, ui, vi, is, ph, Ra, Ru, Rv);
         out[i] = Ra;
         out[P.N + i] = Ru;
         out[2 * P.N + i] = Rv;
@@ -65,8 +65,8 @@ __global__ void LABFM_STAGE_BOUNDS k_rhs_soa(PlanView<T> P, SoA<T> in, T* __rest
 // Q_out = Q_in + dt_i b_k F; X_out = Q_out + dt_i (a - b) F (skipped when X_out
 // is null).  Q_in may equal Q_out, and Q_in may equal X_in (first stage, where
 // X = Q).  dt_i is the uniform dt or the plan's per-node dt.  Lane 0 of the
-// group stores.
-template <typename T, bool SCALED>
+// group stores.  WALL: R is the wall's right-hand side at the plan's wall nodes.
+template <typename T, bool SCALED, bool WALL = false>
 __device__ __forceinline__ void stage_epilogue(const PlanView<T>& P, int i, int gl, const T (&d)[12],
                                                T ai, T ui, T vi, const Packed<T>* X_in,
                                                const Packed<T>* Q_in, Packed<T>* Q_out,
@@ -75,7 +75,7 @@ __device__ __forceinline__ void stage_epilogue(const PlanView<T>& P, int i, int 
     if (i >= 0 && gl == 0) {
         T Ra, Ru, Rv;
         const T is = SCALED ? P.inv_s[i] : T(1);
-        pointwise_rhs<T, SCALED>(d, ai, ui, vi, is, ph.c2, ph.mu, ph.gx, ph.gy, Ra, Ru, Rv);
+        node_rhs<T, SCALED, WALL>(P, i, d, ai, ui, vi, is, ph, Ra, Ru, Rv);
         const double dti = P.dt_node ? P.dt_node[i] : dt;
         const T cb = T(dti * bk), cx = T(dti * ck);
         T qa, qu, qv;
@@ -96,7 +96,7 @@ __device__ __forceinline__ void stage_epilogue(const PlanView<T>& P, int i, int 
 
 // One fused RK stage at node i (i < 0: an idle group that still joins the
 // shuffles).
-template <typename T, int G, bool KAHAN, bool SCALED>
+template <typename T, int G, bool KAHAN, bool SCALED, bool WALL = false>
 __device__ __forceinline__ void stage_node(const PlanView<T>& P, int i, int gl,
                                            const Packed<T>* X_in, const Packed<T>* Q_in,
                                            Packed<T>* Q_out, Packed<T>* X_out, double dt,
@@ -106,7 +106,7 @@ __device__ __forceinline__ void stage_node(const PlanView<T>& P, int i, int gl,
     if (i >= 0) fld.get(i, ai, ui, vi);
     T d[12];
     gather_derivatives<T, G, KAHAN>(P, fld, i, gl, ai, ui, vi, d);
-    stage_epilogue<T, SCALED>(P, i, gl, d, ai, ui, vi, X_in, Q_in, Q_out, X_out, dt, bk, ck, ph);
+    stage_epilogue<T, SCALED, WALL>(P, i, gl, d, ai, ui, vi, X_in, Q_in, Q_out, X_out, dt, bk, ck, ph);
 }
 
 // Nodes per work-queue tile of the persistent stage kernel, per warp.
@@ -118,15 +118,18 @@ constexpr int kTileRows = 4;
 // (*counter, zeroed before the launch), so that uneven stencils and mixed
 // instances balance dynamically across the GPU.
 
-template <typename T, int G, bool KAHAN, bool SCALED, bool PERSIST>
+// WALL (plain grid only): plans with walls, whose wall nodes take the wall's
+// right-hand side.
+template <typename T, int G, bool KAHAN, bool SCALED, bool PERSIST, bool WALL = false>
 __global__ void LABFM_STAGE_BOUNDS k_stage(PlanView<T> P, const Packed<T>* X_in, const Packed<T>* Q_in,
                         Packed<T>* Q_out, Packed<T>* X_out, double dt, double bk, double ck,
                         Phys<T> ph, int* counter) {
+    static_assert(!(PERSIST && WALL), "plans with walls run the plain grid");
     if (!PERSIST) {
         const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
         const int64_t node = gt / G;
         const int i = node < P.N ? int(node) : -1;
-        stage_node<T, G, KAHAN, SCALED>(P, i, int(gt % G), X_in, Q_in, Q_out, X_out, dt, bk, ck, ph);
+        stage_node<T, G, KAHAN, SCALED, WALL>(P, i, int(gt % G), X_in, Q_in, Q_out, X_out, dt, bk, ck, ph);
         return;
     }
     constexpr int per_warp = 32 / G;
@@ -400,18 +403,29 @@ __global__ void k_filter_soa(PlanView<T> P, SoA<T> in, T* __restrict__ out) {
     }
 }
 
-template <typename T, int G, bool KAHAN>
+// PERSIST = false: one group of G lanes per node over a full grid.  PERSIST =
+// true: a grid of (SMs x resident blocks) in which warp w takes the 32/G
+// consecutive nodes starting at w * 32/G, then strides by all the grid's groups,
+// so that no partly filled last wave of blocks idles the GPU at the end.
+template <typename T, int G, bool KAHAN, bool PERSIST>
 __global__ void k_filter_aos(PlanView<T> P, const Packed<T>* in, Packed<T>* out) {
     const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-    const int64_t node = gt / G;
     const int gl = int(gt % G);
-    const int i = node < P.N ? int(node) : -1;
     const AoS<T> fld{in};
-    T ai = 0, ui = 0, vi = 0;
-    if (i >= 0) fld.get(i, ai, ui, vi);
-    T sa, su, sv;
-    filter_sums<T, G, KAHAN>(P, fld, i, gl, ai, ui, vi, sa, su, sv);
-    if (i >= 0 && gl == 0) store(out, i, ai + sa, ui + su, vi + sv);
+    const int64_t stride = PERSIST ? int64_t(gridDim.x) * blockDim.x / G : P.N;
+    // every lane of a warp runs the same iterations (the group sums shuffle
+    // across the whole warp); a group past the end runs idle
+    const int64_t warp_first = (gt / 32) * (32 / G);
+    for (int64_t base = warp_first; base < P.N; base += stride) {
+        const int64_t node = base + (gt % 32) / G;
+        const int i = node < P.N ? int(node) : -1;
+        T ai = 0, ui = 0, vi = 0;
+        if (i >= 0) fld.get(i, ai, ui, vi);
+        T sa, su, sv;
+        filter_sums<T, G, KAHAN>(P, fld, i, gl, ai, ui, vi, sa, su, sv);
+        if (i >= 0 && gl == 0) store(out, i, ai + sa, ui + su, vi + sv);
+        if (!PERSIST) break;
+    }
 }
 
 template <typename T>
@@ -548,10 +562,11 @@ int rhs_launch_g(const labfm_plan* p, const void* fields, void* rhs, const Phys<
     SoA<T> in{f, f + p->N, f + 2 * p->N};
     (void)block;  // the gather kernels always run kGatherBlock-thread blocks
     const int grid = grid_for(p->N * G, kGatherBlock);
-    if constexpr (std::is_same<T, float>::value)
-        k_rhs_soa<T, G, true, true><<<grid, kGatherBlock, 0, st>>>(view<T>(p), in, static_cast<T*>(rhs), ph);
+    constexpr bool F = std::is_same<T, float>::value;
+    if (p->wall_slot)
+        k_rhs_soa<T, G, F, F, true><<<grid, kGatherBlock, 0, st>>>(view<T>(p), in, static_cast<T*>(rhs), ph);
     else
-        k_rhs_soa<T, G, false, false><<<grid, kGatherBlock, 0, st>>>(view<T>(p), in, static_cast<T*>(rhs), ph);
+        k_rhs_soa<T, G, F, F><<<grid, kGatherBlock, 0, st>>>(view<T>(p), in, static_cast<T*>(rhs), ph);
     LABFM_LAUNCH_CHECK("rhs kernel");
     return LABFM_OK;
 }
@@ -576,7 +591,11 @@ int stage_launch_g(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* q
                    int* counter, cudaStream_t st) {
     const int block = kGatherBlock;
     constexpr bool F = std::is_same<T, float>::value;
-    if (p->persistent) {
+    if (p->wall_slot) {
+        const int grid = grid_for(p->N * G, block);
+        k_stage<T, G, F, F, false, true><<<grid, block, 0, st>>>(view<T>(p), xin, qin, qout, xout, dt, bk, ck,
+                                                                 ph, counter);
+    } else if (p->persistent) {
         k_stage<T, G, F, F, true><<<p->persist_grid, block, 0, st>>>(view<T>(p), xin, qin, qout, xout,
                                                                       dt, bk, ck, ph, counter);
     } else {
@@ -615,7 +634,7 @@ int stage_bulk_launch_s(const labfm_plan* p, const Packed<float>* xin, const Pac
 // The staged kernel serves F32 plans with staging on and 16 or 32 lanes per node
 // whose largest round fits in shared memory; every other case runs k_stage.
 bool staged(const labfm_plan* p) {
-    if (p->dtype != LABFM_F32 || p->stages == 0) return false;
+    if (p->dtype != LABFM_F32 || p->stages == 0 || p->wall_slot) return false;
     if (p->group != 16 && p->group != 32) return false;
     return p->stage_grid[p->group == 32 ? 1 : 0] > 0;
 }
@@ -642,15 +661,23 @@ int stage_launch(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* qin
 
 template <typename T, int G>
 int filter_aos_g(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaStream_t st) {
-    const int grid = grid_for(p->N * G, p->block);
-    k_filter_aos<T, G, std::is_same<T, float>::value><<<grid, p->block, 0, st>>>(view<T>(p), in, out);
+    constexpr bool F = std::is_same<T, float>::value;
+    if (p->filter_persistent && p->filter_grid > 0) {
+        k_filter_aos<T, G, F, true><<<p->filter_grid, p->block, 0, st>>>(view<T>(p), in, out);
+    } else {
+        const int grid = grid_for(p->N * G, p->block);
+        k_filter_aos<T, G, F, false><<<grid, p->block, 0, st>>>(view<T>(p), in, out);
+    }
     LABFM_LAUNCH_CHECK("filter kernel");
     return LABFM_OK;
 }
 
+// Lanes per node of the filter: its own setting, else the plan's.
+int filter_lanes(const labfm_plan* p) { return p->filter_group ? p->filter_group : p->group; }
+
 template <typename T>
 int filter_aos(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaStream_t st) {
-    switch (p->group) {
+    switch (filter_lanes(p)) {
         case 2: return filter_aos_g<T, 2>(p, in, out, st);
         case 4: return filter_aos_g<T, 4>(p, in, out, st);
         case 8: return filter_aos_g<T, 8>(p, in, out, st);
@@ -905,6 +932,37 @@ int launch_rk_steps(const labfm_plan* p, void* Q, void* work, double dt, int nst
     for (int step = 0; step < nsteps; ++step)
         if ((rc = rk_one_step(p, work, dt, ph, true, st))) return rc;
     return rk_unpack(p, Q, work, st);
+}
+
+int filter_persistent_grid(const labfm_plan* p) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaErrorInvalidValue;
+#define LABFM_FOCC(T, G)                                                                            \
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                              \
+        &per_sm, k_filter_aos<T, G, std::is_same<T, float>::value, true>, p->block, 0)
+    const int g = filter_lanes(p);
+    if (p->dtype == LABFM_F32) {
+        switch (g) {
+            case 2: LABFM_FOCC(float, 2); break;
+            case 4: LABFM_FOCC(float, 4); break;
+            case 8: LABFM_FOCC(float, 8); break;
+            case 16: LABFM_FOCC(float, 16); break;
+            case 32: LABFM_FOCC(float, 32); break;
+        }
+    } else {
+        switch (g) {
+            case 2: LABFM_FOCC(double, 2); break;
+            case 4: LABFM_FOCC(double, 4); break;
+            case 8: LABFM_FOCC(double, 8); break;
+            case 16: LABFM_FOCC(double, 16); break;
+            case 32: LABFM_FOCC(double, 32); break;
+        }
+    }
+#undef LABFM_FOCC
+    if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+    return sms * per_sm;
 }
 
 int persistent_grid(const labfm_plan* p) {

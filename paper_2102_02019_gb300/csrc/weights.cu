@@ -740,7 +740,8 @@ __global__ void __launch_bounds__(WCfg<M>::NT, stencil_opt_min_blocks<M>())
                   const double* __restrict__ s, int64_t N, double Lx, double Ly, int px_, int py_,
                   const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                   double factor, double amp_max, double resid_coef, int max_iter,
-                  double* __restrict__ h_out, int32_t* __restrict__ solves_out) {
+                  double* __restrict__ h_out, int32_t* __restrict__ solves_out,
+                  double* __restrict__ alpha_out) {
     using C = WCfg<M>;
     constexpr int n = C::n;
     constexpr int NT = C::NT;
@@ -769,6 +770,10 @@ __global__ void __launch_bounds__(WCfg<M>::NT, stencil_opt_min_blocks<M>())
     NodeGeom g{xy[2 * i], xy[2 * i + 1], h0[i], Lx, Ly, px_ != 0, py_ != 0, 1.0 / h0[i]};
     double best = h0[i];
     int solves = 0;
+    // alpha_L at the last h that passed and at the h where the loop stopped (NaN
+    // where none was computed)
+    double alpha_pass = __longlong_as_double(0x7ff8000000000000ll);
+    double alpha_stop = alpha_pass;
     for (int it = 0; it < max_iter; ++it) {
         if (t <= M) s_hp[t] = pow(g.hi, -double(t));  // h^-k (read after the next barrier)
         // nodes inside the current radius (the same exact test as the neighbour search)
@@ -809,12 +814,19 @@ __global__ void __launch_bounds__(WCfg<M>::NT, stencil_opt_min_blocks<M>())
         }
         const double alpha = sqrt(block_sum<NT>(r2, s_red));
         const double alpha0 = resid_coef * eps * double(n) * double(n) * double(n) * double(n) / (g.hi * M);
-        if (!(alpha <= alpha0)) break;
+        if (!(alpha <= alpha0)) {
+            alpha_stop = alpha;
+            break;
+        }
         // steps 3-4: amplitude response up to Nyquist
         const double amax = block_amplitude_max<M, LDA>(xy, col, r0, r1, g, s[i], A, s_he, s_cf3, s_part, &s_amax);
-        if (!(amax <= amp_max)) break;
+        if (!(amax <= amp_max)) {
+            alpha_stop = alpha;
+            break;
+        }
         // step 5
         best = g.hi;
+        alpha_pass = alpha;
         g.hi = g.hi * factor;
         g.ih = 1.0 / g.hi;
         __syncthreads();
@@ -822,6 +834,10 @@ __global__ void __launch_bounds__(WCfg<M>::NT, stencil_opt_min_blocks<M>())
     if (t == 0) {
         h_out[i] = best;
         if (solves_out) solves_out[i] = solves;
+        if (alpha_out) {
+            alpha_out[2 * i] = alpha_pass;
+            alpha_out[2 * i + 1] = alpha_stop;
+        }
     }
 }
 
@@ -829,12 +845,13 @@ template <int M>
 int launch_stencil_opt(const double* xy, const double* h0, const double* s, int64_t N, double Lx,
                        double Ly, uint32_t pm, const int32_t* row_ptr, const int32_t* col,
                        double factor, double amp_max, double resid_coef, int max_iter, double* h_out,
-                       int32_t* solves, cudaStream_t st) {
+                       int32_t* solves, double* alpha, cudaStream_t st) {
     using C = WCfg<M>;
     const size_t sm = C::smem(true);
     LABFM_CUDA_TRY(cudaFuncSetAttribute(k_stencil_opt<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
     k_stencil_opt<M><<<unsigned(N), C::NT, sm, st>>>(xy, h0, s, N, Lx, Ly, pm & 1u, (pm >> 1) & 1u,
-                                                     row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves);
+                                                     row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves,
+                                                     alpha);
     LABFM_LAUNCH_CHECK("stencil optimisation kernel");
     return LABFM_OK;
 }
@@ -975,7 +992,7 @@ extern "C" int labfm_stencil_optimise(const double* xy, const double* h0, const 
                                       double Lx, double Ly, uint32_t periodic_mask,
                                       const int32_t* row_ptr, const int32_t* col, int m,
                                       double factor, double amp_max, double resid_coef, int max_iter,
-                                      double* h_out, int32_t* solves_out, void* stream) {
+                                      double* h_out, int32_t* solves_out, double* alpha_out, void* stream) {
     LABFM_NVTX("labfm_stencil_optimise");
     if (!xy || !h0 || !s || !row_ptr || !col || !h_out)
         return set_error(LABFM_EINVAL, "null pointer argument");
@@ -986,11 +1003,11 @@ extern "C" int labfm_stencil_optimise(const double* xy, const double* h0, const 
     if (!(resid_coef > 0.0)) return set_error(LABFM_EINVAL, "resid_coef must be positive");
     cudaStream_t st = as_stream(stream);
     switch (m) {
-        case 2: return launch_stencil_opt<2>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, st);
-        case 4: return launch_stencil_opt<4>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, st);
-        case 6: return launch_stencil_opt<6>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, st);
-        case 8: return launch_stencil_opt<8>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, st);
-        default: return launch_stencil_opt<10>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, st);
+        case 2: return launch_stencil_opt<2>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, alpha_out, st);
+        case 4: return launch_stencil_opt<4>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, alpha_out, st);
+        case 6: return launch_stencil_opt<6>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, alpha_out, st);
+        case 8: return launch_stencil_opt<8>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, alpha_out, st);
+        default: return launch_stencil_opt<10>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, alpha_out, st);
     }
 }
 

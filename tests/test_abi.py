@@ -61,11 +61,11 @@ def test_later_entry_points_validate_on_the_host(built_lib):
     L = lb.lib
     err = lambda: L.labfm_last_error()
     # stencil optimisation: order and shrink factor are checked before any launch
-    assert L.labfm_stencil_optimise(1, 1, 1, 10, 1.0, 1.0, 3, 1, 1, 5, 0.99, 1.01, 1e-4, 10, 1, None, None) == 1
+    assert L.labfm_stencil_optimise(1, 1, 1, 10, 1.0, 1.0, 3, 1, 1, 5, 0.99, 1.01, 1e-4, 10, 1, None, None, None) == 1
     assert b"order m" in err()
-    assert L.labfm_stencil_optimise(1, 1, 1, 10, 1.0, 1.0, 3, 1, 1, 4, 1.0, 1.01, 1e-4, 10, 1, None, None) == 1
+    assert L.labfm_stencil_optimise(1, 1, 1, 10, 1.0, 1.0, 3, 1, 1, 4, 1.0, 1.01, 1e-4, 10, 1, None, None, None) == 1
     assert b"factor" in err()
-    assert L.labfm_stencil_optimise(1, 1, 1, 10, 1.0, 1.0, 3, 1, 1, 4, 0.99, 1.01, 0.0, 10, 1, None, None) == 1
+    assert L.labfm_stencil_optimise(1, 1, 1, 10, 1.0, 1.0, 3, 1, 1, 4, 0.99, 1.01, 0.0, 10, 1, None, None, None) == 1
     assert b"resid_coef" in err()
     assert L.labfm_modal_response(1, 1, 10, 1.0, 1.0, 3, 1, 1, 10, 1, 0, 1, None) == 1
     assert b"nk" in err()

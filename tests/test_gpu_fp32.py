@@ -1,6 +1,6 @@
 """FP32 path (fields and nondimensionalised weights in float) against the FP64 oracle.
 
-Budget, derived from the arithmetic.  With u = 2^-24 (float unit roundoff),
+Budget, derived from the arithmetic (tests/fp32_budget.py).  With u = 2^-24 (float unit roundoff),
 each input phi_j, each stored weight w~_ji and the scale 1/s_i carry a relative
 rounding of u; phi_j - phi_i, the product and the compensated sum add a few
 more.  For one derivative the error is therefore bounded by
@@ -21,7 +21,7 @@ from oracle import core as oracle
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-U32 = 2.0 ** -24
+from tests.fp32_budget import U32, deriv_bound as _deriv_bound, rhs_bound, step_bound  # noqa: F401
 
 
 @pytest.fixture(scope="module")
@@ -47,36 +47,6 @@ def setup(lb):
     cold = _dev(col, torch.int32)
     plan32 = lb.Plan(rpd, cold, _dev(ow["w"]), _dev(ow["kappa"]), _dev(ns.s), dtype=torch.float32)
     return dict(ns=ns, rp=rp, col=col, ow=ow, plan32=plan32, s=_dev(ns.s))
-
-
-def _deriv_bound(phi, w, rp, col):
-    ri = oracle.row_index(rp)
-    absum = np.bincount(ri, np.abs(w) * (np.abs(phi[col]) + np.abs(phi[ri])), minlength=len(rp) - 1)
-    L = oracle.apply_op(phi, w, rp, col)
-    return 3 * U32 * absum + 2 * U32 * np.abs(L), L
-
-
-def rhs_bound(q, w, rp, col, c2, mu):
-    a, u, v = q
-    B, D = {}, {}
-    B["ax"], D["ax"] = _deriv_bound(a, w[0], rp, col)
-    B["ay"], D["ay"] = _deriv_bound(a, w[1], rp, col)
-    for name, f in (("u", u), ("v", v)):
-        for k, op in enumerate(oracle.RHS_OPS):
-            B[name + op], D[name + op] = _deriv_bound(f, w[k], rp, col)
-    nu = mu * np.exp(-a)
-    ba = (np.abs(u) * B["ax"] + np.abs(v) * B["ay"] + B["ux"] + B["vy"]
-          + 4 * U32 * (np.abs(u * D["ax"]) + np.abs(v * D["ay"]) + np.abs(D["ux"]) + np.abs(D["vy"])))
-    out = [ba]
-    for f, (x1, y1, a1, vis) in (("u", ("ux", "uy", "ax", ("uxx", "uyy", "vxy"))),
-                                 ("v", ("vx", "vy", "ay", ("vyy", "vxx", "uxy")))):
-        coef = (4.0 / 3.0, 1.0, 1.0 / 3.0)
-        visc = sum(c * np.abs(D[n]) for c, n in zip(coef, vis))
-        bvis = sum(c * B[n] for c, n in zip(coef, vis))
-        b = (np.abs(u) * B[x1] + np.abs(v) * B[y1] + c2 * B[a1] + nu * bvis
-             + 4 * U32 * (np.abs(u * D[x1]) + np.abs(v * D[y1]) + c2 * np.abs(D[a1]) + nu * visc))
-        out.append(b)
-    return np.stack(out)
 
 
 def test_rhs_fp32_within_rounding_budget(lb, setup):
@@ -113,14 +83,10 @@ def test_rk_step_fp32_one_step(lb, setup):
     q1 = oracle.time_step(q0, dt, ow["w"], ow["kappa"], rp, col, 100.0, 0.005)
     # per node: storage rounding of Q, plus dt sum_k |b_k| times the RHS budget at the
     # initial state (the stage states differ from it by O(dt)), plus the filter budget
-    B = rhs_bound(q0, ow["w"], rp, col, 100.0, 0.005)
-    bsum = sum(abs(float(b)) for b in oracle.RK_B)
-    wf = ow["w"][5] * np.repeat(ow["kappa"], np.diff(rp))
+    bound = step_bound(q0, q1, dt, ow["w"], ow["kappa"], rp, col, 100.0, 0.005)
     got = Q.double().cpu().numpy()
     for f in range(3):
-        bf, _ = _deriv_bound(q1[f], wf, rp, col)
-        bound = 8 * U32 * np.abs(q1[f]) + 2 * dt * bsum * B[f] + 2 * bf
-        assert np.all(np.abs(got[f] - q1[f]) <= bound), (f, (np.abs(got[f] - q1[f]) / bound).max())
+        assert np.all(np.abs(got[f] - q1[f]) <= bound[f]), (f, (np.abs(got[f] - q1[f]) / bound[f]).max())
 
 
 def test_profiling_and_host_buffer_step(lb, setup):

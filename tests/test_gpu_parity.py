@@ -289,6 +289,66 @@ def test_trajectory_fp64_100_steps(lb):
     assert np.all(_rel_l2(Q.cpu().numpy() - q0, qo - q0) <= 1e-10)
 
 
+def test_trajectory_fp64_100_steps_configured_geometry_shifted(lb):
+    # the small Taylor-Green workload as configured (64 x 64, +-0.3 s jitter, m = 4,
+    # h/s = 1.7) after the paper's ten iterations of iterative shifting (Section 5):
+    # 100 FP64 steps stay finite and match the oracle, GPU-built weights on both sides
+    ns = li.tgv_lattice(64, m=4, h_over_s=1.7, jitter=0.3, seed=0, shift_iterations=10)
+    c = Case(lb, ns)
+    wg = c.gw["w"].cpu().numpy()
+    kg = c.gw["kappa"].cpu().numpy()
+    plan = _plan(lb, c, c.gw["w"], c.gw["kappa"], torch.float64)
+    q0 = li.tgv_fields(ns.xy, 10.0)
+    dt = oracle.stable_dt(q0, ns.s, 10.0, 0.005)
+    Q = _dev(q0)
+    lb.rk_step(plan, Q, dt, 100, lb.Phys(100.0, 0.005))
+    qo = q0
+    for _ in range(100):
+        qo = oracle.time_step(qo, dt, wg, kg, c.rp_o, c.col_o, 100.0, 0.005)
+    qg = Q.cpu().numpy()
+    assert np.all(np.isfinite(qg)) and np.all(np.isfinite(qo))
+    assert np.abs(qo[1:]).max() < 1.0  # decaying vortex, no growth
+    assert np.all(_rel_l2(qg, qo) <= 1e-12), _rel_l2(qg, qo)
+    assert np.all(_rel_l2(qg - q0, qo - q0) <= 1e-10)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_filter_launch_shapes(lb, c1, dtype):
+    # the filter's own lanes per node and its persistent grid: the persistent grid
+    # gives the same state bit for bit; other lane counts sum in another order
+    c = c1
+    plan = _plan(lb, c, c.ow["w"], c.ow["kappa"], dtype)
+    q0 = li.tgv_fields(c.ns.xy, 10.0)
+    dt = oracle.stable_dt(q0, c.ns.s, 10.0, 0.005)
+    phys = lb.Phys(100.0, 0.005)
+    ref = _dev(q0, dtype)
+    lb.rk_step(plan, ref, dt, 2, phys)
+    qo = q0
+    for _ in range(2):
+        qo = oracle.time_step(qo, dt, c.ow["w"], c.ow["kappa"], c.rp_o, c.col_o, 100.0, 0.005)
+    tol = 1e-12 if dtype == torch.float64 else 1e-5
+    for fg in (2, 4, 8, 16, 32):
+        states = []
+        for fp in (False, True):
+            plan.set_filter_launch(fg, fp)
+            info = plan.info()
+            assert info["filter_group"] == fg and info["filter_persistent"] == int(fp)
+            Q = _dev(q0, dtype)
+            lb.rk_step(plan, Q, dt, 2, phys)
+            states.append(Q)
+        assert torch.equal(states[0], states[1]), fg
+        qg = states[0].double().cpu().numpy()
+        if dtype == torch.float64:  # the change over the steps, as in the step tests
+            assert np.all(_rel_l2(qg - q0, qo - q0) <= tol), (fg, _rel_l2(qg - q0, qo - q0))
+        else:  # the state, as in smoke(): FP32 rounding of ln rho ~ 5e-3 dominates
+            assert np.all(_rel_l2(qg, qo) <= tol), (fg, _rel_l2(qg, qo))
+        if fg == 4:  # the plan's own group: identical to the default launch
+            assert torch.equal(states[0], ref)
+    plan.set_filter_launch(0, False)
+    with pytest.raises(lb.LabfmError):
+        plan.set_filter_launch(3, False)
+
+
 def test_zero_steps_and_bad_workspace(lb, c1):
     c = c1
     plan = _plan(lb, c, c.ow["w"], c.ow["kappa"], torch.float64)

@@ -98,20 +98,24 @@ def test_staged_uneven_stencils_and_batches(lb):
 
 
 def test_staged_matches_oracle(lb):
+    # one staged FP32 step against the FP64 oracle within the per-node budget of
+    # one FP32 step derived in tests/fp32_budget.py (the staged kernel does the
+    # unstaged kernel's arithmetic; several steps are covered by the bit-identity
+    # tests above)
+    from tests.fp32_budget import step_bound
     ns = li.tgv_lattice(30, 26, m=6, h_over_s=2.2, jitter=0.1, seed=74)
     d = _operator(lb, ns, 6)
     plan = lb.Plan(d["row_ptr"], d["col"], d["w"], d["kappa"], d["s"], dtype=torch.float32)
     q = li.tgv_fields(ns.xy, C)
     q0 = torch.tensor(q, dtype=torch.float32, device="cuda")
     dt = oracle.stable_dt(q, ns.s, C, MU)
-    got = _run(lb, plan, q0, dt, 2, 32, 3).double().cpu().numpy()
+    got = _run(lb, plan, q0, dt, 1, 32, 3).double().cpu().numpy()
     w, kap = d["w"].cpu().numpy(), d["kappa"].cpu().numpy()
     rp, col = d["row_ptr"].cpu().numpy(), d["col"].cpu().numpy()
-    for _ in range(2):
-        q = oracle.time_step(q, dt, w, kap, rp, col, C * C, MU)
-    err = np.linalg.norm(got - q, axis=1) / np.linalg.norm(q, axis=1)
-    # the FP32 budget of the unstaged kernel (identical arithmetic)
-    assert np.all(err <= 1e-5), err
+    q1 = oracle.time_step(q, dt, w, kap, rp, col, C * C, MU)
+    bound = step_bound(q, q1, dt, w, kap, rp, col, C * C, MU)
+    ratio = np.abs(got - q1) / bound
+    assert ratio.max() <= 1.0, ratio.max()
     plan.close()
 
 
