@@ -58,7 +58,7 @@ def parse():
                     help="lattice side (512 = the benchmark workload; smaller sizes for profiling)")
     ap.add_argument("--ref-cores", type=int, default=0,
                     help="host cores for --impl reference (0 = all, 1 = one, in this process)")
-    ap.add_argument("--only", choices=["stencil_opt", "adjoint"], default=None,
+    ap.add_argument("--only", choices=["stencil_opt", "adjoint", "channel"], default=None,
                     help="run one extra workload alone on --nx and print its JSON (for profiling; "
                          "adjoint: --steps steps)")
     return ap.parse_args()
@@ -377,11 +377,14 @@ def _events(torch):
 
 def run_batch(lb, torch, args):
     """256 independent Taylor-Green instances, N log-uniform in [2k, 64k], m in {4, 6, 8},
-    FP32, each with its own time step: one batched plan, one CUDA graph per step."""
+    FP32, each with its own time step: one batched plan (instances grouped by order),
+    one CUDA graph per step; timed with one launch shape for the whole plan and with
+    one tuned shape per order class (labfm_plan_set_launch_ranges), the faster kept."""
     import labfm_inputs as li
     t0 = time.perf_counter()
     instances = []
-    for ns in li.batch_instances(256):
+    # grouped by order (a stable sort), so that each order class is one node range
+    for ns in sorted(li.batch_instances(256), key=lambda n: n.m):
         d = {"xy": torch.tensor(ns.xy, device="cuda"), "h": torch.tensor(ns.h, device="cuda"),
              "s": torch.tensor(ns.s, device="cuda"), "ns": ns}
         d["row_ptr"], d["col"] = lb.build_stencils(d["xy"], d["h"], ns.Lx, ns.Ly)
@@ -399,18 +402,35 @@ def run_batch(lb, torch, args):
     plan.set_dt(plan.stable_dt_instances(q0, s_all, C, MU).cpu().tolist())
     phys = lb.Phys(C * C, MU)
     tune = plan.tune_step(q0, phys, 0.0)
-    graph = lb.StepGraph(plan, 0.0, phys)
-    Q = q0.clone()
-    graph.run(Q, args.warmup)
-    a, b = _events(torch)
-    torch.cuda.synchronize()
-    a.record()
-    graph.run(Q, args.steps)
-    b.record()
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(b)
+
+    def graph_ms():
+        graph = lb.StepGraph(plan, 0.0, phys)
+        Q = q0.clone()
+        graph.run(Q, args.warmup)
+        a, b = _events(torch)
+        torch.cuda.synchronize()
+        a.record()
+        graph.run(Q, args.steps)
+        b.record()
+        torch.cuda.synchronize()
+        graph.close()
+        return a.elapsed_time(b), Q
+
+    ms_single, _ = graph_ms()
+    # one launch shape per order class (contiguous node ranges), tuned per class
+    classes = []
+    for m in sorted({d["ns"].m for d in instances}):
+        ks = [k for k, d in enumerate(instances) if d["ns"].m == m]
+        n0, n1 = plan.offsets[ks[0]], plan.offsets[ks[-1] + 1]
+        classes.append((n0, n1, m, sum(instances[k]["col"].numel() for k in ks) / (n1 - n0)))
+    per_order = plan.tune_ranges(q0, phys, 0.0, classes)
+    ms_ranges, Q = graph_ms()
+    if ms_ranges <= ms_single:
+        ms = ms_ranges
+    else:  # keep the single shape
+        plan.set_launch_ranges([], [], [])
+        ms, Q = graph_ms()
     ms_one = ms / args.steps
-    ms_pack = 0.0
     out = {"workload": "256 Taylor-Green instances, N log-uniform in [2048, 65536] (rounded to "
                        "square lattices), m uniform in {4, 6, 8}, h/s 1.7/2.2/2.8, FP32, "
                        "per-instance dt, one CUDA graph launch per step",
@@ -418,11 +438,13 @@ def run_batch(lb, torch, args):
            "node_evals_per_s": 4.0 * N * args.steps / (ms * 1e-3),
            "instance_steps_per_s": len(instances) * args.steps / (ms * 1e-3),
            "ms_per_step": ms_one, "tuned": tune, "build_s": build_s,
+           "ms_per_step_one_shape": ms_single / args.steps, "ms_per_step_per_order": ms_ranges / args.steps,
+           "per_order_shapes": [{k: c[k] for k in ("m", "group", "prefetch", "mean_neighbours", "nodes",
+                                                   "from_cache")} for c in per_order],
            "alg_GBps_step": (4 * (24.0 * plan.nnz + 64.0 * N) + 8.0 * plan.nnz + 36.0 * N)
            / (ms_one * 1e-3) / 1e9,
            # +-0.3 s lattices without node shifting go non-finite (see finite_state_control)
            "state_finite_after_run": bool(torch.isfinite(Q).all().item())}
-    graph.close()
     plan.close()
     return out
 
@@ -518,6 +540,107 @@ def run_stencil_opt(lb, torch, args):
                 "ms": c.elapsed_time(d), "nodes_per_s": ns.N / (c.elapsed_time(d) * 1e-3),
                 "max_response": [float(A[:, k].max()) for k in range(3)]}
         out[f"m{m}"] = rec
+    return out
+
+
+def _poiseuille_analytic(y, t, H, g, nu, nterms=400):
+    """Start-up of plane Poiseuille flow from rest under a body force g between
+    no-slip walls at y = 0 and H: the steady parabola minus its sine series, each
+    mode decaying at n^2 pi^2 nu / H^2 (the analytic solution Section 8.2 refers to)."""
+    import numpy as np
+    u = g / (2 * nu) * y * (H - y)
+    for k in range(nterms):
+        n = 2 * k + 1
+        u = u - (4 * g * H * H / (nu * np.pi ** 3 * n ** 3) * np.sin(n * np.pi * y / H)
+                 * np.exp(-(n * np.pi) ** 2 * nu * t / H ** 2))
+    return u
+
+
+def _channel_plan(lb, torch, ns, dtype, m=6, m_wall=4):
+    import labfm_inputs as li
+    cols, normals = li.channel_walls(ns)
+    xy = torch.tensor(ns.xy, device="cuda")
+    h = torch.tensor(ns.h, device="cuda")
+    s = torch.tensor(ns.s, device="cuda")
+    a, b = _events(torch)
+    a.record()
+    op = lb.build_wall_operator(xy, h, s, ns.Lx, ns.Ly, m, m_wall, torch.tensor(cols, device="cuda"),
+                                torch.tensor(normals, device="cuda"), 1.7, periodic=(True, False), check=True)
+    b.record()
+    torch.cuda.synchronize()
+    plan = lb.Plan(op["row_ptr"], op["col"], op["w"], op["kappa"], s, dtype=dtype)
+    plan.set_walls(torch.tensor(cols[:, 0], device="cuda"), torch.tensor(normals, device="cuda"))
+    return plan, s, op, a.elapsed_time(b), cols[:, 0]
+
+
+def run_channel(lb, torch, args, nx=512):
+    """The boundary row (Section 7.1): a channel periodic in x between no-slip walls,
+    nx x nx nodes (five uniform rows along each wall, +-0.05 s jitter inside), LABFM
+    m = 6 inside and m = 4 on the wall rows' second derivatives, the Poiseuille
+    start-up of Section 8.2 (Re = 10, Ma = 0.05): the wall operator build, FP32 steps
+    with the stage kernel's roofline, and the start-up error at t U0/H = 1 against the
+    analytic solution on two coarse channels (FP64)."""
+    import numpy as np
+    import labfm_inputs as li
+    ns = li.channel(nx, nx, m=6, jitter=0.05)
+    H, U0 = ns.Ly, 1.0
+    mu = U0 * H / 10.0
+    g = 8 * mu * U0 / H ** 2
+    c = U0 / 0.05
+    phys = lb.Phys(c * c, mu, g, 0.0)
+    plan, s, op, build_ms, wall_nodes = _channel_plan(lb, torch, ns, torch.float32)
+    nnz = int(op["col"].numel())
+    q0 = torch.zeros((3, ns.N), dtype=torch.float32, device="cuda")
+    dt = float(lb.stable_dt(plan, q0 + torch.tensor([[0.0], [U0], [0.0]], device="cuda"), s, c, mu).item())
+    tune = plan.tune_step(q0, phys, dt)
+    work = lb.workspace(plan)
+    Q = q0.clone()
+    lb.rk_step(plan, Q, dt, args.warmup, phys, work=work)
+    torch.cuda.synchronize()
+    plan.set_profiling(True)
+    a, b = _events(torch)
+    a.record()
+    lb.rk_step(plan, Q, dt, args.steps, phys, work=work)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    prof = plan.read_profile()
+    plan.set_profiling(False)
+    stage_ms = prof["stage_ms"] / max(1, prof["stage_launches"])
+    # per launch: the record stream, row pointer and node state as in the periodic
+    # stage kernel, plus the wall slot of every node (4 B)
+    alg = float(plan.info()["entry_bytes"]) * nnz + 68.0 * ns.N
+    peak, _ = peaks()
+    errs = {}
+    for n in (24, 48):
+        nsc = li.channel(n, n, m=6, jitter=0.05)
+        p64, s64, _, _, wn = _channel_plan(lb, torch, nsc, torch.float64)
+        zero = torch.zeros((3, nsc.N), dtype=torch.float64, device="cuda")
+        dt0 = float(lb.stable_dt(p64, zero + torch.tensor([[0.0], [U0], [0.0]], dtype=torch.float64,
+                                                          device="cuda"), s64, c, mu).item())
+        nsteps = int(np.ceil(1.0 / dt0))
+        lb.rk_step(p64, zero, 1.0 / nsteps, nsteps, phys)
+        u = zero[1].cpu().numpy()
+        ua = _poiseuille_analytic(nsc.xy[:, 1], 1.0, H, g, mu)
+        errs[n] = float(np.linalg.norm(u - ua) / np.linalg.norm(ua))
+        p64.close()
+    out = {"workload": f"channel {nx} x {nx} ({ns.N:,} nodes; walls at y = 0 and 1, five uniform rows "
+                       "each, +-0.05 s jitter inside), m = 6 inside, m = 4 on the wall rows, Poiseuille "
+                       "start-up (Re = 10, Ma = 0.05), FP32",
+           "nodes": ns.N, "nnz": nnz, "wall_nodes": int(len(wall_nodes)),
+           "wall_operator_build_ms": build_ms,
+           "node_evals_per_s": 4.0 * ns.N * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
+           "tuned": tune,
+           "roofline": {"bound": "hbm", "kernel": "k_stage<float> with the wall right-hand side",
+                        "alg_bytes_per_launch": alg, "mean_launch_ms": stage_ms,
+                        "achieved": alg / (stage_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": alg / (stage_ms * 1e-3) / 1e9 / peak},
+           "filter_launch_ms": prof["filter_ms"] / max(1, prof["filter_launches"]),
+           "wall_velocity_zero": bool((Q[1:, torch.tensor(wall_nodes, device="cuda").long()] == 0).all().item()),
+           "state_finite_after_run": bool(torch.isfinite(Q).all().item()),
+           "poiseuille_startup_rel_error_fp64": {"s=H/24": errs[24], "s=H/48": errs[48],
+                                                 "order": float(np.log(errs[24] / errs[48]) / np.log(2.0))}}
+    plan.close()
     return out
 
 
@@ -875,6 +998,7 @@ def run_ours(args, world, rank, local):
             "value": ctl["fp32_node_evals_per_s"], "unit": UNIT,
             "ms_per_step": ctl["ms_per_step"]["fp32"], "nnz": ctl["nnz"], "finite": ctl["finite"]}
         result["stencil_opt"] = run_stencil_opt(lb, torch, args)
+        result["channel"] = run_channel(lb, torch, args)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t0 = time.perf_counter()
@@ -919,6 +1043,8 @@ def main():
         import paper_2102_02019_gb300 as lb
         if args.only == "stencil_opt":
             out = run_stencil_opt(lb, torch, args)
+        elif args.only == "channel":
+            out = run_channel(lb, torch, args, nx=args.nx)
         else:
             out = run_adjoint(lb, torch, args, nsteps=args.steps, every=max(1, min(50, args.steps // 2)),
                               nx=args.nx)

@@ -426,6 +426,22 @@ int labfm_plan_get_info(const labfm_plan* plan, labfm_plan_info* info);
 int labfm_plan_set_launch(labfm_plan* plan, int group, int block);
 
 /*
+ * Launch shapes per node range (for example the order classes of a batched plan
+ * whose instances are grouped by order m): range r covers the nodes
+ * [begin[r], begin[r + 1]) and runs its own plain-grid stage and filter launches
+ * in labfm_rk_step (and the step graph) with group[r] lanes per node and the L2
+ * record prefetch distance prefetch[r] (F32; 0..8).  Results are those of the
+ * same lanes per node in one launch.  With ranges set, the persistent, staged
+ * and filter settings are not used, and the recording and adjoint calls refuse
+ * the plan.  n = 0 removes the ranges.  Host-only; the arrays are copied.
+ *   begin  host, n + 1 int64 (begin[0] = 0, begin[n] = N, not decreasing)
+ *   group, prefetch  host, n int32
+ * Errors: EINVAL (bounds, unsupported lanes per node, prefetch, a plan with walls).
+ */
+int labfm_plan_set_launch_ranges(labfm_plan* plan, int n, const int64_t* begin, const int32_t* group,
+                                 const int32_t* prefetch);
+
+/*
  * Launch shape of the filter kernel of labfm_rk_step (and labfm_rk_step_record):
  * `group` lanes per node (2, 4, 8, 16 or 32; 0 = the plan's group of
  * labfm_plan_set_launch), and persistent = 1 for a grid of (SMs x resident

@@ -21,7 +21,8 @@ Workloads (all doubly periodic, unit square unless stated):
 * ``tgv_fields(xy, c)``: the Taylor-Green initial condition of Section 8.1 in the
   evolved variables (ln rho, u, v), with rho = 1 + p / c^2.
 * ``channel(nx, ny, ...)``: a channel periodic in x between two walls, with the five
-  uniform node rows along each wall that the boundary scheme of Section 7.1 needs.
+  uniform node rows along each wall that the boundary scheme of Section 7.1 needs;
+  ``channel_walls(ns)`` lists its wall nodes' normal columns and normals.
 * ``smooth_perturbation(xy, ...)``: a seeded band-limited random field
   (integer wavevectors with |k| <= kmax), normalised to unit maximum amplitude.
 """
@@ -267,6 +268,22 @@ def channel(nx: int, ny: int, m: int = 4, h_over_s: float | None = None, jitter:
     return NodeSet(xy=xy, s=np.full(N, s), h=hv, Lx=1.0, Ly=H, m=m,
                    meta={"row": np.array(row), "normal": np.array(nrm), "column": np.array(colx),
                          "wall": np.array(wall), "nx": nx, "ny": ny, "h_over_s": hs})
+
+
+def channel_walls(ns: NodeSet) -> tuple[np.ndarray, np.ndarray]:
+    """The walls of a ``channel`` node set as Section 7.1 describes them: for every
+    wall node b (row q = 0) its normal column, the nodes of rows q = 0..4 with the
+    same wall and x index ((n_wall, 5) int32), and its inward unit normal
+    ((n_wall, 2) float64).  Wall nodes are listed bottom wall first, by x index."""
+    meta = ns.meta
+    key = {(int(w), int(c), int(q)): k for k, (w, c, q) in
+           enumerate(zip(meta["wall"], meta["column"], meta["row"])) if q < 5}
+    cols, normals = [], []
+    for w in (0, 1):
+        for c in range(meta["nx"]):
+            cols.append([key[(w, c, q)] for q in range(5)])
+            normals.append(meta["normal"][key[(w, c, 0)]])
+    return np.asarray(cols, dtype=np.int32), np.asarray(normals, dtype=np.float64)
 
 
 def tgv_fields(xy: np.ndarray, c: float = 10.0, H: float = 1.0) -> np.ndarray:

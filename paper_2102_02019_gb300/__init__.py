@@ -90,6 +90,7 @@ _SIGS = {
     "labfm_plan_get_info": (_I32, [_P, ctypes.POINTER(_PlanInfo)]),
     "labfm_plan_set_launch": (_I32, [_P, _I32, _I32]),
     "labfm_plan_set_filter_launch": (_I32, [_P, _I32, _I32]),
+    "labfm_plan_set_launch_ranges": (_I32, [_P, _I32, _P, _P, _P]),
     "labfm_plan_autotune": (_I32, [_P, _P, _P, ctypes.POINTER(_Phys), _I32,
                                    ctypes.POINTER(_I32), ctypes.POINTER(_I32), _P]),
     "labfm_rhs": (_I32, [_P, _P, _P, ctypes.POINTER(_Phys), _P]),
@@ -415,6 +416,81 @@ class Plan:
 
     def set_launch(self, group: int, block: int) -> None:
         _check(lib.labfm_plan_set_launch(self._h, group, block))
+
+    def set_launch_ranges(self, begin, group, prefetch) -> None:
+        """labfm_plan_set_launch_ranges: per node range [begin[r], begin[r+1]) its own
+        lanes per node and prefetch distance (host sequences; empty removes them)."""
+        n = len(group)
+        b = (_I64 * (n + 1))(*[int(v) for v in begin]) if n else None
+        g = (_I32 * n)(*[int(v) for v in group]) if n else None
+        pf = (_I32 * n)(*[int(v) for v in prefetch]) if n else None
+        _check(lib.labfm_plan_set_launch_ranges(self._h, n, ctypes.cast(b, _P) if n else None,
+                                                ctypes.cast(g, _P) if n else None,
+                                                ctypes.cast(pf, _P) if n else None))
+
+    def tune_ranges(self, Q: torch.Tensor, phys: Phys, dt: float, classes, steps: int = 3,
+                    groups=(2, 4, 8, 16), prefetch=(0, 2), cache: bool = True) -> list[dict]:
+        """Per-class launch shapes for a plan whose order classes occupy contiguous node
+        ranges.  classes: (begin, end, m, mean neighbours) per range, covering [0, N).
+        For each class in turn (the others at their current choice) time `steps` RK
+        steps for every lanes-per-node group and prefetch distance and keep the
+        fastest, then set the ranges.  With cache=True a choice is read from and
+        written to a JSON file (LABFM_TUNE_CACHE, else ~/.cache/labfm/tune.json) keyed
+        by GPU name, m, mean-neighbour bucket (steps of 8) and dtype, and a class found
+        there is not timed.  Q is not modified.  Returns the per-class choices."""
+        import json as _json
+        _state(self, Q)
+        dname = "f32" if self.dtype == torch.float32 else "f64"
+        gpu = torch.cuda.get_device_name(self.device)
+        keys = [f"{gpu}|m{int(m)}|nn{int(nn) // 8 * 8}|{dname}" for _, _, m, nn in classes]
+        path = os.environ.get("LABFM_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache", "labfm",
+                                                                   "tune.json")
+        stored = {}
+        if cache and os.path.exists(path):
+            try:
+                stored = _json.load(open(path))
+            except (OSError, ValueError):
+                stored = {}
+        pfs = tuple(prefetch) if self.dtype == torch.float32 else (0,)
+        begin = [int(c[0]) for c in classes] + [int(classes[-1][1])]
+        choice = [dict(stored[k]) if k in stored else {"group": 4, "prefetch": pfs[-1]} for k in keys]
+        from_cache = [k in stored for k in keys]
+        work = workspace(self)
+
+        def timed():
+            self.set_launch_ranges(begin, [c["group"] for c in choice], [c["prefetch"] for c in choice])
+            Qs = Q.clone()
+            rk_step(self, Qs, dt, 1, phys, work=work)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            rk_step(self, Qs, dt, steps, phys, work=work)
+            b.record()
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / steps
+
+        for r in range(len(classes)):
+            if from_cache[r]:
+                continue
+            best = None
+            for g in groups:
+                for pf in pfs:
+                    choice[r] = {"group": g, "prefetch": pf}
+                    ms = timed()
+                    if best is None or ms < best[0]:
+                        best = (ms, g, pf)
+            choice[r] = {"group": best[1], "prefetch": best[2]}
+            stored[keys[r]] = choice[r]
+        ms = timed()
+        if cache and not all(from_cache):
+            try:
+                os.makedirs(os.path.dirname(path), exist_ok=True)
+                with open(path, "w") as f:
+                    _json.dump(stored, f, indent=1, sort_keys=True)
+            except OSError:
+                pass
+        return [dict(c, m=int(cl[2]), mean_neighbours=float(cl[3]), nodes=int(cl[1] - cl[0]), key=k,
+                     from_cache=fc, ms_per_step=ms) for c, cl, k, fc in zip(choice, classes, keys, from_cache)]
 
     def set_filter_launch(self, group: int = 0, persistent: bool = False) -> None:
         """labfm_plan_set_filter_launch: the filter's lanes per node (0 = the plan's

@@ -84,7 +84,7 @@ template <typename T>
 PlanView<T> tview(const labfm_plan* p) {
     return PlanView<T>{p->N, p->tnnz_pad, p->trow_ptr, nullptr, static_cast<const T*>(p->tw),
                        static_cast<const T*>(p->twf), static_cast<const T*>(p->inv_s), p->dt_node, 0,
-                       nullptr, nullptr};
+                       nullptr, nullptr, 0, p->N};
 }
 
 // ---------------------------------------------------------------- pass A
@@ -364,7 +364,9 @@ __global__ void k_write_transposed(PlanView<T> P, int64_t N, const int32_t* __re
                 adjoint_combinations(f, v);
                 vf = *reinterpret_cast<const T*>(reinterpret_cast<const char*>(P.wf) + Rec<T>::fw_e(e));
             }
-            const int64_t dst = int64_t(t0) + rank;
+            // the same transposition within 16-entry segments as the forward records,
+            // so that the lanes of a group gather consecutive entries
+            const int64_t dst = int64_t(t0) + entry_slot(rank, plen);
             char* tb = reinterpret_cast<char*>(tw);
             *reinterpret_cast<int32_t*>(tb + Rec<T>::col_e(dst)) = src_i;
 #pragma unroll
@@ -653,6 +655,7 @@ size_t adjoint_work_bytes(const labfm_plan* p) {
 int check_adjoint(const labfm_plan* p, void* work, size_t work_bytes) {
     if (!p || !p->row_ptr) return set_error(LABFM_EINVAL, "null or empty plan");
     if (p->wall_slot) return set_error(LABFM_EINVAL, "the adjoint of a plan with walls is not implemented");
+    if (p->n_ranges) return set_error(LABFM_EINVAL, "the adjoint calls do not take launch ranges");
     if (!p->trow_ptr) return set_error(LABFM_EINVAL, "call labfm_plan_enable_adjoint first");
     if (!work) return set_error(LABFM_EINVAL, "null work buffer");
     if (work_bytes < adjoint_work_bytes(p))
@@ -715,6 +718,7 @@ extern "C" int labfm_rk_step_record(const labfm_plan* p, void* Q, void* states, 
     LABFM_NVTX("labfm_rk_step_record");
     if (!p || !p->row_ptr) return set_error(LABFM_EINVAL, "null or empty plan");
     if (p->wall_slot) return set_error(LABFM_EINVAL, "the recording step of a plan with walls is not implemented");
+    if (p->n_ranges) return set_error(LABFM_EINVAL, "the recording step does not take launch ranges");
     if (!Q || !states || !work || !phys) return set_error(LABFM_EINVAL, "null pointer argument");
     if (states_bytes < labfm_stage_states_bytes(p))
         return set_error(LABFM_EINVAL, "states buffer smaller than labfm_stage_states_bytes");

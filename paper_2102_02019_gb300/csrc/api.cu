@@ -96,6 +96,13 @@ void free_plan_memory(labfm_plan* p) {
     p->trow_ptr = nullptr;
     p->tw = p->twf = p->rsum = nullptr;
     delete[] p->inst_off_host;
+    delete[] p->range_begin;
+    delete[] p->range_group;
+    delete[] p->range_pf;
+    p->range_begin = nullptr;
+    p->range_group = nullptr;
+    p->range_pf = nullptr;
+    p->n_ranges = 0;
     p->row_ptr = nullptr;
     p->col = nullptr;
     p->w = p->wf = p->inv_s = nullptr;
@@ -298,6 +305,45 @@ extern "C" int labfm_plan_set_launch(labfm_plan* p, int group, int block) {
     p->block = block;
     if (p->persistent) p->persist_grid = persistent_grid(p);
     if (p->filter_persistent) p->filter_grid = filter_persistent_grid(p);
+    return LABFM_OK;
+}
+
+extern "C" int labfm_plan_set_launch_ranges(labfm_plan* p, int n, const int64_t* begin, const int32_t* group,
+                                            const int32_t* prefetch) {
+    if (int rc = check_plan(p)) return rc;
+    if (n < 0) return set_error(LABFM_EINVAL, "negative number of ranges");
+    if (n > 0) {
+        if (!begin || !group || !prefetch) return set_error(LABFM_EINVAL, "null pointer argument");
+        if (p->wall_slot) return set_error(LABFM_EINVAL, "launch ranges are not supported on plans with walls");
+        if (begin[0] != 0 || begin[n] != p->N) return set_error(LABFM_EINVAL, "ranges must cover [0, N)");
+        for (int r = 0; r < n; ++r) {
+            if (begin[r + 1] < begin[r]) return set_error(LABFM_EINVAL, "range boundaries must not decrease");
+            if (!launch_shape_supported(group[r], p->block))
+                return set_error(LABFM_EINVAL, "unsupported lanes per node in range " + std::to_string(r));
+            if (prefetch[r] < 0 || prefetch[r] > 8) return set_error(LABFM_EINVAL, "prefetch must be in [0, 8]");
+        }
+    }
+    int64_t* nb = n ? new (std::nothrow) int64_t[n + 1] : nullptr;
+    int* ng = n ? new (std::nothrow) int[n] : nullptr;
+    int* np = n ? new (std::nothrow) int[n] : nullptr;
+    if (n && (!nb || !ng || !np)) {
+        delete[] nb;
+        delete[] ng;
+        delete[] np;
+        return set_error(LABFM_ENOMEM, "host allocation failed");
+    }
+    for (int r = 0; r <= n && n; ++r) nb[r] = begin[r];
+    for (int r = 0; r < n; ++r) {
+        ng[r] = group[r];
+        np[r] = p->dtype == LABFM_F32 ? prefetch[r] : 0;
+    }
+    delete[] p->range_begin;
+    delete[] p->range_group;
+    delete[] p->range_pf;
+    p->range_begin = nb;
+    p->range_group = ng;
+    p->range_pf = np;
+    p->n_ranges = n;
     return LABFM_OK;
 }
 

@@ -203,6 +203,26 @@ __device__ __forceinline__ void ld8(const void* p, float (&v)[8]) {
 }
 #endif
 
+// Slot of padded row entry e (0 <= e < plen, plen a multiple of 4) within its
+// row.  With LABFM_ENTRY_PERM, each segment of up to 16 entries (nc chunks) is
+// transposed so that chunk q holds entries q, q + nc, q + 2 nc, q + 3 nc: lanes
+// that take consecutive chunks then gather consecutive stencil entries (mostly
+// neighbouring nodes) with each load instruction.
+#ifndef LABFM_ENTRY_PERM
+#define LABFM_ENTRY_PERM 1
+#endif
+__device__ __forceinline__ int entry_slot(int e, int plen) {
+#if LABFM_ENTRY_PERM
+    const int base = e & ~15;
+    const int nc = min(16, plen - base) >> 2;
+    const int r = e - base;
+    return base + 4 * (r % nc) + r / nc;
+#else
+    (void)plen;
+    return e;
+#endif
+}
+
 // Node state (ln rho, u, v) packed for one-instruction gathers: float4 for F32
 // (w unused), two double2 for F64.
 template <typename T> struct Packed;
@@ -299,6 +319,7 @@ struct PlanView {
     int pf;                 // L2 prefetch distance of the F32 record stream, in iterations (0: off)
     const int32_t* wall_slot;  // per node: wall slot, -1 in the fluid (null: no walls)
     const T* wall_n;           // per wall slot: inward unit normal (n_x, n_y)
+    int64_t n_lo, n_hi;        // nodes [n_lo, n_hi) of this launch (plain stage and filter grids)
 };
 
 // Operator loads of one 4-entry chunk starting at entry e (a multiple of 4).
@@ -374,7 +395,7 @@ template <typename T>
 PlanView<T> view(const labfm_plan* p) {
     return PlanView<T>{p->N,        p->nnz_pad,  p->row_ptr, p->col, static_cast<const T*>(p->w),
                        static_cast<const T*>(p->wf), static_cast<const T*>(p->inv_s), p->dt_node,
-                       p->prefetch, p->wall_slot, static_cast<const T*>(p->wall_n)};
+                       p->prefetch, p->wall_slot, static_cast<const T*>(p->wall_n), 0, p->N};
 }
 
 // Chunk loaders for the gathers: from the plan's record stream in global memory,

@@ -92,6 +92,13 @@ struct labfm_plan {
     int filter_group = 0;
     bool filter_persistent = false;
     int filter_grid = 0;
+    // launch ranges (labfm_plan_set_launch_ranges): nodes [range_begin[r],
+    // range_begin[r + 1]) run their own plain stage and filter launches with
+    // range_group[r] lanes per node and prefetch range_pf[r] (host arrays)
+    int n_ranges = 0;
+    int64_t* range_begin = nullptr;
+    int* range_group = nullptr;
+    int* range_pf = nullptr;
     // F32 stage kernel with the operator staged through shared memory
     // (labfm_plan_set_staging): `stages` ring slots per CTA; for 16 and 32 lanes
     // per node ([0], [1]) the bytes of the largest round and the grid (0 = the

@@ -127,8 +127,8 @@ __global__ void LABFM_STAGE_BOUNDS k_stage(PlanView<T> P, const Packed<T>* X_in,
     static_assert(!(PERSIST && WALL), "plans with walls run the plain grid");
     if (!PERSIST) {
         const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
-        const int64_t node = gt / G;
-        const int i = node < P.N ? int(node) : -1;
+        const int64_t node = P.n_lo + gt / G;
+        const int i = node < P.n_hi ? int(node) : -1;
         stage_node<T, G, KAHAN, SCALED, WALL>(P, i, int(gt % G), X_in, Q_in, Q_out, X_out, dt, bk, ck, ph);
         return;
     }
@@ -412,13 +412,13 @@ __global__ void k_filter_aos(PlanView<T> P, const Packed<T>* in, Packed<T>* out)
     const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     const int gl = int(gt % G);
     const AoS<T> fld{in};
-    const int64_t stride = PERSIST ? int64_t(gridDim.x) * blockDim.x / G : P.N;
+    const int64_t stride = PERSIST ? int64_t(gridDim.x) * blockDim.x / G : P.n_hi;
     // every lane of a warp runs the same iterations (the group sums shuffle
     // across the whole warp); a group past the end runs idle
-    const int64_t warp_first = (gt / 32) * (32 / G);
-    for (int64_t base = warp_first; base < P.N; base += stride) {
+    const int64_t warp_first = P.n_lo + (gt / 32) * (32 / G);
+    for (int64_t base = warp_first; base < P.n_hi; base += stride) {
         const int64_t node = base + (gt % 32) / G;
-        const int i = node < P.N ? int(node) : -1;
+        const int i = node < P.n_hi ? int(node) : -1;
         T ai = 0, ui = 0, vi = 0;
         if (i >= 0) fld.get(i, ai, ui, vi);
         T sa, su, sv;
@@ -481,26 +481,6 @@ __global__ void k_padded_counts(int64_t N, const int32_t* __restrict__ row_ptr,
 
 // Warp per row: copy col, scale the RHS weights (F32: w s^l), fold kappa into
 // the filter weights, and fill the pad entries (self, weight 0).
-// Slot of padded row entry e (0 <= e < plen, plen a multiple of 4) within its
-// row.  With LABFM_ENTRY_PERM, each segment of up to 16 entries (nc chunks) is
-// transposed so that chunk q holds entries q, q + nc, q + 2 nc, q + 3 nc: lanes
-// that take consecutive chunks then gather consecutive stencil entries (mostly
-// neighbouring nodes) with each load instruction.
-#ifndef LABFM_ENTRY_PERM
-#define LABFM_ENTRY_PERM 1
-#endif
-__device__ __forceinline__ int entry_slot(int e, int plen) {
-#if LABFM_ENTRY_PERM
-    const int base = e & ~15;
-    const int nc = min(16, plen - base) >> 2;
-    const int r = e - base;
-    return base + 4 * (r % nc) + r / nc;
-#else
-    (void)plen;
-    return e;
-#endif
-}
-
 template <typename T, bool SCALED>
 __global__ void k_pack_rows(int64_t N, int64_t nnz, int64_t nnz_pad, int64_t off,
                             const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
@@ -607,6 +587,24 @@ int stage_launch_g(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* q
     return LABFM_OK;
 }
 
+// One plain-grid stage launch over the nodes of launch range r of the plan
+// (labfm_plan_set_launch_ranges) with that range's lanes per node and prefetch.
+template <typename T, int G>
+int stage_range_launch_g(const labfm_plan* p, int r, const Packed<T>* xin, const Packed<T>* qin,
+                         Packed<T>* qout, Packed<T>* xout, double dt, double bk, double ck, const Phys<T>& ph,
+                         cudaStream_t st) {
+    constexpr bool F = std::is_same<T, float>::value;
+    PlanView<T> v = view<T>(p);
+    v.n_lo = p->range_begin[r];
+    v.n_hi = p->range_begin[r + 1];
+    v.pf = p->range_pf[r];
+    if (v.n_hi <= v.n_lo) return LABFM_OK;
+    const int grid = grid_for((v.n_hi - v.n_lo) * G, kGatherBlock);
+    k_stage<T, G, F, F, false><<<grid, kGatherBlock, 0, st>>>(v, xin, qin, qout, xout, dt, bk, ck, ph, nullptr);
+    LABFM_LAUNCH_CHECK("rk stage kernel (launch range)");
+    return LABFM_OK;
+}
+
 template <int G, int S>
 int stage_bulk_launch(const labfm_plan* p, const Packed<float>* xin, const Packed<float>* qin,
                       Packed<float>* qout, Packed<float>* xout, double dt, double bk, double ck,
@@ -675,6 +673,53 @@ int filter_aos_g(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaS
 // Lanes per node of the filter: its own setting, else the plan's.
 int filter_lanes(const labfm_plan* p) { return p->filter_group ? p->filter_group : p->group; }
 
+template <typename T, int G>
+int filter_range_launch_g(const labfm_plan* p, int r, const Packed<T>* in, Packed<T>* out, cudaStream_t st) {
+    PlanView<T> v = view<T>(p);
+    v.n_lo = p->range_begin[r];
+    v.n_hi = p->range_begin[r + 1];
+    v.pf = p->range_pf[r];
+    if (v.n_hi <= v.n_lo) return LABFM_OK;
+    const int grid = grid_for((v.n_hi - v.n_lo) * G, p->block);
+    k_filter_aos<T, G, std::is_same<T, float>::value, false><<<grid, p->block, 0, st>>>(v, in, out);
+    LABFM_LAUNCH_CHECK("filter kernel (launch range)");
+    return LABFM_OK;
+}
+
+// Stage and filter launches over every launch range, each with its own shape.
+template <typename T>
+int stage_ranges(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* qin, Packed<T>* qout,
+                 Packed<T>* xout, double dt, double bk, double ck, const Phys<T>& ph, cudaStream_t st) {
+    for (int r = 0; r < p->n_ranges; ++r) {
+        int rc = LABFM_EINVAL;
+        switch (p->range_group[r]) {
+            case 2: rc = stage_range_launch_g<T, 2>(p, r, xin, qin, qout, xout, dt, bk, ck, ph, st); break;
+            case 4: rc = stage_range_launch_g<T, 4>(p, r, xin, qin, qout, xout, dt, bk, ck, ph, st); break;
+            case 8: rc = stage_range_launch_g<T, 8>(p, r, xin, qin, qout, xout, dt, bk, ck, ph, st); break;
+            case 16: rc = stage_range_launch_g<T, 16>(p, r, xin, qin, qout, xout, dt, bk, ck, ph, st); break;
+            case 32: rc = stage_range_launch_g<T, 32>(p, r, xin, qin, qout, xout, dt, bk, ck, ph, st); break;
+        }
+        if (rc) return rc;
+    }
+    return LABFM_OK;
+}
+
+template <typename T>
+int filter_ranges(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaStream_t st) {
+    for (int r = 0; r < p->n_ranges; ++r) {
+        int rc = LABFM_EINVAL;
+        switch (p->range_group[r]) {
+            case 2: rc = filter_range_launch_g<T, 2>(p, r, in, out, st); break;
+            case 4: rc = filter_range_launch_g<T, 4>(p, r, in, out, st); break;
+            case 8: rc = filter_range_launch_g<T, 8>(p, r, in, out, st); break;
+            case 16: rc = filter_range_launch_g<T, 16>(p, r, in, out, st); break;
+            case 32: rc = filter_range_launch_g<T, 32>(p, r, in, out, st); break;
+        }
+        if (rc) return rc;
+    }
+    return LABFM_OK;
+}
+
 template <typename T>
 int filter_aos(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaStream_t st) {
     switch (filter_lanes(p)) {
@@ -737,12 +782,13 @@ int rk_one_step_t(const labfm_plan* p, void* work, double dt, const labfm_phys* 
     for (int k = 0; k < 4; ++k) {
         const double bk = kRkB[k];
         const double ck = k < 3 ? kRkA[k] - kRkB[k] : 0.0;
-        if ((rc = stage_launch<T>(p, xin[k], qin[k], P, xout[k], dt, bk, ck, ph, tickets + k, st)))
-            return rc;
+        rc = p->n_ranges ? stage_ranges<T>(p, xin[k], qin[k], P, xout[k], dt, bk, ck, ph, st)
+                         : stage_launch<T>(p, xin[k], qin[k], P, xout[k], dt, bk, ck, ph, tickets + k, st);
+        if (rc) return rc;
     }
     prof_end(pm, evs, st);
     const int ev = profile ? prof_begin(pm, kProfFilter, st) : -1;
-    if ((rc = filter_aos<T>(p, P, X, st))) return rc;
+    if ((rc = p->n_ranges ? filter_ranges<T>(p, P, X, st) : filter_aos<T>(p, P, X, st))) return rc;
     prof_end(pm, ev, st);
     return LABFM_OK;
 }

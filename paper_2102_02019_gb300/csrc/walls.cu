@@ -595,6 +595,7 @@ extern "C" int labfm_plan_set_walls(labfm_plan* p, int64_t n_wall, const int32_t
     if (n_wall < 0 || n_wall > p->N) return set_error(LABFM_EINVAL, "n_wall out of range");
     if (n_wall > 0 && (!wall_nodes || !wall_normal)) return set_error(LABFM_EINVAL, "null pointer argument");
     if (n_wall > 0 && p->n_inst > 1) return set_error(LABFM_EINVAL, "walls are not supported on batched plans");
+    if (n_wall > 0 && p->n_ranges > 0) return set_error(LABFM_EINVAL, "walls are not supported with launch ranges");
     if (n_wall > 0 && fault_alloc()) return injected_alloc_error("labfm_plan_set_walls");
     return set_walls(p, n_wall, wall_nodes, wall_normal, as_stream(stream));
 }

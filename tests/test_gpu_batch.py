@@ -141,3 +141,80 @@ def test_persistent_handles_uneven_stencils(lb):
         out.append(Q.cpu().numpy())
         plan.close()
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+@pytest.mark.parametrize("graph", [False, True])
+def test_launch_ranges_match_instances_alone_with_their_shapes(lb, inst, dtype, graph):
+    # instances grouped by order, one launch range per order class with its own
+    # lanes per node and prefetch: every instance evolves bit for bit as it does
+    # alone with that range's shape
+    order = sorted(range(len(inst)), key=lambda k: inst[k]["ns"].m)
+    grouped = [inst[k] for k in order]
+    shapes = {4: (2, 0), 6: (8, 2), 8: (4, 2)}
+    phys = lb.Phys(C * C, MU)
+    nsteps = 3
+    alone, dts = [], []
+    for d in grouped:
+        plan = lb.Plan(d["row_ptr"], d["col"], d["w"], d["kappa"], d["s"], dtype=dtype)
+        g, pf = shapes[d["ns"].m]
+        plan.set_launch(g, 128)
+        plan.set_prefetch(pf if dtype == torch.float32 else 0)
+        Q = torch.tensor(d["q0"], dtype=dtype, device="cuda")
+        dt = float(lb.stable_dt(plan, Q, d["s"], C, MU).item())
+        dts.append(dt)
+        lb.rk_step(plan, Q, dt, nsteps, phys)
+        alone.append(Q.double().cpu().numpy())
+        plan.close()
+    bplan = lb.Plan.batched(grouped, dtype=dtype)
+    bplan.set_dt(dts)
+    off = bplan.offsets
+    classes = []
+    for m in (4, 6, 8):
+        ks = [k for k, d in enumerate(grouped) if d["ns"].m == m]
+        classes.append((off[ks[0]], off[ks[-1] + 1], m))
+    bplan.set_launch_ranges([c[0] for c in classes] + [classes[-1][1]],
+                            [shapes[c[2]][0] for c in classes], [shapes[c[2]][1] for c in classes])
+    Qb = torch.tensor(_stack([d["q0"] for d in grouped]), dtype=dtype, device="cuda")
+    if graph:
+        gr = lb.StepGraph(bplan, 0.0, phys)
+        gr.run(Qb, nsteps)
+        gr.close()
+    else:
+        lb.rk_step(bplan, Qb, 0.0, nsteps, phys)
+    got = Qb.double().cpu().numpy()
+    for k, d in enumerate(grouped):
+        assert np.array_equal(got[:, off[k]:off[k + 1]], alone[k]), k
+    # argument checks, and removing the ranges
+    with pytest.raises(lb.LabfmError):
+        bplan.set_launch_ranges([0, 5], [4], [2])  # does not cover [0, N)
+    with pytest.raises(lb.LabfmError):
+        bplan.set_launch_ranges([0, bplan.N], [3], [2])  # unsupported lanes per node
+    bplan.set_launch_ranges([], [], [])
+    assert bplan.info()["n_instances"] == len(grouped)
+    bplan.close()
+
+
+def test_range_tuner_and_cache(lb, inst, tmp_path, monkeypatch):
+    # the per-class tuner picks a supported shape for every class, writes its cache,
+    # and a second plan reads the shapes from it without timing
+    monkeypatch.setenv("LABFM_TUNE_CACHE", str(tmp_path / "tune.json"))
+    order = sorted(range(len(inst)), key=lambda k: inst[k]["ns"].m)
+    grouped = [inst[k] for k in order]
+    bplan = lb.Plan.batched(grouped, dtype=torch.float32)
+    Q = torch.tensor(_stack([d["q0"] for d in grouped]), dtype=torch.float32, device="cuda")
+    s_all = torch.cat([d["s"] for d in grouped])
+    bplan.set_dt(bplan.stable_dt_instances(Q, s_all, C, MU).cpu().numpy())
+    off = bplan.offsets
+    classes = []
+    for m in (4, 6, 8):
+        ks = [k for k, d in enumerate(grouped) if d["ns"].m == m]
+        nnz = sum(grouped[k]["col"].numel() for k in ks)
+        classes.append((off[ks[0]], off[ks[-1] + 1], m, nnz / (off[ks[-1] + 1] - off[ks[0]])))
+    first = bplan.tune_ranges(Q, lb.Phys(C * C, MU), 0.0, classes, steps=1)
+    assert all(c["group"] in (2, 4, 8, 16) and not c["from_cache"] for c in first)
+    assert (tmp_path / "tune.json").exists()
+    second = bplan.tune_ranges(Q, lb.Phys(C * C, MU), 0.0, classes, steps=1)
+    assert all(c["from_cache"] for c in second)
+    assert [(c["group"], c["prefetch"]) for c in first] == [(c["group"], c["prefetch"]) for c in second]
+    bplan.close()

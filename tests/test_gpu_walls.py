@@ -1,0 +1,276 @@
+"""The boundary row on the GPU (Section 7.1, Appendix A) against the oracle's
+channel: the wall operator (LABFM inside, five-point differences and 1D LABFM on
+the wall rows, rotated), the no-slip wall's right-hand side in LODI form, whole
+time steps, and the Poiseuille start-up of Section 8.2 converging to the analytic
+solution at the oracle's order."""
+import numpy as np
+import pytest
+
+import labfm_inputs as li
+from oracle import boundary_oracle as bo
+from oracle import core as oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS64 = np.finfo(np.float64).eps
+
+
+@pytest.fixture(scope="module")
+def lb():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2102_02019_gb300 as lb
+    return lb
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _rel_l2(a, b):
+    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
+
+
+class Channel:
+    """A channel node set with the oracle's operator and the GPU-built one."""
+
+    def __init__(self, lb, nx, ny, m=6, m_wall=4, jitter=0.1, seed=0):
+        self.ns = ns = li.channel(nx, ny, m=m, jitter=jitter, seed=seed)
+        self.m, self.m_wall = m, m_wall
+        self.columns, self.normals = li.channel_walls(ns)
+        self.xy, self.h, self.s = _dev(ns.xy), _dev(ns.h), _dev(ns.s)
+        self.gop = lb.build_wall_operator(self.xy, self.h, self.s, ns.Lx, ns.Ly, m, m_wall,
+                                          _dev(self.columns, torch.int32), _dev(self.normals), 1.7,
+                                          periodic=(True, False), check=True)
+        self.op = bo.channel_operator(ns, m, m_wall)
+        self.wall_nodes = self.columns[:, 0]
+
+    def plan(self, lb, dtype, oracle_weights=True):
+        if oracle_weights:
+            rp, col, w, kappa = self.op
+            p = lb.Plan(_dev(rp, torch.int32), _dev(col, torch.int32), _dev(w), _dev(kappa), self.s, dtype=dtype)
+        else:
+            g = self.gop
+            p = lb.Plan(g["row_ptr"], g["col"], g["w"], g["kappa"], self.s, dtype=dtype)
+        p.set_walls(_dev(self.wall_nodes, torch.int32), _dev(self.normals))
+        return p
+
+
+@pytest.fixture(scope="module")
+def ch(lb):
+    return Channel(lb, 20, 18, seed=3)
+
+
+def test_wall_operator_stencils_bit_exact(ch):
+    rp, col, _, _ = ch.op
+    assert np.array_equal(ch.gop["row_ptr"].cpu().numpy(), rp)
+    assert np.array_equal(ch.gop["col"].cpu().numpy(), col)
+    assert ch.gop["n_failed"] == 0
+
+
+def test_wall_operator_weights_match_oracle(ch):
+    # LABFM rows within the conditioning bound of the weight build (the LU is
+    # backward stable; the two sides differ in summation order), strip first
+    # derivatives (five-point differences and a 4 x 4 1D LABFM system) to 1e-12
+    ns = ch.ns
+    rp, col, w, kappa = ch.op
+    wg = ch.gop["w"].cpu().numpy()
+    kg = ch.gop["kappa"].cpu().numpy()
+    row = ns.meta["row"]
+    rpc, colc = oracle.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly, periodic=(True, False))
+    cond = {}
+    for mm in {ch.m, ch.m_wall}:
+        cond[mm] = oracle.build_weights(ns.xy, ns.h, ns.s, rpc, colc, mm, ns.Lx, ns.Ly, periodic=(True, False),
+                                        want_cond=True)["cond1"]
+    n = {mm: oracle.n_unknowns(mm) for mm in cond}
+    for i in range(ns.N):
+        sl = slice(rp[i], rp[i + 1])
+        a, b = wg[:, sl], w[:, sl]
+        if row[i] >= 3:
+            tol = max(50 * n[ch.m] * EPS64 * cond[ch.m][i], 1e-13)
+            assert np.abs(a - b).max() <= tol * np.abs(b).max(), i
+            assert abs(kg[i] - kappa[i]) <= tol * abs(kappa[i]), i
+            continue
+        # strip first derivatives
+        assert np.abs(a[:2] - b[:2]).max() <= 1e-12 * np.abs(b[:2]).max(), i
+        if row[i] == 0:
+            assert np.all(a[2:] == 0.0) and kg[i] == 0.0
+        else:
+            tol = max(50 * n[ch.m_wall] * EPS64 * cond[ch.m_wall][i], 1e-13)
+            assert np.abs(a[2:] - b[2:]).max() <= tol * np.abs(b[2:]).max(), i
+            assert abs(kg[i] - kappa[i]) <= tol * abs(kappa[i]), i
+
+
+def test_wall_rows_differentiate_quartics_exactly(ch):
+    # Section 7.1: the wall rows' first derivatives are exact on every polynomial of
+    # total degree <= 4 (five-point differences, 4th-order 1D LABFM), in the GPU's
+    # operator on both walls
+    ns = ch.ns
+    rp = ch.gop["row_ptr"].cpu().numpy()
+    col = ch.gop["col"].cpu().numpy()
+    w = ch.gop["w"].cpu().numpy()
+    strip = np.flatnonzero(ns.meta["row"] <= 2)
+    rng = np.random.default_rng(7)
+    x, y = ns.xy[:, 0], ns.xy[:, 1]
+    for _ in range(4):
+        c = rng.standard_normal(15)
+        ex = [(a, k - a) for k in range(5) for a in range(k + 1)]
+        # a local polynomial around each node (the channel is periodic in x: no wrap
+        # within the uniform rows' supports except across x = 0, handled by offsets)
+        for i in strip:
+            sl = slice(rp[i], rp[i + 1])
+            dx = oracle.minimum_image(x[col[sl]] - x[i], ns.Lx, True)
+            dy = y[col[sl]] - y[i]
+            p = sum(ck * dx ** a * dy ** b for ck, (a, b) in zip(c, ex))
+            px = c[ex.index((1, 0))]
+            py = c[ex.index((0, 1))]
+            dp = p - c[0]  # difference form: p_j - p_i, p_i = p(0, 0)
+            scale = (np.abs(w[0, sl]).sum() + np.abs(w[1, sl]).sum()) * np.abs(dp).max() + 1.0
+            assert abs(np.dot(w[0, sl], dp) - px) <= 1e-11 * scale, i
+            assert abs(np.dot(w[1, sl], dp) - py) <= 1e-11 * scale, i
+
+
+@pytest.mark.parametrize("g", [(0.0, 0.0), (0.3, -0.2)])
+def test_channel_rhs_matches_oracle(lb, ch, g):
+    ns = ch.ns
+    plan = ch.plan(lb, torch.float64)
+    q = li.perturbed_tgv_fields(ns.xy, 10.0, amplitude=0.05, kmax=4)
+    q[1:, ch.wall_nodes] = 0.0  # no slip
+    R = lb.rhs(plan, _dev(q), lb.Phys(100.0, 0.01, g[0], g[1])).cpu().numpy()
+    Ro = bo.channel_rhs(q, ch.op, ns, 10.0, 0.01, g)
+    assert np.all(_rel_l2(R, Ro) <= 1e-12), _rel_l2(R, Ro)
+    assert np.all(R[1:, ch.wall_nodes] == 0.0)
+    plan.close()
+
+
+def test_channel_time_steps_match_oracle(lb, ch):
+    # ten steps of the channel (interior eq. icns, wall rows, LODI wall, filter off
+    # the wall) from a perturbed state: the change over the steps within 1e-12
+    ns = ch.ns
+    c, mu, g = 10.0, 0.01, (0.5, 0.0)
+    plan = ch.plan(lb, torch.float64)
+    q0 = np.zeros((3, ns.N))
+    q0[0] = 0.02 * li.smooth_perturbation(ns.xy, kmax=3, seed=9, Ly=ns.Ly)
+    q0[1] = 0.1 * li.smooth_perturbation(ns.xy, kmax=3, seed=10, Ly=ns.Ly)
+    q0[1:, ch.wall_nodes] = 0.0
+    dt = 0.5 * oracle.stable_dt(np.stack([q0[0], q0[1] + 1.0, q0[2]]), ns.s, c, mu)
+    Q = _dev(q0)
+    lb.rk_step(plan, Q, dt, 10, lb.Phys(c * c, mu, g[0], g[1]))
+    qo = q0
+    for _ in range(10):
+        qo = bo.channel_time_step(qo, dt, ch.op, ns, c, mu, g)
+    qg = Q.cpu().numpy()
+    assert np.all(qg[1:, ch.wall_nodes] == 0.0)
+    assert np.all(_rel_l2(qg - q0, qo - q0) <= 1e-12), _rel_l2(qg - q0, qo - q0)
+    plan.close()
+
+
+def test_channel_step_with_gpu_operator_and_fp32(lb, ch):
+    # the GPU-built operator gives the oracle's step to the weights' agreement, and
+    # the FP32 plan (nondimensional FP32 weights) the same to FP32 rounding
+    ns = ch.ns
+    c, mu, g = 10.0, 0.01, (0.5, 0.0)
+    q0 = np.zeros((3, ns.N))
+    q0[1] = 0.1 * li.smooth_perturbation(ns.xy, kmax=3, seed=10, Ly=ns.Ly)
+    q0[1:, ch.wall_nodes] = 0.0
+    dt = 0.5 * oracle.stable_dt(np.stack([q0[0], q0[1] + 1.0, q0[2]]), ns.s, c, mu)
+    qo = q0
+    for _ in range(3):
+        qo = bo.channel_time_step(qo, dt, ch.op, ns, c, mu, g)
+    du = np.abs(qo[1] - q0[1]).max()
+    for dtype, tol in ((torch.float64, 1e-7), (torch.float32, 1e-4)):
+        plan = ch.plan(lb, dtype, oracle_weights=False)
+        Q = _dev(q0, dtype)
+        lb.rk_step(plan, Q, dt, 3, lb.Phys(c * c, mu, g[0], g[1]))
+        qg = Q.double().cpu().numpy()
+        assert np.all(qg[1:, ch.wall_nodes] == 0.0)
+        # the change of u over the steps, and v and ln rho (which start at zero)
+        # against the size of that change
+        assert _rel_l2(qg[1] - q0[1], qo[1] - q0[1]) <= tol, (dtype, _rel_l2(qg[1] - q0[1], qo[1] - q0[1]))
+        assert np.abs(qg[2] - qo[2]).max() <= tol * du and np.abs(qg[0] - qo[0]).max() <= tol * du
+        plan.close()
+
+
+def _poiseuille_start_up(y, t, H, g, nu, nterms=400):
+    u = g / (2 * nu) * y * (H - y)
+    for k in range(nterms):
+        n = 2 * k + 1
+        u = u - (4 * g * H * H / (nu * np.pi ** 3 * n ** 3) * np.sin(n * np.pi * y / H)
+                 * np.exp(-(n * np.pi) ** 2 * nu * t / H ** 2))
+    return u
+
+
+def _poiseuille_error(lb, nx, dtype=torch.float64, jitter=0.1):
+    # Section 8.2: Re = 10, Ma = 0.05, from rest, velocity error at t U0 / H = 1
+    ch = Channel(lb, nx, nx, m=6, m_wall=4, jitter=jitter)
+    ns = ch.ns
+    H, U0 = ns.Ly, 1.0
+    mu = U0 * H / 10.0
+    g = 8 * mu * U0 / H ** 2
+    c = U0 / 0.05
+    plan = ch.plan(lb, dtype, oracle_weights=False)
+    q = np.zeros((3, ns.N))
+    dt0 = oracle.stable_dt(np.stack([q[0], q[1] + U0, q[2]]), ns.s, c, mu)
+    nsteps = int(np.ceil(1.0 / dt0))
+    Q = _dev(q, dtype)
+    lb.rk_step(plan, Q, 1.0 / nsteps, nsteps, lb.Phys(c * c, mu, g, 0.0))
+    qg = Q.double().cpu().numpy()
+    plan.close()
+    ua = _poiseuille_start_up(ns.xy[:, 1], 1.0, H, g, mu)
+    assert np.all(qg[1:, ch.wall_nodes] == 0.0)
+    return np.linalg.norm(qg[1] - ua) / np.linalg.norm(ua), float(np.abs(qg[2]).max())
+
+
+def test_poiseuille_start_up_converges_on_the_gpu(lb):
+    # the oracle's pin (order > 4 from s = H/16 to H/24, interior jitter +-0.1 s) on
+    # the GPU path; finer channels at +-0.05 s jitter, where the sixth-order filter
+    # stays stable over the ~1000 steps of s = H/48 (at +-0.1 s the filter of some
+    # m = 6 stencils amplifies a mode: the run goes non-finite, as in the periodic case)
+    errs = {nx: _poiseuille_error(lb, nx) for nx in (16, 24)}
+    errs.update({(nx, 0.05): _poiseuille_error(lb, nx, jitter=0.05) for nx in (24, 48)})
+    e = {k: v[0] for k, v in errs.items()}
+    assert e[16] < 3e-3 and e[24] < 4e-4, e
+    assert np.log(e[16] / e[24]) / np.log(24 / 16) > 4.0, e
+    assert np.log(e[(24, 0.05)] / e[(48, 0.05)]) / np.log(2.0) > 3.5, e
+    assert all(v[1] < 1e-3 for v in errs.values())
+    # FP32: the same error as FP64 at this resolution (FP32 rounding is far below it)
+    e32, _ = _poiseuille_error(lb, 24, torch.float32)
+    print("Poiseuille start-up errors (FP64):", e, "FP32 at 24:", e32)
+    assert abs(e32 / e[24] - 1.0) < 0.2, (e32, e[24])
+
+
+def test_wall_arguments_are_checked(lb, ch):
+    ns = ch.ns
+    plan = ch.plan(lb, torch.float64)
+    nodes = _dev(ch.wall_nodes, torch.int32)
+    with pytest.raises(lb.LabfmError):  # a node listed twice
+        plan.set_walls(torch.cat([nodes[:3], nodes[:1]]), _dev(ch.normals[:4]))
+    bad = ch.normals.copy()
+    bad[0] *= 1.1
+    with pytest.raises(lb.LabfmError):  # not a unit normal
+        plan.set_walls(nodes, _dev(bad))
+    # the failed calls leave no walls; set them again, then the adjoint refuses
+    plan.set_walls(nodes, _dev(ch.normals))
+    lb.enable_adjoint(plan)
+    with pytest.raises(lb.LabfmError):
+        lb.rhs_adjoint(plan, _dev(np.zeros((3, ns.N))), _dev(np.zeros((3, ns.N))), lb.Phys(100.0, 0.01))
+    # removing the walls restores eq. icns everywhere
+    plan.set_walls(torch.empty(0, dtype=torch.int32, device="cuda"), torch.empty((0, 2), dtype=torch.float64,
+                                                                                  device="cuda"))
+    q = li.perturbed_tgv_fields(ns.xy, 10.0, amplitude=0.05, kmax=4)
+    R = lb.rhs(plan, _dev(q), lb.Phys(100.0, 0.01)).cpu().numpy()
+    rp, col, w, _ = ch.op
+    assert np.all(_rel_l2(R, oracle.rhs(q, w[:5], rp, col, 100.0, 0.01)) <= 1e-12)
+    # columns: a node in two columns, and an out-of-range node
+    cols = ch.columns.copy()
+    cols[1, 2] = cols[0, 2]
+    with pytest.raises(lb.LabfmError):
+        lb.build_wall_operator(ch.xy, ch.h, ch.s, ns.Lx, ns.Ly, 6, 4, _dev(cols, torch.int32), _dev(ch.normals))
+    cols = ch.columns.copy()
+    cols[0, 4] = ns.N
+    with pytest.raises(lb.LabfmError):
+        lb.build_wall_operator(ch.xy, ch.h, ch.s, ns.Lx, ns.Ly, 6, 4, _dev(cols, torch.int32), _dev(ch.normals))
+    plan.close()
