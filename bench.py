@@ -689,6 +689,14 @@ def run_adjoint(lb, torch, args, nsteps=500, every=50, nx=512):
                       dtype=torch.float32, device="cuda")
     phys = lb.Phys(C * C, MU)
     dt = float(lb.stable_dt(plan, lb.conserved_to_primitive(c0), s, C, MU).item())
+    # untimed warm-up: one checkpoint segment forward and backward, so that the
+    # autograd engine's device thread and the allocator's segment buffers exist
+    # before the timed pass (the first backward otherwise carries about a second of
+    # one-time set-up)
+    cw = c0.clone().requires_grad_(True)
+    lb.domain_kinetic_energy(lb.rollout(plan, lb.to_primitive(cw), dt, min(every, nsteps), phys,
+                                        checkpoint_every=every), s).backward()
+    del cw
     a, b = _events(torch)
     c = c0.clone().requires_grad_(True)
     torch.cuda.synchronize()

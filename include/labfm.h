@@ -73,6 +73,22 @@ typedef struct labfm_phys {
     double gy;
 } labfm_phys;
 
+/* Kinds of boundary node (labfm_plan_set_boundaries, Section 7.1). */
+#define LABFM_WALL 0     /* no-slip wall */
+#define LABFM_INFLOW 1   /* partially reflecting inflow */
+#define LABFM_OUTFLOW 2  /* partially reflecting outflow (eq. outflowL) */
+
+/* Parameters of the inflow and outflow conditions (Section 7.1): the relaxation
+ * coefficient sigma (0.278 in the paper), the length L of the relaxation terms
+ * (the paper does not give it; the domain's length along the flow), the reference
+ * Mach number M and the reference density rho0 of the inflow's L4. */
+typedef struct labfm_nscbc {
+    double sigma;
+    double L;
+    double mach;
+    double rho0;
+} labfm_nscbc;
+
 /* An operator prepared for the time-step kernels (opaque). */
 typedef struct labfm_plan labfm_plan;
 
@@ -330,6 +346,37 @@ int labfm_plan_create_batched(labfm_plan** plan, int n_inst, const int64_t* N_in
  */
 int labfm_plan_set_walls(labfm_plan* plan, int64_t n_wall, const int32_t* wall_nodes,
                          const double* wall_normal, void* stream);
+
+/*
+ * Boundaries of a plan of any of the three kinds of Section 7.1, each node with
+ * its inward unit normal: LABFM_WALL as labfm_plan_set_walls; LABFM_OUTFLOW and
+ * LABFM_INFLOW follow eq. lodi in the boundary frame (xi along n, eta along
+ * t = (-n_y, n_x)) with L2 = 0, the outgoing waves from eq. Ldef and the incoming
+ * ones
+ *   outflow (eq. outflowL): L4 = sigma/(2L) c (1 - M^2)(p - p_inf) + (1 - M) T4 + V4,
+ *   inflow: L3 = sigma c / L (u_eta - u_eta,IN) + T3 + V3,
+ *           L4 = sigma rho0 c^2 (1 - M^2) / L (u_xi - u_xi,IN) + T4 + V4,
+ * with the transverse and viscous terms T3, T4, V3, V4 as printed, and the viscous
+ * conditions dtau_etaxi/deta = 0 (outflow) and dtau_etaeta/deta = 0 (inflow) taken
+ * out of the viscous forces of eq. lodiu and eq. lodiv respectively.  The paper
+ * prints the inflow's relaxations on the other components ((u_xi - u_xi,IN) in L3,
+ * (u_eta - u_eta,IN) in L4); in eq. lodiu and lodiv L4 drives u_xi and L3 drives
+ * u_eta, so each relaxes its own component here.  The boundary nodes' first and
+ * second derivatives are the plan's own (labfm_build_wall_operator gives the
+ * "FD + 1D-LABFM" schemes of the Table), and they are not filtered (kappa = 0).
+ *   nodes   device, n int32;  normal: device, n x 2 doubles (inward unit normals)
+ *   kind    device, n int32 (LABFM_WALL, LABFM_INFLOW, LABFM_OUTFLOW)
+ *   target  device, n x 2 doubles: an inflow's (u_xi,IN, u_eta,IN); an outflow's
+ *           p_inf in the first (the second unused); unused for walls
+ *   params  host: sigma, L, M, rho0 (one set per plan)
+ * n = 0 removes the boundaries.  As labfm_plan_set_walls otherwise (plain stage
+ * grid, no adjoint, no batched plans, synchronises `stream`).
+ * Errors: EINVAL (node out of range or listed twice, normal not of unit length,
+ * unknown kind, sigma < 0, L <= 0, M outside [0, 1), rho0 <= 0), ENOMEM.
+ */
+int labfm_plan_set_boundaries(labfm_plan* plan, int64_t n, const int32_t* nodes, const double* normal,
+                              const int32_t* kind, const double* target, const labfm_nscbc* params,
+                              void* stream);
 
 /*
  * Per-instance time steps (host, n_instances values > 0).  Afterwards

@@ -23,6 +23,10 @@ Workloads (all doubly periodic, unit square unless stated):
 * ``channel(nx, ny, ...)``: a channel periodic in x between two walls, with the five
   uniform node rows along each wall that the boundary scheme of Section 7.1 needs;
   ``channel_walls(ns)`` lists its wall nodes' normal columns and normals.
+* ``open_box(nx, ny, ...)``: the same layout turned by 90 degrees, bounded in x by an
+  inflow (x = 0) and an outflow (x = Lx), periodic in y (Section 8.3's domain).
+* ``lamb_oseen_fields(xy, c, ...)``: Section 8.3's Lamb-Oseen vortex on a uniform
+  stream in (ln rho, u, v), centred in the unit box.
 * ``smooth_perturbation(xy, ...)``: a seeded band-limited random field
   (integer wavevectors with |k| <= kmax), normalised to unit maximum amplitude.
 """
@@ -270,6 +274,22 @@ def channel(nx: int, ny: int, m: int = 4, h_over_s: float | None = None, jitter:
                          "wall": np.array(wall), "nx": nx, "ny": ny, "h_over_s": hs})
 
 
+def open_box(nx: int, ny: int, m: int = 6, h_over_s: float | None = None, jitter: float = 0.1,
+             seed: int = 0, h_wall_over_s: float = 2.2) -> NodeSet:
+    """A box bounded in x with open boundaries at x = 0 (inflow) and x = nx s
+    (outflow), periodic in y on [0, ny s) (s = 1/ny): the ``channel`` node set with x
+    and y exchanged, so that five uniform columns of nodes (q = 0 on the boundary,
+    q = 1..4 at q s along the inward normal, the x axis) line each boundary and the
+    nodes in between are a jittered lattice.  meta as for ``channel``; ``wall`` is 0
+    for the boundary at x = 0 and 1 for x = nx s."""
+    ch = channel(ny, nx, m=m, h_over_s=h_over_s, jitter=jitter, seed=seed, h_wall_over_s=h_wall_over_s)
+    meta = dict(ch.meta)
+    meta["normal"] = ch.meta["normal"][:, ::-1].copy()
+    meta["nx"], meta["ny"] = nx, ny
+    meta["kind"] = "open_box"
+    return NodeSet(xy=ch.xy[:, ::-1].copy(), s=ch.s, h=ch.h, Lx=ch.Ly, Ly=ch.Lx, m=m, meta=meta)
+
+
 def channel_walls(ns: NodeSet) -> tuple[np.ndarray, np.ndarray]:
     """The walls of a ``channel`` node set as Section 7.1 describes them: for every
     wall node b (row q = 0) its normal column, the nodes of rows q = 0..4 with the
@@ -279,8 +299,9 @@ def channel_walls(ns: NodeSet) -> tuple[np.ndarray, np.ndarray]:
     key = {(int(w), int(c), int(q)): k for k, (w, c, q) in
            enumerate(zip(meta["wall"], meta["column"], meta["row"])) if q < 5}
     cols, normals = [], []
+    per_row = meta["ny"] if meta.get("kind") == "open_box" else meta["nx"]
     for w in (0, 1):
-        for c in range(meta["nx"]):
+        for c in range(per_row):
             cols.append([key[(w, c, q)] for q in range(5)])
             normals.append(meta["normal"][key[(w, c, 0)]])
     return np.asarray(cols, dtype=np.int32), np.asarray(normals, dtype=np.float64)
@@ -299,6 +320,30 @@ def tgv_fields(xy: np.ndarray, c: float = 10.0, H: float = 1.0) -> np.ndarray:
     v = np.sin(k * x) * np.cos(k * y)
     p = -(H / 4.0) * (np.cos(2 * k * x) + np.cos(2 * k * y))
     rho = 1.0 + p / (c * c)
+    return np.stack([np.log(rho), u, v]).astype(np.float64)
+
+
+LAMB_OSEEN_RC_OVER_H = 1.0 / 25.0     # vortex radius R_c = H / 25 (Section 8.3)
+LAMB_OSEEN_C_OVER_CH = 1.0 / 300.0    # vortex strength C = c H / 300
+LAMB_OSEEN_RE = 7500.0                # Re = U0 R_c rho0 / mu
+LAMB_OSEEN_MACH = 0.05                # Ma = U0 / c
+
+
+def lamb_oseen_fields(xy: np.ndarray, c: float, U0: float = 1.0, H: float = 1.0, rho0: float = 1.0,
+                      centre=(0.5, 0.5)) -> np.ndarray:
+    """Section 8.3's initial state as (ln rho, u, v): a Lamb-Oseen vortex of radius R_c
+    and strength C at ``centre`` on the uniform stream (U0, 0),
+        (u, v) = (U0, 0) + (C/rho0) (y', -x') / R_c^2 exp(-r'^2 / (2 R_c^2)),
+        rho = rho0 (1 - C^2 / (c^2 R_c^2) exp(-r'^2 / (2 R_c^2))),
+    with (x', y') = (x, y) - centre and R_c, C from the printed ratios."""
+    Rc = LAMB_OSEEN_RC_OVER_H * H
+    C = LAMB_OSEEN_C_OVER_CH * c * H
+    x = xy[:, 0] - centre[0]
+    y = xy[:, 1] - centre[1]
+    g = np.exp(-(x * x + y * y) / (2.0 * Rc * Rc))
+    u = U0 + C / rho0 * y / (Rc * Rc) * g
+    v = -C / rho0 * x / (Rc * Rc) * g
+    rho = rho0 * (1.0 - C * C / (c * c * Rc * Rc) * g)
     return np.stack([np.log(rho), u, v]).astype(np.float64)
 
 

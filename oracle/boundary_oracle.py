@@ -126,7 +126,10 @@ def strip_first_derivative_rows(ns, i: int, m1d: int = 4, h1d_over_s: float = 1.
     same = np.flatnonzero((meta["wall"] == wall) & (meta["row"] == q))
     same = same[same != i]
     d = ns.xy[same] - ns.xy[i]
-    d[:, 0] -= ns.Lx * np.round(d[:, 0] / ns.Lx)  # minimum image in x
+    if ns.meta.get("kind") == "open_box":  # periodic in y
+        d[:, 1] -= ns.Ly * np.round(d[:, 1] / ns.Ly)
+    else:  # the channel: periodic in x
+        d[:, 0] -= ns.Lx * np.round(d[:, 0] / ns.Lx)
     eta = d @ t
     h = h1d_over_s * s
     keep = np.abs(eta) <= 2 * h
@@ -139,6 +142,82 @@ def strip_first_derivative_rows(ns, i: int, m1d: int = 4, h1d_over_s: float = 1.
     d_eta = np.concatenate([np.zeros(5), w_eta, [-np.sum(w_eta)]])  # difference form
     wx, wy = boundary_to_xy(n, d_xi, d_eta)
     return nodes, wx, wy
+
+
+def _column_and_row(ns, i):
+    """Wall index, row q, column x-index and inward normal of a node of the five
+    uniform rows, and the nodes of its normal column (rows 0..4)."""
+    meta = ns.meta
+    wall, ix, q = meta["wall"][i], meta["column"][i], int(meta["row"][i])
+    col = np.array([int(np.flatnonzero((meta["wall"] == wall) & (meta["column"] == ix) &
+                                       (meta["row"] == r))[0]) for r in range(5)])
+    return wall, q, col, meta["normal"][i]
+
+
+def _row_eta_weights(ns, k, h1d_over_s=1.7, rbf=wendland_c2):
+    """1D LABFM (order 4, Appendix A) along the row of node k: its row neighbours
+    within 2h and the weights of d/deta and d2/deta2 (difference form)."""
+    meta = ns.meta
+    n = meta["normal"][k]
+    t = np.array([-n[1], n[0]])
+    same = np.flatnonzero((meta["wall"] == meta["wall"][k]) & (meta["row"] == meta["row"][k]))
+    same = same[same != k]
+    d = ns.xy[same] - ns.xy[k]
+    per_x = ns.meta.get("kind") != "open_box"  # the channel is periodic in x, the box in y
+    if per_x:
+        d[:, 0] -= ns.Lx * np.round(d[:, 0] / ns.Lx)
+    else:
+        d[:, 1] -= ns.Ly * np.round(d[:, 1] / ns.Ly)
+    eta = d @ t
+    h = h1d_over_s * float(ns.s[k])
+    keep = np.abs(eta) <= 2 * h
+    w1, w2, ok = labfm_1d_weights(eta[keep], h, 4, rbf)
+    if not ok:
+        raise ValueError("singular one-dimensional system")
+    return same[keep], w1, w2
+
+
+def boundary_node_second_derivatives(ns, i: int, h1d_over_s: float = 1.7):
+    """Second derivatives at a boundary node i0 (row q = 0) from "FD + 1D-LABFM"
+    (Table "Schemes for derivatives near boundaries"): d2/dxi2 by the one-sided
+    five-point second difference along the normal column, d2/deta2 by 1D LABFM
+    (C^eta2) along the boundary row, and the mixed d2/dxi deta (reading: the paper
+    does not give its form) as the one-sided five-point first difference along the
+    column of the rows' 1D LABFM d/deta (each column node's own row).  Rotated to
+    (x, y) with d/dx = n_x d/dxi - n_y d/deta, d/dy = n_y d/dxi + n_x d/deta.
+    Returns {node: (w_xx, w_xy, w_yy)} with sum_j w_j phi_j the derivative (the
+    node itself included; the weights of each derivative sum to zero)."""
+    _, q, col, n = _column_and_row(ns, i)
+    if q != 0:
+        raise ValueError("boundary nodes (row 0) only")
+    s = float(ns.s[i])
+    acc = {}
+
+    def add(node, xixi, xieta, etaeta):
+        v = acc.setdefault(int(node), np.zeros(3))
+        v += (xixi, xieta, etaeta)
+
+    w2 = [float(v) for v in fd_weights(FD_ONE_SIDED, 2)]
+    w1 = [float(v) for v in fd_weights(FD_ONE_SIDED, 1)]
+    for r in range(5):
+        add(col[r], w2[r] / s ** 2, 0.0, 0.0)
+    rows0, _, we2 = _row_eta_weights(ns, i, h1d_over_s)
+    for j, w in zip(rows0, we2):
+        add(j, 0.0, 0.0, w)
+    add(i, 0.0, 0.0, -float(np.sum(we2)))
+    for r in range(5):
+        nbrs, we1, _ = _row_eta_weights(ns, col[r], h1d_over_s)
+        c = w1[r] / s
+        for j, w in zip(nbrs, we1):
+            add(j, 0.0, c * w, 0.0)
+        add(col[r], 0.0, -c * float(np.sum(we1)), 0.0)
+    nx, ny = float(n[0]), float(n[1])
+    out = {}
+    for j, (a, b, c) in acc.items():
+        out[j] = (nx * nx * a - 2 * nx * ny * b + ny * ny * c,
+                  nx * ny * a + (nx * nx - ny * ny) * b - nx * ny * c,
+                  ny * ny * a + 2 * nx * ny * b + nx * nx * c)
+    return out
 
 
 # --------------------------------------------------------------------------
@@ -179,15 +258,17 @@ def channel_operator(ns, m: int = 4, m_wall: int = 4, h1d_over_s: float = 1.7):
       stencils |r_ji| <= 2 h_i inside the channel (periodic in x only);
     * rows q = 1, 2: d/dx, d/dy from ``strip_first_derivative_rows``; the second
       derivatives and the filter from LABFM of order m_wall on the same stencils;
-    * wall nodes q = 0: d/dx, d/dy from ``strip_first_derivative_rows`` only (the
-      velocity is held at zero there, the density follows eq. lodilnro), and
-      kappa = 0: the wall node is not filtered (a reading: the paper lists
-      "FD + 1D-LABFM" for its hyperviscous operator without the form of the mixed
-      terms).
+    * boundary nodes q = 0: d/dx, d/dy from ``strip_first_derivative_rows``, the
+      second derivatives from ``boundary_node_second_derivatives`` ("FD +
+      1D-LABFM"; a wall holds the velocity at zero and does not use them), and
+      kappa = 0: the boundary node is not filtered (a reading: the paper lists
+      "FD + 1D-LABFM" for its hyperviscous operator without its form).
+    ``ns`` is a ``labfm_inputs.channel`` (periodic in x) or ``open_box`` (periodic
+    in y) node set.
     """
     from . import labfm_oracle as core
-    rp, col = core.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly, periodic=(True, False))
-    per = (True, False)
+    per = (False, True) if ns.meta.get("kind") == "open_box" else (True, False)
+    rp, col = core.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly, periodic=per)
     bw = core.build_weights(ns.xy, ns.h, ns.s, rp, col, m, ns.Lx, ns.Ly, periodic=per)
     bw4 = bw if m_wall == m else core.build_weights(ns.xy, ns.h, ns.s, rp, col, m_wall, ns.Lx, ns.Ly,
                                                     periodic=per)
@@ -219,6 +300,14 @@ def channel_operator(ns, m: int = 4, m_wall: int = 4, h1d_over_s: float = 1.7):
                 v = acc.setdefault(int(j), np.zeros(6))
                 v[0] += ax
                 v[1] += ay
+            if row[i] == 0:
+                for j, (bxx, bxy, byy) in boundary_node_second_derivatives(ns, i, h1d_over_s).items():
+                    if j == i:
+                        continue
+                    v = acc.setdefault(int(j), np.zeros(6))
+                    v[2] += bxx
+                    v[3] += bxy
+                    v[4] += byy
         entries.append(sorted(acc.items()))
     row_ptr = np.zeros(N + 1, dtype=np.int64)
     row_ptr[1:] = np.cumsum([len(e) for e in entries])
@@ -261,4 +350,141 @@ def channel_time_step(q, dt: float, op, ns, c: float, mu: float, g=(0.0, 0.0)):
     from . import labfm_oracle as core
     row_ptr, col, w, kappa = op
     Q = core.rk_step(q, dt, lambda x: channel_rhs(x, op, ns, c, mu, g))
+    return core.filter_fields(Q, w[5], kappa, row_ptr, col)
+
+
+# --------------------------------------------------------------------------
+# Section 7.1: outflow and inflow in the characteristic (LODI) form
+# --------------------------------------------------------------------------
+
+WALL, INFLOW, OUTFLOW = 0, 1, 2
+
+
+def _boundary_frame(n, d, q):
+    """The node's state and derivatives in the boundary frame (xi along the inward
+    normal n, eta along t = (-n_y, n_x)), from the (x, y) derivatives d of
+    ``labfm_oracle.derivatives`` at the node and its state q = (ln rho, u, v)."""
+    nx, ny = float(n[0]), float(n[1])
+    tx, ty = -ny, nx
+    a, u, v = q
+
+    def dxi(f):
+        return nx * d[f + "x"] + ny * d[f + "y"]
+
+    def deta(f):
+        return tx * d[f + "x"] + ty * d[f + "y"]
+
+    def hess(f, p, r):  # p . H(f) . r
+        return (p[0] * r[0] * d[f + "xx"] + (p[0] * r[1] + p[1] * r[0]) * d[f + "xy"]
+                + p[1] * r[1] * d[f + "yy"])
+
+    N, T = (nx, ny), (tx, ty)
+    fr = {"u_xi": nx * u + ny * v, "u_eta": tx * u + ty * v,
+          "a_xi": dxi("a"), "a_eta": deta("a"),
+          "uxi_xi": nx * dxi("u") + ny * dxi("v"), "uxi_eta": nx * deta("u") + ny * deta("v"),
+          "ueta_xi": tx * dxi("u") + ty * dxi("v"), "ueta_eta": tx * deta("u") + ty * deta("v"),
+          "uxi_xixi": nx * hess("u", N, N) + ny * hess("v", N, N),
+          "uxi_etaeta": nx * hess("u", T, T) + ny * hess("v", T, T),
+          "uxi_xieta": nx * hess("u", N, T) + ny * hess("v", N, T),
+          "ueta_xixi": tx * hess("u", N, N) + ty * hess("v", N, N),
+          "ueta_etaeta": tx * hess("u", T, T) + ty * hess("v", T, T),
+          "ueta_xieta": tx * hess("u", N, T) + ty * hess("v", N, T)}
+    return fr
+
+
+def open_boundary_rhs(kind, n, d, q, c, mu, g, target, L, mach, rho0, sigma=0.278):
+    """d/dt of (ln rho, u, v) at an outflow or inflow node (eq. lodi with L2 = 0 for
+    isothermal flow), from the node's derivatives d (x, y components) and state q.
+    Outgoing waves from eq. Ldef; the incoming ones:
+      outflow (eq. outflowL): L4 = sigma/(2L) c (1 - M^2)(p - p_inf) + (1 - M) T4 + V4,
+        T4 = -1/2 (u_eta dp/deta + p du_eta/deta + rho c u_eta du_xi/deta),
+        V4 = mu c/2 (4/3 u_xi,xixi + u_xi,etaeta + 1/3 u_eta,xieta);  target = p_inf;
+      inflow: L3 = sigma c/L (u_eta - u_eta,IN) + T3 + V3,
+        L4 = sigma rho0 c^2 (1 - M^2)/L (u_xi - u_xi,IN) + T4 + V4,
+        T3 = -(u_eta du_eta/deta + dp/deta / rho),
+        V3 = mu/rho (4/3 u_eta,etaeta + u_eta,xixi + 1/3 u_xi,xieta);
+        target = (u_xi,IN, u_eta,IN).
+    (Reading: the paper prints the inflow's relaxations as (u_xi - u_xi,IN) in L3 and
+    (u_eta - u_eta,IN) in L4; with eq. lodiu and eq. lodiv only L4 drives u_xi and
+    L3 drives u_eta, so each relaxes its own component.)  The viscous conditions:
+    at an outflow dtau_etaxi/deta = 0 drops that term from the viscous force of
+    eq. lodiu, leaving dtau_xixi/dxi / mu = 4/3 u_xi,xixi - 2/3 u_eta,xieta; at an
+    inflow dtau_etaeta/deta = 0 drops it from eq. lodiv, leaving dtau_etaxi/dxi / mu
+    = u_eta,xixi + u_xi,xieta.  V3 and V4 keep the printed brackets.  Returns
+    (R_a, R_u, R_v) in (x, y) components; g = (g_x, g_y)."""
+    fr = _boundary_frame(n, d, q)
+    nx, ny = float(n[0]), float(n[1])
+    tx, ty = -ny, nx
+    a = q[0]
+    rho = np.exp(a)
+    p = c * c * rho
+    p_xi = c * c * rho * fr["a_xi"]
+    p_eta = c * c * rho * fr["a_eta"]
+    u_xi, u_eta = fr["u_xi"], fr["u_eta"]
+    L1 = 0.5 * (u_xi - c) * (p_xi - rho * c * fr["uxi_xi"])
+    visc_xi = 4.0 / 3.0 * fr["uxi_xixi"] + fr["uxi_etaeta"] + 1.0 / 3.0 * fr["ueta_xieta"]
+    visc_eta = 4.0 / 3.0 * fr["ueta_etaeta"] + fr["ueta_xixi"] + 1.0 / 3.0 * fr["uxi_xieta"]
+    T4 = -0.5 * (u_eta * p_eta + p * fr["ueta_eta"] + rho * c * u_eta * fr["uxi_eta"])
+    V4 = 0.5 * mu * c * visc_xi
+    if kind == OUTFLOW:
+        p_inf = target
+        L3 = u_xi * fr["ueta_xi"]
+        L4 = sigma / (2.0 * L) * c * (1.0 - mach * mach) * (p - p_inf) + (1.0 - mach) * T4 + V4
+        visc_xi_eq = 4.0 / 3.0 * fr["uxi_xixi"] - 2.0 / 3.0 * fr["ueta_xieta"]
+        visc_eta_eq = visc_eta
+    elif kind == INFLOW:
+        uxi_in, ueta_in = target
+        T3 = -(u_eta * fr["ueta_eta"] + p_eta / rho)
+        V3 = mu / rho * visc_eta
+        L3 = sigma * c / L * (u_eta - ueta_in) + T3 + V3
+        L4 = sigma * rho0 * c * c * (1.0 - mach * mach) / L * (u_xi - uxi_in) + T4 + V4
+        visc_xi_eq = visc_xi
+        visc_eta_eq = fr["ueta_xixi"] + fr["uxi_xieta"]
+    else:
+        raise ValueError("kind must be INFLOW or OUTFLOW")
+    g_xi = nx * g[0] + ny * g[1]
+    g_eta = tx * g[0] + ty * g[1]
+    Ra = -(L4 + L1) / (rho * c * c) - u_eta * fr["a_eta"] - fr["ueta_eta"]
+    Rxi = -(L4 - L1) / (rho * c) - u_eta * fr["uxi_eta"] + mu / rho * visc_xi_eq + g_xi
+    Reta = -L3 - u_eta * fr["ueta_eta"] - p_eta / rho + mu / rho * visc_eta_eq + g_eta
+    return Ra, nx * Rxi + tx * Reta, ny * Rxi + ty * Reta
+
+
+def boundary_rhs(q, op, bnd, c: float, mu: float, g=(0.0, 0.0)):
+    """d/dt of (ln rho, u, v) in a domain with walls, inflows and outflows: eq. icns
+    at every node but the boundary nodes, which follow ``wall_rhs`` (u held at zero)
+    or ``open_boundary_rhs``.  bnd: dict with nodes, normal (n, 2), kind (WALL,
+    INFLOW, OUTFLOW), target (n, 2: (u_xi,IN, u_eta,IN) for an inflow, p_inf in
+    column 0 for an outflow) and the scalars L, mach, rho0, sigma."""
+    from . import labfm_oracle as core
+    row_ptr, col, w, _ = op
+    R = core.rhs(q, w, row_ptr, col, c * c, mu, g)
+    d = core.derivatives(q, w, row_ptr, col)
+    for b, i in enumerate(bnd["nodes"]):
+        n = bnd["normal"][b]
+        di = {k: v[i] for k, v in d.items()}
+        qi = q[:, i]
+        kind = int(bnd["kind"][b])
+        if kind == WALL:
+            nx, ny = float(n[0]), float(n[1])
+            rho = np.exp(qi[0])
+            a_xi = nx * di["ax"] + ny * di["ay"]
+            du_xi = nx * (nx * di["ux"] + ny * di["uy"]) + ny * (nx * di["vx"] + ny * di["vy"])
+            t = (-ny, nx)
+            du_eta = t[0] * (t[0] * di["ux"] + t[1] * di["uy"]) + t[1] * (t[0] * di["vx"] + t[1] * di["vy"])
+            Ra, _ = wall_rhs(rho, c, c * c * rho * a_xi, du_xi, du_eta, nx * g[0] + ny * g[1])
+            R[:, i] = (Ra, 0.0, 0.0)
+        else:
+            target = bnd["target"][b][0] if kind == OUTFLOW else tuple(bnd["target"][b])
+            R[:, i] = open_boundary_rhs(kind, n, di, qi, c, mu, g, target, bnd["L"], bnd["mach"],
+                                        bnd["rho0"], bnd.get("sigma", 0.278))
+    return R
+
+
+def boundary_time_step(q, dt: float, op, bnd, c: float, mu: float, g=(0.0, 0.0)):
+    """One step with ``boundary_rhs``: the four RK stages, then the filter (Section 6)
+    with the operator's kappa (zero on the boundary nodes)."""
+    from . import labfm_oracle as core
+    row_ptr, col, w, kappa = op
+    Q = core.rk_step(q, dt, lambda x: boundary_rhs(x, op, bnd, c, mu, g))
     return core.filter_fields(Q, w[5], kappa, row_ptr, col)

@@ -47,6 +47,14 @@ class _Phys(ctypes.Structure):
                 ("gx", ctypes.c_double), ("gy", ctypes.c_double)]
 
 
+class _Nscbc(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("L", ctypes.c_double), ("mach", ctypes.c_double),
+                ("rho0", ctypes.c_double)]
+
+
+WALL, INFLOW, OUTFLOW = 0, 1, 2
+
+
 class _PlanInfo(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("nnz", ctypes.c_int64), ("nnz_padded", ctypes.c_int64),
                 ("dtype", ctypes.c_int32), ("group", ctypes.c_int32), ("block", ctypes.c_int32),
@@ -85,6 +93,7 @@ _SIGS = {
                                          _D, _P, _P, _I64, ctypes.POINTER(_I64), _P, _P, _P,
                                          ctypes.POINTER(_I64), _P]),
     "labfm_plan_set_walls": (_I32, [_P, _I64, _P, _P, _P]),
+    "labfm_plan_set_boundaries": (_I32, [_P, _I64, _P, _P, _P, _P, ctypes.POINTER(_Nscbc), _P]),
     "labfm_plan_create": (_I32, [ctypes.POINTER(_P), _I64, _I64, _I32, _P, _P, _P, _P, _P, _P]),
     "labfm_plan_destroy": (_I32, [_P]),
     "labfm_plan_get_info": (_I32, [_P, ctypes.POINTER(_PlanInfo)]),
@@ -378,6 +387,21 @@ class Plan:
             raise ValueError("wall_nodes int32 (n_wall,), wall_normal float64 (n_wall, 2)")
         _check(lib.labfm_plan_set_walls(self._h, n, _ptr(wall_nodes) if n else None,
                                         _ptr(wall_normal.contiguous()) if n else None, _stream(stream)))
+
+    def set_boundaries(self, nodes: torch.Tensor, normal: torch.Tensor, kind: torch.Tensor,
+                       target: torch.Tensor, sigma: float = 0.278, L: float = 1.0, mach: float = 0.0,
+                       rho0: float = 1.0, stream=None) -> None:
+        """labfm_plan_set_boundaries: walls, inflows and outflows (Section 7.1).  nodes,
+        kind: int32 (n,); normal, target: float64 (n, 2)."""
+        n = nodes.numel()
+        for t, dt_, shape, name in ((nodes, torch.int32, (n,), "nodes"), (kind, torch.int32, (n,), "kind"),
+                                    (normal, torch.float64, (n, 2), "normal"),
+                                    (target, torch.float64, (n, 2), "target")):
+            if t.dtype != dt_ or tuple(t.shape) != shape:
+                raise ValueError(f"{name} must be {dt_} of shape {shape}")
+        prm = _Nscbc(float(sigma), float(L), float(mach), float(rho0))
+        args = [_ptr(t.contiguous()) if n else None for t in (nodes, normal, kind, target)]
+        _check(lib.labfm_plan_set_boundaries(self._h, n, *args, ctypes.byref(prm), _stream(stream)))
 
     def set_wait_limit(self, limit_ns: int) -> None:
         """labfm_plan_set_wait_limit: limit of the staged kernel's bounded waits (ns;

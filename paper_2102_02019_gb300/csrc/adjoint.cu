@@ -84,7 +84,7 @@ template <typename T>
 PlanView<T> tview(const labfm_plan* p) {
     return PlanView<T>{p->N, p->tnnz_pad, p->trow_ptr, nullptr, static_cast<const T*>(p->tw),
                        static_cast<const T*>(p->twf), static_cast<const T*>(p->inv_s), p->dt_node, 0,
-                       nullptr, nullptr, 0, p->N};
+                       nullptr, nullptr, 0, p->N, nullptr, nullptr, T(0), T(0), T(0), T(0)};
 }
 
 // ---------------------------------------------------------------- pass A

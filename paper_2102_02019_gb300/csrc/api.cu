@@ -89,8 +89,12 @@ void free_plan_memory(labfm_plan* p) {
     cudaFree(p->dev_status);
     cudaFree(p->wall_slot);
     cudaFree(p->wall_n);
+    cudaFree(p->bnd_kind);
+    cudaFree(p->bnd_target);
     p->wall_slot = nullptr;
     p->wall_n = nullptr;
+    p->bnd_kind = nullptr;
+    p->bnd_target = nullptr;
     p->n_wall = 0;
     p->dev_status = nullptr;
     p->trow_ptr = nullptr;

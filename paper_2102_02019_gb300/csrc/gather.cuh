@@ -317,9 +317,12 @@ struct PlanView {
     const T* inv_s;
     const double* dt_node;  // per-node time step, or null for a uniform dt
     int pf;                 // L2 prefetch distance of the F32 record stream, in iterations (0: off)
-    const int32_t* wall_slot;  // per node: wall slot, -1 in the fluid (null: no walls)
-    const T* wall_n;           // per wall slot: inward unit normal (n_x, n_y)
+    const int32_t* wall_slot;  // per node: boundary slot, -1 in the fluid (null: no boundaries)
+    const T* wall_n;           // per slot: inward unit normal (n_x, n_y)
     int64_t n_lo, n_hi;        // nodes [n_lo, n_hi) of this launch (plain stage and filter grids)
+    const int32_t* bnd_kind;   // per slot: LABFM_WALL, LABFM_INFLOW, LABFM_OUTFLOW (null: all walls)
+    const T* bnd_target;       // per slot: (u_xi,IN, u_eta,IN) of an inflow, p_inf (first) of an outflow
+    T sigma, Lb, mach, rho0;   // relaxation coefficient, length, Mach number, reference density
 };
 
 // Operator loads of one 4-entry chunk starting at entry e (a multiple of 4).
@@ -395,7 +398,9 @@ template <typename T>
 PlanView<T> view(const labfm_plan* p) {
     return PlanView<T>{p->N,        p->nnz_pad,  p->row_ptr, p->col, static_cast<const T*>(p->w),
                        static_cast<const T*>(p->wf), static_cast<const T*>(p->inv_s), p->dt_node,
-                       p->prefetch, p->wall_slot, static_cast<const T*>(p->wall_n), 0, p->N};
+                       p->prefetch, p->wall_slot, static_cast<const T*>(p->wall_n), 0, p->N,
+                       p->bnd_kind, static_cast<const T*>(p->bnd_target), T(p->nscbc.sigma), T(p->nscbc.L),
+                       T(p->nscbc.mach), T(p->nscbc.rho0)};
 }
 
 // Chunk loaders for the gathers: from the plan's record stream in global memory,
@@ -666,15 +671,95 @@ __device__ __forceinline__ void wall_rhs(const T (&d)[12], T a, T inv_s, T c2, T
     Rv = T(0);
 }
 
-// eq. icns, or the wall's right-hand side at a wall node of a plan with walls.
+// Right-hand side at an outflow or inflow node (Section 7.1): eq. lodi in the
+// boundary frame (xi along the inward normal n, eta along t = (-n_y, n_x)) with
+// L2 = 0 (isothermal), the outgoing waves from eq. Ldef
+//   L1 = (u_xi - c)/2 (dp/dxi - rho c du_xi/dxi), L3 = u_xi du_eta/dxi (outflow),
+// and the incoming ones
+//   outflow (eq. outflowL): L4 = sigma/(2 L) c (1 - M^2)(p - p_inf) + (1 - M) T4 + V4;
+//   inflow: L3 = sigma c / L (u_eta - u_eta,IN) + T3 + V3,
+//           L4 = sigma rho0 c^2 (1 - M^2) / L (u_xi - u_xi,IN) + T4 + V4
+// (each relaxation drives its own velocity component: the reading taken where the
+// printed inflow relaxations are exchanged), with
+//   T4 = -1/2 (u_eta dp/deta + p du_eta/deta + rho c u_eta du_xi/deta),
+//   V4 = mu c / 2 (4/3 u_xi,xixi + u_xi,etaeta + 1/3 u_eta,xieta),
+//   T3 = -(u_eta du_eta/deta + dp/deta / rho),
+//   V3 = mu / rho (4/3 u_eta,etaeta + u_eta,xixi + 1/3 u_xi,xieta),
+// and the viscous conditions: dtau_etaxi/deta = 0 at an outflow (the viscous force
+// of eq. lodiu becomes 4/3 u_xi,xixi - 2/3 u_eta,xieta), dtau_etaeta/deta = 0 at an
+// inflow (that of eq. lodiv becomes u_eta,xixi + u_xi,xieta).
+template <typename T, bool SCALED>
+__device__ __forceinline__ void open_rhs(const T (&d)[12], T a, T u, T v, T inv_s, const Phys<T>& ph, T nx,
+                                         T ny, int kind, T t0, T t1, T sigma, T Lb, T mach, T rho0,
+                                         T& Ra, T& Ru, T& Rv) {
+    const T s1 = SCALED ? inv_s : T(1);
+    const T s2 = SCALED ? inv_s * inv_s : T(1);
+    const T ax = d[0] * s1, ay = d[1] * s1;
+    const T ux = d[2] * s1, uy = d[3] * s1, uxx = d[4] * s2, uxy = d[5] * s2, uyy = d[6] * s2;
+    const T vx = d[7] * s1, vy = d[8] * s1, vxx = d[9] * s2, vxy = d[10] * s2, vyy = d[11] * s2;
+    const T tx = -ny, ty = nx;
+    // first derivatives in the boundary frame
+    const T a_xi = nx * ax + ny * ay, a_eta = tx * ax + ty * ay;
+    const T u_n = nx * ux + ny * uy, u_t = tx * ux + ty * uy;  // du/dxi, du/deta
+    const T v_n = nx * vx + ny * vy, v_t = tx * vx + ty * vy;
+    const T u_xi = nx * u + ny * v, u_eta = tx * u + ty * v;
+    const T uxi_xi = nx * u_n + ny * v_n, uxi_eta = nx * u_t + ny * v_t;
+    const T ueta_xi = tx * u_n + ty * v_n, ueta_eta = tx * u_t + ty * v_t;
+    // second derivatives: p . H . r for the Hessians of u and v
+    const T u_nn = nx * nx * uxx + 2 * nx * ny * uxy + ny * ny * uyy;
+    const T u_tt = tx * tx * uxx + 2 * tx * ty * uxy + ty * ty * uyy;
+    const T u_nt = nx * tx * uxx + (nx * ty + ny * tx) * uxy + ny * ty * uyy;
+    const T v_nn = nx * nx * vxx + 2 * nx * ny * vxy + ny * ny * vyy;
+    const T v_tt = tx * tx * vxx + 2 * tx * ty * vxy + ty * ty * vyy;
+    const T v_nt = nx * tx * vxx + (nx * ty + ny * tx) * vxy + ny * ty * vyy;
+    const T uxi_xixi = nx * u_nn + ny * v_nn, uxi_etaeta = nx * u_tt + ny * v_tt, uxi_xieta = nx * u_nt + ny * v_nt;
+    const T ueta_xixi = tx * u_nn + ty * v_nn, ueta_etaeta = tx * u_tt + ty * v_tt, ueta_xieta = tx * u_nt + ty * v_nt;
+    const T c2 = ph.c2, c = sqrt(c2), mu = ph.mu;
+    const T rho = exp_pos(a);
+    const T p = c2 * rho, p_xi = c2 * rho * a_xi, p_eta = c2 * rho * a_eta;
+    const T L1 = T(0.5) * (u_xi - c) * (p_xi - rho * c * uxi_xi);
+    const T third = T(1) / T(3), four_thirds = T(4) / T(3), two_thirds = T(2) / T(3);
+    const T visc_xi = four_thirds * uxi_xixi + uxi_etaeta + third * ueta_xieta;
+    const T visc_eta = four_thirds * ueta_etaeta + ueta_xixi + third * uxi_xieta;
+    const T T4 = T(-0.5) * (u_eta * p_eta + p * ueta_eta + rho * c * u_eta * uxi_eta);
+    const T V4 = T(0.5) * mu * c * visc_xi;
+    T L3, L4, vxi, veta;
+    if (kind == LABFM_OUTFLOW) {
+        L3 = u_xi * ueta_xi;
+        L4 = sigma / (T(2) * Lb) * c * (T(1) - mach * mach) * (p - t0) + (T(1) - mach) * T4 + V4;
+        vxi = four_thirds * uxi_xixi - two_thirds * ueta_xieta;
+        veta = visc_eta;
+    } else {
+        const T T3 = -(u_eta * ueta_eta + p_eta / rho);
+        const T V3 = mu / rho * visc_eta;
+        L3 = sigma * c / Lb * (u_eta - t1) + T3 + V3;
+        L4 = sigma * rho0 * c2 * (T(1) - mach * mach) / Lb * (u_xi - t0) + T4 + V4;
+        vxi = visc_xi;
+        veta = ueta_xixi + uxi_xieta;
+    }
+    const T g_xi = nx * ph.gx + ny * ph.gy, g_eta = tx * ph.gx + ty * ph.gy;
+    Ra = -(L4 + L1) / (rho * c2) - u_eta * a_eta - ueta_eta;
+    const T Rxi = -(L4 - L1) / (rho * c) - u_eta * uxi_eta + mu / rho * vxi + g_xi;
+    const T Reta = -L3 - u_eta * ueta_eta - p_eta / rho + mu / rho * veta + g_eta;
+    Ru = nx * Rxi + tx * Reta;
+    Rv = ny * Rxi + ty * Reta;
+}
+
+// eq. icns, or the boundary's right-hand side at a boundary node of a plan with
+// boundaries (a wall, an outflow or an inflow).
 template <typename T, bool SCALED, bool WALL>
 __device__ __forceinline__ void node_rhs(const PlanView<T>& P, int i, const T (&d)[12], T a, T u, T v,
                                          T inv_s, const Phys<T>& ph, T& Ra, T& Ru, T& Rv) {
     if (WALL) {
         const int slot = P.wall_slot[i];
         if (slot >= 0) {
-            wall_rhs<T, SCALED>(d, a, inv_s, ph.c2, ph.gx, ph.gy, P.wall_n[2 * slot], P.wall_n[2 * slot + 1],
-                                Ra, Ru, Rv);
+            const T nx = P.wall_n[2 * slot], ny = P.wall_n[2 * slot + 1];
+            const int kind = P.bnd_kind ? P.bnd_kind[slot] : LABFM_WALL;
+            if (kind == LABFM_WALL)
+                wall_rhs<T, SCALED>(d, a, inv_s, ph.c2, ph.gx, ph.gy, nx, ny, Ra, Ru, Rv);
+            else
+                open_rhs<T, SCALED>(d, a, u, v, inv_s, ph, nx, ny, kind, P.bnd_target[2 * slot],
+                                    P.bnd_target[2 * slot + 1], P.sigma, P.Lb, P.mach, P.rho0, Ra, Ru, Rv);
             return;
         }
     }

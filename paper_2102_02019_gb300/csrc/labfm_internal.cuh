@@ -121,6 +121,9 @@ struct labfm_plan {
     int32_t* wall_slot = nullptr;
     void* wall_n = nullptr;
     int64_t n_wall = 0;
+    int32_t* bnd_kind = nullptr;   // per slot: LABFM_WALL / INFLOW / OUTFLOW (null: all walls)
+    void* bnd_target = nullptr;    // per slot, 2 values (dtype): inflow velocities or outflow p_inf
+    labfm_nscbc nscbc = {0.278, 1.0, 0.0, 1.0};
     // launch timing (labfm_plan_set_profiling): event pairs around launches
     bool profiling = false;
     cudaEvent_t* prof_ev = nullptr;  // 2 * prof_cap events
@@ -162,8 +165,10 @@ enum ProfKind { kProfStage = 0, kProfFilter = 1, kProfStages4 = 2, kProfRecStage
 int prof_begin(labfm_plan* p, int kind, cudaStream_t st);
 void prof_end(labfm_plan* p, int idx, cudaStream_t st);
 
-// Walls of a plan (walls.cu): wall slots and normals; n_wall = 0 removes them.
-int set_walls(labfm_plan* p, int64_t n_wall, const int32_t* nodes, const double* normal, cudaStream_t st);
+// Boundaries of a plan (walls.cu): slots, normals, and (kind and target null:
+// walls) the kinds and targets; n = 0 removes them.
+int set_walls(labfm_plan* p, int64_t n_wall, const int32_t* nodes, const double* normal, const int32_t* kind,
+              const double* target, cudaStream_t st);
 
 // Plan packing (step.cu): concatenates the instances block-diagonally.
 int pack_plan(labfm_plan* p, const PlanInput* in, int n_inst, cudaStream_t st);

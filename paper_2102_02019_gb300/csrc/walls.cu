@@ -11,9 +11,12 @@
 //     column (asymmetric at q = 1, central at q = 2) and one-dimensional LABFM of
 //     order 4 along the row of the same q (Appendix A), rotated to (x, y); second
 //     derivatives and the filter from LABFM of order m_wall;
-//   wall nodes q = 0: d/dx, d/dy from the one-sided five-point difference and
-//     1D LABFM; no second derivatives and no filter (kappa = 0): the velocity is
-//     held at zero there and ln rho follows the LODI equation of the wall.
+//   boundary nodes q = 0: d/dx, d/dy from the one-sided five-point difference and
+//     1D LABFM; second derivatives from the one-sided second difference along the
+//     column, 1D LABFM d2/deta2 along the boundary row, and d2/dxi deta as the
+//     one-sided first difference along the column of the rows' 1D LABFM d/deta;
+//     no filter (kappa = 0).  A wall holds the velocity at zero there and does not
+//     use the second derivatives; an outflow or inflow follows its LODI equations.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -31,7 +34,8 @@ namespace {
 constexpr int kColumn = 5;    // nodes of a normal column, q = 0..4
 constexpr int kStripRows = 3; // rows with boundary-specific first derivatives
 constexpr int kOrder1d = 4;   // order of the one-dimensional LABFM along the rows
-constexpr int kMaxRow = 64;   // row neighbours per node handled by the merge
+constexpr int kMaxRow = 16;   // row neighbours per node handled by the merge
+constexpr int kMaxEnt = kColumn + kColumn * kMaxRow;  // strip entries of a boundary node
 
 // Five-point first-derivative weights (units of 1/s) for the rows q = 0, 1, 2 of a
 // normal column over its points r = 0..4 (offsets r - q): the derivative at 0 of
@@ -39,10 +43,30 @@ constexpr int kMaxRow = 64;   // row neighbours per node handled by the merge
 //   w_r = sum_{k != r} prod_{l != r, k} (0 - o_l) / prod_{l != r} (o_r - o_l).
 struct FdTable {
     double w[kStripRows][kColumn];
+    double w2[kColumn];  // second derivative at q = 0 (one-sided), units of 1/s^2
 };
 
 FdTable fd_first_derivative_table() {
     FdTable t{};
+    // second derivative at 0 of the Lagrange interpolant over offsets 0..4:
+    //   w2_r = sum_{k != r} sum_{l != r, k} prod_{m != r, k, l} (0 - o_m) / prod_{m != r} (o_r - o_m)
+    for (int r = 0; r < kColumn; ++r) {
+        double den = 1.0;
+        for (int m = 0; m < kColumn; ++m)
+            if (m != r) den *= double(r - m);
+        double num = 0.0;
+        for (int k = 0; k < kColumn; ++k) {
+            if (k == r) continue;
+            for (int l = 0; l < kColumn; ++l) {
+                if (l == r || l == k) continue;
+                double p = 1.0;
+                for (int m = 0; m < kColumn; ++m)
+                    if (m != r && m != k && m != l) p *= -double(m);
+                num += p;
+            }
+        }
+        t.w2[r] = num / den;
+    }
     for (int q = 0; q < kStripRows; ++q) {
         double o[kColumn];
         for (int r = 0; r < kColumn; ++r) o[r] = double(r - q);
@@ -105,16 +129,16 @@ __device__ __forceinline__ double wendland_c2(double q) {
     return a2 * a2 * (1.0 + 2.0 * q);
 }
 
-// One-dimensional LABFM of order 4 (Appendix A) for d/deta at a node from the
-// offsets eta_j of its row neighbours: monomials eta^k / k!, k = 1..4; ABFs
-// psi(|eta|/h) H_k(eta / (h sqrt 2)) / sqrt(2^k) with physicists' Hermite H_k;
-// M = sum_j X_j (x) W_j; M Psi = e_1 (the selector of d/deta); w_j = W_j . Psi.
-// Returns false for a singular M.
-__device__ bool labfm_1d_weights(const double* eta, int n, double h, double* w) {
+// One-dimensional LABFM of order 4 (Appendix A) for d/deta and d2/deta2 at a node
+// from the offsets eta_j of its row neighbours: monomials eta^k / k!, k = 1..4;
+// ABFs psi(|eta|/h) H_k(eta / (h sqrt 2)) / sqrt(2^k) with physicists' Hermite H_k;
+// M = sum_j X_j (x) W_j; M Psi = [e_1 e_2] (the selectors of d/deta and
+// d2/deta2); w_j = W_j . Psi.  w2 may be null.  Returns false for a singular M.
+__device__ bool labfm_1d_weights(const double* eta, int n, double h, double* w, double* w2) {
     constexpr int K = kOrder1d;
-    double M[K][K + 1];
+    double M[K][K + 2];
     for (int a = 0; a < K; ++a)
-        for (int c = 0; c <= K; ++c) M[a][c] = (a == 0 && c == K) ? 1.0 : 0.0;
+        for (int c = 0; c < K + 2; ++c) M[a][c] = (a == 0 && c == K) || (a == 1 && c == K + 1) ? 1.0 : 0.0;
     const double inv_sqrt2 = 0.70710678118654752440;
     const double inv_norm[K] = {inv_sqrt2, 0.5, 0.5 * inv_sqrt2, 0.25};  // 1 / sqrt(2^k)
     for (int j = 0; j < n; ++j) {
@@ -141,22 +165,23 @@ __device__ bool labfm_1d_weights(const double* eta, int n, double h, double* w) 
             if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
         if (!(fabs(M[piv][c]) > 0.0)) return false;
         if (piv != c)
-            for (int k = 0; k <= K; ++k) {
+            for (int k = 0; k < K + 2; ++k) {
                 const double t = M[c][k];
                 M[c][k] = M[piv][k];
                 M[piv][k] = t;
             }
         for (int r = c + 1; r < K; ++r) {
             const double f = M[r][c] / M[c][c];
-            for (int k = c; k <= K; ++k) M[r][k] -= f * M[c][k];
+            for (int k = c; k < K + 2; ++k) M[r][k] -= f * M[c][k];
         }
     }
-    double psi_sol[K];
-    for (int c = K - 1; c >= 0; --c) {
-        double v = M[c][K];
-        for (int k = c + 1; k < K; ++k) v -= M[c][k] * psi_sol[k];
-        psi_sol[c] = v / M[c][c];
-    }
+    double psi_sol[2][K];
+    for (int rhs = 0; rhs < 2; ++rhs)
+        for (int c = K - 1; c >= 0; --c) {
+            double v = M[c][K + rhs];
+            for (int k = c + 1; k < K; ++k) v -= M[c][k] * psi_sol[rhs][k];
+            psi_sol[rhs][c] = v / M[c][c];
+        }
     for (int j = 0; j < n; ++j) {
         const double e = eta[j];
         const double psi = wendland_c2(fabs(e) / h);
@@ -165,9 +190,14 @@ __device__ bool labfm_1d_weights(const double* eta, int n, double h, double* w) 
         H[0] = 1.0;
         H[1] = 2.0 * z;
         for (int k = 1; k < K; ++k) H[k + 1] = 2.0 * z * H[k] - 2.0 * k * H[k - 1];
-        double v = 0.0;
-        for (int c = 0; c < K; ++c) v += psi * H[c + 1] * inv_norm[c] * psi_sol[c];
+        double v = 0.0, v2 = 0.0;
+        for (int c = 0; c < K; ++c) {
+            const double W = psi * H[c + 1] * inv_norm[c];
+            v += W * psi_sol[0][c];
+            v2 += W * psi_sol[1][c];
+        }
         w[j] = v;
+        if (w2) w2[j] = v2;
     }
     return true;
 }
@@ -193,78 +223,140 @@ struct WallOpArgs {
     const double* wB;
     const double* kB;
     const int32_t* stB;
-    // row neighbours (wall indices) of rows q = 0, 1, 2
-    const int32_t* rpR[kStripRows];
-    const int32_t* colR[kStripRows];
+    // row neighbours (wall indices) of the rows q = 0..4
+    const int32_t* rpR[kColumn];
+    const int32_t* colR[kColumn];
 };
 
-// Per-warp scratch (shared memory) of the strip entries of one node.
+// Per-warp scratch (shared memory) of the strip entries of one node: node and
+// its five RHS weights (d/dx, d/dy, d2/dx2, d2/dxdy, d2/dy2).
 struct StripScratch {
-    int32_t node[kColumn + kMaxRow];
-    double wx[kColumn + kMaxRow];
-    double wy[kColumn + kMaxRow];
+    int32_t node[kMaxEnt];
+    double w[5][kMaxEnt];
     double eta[kMaxRow];
-    double weta[kMaxRow];
+    double w1[kMaxRow];
+    double w2[kMaxRow];
 };
 constexpr int kMergeWarps = 4;  // warps per block of the merge kernel
 
-// The strip entries of node i (row q of wall node b): the column nodes (r != q)
-// with the five-point weight along the normal, and the row neighbours with the
-// 1D LABFM weight along the tangent, rotated to (x, y), sorted by node.  Returns
-// the number of entries, or -1 when the row has more than kMaxRow neighbours,
-// -2 for a singular 1D system.
-__device__ int strip_entries(const WallOpArgs& A, int64_t i, int b, int q, StripScratch& S) {
-    int32_t* node = S.node;
-    double* wx = S.wx;
-    double* wy = S.wy;
+// 1D LABFM along row r of column b at its node k (support h1d_over_s s_k):
+// its row neighbours into S.node[at..], the d/deta (and, if want2, d2/deta2)
+// weights into S.w1, S.w2.  Returns the number of neighbours, -1 beyond kMaxRow,
+// -2 for a singular system.
+__device__ int row_weights(const WallOpArgs& A, int b, int r, bool want2, StripScratch& S, int* nodes) {
+    const int32_t k = A.wall_column[int64_t(b) * kColumn + r];
     const double nx = A.wall_normal[2 * b], ny = A.wall_normal[2 * b + 1];
-    const double si = A.s[i];
-    const double xi = A.xy[2 * i], yi = A.xy[2 * i + 1];
-    int n = 0;
-    for (int r = 0; r < kColumn; ++r) {
-        if (r == q) continue;
-        const double wxi = A.fd.w[q][r] / si;
-        node[n] = A.wall_column[int64_t(b) * kColumn + r];
-        wx[n] = nx * wxi;
-        wy[n] = ny * wxi;
-        ++n;
-    }
-    const int e0 = A.rpR[q][b], e1 = A.rpR[q][b + 1];
+    const double tx = -ny, ty = nx;
+    const double xk = A.xy[2 * k], yk = A.xy[2 * k + 1];
+    const int e0 = A.rpR[r][b], e1 = A.rpR[r][b + 1];
     const int nr = e1 - e0;
     if (nr > kMaxRow) return -1;
-    double* eta = S.eta;
-    double* weta = S.weta;
-    const double tx = -ny, ty = nx;
     for (int e = 0; e < nr; ++e) {
-        const int bj = A.colR[q][e0 + e];
-        const int32_t j = A.wall_column[int64_t(bj) * kColumn + q];
-        const double dx = min_image(A.xy[2 * j] - xi, A.Lx, A.px);
-        const double dy = min_image(A.xy[2 * j + 1] - yi, A.Ly, A.py);
-        eta[e] = dx * tx + dy * ty;
-        node[n + e] = j;
+        const int bj = A.colR[r][e0 + e];
+        const int32_t j = A.wall_column[int64_t(bj) * kColumn + r];
+        const double dx = min_image(A.xy[2 * j] - xk, A.Lx, A.px);
+        const double dy = min_image(A.xy[2 * j + 1] - yk, A.Ly, A.py);
+        S.eta[e] = dx * tx + dy * ty;
+        nodes[e] = j;
     }
-    if (nr > 0 && !labfm_1d_weights(eta, nr, A.h1d_over_s * si, weta)) return -2;
-    for (int e = 0; e < nr; ++e) {
-        wx[n + e] = -ny * weta[e];
-        wy[n + e] = nx * weta[e];
+    if (nr > 0 && !labfm_1d_weights(S.eta, nr, A.h1d_over_s * A.s[k], S.w1, want2 ? S.w2 : nullptr))
+        return -2;
+    return nr;
+}
+
+// The strip entries of node i (row q of wall node b), rotated to (x, y) with
+// d/dx = n_x d/dxi - n_y d/deta, d/dy = n_y d/dxi + n_x d/deta:
+//   d/dxi: the five-point difference along the column (rows r != q);
+//   d/deta: 1D LABFM along the node's row;
+//   for a boundary node (q = 0) also d2/dxi2 (the one-sided second difference
+//   along the column), d2/deta2 (1D LABFM along row 0) and d2/dxi deta (the
+//   one-sided first difference along the column of each row's 1D LABFM d/deta:
+//   the row neighbours of column node r with weight w1_r(xi) w^eta_rj, and node r
+//   itself with minus their sum).
+// Entries are summed per node and sorted; the node itself is left out (the
+// difference form).  Returns the number of entries, -1 when a row has more than
+// kMaxRow neighbours, -2 for a singular 1D system.
+__device__ int strip_entries(const WallOpArgs& A, int64_t i, int b, int q, StripScratch& S) {
+    const double nx = A.wall_normal[2 * b], ny = A.wall_normal[2 * b + 1];
+    const double si = A.s[i];
+    int n = 0;
+    auto add = [&](int32_t j, double ax, double ay, double axx, double axy, double ayy) {
+        S.node[n] = j;
+        S.w[0][n] = ax;
+        S.w[1][n] = ay;
+        S.w[2][n] = axx;
+        S.w[3][n] = axy;
+        S.w[4][n] = ayy;
+        ++n;
+    };
+    for (int r = 0; r < kColumn; ++r) {
+        if (r == q) continue;
+        const double c1 = A.fd.w[q][r] / si;
+        const double c2 = q == 0 ? A.fd.w2[r] / (si * si) : 0.0;
+        add(A.wall_column[int64_t(b) * kColumn + r], nx * c1, ny * c1, nx * nx * c2, nx * ny * c2, ny * ny * c2);
     }
-    n += nr;
-    // insertion sort by node (the column and the row are disjoint sets)
+    {
+        const int nr = row_weights(A, b, q, q == 0, S, S.node + n);
+        if (nr < 0) return nr;
+        for (int e = 0; e < nr; ++e) {
+            const double w1 = S.w1[e], w2 = q == 0 ? S.w2[e] : 0.0;
+            S.w[0][n + e] = -ny * w1;
+            S.w[1][n + e] = nx * w1;
+            S.w[2][n + e] = ny * ny * w2;
+            S.w[3][n + e] = -nx * ny * w2;
+            S.w[4][n + e] = nx * nx * w2;
+        }
+        n += nr;
+    }
+    if (q == 0) {
+        for (int r = 0; r < kColumn; ++r) {
+            const int nr = row_weights(A, b, r, false, S, S.node + n);
+            if (nr < 0) return nr;
+            const double cm = A.fd.w[0][r] / si;
+            double sum = 0.0;
+            for (int e = 0; e < nr; ++e) {
+                const double m = cm * S.w1[e];
+                sum += S.w1[e];
+                S.w[0][n + e] = 0.0;
+                S.w[1][n + e] = 0.0;
+                S.w[2][n + e] = -2.0 * nx * ny * m;
+                S.w[3][n + e] = (nx * nx - ny * ny) * m;
+                S.w[4][n + e] = 2.0 * nx * ny * m;
+            }
+            n += nr;
+            if (r > 0) {  // the column node's own term (node i's own is left out)
+                const double m = -cm * sum;
+                add(A.wall_column[int64_t(b) * kColumn + r], 0.0, 0.0, -2.0 * nx * ny * m,
+                    (nx * nx - ny * ny) * m, 2.0 * nx * ny * m);
+            }
+        }
+    }
+    // insertion sort by node, then sum the entries of one node
     for (int a = 1; a < n; ++a) {
-        const int32_t kn = node[a];
-        const double ax = wx[a], ay = wy[a];
+        const int32_t kn = S.node[a];
+        double v[5];
+        for (int d = 0; d < 5; ++d) v[d] = S.w[d][a];
         int c = a - 1;
-        while (c >= 0 && node[c] > kn) {
-            node[c + 1] = node[c];
-            wx[c + 1] = wx[c];
-            wy[c + 1] = wy[c];
+        while (c >= 0 && S.node[c] > kn) {
+            S.node[c + 1] = S.node[c];
+            for (int d = 0; d < 5; ++d) S.w[d][c + 1] = S.w[d][c];
             --c;
         }
-        node[c + 1] = kn;
-        wx[c + 1] = ax;
-        wy[c + 1] = ay;
+        S.node[c + 1] = kn;
+        for (int d = 0; d < 5; ++d) S.w[d][c + 1] = v[d];
     }
-    return n;
+    int m = 0;
+    for (int a = 0; a < n; ++a) {
+        if (S.node[a] == int32_t(i)) continue;
+        if (m > 0 && S.node[m - 1] == S.node[a]) {
+            for (int d = 0; d < 5; ++d) S.w[d][m - 1] += S.w[d][a];
+        } else {
+            S.node[m] = S.node[a];
+            for (int d = 0; d < 5; ++d) S.w[d][m] = S.w[d][a];
+            ++m;
+        }
+    }
+    return m;
 }
 
 // Warp per node.  FILL = false: the number of entries of each merged row (and the
@@ -303,8 +395,6 @@ __global__ void k_wall_merge(WallOpArgs A, int32_t* __restrict__ cnt, const int3
         const int b = code / kColumn;
         const int ns = strip_entries(A, i, b, q, S);
         const int32_t* node = S.node;
-        const double* wx = S.wx;
-        const double* wy = S.wy;
         const bool labfm = q > 0;  // rows 1, 2 keep the LABFM second derivatives and filter
         if (ns < 0) {  // too many row neighbours or a singular 1D system: an empty row
             if (!FILL) {
@@ -324,12 +414,10 @@ __global__ void k_wall_merge(WallOpArgs A, int32_t* __restrict__ cnt, const int3
             const int32_t j = ja < js ? ja : js;
             if (FILL) {
                 double v[6] = {0, 0, 0, 0, 0, 0};
-                if (js == j) {
-                    v[0] = wx[ks];
-                    v[1] = wy[ks];
-                }
-                if (ja == j)
-                    for (int d = 2; d < 6; ++d) v[d] = A.wB[d * A.nnzA + ka];
+                if (js == j)
+                    for (int d = 0; d < 5; ++d) v[d] = S.w[d][ks];
+                if (ja == j)  // rows 1, 2: second derivatives and filter from LABFM of order m_wall
+                    for (int d = 2; d < 6; ++d) v[d] += A.wB[d * A.nnzA + ka];
                 col[dst + n] = j;
                 for (int d = 0; d < 6; ++d) w[d * nnz + dst + n] = v[d];
             }
@@ -389,7 +477,9 @@ int stencils_into(Scratch& sc, const double* xy, const double* h, int64_t n, dou
 namespace {
 template <typename T>
 __global__ void k_set_walls(int64_t n_wall, const int32_t* __restrict__ nodes, const double* __restrict__ normal,
-                            int64_t N, int32_t* __restrict__ slot, T* __restrict__ wn, int* __restrict__ bad) {
+                            const int32_t* __restrict__ kind, const double* __restrict__ target, int64_t N,
+                            int32_t* __restrict__ slot, T* __restrict__ wn, int32_t* __restrict__ wk,
+                            T* __restrict__ wt, int* __restrict__ bad) {
     for (int64_t b = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; b < n_wall;
          b += int64_t(gridDim.x) * blockDim.x) {
         const int32_t i = nodes[b];
@@ -402,49 +492,71 @@ __global__ void k_set_walls(int64_t n_wall, const int32_t* __restrict__ nodes, c
         if (!(fabs(nx * nx + ny * ny - 1.0) <= 1e-12)) atomicOr(bad, 4);
         wn[2 * b] = T(nx);
         wn[2 * b + 1] = T(ny);
+        if (wk) {
+            const int32_t k = kind[b];
+            if (k != LABFM_WALL && k != LABFM_INFLOW && k != LABFM_OUTFLOW) atomicOr(bad, 8);
+            wk[b] = k;
+            wt[2 * b] = T(target[2 * b]);
+            wt[2 * b + 1] = T(target[2 * b + 1]);
+        }
     }
+}
+
+void free_boundaries(labfm_plan* p) {
+    cudaFree(p->wall_slot);
+    cudaFree(p->wall_n);
+    cudaFree(p->bnd_kind);
+    cudaFree(p->bnd_target);
+    p->wall_slot = nullptr;
+    p->wall_n = nullptr;
+    p->bnd_kind = nullptr;
+    p->bnd_target = nullptr;
+    p->n_wall = 0;
 }
 }  // namespace
 
-int set_walls(labfm_plan* p, int64_t n_wall, const int32_t* nodes, const double* normal, cudaStream_t st) {
-    cudaFree(p->wall_slot);
-    cudaFree(p->wall_n);
-    p->wall_slot = nullptr;
-    p->wall_n = nullptr;
-    p->n_wall = 0;
+int set_walls(labfm_plan* p, int64_t n_wall, const int32_t* nodes, const double* normal, const int32_t* kind,
+              const double* target, cudaStream_t st) {
+    free_boundaries(p);
     if (n_wall == 0) return LABFM_OK;
     const size_t es = p->dtype == LABFM_F32 ? sizeof(float) : sizeof(double);
     LABFM_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&p->wall_slot), size_t(p->N) * sizeof(int32_t)));
     LABFM_CUDA_TRY(cudaMalloc(&p->wall_n, size_t(n_wall) * 2 * es));
+    if (kind) {
+        LABFM_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&p->bnd_kind), size_t(n_wall) * sizeof(int32_t)));
+        LABFM_CUDA_TRY(cudaMalloc(&p->bnd_target, size_t(n_wall) * 2 * es));
+    }
     int* bad = nullptr;
     LABFM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&bad), sizeof(int), st));
     cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(p->wall_slot, 0xff, size_t(p->N) * sizeof(int32_t), st);
     if (e == cudaSuccess) {
         if (p->dtype == LABFM_F32)
-            k_set_walls<float><<<grid_of(n_wall), 256, 0, st>>>(n_wall, nodes, normal, p->N, p->wall_slot,
-                                                                  static_cast<float*>(p->wall_n), bad);
+            k_set_walls<float><<<grid_of(n_wall), 256, 0, st>>>(n_wall, nodes, normal, kind, target, p->N,
+                                                                  p->wall_slot, static_cast<float*>(p->wall_n),
+                                                                  p->bnd_kind, static_cast<float*>(p->bnd_target),
+                                                                  bad);
         else
-            k_set_walls<double><<<grid_of(n_wall), 256, 0, st>>>(n_wall, nodes, normal, p->N, p->wall_slot,
-                                                                   static_cast<double*>(p->wall_n), bad);
+            k_set_walls<double><<<grid_of(n_wall), 256, 0, st>>>(n_wall, nodes, normal, kind, target, p->N,
+                                                                   p->wall_slot, static_cast<double*>(p->wall_n),
+                                                                   p->bnd_kind, static_cast<double*>(p->bnd_target),
+                                                                   bad);
         e = cudaGetLastError();
     }
     int hbad = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFreeAsync(bad, st);
-    if (e != cudaSuccess) return cuda_error(e, "setting the walls of a plan");
+    if (e != cudaSuccess) return cuda_error(e, "setting the boundaries of a plan");
     if (hbad) {
-        cudaFree(p->wall_slot);
-        cudaFree(p->wall_n);
-        p->wall_slot = nullptr;
-        p->wall_n = nullptr;
-        return set_error(LABFM_EINVAL, (hbad & 1) ? "a wall node is out of range"
-                                       : (hbad & 2) ? "a wall node is listed twice"
-                                                    : "a wall normal is not of unit length");
+        free_boundaries(p);
+        return set_error(LABFM_EINVAL, (hbad & 1) ? "a boundary node is out of range"
+                                       : (hbad & 2) ? "a boundary node is listed twice"
+                                       : (hbad & 4) ? "a boundary normal is not of unit length"
+                                                    : "unknown boundary kind");
     }
     p->n_wall = n_wall;
-    p->device_bytes += int64_t(p->N) * 4 + n_wall * 2 * int64_t(es);
+    p->device_bytes += int64_t(p->N) * 4 + n_wall * 2 * int64_t(es) + (kind ? n_wall * (4 + 2 * int64_t(es)) : 0);
     return LABFM_OK;
 }
 
@@ -507,8 +619,8 @@ extern "C" int labfm_build_wall_operator(const double* xy, const double* h, cons
     if ((rc = stencils_into(sc, xy, h, N, Lx, Ly, periodic_mask, &rpA, &colA, &A.nnzA))) return rc;
     A.rpA = rpA;
     A.colA = colA;
-    // 3. row neighbours of the rows q = 0, 1, 2 (indices of wall nodes)
-    for (int q = 0; q < kStripRows; ++q) {
+    // 3. row neighbours of the rows q = 0..4 (indices of wall nodes)
+    for (int q = 0; q < kColumn; ++q) {
         double *xy_q = nullptr, *h_q = nullptr;
         if ((rc = sc.get(&xy_q, size_t(2 * n_wall))) || (rc = sc.get(&h_q, size_t(n_wall)))) return rc;
         k_gather_row<<<grid_of(n_wall), 256, 0, st>>>(n_wall, q, wall_column, xy, s, h1d_over_s, xy_q, h_q);
@@ -597,5 +709,23 @@ extern "C" int labfm_plan_set_walls(labfm_plan* p, int64_t n_wall, const int32_t
     if (n_wall > 0 && p->n_inst > 1) return set_error(LABFM_EINVAL, "walls are not supported on batched plans");
     if (n_wall > 0 && p->n_ranges > 0) return set_error(LABFM_EINVAL, "walls are not supported with launch ranges");
     if (n_wall > 0 && fault_alloc()) return injected_alloc_error("labfm_plan_set_walls");
-    return set_walls(p, n_wall, wall_nodes, wall_normal, as_stream(stream));
+    return set_walls(p, n_wall, wall_nodes, wall_normal, nullptr, nullptr, as_stream(stream));
+}
+
+extern "C" int labfm_plan_set_boundaries(labfm_plan* p, int64_t n, const int32_t* nodes, const double* normal,
+                                         const int32_t* kind, const double* target, const labfm_nscbc* params,
+                                         void* stream) {
+    LABFM_NVTX("labfm_plan_set_boundaries");
+    if (!p || !p->row_ptr) return set_error(LABFM_EINVAL, "null or empty plan");
+    if (n < 0 || n > p->N) return set_error(LABFM_EINVAL, "number of boundary nodes out of range");
+    if (n > 0 && (!nodes || !normal || !kind || !target || !params))
+        return set_error(LABFM_EINVAL, "null pointer argument");
+    if (n > 0 && p->n_inst > 1) return set_error(LABFM_EINVAL, "boundaries are not supported on batched plans");
+    if (n > 0 && p->n_ranges > 0) return set_error(LABFM_EINVAL, "boundaries are not supported with launch ranges");
+    if (n > 0 && (!(params->sigma >= 0.0) || !(params->L > 0.0) || !(params->mach >= 0.0 && params->mach < 1.0) ||
+                  !(params->rho0 > 0.0)))
+        return set_error(LABFM_EINVAL, "need sigma >= 0, L > 0, 0 <= mach < 1, rho0 > 0");
+    if (n > 0 && fault_alloc()) return injected_alloc_error("labfm_plan_set_boundaries");
+    if (n > 0) p->nscbc = *params;
+    return set_walls(p, n, nodes, normal, kind, target, as_stream(stream));
 }

@@ -1,0 +1,275 @@
+"""Open boundaries on the GPU (Section 7.1: the outflow of eq. outflowL and the
+inflow, both in LODI form) against the oracle, on a box bounded in x (inflow at
+x = 0, outflow at x = L) and periodic in y: the boundary operator with the
+"FD + 1D-LABFM" second derivatives at the boundary nodes, the right-hand side at
+every node, whole time steps, the closed forms of the relaxation terms, and an
+acoustic pulse that leaves through the outflow where a wall sends it back."""
+import numpy as np
+import pytest
+
+import labfm_inputs as li
+from oracle import boundary_oracle as bo
+from oracle import core as oracle
+from tests.conftest import golden
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS64 = np.finfo(np.float64).eps
+C, U0, MU = 20.0, 1.0, 1e-3
+
+
+@pytest.fixture(scope="module")
+def lb():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    import __graft_entry__ as g
+    g.build()
+    import paper_2102_02019_gb300 as lb
+    return lb
+
+
+def _dev(a, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def _rel_l2(a, b):
+    return np.linalg.norm(a - b, axis=-1) / np.linalg.norm(b, axis=-1)
+
+
+def _sigma():
+    return {k: float(v) for k, v in golden("nscbc.txt")}["sigma"]
+
+
+class Box:
+    """An open box with the oracle's operator and the GPU-built one; the left
+    boundary an inflow at (U0, 0), the right one an outflow to p_inf = c^2 (or a
+    wall, by ``right``)."""
+
+    def __init__(self, lb, nx, ny, m=6, m_wall=4, jitter=0.05, seed=1, right=bo.OUTFLOW, u_in=U0, mach=U0 / C):
+        self.ns = ns = li.open_box(nx, ny, m=m, jitter=jitter, seed=seed)
+        self.columns, self.normals = li.channel_walls(ns)
+        self.xy, self.h, self.s = _dev(ns.xy), _dev(ns.h), _dev(ns.s)
+        self.gop = lb.build_wall_operator(self.xy, self.h, self.s, ns.Lx, ns.Ly, m, m_wall,
+                                          _dev(self.columns, torch.int32), _dev(self.normals), 1.7,
+                                          periodic=(False, True), check=True)
+        self.op = bo.channel_operator(ns, m, m_wall)
+        n_b = self.columns.shape[0] // 2
+        kind = np.array([bo.INFLOW] * n_b + [right] * n_b, dtype=np.int32)
+        target = np.zeros((2 * n_b, 2))
+        target[:n_b, 0] = u_in
+        target[n_b:, 0] = C * C
+        self.bnd = {"nodes": self.columns[:, 0], "normal": self.normals, "kind": kind, "target": target,
+                    "L": ns.Lx, "mach": mach, "rho0": 1.0, "sigma": _sigma()}
+
+    def plan(self, lb, dtype, oracle_weights=True):
+        if oracle_weights:
+            rp, col, w, kappa = self.op
+            p = lb.Plan(_dev(rp, torch.int32), _dev(col, torch.int32), _dev(w), _dev(kappa), self.s, dtype=dtype)
+        else:
+            g = self.gop
+            p = lb.Plan(g["row_ptr"], g["col"], g["w"], g["kappa"], self.s, dtype=dtype)
+        b = self.bnd
+        p.set_boundaries(_dev(b["nodes"], torch.int32), _dev(b["normal"]), _dev(b["kind"], torch.int32),
+                         _dev(b["target"]), sigma=b["sigma"], L=b["L"], mach=b["mach"], rho0=b["rho0"])
+        return p
+
+
+@pytest.fixture(scope="module")
+def box(lb):
+    return Box(lb, 40, 12)
+
+
+def _state(ns, seed=0, amp=0.02):
+    q = np.zeros((3, ns.N))
+    q[0] = amp * li.smooth_perturbation(ns.xy, kmax=3, seed=seed, Lx=ns.Lx, Ly=ns.Ly)
+    q[1] = U0 + amp * C * li.smooth_perturbation(ns.xy, kmax=3, seed=seed + 1, Lx=ns.Lx, Ly=ns.Ly)
+    q[2] = amp * C * li.smooth_perturbation(ns.xy, kmax=3, seed=seed + 2, Lx=ns.Lx, Ly=ns.Ly)
+    return q
+
+
+def test_open_box_operator_matches_oracle(box):
+    ns = box.ns
+    rp, col, w, kappa = box.op
+    assert np.array_equal(box.gop["row_ptr"].cpu().numpy(), rp)
+    assert np.array_equal(box.gop["col"].cpu().numpy(), col)
+    assert box.gop["n_failed"] == 0
+    wg = box.gop["w"].cpu().numpy()
+    kg = box.gop["kappa"].cpu().numpy()
+    row = ns.meta["row"]
+    per = (False, True)
+    rpc, colc = oracle.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly, periodic=per)
+    cond = {mm: oracle.build_weights(ns.xy, ns.h, ns.s, rpc, colc, mm, ns.Lx, ns.Ly, periodic=per,
+                                     want_cond=True)["cond1"] for mm in (6, 4)}
+    for i in range(ns.N):
+        sl = slice(rp[i], rp[i + 1])
+        a, b = wg[:, sl], w[:, sl]
+        if row[i] >= 3:
+            tol = max(50 * oracle.n_unknowns(6) * EPS64 * cond[6][i], 1e-13)
+            assert np.abs(a - b).max() <= tol * np.abs(b).max(), i
+            continue
+        assert np.abs(a[:2] - b[:2]).max() <= 1e-12 * np.abs(b[:2]).max(), i
+        if row[i] == 0:
+            assert np.abs(a[2:5] - b[2:5]).max() <= 1e-12 * np.abs(b[2:5]).max(), i
+            assert np.all(a[5] == 0.0) and kg[i] == 0.0
+        else:
+            tol = max(50 * oracle.n_unknowns(4) * EPS64 * cond[4][i], 1e-13)
+            assert np.abs(a[2:] - b[2:]).max() <= tol * np.abs(b[2:]).max(), i
+
+
+def test_boundary_second_derivatives_exact_on_quartics(box):
+    # the boundary nodes' second derivatives (one-sided five-point difference along
+    # the column, 1D LABFM of order 4 along the row and their product for the mixed
+    # one) are exact on polynomials of degree <= 2 in the rotated frame, hence in
+    # (x, y): check d2/dx2, d2/dxdy, d2/dy2 of random quadratics on the GPU operator
+    ns = box.ns
+    rp = box.gop["row_ptr"].cpu().numpy()
+    col = box.gop["col"].cpu().numpy()
+    w = box.gop["w"].cpu().numpy()
+    rng = np.random.default_rng(3)
+    for i in box.bnd["nodes"]:
+        sl = slice(rp[i], rp[i + 1])
+        dx = ns.xy[col[sl], 0] - ns.xy[i, 0]
+        dy = oracle.minimum_image(ns.xy[col[sl], 1] - ns.xy[i, 1], ns.Ly, True)
+        a, b, c, d, e = rng.standard_normal(5)
+        p = a * dx + b * dy + c * dx * dx + d * dx * dy + e * dy * dy
+        scale = np.abs(w[2:5, sl]).sum(axis=1) * np.abs(p).max() + 1.0
+        got = w[2:5, sl] @ p
+        assert np.all(np.abs(got - (2 * c, d, 2 * e)) <= 1e-10 * scale), (i, got, (2 * c, d, 2 * e))
+
+
+def test_open_box_rhs_matches_oracle(lb, box):
+    plan = box.plan(lb, torch.float64)
+    q = _state(box.ns)
+    R = lb.rhs(plan, _dev(q), lb.Phys(C * C, MU)).cpu().numpy()
+    Ro = bo.boundary_rhs(q, box.op, box.bnd, C, MU)
+    assert np.all(_rel_l2(R, Ro) <= 1e-12), _rel_l2(R, Ro)
+    nb = box.bnd["nodes"]
+    err = np.abs(R[:, nb] - Ro[:, nb]).max(axis=1) / np.abs(Ro[:, nb]).max(axis=1)
+    assert np.all(err <= 1e-11), err
+    plan.close()
+
+
+def test_uniform_flow_is_steady_on_the_gpu(lb, box):
+    plan = box.plan(lb, torch.float64)
+    q = np.zeros((3, box.ns.N))
+    q[1] = U0
+    R = lb.rhs(plan, _dev(q), lb.Phys(C * C, MU)).cpu().numpy()
+    assert np.all(R == 0.0)
+    Q = _dev(q)
+    lb.rk_step(plan, Q, 1e-3, 5, lb.Phys(C * C, MU))
+    assert np.array_equal(Q.cpu().numpy(), q)
+    plan.close()
+
+
+def test_relaxation_rates_on_the_gpu(lb, box):
+    # the closed forms of the oracle's pins: a uniform density excess relaxes at the
+    # outflow by L4 = sigma/(2L) c (1 - M^2)(p - p_inf); a uniform velocity error at
+    # the inflow by L4 = sigma rho0 c^2 (1 - M^2)/L du and L3 = sigma c/L dv
+    plan = box.plan(lb, torch.float64)
+    ns, b = box.ns, box.bnd
+    sigma, M, L = b["sigma"], b["mach"], b["L"]
+    out = b["nodes"][b["kind"] == bo.OUTFLOW]
+    inn = b["nodes"][b["kind"] == bo.INFLOW]
+    rho = 1.01
+    q = np.zeros((3, ns.N))
+    q[0], q[1] = np.log(rho), U0
+    R = lb.rhs(plan, _dev(q), lb.Phys(C * C, MU)).cpu().numpy()
+    L4 = sigma / (2 * L) * C * (1 - M * M) * (C * C * rho - C * C)
+    assert np.allclose(R[0, out], -L4 / (rho * C * C), rtol=1e-12, atol=0)
+    assert np.allclose(R[1, out], L4 / (rho * C), rtol=1e-12, atol=0)
+    du, dv = 0.01, -0.02
+    q = np.zeros((3, ns.N))
+    q[1], q[2] = U0 + du, dv
+    R = lb.rhs(plan, _dev(q), lb.Phys(C * C, MU)).cpu().numpy()
+    L4 = sigma * C * C * (1 - M * M) / L * du
+    L3 = sigma * C / L * dv
+    assert np.allclose(R[0, inn], -L4 / (C * C), rtol=1e-12, atol=0)
+    assert np.allclose(R[1, inn], -L4 / C, rtol=1e-12, atol=0)
+    assert np.allclose(R[2, inn], -L3, rtol=1e-12, atol=0)
+    plan.close()
+
+
+def test_open_box_time_steps_match_oracle(lb, box):
+    # ten steps (interior eq. icns, boundary rows, LODI inflow and outflow, filter
+    # off the boundary nodes): the change over the steps within 1e-12
+    ns = box.ns
+    plan = box.plan(lb, torch.float64)
+    q0 = _state(ns, seed=5)
+    dt = 0.5 * oracle.stable_dt(q0, ns.s, C, MU)
+    Q = _dev(q0)
+    lb.rk_step(plan, Q, dt, 10, lb.Phys(C * C, MU))
+    qo = q0
+    for _ in range(10):
+        qo = bo.boundary_time_step(qo, dt, box.op, box.bnd, C, MU)
+    qg = Q.cpu().numpy()
+    assert np.all(_rel_l2(qg - q0, qo - q0) <= 1e-12), _rel_l2(qg - q0, qo - q0)
+    plan.close()
+
+
+def test_open_box_gpu_operator_and_fp32(lb, box):
+    ns = box.ns
+    q0 = _state(ns, seed=8)
+    dt = 0.5 * oracle.stable_dt(q0, ns.s, C, MU)
+    qo = q0
+    for _ in range(3):
+        qo = bo.boundary_time_step(qo, dt, box.op, box.bnd, C, MU)
+    for dtype, tol in ((torch.float64, 1e-7), (torch.float32, 1e-4)):
+        plan = box.plan(lb, dtype, oracle_weights=False)
+        Q = _dev(q0, dtype)
+        lb.rk_step(plan, Q, dt, 3, lb.Phys(C * C, MU))
+        qg = Q.double().cpu().numpy()
+        assert np.all(_rel_l2(qg - q0, qo - q0) <= tol), (dtype, _rel_l2(qg - q0, qo - q0))
+        plan.close()
+
+
+def _pulse(lb, right, nx=96, ny=12):
+    # a right-going acoustic pulse (u' = c a') in fluid at rest, inflow at zero
+    # velocity on the left; run until a reflected pulse would be a quarter of the
+    # box back from the right boundary
+    bx = Box(lb, nx, ny, seed=2, right=right, u_in=0.0, mach=0.0)
+    ns = bx.ns
+    plan = bx.plan(lb, torch.float64, oracle_weights=False)
+    A, x0, w = 1e-3, 0.6 * ns.Lx, 0.3
+    x = ns.xy[:, 0]
+    pulse = A * np.exp(-((x - x0) / w) ** 2)
+    q = np.zeros((3, ns.N))
+    q[0] = pulse
+    q[1] = C * pulse
+    dt = oracle.stable_dt(q, ns.s, C, MU)
+    n = int(np.ceil((ns.Lx - x0 + 0.25 * ns.Lx) / C / dt))
+    Q = _dev(q)
+    lb.rk_step(plan, Q, dt, n, lb.Phys(C * C, MU))
+    qg = Q.cpu().numpy()
+    plan.close()
+    away = (x > 0.2 * ns.Lx) & (x < 0.85 * ns.Lx)
+    return float(np.abs(qg[0][away]).max()) / A, qg
+
+
+def test_acoustic_pulse_leaves_through_the_outflow_on_the_gpu(lb):
+    out, q = _pulse(lb, bo.OUTFLOW)
+    wall, _ = _pulse(lb, bo.WALL)
+    print("pulse left behind (outflow, wall):", out, wall)
+    assert np.all(np.isfinite(q))
+    assert 0.8 < wall < 1.2, wall
+    assert out < 0.05, out
+
+
+def test_boundary_arguments_are_checked(lb, box):
+    plan = box.plan(lb, torch.float64)
+    b = box.bnd
+    nodes, normal = _dev(b["nodes"], torch.int32), _dev(b["normal"])
+    kind, target = _dev(b["kind"], torch.int32), _dev(b["target"])
+    bad = b["kind"].copy()
+    bad[0] = 7
+    with pytest.raises(lb.LabfmError):
+        plan.set_boundaries(nodes, normal, _dev(bad, torch.int32), target)
+    for kw in ({"sigma": -1.0}, {"L": 0.0}, {"mach": 1.0}, {"rho0": 0.0}):
+        with pytest.raises(lb.LabfmError):
+            plan.set_boundaries(nodes, normal, kind, target, **kw)
+    # the refused calls leave no boundaries: eq. icns everywhere
+    q = _state(box.ns)
+    R = lb.rhs(plan, _dev(q), lb.Phys(C * C, MU)).cpu().numpy()
+    rp, col, w, _ = box.op
+    assert np.all(_rel_l2(R, oracle.rhs(q, w[:5], rp, col, C * C, MU)) <= 1e-12)
+    plan.close()
