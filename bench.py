@@ -58,7 +58,7 @@ def parse():
                     help="lattice side (512 = the benchmark workload; smaller sizes for profiling)")
     ap.add_argument("--ref-cores", type=int, default=0,
                     help="host cores for --impl reference (0 = all, 1 = one, in this process)")
-    ap.add_argument("--only", choices=["stencil_opt", "adjoint", "channel"], default=None,
+    ap.add_argument("--only", choices=["stencil_opt", "adjoint", "channel", "lamb_oseen"], default=None,
                     help="run one extra workload alone on --nx and print its JSON (for profiling; "
                          "adjoint: --steps steps)")
     return ap.parse_args()
@@ -573,6 +573,32 @@ def _channel_plan(lb, torch, ns, dtype, m=6, m_wall=4):
     return plan, s, op, a.elapsed_time(b), cols[:, 0]
 
 
+def run_lamb_oseen(lb, torch):
+    """Section 8.3: the Lamb-Oseen vortex through the outflow at R_c/s = 3 .. 16 (and a
+    finer R_c/s = 24 reference), FP64, to t U0/R_c = 20; the disturbance norm's
+    history, its errors against the finest resolution and the convergence rates,
+    beside the printed ones."""
+    from tests import lamb_oseen as lo
+    st = lo.study(lb, torch)
+    res, printed_rates = lo.printed()
+    runs = {}
+    for r, d in st["runs"].items():
+        every = 10  # t* = 1 apart
+        runs[str(r)] = {k: d[k] for k in ("nodes", "nnz", "dt", "steps", "finite", "build_s", "step_ms")}
+        runs[str(r)]["t_star"] = d["t_star"][::every]
+        runs[str(r)]["norm"] = d["norm"][::every]
+    out = {"workload": "Lamb-Oseen vortex (Ma = 0.05, R_c = H/25, C = cH/300, Re = 7500) in the unit box, "
+                       "inflow at x = 0, outflow at x = H, periodic y, +-0.05 s jitter, m = 6 inside, m = 4 on "
+                       "the boundary rows, FP64, t U0/R_c in [0, 20]",
+           "printed_rates": dict(zip([str(r) for r in res[:-1]], printed_rates)),
+           "error_vs_16": {str(k): v for k, v in st["error_vs_finest"].items()},
+           "rates_vs_16": st["rates"], "runs": runs}
+    for k in st:
+        if k.startswith("error_vs_2") or k.startswith("rates_vs_2"):
+            out[k] = {str(a): b for a, b in st[k].items()}
+    return out
+
+
 def run_channel(lb, torch, args, nx=512):
     """The boundary row (Section 7.1): a channel periodic in x between no-slip walls,
     nx x nx nodes (five uniform rows along each wall, +-0.05 s jitter inside), LABFM
@@ -659,16 +685,16 @@ def adjoint_kernel_bytes(nnz, N):
       recording stage: the stage kernel's 24 B per entry + 64 B per node, and the
         eight derivative combinations it stores (32 B per node);
       pass A: per node the stage state (16 B), its derivative combinations (32 B),
-        the cotangent (16 B), 1/s (4 B) in; twelve derivative adjoints (48 B) and
-        three own-value adjoints (16 B) out;
+        the cotangent (16 B), 1/s (4 B) in; the twelve derivative adjoints as the
+        eight values they reduce to (32 B) and three own-value adjoints (16 B) out;
       pass B: per transposed entry its record (24 B); per node the row pointer
-        (4 B), the twelve derivative adjoints gathered (48 B, once), five row sums
-        (20 B), the own-value adjoints (16 B), the running cotangent in and out
+        (4 B), the eight derivative-adjoint values gathered (32 B, once), five row
+        sums (20 B), the own-value adjoints (16 B), the running cotangent in and out
         (32 B) and the next stage's cotangent (16 B);
       filter transpose: per entry 8 B; per node row pointer, cotangent (gathered
         once), filter row sum, two outputs: 4 + 16 + 4 + 32 B;
       filter (forward, also in the recompute): 8 B per entry + 36 B per node."""
-    return {"rec_stage": 24.0 * nnz + 96.0 * N, "adj_a": 132.0 * N, "adj_b": 24.0 * nnz + 136.0 * N,
+    return {"rec_stage": 24.0 * nnz + 96.0 * N, "adj_a": 116.0 * N, "adj_b": 24.0 * nnz + 120.0 * N,
             "adj_filter": 8.0 * nnz + 56.0 * N, "filter": 8.0 * nnz + 36.0 * N}
 
 
@@ -1053,6 +1079,8 @@ def main():
             out = run_stencil_opt(lb, torch, args)
         elif args.only == "channel":
             out = run_channel(lb, torch, args, nx=args.nx)
+        elif args.only == "lamb_oseen":
+            out = run_lamb_oseen(lb, torch)
         else:
             out = run_adjoint(lb, torch, args, nsteps=args.steps, every=max(1, min(50, args.steps // 2)),
                               nx=args.nx)

@@ -211,13 +211,20 @@ def boundary_node_second_derivatives(ns, i: int, h1d_over_s: float = 1.7):
         for j, w in zip(nbrs, we1):
             add(j, 0.0, c * w, 0.0)
         add(col[r], 0.0, -c * float(np.sum(we1)), 0.0)
+    return {j: hessian_to_xy(n, a, b, c) for j, (a, b, c) in acc.items()}
+
+
+def hessian_to_xy(n, d_xixi, d_xieta, d_etaeta):
+    """Second derivatives in (x, y) from those in the boundary frame (xi along n, eta
+    along t = (-n_y, n_x)): with x = n_x xi - n_y eta and y = n_y xi + n_x eta, the
+    chain rule twice gives
+        d_xx = n_x^2 d_xixi - 2 n_x n_y d_xieta + n_y^2 d_etaeta,
+        d_xy = n_x n_y d_xixi + (n_x^2 - n_y^2) d_xieta - n_x n_y d_etaeta,
+        d_yy = n_y^2 d_xixi + 2 n_x n_y d_xieta + n_x^2 d_etaeta."""
     nx, ny = float(n[0]), float(n[1])
-    out = {}
-    for j, (a, b, c) in acc.items():
-        out[j] = (nx * nx * a - 2 * nx * ny * b + ny * ny * c,
-                  nx * ny * a + (nx * nx - ny * ny) * b - nx * ny * c,
-                  ny * ny * a + 2 * nx * ny * b + nx * nx * c)
-    return out
+    return (nx * nx * d_xixi - 2 * nx * ny * d_xieta + ny * ny * d_etaeta,
+            nx * ny * d_xixi + (nx * nx - ny * ny) * d_xieta - nx * ny * d_etaeta,
+            ny * ny * d_xixi + 2 * nx * ny * d_xieta + nx * nx * d_etaeta)
 
 
 # --------------------------------------------------------------------------

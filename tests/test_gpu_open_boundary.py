@@ -118,24 +118,27 @@ def test_open_box_operator_matches_oracle(box):
 
 
 def test_boundary_second_derivatives_exact_on_quartics(box):
-    # the boundary nodes' second derivatives (one-sided five-point difference along
-    # the column, 1D LABFM of order 4 along the row and their product for the mixed
-    # one) are exact on polynomials of degree <= 2 in the rotated frame, hence in
-    # (x, y): check d2/dx2, d2/dxdy, d2/dy2 of random quadratics on the GPU operator
+    # the boundary nodes' second derivatives in the GPU-built operator (one-sided
+    # five-point difference along the column, 1D LABFM of order 4 along the row, and
+    # the column difference of the rows' tangential derivative for the mixed one) are
+    # exact on every polynomial of total degree <= 4, on both boundaries
     ns = box.ns
     rp = box.gop["row_ptr"].cpu().numpy()
     col = box.gop["col"].cpu().numpy()
     w = box.gop["w"].cpu().numpy()
     rng = np.random.default_rng(3)
-    for i in box.bnd["nodes"]:
-        sl = slice(rp[i], rp[i + 1])
-        dx = ns.xy[col[sl], 0] - ns.xy[i, 0]
-        dy = oracle.minimum_image(ns.xy[col[sl], 1] - ns.xy[i, 1], ns.Ly, True)
-        a, b, c, d, e = rng.standard_normal(5)
-        p = a * dx + b * dy + c * dx * dx + d * dx * dy + e * dy * dy
-        scale = np.abs(w[2:5, sl]).sum(axis=1) * np.abs(p).max() + 1.0
-        got = w[2:5, sl] @ p
-        assert np.all(np.abs(got - (2 * c, d, 2 * e)) <= 1e-10 * scale), (i, got, (2 * c, d, 2 * e))
+    ex = [(a, k - a) for k in range(5) for a in range(k + 1)]
+    for _ in range(3):
+        c = rng.standard_normal(len(ex))
+        for i in box.bnd["nodes"]:
+            sl = slice(rp[i], rp[i + 1])
+            dx = ns.xy[col[sl], 0] - ns.xy[i, 0]
+            dy = oracle.minimum_image(ns.xy[col[sl], 1] - ns.xy[i, 1], ns.Ly, True)
+            p = sum(ck * dx ** a * dy ** b for ck, (a, b) in zip(c, ex))
+            exact = (2 * c[ex.index((2, 0))], c[ex.index((1, 1))], 2 * c[ex.index((0, 2))])
+            got = w[2:5, sl] @ p
+            scale = np.abs(w[2:5, sl]) @ np.abs(p) + 1.0
+            assert np.all(np.abs(got - exact) <= 1e-10 * scale), (i, got, exact)
 
 
 def test_open_box_rhs_matches_oracle(lb, box):

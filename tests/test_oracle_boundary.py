@@ -132,6 +132,22 @@ def test_rotation_from_boundary_coordinates():
         assert abs(dx - g[0]) < 1e-14 and abs(dy - g[1]) < 1e-14
 
 
+def test_hessian_rotation_from_boundary_coordinates():
+    # the Hessian of a quadratic form in (x, y) seen in the boundary frame of any
+    # normal (xi = r.n, eta = r.t): R H R^T with R's rows n and t; the rotation back
+    # must return H
+    rng = np.random.default_rng(5)
+    for th in rng.uniform(0, 2 * np.pi, 16):
+        n = np.array([np.cos(th), np.sin(th)])
+        t = np.array([-n[1], n[0]])
+        A = rng.standard_normal((2, 2))
+        H = A + A.T
+        R = np.stack([n, t])
+        Hb = R @ H @ R.T
+        got = bo.hessian_to_xy(n, Hb[0, 0], Hb[0, 1], Hb[1, 1])
+        assert np.allclose(got, (H[0, 0], H[0, 1], H[1, 1]), rtol=0, atol=1e-13)
+
+
 def _poly(c, x, y):
     # sum over i + j <= 4 of c[i, j] x^i y^j, and its x and y derivatives
     v = dx = dy = 0.0
@@ -166,6 +182,52 @@ def test_strip_first_derivatives_are_exact_on_quartics(q):
         scale = np.sum(np.abs(wx * phi)) + np.sum(np.abs(wy * phi)) + 1.0
         assert abs(np.sum(wx * phi) - gx) <= 1e-11 * scale
         assert abs(np.sum(wy * phi) - gy) <= 1e-11 * scale
+
+
+def _poly2(c, x, y):
+    """sum c_ij x^i y^j (i + j <= 4) and its second derivatives xx, xy, yy."""
+    v = dxx = dxy = dyy = 0.0
+    for i in range(5):
+        for j in range(5 - i):
+            v = v + c[i, j] * x ** i * y ** j
+            if i >= 2:
+                dxx = dxx + i * (i - 1) * c[i, j] * x ** (i - 2) * y ** j
+            if i and j:
+                dxy = dxy + i * j * c[i, j] * x ** (i - 1) * y ** (j - 1)
+            if j >= 2:
+                dyy = dyy + j * (j - 1) * c[i, j] * x ** i * y ** (j - 2)
+    return v, dxx, dxy, dyy
+
+
+@pytest.mark.parametrize("kind", ["channel", "open_box"])
+def test_boundary_node_second_derivatives_are_exact_on_quartics(kind):
+    # "FD + 1D-LABFM" at a boundary node: the one-sided five-point second difference
+    # along the normal column, 4th-order 1D LABFM along the boundary row, and the
+    # normal difference of the rows' 1D-LABFM tangential derivative for the mixed
+    # term, rotated to (x, y): exact on every polynomial of total degree <= 4, on
+    # both boundaries of a channel (normals +-y) and of an open box (normals +-x)
+    import labfm_inputs as li
+    from oracle.labfm_oracle import minimum_image
+    ns = li.channel(32, 14) if kind == "channel" else li.open_box(14, 32, jitter=0.1)
+    per = (True, False) if kind == "channel" else (False, True)
+    rng = np.random.default_rng(11)
+    meta = ns.meta
+    nodes0 = np.flatnonzero(meta["row"] == 0)
+    assert set(meta["wall"][nodes0]) == {0, 1}
+    for trial in range(3):
+        c = rng.standard_normal((5, 5))
+        for i in nodes0[::3]:
+            w = bo.boundary_node_second_derivatives(ns, int(i))
+            nodes = np.array(list(w))
+            W = np.array([w[j] for j in nodes])  # (n, 3): xx, xy, yy
+            assert np.all(np.abs(W.sum(axis=0)) <= 1e-9 * np.abs(W).sum(axis=0))
+            dx = minimum_image(ns.xy[nodes, 0] - ns.xy[i, 0], ns.Lx, per[0])
+            dy = minimum_image(ns.xy[nodes, 1] - ns.xy[i, 1], ns.Ly, per[1])
+            phi = _poly2(c, dx, dy)[0]
+            _, exx, exy, eyy = _poly2(c, 0.0, 0.0)
+            got = W.T @ phi
+            scale = np.abs(W).T @ np.abs(phi) + 1.0
+            assert np.all(np.abs(got - (exx, exy, eyy)) <= 1e-10 * scale), (kind, i, got, (exx, exy, eyy))
 
 
 def test_wall_keeps_a_hydrostatic_column_at_rest_with_the_consistent_wave():
