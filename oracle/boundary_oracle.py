@@ -256,7 +256,7 @@ def wall_rhs(rho, c, dp_dxi, du_xi_dxi, du_eta_deta, g_n, visc_xi=0.0, wall_fact
 # Section 7.1: the channel (walls at y = 0 and H, periodic in x), all operators
 # --------------------------------------------------------------------------
 
-def channel_operator(ns, m: int = 4, m_wall: int = 4, h1d_over_s: float = 1.7):
+def channel_operator(ns, m: int = 4, m_wall: int = 4, h1d_over_s: float = 1.7, rows=None):
     """Difference-form operators (row_ptr, col, w (6, nnz), kappa) for the node set of
     ``labfm_inputs.channel``, following the Table "Schemes for derivatives near
     boundaries":
@@ -271,35 +271,38 @@ def channel_operator(ns, m: int = 4, m_wall: int = 4, h1d_over_s: float = 1.7):
       kappa = 0: the boundary node is not filtered (a reading: the paper lists
       "FD + 1D-LABFM" for its hyperviscous operator without its form).
     ``ns`` is a ``labfm_inputs.channel`` (periodic in x) or ``open_box`` (periodic
-    in y) node set.
+    in y) node set.  ``rows``: the operator rows of these nodes only (row_ptr over
+    them, kappa per listed node), for sampled checks of large node sets.
     """
     from . import labfm_oracle as core
     per = (False, True) if ns.meta.get("kind") == "open_box" else (True, False)
-    rp, col = core.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly, periodic=per)
-    bw = core.build_weights(ns.xy, ns.h, ns.s, rp, col, m, ns.Lx, ns.Ly, periodic=per)
+    sel = np.arange(ns.N) if rows is None else np.asarray(rows, dtype=np.int64)
+    rp, col = core.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly, periodic=per, rows=sel)
+    bw = core.build_weights(ns.xy, ns.h, ns.s, rp, col, m, ns.Lx, ns.Ly, periodic=per, rows=sel)
     bw4 = bw if m_wall == m else core.build_weights(ns.xy, ns.h, ns.s, rp, col, m_wall, ns.Lx, ns.Ly,
-                                                    periodic=per)
+                                                    periodic=per, rows=sel)
     row = ns.meta["row"]
-    N = ns.N
+    N = len(sel)
     entries, kappa = [], np.zeros(N)
-    for i in range(N):
-        a, b = rp[i], rp[i + 1]
+    for k, i in enumerate(sel):
+        i = int(i)
+        a, b = rp[k], rp[k + 1]
         acc = {}
         if row[i] >= 3:
-            if not bw["ok"][i]:
+            if not bw["ok"][k]:
                 raise ValueError(f"singular LABFM system at node {i}")
             for e in range(a, b):
                 acc[int(col[e])] = bw["w"][:, e].copy()
-            kappa[i] = bw["kappa"][i]
+            kappa[k] = bw["kappa"][k]
         else:
             if row[i] > 0:
-                if not bw4["ok"][i]:
+                if not bw4["ok"][k]:
                     raise ValueError(f"singular LABFM system at node {i}")
                 for e in range(a, b):
                     v = np.zeros(6)
                     v[2:] = bw4["w"][2:, e]
                     acc[int(col[e])] = v
-                kappa[i] = bw4["kappa"][i]
+                kappa[k] = bw4["kappa"][k]
             nodes, wx, wy = strip_first_derivative_rows(ns, i, 4, h1d_over_s)
             for j, ax, ay in zip(nodes, wx, wy):
                 if j == i:

@@ -276,3 +276,100 @@ def test_wall_arguments_are_checked(lb, ch):
     with pytest.raises(lb.LabfmError):
         lb.build_wall_operator(ch.xy, ch.h, ch.s, ns.Lx, ns.Ly, 6, 4, _dev(cols, torch.int32), _dev(ch.normals))
     plan.close()
+
+
+# ---------------------------------------------------------------- the channel workload, sampled
+
+@pytest.fixture(scope="module")
+def ch512(lb):
+    # the bench's channel: 512 x 512, +-0.05 s jitter inside, m = 6 inside, m = 4 on the
+    # wall rows; the GPU-built operator; sampled rows of every kind
+    ns = li.channel(512, 512, m=6, jitter=0.05)
+    cols, normals = li.channel_walls(ns)
+    xy, h, s = _dev(ns.xy), _dev(ns.h), _dev(ns.s)
+    gop = lb.build_wall_operator(xy, h, s, ns.Lx, ns.Ly, 6, 4, _dev(cols, torch.int32), _dev(normals), 1.7,
+                                 periodic=(True, False), check=True)
+    rng = np.random.default_rng(21)
+    row = ns.meta["row"]
+    pick = [rng.choice(np.flatnonzero(row == q), 12, replace=False) for q in range(5)]
+    pick.append(rng.choice(np.flatnonzero(row == 5), 24, replace=False))
+    rows = np.unique(np.concatenate(pick + [[0, ns.N - 1]]))
+    return dict(ns=ns, cols=cols, normals=normals, s=s, gop=gop, rows=rows,
+                op=bo.channel_operator(ns, 6, 4, rows=rows))
+
+
+def test_channel_workload_operator_rows_sampled(ch512):
+    ns, rows, gop = ch512["ns"], ch512["rows"], ch512["gop"]
+    rp_o, col_o, w_o, k_o = ch512["op"]
+    rp = gop["row_ptr"].cpu().numpy()
+    col = gop["col"].cpu().numpy()
+    w = gop["w"].cpu().numpy()
+    kap = gop["kappa"].cpu().numpy()
+    assert gop["n_failed"] == 0
+    per = (True, False)
+    rpn, coln = oracle.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly, periodic=per, rows=rows)
+    cond = {mm: oracle.build_weights(ns.xy, ns.h, ns.s, rpn, coln, mm, ns.Lx, ns.Ly, periodic=per, rows=rows,
+                                     want_cond=True)["cond1"] for mm in (6, 4)}
+    row = ns.meta["row"]
+    for k, i in enumerate(rows):
+        sl, so = slice(rp[i], rp[i + 1]), slice(rp_o[k], rp_o[k + 1])
+        assert np.array_equal(col[sl], col_o[so]), i
+        a, b = w[:, sl], w_o[:, so]
+        if row[i] >= 3:
+            tol = max(50 * oracle.n_unknowns(6) * EPS64 * cond[6][k], 1e-13)
+            assert np.abs(a - b).max() <= tol * np.abs(b).max(), i
+            assert abs(kap[i] - k_o[k]) <= tol * abs(k_o[k]), i
+            continue
+        assert np.abs(a[:2] - b[:2]).max() <= 1e-12 * np.abs(b[:2]).max(), i
+        if row[i] == 0:
+            assert np.abs(a[2:5] - b[2:5]).max() <= 1e-12 * np.abs(b[2:5]).max(), i
+            assert np.all(a[5] == 0.0) and kap[i] == 0.0
+        else:
+            tol = max(50 * oracle.n_unknowns(4) * EPS64 * cond[4][k], 1e-13)
+            assert np.abs(a[2:] - b[2:]).max() <= tol * np.abs(b[2:]).max(), i
+
+
+def test_channel_workload_rhs_sampled(lb, ch512):
+    # FP64 right-hand side of the bench's channel at the sampled rows against the oracle
+    # with the same (GPU-built) weights, to 1e-12; and the FP32 plan in the bench's launch
+    # shape within the FP32 budget at the sampled rows that follow eq. icns
+    from tests.fp32_budget import U32, rhs_bound
+    ns, rows, gop = ch512["ns"], ch512["rows"], ch512["gop"]
+    c, mu, g = 20.0, 0.1, (0.5, 0.0)
+    q = np.zeros((3, ns.N))
+    q[0] = 0.01 * li.smooth_perturbation(ns.xy, kmax=4, seed=3, Ly=ns.Ly)
+    q[1] = 0.5 * li.smooth_perturbation(ns.xy, kmax=4, seed=4, Ly=ns.Ly)
+    q[2] = 0.1 * li.smooth_perturbation(ns.xy, kmax=4, seed=5, Ly=ns.Ly)
+    wall = ch512["cols"][:, 0]
+    q[1:, wall] = 0.0
+    rp = gop["row_ptr"].cpu().numpy()
+    col = gop["col"].cpu().numpy()
+    w = gop["w"].cpu().numpy()
+    cnt = np.zeros(ns.N, dtype=np.int64)
+    cnt[rows] = rp[rows + 1] - rp[rows]
+    rps = np.concatenate([[0], np.cumsum(cnt)])
+    idx = np.concatenate([np.arange(rp[i], rp[i + 1]) for i in rows])
+    bnd = {"nodes": wall, "normal": ch512["normals"], "kind": np.zeros(len(wall), dtype=np.int32),
+           "target": np.zeros((len(wall), 2)), "L": 1.0, "mach": 0.0, "rho0": 1.0}
+    Ro = bo.boundary_rhs(q, (rps, col[idx], w[:, idx], None), bnd, c, mu, g)
+    phys = lb.Phys(c * c, mu, g[0], g[1])
+    for dtype in (torch.float64, torch.float32):
+        plan = lb.Plan(gop["row_ptr"], gop["col"], gop["w"], gop["kappa"], ch512["s"], dtype=dtype)
+        plan.set_walls(_dev(wall, torch.int32), _dev(ch512["normals"]))
+        plan.set_launch(4, 128)  # the channel bench's tuned shape (walls run the plain grid)
+        R = lb.rhs(plan, _dev(q, dtype), phys).double().cpu().numpy()
+        plan.close()
+        if dtype == torch.float64:
+            for f in range(3):
+                err = np.abs(R[f][rows] - Ro[f][rows]).max() / np.abs(Ro[f][rows]).max()
+                assert err <= 1e-12, (f, err)
+            assert np.all(R[1:, wall] == 0.0)
+        else:
+            icns = rows[ns.meta["row"][rows] > 0]
+            B = rhs_bound(q, w[:, idx], rps, col[idx], c * c, mu)
+            # the body force enters each momentum sum once more: its rounding and that
+            # of the final addition
+            B[1] += 4 * U32 * abs(g[0])
+            B[2] += 4 * U32 * abs(g[1])
+            ratio = np.abs(R[:, icns] - Ro[:, icns]) / B[:, icns]
+            assert ratio.max() <= 1.0, ratio.max()

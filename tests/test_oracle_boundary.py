@@ -297,3 +297,20 @@ def test_poiseuille_start_up_converges_to_the_analytic_solution():
     assert order > 4.0, order
     # no cross-channel velocity develops beyond the discretisation error
     assert v16 < 1e-3 and v24 < 1e-3
+
+
+def test_sampled_operator_rows_equal_the_full_operator():
+    # channel_operator(rows=...) builds only the listed rows (for sampled checks of
+    # large node sets): each equals the same row of the whole operator
+    import labfm_inputs as li
+    ns = li.channel(20, 18, m=6, jitter=0.1, seed=3)
+    full = bo.channel_operator(ns, 6, 4)
+    rows = np.array([0, 5, 17, 40, 77, 100, 200, ns.N - 1])
+    sub = bo.channel_operator(ns, 6, 4, rows=rows)
+    for k, i in enumerate(rows):
+        a, b = slice(full[0][i], full[0][i + 1]), slice(sub[0][k], sub[0][k + 1])
+        assert np.array_equal(full[1][a], sub[1][b])
+        assert np.array_equal(full[2][:, a], sub[2][:, b])
+        # kappa's F0 sum runs over each batch's padded stencil width (zeros added in
+        # another order): equal to a few ulp
+        assert abs(full[3][i] - sub[3][k]) <= 4 * np.finfo(float).eps * abs(full[3][i])
