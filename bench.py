@@ -688,18 +688,21 @@ def adjoint_kernel_bytes(nnz, N):
     backward pass (every stencil entry's record once, every node value once):
       recording stage: the stage kernel's 24 B per entry + 64 B per node, and the
         eight derivative combinations it stores (32 B per node);
-      pass A: per node the stage state (16 B), its derivative combinations (32 B),
-        the cotangent (16 B), 1/s (4 B) in; the twelve derivative adjoints as the
-        eight values they reduce to (32 B) and three own-value adjoints (16 B) out;
+      pass A (fused into the launch that forms its cotangent): per node the stage
+        state (16 B) and its derivative combinations (32 B) in; the twelve
+        derivative adjoints as the eight values they reduce to (32 B) and three
+        own-value adjoints (16 B) out: 96 B;
       pass B: per transposed entry its record (24 B); per node the row pointer
         (4 B), the eight derivative-adjoint values gathered (32 B, once), five row
-        sums (20 B), the own-value adjoints (16 B), the running cotangent in and out
-        (32 B) and the next stage's cotangent (16 B);
+        sums (20 B), the own-value adjoints (16 B) and the running cotangent in and
+        out (32 B): 104 B, plus the fused pass A in three of the four stages (mean
+        over a step's launches: 104 + 72 = 176 B);
       filter transpose: per entry 8 B; per node row pointer, cotangent (gathered
-        once), filter row sum, two outputs: 4 + 16 + 4 + 32 B;
+        once), filter row sum, the running cotangent out: 4 + 16 + 4 + 16 B, plus
+        stage 4's fused pass A: 136 B;
       filter (forward, also in the recompute): 8 B per entry + 36 B per node."""
-    return {"rec_stage": 24.0 * nnz + 96.0 * N, "adj_a": 116.0 * N, "adj_b": 24.0 * nnz + 120.0 * N,
-            "adj_filter": 8.0 * nnz + 56.0 * N, "filter": 8.0 * nnz + 36.0 * N}
+    return {"rec_stage": 24.0 * nnz + 96.0 * N, "adj_b": 24.0 * nnz + 176.0 * N,
+            "adj_filter": 8.0 * nnz + 136.0 * N, "filter": 8.0 * nnz + 36.0 * N}
 
 
 def run_adjoint(lb, torch, args, nsteps=500, every=50, nx=512):
@@ -719,12 +722,12 @@ def run_adjoint(lb, torch, args, nsteps=500, every=50, nx=512):
                       dtype=torch.float32, device="cuda")
     phys = lb.Phys(C * C, MU)
     dt = float(lb.stable_dt(plan, lb.conserved_to_primitive(c0), s, C, MU).item())
-    # untimed warm-up: one checkpoint segment forward and backward, so that the
+    # untimed warm-up: two checkpoint segments forward and backward, so that the
     # autograd engine's device thread and the allocator's segment buffers exist
     # before the timed pass (the first backward otherwise carries about a second of
     # one-time set-up)
     cw = c0.clone().requires_grad_(True)
-    lb.domain_kinetic_energy(lb.rollout(plan, lb.to_primitive(cw), dt, min(every, nsteps), phys,
+    lb.domain_kinetic_energy(lb.rollout(plan, lb.to_primitive(cw), dt, min(2 * every, nsteps), phys,
                                         checkpoint_every=every), s).backward()
     del cw
     a, b = _events(torch)
@@ -750,13 +753,15 @@ def run_adjoint(lb, torch, args, nsteps=500, every=50, nx=512):
            "backward_over_forward": bwd_ms / fwd_ms, "ke_final": float(ke.item()),
            "grad_finite": bool(torch.isfinite(g).all().item()),
            "grad_norm_per_field": [float(x) for x in g.double().norm(dim=1).cpu()]}
-    # per-kernel breakdown: one segment of `every` steps forward and backward with
-    # launch timing on (CUDA events on the launching stream around every adjoint
-    # launch, around each step's four stage launches and each filter launch)
+    # per-kernel breakdown: two segments of `every` steps forward and backward with
+    # launch timing on (CUDA events on the launching stream around each step's four
+    # stage launches, each filter launch and every adjoint launch): the first
+    # segment steps plainly forward and is recomputed with recording backward, the
+    # second is recorded as it steps forward
     seg = min(every, nsteps)
     plan.set_profiling(True)
     c2 = c0.clone().requires_grad_(True)
-    ke2 = lb.domain_kinetic_energy(lb.rollout(plan, lb.to_primitive(c2), dt, seg, phys,
+    ke2 = lb.domain_kinetic_energy(lb.rollout(plan, lb.to_primitive(c2), dt, 2 * seg, phys,
                                               checkpoint_every=seg), s)
     ke2.backward()
     torch.cuda.synchronize()
@@ -767,10 +772,10 @@ def run_adjoint(lb, torch, args, nsteps=500, every=50, nx=512):
     alg = adjoint_kernel_bytes(nnz, ns.N)
     kernels = {}
     for key, kname, launches in (("rec_stage", "k_stage_rec<float> (recording stage)", "rec_stage_launches"),
-                                 ("adj_a", "k_adj_pointwise_rec<float> (pass A)", "adj_a_launches"),
-                                 ("adj_b", "k_adj_transpose<float> (pass B)", "adj_b_launches"),
-                                 ("adj_filter", "k_filter_adjoint<float> (filter transpose)",
-                                  "adj_filter_launches")):
+                                 ("adj_b", "k_adj_transpose<float> (pass B, pass A of the stage before fused)",
+                                  "adj_b_launches"),
+                                 ("adj_filter", "k_filter_adjoint<float> (filter transpose, stage 4's pass A "
+                                                "fused)", "adj_filter_launches")):
         n = prof[launches]
         ms = prof[key + "_ms"] / max(1, n)
         kernels[key] = {"kernel": kname, "launches": n, "mean_launch_ms": ms,
@@ -786,15 +791,17 @@ def run_adjoint(lb, torch, args, nsteps=500, every=50, nx=512):
     sms = prof["stage_ms"] / max(1, prof["stage_launches"])
     kernels["stage"] = {"kernel": "k_stage<float> (forward rollout)", "launches": prof["stage_launches"],
                         "mean_launch_ms": sms}
-    # backward time per step, kernel by kernel: one recorded recompute (4 recording
-    # stages + filter) and the reverse sweep (4 x (pass A + pass B) + filter transpose)
-    per_step = {"recorded_stages": 4 * kernels["rec_stage"]["mean_launch_ms"],
-                "recorded_filter": fms,
-                "pass_a": 4 * kernels["adj_a"]["mean_launch_ms"],
+    # per step of the full rollout, kernel by kernel: forward steps are plain except
+    # the last segment's, recorded as they go; backward recomputes every other
+    # segment with recording, and sweeps every step (4 x pass B + filter transpose)
+    f_rec = seg / nsteps
+    plain_step = 4 * sms + fms
+    rec_step = 4 * kernels["rec_stage"]["mean_launch_ms"] + fms
+    per_step = {"recorded_recompute": (1.0 - f_rec) * rec_step,
                 "pass_b": 4 * kernels["adj_b"]["mean_launch_ms"],
                 "filter_transpose": kernels["adj_filter"]["mean_launch_ms"]}
-    fwd_step = 4 * sms + fms
-    out["breakdown"] = {"segment_steps": seg, "kernels": kernels, "backward_ms_per_step_by_kernel": per_step,
+    fwd_step = (1.0 - f_rec) * plain_step + f_rec * rec_step
+    out["breakdown"] = {"profiled_steps": 2 * seg, "kernels": kernels, "backward_ms_per_step_by_kernel": per_step,
                         "backward_kernels_ms_per_step": sum(per_step.values()),
                         "forward_kernels_ms_per_step": fwd_step,
                         "backward_kernels_over_forward_kernels": sum(per_step.values()) / fwd_step,

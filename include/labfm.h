@@ -723,9 +723,11 @@ int labfm_rk_step_noalloc(const labfm_plan* plan, void* Q, double dt, int nsteps
  * blocks keeps the events from stalling the stream between every launch.
  * The adjoint calls are timed the same way: the four recording stage launches of
  * labfm_rk_step_record as one block (its filter launch counts as a filter
- * launch), and in the reverse sweep every pass A (pointwise derivative
- * adjoints), pass B (transposed-operator gather) and filter-transpose launch on
- * its own. */
+ * launch), and in the reverse sweep every pass B (transposed-operator gather)
+ * and filter-transpose launch on its own.  The reverse sweep of a step runs each
+ * stage's pass A (pointwise derivative adjoints) inside the launch that forms
+ * its cotangent (the filter transpose for stage 4, pass B of stage k for stage
+ * k - 1), so only labfm_rhs_adjoint launches pass A on its own (untimed). */
 typedef struct labfm_profile {
     double stage_ms;         /* summed duration of the fused RHS + RK stage launches */
     int64_t stage_launches;
@@ -734,7 +736,7 @@ typedef struct labfm_profile {
     int64_t dropped;         /* launches not timed because the event pool was full */
     double rec_stage_ms;     /* recording stage launches (labfm_rk_step_record) */
     int64_t rec_stage_launches;
-    double adj_a_ms;         /* adjoint pass A launches */
+    double adj_a_ms;         /* adjoint pass A launches (none in the reverse sweep: fused) */
     int64_t adj_a_launches;
     double adj_b_ms;         /* adjoint pass B launches */
     int64_t adj_b_launches;

@@ -841,22 +841,34 @@ def probe_momentum_grad(q, px, py, scale: float = 1.0, stream=None):
 class _Rollout(torch.autograd.Function):
     """nsteps time steps of a plan as a differentiable map q0 -> q_final.
 
-    Forward keeps a checkpoint of the state every `every` steps.  Backward walks
-    the segments last to first: it recomputes the segment from its checkpoint with
-    labfm_rk_step_record, keeping every step's stage states, then applies
-    labfm_rk_step_adjoint_recorded step by step in reverse."""
+    Forward keeps a checkpoint of the state every `every` steps, and records the
+    stage states of the last segment as it steps through it (labfm_rk_step_record,
+    the same arithmetic as labfm_rk_step), so that backward need not recompute
+    that segment.  Backward walks the segments last to first: it recomputes each
+    earlier segment from its checkpoint with labfm_rk_step_record, keeping every
+    step's stage states, then applies labfm_rk_step_adjoint_recorded step by step
+    in reverse."""
 
     @staticmethod
     def forward(ctx, q0, plan, dt, nsteps, phys, every):
         work = workspace(plan)
         q = q0.detach().clone()
         ckpts = []
+        # without a gradient to take (no_grad, or q0 not requiring one) nothing is recorded
+        last = ((nsteps - 1) // every) * every if (nsteps > 0 and ctx.needs_input_grad[0]) else nsteps
+        recorded = []
         for k in range(nsteps):
             if k % every == 0:
                 ckpts.append(q.clone())
-            rk_step(plan, q, dt, 1, phys, work=work)
+            if k >= last:
+                X = stage_states(plan)
+                rk_step_record(plan, q, X, dt, phys, work=work)
+                recorded.append(X)
+            else:
+                rk_step(plan, q, dt, 1, phys, work=work)
         ctx.plan, ctx.dt, ctx.nsteps, ctx.phys, ctx.every = plan, dt, nsteps, phys, every
         ctx.ckpts = ckpts
+        ctx.recorded_last = recorded
         return q
 
     @staticmethod
@@ -866,16 +878,21 @@ class _Rollout(torch.autograd.Function):
         work = workspace(plan)
         awork = adjoint_workspace(plan)
         for seg in range(len(ctx.ckpts) - 1, -1, -1):
-            k0 = seg * every
-            k1 = min(nsteps, k0 + every)
-            q = ctx.ckpts[seg].clone()
-            recorded = []
-            for _ in range(k0, k1):
-                X = stage_states(plan)
-                rk_step_record(plan, q, X, dt, phys, work=work)
-                recorded.append(X)
+            if seg == len(ctx.ckpts) - 1:
+                recorded = ctx.recorded_last  # recorded by the forward pass
+                ctx.recorded_last = None
+            else:
+                k0 = seg * every
+                k1 = min(nsteps, k0 + every)
+                q = ctx.ckpts[seg].clone()
+                recorded = []
+                for _ in range(k0, k1):
+                    X = stage_states(plan)
+                    rk_step_record(plan, q, X, dt, phys, work=work)
+                    recorded.append(X)
             for X in reversed(recorded):
                 rk_step_adjoint_recorded(plan, X, lam, dt, phys, work=awork)
+            recorded = None
         ctx.ckpts = None
         return lam, None, None, None, None, None
 

@@ -93,14 +93,12 @@ PlanView<T> tview(const labfm_plan* p) {
 // (own_coeffs) and its cotangent M_i: the twelve derivative adjoints g_i and the
 // own-value adjoints o_i.
 template <typename T, bool SCALED>
-__device__ __forceinline__ void node_adjoints(const PlanView<T>& P, int i, T a, T u, T v,
-                                              const T (&c)[8], const Packed<T>* M,
-                                              G8<T>* __restrict__ gout, Packed<T>* __restrict__ oout,
-                                              const Phys<T>& ph) {
+__device__ __forceinline__ void node_adjoints_m(const PlanView<T>& P, int i, T a, T u, T v,
+                                                const T (&c)[8], T ma, T mu, T mv,
+                                                G8<T>* __restrict__ gout, Packed<T>* __restrict__ oout,
+                                                const Phys<T>& ph) {
     const T is = SCALED ? P.inv_s[i] : T(1);
     const T s1 = SCALED ? is : T(1), s2 = SCALED ? is * is : T(1);
-    T ma, mu, mv;
-    unpack(M, i, ma, mu, mv);
     const T nu = ph.mu * exp_neg(a);
     T g[8];
     g[kGax] = (-u * ma - ph.c2 * mu) * s1;
@@ -117,6 +115,40 @@ __device__ __forceinline__ void node_adjoints(const PlanView<T>& P, int i, T a, 
     const T ou = -(c[0] * ma + c[2] * mu + c[4] * mv);
     const T ov = -(c[1] * ma + c[3] * mu + c[5] * mv);
     store(oout, i, oa, ou, ov);
+}
+
+template <typename T, bool SCALED>
+__device__ __forceinline__ void node_adjoints(const PlanView<T>& P, int i, T a, T u, T v,
+                                              const T (&c)[8], const Packed<T>* M,
+                                              G8<T>* __restrict__ gout, Packed<T>* __restrict__ oout,
+                                              const Phys<T>& ph) {
+    T ma, mu, mv;
+    unpack(M, i, ma, mu, mv);
+    node_adjoints_m<T, SCALED>(P, i, a, u, v, c, ma, mu, mv, gout, oout, ph);
+}
+
+// Pass A of the previous stage, fused into the epilogue of the kernel that forms
+// its cotangent (the filter transpose for stage 4, pass B of stage k for stage
+// k - 1): at node k, from the stage's recorded state X and combinations D, the
+// cotangent just computed in registers, written to g and o.  X == nullptr: none.
+template <typename T>
+struct FusedA {
+    const Packed<T>* X;
+    const D8<T>* D;
+    G8<T>* g;
+    Packed<T>* o;
+    Phys<T> ph;
+};
+
+template <typename T>
+__device__ __forceinline__ void fused_pass_a(const PlanView<T>& P, const FusedA<T>& fa, int k, T ma, T mu,
+                                             T mv) {
+    constexpr bool SCALED = std::is_same<T, float>::value;
+    T a, u, v;
+    unpack(fa.X, k, a, u, v);
+    T c[8];
+    d8_load(fa.D, k, c);
+    node_adjoints_m<T, SCALED>(P, k, a, u, v, c, ma, mu, mv, fa.g, fa.o, fa.ph);
 }
 
 // Pass A with the derivatives gathered at X (the single right-hand-side adjoint).
@@ -138,23 +170,6 @@ __global__ void k_adj_pointwise(PlanView<T> P, const Packed<T>* X, const Packed<
     node_adjoints<T, SCALED>(P, i, a, u, v, c, M, gout, oout, ph);
 }
 
-// Pass A from the derivative combinations the recording step kept (one thread
-// per node, no gather): the reverse sweep of labfm_rk_step_adjoint(_recorded).
-template <typename T, bool SCALED>
-__global__ void k_adj_pointwise_rec(PlanView<T> P, const Packed<T>* X, const D8<T>* __restrict__ D,
-                                    const Packed<T>* M, G8<T>* __restrict__ gout,
-                                    Packed<T>* __restrict__ oout, Phys<T> ph) {
-    for (int64_t k = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; k < P.N;
-         k += int64_t(gridDim.x) * blockDim.x) {
-        const int i = int(k);
-        T a, u, v;
-        unpack(X, i, a, u, v);
-        T c[8];
-        d8_load(D, i, c);
-        node_adjoints<T, SCALED>(P, i, a, u, v, c, M, gout, oout, ph);
-    }
-}
-
 // ---------------------------------------------------------------- pass B
 
 // The transposed records hold, per entry (i -> k), c_0 = w^x_ik, c_1 = w^y_ik,
@@ -165,10 +180,13 @@ __global__ void k_adj_pointwise_rec(PlanView<T> P, const Packed<T>* X, const D8<
 //   sum_d w^d_ik g_{v,d,i} = c_0 g_vx + c_1 g_vy + c_3 B + c_4 A.
 // MODE 0: out = Xbar.  MODE 1 (RK reverse sweep): Lam += Xbar, and when
 // Fnext is not null, Fnext = dt_i (bprev Lam + cprev Xbar).
+// With fa.X set, pass A of the previous stage follows at each node (fused_pass_a):
+// it writes o at the node whose own adjoints this kernel has already read, and a
+// G8 buffer other than gin.
 template <typename T, int G, int MODE>
 __global__ void k_adj_transpose(PlanView<T> PT, const G8<T>* gin, const Packed<T>* oin,
                                 const T* __restrict__ rsum, Packed<T>* out, Packed<T>* Lam,
-                                Packed<T>* Fnext, double dt, double bprev, double cprev) {
+                                Packed<T>* Fnext, double dt, double bprev, double cprev, FusedA<T> fa) {
     const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     const int64_t node = gt / G;
     const int gl = int(gt % G);
@@ -222,10 +240,12 @@ __global__ void k_adj_transpose(PlanView<T> PT, const G8<T>* gin, const Packed<T
     lu += xu;
     lv += xv;
     store(Lam, k, la, lu, lv);
-    if (Fnext) {
+    if (Fnext || fa.X) {
         const double h = PT.dt_node ? PT.dt_node[k] : dt;
         const T cb = T(h * bprev), cx = T(h * cprev);
-        store(Fnext, k, cb * la + cx * xa, cb * lu + cx * xu, cb * lv + cx * xv);
+        const T fa_ = cb * la + cx * xa, fu = cb * lu + cx * xu, fv = cb * lv + cx * xv;
+        if (Fnext) store(Fnext, k, fa_, fu, fv);
+        if (fa.X) fused_pass_a(PT, fa, k, fa_, fu, fv);
     }
 }
 
@@ -235,7 +255,7 @@ __global__ void k_adj_transpose(PlanView<T> PT, const G8<T>* gin, const Packed<T
 // F_out (if not null) = dt_k b4 Lam_out.
 template <typename T, int G>
 __global__ void k_filter_adjoint(PlanView<T> PT, const Packed<T>* lam, const T* __restrict__ rsum_f,
-                                 Packed<T>* Lam_out, Packed<T>* F_out, double dt, double b4) {
+                                 Packed<T>* Lam_out, Packed<T>* F_out, double dt, double b4, FusedA<T> fa) {
     const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     const int64_t node = gt / G;
     const int gl = int(gt % G);
@@ -268,10 +288,11 @@ __global__ void k_filter_adjoint(PlanView<T> PT, const Packed<T>* lam, const T* 
     const T r = rsum_f[k];
     const T la = a + sa - r * a, lu = u + su - r * u, lv = v + sv - r * v;
     store(Lam_out, k, la, lu, lv);
-    if (F_out) {
+    if (F_out || fa.X) {
         const double h = PT.dt_node ? PT.dt_node[k] : dt;
         const T cb = T(h * b4);
-        store(F_out, k, cb * la, cb * lu, cb * lv);
+        if (F_out) store(F_out, k, cb * la, cb * lu, cb * lv);
+        if (fa.X) fused_pass_a(PT, fa, k, cb * la, cb * lu, cb * lv);
     }
 }
 
@@ -481,6 +502,7 @@ struct AdjWork {
     Packed<T>* Ob;
     G8<T>* g;
     D8<T>* D;  // 4 x N: the stages' derivative combinations (recomputing sweep)
+    G8<T>* g2;  // the second derivative-adjoint buffer of the reverse sweep
 };
 
 template <typename T>
@@ -494,6 +516,7 @@ AdjWork<T> split_work(const labfm_plan* p, void* work) {
     w.Ob = base + 7 * p->N;
     w.g = reinterpret_cast<G8<T>*>(base + 8 * p->N);
     w.D = reinterpret_cast<D8<T>*>(w.g + p->N);
+    w.g2 = reinterpret_cast<G8<T>*>(w.D + 4 * p->N);
     return w;
 }
 
@@ -507,38 +530,28 @@ int pass_a_g(const labfm_plan* p, const Packed<T>* X, const Packed<T>* M, G8<T>*
     return LABFM_OK;
 }
 
-template <typename T>
-int pass_a_rec(const labfm_plan* p, const Packed<T>* X, const D8<T>* D, const Packed<T>* M, G8<T>* g,
-               Packed<T>* o, const Phys<T>& ph, cudaStream_t st) {
-    constexpr bool F = std::is_same<T, float>::value;
-    const int grid = int(std::min<int64_t>((p->N + 255) / 256, 152 * 16));
-    k_adj_pointwise_rec<T, F><<<grid, 256, 0, st>>>(view<T>(p), X, D, M, g, o, ph);
-    LABFM_LAUNCH_CHECK("adjoint pointwise kernel (recorded derivatives)");
-    return LABFM_OK;
-}
-
 template <typename T, int G>
 int pass_b_g(const labfm_plan* p, int mode, const G8<T>* g, const Packed<T>* o, Packed<T>* out,
-             Packed<T>* Lam, Packed<T>* Fnext, double dt, double bprev, double cprev,
+             Packed<T>* Lam, Packed<T>* Fnext, double dt, double bprev, double cprev, const FusedA<T>& fa,
              cudaStream_t st) {
     const int grid = int((p->N * G + p->block - 1) / p->block);
     const T* rs = static_cast<const T*>(p->rsum);
     if (mode == 0)
         k_adj_transpose<T, G, 0><<<grid, p->block, 0, st>>>(tview<T>(p), g, o, rs, out, Lam, Fnext, dt,
-                                                            bprev, cprev);
+                                                            bprev, cprev, fa);
     else
         k_adj_transpose<T, G, 1><<<grid, p->block, 0, st>>>(tview<T>(p), g, o, rs, out, Lam, Fnext, dt,
-                                                            bprev, cprev);
+                                                            bprev, cprev, fa);
     LABFM_LAUNCH_CHECK("adjoint transpose kernel");
     return LABFM_OK;
 }
 
 template <typename T, int G>
 int filt_adj_g(const labfm_plan* p, const Packed<T>* lam, Packed<T>* Lam, Packed<T>* F, double dt,
-               double b4, cudaStream_t st) {
+               double b4, const FusedA<T>& fa, cudaStream_t st) {
     const int grid = int((p->N * G + p->block - 1) / p->block);
     const T* rsf = static_cast<const T*>(p->rsum) + 5 * p->N;
-    k_filter_adjoint<T, G><<<grid, p->block, 0, st>>>(tview<T>(p), lam, rsf, Lam, F, dt, b4);
+    k_filter_adjoint<T, G><<<grid, p->block, 0, st>>>(tview<T>(p), lam, rsf, Lam, F, dt, b4, fa);
     LABFM_LAUNCH_CHECK("filter adjoint kernel");
     return LABFM_OK;
 }
@@ -561,14 +574,15 @@ int pass_a(const labfm_plan* p, const Packed<T>* X, const Packed<T>* M, G8<T>* g
 
 template <typename T>
 int pass_b(const labfm_plan* p, int mode, const G8<T>* g, const Packed<T>* o, Packed<T>* out,
-           Packed<T>* Lam, Packed<T>* Fnext, double dt, double bprev, double cprev, cudaStream_t st) {
-    LABFM_G_DISPATCH((pass_b_g<T, G>(p, mode, g, o, out, Lam, Fnext, dt, bprev, cprev, st)));
+           Packed<T>* Lam, Packed<T>* Fnext, double dt, double bprev, double cprev, const FusedA<T>& fa,
+           cudaStream_t st) {
+    LABFM_G_DISPATCH((pass_b_g<T, G>(p, mode, g, o, out, Lam, Fnext, dt, bprev, cprev, fa, st)));
 }
 
 template <typename T>
 int filt_adj(const labfm_plan* p, const Packed<T>* lam, Packed<T>* Lam, Packed<T>* F, double dt,
-             double b4, cudaStream_t st) {
-    LABFM_G_DISPATCH((filt_adj_g<T, G>(p, lam, Lam, F, dt, b4, st)));
+             double b4, const FusedA<T>& fa, cudaStream_t st) {
+    LABFM_G_DISPATCH((filt_adj_g<T, G>(p, lam, Lam, F, dt, b4, fa, st)));
 }
 
 template <typename T>
@@ -580,7 +594,8 @@ int rhs_adjoint_t(const labfm_plan* p, const void* fields, const void* lambda, v
     if ((rc = pack_fields(p, fields, w.X[0], st))) return rc;
     if ((rc = pack_fields(p, lambda, w.Fb, st))) return rc;
     if ((rc = pass_a<T>(p, w.X[0], w.Fb, w.g, w.Ob, ph, st))) return rc;
-    if ((rc = pass_b<T>(p, 0, w.g, w.Ob, w.Lam, nullptr, nullptr, 0.0, 0.0, 0.0, st))) return rc;
+    const FusedA<T> none{nullptr, nullptr, nullptr, nullptr, ph};
+    if ((rc = pass_b<T>(p, 0, w.g, w.Ob, w.Lam, nullptr, nullptr, 0.0, 0.0, 0.0, none, st))) return rc;
     return unpack_fields(p, w.Lam, grad, st);
 }
 
@@ -591,20 +606,24 @@ int adjoint_sweep_t(const labfm_plan* p, const Packed<T>* const (&X)[4], const D
                     double dt, const Phys<T>& ph, AdjWork<T>& w, cudaStream_t st) {
     int rc;
     labfm_plan* pm = const_cast<labfm_plan*>(p);  // only the launch-timing record changes
-    // filter transpose, then the stages backwards
-    if ((rc = pack_fields(p, lambda, w.Ob, st))) return rc;
+    // filter transpose (with pass A of stage 4 fused into it), then the stages
+    // backwards, each pass B with pass A of the stage before it fused in; the
+    // derivative adjoints alternate between two buffers, since pass B gathers its
+    // neighbours' while the fused pass A writes the next stage's
+    if ((rc = pack_fields(p, lambda, w.Fb, st))) return rc;
+    G8<T>* gbuf[2] = {w.g, w.g2};
     int ev = prof_begin(pm, kProfAdjFilter, st);
-    if ((rc = filt_adj<T>(p, w.Ob, w.Lam, w.Fb, dt, kRkB[3], st))) return rc;
+    const FusedA<T> a4{X[3], D + 3 * p->N, gbuf[0], w.Ob, ph};
+    if ((rc = filt_adj<T>(p, w.Fb, w.Lam, nullptr, dt, kRkB[3], a4, st))) return rc;
     prof_end(pm, ev, st);
     for (int k = 3; k >= 0; --k) {
-        ev = prof_begin(pm, kProfAdjA, st);
-        if ((rc = pass_a_rec<T>(p, X[k], D + k * p->N, w.Fb, w.g, w.Ob, ph, st))) return rc;
-        prof_end(pm, ev, st);
+        const int cur = (3 - k) & 1;
         const double bprev = k > 0 ? kRkB[k - 1] : 0.0;
         const double cprev = k > 0 ? kRkA[k - 1] - kRkB[k - 1] : 0.0;
+        const FusedA<T> next = k > 0 ? FusedA<T>{X[k - 1], D + (k - 1) * p->N, gbuf[cur ^ 1], w.Ob, ph}
+                                     : FusedA<T>{nullptr, nullptr, nullptr, nullptr, ph};
         ev = prof_begin(pm, kProfAdjB, st);
-        if ((rc = pass_b<T>(p, 1, w.g, w.Ob, nullptr, w.Lam, k > 0 ? w.Fb : nullptr, dt, bprev, cprev,
-                            st)))
+        if ((rc = pass_b<T>(p, 1, gbuf[cur], w.Ob, nullptr, w.Lam, nullptr, dt, bprev, cprev, next, st)))
             return rc;
         prof_end(pm, ev, st);
     }
@@ -642,14 +661,15 @@ int filter_adjoint_t(const labfm_plan* p, const void* lam_in, void* lam_out, voi
     AdjWork<T> w = split_work<T>(p, work);
     int rc;
     if ((rc = pack_fields(p, lam_in, w.Ob, st))) return rc;
-    if ((rc = filt_adj<T>(p, w.Ob, w.Lam, nullptr, 0.0, 0.0, st))) return rc;
+    const FusedA<T> none{nullptr, nullptr, nullptr, nullptr, Phys<T>{}};
+    if ((rc = filt_adj<T>(p, w.Ob, w.Lam, nullptr, 0.0, 0.0, none, st))) return rc;
     return unpack_fields(p, w.Lam, lam_out, st);
 }
 
 size_t adjoint_work_bytes(const labfm_plan* p) {
     if (p->dtype == LABFM_F32)
-        return size_t(p->N) * (8 * sizeof(Packed<float>) + sizeof(G8<float>) + 4 * sizeof(D8<float>));
-    return size_t(p->N) * (8 * sizeof(Packed<double>) + sizeof(G8<double>) + 4 * sizeof(D8<double>));
+        return size_t(p->N) * (8 * sizeof(Packed<float>) + 2 * sizeof(G8<float>) + 4 * sizeof(D8<float>));
+    return size_t(p->N) * (8 * sizeof(Packed<double>) + 2 * sizeof(G8<double>) + 4 * sizeof(D8<double>));
 }
 
 int check_adjoint(const labfm_plan* p, void* work, size_t work_bytes) {

@@ -136,8 +136,9 @@ def test_boundary_second_derivatives_exact_on_quartics(box):
             dy = oracle.minimum_image(ns.xy[col[sl], 1] - ns.xy[i, 1], ns.Ly, True)
             p = sum(ck * dx ** a * dy ** b for ck, (a, b) in zip(c, ex))
             exact = (2 * c[ex.index((2, 0))], c[ex.index((1, 1))], 2 * c[ex.index((0, 2))])
-            got = w[2:5, sl] @ p
-            scale = np.abs(w[2:5, sl]) @ np.abs(p) + 1.0
+            dp = p - c[0]  # difference form: p_j - p_i, p_i = p(0, 0)
+            got = w[2:5, sl] @ dp
+            scale = np.abs(w[2:5, sl]) @ np.abs(dp) + 1.0
             assert np.all(np.abs(got - exact) <= 1e-10 * scale), (i, got, exact)
 
 
