@@ -26,8 +26,9 @@
  *    labfm_build_stencils with a col buffer returns LABFM_ECAPACITY with
  *    *nnz_out = col_capacity + 1 before touching the device.
  *    "singular_node:<i>": labfm_build_weights also flags node i
- *    LABFM_NODE_SINGULAR (and counts it as failed).  Unset or any other value:
- *    nothing is injected.
+ *    LABFM_NODE_SINGULAR (and counts it as failed).  "timeout":
+ *    labfm_plan_device_status reports LABFM_ETIMEOUT as a bounded wait that ran
+ *    out would.  Unset or any other value: nothing is injected.
  *  - Node arrays are indexed 0..N-1.  Fields are structure-of-arrays, "3 x N":
  *    field f of node i at [f * N + i], f = 0 (ln rho), 1 (u), 2 (v).
  *  - Operator order in every weight array (Section 2, selector C^d):
@@ -449,10 +450,26 @@ int labfm_plan_set_staging(labfm_plan* plan, int stages, void* stream);
 int labfm_plan_set_wait_limit(labfm_plan* plan, int64_t limit_ns);
 
 /*
- * Device-side status of the plan's kernels since the last query: LABFM_OK, or
+ * Check of the evolved state for non-finite values during labfm_rk_step (and
+ * labfm_rk_step_host, labfm_rk_step_noalloc): after every `every`-th step of a
+ * call and after its last step, one pass over the state (12 or 24 bytes per
+ * node) sets LABFM_ENONFINITE for labfm_plan_device_status if any value of
+ * ln rho, u or v is NaN or infinite.  A diverging run is then caught without
+ * copying the state to the host.  every = 0 (the default) turns it off.  Steps
+ * replayed from a step graph are not checked.  No counterpart in the paper
+ * (failure detection).  Host-only call (the first enabling call allocates the
+ * status word, synchronously).
+ * Errors: EINVAL (every < 0), ENOMEM.
+ */
+int labfm_plan_set_check_finite(labfm_plan* plan, int every);
+
+/*
+ * Device-side status of the plan's kernels since the last query: LABFM_OK,
  * LABFM_ETIMEOUT when a bounded wait of the staged stage kernel ran out (that
- * step's results are then invalid).  Synchronises the device and clears the
- * status.
+ * step's results are then invalid), or LABFM_ENONFINITE when the state check of
+ * labfm_plan_set_check_finite found a non-finite value (the first status set
+ * since the last query is kept).  Synchronises the device and clears the status.
+ * With LABFM_FAULT=timeout it reports LABFM_ETIMEOUT without touching the device.
  *   status_out  host (output)
  */
 int labfm_plan_device_status(const labfm_plan* plan, int* status_out);

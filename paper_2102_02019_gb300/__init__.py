@@ -120,6 +120,7 @@ _SIGS = {
     "labfm_plan_set_staging": (_I32, [_P, _I32, _P]),
     "labfm_plan_device_status": (_I32, [_P, ctypes.POINTER(_I32)]),
     "labfm_plan_set_wait_limit": (_I32, [_P, _I64]),
+    "labfm_plan_set_check_finite": (_I32, [_P, _I32]),
     "labfm_step_graph_create": (_I32, [ctypes.POINTER(_P), _P, _P, ctypes.c_size_t, _D, ctypes.POINTER(_Phys)]),
     "labfm_step_graph_run": (_I32, [_P, _P, _I32, _P]),
     "labfm_step_graph_destroy": (_I32, [_P]),
@@ -408,8 +409,14 @@ class Plan:
         0 = one non-blocking test, which makes the waits run out)."""
         _check(lib.labfm_plan_set_wait_limit(self._h, int(limit_ns)))
 
+    def set_check_finite(self, every: int) -> None:
+        """labfm_plan_set_check_finite: check the state for non-finite values every
+        `every` steps of rk_step (and after its last); 0 turns it off."""
+        _check(lib.labfm_plan_set_check_finite(self._h, int(every)))
+
     def device_status(self) -> int:
-        """labfm_plan_device_status: LABFM_OK (0) or LABFM_ETIMEOUT (7); clears it."""
+        """labfm_plan_device_status: LABFM_OK (0), LABFM_ENONFINITE (6) or
+        LABFM_ETIMEOUT (7); clears it."""
         st = _I32(0)
         _check(lib.labfm_plan_device_status(self._h, ctypes.byref(st)))
         return st.value
@@ -627,6 +634,44 @@ def filter(plan: Plan, fields: torch.Tensor, out: torch.Tensor | None = None, st
     out = torch.empty_like(fields) if out is None else out
     _check(lib.labfm_filter(plan.handle, fp, _state(plan, out, "out"), _stream(stream)))
     return out
+
+
+def save_operator(path: str, row_ptr, col, w, kappa, s, **meta) -> None:
+    """Write a built operator (the inputs of labfm_plan_create: CSR row_ptr and col,
+    the FP64 weights (6, nnz), kappa and s) with any scalar metadata to one .npz
+    file, so that a run can resume without the neighbour search and weight build."""
+    import numpy as np
+    arrays = {k: t.detach().cpu().numpy() for k, t in
+              (("row_ptr", row_ptr), ("col", col), ("w", w), ("kappa", kappa), ("s", s))}
+    np.savez(path, **arrays, meta_keys=np.array(sorted(meta), dtype=object),
+             meta_values=np.array([meta[k] for k in sorted(meta)], dtype=object))
+
+
+def load_operator(path: str, device="cuda") -> dict:
+    """The operator save_operator wrote, as tensors on `device` (row_ptr, col, w,
+    kappa, s) plus its metadata under "meta"."""
+    import numpy as np
+    with np.load(path, allow_pickle=True) as f:
+        out = {k: torch.from_numpy(f[k]).to(device) for k in ("row_ptr", "col", "w", "kappa", "s")}
+        out["meta"] = dict(zip(f["meta_keys"].tolist(), f["meta_values"].tolist()))
+    return out
+
+
+def save_state(path: str, Q, step: int, t: float, dt: float, **meta) -> None:
+    """A checkpoint of the evolved state (ln rho, u, v) after `step` steps at time t
+    with time step dt (and scalar metadata), as one .npz file."""
+    import numpy as np
+    np.savez(path, Q=Q.detach().cpu().numpy(), step=np.int64(step), t=np.float64(t), dt=np.float64(dt),
+             meta_keys=np.array(sorted(meta), dtype=object),
+             meta_values=np.array([meta[k] for k in sorted(meta)], dtype=object))
+
+
+def load_state(path: str, device="cuda") -> dict:
+    """The checkpoint save_state wrote: Q on `device`, step, t, dt and "meta"."""
+    import numpy as np
+    with np.load(path, allow_pickle=True) as f:
+        return {"Q": torch.from_numpy(f["Q"]).to(device), "step": int(f["step"]), "t": float(f["t"]),
+                "dt": float(f["dt"]), "meta": dict(zip(f["meta_keys"].tolist(), f["meta_values"].tolist()))}
 
 
 def workspace(plan: Plan) -> torch.Tensor:

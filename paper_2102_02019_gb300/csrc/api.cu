@@ -40,6 +40,8 @@ bool fault_alloc() { return strcmp(fault_spec(), "alloc") == 0; }
 
 bool fault_capacity() { return strcmp(fault_spec(), "capacity") == 0; }
 
+bool fault_timeout() { return strcmp(fault_spec(), "timeout") == 0; }
+
 int64_t fault_singular_node() {
     const char* f = fault_spec();
     const char* key = "singular_node:";
@@ -258,10 +260,26 @@ extern "C" int labfm_plan_set_wait_limit(labfm_plan* p, int64_t limit_ns) {
     return LABFM_OK;
 }
 
+extern "C" int labfm_plan_set_check_finite(labfm_plan* p, int every) {
+    if (int rc = check_plan(p)) return rc;
+    if (every < 0) return set_error(LABFM_EINVAL, "every must be >= 0");
+    if (every > 0 && !p->dev_status) {
+        if (fault_alloc()) return injected_alloc_error("labfm_plan_set_check_finite");
+        LABFM_CUDA_TRY(cudaMalloc(reinterpret_cast<void**>(&p->dev_status), sizeof(int)));
+        LABFM_CUDA_TRY(cudaMemset(p->dev_status, 0, sizeof(int)));
+    }
+    p->check_every = every;
+    return LABFM_OK;
+}
+
 extern "C" int labfm_plan_device_status(const labfm_plan* p, int* status_out) {
     if (int rc = check_plan(p)) return rc;
     if (!status_out) return set_error(LABFM_EINVAL, "null status output");
     *status_out = LABFM_OK;
+    if (fault_timeout()) {  // LABFM_FAULT=timeout: as if a bounded wait had run out
+        *status_out = LABFM_ETIMEOUT;
+        return LABFM_OK;
+    }
     if (!p->dev_status) return LABFM_OK;
     LABFM_CUDA_TRY(cudaMemcpy(status_out, p->dev_status, sizeof(int), cudaMemcpyDeviceToHost));
     LABFM_CUDA_TRY(cudaMemset(p->dev_status, 0, sizeof(int)));

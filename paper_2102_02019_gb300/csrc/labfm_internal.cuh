@@ -38,6 +38,7 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 // Nothing is injected when the variable is unset or holds anything else.
 bool fault_alloc();
 bool fault_capacity();
+bool fault_timeout();
 int64_t fault_singular_node();  // the node to flag, or -1
 int injected_alloc_error(const char* where);
 
@@ -108,6 +109,7 @@ struct labfm_plan {
     int stage_grid[2] = {0, 0};
     int* dev_status = nullptr;   // device word: LABFM_ETIMEOUT after a bounded wait ran out
     uint64_t wait_ns = 1000000000ull;  // limit of each bounded wait (labfm_plan_set_wait_limit)
+    int check_every = 0;               // labfm_plan_set_check_finite: steps between state checks
     // transposed operator for the adjoint (labfm_plan_enable_adjoint): for node k
     // the entries (i, w_ik) of every row i whose stencil contains k, in the same
     // record layout as the forward operator, plus row sums of the forward weights

@@ -970,13 +970,46 @@ size_t rk_work_bytes(const labfm_plan* p) {
     return size_t(3) * size_t(p->N) * per + (p->persistent ? 64 : 0);
 }
 
+namespace {
+// LABFM_ENONFINITE into the plan's status word (unless a status is already set)
+// when any value of the packed state is not finite: one vote per warp, one
+// atomic per warp that saw one.
+template <typename T>
+__global__ void k_check_finite(int64_t N, const Packed<T>* __restrict__ X, int* status) {
+    bool bad = false;
+    for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < N;
+         i += int64_t(gridDim.x) * blockDim.x) {
+        T a, u, v;
+        unpack(X, int(i), a, u, v);
+        bad |= !(isfinite(a) && isfinite(u) && isfinite(v));
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicCAS(status, 0, LABFM_ENONFINITE);
+}
+
+int check_finite(const labfm_plan* p, const void* work, cudaStream_t st) {
+    const int grid = int(std::min<int64_t>((p->N + 255) / 256, 152 * 8));
+    if (p->dtype == LABFM_F32)
+        k_check_finite<float><<<grid, 256, 0, st>>>(p->N, static_cast<const Packed<float>*>(work) + p->N,
+                                                   p->dev_status);
+    else
+        k_check_finite<double><<<grid, 256, 0, st>>>(p->N, static_cast<const Packed<double>*>(work) + p->N,
+                                                    p->dev_status);
+    LABFM_LAUNCH_CHECK("state check kernel");
+    return LABFM_OK;
+}
+}  // namespace
+
 int launch_rk_steps(const labfm_plan* p, void* Q, void* work, double dt, int nsteps,
                     const labfm_phys* ph, cudaStream_t st) {
     if (nsteps == 0) return LABFM_OK;
     int rc;
     if ((rc = rk_pack(p, Q, work, st))) return rc;
-    for (int step = 0; step < nsteps; ++step)
+    const int every = p->dev_status ? p->check_every : 0;
+    for (int step = 0; step < nsteps; ++step) {
         if ((rc = rk_one_step(p, work, dt, ph, true, st))) return rc;
+        if (every > 0 && ((step + 1) % every == 0 || step + 1 == nsteps))
+            if ((rc = check_finite(p, work, st))) return rc;
+    }
     return rk_unpack(p, Q, work, st);
 }
 

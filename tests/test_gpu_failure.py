@@ -101,3 +101,53 @@ def test_injected_allocation_failure_leaves_device_memory_alone(lb, monkeypatch)
     lb.rk_step(plan, Q, 1e-4, 1, lb.Phys(C * C, MU))
     assert torch.isfinite(Q).all()
     plan.close()
+
+
+def test_state_check_reports_a_diverging_run(lb):
+    # the +-0.3 s lattice without node shifting goes non-finite within tens of steps
+    # (the filter amplifies a few modes); with the state check on, the run reports
+    # LABFM_ENONFINITE, and a finite run on the +-0.05 s lattice reports nothing
+    phys = lb.Phys(C * C, MU)
+    for jitter, diverges in ((0.3, True), (0.05, False)):
+        ns = li.tgv_lattice(64, m=4, h_over_s=1.7, jitter=jitter, seed=0)
+        xy, h, s, rp, col = _inputs(lb, ns)
+        wb = lb.build_weights(xy, h, s, ns.Lx, ns.Ly, rp, col, 4, residual=False)
+        for dtype in (torch.float64, torch.float32):
+            plan = lb.Plan(rp, col, wb["w"], wb["kappa"], s, dtype=dtype)
+            Q = torch.tensor(li.tgv_fields(ns.xy, C), dtype=dtype, device="cuda")
+            dt = float(lb.stable_dt(plan, Q, s, C, MU).item())
+            plan.set_check_finite(25)
+            lb.rk_step(plan, Q, dt, 300, phys)
+            finite = bool(torch.isfinite(Q).all().item())
+            status = plan.device_status()
+            assert finite != diverges, (jitter, dtype)
+            assert status == (6 if diverges else 0), (jitter, dtype, status)  # LABFM_ENONFINITE
+            assert plan.device_status() == 0  # the query clears it
+            # turned off, the same run reports nothing
+            plan.set_check_finite(0)
+            Q = torch.tensor(li.tgv_fields(ns.xy, C), dtype=dtype, device="cuda")
+            lb.rk_step(plan, Q, dt, 300, phys)
+            assert plan.device_status() == 0
+            with pytest.raises(lb.LabfmError):
+                plan.set_check_finite(-1)
+            plan.close()
+
+
+def test_injected_timeout_is_reported(lb, monkeypatch):
+    ns = li.tgv_lattice(24, 20, m=4, jitter=0.1, seed=84)
+    xy, h, s, rp, col = _inputs(lb, ns)
+    wb = lb.build_weights(xy, h, s, ns.Lx, ns.Ly, rp, col, 4)
+    plan = lb.Plan(rp, col, wb["w"], wb["kappa"], s, dtype=torch.float32)
+    assert plan.device_status() == 0
+    monkeypatch.setenv("LABFM_FAULT", "timeout")
+    assert plan.device_status() == 7  # LABFM_ETIMEOUT, as a bounded wait that ran out
+    monkeypatch.delenv("LABFM_FAULT")
+    assert plan.device_status() == 0
+    # an injected allocation failure of the status word
+    monkeypatch.setenv("LABFM_FAULT", "alloc")
+    with pytest.raises(lb.LabfmError) as ei:
+        plan.set_check_finite(5)
+    assert ei.value.status == 3
+    monkeypatch.delenv("LABFM_FAULT")
+    plan.set_check_finite(5)
+    plan.close()
