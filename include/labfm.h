@@ -29,6 +29,12 @@
  *    LABFM_NODE_SINGULAR (and counts it as failed).  "timeout":
  *    labfm_plan_device_status reports LABFM_ETIMEOUT as a bounded wait that ran
  *    out would.  Unset or any other value: nothing is injected.
+ *  - A caller's CSR (row_ptr N + 1 int32, col nnz int32) is checked before any
+ *    kernel indexes with it, by labfm_plan_create(_batched), labfm_build_weights,
+ *    labfm_stencil_optimise and labfm_modal_response: row_ptr[0] = 0, row_ptr
+ *    non-decreasing, row_ptr[N] = nnz where nnz is given, every column in [0, N).
+ *    A malformed one returns LABFM_EINVAL naming the problem; the check reads only
+ *    the declared buffers and synchronises the stream.
  *  - Node arrays are indexed 0..N-1.  Fields are structure-of-arrays, "3 x N":
  *    field f of node i at [f * N + i], f = 0 (ln rho), 1 (u), 2 (v).
  *  - Operator order in every weight array (Section 2, selector C^d):

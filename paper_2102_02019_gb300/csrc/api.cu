@@ -182,6 +182,7 @@ extern "C" int labfm_plan_create(labfm_plan** out, int64_t N, int64_t nnz, labfm
     if (nnz < 0 || nnz >= (int64_t(1) << 31)) return set_error(LABFM_EINVAL, "nnz out of range");
     if (dtype != LABFM_F32 && dtype != LABFM_F64) return set_error(LABFM_EINVAL, "unknown dtype");
     if (fault_alloc()) return injected_alloc_error("labfm_plan_create");
+    if (int rc = validate_csr(row_ptr, col, N, nnz, as_stream(stream))) return rc;
     const PlanInput in{N, nnz, row_ptr, col, w, kappa, s};
     return create_plan(out, &in, 1, dtype, stream);
 }
@@ -212,6 +213,9 @@ extern "C" int labfm_plan_create_batched(labfm_plan** out, int n_inst, const int
     if (rc == LABFM_OK && (Ntot >= (int64_t(1) << 31) - 1 || nnztot >= (int64_t(1) << 31)))
         rc = set_error(LABFM_EINVAL, "combined size out of range");
     if (rc == LABFM_OK && fault_alloc()) rc = injected_alloc_error("labfm_plan_create_batched");
+    for (int k = 0; k < n_inst && rc == LABFM_OK; ++k)
+        if ((rc = validate_csr(in[k].row_ptr, in[k].col, in[k].N, in[k].nnz, as_stream(stream))))
+            rc = set_error(LABFM_EINVAL, "instance " + std::to_string(k) + ": " + labfm_last_error());
     if (rc == LABFM_OK) rc = create_plan(out, in, n_inst, dtype, stream);
     delete[] in;
     return rc;

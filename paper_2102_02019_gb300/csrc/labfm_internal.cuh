@@ -62,6 +62,13 @@ int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int64_t* tota
                        void* scratch, size_t scratch_bytes, cudaStream_t st);
 size_t exclusive_scan_scratch_bytes(int64_t n);
 
+// Checks a caller's CSR before any kernel indexes with it: row_ptr[0] == 0,
+// row_ptr non-decreasing, row_ptr[N] == nnz (nnz < 0: not given; col then holds
+// row_ptr[N] entries), every column in [0, N).  Reads only row_ptr[0..N] and the
+// columns the row pointers cover, and those only once the row pointers passed.
+// Synchronises st.  EINVAL naming the first problem found.
+int validate_csr(const int32_t* row_ptr, const int32_t* col, int64_t N, int64_t nnz, cudaStream_t st);
+
 }  // namespace labfm
 
 // The prepared operator behind labfm_plan (see labfm.h).

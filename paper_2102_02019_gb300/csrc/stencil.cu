@@ -121,6 +121,64 @@ int exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, int64_t* tota
     return LABFM_OK;
 }
 
+// ---------------------------------------------------------------- CSR check
+
+namespace {
+__global__ void k_check_row_ptr(const int32_t* __restrict__ rp, int64_t N, int64_t nnz, int* flags) {
+    const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
+    bool bad = false;
+    for (int64_t i = gt; i < N; i += int64_t(gridDim.x) * blockDim.x) bad |= rp[i + 1] < rp[i];
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, 4);
+    if (gt == 0) {
+        if (rp[0] != 0) atomicOr(flags, 1);
+        if (nnz >= 0 && int64_t(rp[N]) != nnz) atomicOr(flags, 2);
+    }
+}
+
+__global__ void k_check_cols(const int32_t* __restrict__ col, int64_t n, int64_t N, int* flags) {
+    bool bad = false;
+    for (int64_t e = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+        const int32_t c = col[e];
+        bad |= c < 0 || int64_t(c) >= N;
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, 8);
+}
+}  // namespace
+
+int validate_csr(const int32_t* row_ptr, const int32_t* col, int64_t N, int64_t nnz, cudaStream_t st) {
+    int* f = nullptr;
+    LABFM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&f), sizeof(int), st));
+    int flags = 0, total = 0;
+    cudaError_t e = cudaMemsetAsync(f, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        const int g = int(std::min<int64_t>((N + 255) / 256, 152 * 8));
+        k_check_row_ptr<<<g, 256, 0, st>>>(row_ptr, N, nnz, f);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, f, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&total, row_ptr + N, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && flags == 0 && total > 0) {
+        if (!col) {
+            flags = 16;
+        } else {
+            const int g = int(std::min<int64_t>((int64_t(total) + 255) / 256, 152 * 8));
+            k_check_cols<<<g, 256, 0, st>>>(col, total, N, f);
+            e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaMemcpyAsync(&flags, f, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        }
+    }
+    cudaFreeAsync(f, st);
+    if (e != cudaSuccess) return cuda_error(e, "checking the CSR");
+    if (flags & 1) return set_error(LABFM_EINVAL, "row_ptr[0] is not 0");
+    if (flags & 2) return set_error(LABFM_EINVAL, "row_ptr[N] differs from nnz");
+    if (flags & 4) return set_error(LABFM_EINVAL, "row_ptr decreases");
+    if (flags & 16) return set_error(LABFM_EINVAL, "null col for a non-empty CSR");
+    if (flags & 8) return set_error(LABFM_EINVAL, "a column index is outside [0, N)");
+    return LABFM_OK;
+}
+
 // ---------------------------------------------------------------- cell list
 
 namespace {

@@ -952,6 +952,7 @@ extern "C" int labfm_build_weights(const double* xy, const double* h, const doub
         return set_error(LABFM_EINVAL, "order m must be even and in [2, 10], got " + std::to_string(m));
     if (!(Lx > 0.0) || !(Ly > 0.0)) return set_error(LABFM_EINVAL, "domain size must be positive");
     if (n_failed_out && fault_alloc()) return injected_alloc_error("labfm_build_weights");
+    if (int rc = validate_csr(row_ptr, col, N, nnz, as_stream(stream))) return rc;
     cudaStream_t st = as_stream(stream);
     unsigned long long* nf = nullptr;
     if (n_failed_out) {
@@ -1002,6 +1003,7 @@ extern "C" int labfm_stencil_optimise(const double* xy, const double* h0, const 
     if (max_iter < 0) return set_error(LABFM_EINVAL, "negative max_iter");
     if (!(resid_coef > 0.0)) return set_error(LABFM_EINVAL, "resid_coef must be positive");
     cudaStream_t st = as_stream(stream);
+    if (int rc = validate_csr(row_ptr, col, N, -1, st)) return rc;
     switch (m) {
         case 2: return launch_stencil_opt<2>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, alpha_out, st);
         case 4: return launch_stencil_opt<4>(xy, h0, s, N, Lx, Ly, periodic_mask, row_ptr, col, factor, amp_max, resid_coef, max_iter, h_out, solves_out, alpha_out, st);
@@ -1021,6 +1023,7 @@ extern "C" int labfm_modal_response(const double* xy, const double* s, int64_t N
     if (N <= 0 || N >= (int64_t(1) << 31) - 1) return set_error(LABFM_EINVAL, "N out of range");
     if (nk < 1 || nk > 4096) return set_error(LABFM_EINVAL, "nk out of range");
     cudaStream_t st = as_stream(stream);
+    if (int rc = validate_csr(row_ptr, col, N, nnz, st)) return rc;
     const int grid = int(std::min<int64_t>((N + 7) / 8, 1 << 20));
     k_modal_response<<<grid, 256, 0, st>>>(xy, s, N, Lx, Ly, periodic_mask & 1u, (periodic_mask >> 1) & 1u,
                                            row_ptr, col, nnz, w, nk, out);

@@ -120,6 +120,58 @@ def test_stencil_capacity_and_invalid_input(lb):
     assert ei.value.status == 1
 
 
+def test_malformed_csr_is_refused_before_any_kernel_uses_it(lb):
+    # a caller's CSR is checked when a plan, weights, an optimisation or a modal
+    # response is asked for it: row_ptr[0] = 0, non-decreasing, row_ptr[N] = nnz,
+    # columns in [0, N).  Every buffer here has the declared size; only its
+    # contents are wrong, so the checks read nothing out of bounds
+    ns = li.tgv_lattice(16, m=4, seed=1)
+    xy, h, s = _dev(ns.xy), _dev(ns.h), _dev(ns.s)
+    rp, col = lb.build_stencils(xy, h, ns.Lx, ns.Ly)
+    wb = lb.build_weights(xy, h, s, ns.Lx, ns.Ly, rp, col, 4)
+    N, nnz = ns.N, col.numel()
+    cases = {}
+    c = col.clone()
+    c[nnz // 2] = N
+    cases["column >= N"] = (rp, c)
+    c = col.clone()
+    c[3] = -1
+    cases["negative column"] = (rp, c)
+    r = rp.clone()
+    r[7], r[8] = r[8], r[7].clone() + 1
+    cases["row_ptr decreases"] = (r, col)
+    r = rp.clone()
+    r[0] = 1
+    cases["row_ptr[0] != 0"] = (r, col)
+    for name, (r, c) in cases.items():
+        with pytest.raises(lb.LabfmError) as ei:
+            lb.Plan(r, c, wb["w"], wb["kappa"], s, dtype=torch.float32)
+        assert ei.value.status == 1, name
+        with pytest.raises(lb.LabfmError) as ei:
+            lb.build_weights(xy, h, s, ns.Lx, ns.Ly, r, c, 4)
+        assert ei.value.status == 1, name
+        with pytest.raises(lb.LabfmError):
+            lb.modal_response(xy, s, ns.Lx, ns.Ly, r, c, wb["w"], nk=4)
+        with pytest.raises(lb.LabfmError):
+            lb.stencil_optimise(xy, h, s, ns.Lx, ns.Ly, r, c, 4, max_iter=1)
+    # row_ptr[N] != nnz: the plan is given one column fewer than the rows cover
+    with pytest.raises(lb.LabfmError) as ei:
+        lb.Plan(rp, col[:-1], wb["w"][:, :-1], wb["kappa"], s, dtype=torch.float64)
+    assert ei.value.status == 1 and "row_ptr[N]" in str(ei.value)
+    # a batched plan names the instance
+    inst = [dict(row_ptr=rp, col=col, w=wb["w"], kappa=wb["kappa"], s=s),
+            dict(row_ptr=rp, col=cases["column >= N"][1], w=wb["w"], kappa=wb["kappa"], s=s)]
+    with pytest.raises(lb.LabfmError) as ei:
+        lb.Plan.batched(inst, dtype=torch.float32)
+    assert ei.value.status == 1 and "instance 1" in str(ei.value)
+    # the well-formed CSR still makes a plan that steps
+    plan = lb.Plan(rp, col, wb["w"], wb["kappa"], s, dtype=torch.float32)
+    Q = _dev(li.tgv_fields(ns.xy, 10.0), torch.float32)
+    lb.rk_step(plan, Q, 1e-4, 2, lb.Phys(100.0, 0.005))
+    assert bool(torch.isfinite(Q).all())
+    plan.close()
+
+
 # ---------------------------------------------------------------- weights
 
 def _weight_errors(c):
