@@ -214,3 +214,109 @@ def step_vjp_bound(q, lam, lam_out, dt, w, kappa, rp, col, c2, mu, G=4):
     # result through the transposed Jacobian like E_F
     return (8 * U32 * (np.abs(lam_out) + np.abs(lam4)) + EF
             + 2 * dt * bsum * (Ev + Sprop + 3 * U32 * S4))
+
+
+# ---------------------------------------------------------------- boundaries (Section 7.1)
+
+DERIVS = ("ax", "ay") + tuple(f + op for f in ("u", "v") for op in ("x", "y", "xx", "xy", "yy"))
+
+
+def _node_rhs(kind, n, d, q, c, mu, g, target, L, mach, rho0, sigma):
+    """(R_a, R_u, R_v) at one boundary node from its derivatives d and state q, as
+    the oracle's boundary_rhs forms it (walls: the LODI wall with u held at zero)."""
+    from oracle import boundary_oracle as bo
+    if kind == bo.WALL:
+        nx, ny = float(n[0]), float(n[1])
+        rho = np.exp(q[0])
+        a_xi = nx * d["ax"] + ny * d["ay"]
+        du_xi = nx * (nx * d["ux"] + ny * d["uy"]) + ny * (nx * d["vx"] + ny * d["vy"])
+        t = (-ny, nx)
+        du_eta = t[0] * (t[0] * d["ux"] + t[1] * d["uy"]) + t[1] * (t[0] * d["vx"] + t[1] * d["vy"])
+        Ra, _ = bo.wall_rhs(rho, c, c * c * rho * a_xi, du_xi, du_eta, nx * g[0] + ny * g[1])
+        return np.array([Ra, 0.0, 0.0])
+    return np.array(bo.open_boundary_rhs(kind, n, d, q, c, mu, g, target, L, mach, rho0, sigma))
+
+
+def _abs_terms(kind, n, d, q, c, mu, g, target, L, mach, rho0, sigma):
+    """S: the sum of the absolute values of the terms each boundary formula adds up
+    (every product, relaxation and wave amplitude by its magnitude), per field.
+    Frame components are bounded by the sums of the (x, y) components' magnitudes,
+    and each viscous bracket (4/3 + 1 + 1/3 of frame second derivatives) by 8/3 of
+    the summed magnitudes of both fields' Hessians."""
+    from oracle import boundary_oracle as bo
+    nx, ny = abs(float(n[0])), abs(float(n[1]))
+    a, u, v = (float(x) for x in q)
+    rho = np.exp(a)
+    p = c * c * rho
+    axi = nx * abs(d["ax"]) + ny * abs(d["ay"])
+    aeta = ny * abs(d["ax"]) + nx * abs(d["ay"])
+    uxi = nx * abs(u) + ny * abs(v)
+    ueta = ny * abs(u) + nx * abs(v)
+    grad = abs(d["ux"]) + abs(d["uy"]) + abs(d["vx"]) + abs(d["vy"])  # bounds every frame velocity derivative
+    hess = sum(abs(d[f + "xx"]) + 2 * abs(d[f + "xy"]) + abs(d[f + "yy"]) for f in ("u", "v"))
+    visc = 8.0 / 3.0 * hess
+    L1 = 0.5 * (uxi + c) * (p * axi + rho * c * grad)
+    if kind == bo.WALL:
+        gn = nx * abs(g[0]) + ny * abs(g[1])
+        return np.array([(2 * L1 + rho * c * gn) / (rho * c * c) + grad, 0.0, 0.0])
+    T4 = 0.5 * (ueta * p * aeta + p * grad + rho * c * ueta * grad)
+    V4 = 0.5 * mu * c * visc
+    if kind == bo.OUTFLOW:
+        L3 = uxi * grad
+        L4 = sigma / (2 * L) * c * (1 - mach * mach) * (p + abs(target[0])) + (1 + mach) * T4 + V4
+    else:
+        T3 = ueta * grad + p * aeta / rho
+        V3 = mu / rho * visc
+        L3 = sigma * c / L * (ueta + abs(target[1])) + T3 + V3
+        L4 = sigma * rho0 * c * c * (1 - mach * mach) / L * (uxi + abs(target[0])) + T4 + V4
+    gsum = abs(g[0]) + abs(g[1])
+    Sa = (L4 + L1) / (rho * c * c) + ueta * aeta + grad
+    Sxi = (L4 + L1) / (rho * c) + ueta * grad + mu / rho * visc + gsum
+    Seta = L3 + ueta * grad + p * aeta / rho + mu / rho * visc + gsum
+    return np.array([Sa, nx * Sxi + ny * Seta, ny * Sxi + nx * Seta])
+
+
+def boundary_rhs_bound(q, w, rp, col, bnd, c, mu, g=(0.0, 0.0), K=16):
+    """Elementwise budget of one FP32 right-hand side of a domain with boundaries
+    against the FP64 oracle (same weights).  Off the boundary nodes: rhs_bound (eq.
+    icns) plus the body force's rounding.  At a boundary node (wall, inflow,
+    outflow): the derivative budgets B_k propagated through the node's formula
+    linearly, sum_k |dR/dd_k| B_k (the formulas are linear in each derivative, so
+    central differences give these partials exactly up to rounding); the state's
+    own rounding and the float exp (2 ulp, argument rounded), sum_f |dR/dq_f| (2 +
+    |a|) u |q_f|; and K u S for the roundings inside the formula, S the sum of the
+    absolute values of its terms and K = 16 the longest chain of operations through
+    which one rounding can pass (frame rotation, wave amplitude, relaxation, the
+    LODI combination and the rotation back)."""
+    from oracle import boundary_oracle as bo
+    B, D = derivative_bounds(q, w, rp, col)
+    out = rhs_bound(q, w, rp, col, c * c, mu)
+    out[1] += 4 * U32 * abs(g[0])
+    out[2] += 4 * U32 * abs(g[1])
+    sig = bnd.get("sigma", 0.278)
+    for b, i in enumerate(bnd["nodes"]):
+        kind = int(bnd["kind"][b])
+        n = bnd["normal"][b]
+        tgt = bnd["target"][b] if kind != bo.OUTFLOW else (bnd["target"][b][0], 0.0)
+        tg = tgt[0] if kind == bo.OUTFLOW else tuple(tgt)
+        d = {k: float(D[k][i]) for k in DERIVS}
+        qi = q[:, i].astype(float)
+        args = (c, mu, g, tg, bnd["L"], bnd["mach"], bnd["rho0"], sig)
+        tot = np.zeros(3)
+        for k in DERIVS:
+            hk = 1e-6 * (abs(d[k]) + 1.0)
+            dp, dm = dict(d), dict(d)
+            dp[k] += hk
+            dm[k] -= hk
+            Jk = (_node_rhs(kind, n, dp, qi, *args) - _node_rhs(kind, n, dm, qi, *args)) / (2 * hk)
+            tot += np.abs(Jk) * B[k][i]
+        for f in range(3):
+            hf = 1e-6 * (abs(qi[f]) + 1.0)
+            qp, qm = qi.copy(), qi.copy()
+            qp[f] += hf
+            qm[f] -= hf
+            Jf = (_node_rhs(kind, n, d, qp, *args) - _node_rhs(kind, n, d, qm, *args)) / (2 * hf)
+            tot += np.abs(Jf) * (2.0 + abs(qi[0])) * U32 * abs(qi[f])
+        S = _abs_terms(kind, n, d, qi, c, mu, g, tgt, bnd["L"], bnd["mach"], bnd["rho0"], sig)
+        out[:, i] = tot + K * U32 * S
+    return out

@@ -277,3 +277,76 @@ def test_boundary_arguments_are_checked(lb, box):
     rp, col, w, _ = box.op
     assert np.all(_rel_l2(R, oracle.rhs(q, w[:5], rp, col, C * C, MU)) <= 1e-12)
     plan.close()
+
+
+def test_lamb_oseen_workload_sampled(lb):
+    # the finest box of the Lamb-Oseen study (R_c/s = 16: 400 x 400, 160,400 nodes):
+    # the GPU-built operator at sampled rows of every kind against the oracle's rows,
+    # and the FP64 right-hand side of the vortex state (inflow and outflow active) at
+    # those rows against the oracle with the same weights, to 1e-12
+    from tests import lamb_oseen as lo
+    n = 400
+    ns = li.open_box(n, n, m=6, jitter=0.05, seed=0)
+    cols, normals = li.channel_walls(ns)
+    xy, h, s = _dev(ns.xy), _dev(ns.h), _dev(ns.s)
+    gop = lb.build_wall_operator(xy, h, s, ns.Lx, ns.Ly, 6, 4, _dev(cols, torch.int32), _dev(normals), 1.7,
+                                 periodic=(False, True), check=True)
+    assert gop["n_failed"] == 0
+    rng = np.random.default_rng(31)
+    row = ns.meta["row"]
+    pick = [rng.choice(np.flatnonzero(row == q), 8, replace=False) for q in range(5)]
+    pick.append(rng.choice(np.flatnonzero(row == 5), 16, replace=False))
+    rows = np.unique(np.concatenate(pick))
+    rp_o, col_o, w_o, _ = bo.channel_operator(ns, 6, 4, rows=rows)
+    rp = gop["row_ptr"].cpu().numpy()
+    col = gop["col"].cpu().numpy()
+    w = gop["w"].cpu().numpy()
+    for k, i in enumerate(rows):
+        sl, so = slice(rp[i], rp[i + 1]), slice(rp_o[k], rp_o[k + 1])
+        assert np.array_equal(col[sl], col_o[so]), i
+        if row[i] <= 2:
+            assert np.abs(w[:2, sl] - w_o[:2, so]).max() <= 1e-12 * np.abs(w_o[:2, so]).max(), i
+    c = 1.0 / li.LAMB_OSEEN_MACH
+    mu = li.LAMB_OSEEN_RC_OVER_H / li.LAMB_OSEEN_RE
+    q = li.lamb_oseen_fields(ns.xy, c, centre=(0.5 * ns.Lx, 0.5))
+    n_b = cols.shape[0] // 2
+    kind = np.array([bo.INFLOW] * n_b + [bo.OUTFLOW] * n_b, dtype=np.int32)
+    target = np.zeros((2 * n_b, 2))
+    target[:n_b, 0] = 1.0
+    target[n_b:, 0] = c * c
+    bnd = {"nodes": cols[:, 0], "normal": normals, "kind": kind, "target": target, "L": ns.Lx,
+           "mach": li.LAMB_OSEEN_MACH, "rho0": 1.0, "sigma": lo.sigma()}
+    plan = lb.Plan(gop["row_ptr"], gop["col"], gop["w"], gop["kappa"], s, dtype=torch.float64)
+    plan.set_boundaries(_dev(bnd["nodes"], torch.int32), _dev(normals), _dev(kind, torch.int32), _dev(target),
+                        sigma=bnd["sigma"], L=bnd["L"], mach=bnd["mach"], rho0=1.0)
+    # perturb the far field so that the boundary terms are not at rest
+    q[1] += 0.01 * li.smooth_perturbation(ns.xy, kmax=3, seed=2, Lx=ns.Lx, Ly=ns.Ly)
+    R = lb.rhs(plan, _dev(q), lb.Phys(c * c, mu)).cpu().numpy()
+    plan.close()
+    cnt = np.zeros(ns.N, dtype=np.int64)
+    cnt[rows] = rp[rows + 1] - rp[rows]
+    rps = np.concatenate([[0], np.cumsum(cnt)])
+    idx = np.concatenate([np.arange(rp[i], rp[i + 1]) for i in rows])
+    Ro = bo.boundary_rhs(q, (rps, col[idx], w[:, idx], None), bnd, c, mu)
+    for f in range(3):
+        err = np.abs(R[f][rows] - Ro[f][rows]).max() / np.abs(Ro[f][rows]).max()
+        assert err <= 1e-12, (f, err)
+
+
+def test_open_box_fp32_rhs_within_derived_budget(lb, box):
+    # one FP32 right-hand side (FP32 state, nondimensional FP32 weights) against the
+    # FP64 oracle with the same operator, elementwise within the budget derived in
+    # tests/fp32_budget.py (eq. icns off the boundary, the linearised inflow and
+    # outflow formulas on it)
+    from tests.fp32_budget import boundary_rhs_bound
+    plan = box.plan(lb, torch.float32)
+    q = _state(box.ns, seed=11)
+    R = lb.rhs(plan, _dev(q, torch.float32), lb.Phys(C * C, MU)).double().cpu().numpy()
+    plan.close()
+    Ro = bo.boundary_rhs(q, box.op, box.bnd, C, MU)
+    rp, col, w, _ = box.op
+    B = boundary_rhs_bound(q, w, rp, col, box.bnd, C, MU)
+    ratio = np.abs(R - Ro) / B
+    nb = box.bnd["nodes"]
+    print("FP32 open box: max error / budget, all nodes", ratio.max(), "boundary nodes", ratio[:, nb].max())
+    assert ratio.max() <= 1.0, ratio.max()

@@ -373,3 +373,26 @@ def test_channel_workload_rhs_sampled(lb, ch512):
             B[2] += 4 * U32 * abs(g[1])
             ratio = np.abs(R[:, icns] - Ro[:, icns]) / B[:, icns]
             assert ratio.max() <= 1.0, ratio.max()
+
+
+@pytest.mark.parametrize("g", [(0.0, 0.0), (0.3, -0.2)])
+def test_channel_fp32_rhs_within_derived_budget(lb, ch, g):
+    # one FP32 right-hand side of the channel (no-slip walls in LODI form) against
+    # the FP64 oracle with the same operator, elementwise within the budget derived in
+    # tests/fp32_budget.py
+    from tests.fp32_budget import boundary_rhs_bound
+    ns = ch.ns
+    plan = ch.plan(lb, torch.float32)
+    q = li.perturbed_tgv_fields(ns.xy, 10.0, amplitude=0.05, kmax=4)
+    q[1:, ch.wall_nodes] = 0.0
+    R = lb.rhs(plan, _dev(q, torch.float32), lb.Phys(100.0, 0.01, g[0], g[1])).double().cpu().numpy()
+    plan.close()
+    Ro = bo.channel_rhs(q, ch.op, ns, 10.0, 0.01, g)
+    rp, col, w, _ = ch.op
+    bnd = {"nodes": ch.wall_nodes, "normal": ch.normals, "kind": np.zeros(len(ch.wall_nodes), dtype=np.int32),
+           "target": np.zeros((len(ch.wall_nodes), 2)), "L": 1.0, "mach": 0.0, "rho0": 1.0}
+    B = boundary_rhs_bound(q, w, rp, col, bnd, 10.0, 0.01, g)
+    ratio = np.abs(R - Ro) / np.where(B > 0, B, np.inf)
+    assert np.all(R[1:, ch.wall_nodes] == 0.0)
+    print("FP32 channel: max error / budget", ratio.max(), "walls", ratio[0, ch.wall_nodes].max())
+    assert ratio.max() <= 1.0, ratio.max()
