@@ -87,6 +87,59 @@ def test_rbf_scaling_does_not_change_weights():
     assert np.allclose(a["w"], b["w"], rtol=1e-9, atol=1e-9 * np.abs(a["w"]).max())
 
 
+@pytest.mark.parametrize("m", [4, 6, 8])
+def test_h_scaling_leaves_the_solution_unchanged(m):
+    # Section 2 (vector H): scaling the monomials and the selectors by powers of h
+    # improves the conditioning of M but leaves the exact weights unchanged.  The
+    # unscaled system (monomials x^a y^b / (a! b!) in physical units, selectors with
+    # a unit entry at the derivative's position) solved by LAPACK gives the oracle's
+    # weights to within its conditioning
+    ns = li.tgv_lattice(24, m=m, h_over_s=li.H_OVER_S[m], jitter=0.2, seed=40 + m)
+    rows = np.array([5, 123, 400])
+    rp, col = o.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly, rows=rows)
+    ref = o.build_weights(ns.xy, ns.h, ns.s, rp, col, m, ns.Lx, ns.Ly, rows=rows)
+    ex = o.monomial_exponents(m)
+    unit = {"x": [(1, 0)], "y": [(0, 1)], "xx": [(2, 0)], "xy": [(1, 1)], "yy": [(0, 2)]}
+    for k, i in enumerate(rows):
+        nb = col[rp[k]:rp[k + 1]]
+        dx, dy = o.offsets(ns.xy, np.full(len(nb), i), nb, ns.Lx, ns.Ly)
+        X = np.stack([dx ** a * dy ** b / (math.factorial(a) * math.factorial(b)) for a, b in ex], axis=1)
+        W = o.abf_matrix(dx, dy, ns.h[i], m)
+        M = X.T @ W
+        for d, op in enumerate(("x", "y", "xx", "xy", "yy")):
+            C = np.array([1.0 if e in unit[op] else 0.0 for e in ex])
+            w = W @ np.linalg.solve(M, C)
+            got = ref["w"][d, rp[k]:rp[k + 1]]
+            cond = np.linalg.cond(M, 1)
+            assert np.abs(w - got).max() <= max(1e-12, 100 * cond * np.finfo(float).eps) * np.abs(got).max(), \
+                (m, i, op, np.abs(w - got).max() / np.abs(got).max(), cond)
+
+
+@pytest.mark.parametrize("m", [4, 6, 8])
+def test_weights_follow_the_lattice_symmetries(m):
+    # on an unjittered lattice every stencil is symmetric under x -> -x, y -> -y and
+    # x <-> y, so the weights must be: w^x odd in x and even in y, w^xx even in both,
+    # w^xy odd in each, and w^x(dx, dy) = w^y(dy, dx), w^xx(dx, dy) = w^yy(dy, dx)
+    ns = li.tgv_lattice(16, m=m, h_over_s=li.H_OVER_S[m], jitter=0.0, seed=0)
+    rows = np.array([0, 77])
+    rp, col = o.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly, rows=rows)
+    wb = o.build_weights(ns.xy, ns.h, ns.s, rp, col, m, ns.Lx, ns.Ly, rows=rows)
+    for k, i in enumerate(rows):
+        nb = col[rp[k]:rp[k + 1]]
+        dx, dy = o.offsets(ns.xy, np.full(len(nb), i), nb, ns.Lx, ns.Ly)
+        key = {(round(a / ns.s[i]), round(b / ns.s[i])): e for e, (a, b) in enumerate(zip(dx, dy))}
+        w = wb["w"][:, rp[k]:rp[k + 1]]
+        tol = 1e-9 * np.abs(w).max(axis=1)
+        for (a, b), e in key.items():
+            mx, my, sw = key[(-a, b)], key[(a, -b)], key[(b, a)]
+            for d, (sx, sy) in enumerate(((-1, 1), (1, -1), (1, 1), (-1, -1), (1, 1))):
+                assert abs(w[d, mx] - sx * w[d, e]) <= tol[d], (m, "x-mirror", d)
+                assert abs(w[d, my] - sy * w[d, e]) <= tol[d], (m, "y-mirror", d)
+            assert abs(w[0, sw] - w[1, e]) <= tol[0] and abs(w[2, sw] - w[4, e]) <= tol[2]
+            assert abs(w[3, sw] - w[3, e]) <= tol[3]
+            assert abs(w[5, mx] - w[5, e]) <= tol[5] and abs(w[5, sw] - w[5, e]) <= tol[5]
+
+
 # --------------------------------------------- unisolvent stencils: classical FD
 
 def _single_node_set(offs, s, h):
