@@ -93,26 +93,36 @@ def test_h_scaling_leaves_the_solution_unchanged(m):
     # improves the conditioning of M but leaves the exact weights unchanged.  The
     # unscaled system (monomials x^a y^b / (a! b!) in physical units, selectors with
     # a unit entry at the derivative's position) solved by LAPACK gives the oracle's
-    # weights to within its conditioning
-    ns = li.tgv_lattice(24, m=m, h_over_s=li.H_OVER_S[m], jitter=0.2, seed=40 + m)
-    rows = np.array([5, 123, 400])
-    rp, col = o.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly, rows=rows)
-    ref = o.build_weights(ns.xy, ns.h, ns.s, rp, col, m, ns.Lx, ns.Ly, rows=rows)
+    # weights to within the conditioning of both.  A jittered cloud with spacing
+    # s = 0.6 keeps the unscaled system solvable at m = 8 while h^k still spans
+    # more than a decade
+    s0 = 0.6
+    h0 = li.H_OVER_S[m] * s0
+    rng = np.random.default_rng(40 + m)
+    k = int(np.ceil(2 * h0 / s0)) + 1
+    g = np.array([(i, j) for i in range(-k, k + 1) for j in range(-k, k + 1) if (i, j) != (0, 0)], dtype=float)
+    offs = (g + rng.uniform(-0.2, 0.2, g.shape)) * s0
+    offs = offs[np.hypot(offs[:, 0], offs[:, 1]) <= 2 * h0]
+    xy = np.vstack([[50.0, 50.0], 50.0 + offs])
+    N = xy.shape[0]
+    rp = np.array([0, N - 1])
+    col = np.arange(1, N, dtype=np.int32)
+    ref = o.build_weights(xy, np.full(N, h0), np.full(N, s0), rp, col, m, 100.0, 100.0, rows=np.array([0]),
+                          want_cond=True)
     ex = o.monomial_exponents(m)
     unit = {"x": [(1, 0)], "y": [(0, 1)], "xx": [(2, 0)], "xy": [(1, 1)], "yy": [(0, 2)]}
-    for k, i in enumerate(rows):
-        nb = col[rp[k]:rp[k + 1]]
-        dx, dy = o.offsets(ns.xy, np.full(len(nb), i), nb, ns.Lx, ns.Ly)
-        X = np.stack([dx ** a * dy ** b / (math.factorial(a) * math.factorial(b)) for a, b in ex], axis=1)
-        W = o.abf_matrix(dx, dy, ns.h[i], m)
-        M = X.T @ W
-        for d, op in enumerate(("x", "y", "xx", "xy", "yy")):
-            C = np.array([1.0 if e in unit[op] else 0.0 for e in ex])
-            w = W @ np.linalg.solve(M, C)
-            got = ref["w"][d, rp[k]:rp[k + 1]]
-            cond = np.linalg.cond(M, 1)
-            assert np.abs(w - got).max() <= max(1e-12, 100 * cond * np.finfo(float).eps) * np.abs(got).max(), \
-                (m, i, op, np.abs(w - got).max() / np.abs(got).max(), cond)
+    dx, dy = offs[:, 0], offs[:, 1]
+    X = np.stack([dx ** a * dy ** b / (math.factorial(a) * math.factorial(b)) for a, b in ex], axis=1)
+    W = o.abf_matrix(dx, dy, h0, m)
+    M = X.T @ W
+    cond = max(np.linalg.cond(M, 1), ref["cond1"][0])
+    assert cond < 1e12, cond  # the comparison is meaningful
+    for d, op in enumerate(("x", "y", "xx", "xy", "yy")):
+        C = np.array([1.0 if e in unit[op] else 0.0 for e in ex])
+        w = W @ np.linalg.solve(M, C)
+        got = ref["w"][d]
+        err = np.abs(w - got).max() / np.abs(got).max()
+        assert err <= max(1e-12, 100 * cond * np.finfo(float).eps), (m, op, err, cond)
 
 
 @pytest.mark.parametrize("m", [4, 6, 8])
