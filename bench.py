@@ -40,6 +40,7 @@ def workload_config(nx):
     return dict(WORKLOAD, workload=f"taylor-green {nx}x{nx} jittered lattice ({nx * nx} nodes), "
                 "m=8, h/s=2.8 (reduced size)", nodes=nx * nx)
 SAMPLE_ROWS = 2048
+PROFILE_EVERY = 5  # timed steps per step whose launches carry CUDA events
 
 
 def parse():
@@ -627,7 +628,7 @@ def run_channel(lb, torch, args, nx=512):
     Q = q0.clone()
     lb.rk_step(plan, Q, dt, args.warmup, phys, work=work)
     torch.cuda.synchronize()
-    plan.set_profiling(True)
+    plan.set_profiling(True, every=PROFILE_EVERY)
     a, b = _events(torch)
     a.record()
     lb.rk_step(plan, Q, dt, args.steps, phys, work=work)
@@ -912,7 +913,10 @@ def run_ours(args, world, rank, local):
         work = lb.workspace(plan)
         lb.rk_step(plan, Q, dt, warmup, phys, work=work)
         torch.cuda.synchronize()
-        plan.set_profiling(True)
+        # CUDA events around the four stage launches and the filter launch of every
+        # PROFILE_EVERY-th timed step: the per-launch durations of the roofline, with
+        # less perturbation of the timed steps than events on every step
+        plan.set_profiling(True, every=PROFILE_EVERY)
         a, b = ev(), ev()
         barrier(world)
         torch.cuda.synchronize()

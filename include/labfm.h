@@ -767,7 +767,11 @@ typedef struct labfm_profile {
     int64_t adj_filter_launches;
 } labfm_profile;
 
-/* Enable (1) or disable (0) launch timing on this plan; enabling clears the record. */
+/* Enable (enable >= 1) or disable (0) launch timing on this plan; enabling clears
+ * the record.  With enable = k the stage and filter launches of labfm_rk_step are
+ * timed on every k-th step only (k = 1: every step), so that the events perturb
+ * a long timed run less; the adjoint calls' launches are timed on every call.
+ * Errors: EINVAL (enable < 0). */
 int labfm_plan_set_profiling(labfm_plan* plan, int enable);
 
 /* Read and clear the launch timings (synchronises on the last recorded event). */

@@ -537,8 +537,10 @@ class Plan:
                                        ctypes.byref(g), ctypes.byref(b), _stream(stream)))
         return g.value, b.value
 
-    def set_profiling(self, enable: bool = True) -> None:
-        _check(lib.labfm_plan_set_profiling(self._h, 1 if enable else 0))
+    def set_profiling(self, enable: bool = True, every: int = 1) -> None:
+        """labfm_plan_set_profiling: launch timing on (every `every`-th step of
+        rk_step timed) or off."""
+        _check(lib.labfm_plan_set_profiling(self._h, int(every) if enable else 0))
 
     def read_profile(self) -> dict:
         pr = _Profile()

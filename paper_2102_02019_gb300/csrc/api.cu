@@ -160,6 +160,11 @@ int prof_begin(labfm_plan* p, int kind, cudaStream_t st) {
     return idx;
 }
 
+bool prof_step_sampled(labfm_plan* p) {
+    if (!p->profiling) return false;
+    return p->prof_step++ % p->prof_period == 0;
+}
+
 void prof_end(labfm_plan* p, int idx, cudaStream_t st) {
     if (idx >= 0) cudaEventRecord(p->prof_ev[2 * idx + 1], st);
 }
@@ -510,6 +515,7 @@ extern "C" int labfm_rk_step_host(const labfm_plan* p, void* Q_host, void* Q_dev
 
 extern "C" int labfm_plan_set_profiling(labfm_plan* p, int enable) {
     if (int rc = check_plan(p)) return rc;
+    if (enable < 0) return set_error(LABFM_EINVAL, "enable must be >= 0");
     if (enable && !p->prof_ev) {
         const int cap = 8192;
         p->prof_ev = new (std::nothrow) cudaEvent_t[2 * cap];
@@ -535,6 +541,8 @@ extern "C" int labfm_plan_set_profiling(labfm_plan* p, int enable) {
         p->prof_cap = cap;
     }
     p->profiling = enable != 0;
+    p->prof_period = enable > 0 ? enable : 1;
+    p->prof_step = 0;
     p->prof_used = 0;
     p->prof_dropped = 0;
     return LABFM_OK;

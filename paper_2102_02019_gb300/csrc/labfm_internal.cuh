@@ -135,6 +135,8 @@ struct labfm_plan {
     labfm_nscbc nscbc = {0.278, 1.0, 0.0, 1.0};
     // launch timing (labfm_plan_set_profiling): event pairs around launches
     bool profiling = false;
+    int prof_period = 1;       // time the step launches of every prof_period-th step
+    int64_t prof_step = 0;     // steps seen since profiling was enabled
     cudaEvent_t* prof_ev = nullptr;  // 2 * prof_cap events
     char* prof_kind = nullptr;       // labfm::ProfKind of each pair
     int prof_cap = 0;
@@ -172,6 +174,9 @@ bool launch_shape_supported(int group, int block);
 enum ProfKind { kProfStage = 0, kProfFilter = 1, kProfStages4 = 2, kProfRecStages4 = 3,
                 kProfAdjA = 4, kProfAdjB = 5, kProfAdjFilter = 6 };
 int prof_begin(labfm_plan* p, int kind, cudaStream_t st);
+// Whether the launches of the step about to be enqueued are timed (every
+// prof_period-th step while profiling); counts the step.
+bool prof_step_sampled(labfm_plan* p);
 void prof_end(labfm_plan* p, int idx, cudaStream_t st);
 
 // Boundaries of a plan (walls.cu): slots, normals, and (kind and target null:

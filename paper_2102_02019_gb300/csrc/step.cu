@@ -778,7 +778,8 @@ int rk_one_step_t(const labfm_plan* p, void* work, double dt, const labfm_phys* 
     const Packed<T>* xin[4] = {X, Y, X, Y};
     const Packed<T>* qin[4] = {X, P, P, P};
     Packed<T>* xout[4] = {Y, X, Y, nullptr};
-    const int evs = profile ? prof_begin(pm, kProfStages4, st) : -1;  // the four stages as one block
+    const bool timed = profile && prof_step_sampled(pm);
+    const int evs = timed ? prof_begin(pm, kProfStages4, st) : -1;  // the four stages as one block
     for (int k = 0; k < 4; ++k) {
         const double bk = kRkB[k];
         const double ck = k < 3 ? kRkA[k] - kRkB[k] : 0.0;
@@ -787,7 +788,7 @@ int rk_one_step_t(const labfm_plan* p, void* work, double dt, const labfm_phys* 
         if (rc) return rc;
     }
     prof_end(pm, evs, st);
-    const int ev = profile ? prof_begin(pm, kProfFilter, st) : -1;
+    const int ev = timed ? prof_begin(pm, kProfFilter, st) : -1;
     if ((rc = p->n_ranges ? filter_ranges<T>(p, P, X, st) : filter_aos<T>(p, P, X, st))) return rc;
     prof_end(pm, ev, st);
     return LABFM_OK;

@@ -102,6 +102,14 @@ def test_profiling_and_host_buffer_step(lb, setup):
     plan.set_profiling(False)
     assert prof["stage_launches"] == 12 and prof["filter_launches"] == 3 and prof["dropped"] == 0
     assert prof["stage_ms"] > 0 and prof["filter_ms"] > 0
+    # sampled: every 3rd of 7 steps (steps 0, 3, 6) carries the events
+    plan.set_profiling(True, every=3)
+    lb.rk_step(plan, Qref.clone(), 1e-4, 7, lb.Phys(100.0, 0.005), work=work)
+    prof = plan.read_profile()
+    plan.set_profiling(False)
+    assert prof["stage_launches"] == 12 and prof["filter_launches"] == 3 and prof["dropped"] == 0
+    with pytest.raises(lb.LabfmError):
+        plan.set_profiling(True, every=-1)
     # pinned host memory (stepped in place over the host link) and pageable host
     # memory (staged through the device scratch) give the device result
     scratch = torch.empty_like(Qd)
