@@ -66,7 +66,7 @@ def test_noalloc_step_matches_rk_step_twice(lb, dtype, tol, persistent):
         lb.rk_step(plan, Qa, dt, nsteps, phys)
         torch.cuda.synchronize()
         # through the C ABI directly: no work buffer, and nothing allocated by the
-        # call (device memory as the driver and torch's allocator see it is unchanged)
+        # call (device memory as the CUDA driver and torch's allocator see it is unchanged)
         free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
         rc = _noalloc_call(lb, plan, Qb, dt, nsteps, phys)
         assert rc == 0, lb.lib.labfm_last_error()
