@@ -59,7 +59,8 @@ def parse():
                     help="lattice side (512 = the benchmark workload; smaller sizes for profiling)")
     ap.add_argument("--ref-cores", type=int, default=0,
                     help="host cores for --impl reference (0 = all, 1 = one, in this process)")
-    ap.add_argument("--only", choices=["stencil_opt", "adjoint", "channel", "lamb_oseen"], default=None,
+    ap.add_argument("--only", choices=["stencil_opt", "adjoint", "channel", "lamb_oseen", "matrix_free"],
+                    default=None,
                     help="run one extra workload alone on --nx and print its JSON (for profiling; "
                          "adjoint: --steps steps)")
     return ap.parse_args()
@@ -600,6 +601,61 @@ def run_lamb_oseen(lb, torch):
     return out
 
 
+def run_matrix_free(lb, torch, args, nx=512, reps=10):
+    """The matrix-free FP64 right-hand side (weights recomputed per stencil entry from
+    each node's weight polynomials) against the stored-weight FP64 right-hand side, on
+    the headline workload: evaluations per second, and the FP64 roofline of the
+    recomputation (per entry 5 Horner evaluations of (m+1)(m+2)/2 fused multiply-adds,
+    the psi and offset arithmetic, the 12 accumulations and 3 differences)."""
+    import numpy as np
+    import labfm_inputs as li
+    m = 8
+    ns = li.tgv_lattice(nx, m=m, h_over_s=2.8, jitter=0.3, seed=1)
+    xy, h, s = (torch.tensor(a, device="cuda") for a in (ns.xy, ns.h, ns.s))
+    rp, col = lb.build_stencils(xy, h, ns.Lx, ns.Ly)
+    a, b = _events(torch)
+    a.record()
+    wc = lb.weight_coefficients(xy, h, s, ns.Lx, ns.Ly, rp, col, m, weights=True)
+    b.record()
+    torch.cuda.synchronize()
+    build_ms = a.elapsed_time(b)
+    q = torch.tensor(li.tgv_fields(ns.xy, C), device="cuda")
+    phys = lb.Phys(C * C, MU)
+    plan = lb.Plan(rp, col, wc["w"], wc["kappa"], s, dtype=torch.float64)
+    out = torch.empty_like(q)
+    times = {}
+    for name, fn in (("matrix_free", lambda: lb.rhs_matrix_free(xy, h, ns.Lx, ns.Ly, rp, col, m, wc["coef"], q,
+                                                                  phys, out=out)),
+                     ("stored", lambda: lb.rhs(plan, q, phys, out=out))):
+        for _ in range(3):
+            fn()
+        a, b = _events(torch)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        times[name] = a.elapsed_time(b) / reps
+    plan.close()
+    nnz = int(col.numel())
+    nc = (m + 1) * (m + 2) // 2
+    flops_entry = 2 * (5 * nc + 12) + 3 + 24  # Horner FMAs, accumulations, differences, offsets and psi
+    fp64_peak = lb.probe_fma_rate(torch.float64)
+    achieved = flops_entry * nnz / (times["matrix_free"] * 1e-3) / 1e9
+    return {"workload": f"{ns.N:,}-node lattice (+-0.3 s), m = {m}, FP64, one right-hand-side evaluation",
+            "nodes": ns.N, "nnz": nnz, "coefficients_per_node": 6 * nc,
+            "coefficient_build_ms": build_ms,
+            "matrix_free_ms": times["matrix_free"], "stored_weights_ms": times["stored"],
+            "matrix_free_node_evals_per_s": ns.N / (times["matrix_free"] * 1e-3),
+            "stored_node_evals_per_s": ns.N / (times["stored"] * 1e-3),
+            "matrix_free_over_stored_time": times["matrix_free"] / times["stored"],
+            "roofline": {"bound": "alu", "kernel": "k_rhs_matrix_free<8>", "flops_per_entry": flops_entry,
+                         "achieved": achieved, "peak": fp64_peak, "unit": "GFLOP/s", "frac": achieved / fp64_peak,
+                         "peak_source": "measured FP64 FMA probe (labfm_probe_fma_rate)"},
+            "bytes_per_entry_saved": 40}
+
+
 def run_channel(lb, torch, args, nx=512):
     """The boundary row (Section 7.1): a channel periodic in x between no-slip walls,
     nx x nx nodes (five uniform rows along each wall, +-0.05 s jitter inside), LABFM
@@ -1048,6 +1104,7 @@ def run_ours(args, world, rank, local):
             "ms_per_step": ctl["ms_per_step"]["fp32"], "nnz": ctl["nnz"], "finite": ctl["finite"]}
         result["stencil_opt"] = run_stencil_opt(lb, torch, args)
         result["channel"] = run_channel(lb, torch, args)
+        result["matrix_free"] = run_matrix_free(lb, torch, args)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t0 = time.perf_counter()
@@ -1096,6 +1153,8 @@ def main():
             out = run_channel(lb, torch, args, nx=args.nx)
         elif args.only == "lamb_oseen":
             out = run_lamb_oseen(lb, torch)
+        elif args.only == "matrix_free":
+            out = run_matrix_free(lb, torch, args, nx=args.nx)
         else:
             out = run_adjoint(lb, torch, args, nsteps=args.steps, every=max(1, min(50, args.steps // 2)),
                               nx=args.nx)

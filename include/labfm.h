@@ -182,6 +182,48 @@ int labfm_build_weights(const double* xy, const double* h, const double* s, int6
                         int64_t* n_failed_out, void* stream);
 
 /*
+ * labfm_build_weights that also writes, for the matrix-free right-hand side,
+ * every node's weight polynomials: with W = psi He_a(x/h) He_b(y/h),
+ * w^d_ji = psi(|r_ji|/h_i) P^d_i(x_ji/h_i, y_ji/h_i) where
+ * P^d_i = sum_{p+q<=m} c^d_pq x^p y^q has (m+1)(m+2)/2 coefficients per operator.
+ *   coef_out  device, N x labfm_weight_coefficients_per_node(m) doubles (output,
+ *             may be NULL), node-major; within a node monomial major (p ascending,
+ *             then q = 0..m-p), operator minor: c^d_pq of node i at
+ *             coef_out[i * 6 (m+1)(m+2)/2 + 6 idx(p, q) + d], idx(p, q) = p (2m + 3 - p)/2 + q;
+ *             zeros for a node whose system is singular or has too few neighbours
+ *   w         may be NULL when coef_out is given (the weights are not stored)
+ * Other arguments, outputs and errors as labfm_build_weights.
+ */
+int labfm_build_weights_ex(const double* xy, const double* h, const double* s, int64_t N, double Lx,
+                           double Ly, uint32_t periodic_mask, const int32_t* row_ptr, const int32_t* col,
+                           int64_t nnz, int m, double* w, double* kappa, double* residual,
+                           int32_t* node_status, int64_t* n_failed_out, double* coef_out, void* stream);
+
+/* Doubles of weight-polynomial coefficients per node for order m: 6 (m+1)(m+2)/2
+ * (0 for an unsupported m). */
+size_t labfm_weight_coefficients_per_node(int m);
+
+/*
+ * Matrix-free right-hand side of eq. icns, FP64: as labfm_rhs, but each
+ * neighbour's five weights (x, y, xx, xy, yy) are recomputed from the node's
+ * weight polynomials (labfm_build_weights_ex) instead of read from a plan:
+ * w^d_ji = psi(|r_ji|/h_i) P^d_i(x_ji/h_i, y_ji/h_i) by Horner's rule, the same
+ * operations as the weight build.  This trades the 40 bytes of stored FP64
+ * weights per stencil entry for about 5 (m+1)(m+2)/2 fused multiply-adds (the
+ * alternative the paper's conclusions name for Lagrangian node sets).  One warp
+ * per node.
+ *   xy, h     device, N x 2 / N doubles (the node set of the weight build)
+ *   row_ptr, col  device CSR of the stencils; coef: device, from labfm_build_weights_ex
+ *   fields    device, 3 x N doubles (ln rho, u, v); rhs: device, 3 x N doubles
+ *             (output, must not alias fields)
+ * Errors: EINVAL (sizes, m, aliasing, a malformed CSR).
+ */
+int labfm_rhs_matrix_free(const double* xy, const double* h, int64_t N, double Lx, double Ly,
+                          uint32_t periodic_mask, const int32_t* row_ptr, const int32_t* col, int m,
+                          const double* coef, const double* fields, double* rhs, const labfm_phys* phys,
+                          void* stream);
+
+/*
  * Stencil optimisation (Section 4), FP64.  For every node i, starting from
  * h = h0_i and the stencil of labfm_build_stencils at h0_i, repeat:
  *   1. stop if fewer than n = (m^2 + 3m)/2 stencil nodes lie within |r_ji| <= 2h;

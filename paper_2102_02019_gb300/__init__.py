@@ -93,6 +93,11 @@ _SIGS = {
                                          _D, _P, _P, _I64, ctypes.POINTER(_I64), _P, _P, _P,
                                          ctypes.POINTER(_I64), _P]),
     "labfm_plan_set_walls": (_I32, [_P, _I64, _P, _P, _P]),
+    "labfm_build_weights_ex": (_I32, [_P, _P, _P, _I64, _D, _D, ctypes.c_uint32, _P, _P, _I64, _I32,
+                                      _P, _P, _P, _P, ctypes.POINTER(_I64), _P, _P]),
+    "labfm_weight_coefficients_per_node": (ctypes.c_size_t, [_I32]),
+    "labfm_rhs_matrix_free": (_I32, [_P, _P, _I64, _D, _D, ctypes.c_uint32, _P, _P, _I32, _P, _P, _P,
+                                     ctypes.POINTER(_Phys), _P]),
     "labfm_plan_set_boundaries": (_I32, [_P, _I64, _P, _P, _P, _P, ctypes.POINTER(_Nscbc), _P]),
     "labfm_plan_create": (_I32, [ctypes.POINTER(_P), _I64, _I64, _I32, _P, _P, _P, _P, _P, _P]),
     "labfm_plan_destroy": (_I32, [_P]),
@@ -257,6 +262,51 @@ def build_weights(xy, h, s, Lx, Ly, row_ptr, col, m, periodic=(True, True), resi
     _check(rc)
     return {"w": w[:, :nnz] if nnz else w[:, :0], "kappa": kappa, "status": status,
             "residual": res, "n_failed": nf.value if check else None}
+
+
+def weight_coefficients(xy, h, s, Lx, Ly, row_ptr, col, m, periodic=(True, True), weights=False,
+                        check=False, stream=None):
+    """labfm_build_weights_ex: every node's weight polynomials (N, (m+1)(m+2)/2, 6) for the
+    matrix-free right-hand side, with kappa and status; weights=True also returns the
+    stored weights w (6, nnz)."""
+    N = xy.shape[0]
+    nnz = col.numel()
+    dev = xy.device
+    mask = (1 if periodic[0] else 0) | (2 if periodic[1] else 0)
+    nc = int(lib.labfm_weight_coefficients_per_node(int(m)))
+    if nc == 0:
+        raise ValueError("order m must be even and in [2, 10]")
+    coef = torch.empty((N, nc // 6, 6), dtype=torch.float64, device=dev)
+    w = torch.empty((6, max(nnz, 1)), dtype=torch.float64, device=dev) if weights else None
+    kappa = torch.empty(N, dtype=torch.float64, device=dev)
+    status = torch.empty(N, dtype=torch.int32, device=dev)
+    nf = _I64(0)
+    _check(lib.labfm_build_weights_ex(_ptr(xy), _ptr(h), _ptr(s), N, Lx, Ly, mask, _ptr(row_ptr),
+                                      _ptr(col) if nnz else None, nnz, m, _ptr(w), _ptr(kappa), None,
+                                      _ptr(status), ctypes.byref(nf) if check else None, _ptr(coef),
+                                      _stream(stream)))
+    out = {"coef": coef, "kappa": kappa, "status": status, "n_failed": nf.value if check else None}
+    if weights:
+        out["w"] = w[:, :nnz]
+    return out
+
+
+def rhs_matrix_free(xy, h, Lx, Ly, row_ptr, col, m, coef, fields, phys, periodic=(True, True),
+                    out=None, stream=None):
+    """labfm_rhs_matrix_free: the FP64 eq. icns right-hand side with every neighbour's
+    weights recomputed from the weight polynomials (3 x N float64)."""
+    N = xy.shape[0]
+    mask = (1 if periodic[0] else 0) | (2 if periodic[1] else 0)
+    if fields.dtype != torch.float64 or fields.numel() < 3 * N or not fields.is_contiguous():
+        raise ValueError("fields must be a contiguous float64 tensor of 3 x N values")
+    if coef.dtype != torch.float64 or coef.numel() < N * int(lib.labfm_weight_coefficients_per_node(int(m))):
+        raise ValueError("coef must be the float64 weight polynomials of order m")
+    out = torch.empty_like(fields) if out is None else out
+    ph = phys.c()
+    _check(lib.labfm_rhs_matrix_free(_ptr(xy), _ptr(h), N, Lx, Ly, mask, _ptr(row_ptr),
+                                     _ptr(col) if col.numel() else None, int(m), _ptr(coef), _ptr(fields),
+                                     _ptr(out), ctypes.byref(ph), _stream(stream)))
+    return out
 
 
 def stencil_optimise(xy, h0, s, Lx, Ly, row_ptr, col, m, factor=0.99, amp_max=1.01, resid_coef=1e-4,

@@ -381,11 +381,13 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
                    const double* __restrict__ s, int64_t N, double Lx, double Ly, int px_, int py_,
                    const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col, int64_t nnz,
                    double* __restrict__ w, double* __restrict__ kappa, double* __restrict__ residual,
-                   int32_t* __restrict__ node_status, unsigned long long* __restrict__ n_failed) {
+                   int32_t* __restrict__ node_status, unsigned long long* __restrict__ n_failed,
+                   double* __restrict__ coef) {
     using C = WCfg<M>;
     constexpr int n = C::n;
     constexpr int NT = C::NT;
     constexpr int LDA = C::LDA;
+    constexpr int NC = (M + 1) * (M + 2) / 2;
     extern __shared__ double smem[];
     double* A = smem;              // [n][LDA], aliases the moment scratch after assembly
     double* A0 = smem + n * LDA;   // [n][n] copy of M for the residual
@@ -407,8 +409,11 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
     const int r0 = row_ptr[i];
     const int r1 = row_ptr[i + 1];
     if (r1 - r0 < n) {  // M_i singular: fewer stencil nodes than unknowns
-        for (int e = r0 + t; e < r1; e += NT)
-            for (int d = 0; d < 6; ++d) w[int64_t(d) * nnz + e] = 0.0;
+        if (w)
+            for (int e = r0 + t; e < r1; e += NT)
+                for (int d = 0; d < 6; ++d) w[int64_t(d) * nnz + e] = 0.0;
+        if (coef)
+            for (int idx = t; idx < NC * 6; idx += NT) coef[i * (NC * 6) + idx] = 0.0;
         if (t == 0) {
             kappa[i] = 0.0;
             if (RESID) residual[i] = INFINITY;
@@ -462,7 +467,6 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
     // P^d = sum_{a,b} Psi^d_ab He_a He_b = sum_{p+q<=M} c^d_pq x^p y^q, whose
     // coefficients follow from the Hermite expansions once per node; each
     // neighbour then takes P^d by Horner's rule (x outer, y inner).
-    constexpr int NC = (M + 1) * (M + 2) / 2;
     __shared__ double s_cf[NC * 6];
     if (!singular) {
         for (int idx = t; idx < NC * 6; idx += NT) {
@@ -484,6 +488,8 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
         }
     }
     __syncthreads();
+    if (coef)  // the polynomial coefficients, for the matrix-free right-hand side
+        for (int idx = t; idx < NC * 6; idx += NT) coef[i * (NC * 6) + idx] = singular ? 0.0 : s_cf[idx];
     const double kx = 3.0 * 3.141592653589793 / (2.0 * s[i]);
     double f0 = 0.0;
     bool bad = false;
@@ -521,7 +527,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
         }
 #pragma unroll
         for (int d = 0; d < 6; ++d) {
-            w[int64_t(d) * nnz + e] = wd[d];
+            if (w) w[int64_t(d) * nnz + e] = wd[d];
             bad |= !isfinite(wd[d]);
         }
         const double phi = 1.0 - cos(kx * dx) * cos(kx * dy);
@@ -546,7 +552,7 @@ __global__ void __launch_bounds__(WCfg<M>::NT)
                 acc = fma(acc, xh, in);
             }
             const double wv = acc * psi;
-            w[int64_t(d) * nnz + e] = wv;
+            if (w) w[int64_t(d) * nnz + e] = wv;
             bad |= !isfinite(wv);
             if (d == 5) f0 = fma(1.0 - cos(kx * dx) * cos(kx * dy), wv, f0);
         }
@@ -913,7 +919,7 @@ template <int M>
 int launch_weights(const double* xy, const double* h, const double* s, int64_t N, double Lx,
                    double Ly, uint32_t pm, const int32_t* row_ptr, const int32_t* col, int64_t nnz,
                    double* w, double* kappa, double* residual, int32_t* status,
-                   unsigned long long* n_failed, cudaStream_t st) {
+                   unsigned long long* n_failed, double* coef, cudaStream_t st) {
     using C = WCfg<M>;
     const bool resid = residual != nullptr;
     const size_t sm = C::smem(resid);
@@ -921,12 +927,12 @@ int launch_weights(const double* xy, const double* h, const double* s, int64_t N
         auto kern = k_weight_build<M, true>;
         LABFM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
         kern<<<unsigned(N), C::NT, sm, st>>>(xy, h, s, N, Lx, Ly, pm & 1u, (pm >> 1) & 1u, row_ptr,
-                                             col, nnz, w, kappa, residual, status, n_failed);
+                                             col, nnz, w, kappa, residual, status, n_failed, coef);
     } else {
         auto kern = k_weight_build<M, false>;
         LABFM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
         kern<<<unsigned(N), C::NT, sm, st>>>(xy, h, s, N, Lx, Ly, pm & 1u, (pm >> 1) & 1u, row_ptr,
-                                             col, nnz, w, kappa, residual, status, n_failed);
+                                             col, nnz, w, kappa, residual, status, n_failed, coef);
     }
     LABFM_LAUNCH_CHECK("weight build kernel");
     return LABFM_OK;
@@ -937,13 +943,13 @@ int launch_weights(const double* xy, const double* h, const double* s, int64_t N
 
 using namespace labfm;
 
-extern "C" int labfm_build_weights(const double* xy, const double* h, const double* s, int64_t N,
-                                   double Lx, double Ly, uint32_t periodic_mask,
-                                   const int32_t* row_ptr, const int32_t* col, int64_t nnz, int m,
-                                   double* w, double* kappa, double* residual,
-                                   int32_t* node_status, int64_t* n_failed_out, void* stream) {
+extern "C" int labfm_build_weights_ex(const double* xy, const double* h, const double* s, int64_t N,
+                                      double Lx, double Ly, uint32_t periodic_mask,
+                                      const int32_t* row_ptr, const int32_t* col, int64_t nnz, int m,
+                                      double* w, double* kappa, double* residual, int32_t* node_status,
+                                      int64_t* n_failed_out, double* coef_out, void* stream) {
     LABFM_NVTX("labfm_build_weights");
-    if (!xy || !h || !s || !row_ptr || !kappa || !node_status || (nnz > 0 && !w))
+    if (!xy || !h || !s || !row_ptr || !kappa || !node_status || (nnz > 0 && !w && !coef_out))
         return set_error(LABFM_EINVAL, "null pointer argument");
     if (nnz > 0 && !col) return set_error(LABFM_EINVAL, "null col with nnz > 0");
     if (N <= 0 || N >= (int64_t(1) << 31) - 1) return set_error(LABFM_EINVAL, "N out of range");
@@ -961,11 +967,11 @@ extern "C" int labfm_build_weights(const double* xy, const double* h, const doub
     }
     int rc = LABFM_OK;
     switch (m) {
-        case 2: rc = launch_weights<2>(xy, h, s, N, Lx, Ly, periodic_mask, row_ptr, col, nnz, w, kappa, residual, node_status, nf, st); break;
-        case 4: rc = launch_weights<4>(xy, h, s, N, Lx, Ly, periodic_mask, row_ptr, col, nnz, w, kappa, residual, node_status, nf, st); break;
-        case 6: rc = launch_weights<6>(xy, h, s, N, Lx, Ly, periodic_mask, row_ptr, col, nnz, w, kappa, residual, node_status, nf, st); break;
-        case 8: rc = launch_weights<8>(xy, h, s, N, Lx, Ly, periodic_mask, row_ptr, col, nnz, w, kappa, residual, node_status, nf, st); break;
-        case 10: rc = launch_weights<10>(xy, h, s, N, Lx, Ly, periodic_mask, row_ptr, col, nnz, w, kappa, residual, node_status, nf, st); break;
+        case 2: rc = launch_weights<2>(xy, h, s, N, Lx, Ly, periodic_mask, row_ptr, col, nnz, w, kappa, residual, node_status, nf, coef_out, st); break;
+        case 4: rc = launch_weights<4>(xy, h, s, N, Lx, Ly, periodic_mask, row_ptr, col, nnz, w, kappa, residual, node_status, nf, coef_out, st); break;
+        case 6: rc = launch_weights<6>(xy, h, s, N, Lx, Ly, periodic_mask, row_ptr, col, nnz, w, kappa, residual, node_status, nf, coef_out, st); break;
+        case 8: rc = launch_weights<8>(xy, h, s, N, Lx, Ly, periodic_mask, row_ptr, col, nnz, w, kappa, residual, node_status, nf, coef_out, st); break;
+        case 10: rc = launch_weights<10>(xy, h, s, N, Lx, Ly, periodic_mask, row_ptr, col, nnz, w, kappa, residual, node_status, nf, coef_out, st); break;
     }
     const int64_t fnode = fault_singular_node();
     if (rc == LABFM_OK && fnode >= 0 && fnode < N) {
@@ -987,6 +993,16 @@ extern "C" int labfm_build_weights(const double* xy, const double* h, const doub
             return set_error(LABFM_ESINGULAR, std::to_string(hf) + " node(s) failed; see node_status");
     }
     return rc;
+}
+
+extern "C" int labfm_build_weights(const double* xy, const double* h, const double* s, int64_t N,
+                                   double Lx, double Ly, uint32_t periodic_mask,
+                                   const int32_t* row_ptr, const int32_t* col, int64_t nnz, int m,
+                                   double* w, double* kappa, double* residual,
+                                   int32_t* node_status, int64_t* n_failed_out, void* stream) {
+    if (nnz > 0 && !w) return set_error(LABFM_EINVAL, "null pointer argument");
+    return labfm_build_weights_ex(xy, h, s, N, Lx, Ly, periodic_mask, row_ptr, col, nnz, m, w, kappa, residual,
+                                  node_status, n_failed_out, nullptr, stream);
 }
 
 extern "C" int labfm_stencil_optimise(const double* xy, const double* h0, const double* s, int64_t N,
