@@ -1088,23 +1088,32 @@ def run_ours(args, world, rank, local):
     }
 
     if not args.no_extras:
-        result["batch256"] = run_batch(lb, torch, args)
-        result["varres_m10"] = run_varres(lb, torch, args)
-        result["adjoint"] = run_adjoint(lb, torch, args)
-        result["fp32_error"] = run_fp32_error(lb, torch, args, shape=tuned_shape[torch.float32])
+        def extra(key, fn):
+            # an extra workload that fails is reported in its own object; the headline
+            # line is printed all the same
+            try:
+                result[key] = fn()
+            except Exception as e:  # noqa: BLE001
+                result[key] = {"error": f"{type(e).__name__}: {e}"}
+
+        extra("batch256", lambda: run_batch(lb, torch, args))
+        extra("varres_m10", lambda: run_varres(lb, torch, args))
+        extra("adjoint", lambda: run_adjoint(lb, torch, args))
+        extra("fp32_error", lambda: run_fp32_error(lb, torch, args, shape=tuned_shape[torch.float32]))
         # the +-0.3 s lattice without node shifting goes non-finite within tens of steps
         # (the filter amplifies modes of a few badly shaped stencils); the same step on
         # the +-0.05 s lattice, which stays finite, shows that the values do not change
         # the throughput
-        ctl = result["fp32_error"]["m8_512x512"]
-        result["finite_state_control"] = {
-            "workload": "512x512 lattice at +-0.05 s jitter (262,144 nodes), m=8, h/s=2.8, "
-                        "1000 FP32 steps in the headline launch shape",
-            "value": ctl["fp32_node_evals_per_s"], "unit": UNIT,
-            "ms_per_step": ctl["ms_per_step"]["fp32"], "nnz": ctl["nnz"], "finite": ctl["finite"]}
-        result["stencil_opt"] = run_stencil_opt(lb, torch, args)
-        result["channel"] = run_channel(lb, torch, args)
-        result["matrix_free"] = run_matrix_free(lb, torch, args)
+        ctl = result["fp32_error"].get("m8_512x512")
+        if ctl:
+            result["finite_state_control"] = {
+                "workload": "512x512 lattice at +-0.05 s jitter (262,144 nodes), m=8, h/s=2.8, "
+                            "1000 FP32 steps in the headline launch shape",
+                "value": ctl["fp32_node_evals_per_s"], "unit": UNIT,
+                "ms_per_step": ctl["ms_per_step"]["fp32"], "nnz": ctl["nnz"], "finite": ctl["finite"]}
+        extra("stencil_opt", lambda: run_stencil_opt(lb, torch, args))
+        extra("channel", lambda: run_channel(lb, torch, args))
+        extra("matrix_free", lambda: run_matrix_free(lb, torch, args))
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t0 = time.perf_counter()
