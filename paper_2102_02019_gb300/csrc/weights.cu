@@ -109,21 +109,12 @@ __device__ __forceinline__ void neighbour_factors(const double* __restrict__ xy,
     }
 }
 
-// 1/k! and 1/sqrt(2^k) tables in constant memory (indexed at run time).
+// 1/k! in constant memory (indexed at run time).
 __constant__ double c_inv_fact[11] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0,
                                       1.0 / 720.0, 1.0 / 5040.0, 1.0 / 40320.0, 1.0 / 362880.0,
                                       1.0 / 3628800.0};
-__constant__ double c_inv_sqrt2_pow[21] = {
-    1.0, 0.70710678118654752440, 0.5, 0.35355339059327376220, 0.25, 0.17677669529663688110,
-    0.125, 0.088388347648318440550, 0.0625, 0.044194173824159220275, 0.03125,
-    0.022097086912079610138, 0.015625, 0.011048543456039805069, 0.0078125,
-    0.0055242717280199025344, 0.00390625, 0.0027621358640099512672, 0.001953125,
-    0.0013810679320049756336, 0.0009765625};
 
 __device__ __forceinline__ double inv_factorial(int k) { return c_inv_fact[k]; }
-
-// 1 / sqrt(2^k)
-__device__ __forceinline__ double inv_sqrt2_pow(int k) { return c_inv_sqrt2_pow[k]; }
 
 // Selector entry C~^d_q / h^-deg for op d at monomial (a, b) (Section 2 and,
 // for d = 5, the expansion of (d_xx + d_yy)^{M/2} from Section 6).
