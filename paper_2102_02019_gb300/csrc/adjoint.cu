@@ -80,10 +80,17 @@ __device__ __forceinline__ void g8_load(const G8<double>* p, int i, double (&g)[
 // Slots of G8.
 constexpr int kGax = 0, kGay = 1, kGux = 2, kGuy = 3, kGvx = 4, kGvy = 5, kGA = 6, kGB = 7;
 
+// LABFM_ADJ_PREFETCH: pass B takes the forward plan's L2 prefetch of the record
+// stream (two iterations ahead, rows of kPrefetchMinRow entries or more).
+#ifndef LABFM_ADJ_PREFETCH
+#define LABFM_ADJ_PREFETCH 1
+#endif
+
 template <typename T>
 PlanView<T> tview(const labfm_plan* p) {
     return PlanView<T>{p->N, p->tnnz_pad, p->trow_ptr, nullptr, static_cast<const T*>(p->tw),
-                       static_cast<const T*>(p->twf), static_cast<const T*>(p->inv_s), p->dt_node, 0,
+                       static_cast<const T*>(p->twf), static_cast<const T*>(p->inv_s), p->dt_node,
+                       LABFM_ADJ_PREFETCH ? p->prefetch : 0,
                        nullptr, nullptr, 0, p->N, nullptr, nullptr, T(0), T(0), T(0), T(0)};
 }
 
@@ -196,6 +203,19 @@ __global__ void k_adj_transpose(PlanView<T> PT, const G8<T>* gin, const Packed<T
         const int e0 = PT.row_ptr[k];
         const int e1 = PT.row_ptr[k + 1];
         for (int e = e0 + 4 * gl; e < e1; e += 4 * G) {
+#if LABFM_CHUNK_AOS == 3
+            if constexpr (std::is_same<T, float>::value) {
+                // lanes 0-2 of the group fetch into L2 one 128-byte segment each of the
+                // record block they will read two iterations later (within the row)
+                if (PT.pf > 0 && gl < 3 && e1 - e0 >= kPrefetchMinRow) {
+                    const int ep = e + 4 * G * PT.pf;
+                    if (ep < e1) {
+                        const char* a = reinterpret_cast<const char*>(PT.w) + Rec<float>::col(ep >> 2) + gl * 128;
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+                    }
+                }
+            }
+#endif
             int ci[4];
             T c0[4], c1[4], c2[4], c3[4], c4[4];
             load_rhs_chunk(PT, e, ci, c0, c1, c2, c3, c4, 0);
