@@ -419,6 +419,26 @@ def test_filter_response_is_one_third_at_two_thirds_nyquist():
     assert np.all(out["kappa"] > 0)
 
 
+@pytest.mark.parametrize("m, hs", [(4, 1.7), (6, 2.2), (8, 2.8)])
+def test_filter_is_a_contraction_on_a_uniform_lattice(m, hs):
+    # Section 6: on a uniform lattice the filter 1 + kappa nabla^m is a symmetric
+    # convolution that keeps constants (eigenvalue 1) and damps every other mode:
+    # all eigenvalues of the filter matrix are real and in (-1, 1]; a wrong sign of
+    # kappa or of the hyperviscous selector would push some above 1
+    ns = li.tgv_lattice(16, m=m, h_over_s=hs, jitter=0.0, seed=0)
+    rp, col = o.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly)
+    out = o.build_weights(ns.xy, ns.h, ns.s, rp, col, m, ns.Lx, ns.Ly)
+    ri = o.row_index(rp)
+    F = np.eye(ns.N)
+    wf = out["w"][5] * out["kappa"][ri]
+    np.add.at(F, (ri, col), wf)
+    np.add.at(F, (ri, ri), -wf)
+    ev = np.linalg.eigvals(F)
+    assert np.abs(ev.imag).max() < 1e-10
+    assert ev.real.max() <= 1.0 + 1e-12 and ev.real.min() > -1.0, (ev.real.min(), ev.real.max())
+    assert np.sum(np.abs(ev.real - 1.0) < 1e-9) == 1  # only the constant mode is kept
+
+
 def test_stable_dt_for_taylor_green():
     ns = li.tgv_lattice(64, m=4, jitter=0.0)
     q = li.tgv_fields(ns.xy, 10.0)
