@@ -350,3 +350,22 @@ def test_open_box_fp32_rhs_within_derived_budget(lb, box):
     nb = box.bnd["nodes"]
     print("FP32 open box: max error / budget, all nodes", ratio.max(), "boundary nodes", ratio[:, nb].max())
     assert ratio.max() <= 1.0, ratio.max()
+
+
+def test_open_box_fp32_step_within_derived_budget(lb, box):
+    # one FP32 time step (oracle operator) against the FP64 oracle step, elementwise
+    # within the step budget derived from the right-hand-side budget
+    from tests.fp32_budget import boundary_step_bound
+    ns = box.ns
+    q0 = _state(ns, seed=13)
+    dt = 0.5 * oracle.stable_dt(q0, ns.s, C, MU)
+    q1 = bo.boundary_time_step(q0, dt, box.op, box.bnd, C, MU)
+    plan = box.plan(lb, torch.float32)
+    Q = _dev(q0, torch.float32)
+    lb.rk_step(plan, Q, dt, 1, lb.Phys(C * C, MU))
+    plan.close()
+    rp, col, w, kappa = box.op
+    B = boundary_step_bound(q0, q1, dt, w, kappa, rp, col, box.bnd, C, MU)
+    ratio = np.abs(Q.double().cpu().numpy() - q1) / B
+    print("FP32 open-box step: max error / budget", ratio.max())
+    assert ratio.max() <= 1.0, ratio.max()

@@ -396,3 +396,30 @@ def test_channel_fp32_rhs_within_derived_budget(lb, ch, g):
     assert np.all(R[1:, ch.wall_nodes] == 0.0)
     print("FP32 channel: max error / budget", ratio.max(), "walls", ratio[0, ch.wall_nodes].max())
     assert ratio.max() <= 1.0, ratio.max()
+
+
+def test_channel_fp32_step_within_derived_budget(lb, ch):
+    # one FP32 time step of the channel (oracle operator, gravity on) against the FP64
+    # oracle step within the derived step budget; the wall velocity stays exactly zero
+    from tests.fp32_budget import boundary_step_bound
+    ns = ch.ns
+    c, mu, g = 10.0, 0.01, (0.5, 0.0)
+    q0 = np.zeros((3, ns.N))
+    q0[0] = 0.02 * li.smooth_perturbation(ns.xy, kmax=3, seed=9, Ly=ns.Ly)
+    q0[1] = 0.1 * li.smooth_perturbation(ns.xy, kmax=3, seed=10, Ly=ns.Ly)
+    q0[1:, ch.wall_nodes] = 0.0
+    dt = 0.5 * oracle.stable_dt(np.stack([q0[0], q0[1] + 1.0, q0[2]]), ns.s, c, mu)
+    q1 = bo.channel_time_step(q0, dt, ch.op, ns, c, mu, g)
+    plan = ch.plan(lb, torch.float32)
+    Q = _dev(q0, torch.float32)
+    lb.rk_step(plan, Q, dt, 1, lb.Phys(c * c, mu, g[0], g[1]))
+    plan.close()
+    rp, col, w, kappa = ch.op
+    bnd = {"nodes": ch.wall_nodes, "normal": ch.normals, "kind": np.zeros(len(ch.wall_nodes), dtype=np.int32),
+           "target": np.zeros((len(ch.wall_nodes), 2)), "L": 1.0, "mach": 0.0, "rho0": 1.0}
+    B = boundary_step_bound(q0, q1, dt, w, kappa, rp, col, bnd, c, mu, g)
+    got = Q.double().cpu().numpy()
+    assert np.all(got[1:, ch.wall_nodes] == 0.0)
+    ratio = np.abs(got - q1) / np.where(B > 0, B, np.inf)
+    print("FP32 channel step: max error / budget", ratio.max())
+    assert ratio.max() <= 1.0, ratio.max()
