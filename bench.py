@@ -583,6 +583,14 @@ def run_lamb_oseen(lb, torch):
     from tests import lamb_oseen as lo
     st = lo.study(lb, torch)
     res, printed_rates = lo.printed()
+    # the FP32 path on the same runs: its disturbance-norm history against FP64's
+    fp32 = {}
+    for r in (8, 16):
+        d32 = lo.run(lb, torch, r, dtype=torch.float32)
+        n64 = st["runs"][r]["norm"]
+        diff = max(abs(a - b) for a, b in zip(d32["norm"], n64))
+        fp32[str(r)] = {"finite": d32["finite"], "max_norm_difference_over_initial": diff / n64[0],
+                        "step_ms": d32["step_ms"], "steps": d32["steps"]}
     runs = {}
     for r, d in st["runs"].items():
         every = 10  # t* = 1 apart
@@ -594,7 +602,7 @@ def run_lamb_oseen(lb, torch):
                        "the boundary rows, FP64, t U0/R_c in [0, 20]",
            "printed_rates": dict(zip([str(r) for r in res[:-1]], printed_rates)),
            "error_vs_16": {str(k): v for k, v in st["error_vs_finest"].items()},
-           "rates_vs_16": st["rates"], "runs": runs}
+           "rates_vs_16": st["rates"], "runs": runs, "fp32_vs_fp64": fp32}
     for k in st:
         if k.startswith("error_vs_2") or k.startswith("rates_vs_2"):
             out[k] = {str(a): b for a, b in st[k].items()}
