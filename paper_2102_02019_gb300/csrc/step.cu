@@ -120,8 +120,14 @@ constexpr int kTileRows = 4;
 
 // WALL (plain grid only): plans with walls, whose wall nodes take the wall's
 // right-hand side.
+#ifndef LABFM_PERSIST_MINB
+#define LABFM_PERSIST_MINB 7
+#endif
+// The work-queue instantiation keeps 7 resident blocks per SM (at most 73 registers;
+// left to itself it takes 78 and fits 6).
 template <typename T, int G, bool KAHAN, bool SCALED, bool PERSIST, bool WALL = false>
-__global__ void LABFM_STAGE_BOUNDS k_stage(PlanView<T> P, const Packed<T>* X_in, const Packed<T>* Q_in,
+__global__ void __launch_bounds__(kGatherBlock, sizeof(T) == 4 ? (PERSIST ? LABFM_PERSIST_MINB : LABFM_STAGE_MINB) : 6)
+    k_stage(PlanView<T> P, const Packed<T>* X_in, const Packed<T>* Q_in,
                         Packed<T>* Q_out, Packed<T>* X_out, double dt, double bk, double ck,
                         Phys<T> ph, int* counter) {
     static_assert(!(PERSIST && WALL), "plans with walls run the plain grid");
