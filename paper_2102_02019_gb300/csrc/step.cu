@@ -111,6 +111,9 @@ __device__ __forceinline__ void stage_node(const PlanView<T>& P, int i, int gl,
 
 // Nodes per work-queue tile of the persistent stage kernel, per warp.
 constexpr int kTileRows = 4;
+#ifndef LABFM_PERSIST_BLOCK_TILES
+#define LABFM_PERSIST_BLOCK_TILES 1
+#endif
 
 // PERSIST = false: one group of G lanes per node over a full grid.
 // PERSIST = true: a grid of (SMs x resident blocks); every warp repeatedly takes
@@ -139,8 +142,32 @@ __global__ void __launch_bounds__(kGatherBlock, sizeof(T) == 4 ? (PERSIST ? LABF
         return;
     }
     constexpr int per_warp = 32 / G;
-    constexpr int tile = kTileRows * per_warp;
     const int lane = threadIdx.x & 31;
+#if LABFM_PERSIST_BLOCK_TILES
+    // the block claims kGatherBlock / G consecutive nodes at a time and its warps
+    // take them together, as a block of the plain grid would (neighbouring nodes'
+    // gathers share the SM's L1); the counter balances the blocks
+    // The next tile is claimed when the current one starts, so the counter's round
+    // trip overlaps the work; s_tile[b] holds the tile of the current pass.
+    __shared__ int s_tile[2];
+    constexpr int tile = kGatherBlock / G;
+    const int64_t ntiles = (P.N + tile - 1) / tile;
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_tile[0] = atomicAdd(counter, 1);
+    __syncthreads();
+    for (int b = 0;; b ^= 1) {
+        const int t = s_tile[b];
+        if (t >= ntiles) break;
+        int next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+        const int64_t node = int64_t(t) * tile + warp * per_warp + lane / G;
+        const int i = node < P.N ? int(node) : -1;
+        stage_node<T, G, KAHAN, SCALED>(P, i, lane % G, X_in, Q_in, Q_out, X_out, dt, bk, ck, ph);
+        if (threadIdx.x == 0) s_tile[b ^ 1] = next;
+        __syncthreads();  // the next tile is published; every warp has read s_tile[b]
+    }
+#else
+    constexpr int tile = kTileRows * per_warp;
     const int64_t ntiles = (P.N + tile - 1) / tile;
     while (true) {
         int t = 0;
@@ -154,6 +181,7 @@ __global__ void __launch_bounds__(kGatherBlock, sizeof(T) == 4 ? (PERSIST ? LABF
             stage_node<T, G, KAHAN, SCALED>(P, i, lane % G, X_in, Q_in, Q_out, X_out, dt, bk, ck, ph);
         }
     }
+#endif
 }
 
 // The stage kernel of the recording time step: k_stage (plain grid) that also
