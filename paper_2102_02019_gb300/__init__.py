@@ -209,6 +209,46 @@ def _nodes(plan, t: torch.Tensor, name: str) -> torch.Tensor:
     return t
 
 
+# Argument checks of the calls that take node sets, operators and states outside a
+# plan.  The C side sees only pointers and counts derived from the shapes, so a
+# tensor of another element type or of fewer elements would be read (or written)
+# past its end; each check runs before the tensor's pointer is taken.
+
+def _check_tensor(t: torch.Tensor, dtype: torch.dtype, shape: tuple, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a tensor")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must be {dtype} of shape {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+    return t
+
+
+def _node_set(xy: torch.Tensor, **per_node) -> int:
+    """N of an (N, 2) float64 position tensor; every keyword tensor must hold N float64
+    values (None is skipped)."""
+    if not isinstance(xy, torch.Tensor) or xy.dim() != 2 or xy.shape[1] != 2 or xy.dtype != torch.float64:
+        raise ValueError("xy must be float64 of shape (N, 2)")
+    N = int(xy.shape[0])
+    for name, t in per_node.items():
+        if t is not None:
+            _check_tensor(t, torch.float64, (N,), name)
+    return N
+
+
+def _csr(row_ptr: torch.Tensor, col: torch.Tensor, N: int) -> None:
+    """int32 row pointers (N + 1) and columns (one dimension)."""
+    _check_tensor(row_ptr, torch.int32, (N + 1,), "row_ptr")
+    if not isinstance(col, torch.Tensor) or col.dtype != torch.int32 or col.dim() != 1:
+        raise ValueError("col must be a one-dimensional int32 tensor")
+
+
+def _field_dtype(t: torch.Tensor, name: str, rows: int = 3) -> int:
+    """N of a (rows, N) float32 or float64 tensor."""
+    if not isinstance(t, torch.Tensor) or t.dtype not in (torch.float32, torch.float64) or t.dim() != 2 \
+            or t.shape[0] != rows:
+        raise ValueError(f"{name} must be float32 or float64 of shape ({rows}, N)")
+    return int(t.shape[1])
+
+
 def _stream(stream=None) -> int:
     s = stream if stream is not None else torch.cuda.current_stream()
     return s.cuda_stream
@@ -229,7 +269,7 @@ class Phys:
 def build_stencils(xy: torch.Tensor, h: torch.Tensor, Lx: float, Ly: float,
                    periodic=(True, True), stream=None):
     """CSR (row_ptr int32 [N+1], col int32 [nnz]) of |r_ji| <= 2 h_i (labfm_build_stencils)."""
-    N = xy.shape[0]
+    N = _node_set(xy, h=h)
     mask = (1 if periodic[0] else 0) | (2 if periodic[1] else 0)
     row_ptr = torch.empty(N + 1, dtype=torch.int32, device=xy.device)
     nnz = _I64(0)
@@ -247,7 +287,8 @@ def build_weights(xy, h, s, Lx, Ly, row_ptr, col, m, periodic=(True, True), resi
     """FP64 weights (labfm_build_weights): dict with w (6, nnz), kappa, status, residual, n_failed.
 
     With check=True the call synchronises and raises LabfmError(ESINGULAR) if a node failed."""
-    N = xy.shape[0]
+    N = _node_set(xy, h=h, s=s)
+    _csr(row_ptr, col, N)
     nnz = col.numel()
     dev = xy.device
     mask = (1 if periodic[0] else 0) | (2 if periodic[1] else 0)
@@ -269,7 +310,8 @@ def weight_coefficients(xy, h, s, Lx, Ly, row_ptr, col, m, periodic=(True, True)
     """labfm_build_weights_ex: every node's weight polynomials (N, (m+1)(m+2)/2, 6) for the
     matrix-free right-hand side, with kappa and status; weights=True also returns the
     stored weights w (6, nnz)."""
-    N = xy.shape[0]
+    N = _node_set(xy, h=h, s=s)
+    _csr(row_ptr, col, N)
     nnz = col.numel()
     dev = xy.device
     mask = (1 if periodic[0] else 0) | (2 if periodic[1] else 0)
@@ -295,13 +337,16 @@ def rhs_matrix_free(xy, h, Lx, Ly, row_ptr, col, m, coef, fields, phys, periodic
                     out=None, stream=None):
     """labfm_rhs_matrix_free: the FP64 eq. icns right-hand side with every neighbour's
     weights recomputed from the weight polynomials (3 x N float64)."""
-    N = xy.shape[0]
+    N = _node_set(xy, h=h)
+    _csr(row_ptr, col, N)
     mask = (1 if periodic[0] else 0) | (2 if periodic[1] else 0)
     if fields.dtype != torch.float64 or fields.numel() < 3 * N or not fields.is_contiguous():
         raise ValueError("fields must be a contiguous float64 tensor of 3 x N values")
     if coef.dtype != torch.float64 or coef.numel() < N * int(lib.labfm_weight_coefficients_per_node(int(m))):
         raise ValueError("coef must be the float64 weight polynomials of order m")
     out = torch.empty_like(fields) if out is None else out
+    if out.dtype != torch.float64 or out.numel() < 3 * N:
+        raise ValueError("out must be a float64 tensor of 3 x N values")
     ph = phys.c()
     _check(lib.labfm_rhs_matrix_free(_ptr(xy), _ptr(h), N, Lx, Ly, mask, _ptr(row_ptr),
                                      _ptr(col) if col.numel() else None, int(m), _ptr(coef), _ptr(fields),
@@ -315,7 +360,8 @@ def stencil_optimise(xy, h0, s, Lx, Ly, row_ptr, col, m, factor=0.99, amp_max=1.
     solved per node, as (h, solves) device tensors, and with alpha=True also the
     (N, 2) Laplacian residuals alpha_L at the returned h and where the iteration
     stopped.  resid_coef=math.inf switches the Laplacian-residual test off."""
-    N = xy.shape[0]
+    N = _node_set(xy, h0=h0, s=s)
+    _csr(row_ptr, col, N)
     mask = (1 if periodic[0] else 0) | (2 if periodic[1] else 0)
     h = torch.empty(N, dtype=torch.float64, device=xy.device)
     solves = torch.empty(N, dtype=torch.int32, device=xy.device)
@@ -332,7 +378,7 @@ def build_wall_operator(xy, h, s, Lx, Ly, m, m_wall, wall_column, wall_normal, h
     dict(row_ptr, col, w (6, nnz), kappa, status, n_failed), ready for Plan.
     wall_column: (n_wall, 5) int32 nodes q = 0..4 of each wall column; wall_normal:
     (n_wall, 2) float64 inward unit normals."""
-    N = xy.shape[0]
+    N = _node_set(xy, h=h, s=s)
     n_wall = wall_column.shape[0]
     if wall_column.dtype != torch.int32 or tuple(wall_column.shape) != (n_wall, 5):
         raise ValueError("wall_column must be int32 of shape (n_wall, 5)")
@@ -360,8 +406,10 @@ def build_wall_operator(xy, h, s, Lx, Ly, m, m_wall, wall_column, wall_normal, h
 def modal_response(xy, s, Lx, Ly, row_ptr, col, w, nk=16, periodic=(True, True), stream=None):
     """labfm_modal_response: (N, 3, nk) amplitude responses of d/dx, d/dy and the
     Laplacian of FP64 weights w (6, nnz) (Section 3)."""
-    N = xy.shape[0]
+    N = _node_set(xy, s=s)
+    _csr(row_ptr, col, N)
     nnz = col.numel()
+    _check_tensor(w, torch.float64, (6, nnz), "w")
     mask = (1 if periodic[0] else 0) | (2 if periodic[1] else 0)
     w = w.contiguous()
     out = torch.empty((N, 3, nk), dtype=torch.float64, device=xy.device)
@@ -378,6 +426,8 @@ class Plan:
     def batched(cls, instances, dtype=torch.float32, stream=None):
         """labfm_plan_create_batched over a list of dicts with row_ptr, col, w, kappa, s."""
         n = len(instances)
+        for k, d in enumerate(instances):
+            cls._check_operator(d["row_ptr"], d["col"], d["w"], d["kappa"], d["s"], where=f"instance {k}: ")
         arr = lambda vals, ct: (ct * n)(*vals)
         Ns = arr([d["row_ptr"].numel() - 1 for d in instances], _I64)
         nnzs = arr([d["col"].numel() for d in instances], _I64)
@@ -472,6 +522,7 @@ class Plan:
         return st.value
 
     def __init__(self, row_ptr, col, w, kappa, s, dtype=torch.float32, stream=None):
+        self._check_operator(row_ptr, col, w, kappa, s)
         self.N = row_ptr.numel() - 1
         self.nnz = col.numel()
         self.dtype = dtype
@@ -485,6 +536,16 @@ class Plan:
                                      _stream(stream)))
         self._h = handle
         self.device = row_ptr.device
+
+    @staticmethod
+    def _check_operator(row_ptr, col, w, kappa, s, where=""):
+        if not isinstance(row_ptr, torch.Tensor) or row_ptr.dim() != 1 or row_ptr.numel() < 1:
+            raise ValueError(f"{where}row_ptr must be a one-dimensional int32 tensor of N + 1 values")
+        N = row_ptr.numel() - 1
+        _csr(row_ptr, col, N)
+        _check_tensor(w, torch.float64, (6, col.numel()), where + "w")
+        _check_tensor(kappa, torch.float64, (N,), where + "kappa")
+        _check_tensor(s, torch.float64, (N,), where + "s")
 
     @property
     def handle(self):
@@ -895,12 +956,15 @@ def filter_adjoint(plan: Plan, lam, work=None, stream=None):
 
 
 def conserved_to_primitive(c, stream=None):
+    _field_dtype(c, "c")
     q = torch.empty_like(c)
     _check(lib.labfm_conserved_to_primitive(_ptr(c), _ptr(q), c.shape[1], _dcode(c), _stream(stream)))
     return q
 
 
 def conserved_vjp(c, qbar, stream=None):
+    _field_dtype(c, "c")
+    _check_tensor(qbar, c.dtype, tuple(c.shape), "qbar")
     cb = torch.empty_like(c)
     _check(lib.labfm_conserved_vjp(_ptr(c), _ptr(qbar), _ptr(cb), c.shape[1], _dcode(c),
                                    _stream(stream)))
@@ -908,12 +972,14 @@ def conserved_vjp(c, qbar, stream=None):
 
 
 def kinetic_energy(q, s, stream=None) -> torch.Tensor:
+    _check_tensor(s, torch.float64, (_field_dtype(q, "q"),), "s")
     out = torch.empty(1, dtype=torch.float64, device=q.device)
     _check(lib.labfm_kinetic_energy(_ptr(q), _ptr(s), q.shape[1], _dcode(q), _ptr(out), _stream(stream)))
     return out
 
 
 def kinetic_energy_grad(q, s, scale: float = 1.0, stream=None):
+    _check_tensor(s, torch.float64, (_field_dtype(q, "q"),), "s")
     g = torch.empty_like(q)
     _check(lib.labfm_kinetic_energy_grad(_ptr(q), _ptr(s), q.shape[1], _dcode(q), float(scale), _ptr(g),
                                          _stream(stream)))
@@ -922,6 +988,9 @@ def kinetic_energy_grad(q, s, scale: float = 1.0, stream=None):
 
 def probe_momentum(q, px, py, stream=None) -> torch.Tensor:
     """labfm_probe_momentum: sum_i rho_i (px_i u_i + py_i v_i), 1-element float64 tensor."""
+    N = _field_dtype(q, "q")
+    _check_tensor(px, torch.float64, (N,), "px")
+    _check_tensor(py, torch.float64, (N,), "py")
     out = torch.empty(1, dtype=torch.float64, device=q.device)
     _check(lib.labfm_probe_momentum(_ptr(q), _ptr(px), _ptr(py), q.shape[1], _dcode(q), _ptr(out),
                                     _stream(stream)))
@@ -929,6 +998,9 @@ def probe_momentum(q, px, py, stream=None) -> torch.Tensor:
 
 
 def probe_momentum_grad(q, px, py, scale: float = 1.0, stream=None):
+    N = _field_dtype(q, "q")
+    _check_tensor(px, torch.float64, (N,), "px")
+    _check_tensor(py, torch.float64, (N,), "py")
     g = torch.empty_like(q)
     _check(lib.labfm_probe_momentum_grad(_ptr(q), _ptr(px), _ptr(py), q.shape[1], _dcode(q), float(scale),
                                          _ptr(g), _stream(stream)))

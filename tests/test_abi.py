@@ -141,3 +141,53 @@ def test_binding_rejects_states_that_do_not_match_the_plan(built_lib):
         lb.rk_step(plan, torch.zeros(3, 10, dtype=torch.float64), 1e-3, 1, phys)
     with pytest.raises(ValueError, match="float64 values"):
         lb.stable_dt(plan, torch.zeros(3, 10, dtype=torch.float64), s[:5], 10.0, 0.005)
+
+
+def test_binding_rejects_node_sets_and_operators_of_the_wrong_shape(built_lib):
+    # node sets, CSRs, weights and objective inputs outside a plan are checked for
+    # element type and shape before any pointer is taken (CPU tensors: a tensor that
+    # passed the checks would be refused next for living on the host)
+    import torch
+
+    import paper_2102_02019_gb300 as lb
+    N = 8
+    f64 = lambda *s: torch.zeros(*s, dtype=torch.float64)
+    xy, h, s = f64(N, 2), f64(N), f64(N)
+    rp = torch.zeros(N + 1, dtype=torch.int32)
+    col = torch.zeros(16, dtype=torch.int32)
+    w, kap = f64(6, 16), f64(N)
+    calls = [
+        (lambda: lb.build_stencils(xy.float(), h, 1.0, 1.0), "xy"),
+        (lambda: lb.build_stencils(xy, h[:-1], 1.0, 1.0), "h"),
+        (lambda: lb.build_weights(xy, h, s.float(), 1.0, 1.0, rp, col, 4), "s"),
+        (lambda: lb.build_weights(xy, h, s, 1.0, 1.0, rp.long(), col, 4), "row_ptr"),
+        (lambda: lb.build_weights(xy, h, s, 1.0, 1.0, rp[:-1], col, 4), "row_ptr"),
+        (lambda: lb.build_weights(xy, h, s, 1.0, 1.0, rp, col.long(), 4), "col"),
+        (lambda: lb.weight_coefficients(xy.T.contiguous(), h, s, 1.0, 1.0, rp, col, 4), "xy"),
+        (lambda: lb.stencil_optimise(xy, h, s[:3], 1.0, 1.0, rp, col, 4), "s"),
+        (lambda: lb.modal_response(xy, s, 1.0, 1.0, rp, col, w[:5]), "w"),
+        (lambda: lb.modal_response(xy, s, 1.0, 1.0, rp, col, w.float()), "w"),
+        (lambda: lb.build_wall_operator(xy, h, s.float(), 1.0, 1.0, 6, 4, torch.zeros(1, 5, dtype=torch.int32),
+                                        f64(1, 2)), "s"),
+        (lambda: lb.rhs_matrix_free(xy, h, 1.0, 1.0, rp, col, 4, f64(N * 90), f64(3, N), lb.Phys(1.0, 0.0),
+                                    out=torch.zeros(3, N)), "out"),
+        (lambda: lb.Plan(rp, col, w.float(), kap, s), "w"),
+        (lambda: lb.Plan(rp, col, w[:, :8], kap, s), "w"),
+        (lambda: lb.Plan(rp, col, w, kap[:4], s), "kappa"),
+        (lambda: lb.Plan(rp, col.long(), w, kap, s), "col"),
+        (lambda: lb.Plan.batched([dict(row_ptr=rp, col=col, w=w, kappa=kap, s=s.float())]), "instance 0: s"),
+        (lambda: lb.kinetic_energy(f64(3, N), s[:4]), "s"),
+        (lambda: lb.kinetic_energy(f64(2, N), s), "q"),
+        (lambda: lb.probe_momentum(f64(3, N), s.float(), s), "px"),
+        (lambda: lb.probe_momentum_grad(torch.zeros(3, N), s, s[:2]), "py"),
+        (lambda: lb.conserved_vjp(f64(3, N), torch.zeros(3, N)), "qbar"),
+        (lambda: lb.conserved_to_primitive(torch.zeros(3, N, dtype=torch.int32)), "c"),
+    ]
+    for call, name in calls:
+        with pytest.raises(ValueError, match=name):
+            call()
+    # well-formed arguments pass the checks and are refused for living on the host
+    with pytest.raises(ValueError, match="CUDA"):
+        lb.build_weights(xy, h, s, 1.0, 1.0, rp, col, 4)
+    with pytest.raises(ValueError, match="CUDA"):
+        lb.Plan(rp, col, w, kap, s)
