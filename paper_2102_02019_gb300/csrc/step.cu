@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(kGatherBlock, sizeof(T) == 4 ? (PERSIST ? LABF
         const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
         const int64_t node = P.n_lo + gt / G;
         const int i = node < P.n_hi ? int(node) : -1;
+        launch_prologue<T, false, G>(P, i, int(gt % G));
         stage_node<T, G, KAHAN, SCALED, WALL>(P, i, int(gt % G), X_in, Q_in, Q_out, X_out, dt, bk, ck, ph);
         return;
     }
@@ -450,6 +451,10 @@ __global__ void k_filter_aos(PlanView<T> P, const Packed<T>* in, Packed<T>* out)
     // every lane of a warp runs the same iterations (the group sums shuffle
     // across the whole warp); a group past the end runs idle
     const int64_t warp_first = P.n_lo + (gt / 32) * (32 / G);
+    if constexpr (!PERSIST) {
+        const int64_t node = warp_first + (gt % 32) / G;
+        launch_prologue<T, true, G>(P, node < P.n_hi ? int(node) : -1, gl);
+    }
     for (int64_t base = warp_first; base < P.n_hi; base += stride) {
         const int64_t node = base + (gt % 32) / G;
         const int i = node < P.n_hi ? int(node) : -1;
@@ -567,6 +572,25 @@ __global__ void k_pack_rows(int64_t N, int64_t nnz, int64_t nnz_pad, int64_t off
 
 int grid_for(int64_t threads, int block) { return int((threads + block - 1) / block); }
 
+// Launch of a plain-grid stage or filter kernel with programmatic stream
+// serialization (LABFM_PDL; without it a plain launch): the kernel may start while
+// the previous kernel of the stream finishes, and waits for it in launch_prologue
+// before reading anything that kernel writes.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(unsigned(block));
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = LABFM_PDL ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ---------------------------------------------------------------- dispatch
 
 template <typename T, int G>
@@ -607,15 +631,17 @@ int stage_launch_g(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* q
     constexpr bool F = std::is_same<T, float>::value;
     if (p->wall_slot) {
         const int grid = grid_for(p->N * G, block);
-        k_stage<T, G, F, F, false, true><<<grid, block, 0, st>>>(view<T>(p), xin, qin, qout, xout, dt, bk, ck,
-                                                                 ph, counter);
+        cudaError_t e = launch_pdl(k_stage<T, G, F, F, false, true>, grid, block, st, view<T>(p), xin, qin, qout,
+                                   xout, dt, bk, ck, ph, counter);
+        if (e != cudaSuccess) return cuda_error(e, "rk stage kernel");
     } else if (p->persistent) {
         k_stage<T, G, F, F, true><<<p->persist_grid, block, 0, st>>>(view<T>(p), xin, qin, qout, xout,
                                                                       dt, bk, ck, ph, counter);
     } else {
         const int grid = grid_for(p->N * G, block);
-        k_stage<T, G, F, F, false><<<grid, block, 0, st>>>(view<T>(p), xin, qin, qout, xout, dt, bk,
-                                                           ck, ph, counter);
+        cudaError_t e = launch_pdl(k_stage<T, G, F, F, false>, grid, block, st, view<T>(p), xin, qin, qout, xout,
+                                   dt, bk, ck, ph, counter);
+        if (e != cudaSuccess) return cuda_error(e, "rk stage kernel");
     }
     LABFM_LAUNCH_CHECK("rk stage kernel");
     return LABFM_OK;
@@ -634,7 +660,10 @@ int stage_range_launch_g(const labfm_plan* p, int r, const Packed<T>* xin, const
     v.pf = p->range_pf[r];
     if (v.n_hi <= v.n_lo) return LABFM_OK;
     const int grid = grid_for((v.n_hi - v.n_lo) * G, kGatherBlock);
-    k_stage<T, G, F, F, false><<<grid, kGatherBlock, 0, st>>>(v, xin, qin, qout, xout, dt, bk, ck, ph, nullptr);
+    int* no_counter = nullptr;
+    cudaError_t e = launch_pdl(k_stage<T, G, F, F, false>, grid, kGatherBlock, st, v, xin, qin, qout, xout, dt, bk,
+                               ck, ph, no_counter);
+    if (e != cudaSuccess) return cuda_error(e, "rk stage kernel (launch range)");
     LABFM_LAUNCH_CHECK("rk stage kernel (launch range)");
     return LABFM_OK;
 }
@@ -698,7 +727,8 @@ int filter_aos_g(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaS
         k_filter_aos<T, G, F, true><<<p->filter_grid, p->block, 0, st>>>(view<T>(p), in, out);
     } else {
         const int grid = grid_for(p->N * G, p->block);
-        k_filter_aos<T, G, F, false><<<grid, p->block, 0, st>>>(view<T>(p), in, out);
+        cudaError_t e = launch_pdl(k_filter_aos<T, G, F, false>, grid, p->block, st, view<T>(p), in, out);
+        if (e != cudaSuccess) return cuda_error(e, "filter kernel");
     }
     LABFM_LAUNCH_CHECK("filter kernel");
     return LABFM_OK;
@@ -715,7 +745,9 @@ int filter_range_launch_g(const labfm_plan* p, int r, const Packed<T>* in, Packe
     v.pf = p->range_pf[r];
     if (v.n_hi <= v.n_lo) return LABFM_OK;
     const int grid = grid_for((v.n_hi - v.n_lo) * G, p->block);
-    k_filter_aos<T, G, std::is_same<T, float>::value, false><<<grid, p->block, 0, st>>>(v, in, out);
+    cudaError_t e = launch_pdl(k_filter_aos<T, G, std::is_same<T, float>::value, false>, grid, p->block, st, v, in,
+                               out);
+    if (e != cudaSuccess) return cuda_error(e, "filter kernel (launch range)");
     LABFM_LAUNCH_CHECK("filter kernel (launch range)");
     return LABFM_OK;
 }
