@@ -166,6 +166,7 @@ __global__ void k_adj_pointwise(PlanView<T> P, const Packed<T>* X, const Packed<
     const int64_t node = gt / G;
     const int gl = int(gt % G);
     const int i = node < P.N ? int(node) : -1;
+    launch_prologue<T, false, G>(P, i, gl);
     const AoS<T> fld{X};
     T a = 0, u = 0, v = 0;
     if (i >= 0) fld.get(i, a, u, v);
@@ -198,6 +199,7 @@ __global__ void k_adj_transpose(PlanView<T> PT, const G8<T>* gin, const Packed<T
     const int64_t node = gt / G;
     const int gl = int(gt % G);
     const int k = node < PT.N ? int(node) : -1;
+    launch_prologue<T, false, G>(PT, k, gl);
     T sa = 0, su = 0, sv = 0;
     if (k >= 0) {
         const int e0 = PT.row_ptr[k];
@@ -280,6 +282,7 @@ __global__ void k_filter_adjoint(PlanView<T> PT, const Packed<T>* lam, const T* 
     const int64_t node = gt / G;
     const int gl = int(gt % G);
     const int k = node < PT.N ? int(node) : -1;
+    launch_prologue<T, true, G>(PT, k, gl);
     const AoS<T> fld{lam};
     T sa = 0, su = 0, sv = 0;
     if (k >= 0) {
@@ -545,8 +548,8 @@ int pass_a_g(const labfm_plan* p, const Packed<T>* X, const Packed<T>* M, G8<T>*
              const Phys<T>& ph, cudaStream_t st) {
     constexpr bool F = std::is_same<T, float>::value;
     const int grid = int((p->N * G + p->block - 1) / p->block);
-    k_adj_pointwise<T, G, F, F><<<grid, p->block, 0, st>>>(view<T>(p), X, M, g, o, ph);
-    LABFM_LAUNCH_CHECK("adjoint pointwise kernel");
+    cudaError_t e = launch_pdl(k_adj_pointwise<T, G, F, F>, grid, p->block, st, view<T>(p), X, M, g, o, ph);
+    if (e != cudaSuccess) return cuda_error(e, "adjoint pointwise kernel");
     return LABFM_OK;
 }
 
@@ -556,13 +559,11 @@ int pass_b_g(const labfm_plan* p, int mode, const G8<T>* g, const Packed<T>* o, 
              cudaStream_t st) {
     const int grid = int((p->N * G + p->block - 1) / p->block);
     const T* rs = static_cast<const T*>(p->rsum);
-    if (mode == 0)
-        k_adj_transpose<T, G, 0><<<grid, p->block, 0, st>>>(tview<T>(p), g, o, rs, out, Lam, Fnext, dt,
-                                                            bprev, cprev, fa);
-    else
-        k_adj_transpose<T, G, 1><<<grid, p->block, 0, st>>>(tview<T>(p), g, o, rs, out, Lam, Fnext, dt,
-                                                            bprev, cprev, fa);
-    LABFM_LAUNCH_CHECK("adjoint transpose kernel");
+    cudaError_t e = mode == 0 ? launch_pdl(k_adj_transpose<T, G, 0>, grid, p->block, st, tview<T>(p), g, o, rs, out,
+                                           Lam, Fnext, dt, bprev, cprev, fa)
+                              : launch_pdl(k_adj_transpose<T, G, 1>, grid, p->block, st, tview<T>(p), g, o, rs, out,
+                                           Lam, Fnext, dt, bprev, cprev, fa);
+    if (e != cudaSuccess) return cuda_error(e, "adjoint transpose kernel");
     return LABFM_OK;
 }
 
@@ -571,8 +572,8 @@ int filt_adj_g(const labfm_plan* p, const Packed<T>* lam, Packed<T>* Lam, Packed
                double b4, const FusedA<T>& fa, cudaStream_t st) {
     const int grid = int((p->N * G + p->block - 1) / p->block);
     const T* rsf = static_cast<const T*>(p->rsum) + 5 * p->N;
-    k_filter_adjoint<T, G><<<grid, p->block, 0, st>>>(tview<T>(p), lam, rsf, Lam, F, dt, b4, fa);
-    LABFM_LAUNCH_CHECK("filter adjoint kernel");
+    cudaError_t e = launch_pdl(k_filter_adjoint<T, G>, grid, p->block, st, tview<T>(p), lam, rsf, Lam, F, dt, b4, fa);
+    if (e != cudaSuccess) return cuda_error(e, "filter adjoint kernel");
     return LABFM_OK;
 }
 

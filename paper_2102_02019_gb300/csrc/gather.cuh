@@ -476,6 +476,25 @@ __device__ __forceinline__ void launch_prologue(const PlanView<T>& P, int i, int
 #endif
 }
 
+// Launch of a kernel that starts with launch_prologue, with programmatic stream
+// serialization (LABFM_PDL; without it a plain launch): the kernel may start while
+// the previous kernel of the stream finishes, and waits for it in launch_prologue
+// before reading anything that kernel writes.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(grid));
+    cfg.blockDim = dim3(unsigned(block));
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = LABFM_PDL ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 template <typename T>
 struct GlobalChunks {
     static constexpr bool kColAhead = LABFM_CHUNK_AOS >= 2;

@@ -195,6 +195,7 @@ __global__ void LABFM_STAGE_BOUNDS k_stage_rec(PlanView<T> P, const Packed<T>* X
     const int64_t node = gt / G;
     const int gl = int(gt % G);
     const int i = node < P.N ? int(node) : -1;
+    launch_prologue<T, false, G>(P, i, gl);
     const AoS<T> fld{X_in};
     T ai = 0, ui = 0, vi = 0;
     if (i >= 0) fld.get(i, ai, ui, vi);
@@ -572,24 +573,6 @@ __global__ void k_pack_rows(int64_t N, int64_t nnz, int64_t nnz_pad, int64_t off
 
 int grid_for(int64_t threads, int block) { return int((threads + block - 1) / block); }
 
-// Launch of a plain-grid stage or filter kernel with programmatic stream
-// serialization (LABFM_PDL; without it a plain launch): the kernel may start while
-// the previous kernel of the stream finishes, and waits for it in launch_prologue
-// before reading anything that kernel writes.
-template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(unsigned(grid));
-    cfg.blockDim = dim3(unsigned(block));
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = LABFM_PDL ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
-}
 
 // ---------------------------------------------------------------- dispatch
 
@@ -893,9 +876,9 @@ int stage_rec_launch_g(const labfm_plan* p, const Packed<T>* xin, const Packed<T
                        cudaStream_t st) {
     constexpr bool F = std::is_same<T, float>::value;
     const int grid = grid_for(p->N * G, kGatherBlock);
-    k_stage_rec<T, G, F, F><<<grid, kGatherBlock, 0, st>>>(view<T>(p), xin, qin, qout, xout, dt, bk, ck, ph,
-                                                           D);
-    LABFM_LAUNCH_CHECK("recording rk stage kernel");
+    cudaError_t e = launch_pdl(k_stage_rec<T, G, F, F>, grid, kGatherBlock, st, view<T>(p), xin, qin, qout, xout,
+                               dt, bk, ck, ph, D);
+    if (e != cudaSuccess) return cuda_error(e, "recording rk stage kernel");
     return LABFM_OK;
 }
 
