@@ -40,7 +40,7 @@ def workload_config(nx):
     return dict(WORKLOAD, workload=f"taylor-green {nx}x{nx} jittered lattice ({nx * nx} nodes), "
                 "m=8, h/s=2.8 (reduced size)", nodes=nx * nx)
 SAMPLE_ROWS = 2048
-PROFILE_EVERY = 5  # timed steps per step whose launches carry CUDA events
+PROFILE_EVERY = 10  # timed steps per step whose launches carry CUDA events
 
 
 def parse():

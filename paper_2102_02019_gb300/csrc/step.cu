@@ -470,6 +470,10 @@ __global__ void k_filter_aos(PlanView<T> P, const Packed<T>* in, Packed<T>* out)
 
 template <typename T>
 __global__ void k_pack(int64_t N, const T* __restrict__ soa, Packed<T>* __restrict__ out) {
+#if LABFM_PDL
+    pdl_launch_dependents();
+    pdl_wait();
+#endif
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < N;
          i += int64_t(gridDim.x) * blockDim.x)
         store(out, i, soa[i], soa[N + i], soa[2 * N + i]);
@@ -477,6 +481,10 @@ __global__ void k_pack(int64_t N, const T* __restrict__ soa, Packed<T>* __restri
 
 template <typename T>
 __global__ void k_unpack(int64_t N, const Packed<T>* __restrict__ in, T* __restrict__ soa) {
+#if LABFM_PDL
+    pdl_launch_dependents();
+    pdl_wait();
+#endif
     for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < N;
          i += int64_t(gridDim.x) * blockDim.x) {
         T a, u, v;
@@ -968,12 +976,11 @@ int rk_pack(const labfm_plan* p, const void* Q, void* work, cudaStream_t st) {
     const int pg = int(std::min<int64_t>((p->N + 255) / 256, 65535));
     if (p->dtype == LABFM_F32) {
         Packed<float>* X = static_cast<Packed<float>*>(work) + p->N;
-        k_pack<float><<<pg, 256, 0, st>>>(p->N, static_cast<const float*>(Q), X);
+        LABFM_CUDA_TRY(launch_pdl(k_pack<float>, pg, 256, st, p->N, static_cast<const float*>(Q), X));
     } else {
         Packed<double>* X = static_cast<Packed<double>*>(work) + p->N;
-        k_pack<double><<<pg, 256, 0, st>>>(p->N, static_cast<const double*>(Q), X);
+        LABFM_CUDA_TRY(launch_pdl(k_pack<double>, pg, 256, st, p->N, static_cast<const double*>(Q), X));
     }
-    LABFM_LAUNCH_CHECK("pack kernel");
     return LABFM_OK;
 }
 
@@ -981,12 +988,11 @@ int rk_unpack(const labfm_plan* p, void* Q, const void* work, cudaStream_t st) {
     const int pg = int(std::min<int64_t>((p->N + 255) / 256, 65535));
     if (p->dtype == LABFM_F32) {
         const Packed<float>* X = static_cast<const Packed<float>*>(work) + p->N;
-        k_unpack<float><<<pg, 256, 0, st>>>(p->N, X, static_cast<float*>(Q));
+        LABFM_CUDA_TRY(launch_pdl(k_unpack<float>, pg, 256, st, p->N, X, static_cast<float*>(Q)));
     } else {
         const Packed<double>* X = static_cast<const Packed<double>*>(work) + p->N;
-        k_unpack<double><<<pg, 256, 0, st>>>(p->N, X, static_cast<double*>(Q));
+        LABFM_CUDA_TRY(launch_pdl(k_unpack<double>, pg, 256, st, p->N, X, static_cast<double*>(Q)));
     }
-    LABFM_LAUNCH_CHECK("unpack kernel");
     return LABFM_OK;
 }
 
