@@ -399,7 +399,7 @@ extern "C" int labfm_plan_autotune(labfm_plan* p, const void* fields, void* scra
     cudaEvent_t e0, e1;
     LABFM_CUDA_TRY(cudaEventCreate(&e0));
     LABFM_CUDA_TRY(cudaEventCreate(&e1));
-    // the gather kernels run fixed 128-thread blocks; the lanes per node are tuned
+    // the gather kernels run fixed one-warp blocks; the lanes per node are tuned
     const int groups[] = {2, 4, 8, 16, 32};
     const int blocks[] = {p->block};
     float best = 1e30f;

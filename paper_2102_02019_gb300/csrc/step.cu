@@ -28,18 +28,22 @@ namespace {
 
 // ---------------------------------------------------------------- kernels
 
-// The fused gather kernels (stage, right-hand side) run 128-thread blocks.  A
-// register budget for 8 resident blocks per SM (64 registers) had been faster
-// than the unconstrained allocation while the lanes' own loads were the only
-// bytes in flight; with the L2 prefetch of the record stream the natural 72
-// registers (7 blocks per SM) are faster (m = 8: 111.4 -> 106.7 us, m = 10:
-// 599 -> 572 us), so the bound asks for no more than 6.
-constexpr int kGatherBlock = 128;
-#ifndef LABFM_STAGE_MINB
-#define LABFM_STAGE_MINB 6
+// The fused gather kernels (stage, right-hand side) run one-warp blocks, so that
+// every warp retires on its own instead of waiting for the slowest warp of a
+// larger block (with programmatic launches, per step: m = 8 451.1 -> 445.1 us,
+// m = 10 370.4 -> 365.0 us, m = 6 316.5 -> 310.3 us, m = 4 230.7 -> 225.8 us
+// against 128-thread blocks; 64-thread blocks in between).  The register budget
+// is set in resident threads per SM: a budget for 1024 (64 registers) had been
+// faster than the unconstrained allocation while the lanes' own loads were the
+// only bytes in flight; with the L2 prefetch of the record stream the natural 72
+// registers (896 threads per SM) are faster (m = 8: 111.4 -> 106.7 us, m = 10:
+// 599 -> 572 us), so the bound asks for no more than 768.
+constexpr int kGatherBlock = 32;
+#ifndef LABFM_STAGE_MIN_THREADS
+#define LABFM_STAGE_MIN_THREADS 768
 #endif
 #define LABFM_STAGE_BOUNDS \
-    __launch_bounds__(kGatherBlock, sizeof(T) == 4 ? LABFM_STAGE_MINB : 6)
+    __launch_bounds__(kGatherBlock, (sizeof(T) == 4 ? LABFM_STAGE_MIN_THREADS : 768) / kGatherBlock)
 
 template <typename T, int G, bool KAHAN, bool SCALED, bool WALL = false>
 __global__ void LABFM_STAGE_BOUNDS k_rhs_soa(PlanView<T> P, SoA<T> in, T* __restrict__ out, Phys<T> ph) {
@@ -123,13 +127,15 @@ constexpr int kTileRows = 4;
 
 // WALL (plain grid only): plans with walls, whose wall nodes take the wall's
 // right-hand side.
-#ifndef LABFM_PERSIST_MINB
-#define LABFM_PERSIST_MINB 7
+#ifndef LABFM_PERSIST_MIN_THREADS
+#define LABFM_PERSIST_MIN_THREADS 896
 #endif
-// The work-queue instantiation keeps 7 resident blocks per SM (at most 73 registers;
-// left to itself it takes 78 and fits 6).
+// The work-queue instantiation keeps 896 resident threads per SM (at most 73
+// registers; left to itself it takes 78 and fits 768).
 template <typename T, int G, bool KAHAN, bool SCALED, bool PERSIST, bool WALL = false>
-__global__ void __launch_bounds__(kGatherBlock, sizeof(T) == 4 ? (PERSIST ? LABFM_PERSIST_MINB : LABFM_STAGE_MINB) : 6)
+__global__ void __launch_bounds__(kGatherBlock, (sizeof(T) == 4 ? (PERSIST ? LABFM_PERSIST_MIN_THREADS
+                                                                          : LABFM_STAGE_MIN_THREADS)
+                                                                : 768) / kGatherBlock)
     k_stage(PlanView<T> P, const Packed<T>* X_in, const Packed<T>* Q_in,
                         Packed<T>* Q_out, Packed<T>* X_out, double dt, double bk, double ck,
                         Phys<T> ph, int* counter) {
