@@ -660,13 +660,14 @@ class Plan:
 
     def tune_step(self, Q: torch.Tensor, phys: Phys, dt: float, steps: int = 3,
                   groups=(2, 4, 8, 16), staged=((16, 3), (32, 3), (32, 4)),
-                  prefetch=(0, 2), filter_groups=(2, 4, 8, 16)) -> dict:
+                  prefetch=(0, 2), filter_groups=(2, 4, 8, 16), filter_blocks=(64, 128)) -> dict:
         """Autotune the time step itself: time `steps` RK steps (CUDA events) for every
         lanes-per-node group with the plain and the persistent stage kernel (F32: with
         each L2 prefetch distance), and (F32) for the staged kernel at the given (lanes
         per node, ring slots), keep the fastest; then, with that stage kernel, time the
-        filter's own lanes per node with its plain and persistent grids and keep the
-        fastest.  Q is not modified.  Returns the chosen configuration."""
+        filter's own lanes per node with its plain and persistent grids and the plan's
+        block size (which only the filter and adjoint kernels use; the stage kernels run
+        one-warp blocks), and keep the fastest.  Q is not modified.  Returns the chosen configuration."""
         _state(self, Q)
         info = self.info()
         block = info["block"]
@@ -702,13 +703,19 @@ class Plan:
         self.set_staging(stages)
         self.set_prefetch(pf)
         self.set_launch(g, block)
-        fbest = (best[0], 0, False)
-        for fg in filter_groups:
-            for fp in (False, True):
-                self.set_filter_launch(fg, fp)
-                ms = timed()
-                if ms < fbest[0]:
-                    fbest = (ms, fg, fp)
+        fbest = (best[0], 0, False, block)
+        for fb in filter_blocks:
+            for fg in filter_groups:
+                if fb % fg or fb % 32:
+                    continue
+                self.set_launch(g, fb)
+                for fp in (False, True):
+                    self.set_filter_launch(fg, fp)
+                    ms = timed()
+                    if ms < fbest[0]:
+                        fbest = (ms, fg, fp, fb)
+        block = fbest[3]
+        self.set_launch(g, block)
         self.set_filter_launch(fbest[1], fbest[2])
         if self.device_status() != 0:
             raise LabfmError(7, "a staged stage kernel's bounded wait ran out while tuning")
