@@ -114,6 +114,7 @@ typedef struct labfm_plan_info {
     int32_t stages;       /* shared-memory staging slots (labfm_plan_set_staging; 0 = off) */
     int32_t filter_group; /* lanes per node of the filter kernel (labfm_plan_set_filter_launch) */
     int32_t filter_persistent; /* 1 if the filter runs a persistent grid-stride grid */
+    int32_t programmatic; /* 1 if the kernels use programmatic launches (labfm_plan_set_programmatic_launch) */
 } labfm_plan_info;
 
 /* Message for the most recent failing call on this thread ("" if none). */
@@ -465,6 +466,19 @@ int labfm_plan_set_persistent(labfm_plan* plan, int enable);
  * plans (whose kernels do not prefetch).  Host-only call.
  */
 int labfm_plan_set_prefetch(labfm_plan* plan, int distance);
+
+/*
+ * Programmatic dependent launches (enable = 1, the default) or plain launches
+ * (enable = 0) for the plan's plain-grid stage, filter, recording-stage, adjoint,
+ * pack and unpack kernels.  With them on, each such kernel is launched with
+ * programmatic stream serialization: it may start while the previous kernel of the
+ * stream finishes, reads only the plan's constant operator (row pointers, and an L2
+ * prefetch of its rows' first record blocks) until griddepcontrol.wait has seen the
+ * previous kernel complete, and only then reads or writes the state; results are
+ * bit-identical either way.  No counterpart in the paper: a launch-scheduling
+ * setting (sm_90 and later).  EINVAL for another value of enable.  Host-only call.
+ */
+int labfm_plan_set_programmatic_launch(labfm_plan* plan, int enable);
 
 /*
  * Shared-memory staging of the operator stream for the F32 stage kernel

@@ -61,7 +61,8 @@ class _PlanInfo(ctypes.Structure):
                 ("n_instances", ctypes.c_int32), ("entry_bytes", ctypes.c_int32),
                 ("filter_entry_bytes", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
                 ("prefetch", ctypes.c_int32), ("stages", ctypes.c_int32),
-                ("filter_group", ctypes.c_int32), ("filter_persistent", ctypes.c_int32)]
+                ("filter_group", ctypes.c_int32), ("filter_persistent", ctypes.c_int32),
+                ("programmatic", ctypes.c_int32)]
 
 
 class _Profile(ctypes.Structure):
@@ -122,6 +123,7 @@ _SIGS = {
     "labfm_stable_dt_instances": (_I32, [_P, _P, _P, _D, _D, _P, _P]),
     "labfm_plan_set_persistent": (_I32, [_P, _I32]),
     "labfm_plan_set_prefetch": (_I32, [_P, _I32]),
+    "labfm_plan_set_programmatic_launch": (_I32, [_P, _I32]),
     "labfm_plan_set_staging": (_I32, [_P, _I32, _P]),
     "labfm_plan_device_status": (_I32, [_P, ctypes.POINTER(_I32)]),
     "labfm_plan_set_wait_limit": (_I32, [_P, _I64]),
@@ -149,7 +151,7 @@ _SIGS = {
 
 
 # the C ABI this binding's signatures and structures follow (include/labfm.h)
-ABI_VERSION = 4
+ABI_VERSION = 5
 
 
 def _load() -> ctypes.CDLL:
@@ -472,6 +474,11 @@ class Plan:
     def set_prefetch(self, distance: int) -> None:
         """labfm_plan_set_prefetch: L2 prefetch distance of the F32 record stream (0 = off)."""
         _check(lib.labfm_plan_set_prefetch(self._h, int(distance)))
+
+    def set_programmatic_launch(self, enable: bool = True) -> None:
+        """labfm_plan_set_programmatic_launch: programmatic dependent launches of the
+        plan's kernels (on by default) or plain launches; results are the same."""
+        _check(lib.labfm_plan_set_programmatic_launch(self._h, 1 if enable else 0))
 
     def set_staging(self, stages: int = 3, stream=None) -> None:
         """labfm_plan_set_staging: shared-memory staging of the operator stream for the

@@ -548,7 +548,7 @@ int pass_a_g(const labfm_plan* p, const Packed<T>* X, const Packed<T>* M, G8<T>*
              const Phys<T>& ph, cudaStream_t st) {
     constexpr bool F = std::is_same<T, float>::value;
     const int grid = int((p->N * G + p->block - 1) / p->block);
-    cudaError_t e = launch_pdl(k_adj_pointwise<T, G, F, F>, grid, p->block, st, view<T>(p), X, M, g, o, ph);
+    cudaError_t e = launch_pdl(p, k_adj_pointwise<T, G, F, F>, grid, p->block, st, view<T>(p), X, M, g, o, ph);
     if (e != cudaSuccess) return cuda_error(e, "adjoint pointwise kernel");
     return LABFM_OK;
 }
@@ -559,9 +559,9 @@ int pass_b_g(const labfm_plan* p, int mode, const G8<T>* g, const Packed<T>* o, 
              cudaStream_t st) {
     const int grid = int((p->N * G + p->block - 1) / p->block);
     const T* rs = static_cast<const T*>(p->rsum);
-    cudaError_t e = mode == 0 ? launch_pdl(k_adj_transpose<T, G, 0>, grid, p->block, st, tview<T>(p), g, o, rs, out,
+    cudaError_t e = mode == 0 ? launch_pdl(p, k_adj_transpose<T, G, 0>, grid, p->block, st, tview<T>(p), g, o, rs, out,
                                            Lam, Fnext, dt, bprev, cprev, fa)
-                              : launch_pdl(k_adj_transpose<T, G, 1>, grid, p->block, st, tview<T>(p), g, o, rs, out,
+                              : launch_pdl(p, k_adj_transpose<T, G, 1>, grid, p->block, st, tview<T>(p), g, o, rs, out,
                                            Lam, Fnext, dt, bprev, cprev, fa);
     if (e != cudaSuccess) return cuda_error(e, "adjoint transpose kernel");
     return LABFM_OK;
@@ -572,7 +572,7 @@ int filt_adj_g(const labfm_plan* p, const Packed<T>* lam, Packed<T>* Lam, Packed
                double b4, const FusedA<T>& fa, cudaStream_t st) {
     const int grid = int((p->N * G + p->block - 1) / p->block);
     const T* rsf = static_cast<const T*>(p->rsum) + 5 * p->N;
-    cudaError_t e = launch_pdl(k_filter_adjoint<T, G>, grid, p->block, st, tview<T>(p), lam, rsf, Lam, F, dt, b4, fa);
+    cudaError_t e = launch_pdl(p, k_filter_adjoint<T, G>, grid, p->block, st, tview<T>(p), lam, rsf, Lam, F, dt, b4, fa);
     if (e != cudaSuccess) return cuda_error(e, "filter adjoint kernel");
     return LABFM_OK;
 }

@@ -173,7 +173,7 @@ void prof_end(labfm_plan* p, int idx, cudaStream_t st) {
 
 extern "C" const char* labfm_last_error(void) { return g_last_error.c_str(); }
 
-extern "C" int labfm_abi_version(void) { return 4; }
+extern "C" int labfm_abi_version(void) { return 5; }
 
 extern "C" int labfm_plan_create(labfm_plan** out, int64_t N, int64_t nnz, labfm_dtype dtype,
                                  const int32_t* row_ptr, const int32_t* col, const double* w,
@@ -255,6 +255,13 @@ extern "C" int labfm_plan_set_prefetch(labfm_plan* p, int distance) {
     return LABFM_OK;
 }
 
+extern "C" int labfm_plan_set_programmatic_launch(labfm_plan* p, int enable) {
+    if (int rc = check_plan(p)) return rc;
+    if (enable != 0 && enable != 1) return set_error(LABFM_EINVAL, "enable must be 0 or 1");
+    p->programmatic = enable != 0;
+    return LABFM_OK;
+}
+
 extern "C" int labfm_plan_set_staging(labfm_plan* p, int stages, void* stream) {
     if (int rc = check_plan(p)) return rc;
     if (stages != 0 && fault_alloc()) return injected_alloc_error("labfm_plan_set_staging");
@@ -324,6 +331,7 @@ extern "C" int labfm_plan_get_info(const labfm_plan* p, labfm_plan_info* info) {
     info->stages = p->stages;
     info->filter_group = p->filter_group ? p->filter_group : p->group;
     info->filter_persistent = p->filter_persistent ? 1 : 0;
+    info->programmatic = p->programmatic ? 1 : 0;
     return LABFM_OK;
 }
 

@@ -477,11 +477,12 @@ __device__ __forceinline__ void launch_prologue(const PlanView<T>& P, int i, int
 }
 
 // Launch of a kernel that starts with launch_prologue, with programmatic stream
-// serialization (LABFM_PDL; without it a plain launch): the kernel may start while
+// serialization (LABFM_PDL and the plan's setting; otherwise a plain launch): the kernel may start while
 // the previous kernel of the stream finishes, and waits for it in launch_prologue
 // before reading anything that kernel writes.
 template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t st, Args... args) {
+cudaError_t launch_pdl(const labfm_plan* p, void (*kernel)(KArgs...), int grid, int block, cudaStream_t st,
+                       Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(unsigned(grid));
     cfg.blockDim = dim3(unsigned(block));
@@ -491,7 +492,7 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = LABFM_PDL ? 1 : 0;
+    cfg.numAttrs = (LABFM_PDL && p->programmatic) ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 

@@ -94,6 +94,7 @@ struct labfm_plan {
     double* dt_node = nullptr;   // per-node time step (labfm_plan_set_dt), or null
     bool persistent = false;     // stage kernel takes node tiles from a work queue
     int prefetch = 0;            // L2 prefetch distance of the F32 record stream (labfm_plan_set_prefetch)
+    bool programmatic = true;    // programmatic dependent launches (labfm_plan_set_programmatic_launch)
     int persist_grid = 0;
     // filter launch (labfm_plan_set_filter_launch): lanes per node (0 = the plan's
     // group) and a persistent grid-stride grid of filter_grid blocks

@@ -628,7 +628,7 @@ int stage_launch_g(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* q
     constexpr bool F = std::is_same<T, float>::value;
     if (p->wall_slot) {
         const int grid = grid_for(p->N * G, block);
-        cudaError_t e = launch_pdl(k_stage<T, G, F, F, false, true>, grid, block, st, view<T>(p), xin, qin, qout,
+        cudaError_t e = launch_pdl(p, k_stage<T, G, F, F, false, true>, grid, block, st, view<T>(p), xin, qin, qout,
                                    xout, dt, bk, ck, ph, counter);
         if (e != cudaSuccess) return cuda_error(e, "rk stage kernel");
     } else if (p->persistent) {
@@ -636,7 +636,7 @@ int stage_launch_g(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* q
                                                                       dt, bk, ck, ph, counter);
     } else {
         const int grid = grid_for(p->N * G, block);
-        cudaError_t e = launch_pdl(k_stage<T, G, F, F, false>, grid, block, st, view<T>(p), xin, qin, qout, xout,
+        cudaError_t e = launch_pdl(p, k_stage<T, G, F, F, false>, grid, block, st, view<T>(p), xin, qin, qout, xout,
                                    dt, bk, ck, ph, counter);
         if (e != cudaSuccess) return cuda_error(e, "rk stage kernel");
     }
@@ -658,7 +658,7 @@ int stage_range_launch_g(const labfm_plan* p, int r, const Packed<T>* xin, const
     if (v.n_hi <= v.n_lo) return LABFM_OK;
     const int grid = grid_for((v.n_hi - v.n_lo) * G, kGatherBlock);
     int* no_counter = nullptr;
-    cudaError_t e = launch_pdl(k_stage<T, G, F, F, false>, grid, kGatherBlock, st, v, xin, qin, qout, xout, dt, bk,
+    cudaError_t e = launch_pdl(p, k_stage<T, G, F, F, false>, grid, kGatherBlock, st, v, xin, qin, qout, xout, dt, bk,
                                ck, ph, no_counter);
     if (e != cudaSuccess) return cuda_error(e, "rk stage kernel (launch range)");
     LABFM_LAUNCH_CHECK("rk stage kernel (launch range)");
@@ -724,7 +724,7 @@ int filter_aos_g(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaS
         k_filter_aos<T, G, F, true><<<p->filter_grid, p->block, 0, st>>>(view<T>(p), in, out);
     } else {
         const int grid = grid_for(p->N * G, p->block);
-        cudaError_t e = launch_pdl(k_filter_aos<T, G, F, false>, grid, p->block, st, view<T>(p), in, out);
+        cudaError_t e = launch_pdl(p, k_filter_aos<T, G, F, false>, grid, p->block, st, view<T>(p), in, out);
         if (e != cudaSuccess) return cuda_error(e, "filter kernel");
     }
     LABFM_LAUNCH_CHECK("filter kernel");
@@ -742,7 +742,7 @@ int filter_range_launch_g(const labfm_plan* p, int r, const Packed<T>* in, Packe
     v.pf = p->range_pf[r];
     if (v.n_hi <= v.n_lo) return LABFM_OK;
     const int grid = grid_for((v.n_hi - v.n_lo) * G, p->block);
-    cudaError_t e = launch_pdl(k_filter_aos<T, G, std::is_same<T, float>::value, false>, grid, p->block, st, v, in,
+    cudaError_t e = launch_pdl(p, k_filter_aos<T, G, std::is_same<T, float>::value, false>, grid, p->block, st, v, in,
                                out);
     if (e != cudaSuccess) return cuda_error(e, "filter kernel (launch range)");
     LABFM_LAUNCH_CHECK("filter kernel (launch range)");
@@ -890,7 +890,7 @@ int stage_rec_launch_g(const labfm_plan* p, const Packed<T>* xin, const Packed<T
                        cudaStream_t st) {
     constexpr bool F = std::is_same<T, float>::value;
     const int grid = grid_for(p->N * G, kGatherBlock);
-    cudaError_t e = launch_pdl(k_stage_rec<T, G, F, F>, grid, kGatherBlock, st, view<T>(p), xin, qin, qout, xout,
+    cudaError_t e = launch_pdl(p, k_stage_rec<T, G, F, F>, grid, kGatherBlock, st, view<T>(p), xin, qin, qout, xout,
                                dt, bk, ck, ph, D);
     if (e != cudaSuccess) return cuda_error(e, "recording rk stage kernel");
     return LABFM_OK;
@@ -982,10 +982,10 @@ int rk_pack(const labfm_plan* p, const void* Q, void* work, cudaStream_t st) {
     const int pg = int(std::min<int64_t>((p->N + 255) / 256, 65535));
     if (p->dtype == LABFM_F32) {
         Packed<float>* X = static_cast<Packed<float>*>(work) + p->N;
-        LABFM_CUDA_TRY(launch_pdl(k_pack<float>, pg, 256, st, p->N, static_cast<const float*>(Q), X));
+        LABFM_CUDA_TRY(launch_pdl(p, k_pack<float>, pg, 256, st, p->N, static_cast<const float*>(Q), X));
     } else {
         Packed<double>* X = static_cast<Packed<double>*>(work) + p->N;
-        LABFM_CUDA_TRY(launch_pdl(k_pack<double>, pg, 256, st, p->N, static_cast<const double*>(Q), X));
+        LABFM_CUDA_TRY(launch_pdl(p, k_pack<double>, pg, 256, st, p->N, static_cast<const double*>(Q), X));
     }
     return LABFM_OK;
 }
@@ -994,10 +994,10 @@ int rk_unpack(const labfm_plan* p, void* Q, const void* work, cudaStream_t st) {
     const int pg = int(std::min<int64_t>((p->N + 255) / 256, 65535));
     if (p->dtype == LABFM_F32) {
         const Packed<float>* X = static_cast<const Packed<float>*>(work) + p->N;
-        LABFM_CUDA_TRY(launch_pdl(k_unpack<float>, pg, 256, st, p->N, X, static_cast<float*>(Q)));
+        LABFM_CUDA_TRY(launch_pdl(p, k_unpack<float>, pg, 256, st, p->N, X, static_cast<float*>(Q)));
     } else {
         const Packed<double>* X = static_cast<const Packed<double>*>(work) + p->N;
-        LABFM_CUDA_TRY(launch_pdl(k_unpack<double>, pg, 256, st, p->N, X, static_cast<double*>(Q)));
+        LABFM_CUDA_TRY(launch_pdl(p, k_unpack<double>, pg, 256, st, p->N, X, static_cast<double*>(Q)));
     }
     return LABFM_OK;
 }

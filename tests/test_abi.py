@@ -36,7 +36,7 @@ def test_library_exports_every_declared_symbol(built_lib):
 
 def test_binding_loads_and_covers_the_header(built_lib):
     import paper_2102_02019_gb300 as lb
-    assert lb.lib.labfm_abi_version() == 4
+    assert lb.lib.labfm_abi_version() == 5
     assert lb.lib.labfm_last_error() == b""
     declared = set(_declared_functions())
     assert declared <= set(lb.exported_symbols()), declared - set(lb.exported_symbols())
