@@ -1010,6 +1010,25 @@ def run_ours(args, world, rank, local):
     ms64 = max_over_ranks(ms64, world)
     value64 = 4.0 * N * k64 * world / (ms64 * 1e-3)
 
+    # the same FP32 steps without programmatic launches, and again with them, both
+    # without launch events (the schedule, not the arithmetic, differs)
+    def plain_vs_programmatic(steps=max(10, args.steps)):
+        out = {}
+        for key, on in (("ms_per_step_plain_launches", False), ("ms_per_step_programmatic", True)):
+            plan32.set_programmatic_launch(on)
+            lb.rk_step(plan32, Q32, dt32, 3, phys, work=work32)
+            a, b = ev(), ev()
+            torch.cuda.synchronize()
+            a.record()
+            lb.rk_step(plan32, Q32, dt32, steps, phys, work=work32)
+            b.record()
+            torch.cuda.synchronize()
+            out[key] = a.elapsed_time(b) / steps
+        plan32.set_programmatic_launch(True)
+        out["steps"] = steps
+        return out
+    launch_modes = plain_vs_programmatic()
+
     # end to end through the C ABI with host buffers: pinned host state in,
     # one step on the device, state back to the host, every step
     Qh = q0.to(torch.float32).cpu().pin_memory()
@@ -1093,6 +1112,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": 5 * args.steps + 2,
         "clocks": clocks,
         "kernel_source_hash": khash,
+        "launch_modes": launch_modes,
     }
 
     if not args.no_extras:
