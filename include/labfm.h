@@ -545,8 +545,8 @@ int labfm_plan_get_info(const labfm_plan* plan, labfm_plan_info* info);
 /*
  * Override the launch shape: `group` lanes per node (2, 4, 8, 16 or 32) in every
  * gather kernel, and `block` threads per block (a multiple of 32 and of group,
- * 64..1024) for the filter and adjoint kernels; the fused right-hand-side and
- * stage kernels always run one-warp (32-thread) blocks.  Defaults: group 4, block 128;
+ * 64..1024) for the filter and filter-transpose kernels; the fused right-hand-side,
+ * stage and adjoint gather kernels always run one-warp (32-thread) blocks.  Defaults: group 4, block 128;
  * labfm_plan_autotune picks the fastest group.
  */
 int labfm_plan_set_launch(labfm_plan* plan, int group, int block);

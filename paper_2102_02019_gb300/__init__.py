@@ -673,8 +673,8 @@ class Plan:
         each L2 prefetch distance), and (F32) for the staged kernel at the given (lanes
         per node, ring slots), keep the fastest; then, with that stage kernel, time the
         filter's own lanes per node with its plain and persistent grids and the plan's
-        block size (which only the filter and adjoint kernels use; the stage kernels run
-        one-warp blocks), and keep the fastest.  Q is not modified.  Returns the chosen configuration."""
+        block size (which only the filter and filter-transpose kernels use; the stage and
+        adjoint gather kernels run one-warp blocks), and keep the fastest.  Q is not modified.  Returns the chosen configuration."""
         _state(self, Q)
         info = self.info()
         block = info["block"]
