@@ -214,7 +214,7 @@ def test_open_box_time_steps_match_oracle(lb, box):
 def test_open_box_gpu_operator_and_fp32(lb, box):
     # the GPU-built operator (weights within the weight build's conditioning bound of
     # the oracle's, test above) stepped on the GPU against the oracle's step with those
-    # same weights: FP64 to the spec bar over three steps, FP32 one step within
+    # same weights: FP64 to 1e-12 over three steps, FP32 one step within
     # the derived step budget
     from tests.fp32_budget import boundary_step_bound
     ns = box.ns

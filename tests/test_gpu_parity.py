@@ -368,7 +368,7 @@ def test_trajectory_fp64_100_steps_configured_geometry_shifted(lb):
 def test_filter_launch_shapes(lb, c1, dtype):
     # the filter's own lanes per node and its persistent grid: the persistent grid
     # gives the same state bit for bit; other lane counts sum in another order.  FP64:
-    # two steps to the spec bar; FP32: one step elementwise within the derived
+    # two steps to 1e-12; FP32: one step elementwise within the derived
     # step budget
     from tests.fp32_budget import step_bound
     c = c1

@@ -173,7 +173,7 @@ def test_channel_time_steps_match_oracle(lb, ch):
 def test_channel_step_with_gpu_operator_and_fp32(lb, ch):
     # the GPU-built operator (whose weights match the oracle's within the weight
     # build's conditioning bound, test above) stepped on the GPU against the oracle's
-    # step with those same weights: FP64 to the spec bar, FP32 one step within
+    # step with those same weights: FP64 to 1e-12, FP32 one step within
     # the derived step budget; the wall velocity stays exactly zero
     from tests.fp32_budget import boundary_step_bound
     ns = ch.ns
