@@ -390,7 +390,9 @@ int labfm_plan_create_batched(labfm_plan** plan, int n_inst, const int64_t* N_in
  *   wall_nodes   device, n_wall int32; wall_normal: device, n_wall x 2 doubles
  *                (inward unit normals); n_wall = 0 removes the walls
  * Plans with walls run the plain stage grid (not the persistent or staged
- * kernels); the adjoint and recording calls refuse them.  Not for batched plans.
+ * kernels); the adjoint and recording calls refuse them.  On a batched plan the
+ * nodes are the plan's (instance k's node q is inst_off[k] + q); launch ranges
+ * (labfm_plan_set_launch_ranges) and walls exclude each other.
  * Synchronises `stream`.  Errors: EINVAL (node out of range or listed twice,
  * normal not of unit length), ENOMEM.
  */
@@ -420,7 +422,7 @@ int labfm_plan_set_walls(labfm_plan* plan, int64_t n_wall, const int32_t* wall_n
  *           p_inf in the first (the second unused); unused for walls
  *   params  host: sigma, L, M, rho0 (one set per plan)
  * n = 0 removes the boundaries.  As labfm_plan_set_walls otherwise (plain stage
- * grid, no adjoint, no batched plans, synchronises `stream`).
+ * grid, no adjoint, the plan's node numbering on batched plans, synchronises `stream`).
  * Errors: EINVAL (node out of range or listed twice, normal not of unit length,
  * unknown kind, sigma < 0, L <= 0, M outside [0, 1), rho0 <= 0), ENOMEM.
  */
