@@ -391,8 +391,8 @@ int labfm_plan_create_batched(labfm_plan** plan, int n_inst, const int64_t* N_in
  *                (inward unit normals); n_wall = 0 removes the walls
  * Plans with walls run the plain stage grid (not the persistent or staged
  * kernels); the adjoint and recording calls refuse them.  On a batched plan the
- * nodes are the plan's (instance k's node q is inst_off[k] + q); launch ranges
- * (labfm_plan_set_launch_ranges) and walls exclude each other.
+ * nodes are the plan's (instance k's node q is inst_off[k] + q), and launch
+ * ranges (labfm_plan_set_launch_ranges) run the same boundary right-hand side.
  * Synchronises `stream`.  Errors: EINVAL (node out of range or listed twice,
  * normal not of unit length), ENOMEM.
  */
@@ -564,7 +564,7 @@ int labfm_plan_set_launch(labfm_plan* plan, int group, int block);
  * the plan.  n = 0 removes the ranges.  Host-only; the arrays are copied.
  *   begin  host, n + 1 int64 (begin[0] = 0, begin[n] = N, not decreasing)
  *   group, prefetch  host, n int32
- * Errors: EINVAL (bounds, unsupported lanes per node, prefetch, a plan with walls).
+ * Errors: EINVAL (bounds, unsupported lanes per node, prefetch).
  */
 int labfm_plan_set_launch_ranges(labfm_plan* plan, int n, const int64_t* begin, const int32_t* group,
                                  const int32_t* prefetch);

@@ -353,7 +353,6 @@ extern "C" int labfm_plan_set_launch_ranges(labfm_plan* p, int n, const int64_t*
     if (n < 0) return set_error(LABFM_EINVAL, "negative number of ranges");
     if (n > 0) {
         if (!begin || !group || !prefetch) return set_error(LABFM_EINVAL, "null pointer argument");
-        if (p->wall_slot) return set_error(LABFM_EINVAL, "launch ranges are not supported on plans with walls");
         if (begin[0] != 0 || begin[n] != p->N) return set_error(LABFM_EINVAL, "ranges must cover [0, N)");
         for (int r = 0; r < n; ++r) {
             if (begin[r + 1] < begin[r]) return set_error(LABFM_EINVAL, "range boundaries must not decrease");

@@ -411,8 +411,9 @@ PlanView<T> view(const labfm_plan* p) {
 // m = 4 (~35) neither.
 constexpr int kPrefetchMinRow = 80;
 
-// Programmatic dependent launch (sm_90 and later).  The plain-grid stage and
-// filter launches carry programmatic stream serialization: such a kernel may start
+// Programmatic dependent launch (sm_90 and later).  The plain-grid stage, filter,
+// recording-stage, adjoint pass A and B, filter-transpose, pack and unpack launches
+// carry programmatic stream serialization (launch_pdl): such a kernel may start
 // while the kernel before it in the stream still runs, once every block of that
 // kernel has signalled launch_dependents, and griddepcontrol.wait holds it until
 // that kernel has completed and its writes are visible.  Without the launch

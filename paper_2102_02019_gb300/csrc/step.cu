@@ -658,8 +658,10 @@ int stage_range_launch_g(const labfm_plan* p, int r, const Packed<T>* xin, const
     if (v.n_hi <= v.n_lo) return LABFM_OK;
     const int grid = grid_for((v.n_hi - v.n_lo) * G, kGatherBlock);
     int* no_counter = nullptr;
-    cudaError_t e = launch_pdl(p, k_stage<T, G, F, F, false>, grid, kGatherBlock, st, v, xin, qin, qout, xout, dt, bk,
-                               ck, ph, no_counter);
+    cudaError_t e = p->wall_slot ? launch_pdl(p, k_stage<T, G, F, F, false, true>, grid, kGatherBlock, st, v, xin,
+                                              qin, qout, xout, dt, bk, ck, ph, no_counter)
+                                 : launch_pdl(p, k_stage<T, G, F, F, false>, grid, kGatherBlock, st, v, xin, qin,
+                                              qout, xout, dt, bk, ck, ph, no_counter);
     if (e != cudaSuccess) return cuda_error(e, "rk stage kernel (launch range)");
     LABFM_LAUNCH_CHECK("rk stage kernel (launch range)");
     return LABFM_OK;

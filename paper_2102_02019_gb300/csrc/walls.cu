@@ -706,7 +706,6 @@ extern "C" int labfm_plan_set_walls(labfm_plan* p, int64_t n_wall, const int32_t
     if (!p || !p->row_ptr) return set_error(LABFM_EINVAL, "null or empty plan");
     if (n_wall < 0 || n_wall > p->N) return set_error(LABFM_EINVAL, "n_wall out of range");
     if (n_wall > 0 && (!wall_nodes || !wall_normal)) return set_error(LABFM_EINVAL, "null pointer argument");
-    if (n_wall > 0 && p->n_ranges > 0) return set_error(LABFM_EINVAL, "walls are not supported with launch ranges");
     if (n_wall > 0 && fault_alloc()) return injected_alloc_error("labfm_plan_set_walls");
     return set_walls(p, n_wall, wall_nodes, wall_normal, nullptr, nullptr, as_stream(stream));
 }
@@ -719,7 +718,6 @@ extern "C" int labfm_plan_set_boundaries(labfm_plan* p, int64_t n, const int32_t
     if (n < 0 || n > p->N) return set_error(LABFM_EINVAL, "number of boundary nodes out of range");
     if (n > 0 && (!nodes || !normal || !kind || !target || !params))
         return set_error(LABFM_EINVAL, "null pointer argument");
-    if (n > 0 && p->n_ranges > 0) return set_error(LABFM_EINVAL, "boundaries are not supported with launch ranges");
     if (n > 0 && (!(params->sigma >= 0.0) || !(params->L > 0.0) || !(params->mach >= 0.0 && params->mach < 1.0) ||
                   !(params->rho0 > 0.0)))
         return set_error(LABFM_EINVAL, "need sigma >= 0, L > 0, 0 <= mach < 1, rho0 > 0");

@@ -1,7 +1,7 @@
 """Boundaries on batched plans (Section 7.1): channels between no-slip walls and open
 boxes with an inflow and an outflow, batched with their boundary nodes given in the
 plan's numbering, evolve bit for bit as each instance does alone, with plain launches
-and inside a captured step graph."""
+and inside a captured step graph, also with a launch range per interior order."""
 import numpy as np
 import pytest
 
@@ -31,7 +31,7 @@ def _dev(a, dtype=torch.float64):
 def _instance(lb, ns, periodic, seed):
     cols, normals = li.channel_walls(ns)
     xy, h, s = _dev(ns.xy), _dev(ns.h), _dev(ns.s)
-    op = lb.build_wall_operator(xy, h, s, ns.Lx, ns.Ly, 6, 4, _dev(cols, torch.int32), _dev(normals),
+    op = lb.build_wall_operator(xy, h, s, ns.Lx, ns.Ly, ns.m, 4, _dev(cols, torch.int32), _dev(normals),
                                 periodic=periodic, check=True)
     q0 = np.zeros((3, ns.N))
     q0[0] = 0.01 * li.smooth_perturbation(ns.xy, kmax=3, seed=seed, Lx=ns.Lx, Ly=ns.Ly)
@@ -81,9 +81,40 @@ def test_batched_channels_match_channels_alone(lb, dtype, graph):
         assert np.all(np.isfinite(part))
         assert np.all(part[1:, d["nodes"]] == 0.0)
         assert np.array_equal(part, alone[k]), k
-    # walls and launch ranges exclude each other
-    with pytest.raises(lb.LabfmError):
-        bp.set_launch_ranges(off, [4, 4], [0, 0])
+    bp.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_batched_channels_of_two_orders_with_launch_ranges(lb, dtype):
+    # interior orders m = 6 and 4, each class its own launch range and shape: every
+    # instance evolves as it does alone in that shape
+    inst = [_instance(lb, li.channel(26, 18, m=4, jitter=0.1, seed=95), (True, False), 21),
+            _instance(lb, li.channel(24, 20, m=6, jitter=0.1, seed=96), (True, False), 25)]
+    shapes = [(2, 0), (4, 2)]
+    for d in inst:
+        d["q0"][1:, d["nodes"]] = 0.0
+    phys = lb.Phys(C * C, MU, 0.5, 0.0)
+    alone, dts = [], []
+    for d, (g, pf) in zip(inst, shapes):
+        plan = lb.Plan(d["row_ptr"], d["col"], d["w"], d["kappa"], d["s"], dtype=dtype)
+        plan.set_walls(_dev(d["nodes"], torch.int32), _dev(d["normal"]))
+        plan.set_launch(g, 128)
+        plan.set_prefetch(pf if dtype == torch.float32 else 0)
+        dt = 0.25 * float(lb.stable_dt(plan, _dev(np.stack([d["q0"][0], d["q0"][1] + 1.0, d["q0"][2]]), dtype),
+                                       d["s"], C, MU).item())
+        dts.append(dt)
+        alone.append(_run(lb, plan, d["q0"], dt, 3, phys, False, dtype))
+        plan.close()
+    bp = lb.Plan.batched(inst, dtype=dtype)
+    off = bp.offsets
+    bp.set_walls(_dev(np.concatenate([d["nodes"] + off[k] for k, d in enumerate(inst)]), torch.int32),
+                 _dev(np.concatenate([d["normal"] for d in inst])))
+    bp.set_dt(dts)
+    bp.set_launch_ranges(off, [g for g, _ in shapes], [pf for _, pf in shapes])
+    for graph in (False, True):
+        got = _run(lb, bp, np.concatenate([d["q0"] for d in inst], axis=1), 0.0, 3, phys, graph, dtype)
+        for k in range(len(inst)):
+            assert np.array_equal(got[:, off[k]:off[k + 1]], alone[k]), (k, graph)
     bp.close()
 
 
