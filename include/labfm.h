@@ -462,9 +462,9 @@ int labfm_plan_set_persistent(labfm_plan* plan, int enable);
  * three lanes of each group issue an L2 prefetch of the three 128-byte segments
  * of the record block they will read `distance` iterations later (in the filter,
  * one lane the 128-byte filter block), if it lies within the node's row.
- * Results do not change.  Rows of fewer than 80 padded entries are
- * never prefetched (measured faster for the long rows of m = 8 and 10, slower for
- * the ~60-entry rows of m = 6).  Plan creation sets 2 for F32 plans and 0 for F64
+ * Results do not change.  Rows of fewer than 48 padded entries are
+ * never prefetched (measured faster for the rows of m = 6, 8 and 10, ~60-220
+ * entries; a lower threshold slowed the ~35-entry rows of m = 4).  Plan creation sets 2 for F32 plans and 0 for F64
  * plans (whose kernels do not prefetch).  Host-only call.
  */
 int labfm_plan_set_prefetch(labfm_plan* plan, int distance);

@@ -407,9 +407,12 @@ PlanView<T> view(const labfm_plan* p) {
 // or from a copy of a contiguous range of its blocks in shared memory.
 // Shortest row (padded entries) whose record stream the stage and filter kernels
 // prefetch: m = 8 and 10 stencils (~100-220 entries, 6 or more iterations of a lane
-// group) gained 4-8 %, m = 6 stencils (~60 entries, 4 iterations) lost 2-3 %,
-// m = 4 (~35) neither.
-constexpr int kPrefetchMinRow = 80;
+// group) gained 4-8 %.  With plain launches and 128-thread blocks m = 6 stencils
+// (~60 entries) lost 2-3 % and m = 4 (~35) neither; with programmatic launches and
+// one-warp blocks the m = 6 step gains 5.7 % (512^2 lattice: 310.2 -> 292.6 us with
+// a threshold of 48 entries instead of 80), while a threshold of 32 leaves m = 6 as
+// at 48 and makes the m = 4 step 1 % slower.
+constexpr int kPrefetchMinRow = 48;
 
 // Programmatic dependent launch (sm_90 and later).  The plain-grid stage, filter,
 // recording-stage, adjoint pass A and B, filter-transpose, pack and unpack launches
