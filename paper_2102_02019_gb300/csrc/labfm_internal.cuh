@@ -193,8 +193,9 @@ int pack_plan(labfm_plan* p, const PlanInput* in, int n_inst, cudaStream_t st);
 // launch-timing hooks (off while a graph is being captured).
 int rk_pack(const labfm_plan* p, const void* Q, void* work, cudaStream_t st);
 int rk_unpack(const labfm_plan* p, void* Q, const void* work, cudaStream_t st);
+// soa_out (or null): the step's filter also stores the new state there (3 x N).
 int rk_one_step(const labfm_plan* p, void* work, double dt, const labfm_phys* ph, bool profile,
-                cudaStream_t st);
+                cudaStream_t st, void* soa_out = nullptr);
 int set_node_dt(labfm_plan* p, const double* dt_inst_host, cudaStream_t st);
 // Pack / unpack a 3 x N structure-of-arrays state into / out of the packed node
 // layout of the step kernels (step.cu).

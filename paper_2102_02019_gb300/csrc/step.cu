@@ -449,8 +449,10 @@ __global__ void k_filter_soa(PlanView<T> P, SoA<T> in, T* __restrict__ out) {
 // true: a grid of (SMs x resident blocks) in which warp w takes the 32/G
 // consecutive nodes starting at w * 32/G, then strides by all the grid's groups,
 // so that no partly filled last wave of blocks idles the GPU at the end.
+// soa (or null): the filtered state is also stored there as 3 x N values (the
+// caller's state at the end of a time-step call, so that no unpack launch follows).
 template <typename T, int G, bool KAHAN, bool PERSIST>
-__global__ void k_filter_aos(PlanView<T> P, const Packed<T>* in, Packed<T>* out) {
+__global__ void k_filter_aos(PlanView<T> P, const Packed<T>* in, Packed<T>* out, T* soa) {
     const int64_t gt = blockIdx.x * int64_t(blockDim.x) + threadIdx.x;
     const int gl = int(gt % G);
     const AoS<T> fld{in};
@@ -469,7 +471,14 @@ __global__ void k_filter_aos(PlanView<T> P, const Packed<T>* in, Packed<T>* out)
         if (i >= 0) fld.get(i, ai, ui, vi);
         T sa, su, sv;
         filter_sums<T, G, KAHAN>(P, fld, i, gl, ai, ui, vi, sa, su, sv);
-        if (i >= 0 && gl == 0) store(out, i, ai + sa, ui + su, vi + sv);
+        if (i >= 0 && gl == 0) {
+            store(out, i, ai + sa, ui + su, vi + sv);
+            if (soa) {
+                soa[i] = ai + sa;
+                soa[P.N + i] = ui + su;
+                soa[2 * P.N + i] = vi + sv;
+            }
+        }
         if (!PERSIST) break;
     }
 }
@@ -720,13 +729,13 @@ int stage_launch(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* qin
 }
 
 template <typename T, int G>
-int filter_aos_g(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaStream_t st) {
+int filter_aos_g(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, T* soa, cudaStream_t st) {
     constexpr bool F = std::is_same<T, float>::value;
     if (p->filter_persistent && p->filter_grid > 0) {
-        k_filter_aos<T, G, F, true><<<p->filter_grid, p->block, 0, st>>>(view<T>(p), in, out);
+        k_filter_aos<T, G, F, true><<<p->filter_grid, p->block, 0, st>>>(view<T>(p), in, out, soa);
     } else {
         const int grid = grid_for(p->N * G, p->block);
-        cudaError_t e = launch_pdl(p, k_filter_aos<T, G, F, false>, grid, p->block, st, view<T>(p), in, out);
+        cudaError_t e = launch_pdl(p, k_filter_aos<T, G, F, false>, grid, p->block, st, view<T>(p), in, out, soa);
         if (e != cudaSuccess) return cuda_error(e, "filter kernel");
     }
     LABFM_LAUNCH_CHECK("filter kernel");
@@ -737,7 +746,7 @@ int filter_aos_g(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaS
 int filter_lanes(const labfm_plan* p) { return p->filter_group ? p->filter_group : p->group; }
 
 template <typename T, int G>
-int filter_range_launch_g(const labfm_plan* p, int r, const Packed<T>* in, Packed<T>* out, cudaStream_t st) {
+int filter_range_launch_g(const labfm_plan* p, int r, const Packed<T>* in, Packed<T>* out, T* soa, cudaStream_t st) {
     PlanView<T> v = view<T>(p);
     v.n_lo = p->range_begin[r];
     v.n_hi = p->range_begin[r + 1];
@@ -745,7 +754,7 @@ int filter_range_launch_g(const labfm_plan* p, int r, const Packed<T>* in, Packe
     if (v.n_hi <= v.n_lo) return LABFM_OK;
     const int grid = grid_for((v.n_hi - v.n_lo) * G, p->block);
     cudaError_t e = launch_pdl(p, k_filter_aos<T, G, std::is_same<T, float>::value, false>, grid, p->block, st, v, in,
-                               out);
+                               out, soa);
     if (e != cudaSuccess) return cuda_error(e, "filter kernel (launch range)");
     LABFM_LAUNCH_CHECK("filter kernel (launch range)");
     return LABFM_OK;
@@ -770,15 +779,15 @@ int stage_ranges(const labfm_plan* p, const Packed<T>* xin, const Packed<T>* qin
 }
 
 template <typename T>
-int filter_ranges(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaStream_t st) {
+int filter_ranges(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaStream_t st, T* soa = nullptr) {
     for (int r = 0; r < p->n_ranges; ++r) {
         int rc = LABFM_EINVAL;
         switch (p->range_group[r]) {
-            case 2: rc = filter_range_launch_g<T, 2>(p, r, in, out, st); break;
-            case 4: rc = filter_range_launch_g<T, 4>(p, r, in, out, st); break;
-            case 8: rc = filter_range_launch_g<T, 8>(p, r, in, out, st); break;
-            case 16: rc = filter_range_launch_g<T, 16>(p, r, in, out, st); break;
-            case 32: rc = filter_range_launch_g<T, 32>(p, r, in, out, st); break;
+            case 2: rc = filter_range_launch_g<T, 2>(p, r, in, out, soa, st); break;
+            case 4: rc = filter_range_launch_g<T, 4>(p, r, in, out, soa, st); break;
+            case 8: rc = filter_range_launch_g<T, 8>(p, r, in, out, soa, st); break;
+            case 16: rc = filter_range_launch_g<T, 16>(p, r, in, out, soa, st); break;
+            case 32: rc = filter_range_launch_g<T, 32>(p, r, in, out, soa, st); break;
         }
         if (rc) return rc;
     }
@@ -786,13 +795,13 @@ int filter_ranges(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cuda
 }
 
 template <typename T>
-int filter_aos(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaStream_t st) {
+int filter_aos(const labfm_plan* p, const Packed<T>* in, Packed<T>* out, cudaStream_t st, T* soa = nullptr) {
     switch (filter_lanes(p)) {
-        case 2: return filter_aos_g<T, 2>(p, in, out, st);
-        case 4: return filter_aos_g<T, 4>(p, in, out, st);
-        case 8: return filter_aos_g<T, 8>(p, in, out, st);
-        case 16: return filter_aos_g<T, 16>(p, in, out, st);
-        case 32: return filter_aos_g<T, 32>(p, in, out, st);
+        case 2: return filter_aos_g<T, 2>(p, in, out, soa, st);
+        case 4: return filter_aos_g<T, 4>(p, in, out, soa, st);
+        case 8: return filter_aos_g<T, 8>(p, in, out, soa, st);
+        case 16: return filter_aos_g<T, 16>(p, in, out, soa, st);
+        case 32: return filter_aos_g<T, 32>(p, in, out, soa, st);
     }
     return set_error(LABFM_EINVAL, "unsupported group size");
 }
@@ -831,7 +840,7 @@ int filter_soa(const labfm_plan* p, const void* in, void* out, cudaStream_t st) 
 //   Q <- unpack(X)
 template <typename T>
 int rk_one_step_t(const labfm_plan* p, void* work, double dt, const labfm_phys* php, bool profile,
-                  cudaStream_t st) {
+                  cudaStream_t st, void* soa_out) {
     const Phys<T> ph{T(php->c2), T(php->mu), T(php->gx), T(php->gy)};
     Packed<T>* P = static_cast<Packed<T>*>(work);
     Packed<T>* X = P + p->N;
@@ -854,7 +863,8 @@ int rk_one_step_t(const labfm_plan* p, void* work, double dt, const labfm_phys* 
     }
     prof_end(pm, evs, st);
     const int ev = timed ? prof_begin(pm, kProfFilter, st) : -1;
-    if ((rc = p->n_ranges ? filter_ranges<T>(p, P, X, st) : filter_aos<T>(p, P, X, st))) return rc;
+    T* soa = static_cast<T*>(soa_out);
+    if ((rc = p->n_ranges ? filter_ranges<T>(p, P, X, st, soa) : filter_aos<T>(p, P, X, st, soa))) return rc;
     prof_end(pm, ev, st);
     return LABFM_OK;
 }
@@ -1005,9 +1015,9 @@ int rk_unpack(const labfm_plan* p, void* Q, const void* work, cudaStream_t st) {
 }
 
 int rk_one_step(const labfm_plan* p, void* work, double dt, const labfm_phys* ph, bool profile,
-                cudaStream_t st) {
-    return p->dtype == LABFM_F32 ? rk_one_step_t<float>(p, work, dt, ph, profile, st)
-                                 : rk_one_step_t<double>(p, work, dt, ph, profile, st);
+                cudaStream_t st, void* soa_out) {
+    return p->dtype == LABFM_F32 ? rk_one_step_t<float>(p, work, dt, ph, profile, st, soa_out)
+                                 : rk_one_step_t<double>(p, work, dt, ph, profile, st, soa_out);
 }
 
 namespace {
@@ -1069,12 +1079,13 @@ int launch_rk_steps(const labfm_plan* p, void* Q, void* work, double dt, int nst
     int rc;
     if ((rc = rk_pack(p, Q, work, st))) return rc;
     const int every = p->dev_status ? p->check_every : 0;
+    // the last step's filter also stores the state into Q (no unpack launch)
     for (int step = 0; step < nsteps; ++step) {
-        if ((rc = rk_one_step(p, work, dt, ph, true, st))) return rc;
+        if ((rc = rk_one_step(p, work, dt, ph, true, st, step + 1 == nsteps ? Q : nullptr))) return rc;
         if (every > 0 && ((step + 1) % every == 0 || step + 1 == nsteps))
             if ((rc = check_finite(p, work, st))) return rc;
     }
-    return rk_unpack(p, Q, work, st);
+    return LABFM_OK;
 }
 
 int filter_persistent_grid(const labfm_plan* p) {
