@@ -46,7 +46,7 @@ PROFILE_EVERY = 10  # timed steps per step whose launches carry CUDA events
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=None)
@@ -105,7 +105,7 @@ def max_over_ranks(x, world):
 class ClockSampler:
     """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
 
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -130,7 +130,7 @@ class ClockSampler:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
                 stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -146,32 +146,53 @@ class ClockSampler:
                 self.proc.kill()
             self.f.close()
 
-    def summary(self):
+    @staticmethod
+    def _epoch(stamp):
+        """nvidia-smi's local-time timestamp ("2026/12/04 08:47:21.123") as epoch seconds."""
+        import datetime
+        try:
+            return datetime.datetime.strptime(stamp, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
+    def summary(self, window=None):
+        """Median SM clock, maximum clock and throttle reasons over every sample of the
+        sampler's lifetime; with window = (t0, t1) (time.time() around the timed
+        region) also the samples inside it (`timed_window`)."""
         if self.proc is None or not os.path.exists(self.path):
             if not self.keep and os.path.exists(self.path):
                 os.remove(self.path)
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         sm, smax, reasons = [], None, set()
+        sm_w, reasons_w = [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax = float(parts[2])
+                mhz = float(parts[2])
+                smax = float(parts[3])
             except ValueError:
                 continue
-            for k, nm in enumerate(names):
-                if parts[5 + k].lower().startswith("active"):
-                    reasons.add(nm)
+            active = {nm for k, nm in enumerate(names) if parts[6 + k].lower().startswith("active")}
+            sm.append(mhz)
+            reasons |= active
+            t = self._epoch(parts[0])
+            if window is not None and t is not None and window[0] <= t <= window[1]:
+                sm_w.append(mhz)
+                reasons_w |= active
         if not self.keep:
             try:
                 os.remove(self.path)
             except OSError:
                 pass
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+               "reasons": sorted(reasons), "samples": len(sm)}
+        if window is not None:
+            out["timed_window"] = {"samples": len(sm_w), "sm_mhz": statistics.median(sm_w) if sm_w else None,
+                                   "reasons": sorted(reasons_w), "seconds": window[1] - window[0]}
+        return out
 
 
 # ---------------------------------------------------------------- oracle baseline
@@ -960,6 +981,7 @@ def run_ours(args, world, rank, local):
     q0 = torch.tensor(li.tgv_fields(ns.xy, C), device=dev)
 
     tuned_shape = {}
+    timed_window = {}
 
     def measure(dtype, steps, warmup):
         plan = lb.Plan(row_ptr, col, wb["w"], wb["kappa"], s, dtype=dtype)
@@ -984,10 +1006,12 @@ def run_ours(args, world, rank, local):
         a, b = ev(), ev()
         barrier(world)
         torch.cuda.synchronize()
+        t_wall0 = time.time()
         a.record()
         lb.rk_step(plan, Q, dt, steps, phys, work=work)
         b.record()
         torch.cuda.synchronize()
+        timed_window[dtype] = (t_wall0, time.time())
         barrier(world)
         ms = a.elapsed_time(b)
         prof = plan.read_profile()
@@ -1000,7 +1024,7 @@ def run_ours(args, world, rank, local):
     # FP32 headline
     with ClockSampler(local) as clk:
         plan32, Q32, dt32, ms32, prof32, shape32, fin32, work32 = measure(torch.float32, args.steps, args.warmup)
-    clocks = clk.summary()
+    clocks = clk.summary(window=timed_window[torch.float32])
     ms32 = max_over_ranks(ms32, world)
     value = 4.0 * N * args.steps * world / (ms32 * 1e-3)
 
