@@ -39,11 +39,12 @@ design notes):
 * Periodic minimum image: dx = x_j - x_i; if dx > L/2: dx -= L; elif dx < -L/2: dx += L.
   Self is excluded from the stencil (it contributes exactly zero).
 
-Parity pins: see tests/test_oracle_*.py.  Parity unpinned: the absolute weight
-values when a stencil has more nodes than unknowns depend on the Wendland /
-Hermite reading above, which the paper fixes only by reference; the tests pin
-everything that the paper and the mathematics fix (reproduction, unisolvent
-finite-difference limits, symmetry, convergence order, Taylor-Green decay).
+Parity pins: see tests/test_oracle_*.py.  When a stencil has more nodes than
+unknowns the weights follow from the Wendland / Hermite reading above (which the
+paper fixes only by reference); under that reading they are pinned by lying in the
+span of the node's ABFs together with reproducing the monomials, besides the
+unisolvent finite-difference limits, symmetry, convergence order and the
+Taylor-Green decay.
 """
 from __future__ import annotations
 

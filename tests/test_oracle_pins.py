@@ -245,6 +245,60 @@ def test_polynomial_reproduction(m):
             assert np.all(np.abs(got - C[q]) <= 1e-10 * scale), (op, a, b)
 
 
+def _abf_matrix(dx, dy, h, m, x_scale=math.sqrt(2.0), rbf=None):
+    """The ABFs of Section 3 built here from numpy's physicists' Hermite series:
+    W^ab_j = psi(|r_j|/h) H_a(x_j/(h x_scale)) H_b(y_j/(h x_scale)), 1 <= a + b <= m,
+    psi the Wendland C2 function (support 2h), one column per (a, b)."""
+    from numpy.polynomial import hermite as H
+    q = np.hypot(dx, dy) / h
+    psi = np.where(q < 2.0, (1.0 - q / 2.0) ** 4 * (2.0 * q + 1.0), 0.0) if rbf is None else rbf(q)
+    cols = []
+    for k in range(1, m + 1):
+        for b in range(k + 1):
+            a = k - b
+            ca = np.zeros(a + 1)
+            ca[a] = 1.0
+            cb = np.zeros(b + 1)
+            cb[b] = 1.0
+            cols.append(psi * H.hermval(dx / (h * x_scale), ca) * H.hermval(dy / (h * x_scale), cb))
+    return np.stack(cols, axis=1)
+
+
+@pytest.mark.parametrize("m", [4, 6, 8])
+def test_weights_lie_in_the_span_of_the_hermite_wendland_abfs(m):
+    """eq. w_abf: every weight vector of a node is a combination of its ABFs, which
+    with the reproduction conditions (eq. lsys, pinned above) fixes the weights when a
+    stencil has more nodes than unknowns.  The ABFs are built here independently of
+    the oracle (numpy's Hermite series, the textbook Wendland function); ABFs with a
+    planted mistake (the argument scaled by h instead of h sqrt 2, or another radial
+    function) do not contain the oracle's weights."""
+    hs = {int(a): float(b) for a, b in golden("hs_convergence.txt")}[m]
+    ns = li.tgv_lattice(20, m=m, h_over_s=hs, jitter=0.3, seed=13)
+    rows = np.arange(5, ns.N, 53)
+    rp, col = o.neighbours(ns.xy, ns.h, ns.Lx, ns.Ly, rows=rows)
+    out = o.build_weights(ns.xy, ns.h, ns.s, rp, col, m, ns.Lx, ns.Ly, rows=rows)
+    assert out["ok"].all()
+    ri = o.row_index(rp)
+    dx, dy = o.offsets(ns.xy, rows[ri], col, ns.Lx, ns.Ly)
+    n = o.n_unknowns(m)
+
+    def worst_residual(**abf):
+        worst = 0.0
+        for r, i in enumerate(rows):
+            sl = slice(rp[r], rp[r + 1])
+            A = _abf_matrix(dx[sl], dy[sl], ns.h[i], m, **abf)
+            assert A.shape == (rp[r + 1] - rp[r], n) and A.shape[0] > n
+            for d in range(len(o.OPS)):
+                wv = out["w"][d][sl]
+                coef, *_ = np.linalg.lstsq(A, wv, rcond=None)
+                worst = max(worst, np.linalg.norm(A @ coef - wv) / np.linalg.norm(wv))
+        return worst
+
+    assert worst_residual() <= 1e-8
+    assert worst_residual(x_scale=1.0) > 1e-3
+    assert worst_residual(rbf=lambda q: np.where(q < 2.0, (1.0 - q / 2.0) ** 4, 0.0)) > 1e-3
+
+
 def test_laplacian_is_sum_of_second_derivatives_on_test_function():
     # eq. p6 test function: the operator with C^L equals w^xx + w^yy (linearity of eq. lsys)
     ns = li.tgv_lattice(16, m=6, h_over_s=1.8, jitter=0.3, seed=3)
